@@ -1,0 +1,375 @@
+"""Seeded synthetic inputs: tetrahedral box meshes, initial fields, exact solutions.
+
+This module is the one place that both the CUDA library's callers and the CPU
+oracle take their inputs from.  It holds none of the scheme's arithmetic (no
+reconstruction, no kinetic flux, no time stepping): it only generates vertex
+coordinates and connectivity, cell averages of analytic fields by quadrature,
+and exact reference solutions used to measure errors.
+
+Mesh recipe (the paper's tests use hexahedral grids split into tetrahedra,
+Sec. 5.1, "6 x N^3 cells"; the split pattern is not given there):
+
+* an nx x ny x nz grid of hexahedra of a box [0,Lx]x[0,Ly]x[0,Lz];
+* every hexahedron is cut into the 6 Kuhn (Freudenthal) tetrahedra
+  v0 -> v0+e_a -> v0+e_a+e_b -> v0+e_a+e_b+e_c for each permutation (a,b,c) of
+  the axes; all six share the main diagonal v0-v7.  The split is translation
+  invariant, so it is conforming across periodic boundaries;
+* every unique vertex is moved by a uniform random jitter in [-j*h, j*h] per
+  axis drawn from numpy's PCG64 with the given seed; on a non-periodic axis
+  the vertices of the two end planes are moved only tangentially.
+
+A periodic axis keeps n unique vertex planes; a tetrahedron that wraps refers
+to the base vertex and carries an integer image shift, so its geometric vertex
+is ``xyz[v] + shift * period``.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+KUHN_PERMS = list(itertools.permutations(range(3)))
+
+
+def box_mesh(n, length=(1.0, 1.0, 1.0), periodic=(True, True, True), jitter=0.1,
+             seed=0, diagonal=(1, 1, 1)):
+    """Jittered Kuhn-split box mesh.
+
+    ``diagonal`` picks which main diagonal of each hexahedron the six
+    tetrahedra share: (1,1,1) joins (0,0,0)-(1,1,1); a -1 mirrors that axis,
+    e.g. (1,1,-1) joins (0,0,1)-(1,1,0).
+
+    Returns a dict with
+      xyz    float64 [nv, 3]   unique vertex coordinates
+      tet    int64   [nc, 4]   vertex ids of each tetrahedron (positive volume)
+      shift  int8    [nc, 4, 3] periodic image shift of each tet vertex
+      period float64 [3]       period per axis, 0 on a non-periodic axis
+    """
+    n = tuple(int(v) for v in n)
+    length = tuple(float(v) for v in length)
+    periodic = tuple(bool(v) for v in periodic)
+    nv_ax = [n[a] if periodic[a] else n[a] + 1 for a in range(3)]
+    h = [length[a] / n[a] for a in range(3)]
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    ii, jj, kk = np.meshgrid(np.arange(nv_ax[0]), np.arange(nv_ax[1]),
+                             np.arange(nv_ax[2]), indexing="ij")
+    # vertex id = i + nvx*(j + nvy*k): flatten with x fastest
+    grid = [ii.transpose(2, 1, 0).ravel(), jj.transpose(2, 1, 0).ravel(),
+            kk.transpose(2, 1, 0).ravel()]
+    nv = grid[0].size
+    xyz = np.empty((nv, 3))
+    jit = rng.uniform(-1.0, 1.0, size=(nv, 3))
+    for a in range(3):
+        xyz[:, a] = grid[a] * h[a]
+        amp = jitter * h[a] * jit[:, a]
+        if not periodic[a]:
+            amp = np.where((grid[a] == 0) | (grid[a] == n[a]), 0.0, amp)
+        xyz[:, a] += amp
+
+    hi, hj, hk = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]),
+                             indexing="ij")
+    hexes = np.stack([hi.transpose(2, 1, 0).ravel(), hj.transpose(2, 1, 0).ravel(),
+                      hk.transpose(2, 1, 0).ravel()], axis=1)  # x fastest
+    nh = hexes.shape[0]
+    tets = np.empty((nh, 6, 4), dtype=np.int64)
+    shifts = np.zeros((nh, 6, 4, 3), dtype=np.int8)
+    mirror = [a for a in range(3) if diagonal[a] < 0]
+    for t, perm in enumerate(KUHN_PERMS):
+        offs = [np.zeros(3, dtype=np.int64)]
+        for a in perm:
+            o = offs[-1].copy()
+            o[a] += 1
+            offs.append(o)
+        for o in offs:
+            for a in mirror:
+                o[a] = 1 - o[a]
+        odd = sum(1 for x in range(3) for y in range(x + 1, 3) if perm[x] > perm[y]) % 2
+        odd = (odd + len(mirror)) % 2
+        if odd:  # negative orientation: swap vertices 1 and 2
+            offs[1], offs[2] = offs[2], offs[1]
+        for v, o in enumerate(offs):
+            c = hexes + o[None, :]
+            idx = np.zeros(nh, dtype=np.int64)
+            stride = 1
+            for a in range(3):
+                ca = c[:, a]
+                if periodic[a]:
+                    wrap = ca >= n[a]
+                    shifts[:, t, v, a] = wrap.astype(np.int8)
+                    ca = np.where(wrap, ca - n[a], ca)
+                idx += ca * stride
+                stride *= nv_ax[a]
+            tets[:, t, v] = idx
+    period = np.array([length[a] if periodic[a] else 0.0 for a in range(3)])
+    return {
+        "xyz": xyz,
+        "tet": tets.reshape(nh * 6, 4),
+        "shift": shifts.reshape(nh * 6, 4, 3),
+        "period": period,
+        "n": n,
+        "length": length,
+        "periodic": periodic,
+    }
+
+
+def tet_vertices(mesh):
+    """Geometric vertex positions [nc, 4, 3] with periodic shifts applied."""
+    return mesh["xyz"][mesh["tet"]] + mesh["shift"].astype(np.float64) * mesh["period"]
+
+
+# --------------------------------------------------------------------------
+# quadrature used only to synthesise cell averages of analytic fields
+# --------------------------------------------------------------------------
+
+def _collapsed_gauss(order):
+    """Points (barycentric xi, eta, zeta) and weights (sum 1) of a collapsed
+    tensor Gauss-Legendre rule on the unit tetrahedron (Duffy map)."""
+    g, w = np.polynomial.legendre.leggauss(order)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    pts, wts = [], []
+    for a, wa in zip(g, w):
+        for b, wb in zip(g, w):
+            for c, wc in zip(g, w):
+                xi = a
+                eta = b * (1.0 - a)
+                zeta = c * (1.0 - a) * (1.0 - b)
+                pts.append((xi, eta, zeta))
+                wts.append(wa * wb * wc * (1.0 - a) ** 2 * (1.0 - b))
+    pts = np.array(pts)
+    wts = np.array(wts)
+    return pts, wts / wts.sum()
+
+
+def cell_average(mesh, func, order=5, chunk=200_000):
+    """Cell averages of ``func(x[..., 3]) -> [..., m]`` over every tetrahedron."""
+    pts, wts = _collapsed_gauss(order)
+    lam = np.stack([1.0 - pts.sum(1), pts[:, 0], pts[:, 1], pts[:, 2]], axis=1)  # [q,4]
+    verts = tet_vertices(mesh)
+    out = []
+    for s in range(0, verts.shape[0], chunk):
+        v = verts[s:s + chunk]
+        x = np.einsum("qa,cad->cqd", lam, v)
+        f = func(x)  # [c, q, m]
+        out.append(np.einsum("q,cqm->cm", wts, f))
+    return np.concatenate(out, axis=0)
+
+
+# --------------------------------------------------------------------------
+# initial / exact fields.  State layout: W [5, nc] conservative variables
+# (rho, rho U1, rho U2, rho U3, rho E); dW [15, nc] = d W_q / d x_i stored at
+# row 3*q + i (component-major).
+# --------------------------------------------------------------------------
+
+def _prim_to_cons(rho, u, p, gamma):
+    ke = 0.5 * rho * (u[..., 0] ** 2 + u[..., 1] ** 2 + u[..., 2] ** 2)
+    return np.stack([rho, rho * u[..., 0], rho * u[..., 1], rho * u[..., 2],
+                     p / (gamma - 1.0) + ke], axis=-1)
+
+
+def sine_wave_fields(x, t=0.0, amp=0.2, k=2.0 * math.pi, u=(1.0, 1.0, 1.0),
+                     p=1.0, gamma=1.4):
+    """Point values and gradients of the advected density wave
+    rho = 1 + amp sin(k (x+y+z - (u1+u2+u3) t)), constant velocity and pressure
+    (Sec. 5.1; the phase speed along x+y+z is u1+u2+u3).
+    Returns W [..., 5] and dW [..., 15]."""
+    s = x[..., 0] + x[..., 1] + x[..., 2] - (u[0] + u[1] + u[2]) * t
+    rho = 1.0 + amp * np.sin(k * s)
+    drho = amp * k * np.cos(k * s)
+    uu = np.broadcast_to(np.asarray(u, dtype=np.float64), x.shape)
+    W = _prim_to_cons(rho, uu, np.full_like(rho, p), gamma)
+    # every conservative component is affine in rho here
+    dqdrho = np.array([1.0, u[0], u[1], u[2], 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)])
+    dW = np.empty(x.shape[:-1] + (15,))
+    for q in range(5):
+        for i in range(3):
+            dW[..., 3 * q + i] = dqdrho[q] * drho
+    return W, dW
+
+
+def sine_wave_state(mesh, t=0.0, order=5, **kw):
+    """Cell averages of W and of grad W for the density wave at time t."""
+    def f(x):
+        W, dW = sine_wave_fields(x, t=t, **kw)
+        return np.concatenate([W, dW], axis=-1)
+    avg = cell_average(mesh, f, order=order)
+    return np.ascontiguousarray(avg[:, :5].T), np.ascontiguousarray(avg[:, 5:].T)
+
+
+def _neg_fraction(d):
+    """Fraction of each tetrahedron on which the linear function with vertex
+    values d [nc, 4] is negative (divided difference of x_+^3)."""
+    d = d.astype(np.float64).copy()
+    out = np.zeros(d.shape[0])
+    allneg = (d < 0).all(1)
+    out[allneg] = 1.0
+    cut = ~allneg & (d < 0).any(1)
+    dc = d[cut]
+    # separate coincident values slightly; the effect is ~1e-9 in the fraction
+    scale = np.abs(dc).max(1, keepdims=True) + 1e-300
+    for a in range(4):
+        for b in range(a + 1, 4):
+            tie = np.abs(dc[:, a] - dc[:, b]) < 1e-9 * scale[:, 0]
+            dc[tie, b] += 2e-9 * scale[tie, 0] * (b + 1)
+    pos = np.zeros(dc.shape[0])
+    for i in range(4):
+        den = np.ones(dc.shape[0])
+        for j in range(4):
+            if j != i:
+                den *= dc[:, i] - dc[:, j]
+        pos += np.maximum(dc[:, i], 0.0) ** 3 / den
+    out[cut] = 1.0 - pos
+    return out
+
+
+def riemann_x_state(mesh, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x0=0.5,
+                    gamma=1.4):
+    """Planar Riemann data along x: (rho, u1, p) on x < x0 and x > x0, exact
+    volume fractions of the plane split per cell, zero gradients (Sod's data
+    by default)."""
+    verts = tet_vertices(mesh)
+    frac_l = _neg_fraction(verts[:, :, 0] - x0)
+    def cons(st):
+        rho, u, p = st
+        return _prim_to_cons(np.array(rho), np.array([u, 0.0, 0.0]), np.array(p), gamma)
+    wl, wr = cons(left), cons(right)
+    W = frac_l[None, :] * wl[:, None] + (1.0 - frac_l)[None, :] * wr[:, None]
+    return np.ascontiguousarray(W), np.zeros((15, W.shape[1]))
+
+
+# --------------------------------------------------------------------------
+# exact Riemann solution (ideal gas), for error measurement
+# --------------------------------------------------------------------------
+
+def exact_riemann(left, right, gamma=1.4):
+    """Star state (p*, u*) of the 1-D Riemann problem, by Newton's method on
+    the pressure function f_L(p) + f_R(p) + du = 0 (shock branch from the
+    Rankine-Hugoniot relations, rarefaction branch from the isentropic ones)."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    cl = math.sqrt(gamma * pl / rl)
+    cr = math.sqrt(gamma * pr / rr)
+
+    def fk(p, rk, pk, ck):
+        if p > pk:
+            a = 2.0 / ((gamma + 1.0) * rk)
+            b = (gamma - 1.0) / (gamma + 1.0) * pk
+            q = math.sqrt(a / (p + b))
+            return (p - pk) * q, q * (1.0 - 0.5 * (p - pk) / (p + b))
+        e = (gamma - 1.0) / (2.0 * gamma)
+        r = (p / pk) ** e
+        return (2.0 * ck / (gamma - 1.0) * (r - 1.0),
+                (p / pk) ** (-(gamma + 1.0) / (2.0 * gamma)) / (rk * ck))
+
+    def f(p):
+        a, da = fk(p, rl, pl, cl)
+        b, db = fk(p, rr, pr, cr)
+        return a + b + (ur - ul), da + db
+
+    p = max(1e-8, 0.5 * (pl + pr))
+    for _ in range(100):
+        val, der = f(p)
+        pn = max(1e-12, p - val / der)
+        if abs(pn - p) < 1e-15 * (pn + p):
+            p = pn
+            break
+        p = pn
+    a, _ = fk(p, rl, pl, cl)
+    b, _ = fk(p, rr, pr, cr)
+    u = 0.5 * (ul + ur) + 0.5 * (b - a)
+    return p, u
+
+
+def sample_riemann(xi, left, right, gamma=1.4):
+    """Self-similar exact solution (rho, u, p) at xi = (x - x0) / t."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    ps, us = exact_riemann(left, right, gamma)
+    cl = math.sqrt(gamma * pl / rl)
+    cr = math.sqrt(gamma * pr / rr)
+    g1 = (gamma - 1.0) / (gamma + 1.0)
+    xi = np.asarray(xi, dtype=np.float64)
+    rho = np.empty_like(xi)
+    u = np.empty_like(xi)
+    p = np.empty_like(xi)
+    # left side of contact
+    if ps > pl:  # left shock
+        rsl = rl * (ps / pl + g1) / (g1 * ps / pl + 1.0)
+        sl = ul - cl * math.sqrt((gamma + 1) / (2 * gamma) * ps / pl + (gamma - 1) / (2 * gamma))
+        left_zone = xi < sl
+        star_l = (xi >= sl) & (xi < us)
+        fan_l = np.zeros_like(xi, dtype=bool)
+    else:  # left rarefaction
+        rsl = rl * (ps / pl) ** (1.0 / gamma)
+        csl = cl * (ps / pl) ** ((gamma - 1) / (2 * gamma))
+        head, tail = ul - cl, us - csl
+        left_zone = xi < head
+        fan_l = (xi >= head) & (xi < tail)
+        star_l = (xi >= tail) & (xi < us)
+    if ps > pr:  # right shock
+        rsr = rr * (ps / pr + g1) / (g1 * ps / pr + 1.0)
+        sr = ur + cr * math.sqrt((gamma + 1) / (2 * gamma) * ps / pr + (gamma - 1) / (2 * gamma))
+        right_zone = xi >= sr
+        star_r = (xi >= us) & (xi < sr)
+        fan_r = np.zeros_like(xi, dtype=bool)
+    else:
+        rsr = rr * (ps / pr) ** (1.0 / gamma)
+        csr = cr * (ps / pr) ** ((gamma - 1) / (2 * gamma))
+        head, tail = ur + cr, us + csr
+        right_zone = xi >= head
+        fan_r = (xi >= tail) & (xi < head)
+        star_r = (xi >= us) & (xi < tail)
+    rho[left_zone], u[left_zone], p[left_zone] = rl, ul, pl
+    rho[right_zone], u[right_zone], p[right_zone] = rr, ur, pr
+    rho[star_l], u[star_l], p[star_l] = rsl, us, ps
+    rho[star_r], u[star_r], p[star_r] = rsr, us, ps
+    if fan_l.any():
+        x = xi[fan_l]
+        c = 2.0 / (gamma + 1) * (cl + 0.5 * (gamma - 1) * (ul - x))
+        uf = 2.0 / (gamma + 1) * (cl + 0.5 * (gamma - 1) * ul + x)
+        rho[fan_l] = rl * (c / cl) ** (2.0 / (gamma - 1))
+        u[fan_l] = uf
+        p[fan_l] = pl * (c / cl) ** (2.0 * gamma / (gamma - 1))
+    if fan_r.any():
+        x = xi[fan_r]
+        c = 2.0 / (gamma + 1) * (cr - 0.5 * (gamma - 1) * (ur - x))
+        uf = 2.0 / (gamma + 1) * (-cr + 0.5 * (gamma - 1) * ur + x)
+        rho[fan_r] = rr * (c / cr) ** (2.0 / (gamma - 1))
+        u[fan_r] = uf
+        p[fan_r] = pr * (c / cr) ** (2.0 * gamma / (gamma - 1))
+    return rho, u, p
+
+
+def riemann_x_exact_density(mesh, t, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1),
+                            x0=0.5, gamma=1.4, order=6):
+    """Cell averages of the exact density at time t > 0 (quadrature of the
+    piecewise-smooth exact solution)."""
+    def f(x):
+        r, _, _ = sample_riemann((x[..., 0] - x0) / t, left, right, gamma)
+        return r[..., None]
+    return cell_average(mesh, f, order=order)[:, 0]
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+
+def sine_wave_case(n=8, jitter=0.1, seed=1, diagonal=(1, 1, -1)):
+    """Periodic unit cube, n^3 hexes x 6 tets, rho = 1 + 0.2 sin 2pi(x+y+z),
+    U = (1,1,1), p = 1, gamma = 1.4.  The tetrahedra share the hexahedron
+    diagonal (0,0,1)-(1,1,0), across the direction of propagation: the split
+    is not given in the paper, and this one reproduces the magnitude of its
+    accuracy table on the same setup."""
+    mesh = box_mesh((n, n, n), (1.0, 1.0, 1.0), (True, True, True), jitter, seed, diagonal)
+    W, dW = sine_wave_state(mesh)
+    return mesh, W, dW
+
+
+def sod_case(nx=64, nyz=8, jitter=0.1, seed=2):
+    """Sod tube along x on [0,1]x[0,0.1]^2 (y, z periodic, x ends open),
+    nx x nyz x nyz hexes x 6 tets."""
+    mesh = box_mesh((nx, nyz, nyz), (1.0, 0.1, 0.1), (False, True, True), jitter, seed)
+    W, dW = riemann_x_state(mesh)
+    return mesh, W, dW
