@@ -1,0 +1,335 @@
+"""Benchmark of one two-stage step of the compact gas-kinetic scheme.
+
+Workload: the Sod shock tube on [0,1]x[0,0.1]^2, 64 x 8 x 8 hexahedra x 6
+Kuhn tetrahedra = 24,576 cells (49,280 faces), jittered 10%, y and z
+periodic, two-step multi-resolution WENO, full kinetic flux, CFL 0.5.  A
+"step" is one pass of the whole hot path: time-step minimum, two stages of
+(reconstruction step 1, reconstruction step 2, face flux, cell update).
+
+Metric: Mcell-stage updates/s = cells x 2 stages x steps / device time.
+``value`` is the FP32-bulk path; the FP64 path is reported beside it, both
+with their L1 density error against the exact Riemann solution at t = 0.2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(the scheme has no data exchange between independent cases): weak scaling,
+max time over ranks.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2102_01366_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Mcell-stage updates/s"
+WORKLOAD = "sod_tube_64x8x8_hex_x6_tets_24576_cells_weno3_cfl0.5"
+CPU_SAMPLE = dict(nx=16, nyz=4)  # same recipe, 1,536 cells: oracle per-cell cost is size independent
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# per-launch algorithmic work of the dominant kernel (face flux); see the design doc
+FLUX_FLOPS_PER_GP = {"fp32": None, "fp64": None}
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(torch, value, ws):
+    if ws == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_device(torch, s, steps, warmup, flush):
+    """Per-step CUDA-event timing on the state's stream, L2 flushed between steps."""
+    for _ in range(warmup):
+        s.step(1)
+    s.sync()
+    ms = 0.0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(s.stream):
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(s.stream)
+            s.step(1)
+            ev[i][1].record(s.stream)
+    s.sync()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        ms += a.elapsed_time(b)
+    return ms / steps
+
+
+def l1_at(torch, gks, mesh, W0, dW0, precision, t_end):
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+    s.init(W0, dW0)
+    t = s.run(t_end=t_end, chunk=64)
+    W, _ = s.get()
+    exact = I.riemann_x_exact_density(mesh, t)
+    vol = g.geometry()["vol"]
+    return float((vol * np.abs(W[0].cpu().numpy() - exact)).sum() / vol.sum()), W.cpu().numpy()
+
+
+def cpu_baseline(max_seconds=20.0, max_steps=40):
+    """The FP64 oracle as it stands, single thread, on a bounded sample."""
+    from oracle import oracle as O
+    mesh, W, dW = I.sod_case(**CPU_SAMPLE)
+    om = O.Mesh(mesh)
+    p = O.params(weno=1, cfl=0.5)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (time.perf_counter() - t0) < max_seconds:
+        W, dW, _ = om.step(p, W, dW)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": om.nc * 2 * n / el / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the Sod tube at 16x4x4 hexes x 6 = %d cells (same recipe, 1/16 size), "
+                      "FP64 C oracle, 1 thread" % (n, om.nc)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    mesh, W, dW = I.sod_case(**CPU_SAMPLE)
+    om = O.Mesh(mesh)
+    p = O.params(weno=1, cfl=0.5)
+    for _ in range(args.warmup):
+        W, dW, _ = om.step(p, W, dW)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, dW, _ = om.step(p, W, dW)
+    el = time.perf_counter() - t0
+    v = om.nc * 2 * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1000 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_cells": om.nc, "cells": 24576},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "each step one oracle step of the Sod tube at 16x4x4 hexes x 6 = "
+                                       "%d cells (same recipe, 1/16 size)" % om.nc},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="only the FP32 timed steps (for profilers); no accuracy, e2e or CPU legs")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of --profile-case")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2102_01366_gb300 import _build, gks
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    gks.lib()
+
+    mesh, W0, dW0 = I.sod_case()
+    g = gks.Mesh(mesh)
+    nc = g.nc
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    if args.profile_case:
+        prec = 1 if args.precision == "fp32" else 0
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
+        s.init(W0, dW0)
+        ms = time_device(torch, s, args.steps, args.warmup, flush)
+        if rank == 0:
+            print(json.dumps({"profile_case": WORKLOAD, "precision": args.precision, "ms_per_step": ms}))
+        return
+
+    results = {}
+    for name, prec in (("fp64", 0), ("fp32", 1)):
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
+        s.init(W0, dW0)
+        if name == "fp32":
+            with ClockSampler(local) as clk:
+                ms = time_device(torch, s, args.steps, args.warmup, flush)
+            clocks = clk.summary()
+        else:
+            ms = time_device(torch, s, max(3, args.steps // 5), args.warmup, flush)
+        ms = _barrier_max(torch, ms, ws)
+        # kernel breakdown: same steps, kernel by kernel, events between launches
+        s.init(W0, dW0)
+        for _ in range(args.warmup):
+            s.step(1)
+        s.sync()
+        br = s.step_timed(max(3, args.steps // 5 if name == "fp64" else args.steps))
+        results[name] = {"ms": ms, "breakdown": br}
+    # equal-L1 comparison at t = 0.2 (untimed)
+    l1_64, W64 = l1_at(torch, gks, mesh, W0, dW0, 0, 0.2)
+    l1_32, W32 = l1_at(torch, gks, mesh, W0, dW0, 1, 0.2)
+    fp32_vs_fp64 = max(np.abs(W32[q] - W64[q]).max() / np.abs(W64[q]).max() for q in range(5))
+
+    # end to end through the host-buffer entry point (pinned buffers, copies timed)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    Wh = torch.tensor(W0).pin_memory()
+    dWh = torch.tensor(dW0).pin_memory()
+    for _ in range(args.warmup):
+        s.step_host(Wh, dWh, nsteps=1)
+    Wh.copy_(torch.tensor(W0))
+    dWh.copy_(torch.tensor(dW0))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step_host(Wh, dWh, nsteps=1)
+    e2e_s = _barrier_max(torch, (time.perf_counter() - t0) / args.steps, ws)
+
+    ms32 = results["fp32"]["ms"]
+    value = ws * nc * 2 / (ms32 / 1000.0) / 1e6
+    value64 = ws * nc * 2 / (results["fp64"]["ms"] / 1000.0) / 1e6
+    br = results["fp32"]["breakdown"]
+    flux_ms = (br["flux1"][0] + br["flux2"][0]) / max(1, br["flux1"][1] + br["flux2"][1])
+    total_ms = sum(v[0] for v in br.values())
+    launches_per_step = sum(v[1] for v in br.values()) / max(1, br["dt"][1]) + 1  # + control kernel
+    gps = 3 * g.nf
+    peaks, peak_src = _peaks()
+    clk_mhz = SM_MAX_MHZ
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
+    fpg = FLUX_FLOPS_PER_GP["fp32"]
+    if fpg:
+        achieved = fpg * gps / (flux_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_flux<float>",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % clk_mhz,
+                "flux_ms_per_launch": flux_ms, "flux_share_of_step": sum(
+                    br[k][0] for k in ("flux1", "flux2")) / total_ms}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": "k_flux<float>", "flux_ms_per_launch": flux_ms,
+                "flux_share_of_step": sum(br[k][0] for k in ("flux1", "flux2")) / total_ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": nc, "faces": g.nf, "precision": "fp32-bulk",
+                   "l2": "flushed between timed steps (512 MB write)", "graph": "one CUDA graph per step",
+                   "replicas": ws},
+        "fp64": {"value": value64, "ms_per_step": results["fp64"]["ms"], "dtype": "f64"},
+        "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32,
+                          "fp32_vs_fp64_rel": fp32_vs_fp64},
+        "fp32_speedup_over_fp64": value / value64,
+        "kernel_ms_per_step": {k: v[0] / max(1, br["dt"][1]) for k, v in br.items()},
+        "roofline": roof,
+        "e2e": {"value": ws * nc * 2 / e2e_s / 1e6, "unit": METRIC,
+                "h2d_bytes_per_step": 20 * nc * 8, "d2h_bytes_per_step": 20 * nc * 8},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clocks,
+        "peaks": {"source": peak_src, **{k: peaks[k] for k in ("hbm_gbs", "bf16_tflops") if k in peaks}},
+    }
+    if rank == 0 and ws == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * gks.h -- C ABI of libgks: one two-stage time step of the third-order
+ * compact gas-kinetic scheme with two-step multi-resolution WENO
+ * reconstruction on tetrahedral meshes, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (paper: Ji, Zhao, Shyy, Xu, "Two-step multi-resolution
+ * reconstruction-based compact gas-kinetic scheme on tetrahedral mesh"):
+ *   - cell averages W and cell-averaged gradients dW are the unknowns (Sec. 2.3);
+ *   - each stage reconstructs a quadratic R per cell and component from the
+ *     compact stencil (Sec. 4.1-4.3), evaluates the time-dependent kinetic
+ *     solution at the three Gauss points of every face (Sec. 2.2, Sec. 4.5),
+ *     and updates W by the face fluxes and dW by the divergence theorem
+ *     applied to the time-accurate interface values (Sec. 2.3, Sec. 3);
+ *   - two stages form one fourth-order step (Sec. 3, Eq. s2o4).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: GKS_OK (0) or a negative gks_status; gks_last_error()
+ *     then returns a message (thread-local, valid until the next call on
+ *     the same thread).  No C++ exception crosses this interface.
+ *   - Host arrays are row-major and are copied; the caller keeps ownership.
+ *   - Device pointers (prefix d_) must be device memory of the current
+ *     device; the caller owns them.  The library never allocates or frees
+ *     device memory: all device storage lives in one caller-allocated
+ *     workspace of gks_workspace_bytes() bytes.
+ *   - State layout: W[5][nc] conservative variables (rho, rho U1, rho U2,
+ *     rho U3, rho E); dW[15][nc] with row 3*q + i holding d W_q / d x_i.
+ *   - All device work is enqueued on the stream given to gks_state_create;
+ *     calls that return host values synchronise that stream.
+ *   - Asynchronous CUDA errors and device-side error flags (non-positive
+ *     density or pressure in an updated cell average) surface at the next
+ *     gks_step / gks_get_state / gks_sync as GKS_E_CUDA / GKS_E_STATE.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gks_status;
+enum {
+    GKS_OK = 0,
+    GKS_E_ARG = -1,         /* invalid argument (null pointer, bad size, bad option) */
+    GKS_E_MESH = -2,        /* invalid mesh (id out of range, non-positive volume,
+                               face shared by more than two cells, ...) */
+    GKS_E_STENCIL = -3,     /* stencils not built, or a cell's least-squares system
+                               is singular (count in gks_stencil_build's output) */
+    GKS_E_STATE = -4,       /* non-positive density or pressure in a cell average */
+    GKS_E_CUDA = -5,        /* a CUDA runtime call failed */
+    GKS_E_TIMEOUT = -6,     /* reserved: a bounded device wait gave up */
+    GKS_E_NOMEM = -7,       /* host allocation failed or workspace too small */
+    GKS_E_UNSUPPORTED = -8  /* option combination not implemented */
+};
+
+/* Scheme parameters (plain data, passed by pointer and copied). */
+typedef struct gks_params {
+    double gamma;        /* specific heat ratio; K = (5 - 3 gamma)/(gamma - 1), Sec. 2 */
+    double cfl;          /* C_CFL of the time-step rule, Sec. 5 Eq. time-step */
+    double mu;           /* dynamic viscosity (used when viscous = 1) */
+    double eps_weno;     /* epsilon of the nonlinear weights, Sec. 4.2 (paper: 1e-8) */
+    double tau_eps;      /* epsilon of the numerical collision time, Sec. 2.2 (0.01) */
+    double tau_c;        /* C of the numerical collision time, Sec. 2.2 (1) */
+    int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2); 1: nonlinear */
+    int32_t order;       /* 3: R^3rd (Eq. final_weno_expression-3rd); 2: R^2nd */
+    int32_t smooth_flux; /* 0: full solver Eq. 2nd-flux; 1: smooth Eq. 2nd-smooth-flux */
+    int32_t viscous;     /* 0: Euler, tau = 0; 1: tau = mu / p (Sec. 2.2) */
+    int32_t precision;   /* 0: FP64 throughout; 1: FP32 bulk (reconstruction, flux,
+                            face records and stage states in FP32; FP64 master cell
+                            averages updated by compensated sums) */
+    int32_t reserved;    /* must be 0 */
+} gks_params;
+
+/* Fills the paper's defaults: gamma 1.4, cfl 1, mu 0, eps_weno 1e-8,
+ * tau_eps 0.01, tau_c 1, weno 1, order 3, full flux, Euler, FP64. */
+void gks_params_default(gks_params* p);
+
+typedef struct gks_mesh gks_mesh;   /* opaque, library-owned host object */
+typedef struct gks_state gks_state; /* opaque, library-owned handle over a
+                                       caller-allocated device workspace */
+
+/* ---------------------------------------------------------------- mesh -- */
+
+/* Tetrahedral mesh from vertices and connectivity (Sec. 2.1: cells with four
+ * triangular faces).
+ *   xyz[n_vert][3]     vertex coordinates
+ *   tet[n_cell][4]     vertex ids, positive orientation required
+ *   shift[n_cell][4][3] periodic image of each tet vertex: its position is
+ *                      xyz[v] + shift * period (NULL: all zero)
+ *   period[3]          period per axis, 0 on a non-periodic axis (NULL: none)
+ * Faces are the vertex triples, matched across periodic images; a face met
+ * once is an open boundary face.  Canonical numbering: faces sorted by their
+ * ascending vertex-id triple, then by the image shifts of the second and
+ * third vertex relative to the first; each face's unit normal has its first
+ * nonzero component positive and points out of its "left" cell.
+ * Errors: GKS_E_ARG (null/size), GKS_E_MESH (see enum). */
+gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet,
+                           const int8_t* shift, int64_t n_cell, const double* period,
+                           gks_mesh** out);
+void gks_mesh_destroy(gks_mesh* mesh);
+
+/* Counts: cells, faces, open boundary faces. Any output may be NULL. */
+gks_status gks_mesh_info(const gks_mesh* mesh, int64_t* n_cell, int64_t* n_face,
+                         int64_t* n_boundary_face);
+
+/* Host copies of the connectivity (any output may be NULL):
+ *   face_v[nf][3] ascending vertex ids; face_lr[nf][2] left and right cell
+ *   (-1: none); nbr[nc][4] cell across the face opposite local vertex f
+ *   (-1: none); csr_face[nc][4] face ids in local-face order; csr_sign[nc][4]
+ *   +1 if the cell is that face's left cell, else -1. */
+gks_status gks_mesh_topology(const gks_mesh* mesh, int64_t* face_v, int64_t* face_lr,
+                             int64_t* nbr, int64_t* csr_face, int8_t* csr_sign);
+
+/* Host copies of the FP64 geometry (any output may be NULL):
+ *   vol[nc]; cen[nc][3]; mom2[nc][6] central second moments / volume in the
+ *   order xx, xy, xz, yy, yz, zz; dr[nc] = 3|Omega| / sum |Gamma| (Sec. 5);
+ *   farea[nf]; fnorm[nf][3]; gp_l[nf][3][3] and gp_r[nf][3][3] the face's
+ *   Gauss points (Sec. 2.1: (1/6,1/6), (2/3,1/6), (1/6,2/3), weight area/3)
+ *   relative to the left / right centroid, periodic image applied. */
+gks_status gks_mesh_geometry(const gks_mesh* mesh, double* vol, double* cen, double* mom2,
+                             double* dr, double* farea, double* fnorm, double* gp_l,
+                             double* gp_r);
+
+/* FP64 least-squares operators of every cell (Sec. 4.1, Sec. 4.3):
+ *   M1 (3x4): slopes of P1 from the neighbours' averages minus the own,
+ *   least squares (Eq. p1-stenci-condition);
+ *   M2 (9x16): the 9 coefficients of P2 in the zero-mean basis of Eq. base
+ *   from [dQ_f (4); grad Q_{f,l} at 4 + 3 f + l (12)], neighbour averages
+ *   exact and neighbour gradients in the least-squares sense
+ *   (Eqs. large-stenci-condition-1/2).
+ * Columns of absent neighbours are zero.  *n_singular (may be NULL) counts
+ * cells whose system is singular (fewer than 3 neighbours or reciprocal
+ * pivot ratio below 1e-12); such cells reconstruct a constant.  Returns
+ * GKS_OK even when n_singular > 0. */
+gks_status gks_stencil_build(gks_mesh* mesh, int64_t* n_singular);
+
+/* Host copies of M1[nc][3][4] and M2[nc][9][16] (GKS_E_STENCIL if not built). */
+gks_status gks_mesh_stencils(const gks_mesh* mesh, double* M1, double* M2);
+
+/* --------------------------------------------------------------- state -- */
+
+/* Bytes of device workspace needed for this mesh and parameter set
+ * (0 on error). */
+size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params);
+
+/* Binds a state to a mesh (stencils must be built), a parameter set, a
+ * device workspace (256-byte aligned, at least gks_workspace_bytes) and a
+ * CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream).
+ * Uploads the mesh data into the workspace (synchronously).  The mesh must
+ * outlive the state. */
+gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
+                            void* d_workspace, size_t workspace_bytes, void* stream,
+                            gks_state** out);
+void gks_state_destroy(gks_state* state);
+
+/* Sets the cell averages and gradients from device arrays W[5][nc],
+ * dW[15][nc] (FP64) and the time to 0. */
+gks_status gks_init_state(gks_state* state, const double* d_W, const double* d_dW);
+
+/* Advances nsteps two-stage steps (Sec. 3).  dt_fixed > 0 fixes the step;
+ * otherwise each step takes the time-step rule of Sec. 5 from the current
+ * averages (a device-side reduction).  t_end > 0 clips the step so that the
+ * time does not pass t_end (steps at t = t_end are no-ops).  The step
+ * sequence is captured once into a CUDA graph per option set and replayed.
+ * Returns after enqueueing; host outputs need gks_sync or gks_get_time. */
+gks_status gks_step(gks_state* state, int32_t nsteps, double dt_fixed, double t_end);
+
+/* Waits for the state's stream and reports deferred errors. */
+gks_status gks_sync(gks_state* state);
+
+/* Copies the current W, dW (FP64) to device arrays (either may be NULL). */
+gks_status gks_get_state(const gks_state* state, double* d_W, double* d_dW);
+
+/* Time and last step size (host values; synchronises). */
+gks_status gks_get_time(gks_state* state, double* t, double* dt_last);
+
+/* The same step through host buffers: copies h_W[5][nc], h_dW[15][nc] from
+ * host memory (pinned for asynchronous copies), advances nsteps, and copies
+ * the result to h_W_out, h_dW_out; synchronises.  In-place is allowed. */
+gks_status gks_step_host(gks_state* state, const double* h_W, const double* h_dW,
+                         int32_t nsteps, double dt_fixed, double* h_W_out,
+                         double* h_dW_out);
+
+/* Kernel classes timed by gks_step_timed. */
+enum {
+    GKS_K_DT = 0,      /* time-step minimum and control update */
+    GKS_K_SLOPES = 1,  /* reconstruction step 1, both stages */
+    GKS_K_RECON = 2,   /* reconstruction step 2, both stages */
+    GKS_K_FLUX1 = 3,   /* face flux, stage 1 */
+    GKS_K_UPDATE1 = 4, /* cell update, stage 1 */
+    GKS_K_FLUX2 = 5,   /* face flux, stage 2 */
+    GKS_K_UPDATE2 = 6, /* cell update, stage 2 */
+    GKS_NKERNELS = 7
+};
+
+/* The same steps as gks_step, launched kernel by kernel (no graph) with a
+ * CUDA event between consecutive launches on the state's stream; adds each
+ * kernel class's device time in milliseconds to kernel_ms[GKS_NKERNELS]
+ * and its launch count to launches[GKS_NKERNELS] (may be NULL).
+ * Synchronises.  For profiling breakdowns; numerically identical to
+ * gks_step. */
+gks_status gks_step_timed(gks_state* state, int32_t nsteps, double dt_fixed, double t_end,
+                          double* kernel_ms, int64_t* launches);
+
+/* Time step of the Sec. 5 rule for the current averages (host value). */
+gks_status gks_timestep(gks_state* state, double* dt);
+
+/* Per-component root mean square over cells of (W(t) - W_prev) / dt_last,
+ * where W_prev is the state before the last step (host out_l2[5];
+ * synchronises). */
+gks_status gks_residual(gks_state* state, double* out_l2);
+
+/* ------------------------------------------------------- diagnostics -- */
+
+/* Reconstruction of the current state (Sec. 4), written to device arrays:
+ * d_poly[nc][5][10] R about each centroid in monomial form
+ * (c0, cx, cy, cz, cxx, cxy, cxz, cyy, cyz, czz); d_slopes[nc][5][3] step-1
+ * slopes (may be NULL; zero with linear weights); d_fallback[nc] 1 where the
+ * positivity check replaced R by the average (may be NULL).  FP64 outputs
+ * in both precisions. */
+gks_status gks_debug_reconstruct(gks_state* state, double* d_poly, double* d_slopes,
+                                 int32_t* d_fallback);
+
+/* Face records of one stage for the current state and a given dt, written as
+ * FP64 to d_rec[nf][40] (stage 1) or d_rec[nf][20] (stage 2), same layout as
+ * used by the step: stage 1 = (sum_k w Fh, sum_k w (8/3 Fh - 1/3 F),
+ * sum_k w (W0+Wdt)/2 n, sum_k w W0 n); stage 2 = (sum_k w 4/3 (F - 2 Fh),
+ * sum_k w (Wdt - W0) n); vector entries at 3*q + i.  Fh, F are the flux
+ * integrals over [0, dt/2] and [0, dt]; W0, Wdt the interface states
+ * (Sec. 2.2, Sec. 3 Eqs. linear-system, step-du). */
+gks_status gks_debug_face_records(gks_state* state, double dt, int32_t stage, double* d_rec);
+
+/* Last error message of this thread ("" if none). */
+const char* gks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

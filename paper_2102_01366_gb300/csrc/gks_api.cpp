@@ -1,0 +1,763 @@
+// gks_api.cpp -- the extern "C" entry points of libgks (include/gks.h).
+//
+// Host objects: gks_mesh (connectivity, FP64 geometry and stencils) and
+// gks_state (views into one caller-allocated device workspace, the stream,
+// and the CUDA graph of one step).  Device storage is laid out once by
+// layout_workspace(); nothing here allocates device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gks_internal.h"
+#include "gks_kernels.h"
+
+namespace gks {
+namespace {
+thread_local std::string g_err;
+}
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace gks
+
+using namespace gks;
+
+#define GKS_CHECK_CUDA(call)                                                        \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return GKS_E_CUDA;                                                      \
+        }                                                                           \
+    } while (0)
+
+extern "C" const char* gks_last_error(void) { return g_err.c_str(); }
+
+extern "C" void gks_params_default(gks_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->gamma = 1.4;
+    p->cfl = 1.0;
+    p->mu = 0.0;
+    p->eps_weno = 1e-8;
+    p->tau_eps = 0.01;
+    p->tau_c = 1.0;
+    p->weno = 1;
+    p->order = 3;
+    p->smooth_flux = 0;
+    p->viscous = 0;
+    p->precision = 0;
+}
+
+static gks_status check_params(const gks_params* p) {
+    if (!p) { set_error("params is NULL"); return GKS_E_ARG; }
+    if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) {
+        set_error("gamma must lie in (1, 5/3]");
+        return GKS_E_ARG;
+    }
+    if (!(p->cfl > 0.0) || !(p->eps_weno > 0.0) || !(p->tau_eps >= 0.0) || !(p->tau_c >= 0.0) ||
+        !(p->mu >= 0.0)) {
+        set_error("cfl, eps_weno must be positive; tau_eps, tau_c, mu non-negative");
+        return GKS_E_ARG;
+    }
+    if ((p->weno != 0 && p->weno != 1) || (p->order != 2 && p->order != 3) ||
+        (p->smooth_flux != 0 && p->smooth_flux != 1) || (p->viscous != 0 && p->viscous != 1) ||
+        (p->precision != 0 && p->precision != 1) || p->reserved != 0) {
+        set_error("weno, smooth_flux, viscous, precision must be 0 or 1; order 2 or 3; reserved 0");
+        return GKS_E_ARG;
+    }
+    if (p->viscous && !(p->mu > 0.0)) {
+        set_error("viscous flow needs mu > 0");
+        return GKS_E_ARG;
+    }
+    if (!p->viscous && !(p->tau_eps > 0.0)) {
+        set_error("inviscid flow needs tau_eps > 0 (numerical collision time)");
+        return GKS_E_ARG;
+    }
+    return GKS_OK;
+}
+
+// ------------------------------------------------------------------ mesh --
+
+extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet,
+                                      const int8_t* shift, int64_t n_cell, const double* period,
+                                      gks_mesh** out) {
+    if (!out) { set_error("gks_mesh_create: out is NULL"); return GKS_E_ARG; }
+    *out = nullptr;
+    if (!xyz || !tet || n_vert <= 0 || n_cell <= 0) {
+        set_error("gks_mesh_create: empty mesh or NULL arrays");
+        return GKS_E_ARG;
+    }
+    if (n_cell >= ((int64_t)1 << 30) || n_vert >= ((int64_t)1 << 40)) {
+        set_error("gks_mesh_create: mesh too large (cells and faces are indexed by int32)");
+        return GKS_E_ARG;
+    }
+    gks_mesh* m = new (std::nothrow) gks_mesh();
+    if (!m) { set_error("out of memory"); return GKS_E_NOMEM; }
+    try {
+        m->nv = n_vert;
+        m->nc = n_cell;
+        for (int a = 0; a < 3; ++a) m->period[a] = period ? period[a] : 0.0;
+        m->xyz.assign(xyz, xyz + n_vert * 3);
+        m->tet.assign(tet, tet + n_cell * 4);
+        if (shift) m->shift.assign(shift, shift + n_cell * 12);
+        else m->shift.assign((size_t)n_cell * 12, 0);
+        for (int64_t i = 0; i < n_cell * 4; ++i)
+            if (tet[i] < 0 || tet[i] >= n_vert) {
+                set_error("gks_mesh_create: vertex id out of range");
+                delete m;
+                return GKS_E_MESH;
+            }
+        for (int a = 0; a < 3; ++a)
+            if (!(m->period[a] >= 0.0)) {
+                set_error("gks_mesh_create: negative period");
+                delete m;
+                return GKS_E_ARG;
+            }
+        gks_status st = build_mesh(*m);
+        if (st != GKS_OK) { delete m; return st; }
+        if (m->nf >= ((int64_t)1 << 30)) {
+            set_error("gks_mesh_create: too many faces");
+            delete m;
+            return GKS_E_ARG;
+        }
+    } catch (const std::bad_alloc&) {
+        delete m;
+        set_error("out of memory");
+        return GKS_E_NOMEM;
+    }
+    *out = m;
+    return GKS_OK;
+}
+
+extern "C" void gks_mesh_destroy(gks_mesh* mesh) { delete mesh; }
+
+extern "C" gks_status gks_mesh_info(const gks_mesh* m, int64_t* n_cell, int64_t* n_face,
+                                    int64_t* n_boundary_face) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    if (n_cell) *n_cell = m->nc;
+    if (n_face) *n_face = m->nf;
+    if (n_boundary_face) *n_boundary_face = m->nbf;
+    return GKS_OK;
+}
+
+template <typename A>
+static void copy_out(A* dst, const std::vector<A>& src) {
+    if (dst) std::memcpy(dst, src.data(), sizeof(A) * src.size());
+}
+
+extern "C" gks_status gks_mesh_topology(const gks_mesh* m, int64_t* face_v, int64_t* face_lr,
+                                        int64_t* nbr, int64_t* csr_face, int8_t* csr_sign) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    copy_out(face_v, m->face_v);
+    copy_out(face_lr, m->face_lr);
+    copy_out(nbr, m->nbr);
+    copy_out(csr_face, m->csr_face);
+    copy_out(csr_sign, m->csr_sign);
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_mesh_geometry(const gks_mesh* m, double* vol, double* cen, double* mom2,
+                                        double* dr, double* farea, double* fnorm, double* gp_l,
+                                        double* gp_r) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    copy_out(vol, m->vol);
+    copy_out(cen, m->cen);
+    copy_out(mom2, m->mom2);
+    copy_out(dr, m->dr);
+    copy_out(farea, m->farea);
+    copy_out(fnorm, m->fnorm);
+    copy_out(gp_l, m->gp_l);
+    copy_out(gp_r, m->gp_r);
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_stencil_build(gks_mesh* m, int64_t* n_singular) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    try {
+        gks_status st = build_stencils(*m);
+        if (st != GKS_OK) return st;
+    } catch (const std::bad_alloc&) {
+        set_error("out of memory");
+        return GKS_E_NOMEM;
+    }
+    if (n_singular) *n_singular = m->n_singular;
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_mesh_stencils(const gks_mesh* m, double* M1, double* M2) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    if (!m->has_stencils) { set_error("stencils not built"); return GKS_E_STENCIL; }
+    copy_out(M1, m->M1);
+    copy_out(M2, m->M2);
+    return GKS_OK;
+}
+
+// ----------------------------------------------------------------- state --
+
+namespace {
+
+struct Layout {
+    size_t total = 0;
+    // mesh
+    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo;
+    // state
+    size_t Wd, Wr, dW, Ws, dWs, S, G, slopes, poly, rec, ctrl, part, err, stage;
+    size_t add(size_t bytes) {
+        size_t off = total;
+        total += (bytes + 255) & ~(size_t)255;
+        return off;
+    }
+};
+
+Layout layout_workspace(int64_t nc, int64_t nf, bool fp32) {
+    Layout L;
+    const size_t T = fp32 ? 4 : 8;
+    const size_t nblk = (size_t)update_blocks(nc);
+    L.nbr = L.add(4 * 4 * nc);
+    L.cface = L.add(4 * 4 * nc);
+    L.inv_vol = L.add(8 * nc);
+    L.vol23 = L.add(T * nc);
+    L.vol43 = L.add(T * nc);
+    L.dr = L.add(T * nc);
+    L.mom2 = L.add(T * 6 * nc);
+    L.cgp = L.add(T * 36 * nc);
+    L.M1 = L.add(T * 12 * nc);
+    L.M2 = L.add(T * 144 * nc);
+    L.flr = L.add(4 * 2 * nf);
+    L.fgeo = L.add(T * FGEO * nf);
+    L.Wd = L.add(8 * 5 * nc);
+    L.Wr = fp32 ? L.add(T * 5 * nc) : L.Wd;
+    L.dW = L.add(T * 15 * nc);
+    L.Ws = L.add(T * 5 * nc);
+    L.dWs = L.add(T * 15 * nc);
+    L.S = L.add(8 * 5 * nc);
+    L.G = L.add(T * 15 * nc);
+    L.slopes = L.add(T * 15 * nc);
+    L.poly = L.add(T * 50 * nc);
+    L.rec = L.add(T * 40 * nf);
+    L.ctrl = L.add(8 * CTRL_N);
+    L.part = L.add(8 * PART_N * nblk);
+    L.err = L.add(4);
+    L.stage = L.add(8 * 15 * nc);
+    return L;
+}
+
+}  // namespace
+
+struct gks_state {
+    const gks_mesh* mesh = nullptr;
+    gks_params params;
+    HostPhys phys;
+    bool fp32 = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* ws = nullptr;
+    Layout L;
+    DevMesh<double> m64;
+    DevMesh<float> m32;
+    DevState<double> s64;
+    DevState<float> s32;
+    cudaGraphExec_t graph = nullptr;
+    bool initialised = false;
+};
+
+template <typename T>
+static T* at(gks_state* s, size_t off) {
+    return reinterpret_cast<T*>(s->ws + off);
+}
+
+template <typename T>
+static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
+    const Layout& L = s->L;
+    m.nc = s->mesh->nc;
+    m.nf = s->mesh->nf;
+    m.nbr = at<int32_t>(s, L.nbr);
+    m.cface = at<int32_t>(s, L.cface);
+    m.inv_vol = at<double>(s, L.inv_vol);
+    m.vol23 = at<T>(s, L.vol23);
+    m.vol43 = at<T>(s, L.vol43);
+    m.dr = at<T>(s, L.dr);
+    m.mom2 = at<T>(s, L.mom2);
+    m.cgp = at<T>(s, L.cgp);
+    m.M1 = at<T>(s, L.M1);
+    m.M2 = at<T>(s, L.M2);
+    m.flr = at<int32_t>(s, L.flr);
+    m.fgeo = at<T>(s, L.fgeo);
+    st.Wd = at<double>(s, L.Wd);
+    st.Wr = at<T>(s, L.Wr);
+    st.dW = at<T>(s, L.dW);
+    st.Ws = at<T>(s, L.Ws);
+    st.dWs = at<T>(s, L.dWs);
+    st.S = at<double>(s, L.S);
+    st.G = at<T>(s, L.G);
+    st.slopes = at<T>(s, L.slopes);
+    st.poly = at<T>(s, L.poly);
+    st.rec = at<T>(s, L.rec);
+    st.ctrl = at<double>(s, L.ctrl);
+    st.part = at<double>(s, L.part);
+    st.err = at<int32_t>(s, L.err);
+}
+
+template <typename T>
+static gks_status upload_mesh(gks_state* s) {
+    const gks_mesh& g = *s->mesh;
+    const int64_t nc = g.nc, nf = g.nf;
+    const Layout& L = s->L;
+    std::vector<int32_t> nbr(4 * nc), cface(4 * nc), flr(2 * nf);
+    std::vector<double> inv_vol(nc);
+    std::vector<T> vol23(nc), vol43(nc), dr(nc), mom2(6 * nc), cgp(36 * nc), M1(12 * nc), M2(144 * nc),
+        fgeo(FGEO * nf, T(0));
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int f = 0; f < 4; ++f) {
+            nbr[f * nc + c] = (int32_t)g.nbr[c * 4 + f];
+            const int64_t fi = g.csr_face[c * 4 + f];
+            const bool left = g.csr_sign[c * 4 + f] > 0;
+            cface[f * nc + c] = (int32_t)(fi * 2 + (left ? 0 : 1));
+            const double* gp = left ? &g.gp_l[fi * 9] : &g.gp_r[fi * 9];
+            for (int k = 0; k < 9; ++k) cgp[(f * 9 + k) * nc + c] = (T)gp[k];
+        }
+        inv_vol[c] = 1.0 / g.vol[c];
+        vol23[c] = (T)std::pow(g.vol[c], 2.0 / 3.0);
+        vol43[c] = (T)std::pow(g.vol[c], 4.0 / 3.0);
+        dr[c] = (T)g.dr[c];
+        for (int q = 0; q < 6; ++q) mom2[q * nc + c] = (T)g.mom2[c * 6 + q];
+        for (int k = 0; k < 12; ++k) M1[k * nc + c] = (T)g.M1[c * 12 + k];
+        for (int k = 0; k < 144; ++k) M2[k * nc + c] = (T)g.M2[c * 144 + k];
+    }
+    for (int64_t f = 0; f < nf; ++f) {
+        flr[f] = (int32_t)g.face_lr[f * 2];
+        flr[nf + f] = (int32_t)g.face_lr[f * 2 + 1];
+        T* r = &fgeo[f * FGEO];
+        for (int a = 0; a < 3; ++a) r[a] = (T)g.fnorm[f * 3 + a];
+        r[3] = (T)(g.farea[f] / 3.0);
+        for (int k = 0; k < 9; ++k) {
+            r[4 + k] = (T)g.gp_l[f * 9 + k];
+            r[13 + k] = (T)g.gp_r[f * 9 + k];
+        }
+    }
+    auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+        return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    GKS_CHECK_CUDA(put(L.nbr, nbr.data(), 4 * nbr.size()));
+    GKS_CHECK_CUDA(put(L.cface, cface.data(), 4 * cface.size()));
+    GKS_CHECK_CUDA(put(L.inv_vol, inv_vol.data(), 8 * inv_vol.size()));
+    GKS_CHECK_CUDA(put(L.vol23, vol23.data(), sizeof(T) * vol23.size()));
+    GKS_CHECK_CUDA(put(L.vol43, vol43.data(), sizeof(T) * vol43.size()));
+    GKS_CHECK_CUDA(put(L.dr, dr.data(), sizeof(T) * dr.size()));
+    GKS_CHECK_CUDA(put(L.mom2, mom2.data(), sizeof(T) * mom2.size()));
+    GKS_CHECK_CUDA(put(L.cgp, cgp.data(), sizeof(T) * cgp.size()));
+    GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(T) * M1.size()));
+    GKS_CHECK_CUDA(put(L.M2, M2.data(), sizeof(T) * M2.size()));
+    GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
+    GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
+    GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
+    GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
+    return GKS_OK;
+}
+
+extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
+    if (!mesh || check_params(params) != GKS_OK) return 0;
+    return layout_workspace(mesh->nc, mesh->nf, params->precision == 1).total;
+}
+
+extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
+                                       void* d_workspace, size_t workspace_bytes, void* stream,
+                                       gks_state** out) {
+    if (!out) { set_error("gks_state_create: out is NULL"); return GKS_E_ARG; }
+    *out = nullptr;
+    if (!mesh) { set_error("gks_state_create: mesh is NULL"); return GKS_E_ARG; }
+    gks_status ps = check_params(params);
+    if (ps != GKS_OK) return ps;
+    if (!mesh->has_stencils) { set_error("gks_state_create: stencils not built"); return GKS_E_STENCIL; }
+    const bool fp32 = params->precision == 1;
+    Layout L = layout_workspace(mesh->nc, mesh->nf, fp32);
+    if (!d_workspace || workspace_bytes < L.total) {
+        set_error("gks_state_create: workspace missing or smaller than gks_workspace_bytes()");
+        return GKS_E_NOMEM;
+    }
+    if (((uintptr_t)d_workspace & 255) != 0) {
+        set_error("gks_state_create: workspace must be 256-byte aligned");
+        return GKS_E_ARG;
+    }
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        set_error("gks_state_create: workspace is not device memory");
+        return GKS_E_ARG;
+    }
+    gks_state* s = new (std::nothrow) gks_state();
+    if (!s) { set_error("out of memory"); return GKS_E_NOMEM; }
+    s->mesh = mesh;
+    s->params = *params;
+    s->phys = HostPhys{params->gamma, params->cfl, params->mu, params->eps_weno, params->tau_eps,
+                       params->tau_c, params->weno, params->order, params->smooth_flux, params->viscous};
+    s->fp32 = fp32;
+    s->ws = static_cast<char*>(d_workspace);
+    s->L = L;
+    if (stream) {
+        s->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        // the legacy default stream cannot be captured into a graph
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            set_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+            delete s;
+            return GKS_E_CUDA;
+        }
+        s->own_stream = true;
+    }
+    gks_status st;
+    if (fp32) {
+        make_views<float>(s, s->m32, s->s32);
+        st = upload_mesh<float>(s);
+    } else {
+        make_views<double>(s, s->m64, s->s64);
+        st = upload_mesh<double>(s);
+    }
+    if (st != GKS_OK) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return GKS_OK;
+}
+
+extern "C" void gks_state_destroy(gks_state* s) {
+    if (!s) return;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->own_stream) {
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+    }
+    delete s;
+}
+
+// the caller's legacy-stream work must finish before an internal stream reads
+static void order_after_caller(gks_state* s) {
+    if (s->own_stream) cudaStreamSynchronize(0);
+}
+
+template <typename T>
+static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const double* d_W,
+                            const double* d_dW) {
+    const int64_t nc = m.nc;
+    GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
+    if ((void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
+    if (sizeof(T) == 8)
+        GKS_CHECK_CUDA(cudaMemcpyAsync(st.dW, d_dW, 8 * 15 * nc, cudaMemcpyDeviceToDevice, s->stream));
+    else
+        GKS_CHECK_CUDA(Launch<T>::from_double(d_dW, st.dW, 15 * nc, s->stream));
+    GKS_CHECK_CUDA(launch_set_control(st.ctrl, 0.0, 0.0, 1, s->stream));
+    GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, st.part, s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_init_state(gks_state* s, const double* d_W, const double* d_dW) {
+    if (!s || !d_W || !d_dW) { set_error("gks_init_state: NULL argument"); return GKS_E_ARG; }
+    order_after_caller(s);
+    gks_status st = s->fp32 ? init_impl<float>(s, s->m32, s->s32, d_W, d_dW)
+                            : init_impl<double>(s, s->m64, s->s64, d_W, d_dW);
+    if (st != GKS_OK) return st;
+    s->initialised = true;
+    if (s->own_stream) GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    return GKS_OK;
+}
+
+// one two-stage step (Sec. 3): enqueued on s->stream (captured into a graph)
+template <typename T>
+static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
+    const HostPhys& p = s->phys;
+    cudaStream_t q = s->stream;
+    const bool need_b = p.weno || p.order == 2;
+    cudaError_t e;
+    if ((e = launch_dt_finalize(st.part, update_blocks(m.nc), p.cfl, st.ctrl, q)) != cudaSuccess) return e;
+    // stage 1 from (W^n, grad W^n)
+    if (need_b && (e = Launch<T>::slopes(m, st.Wr, st.slopes, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
+    // stage 2 from (W*, grad W*)
+    if (need_b && (e = Launch<T>::slopes(m, st.Ws, st.slopes, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
+    return Launch<T>::update2(m, p, st, q);
+}
+
+static gks_status build_graph(gks_state* s) {
+    cudaGraph_t g = nullptr;
+    GKS_CHECK_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = s->fp32 ? enqueue_step<float>(s, s->m32, s->s32) : enqueue_step<double>(s, s->m64, s->s64);
+    cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error(std::string("step capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return GKS_E_CUDA;
+    }
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph = nullptr;
+        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return GKS_E_CUDA;
+    }
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_step(gks_state* s, int32_t nsteps, double dt_fixed, double t_end) {
+    if (!s) { set_error("gks_step: state is NULL"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("gks_step: state not initialised"); return GKS_E_STATE; }
+    if (nsteps < 0) { set_error("gks_step: negative nsteps"); return GKS_E_ARG; }
+    if (!std::isfinite(dt_fixed) || !std::isfinite(t_end)) { set_error("gks_step: non-finite dt/t_end"); return GKS_E_ARG; }
+    if (!s->graph) {
+        gks_status st = build_graph(s);
+        if (st != GKS_OK) return st;
+    }
+    double* ctrl = s->fp32 ? s->s32.ctrl : s->s64.ctrl;
+    GKS_CHECK_CUDA(launch_set_control(ctrl, dt_fixed, t_end, 0, s->stream));
+    for (int32_t i = 0; i < nsteps; ++i) GKS_CHECK_CUDA(cudaGraphLaunch(s->graph, s->stream));
+    return GKS_OK;
+}
+
+// kernel-by-kernel step with events between launches (profiling breakdown)
+template <typename T>
+static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, int32_t nsteps,
+                                  double* kernel_ms, int64_t* launches) {
+    const HostPhys& p = s->phys;
+    cudaStream_t q = s->stream;
+    const bool need_b = p.weno || p.order == 2;
+    const int nev = 16;
+    cudaEvent_t ev[nev];
+    for (int i = 0; i < nev; ++i) GKS_CHECK_CUDA(cudaEventCreate(&ev[i]));
+    double acc[GKS_NKERNELS] = {0};
+    int64_t cnt[GKS_NKERNELS] = {0};
+    gks_status status = GKS_OK;
+    for (int32_t it = 0; it < nsteps && status == GKS_OK; ++it) {
+        int kid[nev];
+        int ne = 0;
+        auto mark = [&](int k) {
+            kid[ne] = k;
+            return cudaEventRecord(ev[ne++], q);
+        };
+        cudaError_t e = cudaEventRecord(ev[ne], q);
+        kid[ne++] = -1;
+        if (e == cudaSuccess) e = launch_dt_finalize(st.part, update_blocks(m.nc), p.cfl, st.ctrl, q);
+        if (e == cudaSuccess) e = mark(GKS_K_DT);
+        for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+            const T* W = stage == 1 ? st.Wr : st.Ws;
+            const T* dW = stage == 1 ? st.dW : st.dWs;
+            if (need_b) {
+                e = Launch<T>::slopes(m, W, st.slopes, q);
+                if (e == cudaSuccess) e = mark(GKS_K_SLOPES);
+            }
+            if (e == cudaSuccess) e = Launch<T>::recon(m, p, W, dW, st.slopes, st.poly, nullptr, q);
+            if (e == cudaSuccess) e = mark(GKS_K_RECON);
+            if (e == cudaSuccess) e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, stage, q);
+            if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
+            if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
+            if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[ne - 1]);
+        for (int i = 1; i < ne && e == cudaSuccess; ++i) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+            acc[kid[i]] += ms;
+            cnt[kid[i]] += 1;
+        }
+        if (e != cudaSuccess) {
+            set_error(std::string("gks_step_timed: ") + cudaGetErrorString(e));
+            status = GKS_E_CUDA;
+        }
+    }
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    if (status != GKS_OK) return status;
+    for (int k = 0; k < GKS_NKERNELS; ++k) {
+        if (kernel_ms) kernel_ms[k] += acc[k];
+        if (launches) launches[k] += cnt[k];
+    }
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_step_timed(gks_state* s, int32_t nsteps, double dt_fixed, double t_end,
+                                     double* kernel_ms, int64_t* launches) {
+    if (!s) { set_error("gks_step_timed: state is NULL"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("gks_step_timed: state not initialised"); return GKS_E_STATE; }
+    if (nsteps < 0) { set_error("gks_step_timed: negative nsteps"); return GKS_E_ARG; }
+    double* ctrl = s->fp32 ? s->s32.ctrl : s->s64.ctrl;
+    GKS_CHECK_CUDA(launch_set_control(ctrl, dt_fixed, t_end, 0, s->stream));
+    gks_status st = s->fp32 ? step_timed_impl<float>(s, s->m32, s->s32, nsteps, kernel_ms, launches)
+                            : step_timed_impl<double>(s, s->m64, s->s64, nsteps, kernel_ms, launches);
+    if (st != GKS_OK) return st;
+    return gks_sync(s);
+}
+
+extern "C" gks_status gks_sync(gks_state* s) {
+    if (!s) { set_error("gks_sync: state is NULL"); return GKS_E_ARG; }
+    int32_t err = 0;
+    GKS_CHECK_CUDA(cudaMemcpyAsync(&err, s->fp32 ? s->s32.err : s->s64.err, 4, cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    if (err & ERR_STATE) {
+        set_error("non-positive density or pressure in an updated cell average");
+        return GKS_E_STATE;
+    }
+    return GKS_OK;
+}
+
+template <typename T>
+static gks_status get_impl(gks_state* s, DevState<T>& st, int64_t nc, double* d_W, double* d_dW) {
+    if (d_W) GKS_CHECK_CUDA(cudaMemcpyAsync(d_W, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
+    if (d_dW) {
+        if (sizeof(T) == 8)
+            GKS_CHECK_CUDA(cudaMemcpyAsync(d_dW, st.dW, 8 * 15 * nc, cudaMemcpyDeviceToDevice, s->stream));
+        else
+            GKS_CHECK_CUDA(Launch<T>::to_double(st.dW, d_dW, 15 * nc, s->stream));
+    }
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_get_state(const gks_state* cs, double* d_W, double* d_dW) {
+    gks_state* s = const_cast<gks_state*>(cs);
+    if (!s) { set_error("gks_get_state: state is NULL"); return GKS_E_ARG; }
+    gks_status st = s->fp32 ? get_impl<float>(s, s->s32, s->mesh->nc, d_W, d_dW)
+                            : get_impl<double>(s, s->s64, s->mesh->nc, d_W, d_dW);
+    if (st != GKS_OK) return st;
+    if (s->own_stream) return gks_sync(s);
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_get_time(gks_state* s, double* t, double* dt_last) {
+    if (!s) { set_error("gks_get_time: state is NULL"); return GKS_E_ARG; }
+    double c[CTRL_N];
+    GKS_CHECK_CUDA(cudaMemcpyAsync(c, s->fp32 ? s->s32.ctrl : s->s64.ctrl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    if (t) *t = c[CTRL_T];
+    if (dt_last) *dt_last = c[CTRL_DT];
+    return GKS_OK;
+}
+
+template <typename T>
+static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const double* h_W,
+                                 const double* h_dW, int32_t nsteps, double dt_fixed, double* h_W_out,
+                                 double* h_dW_out) {
+    const int64_t nc = m.nc;
+    double* stage = at<double>(s, s->L.stage);
+    GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
+    if ((void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
+    if (sizeof(T) == 8) {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(st.dW, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
+    } else {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
+        GKS_CHECK_CUDA(Launch<T>::from_double(stage, st.dW, 15 * nc, s->stream));
+    }
+    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, st.part, s->stream));
+    s->initialised = true;
+    gks_status r = gks_step(s, nsteps, dt_fixed, 0.0);
+    if (r != GKS_OK) return r;
+    GKS_CHECK_CUDA(cudaMemcpyAsync(h_W_out, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToHost, s->stream));
+    if (sizeof(T) == 8) {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, st.dW, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        GKS_CHECK_CUDA(Launch<T>::to_double(st.dW, stage, 15 * nc, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, stage, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
+    }
+    return gks_sync(s);
+}
+
+extern "C" gks_status gks_step_host(gks_state* s, const double* h_W, const double* h_dW, int32_t nsteps,
+                                    double dt_fixed, double* h_W_out, double* h_dW_out) {
+    if (!s || !h_W || !h_dW || !h_W_out || !h_dW_out) {
+        set_error("gks_step_host: NULL argument");
+        return GKS_E_ARG;
+    }
+    return s->fp32 ? step_host_impl<float>(s, s->m32, s->s32, h_W, h_dW, nsteps, dt_fixed, h_W_out, h_dW_out)
+                   : step_host_impl<double>(s, s->m64, s->s64, h_W, h_dW, nsteps, dt_fixed, h_W_out, h_dW_out);
+}
+
+template <typename T>
+static gks_status timestep_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, double* dt) {
+    const int nblk = update_blocks(m.nc);
+    double* tmp = at<double>(s, s->L.stage);  // scratch for the partials
+    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, tmp, s->stream));
+    std::vector<double> part((size_t)nblk * PART_N);
+    GKS_CHECK_CUDA(cudaMemcpyAsync(part.data(), tmp, 8 * part.size(), cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    double mn = INFINITY;
+    for (int b = 0; b < nblk; ++b) mn = std::fmin(mn, part[(size_t)b * PART_N + PART_DTMIN]);
+    *dt = s->params.cfl * mn;
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_timestep(gks_state* s, double* dt) {
+    if (!s || !dt) { set_error("gks_timestep: NULL argument"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("gks_timestep: state not initialised"); return GKS_E_STATE; }
+    return s->fp32 ? timestep_impl<float>(s, s->m32, s->s32, dt) : timestep_impl<double>(s, s->m64, s->s64, dt);
+}
+
+extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
+    if (!s || !out_l2) { set_error("gks_residual: NULL argument"); return GKS_E_ARG; }
+    const int nblk = update_blocks(s->mesh->nc);
+    std::vector<double> part((size_t)nblk * PART_N);
+    GKS_CHECK_CUDA(cudaMemcpyAsync(part.data(), s->fp32 ? s->s32.part : s->s64.part, 8 * part.size(),
+                                   cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    for (int q = 0; q < 5; ++q) {
+        double acc = 0.0;
+        for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * PART_N + PART_RES + q];
+        out_l2[q] = std::sqrt(acc / (double)s->mesh->nc);
+    }
+    return GKS_OK;
+}
+
+// ----------------------------------------------------------- diagnostics --
+
+template <typename T>
+static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, double* d_poly,
+                                   double* d_slopes, int32_t* d_fallback) {
+    const HostPhys& p = s->phys;
+    const bool need_b = p.weno || p.order == 2;
+    const int64_t nc = m.nc;
+    if (need_b) GKS_CHECK_CUDA(Launch<T>::slopes(m, st.Wr, st.slopes, s->stream));
+    else GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, d_fallback, s->stream));
+    if (d_poly) GKS_CHECK_CUDA(Launch<T>::to_double(st.poly, d_poly, 50 * nc, s->stream));
+    if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_debug_reconstruct(gks_state* s, double* d_poly, double* d_slopes,
+                                            int32_t* d_fallback) {
+    if (!s) { set_error("gks_debug_reconstruct: state is NULL"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("state not initialised"); return GKS_E_STATE; }
+    gks_status st = s->fp32 ? debug_recon_impl<float>(s, s->m32, s->s32, d_poly, d_slopes, d_fallback)
+                            : debug_recon_impl<double>(s, s->m64, s->s64, d_poly, d_slopes, d_fallback);
+    if (st != GKS_OK) return st;
+    if (s->own_stream) return gks_sync(s);
+    return GKS_OK;
+}
+
+template <typename T>
+static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, double dt, int stage,
+                                 double* d_rec) {
+    gks_status r = debug_recon_impl<T>(s, m, st, nullptr, nullptr, nullptr);
+    if (r != GKS_OK) return r;
+    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.poly, st.rec, st.ctrl, dt, stage, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::to_double(st.rec, d_rec, (stage == 1 ? 40 : 20) * m.nf, s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_debug_face_records(gks_state* s, double dt, int32_t stage, double* d_rec) {
+    if (!s || !d_rec) { set_error("gks_debug_face_records: NULL argument"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("state not initialised"); return GKS_E_STATE; }
+    if ((stage != 1 && stage != 2) || !(dt > 0.0)) { set_error("stage must be 1 or 2 and dt > 0"); return GKS_E_ARG; }
+    gks_status st = s->fp32 ? debug_rec_impl<float>(s, s->m32, s->s32, dt, stage, d_rec)
+                            : debug_rec_impl<double>(s, s->m64, s->s64, dt, stage, d_rec);
+    if (st != GKS_OK) return st;
+    if (s->own_stream) return gks_sync(s);
+    return GKS_OK;
+}

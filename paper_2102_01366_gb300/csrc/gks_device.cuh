@@ -1,0 +1,361 @@
+// gks_device.cuh -- device-side building blocks of libgks, templated on the
+// working precision T (double: FP64 path; float: FP32-bulk path).
+//
+//   * Maxwellian moments <u^p v^q w^r> over the full space or a half space
+//     (Sec. 2.2; the half-space zeroth and first moments come from erfc and
+//     the Gaussian tail, higher ones from the standard recursion);
+//   * micro-slopes a = a_1 + a_2 u + a_3 v + a_4 w + a_5 (u^2+xi^2)/2 solving
+//     <a psi> = dW / rho (Eq. co) in closed form (the inverse of the 5x5
+//     moment matrix of a Maxwellian);
+//   * the time-dependent kinetic solution at one Gauss point in the face
+//     frame (Eq. 2nd-flux / Eq. 2nd-smooth-flux with the equilibrium state
+//     of Eq. new-equ-part): time integrals of the flux over [0, dt/2] and
+//     [0, dt], and the interface states at t = 0 and t = dt.
+#pragma once
+
+#include <cstdint>
+
+namespace gks {
+
+// --------------------------------------------------------------- math --
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float d_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double d_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float d_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double d_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float d_cbrt(float x) { return cbrtf(x); }
+
+// |x|^(4/3) as x * cbrt(x) for x >= 0
+template <typename T>
+__device__ __forceinline__ T pow43(T x) { return x * d_cbrt(x); }
+
+// Error-free transformation of a sum (Knuth's TwoSum): a + b = s + e exactly.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated accumulator: value = hi + lo.
+template <typename T>
+struct CSum {
+    T hi, lo;
+    __device__ __forceinline__ void init() { hi = T(0); lo = T(0); }
+    __device__ __forceinline__ void add(T x) {
+        T s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ------------------------------------------------------------ params --
+template <typename T>
+struct Phys {
+    T gamma, gm1, K;     // K internal degrees of freedom
+    T tau_eps, tau_c, mu;
+    T eps_w;
+    int viscous, smooth;
+};
+
+// ------------------------------------------------------- Maxwellian --
+template <typename T>
+struct Prim {
+    T rho, u, v, w, lam, p;
+};
+
+template <typename T>
+__device__ __forceinline__ Prim<T> to_prim(const T* W, T gm1) {
+    Prim<T> s;
+    s.rho = W[0];
+    T ir = T(1) / W[0];
+    s.u = W[1] * ir;
+    s.v = W[2] * ir;
+    s.w = W[3] * ir;
+    s.p = gm1 * (W[4] - T(0.5) * (W[1] * s.u + W[2] * s.v + W[3] * s.w));
+    s.lam = T(0.5) * s.rho / s.p;
+    return s;
+}
+
+// normalised moments <u^k> (k < 7) for u (full or half space), v, w and
+// <xi^2>, <xi^4>
+template <typename T>
+struct Tab {
+    T u[7], v[7], w[7];
+    T xi2, xi4;
+};
+
+template <typename T>
+__device__ __forceinline__ void mom_recur(T* m, T U, T h) {
+    // h = 1 / (2 lambda); <u^(k+2)> = U <u^(k+1)> + (k+1) h <u^k>
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m[k + 2] = U * m[k + 1] + T(k + 1) * h * m[k];
+}
+
+// half: +1 restricts u > 0, -1 restricts u < 0, 0 is the whole space
+template <typename T>
+__device__ __forceinline__ void make_tab(Tab<T>& t, const Prim<T>& s, T K, int half) {
+    const T h = T(0.5) / s.lam;
+    if (half == 0) {
+        t.u[0] = T(1);
+        t.u[1] = s.u;
+    } else {
+        const T sg = half > 0 ? T(1) : T(-1);
+        const T sl = d_sqrt(s.lam);
+        t.u[0] = T(0.5) * d_erfc(-sg * sl * s.u);
+        // Gaussian tail term exp(-lam U^2) / (2 sqrt(pi lam))
+        const T inv_sqrt_pi = T(0.56418958354775628695);
+        t.u[1] = s.u * t.u[0] + sg * T(0.5) * inv_sqrt_pi * d_exp(-s.lam * s.u * s.u) / sl;
+    }
+    mom_recur(t.u, s.u, h);
+    t.v[0] = T(1);
+    t.v[1] = s.v;
+    mom_recur(t.v, s.v, h);
+    t.w[0] = T(1);
+    t.w[1] = s.w;
+    mom_recur(t.w, s.w, h);
+    t.xi2 = K * h;
+    t.xi4 = (K * K + T(2) * K) * h * h;
+}
+
+// only the u-moments change between the full space and a half space
+template <typename T>
+__device__ __forceinline__ void make_half_u(Tab<T>& t, const Prim<T>& s, int half) {
+    const T h = T(0.5) / s.lam;
+    const T sg = half > 0 ? T(1) : T(-1);
+    const T sl = d_sqrt(s.lam);
+    t.u[0] = T(0.5) * d_erfc(-sg * sl * s.u);
+    const T inv_sqrt_pi = T(0.56418958354775628695);
+    t.u[1] = s.u * t.u[0] + sg * T(0.5) * inv_sqrt_pi * d_exp(-s.lam * s.u * s.u) / sl;
+    mom_recur(t.u, s.u, h);
+}
+
+template <int P, int Q, int R, typename T>
+__device__ __forceinline__ T Gm(const Tab<T>& t) {
+    return t.u[P] * t.v[Q] * t.w[R];
+}
+
+// <eps u^P v^Q w^R>, eps = (u^2 + v^2 + w^2 + xi^2) / 2
+template <int P, int Q, int R, typename T>
+__device__ __forceinline__ T Em(const Tab<T>& t) {
+    return T(0.5) * (Gm<P + 2, Q, R>(t) + Gm<P, Q + 2, R>(t) + Gm<P, Q, R + 2>(t) + t.xi2 * Gm<P, Q, R>(t));
+}
+
+// <eps^2 u^P v^Q w^R>
+template <int P, int Q, int R, typename T>
+__device__ __forceinline__ T E2m(const Tab<T>& t) {
+    return T(0.25) * (Gm<P + 4, Q, R>(t) + Gm<P, Q + 4, R>(t) + Gm<P, Q, R + 4>(t) + t.xi4 * Gm<P, Q, R>(t) +
+                      T(2) * (Gm<P + 2, Q + 2, R>(t) + Gm<P + 2, Q, R + 2>(t) + Gm<P, Q + 2, R + 2>(t)) +
+                      T(2) * t.xi2 * (Gm<P + 2, Q, R>(t) + Gm<P, Q + 2, R>(t) + Gm<P, Q, R + 2>(t)));
+}
+
+// out_alpha += c * <psi_alpha u^P v^Q w^R>
+template <int P, int Q, int R, typename T>
+__device__ __forceinline__ void acc_psi(const Tab<T>& t, T c, T* out) {
+    out[0] += c * Gm<P, Q, R>(t);
+    out[1] += c * Gm<P + 1, Q, R>(t);
+    out[2] += c * Gm<P, Q + 1, R>(t);
+    out[3] += c * Gm<P, Q, R + 1>(t);
+    out[4] += c * Em<P, Q, R>(t);
+}
+
+// out_alpha += c * <psi_alpha (a.psi) u^P v^Q w^R>
+template <int P, int Q, int R, typename T>
+__device__ __forceinline__ void acc_apsi(const Tab<T>& t, const T* a, T c, T* out) {
+    const T a0 = c * a[0], a1 = c * a[1], a2 = c * a[2], a3 = c * a[3], a4 = c * a[4];
+    out[0] += a0 * Gm<P, Q, R>(t) + a1 * Gm<P + 1, Q, R>(t) + a2 * Gm<P, Q + 1, R>(t) +
+              a3 * Gm<P, Q, R + 1>(t) + a4 * Em<P, Q, R>(t);
+    out[1] += a0 * Gm<P + 1, Q, R>(t) + a1 * Gm<P + 2, Q, R>(t) + a2 * Gm<P + 1, Q + 1, R>(t) +
+              a3 * Gm<P + 1, Q, R + 1>(t) + a4 * Em<P + 1, Q, R>(t);
+    out[2] += a0 * Gm<P, Q + 1, R>(t) + a1 * Gm<P + 1, Q + 1, R>(t) + a2 * Gm<P, Q + 2, R>(t) +
+              a3 * Gm<P, Q + 1, R + 1>(t) + a4 * Em<P, Q + 1, R>(t);
+    out[3] += a0 * Gm<P, Q, R + 1>(t) + a1 * Gm<P + 1, Q, R + 1>(t) + a2 * Gm<P, Q + 1, R + 1>(t) +
+              a3 * Gm<P, Q, R + 2>(t) + a4 * Em<P, Q, R + 1>(t);
+    out[4] += a0 * Em<P, Q, R>(t) + a1 * Em<P + 1, Q, R>(t) + a2 * Em<P, Q + 1, R>(t) +
+              a3 * Em<P, Q, R + 1>(t) + a4 * E2m<P, Q, R>(t);
+}
+
+// out += c * sum_i <psi (a_i . psi) u_i u^P>   (P = 0 or 1 extra powers of u)
+template <int P, typename T>
+__device__ __forceinline__ void acc_grad(const Tab<T>& t, const T (*a)[5], T c, T* out) {
+    acc_apsi<P + 1, 0, 0>(t, a[0], c, out);
+    acc_apsi<P, 1, 0>(t, a[1], c, out);
+    acc_apsi<P, 0, 1>(t, a[2], c, out);
+}
+
+// Micro-slope of a Maxwellian: solves <a psi> = b (full space) for a, with
+// the closed-form inverse of the moment matrix.
+template <typename T>
+__device__ __forceinline__ void micro_slope(const Prim<T>& s, T K, const T* b, T* a) {
+    const T q = s.u * s.u + s.v * s.v + s.w * s.w;
+    const T e = q + (K + T(3)) * T(0.5) / s.lam;  // 2 <eps>
+    const T r1 = b[1] - s.u * b[0];
+    const T r2 = b[2] - s.v * b[0];
+    const T r3 = b[3] - s.w * b[0];
+    const T r4 = T(2) * b[4] - e * b[0];
+    const T a4 = T(4) * s.lam * s.lam / (K + T(3)) * (r4 - T(2) * (s.u * r1 + s.v * r2 + s.w * r3));
+    const T tl = T(2) * s.lam;
+    a[1] = tl * r1 - s.u * a4;
+    a[2] = tl * r2 - s.v * a4;
+    a[3] = tl * r3 - s.w * a4;
+    a[4] = a4;
+    a[0] = b[0] - s.u * a[1] - s.v * a[2] - s.w * a[3] - T(0.5) * a4 * e;
+}
+
+// Slopes a_x, a_y, a_z and A of a Maxwellian with conservative gradients
+// g[i][q] (Eq. co): <a_i psi> = g_i / rho, <(A + sum_i a_i u_i) psi> = 0.
+template <typename T>
+__device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& full, T K,
+                                             const T (*g)[5], T (*a)[5], T* A) {
+    const T ir = T(1) / s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T b[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) b[k] = g[i][k] * ir;
+        micro_slope(s, K, b, a[i]);
+    }
+    T r[5] = {T(0), T(0), T(0), T(0), T(0)};
+    acc_grad<0>(full, a, T(-1), r);
+    micro_slope(s, K, r, A);
+}
+
+// Time-dependent kinetic solution at one Gauss point, face frame.
+//   Wl, Wr: states; gl[i][q], gr[i][q]: gradients (direction i, comp q)
+// Outputs Fh = int_0^{dt/2} F, F = int_0^dt F, W0 = W(0), Wdt = W(dt).
+template <typename T>
+__device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const T (*gl)[5],
+                                          const T* Wr, const T (*gr)[5], T dt, T* Fh, T* F,
+                                          T* W0, T* Wdt) {
+    const Prim<T> L = to_prim(Wl, ph.gm1);
+    const Prim<T> R = to_prim(Wr, ph.gm1);
+
+    // -- equilibrium state at the interface, Eq. new-equ-part (values) --
+    T Wc[5] = {T(0), T(0), T(0), T(0), T(0)};
+    {
+        Tab<T> t;
+        make_tab(t, L, ph.K, +1);
+        acc_psi<0, 0, 0>(t, L.rho, Wc);
+        make_tab(t, R, ph.K, -1);
+        acc_psi<0, 0, 0>(t, R.rho, Wc);
+    }
+    const Prim<T> C = to_prim(Wc, ph.gm1);
+
+    // -- collision times, Sec. 2.2 --
+    const T tau = ph.viscous ? ph.mu / C.p : T(0);
+    const T jump = d_abs((L.p - R.p) / (L.p + R.p)) * dt;
+    const T tau_n = (ph.viscous ? ph.mu / C.p : ph.tau_eps * dt) + ph.tau_c * jump;
+
+    // -- time coefficients: integrals over [0, d] for d = dt/2, dt --
+    T k0[2], k1[2], q1[2], q2[2], q3[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const T d = h == 0 ? T(0.5) * dt : dt;
+        const T E = d_exp(-d / tau_n);
+        k0[h] = tau_n * (T(1) - E);                      // int e
+        k1[h] = tau_n * (tau_n * (T(1) - E) - d * E);    // int t e
+        q1[h] = d - k0[h];                               // int C1
+        q2[h] = k1[h] + tau * k0[h] - tau * d;           // int C2
+        q3[h] = T(0.5) * d * d - tau * d + tau * k0[h];  // int C3
+    }
+    const T Edt = d_exp(-dt / tau_n);
+
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Fh[k] = T(0);
+        F[k] = T(0);
+        W0[k] = T(0);
+        Wdt[k] = T(0);
+    }
+    T dWc[3][5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dWc[i][k] = T(0);
+
+    // -- kinetic (initial-state) parts of the two sides --
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const Prim<T> S = side == 0 ? L : R;
+        const T (*g)[5] = side == 0 ? gl : gr;
+        Tab<T> t;
+        make_tab(t, S, ph.K, 0);
+        T a[3][5], A[5];
+        state_slopes(S, t, ph.K, g, a, A);
+        make_half_u(t, S, side == 0 ? +1 : -1);
+        // slope of the interface equilibrium, Eq. new-equ-part (gradients)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
+        if (!ph.smooth) {
+            // e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1), Eq. 2nd-flux
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                T* out = h == 0 ? Fh : F;
+                const T c0 = S.rho * k0[h];
+                const T c1 = -S.rho * (tau * k0[h] + k1[h]);
+                const T c2 = -S.rho * tau * k0[h];
+                acc_psi<1, 0, 0>(t, c0, out);
+                acc_grad<1>(t, a, c1, out);
+                acc_apsi<1, 0, 0>(t, A, c2, out);
+            }
+            // point values at t = 0 (e = 1) and t = dt (e = Edt)
+            acc_psi<0, 0, 0>(t, S.rho, W0);
+            acc_grad<0>(t, a, -S.rho * tau, W0);
+            acc_apsi<0, 0, 0>(t, A, -S.rho * tau, W0);
+            acc_psi<0, 0, 0>(t, S.rho * Edt, Wdt);
+            acc_grad<0>(t, a, -S.rho * (tau + dt) * Edt, Wdt);
+            acc_apsi<0, 0, 0>(t, A, -S.rho * tau * Edt, Wdt);
+        }
+    }
+
+    // -- hydrodynamic (equilibrium) part --
+    {
+        Tab<T> t;
+        make_tab(t, C, ph.K, 0);
+        T ac[3][5], Ac[5];
+        state_slopes(C, t, ph.K, dWc, ac, Ac);
+        if (ph.smooth) {
+            // f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t, Eq. 2nd-smooth-flux
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                T* out = h == 0 ? Fh : F;
+                const T d = h == 0 ? T(0.5) * dt : dt;
+                acc_psi<1, 0, 0>(t, C.rho * d, out);
+                acc_grad<1>(t, ac, -C.rho * tau * d, out);
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * d * d - tau * d), out);
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) W0[k] = Wc[k];
+            acc_grad<0>(t, ac, -C.rho * tau, W0);
+            acc_apsi<0, 0, 0>(t, Ac, -C.rho * tau, W0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Wdt[k] = W0[k];
+            acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, Wdt);
+        } else {
+            // C1 g^c + C2 a^c.u g^c + C3 A^c g^c, Eq. 2nd-flux
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                T* out = h == 0 ? Fh : F;
+                acc_psi<1, 0, 0>(t, C.rho * q1[h], out);
+                acc_grad<1>(t, ac, C.rho * q2[h], out);
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * q3[h], out);
+            }
+            // t = 0: C1 = C2 = C3 = 0.  t = dt:
+            const T C1 = T(1) - Edt, C2 = (dt + tau) * Edt - tau, C3 = dt - tau + tau * Edt;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Wdt[k] += C1 * Wc[k];
+            acc_grad<0>(t, ac, C.rho * C2, Wdt);
+            acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, Wdt);
+        }
+    }
+}
+
+}  // namespace gks

@@ -1,0 +1,84 @@
+// gks_kernels.h -- device data views and kernel launchers of libgks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gks {
+
+// control block in device memory (doubles)
+enum { CTRL_T = 0, CTRL_DT = 1, CTRL_DT_FIXED = 2, CTRL_T_END = 3, CTRL_N = 8 };
+// per-block partial results of the update / time-step kernels
+enum { PART_DTMIN = 0, PART_RES = 1, PART_N = 6 };
+// device error flags
+enum { ERR_STATE = 1 };
+
+constexpr int FLUX_FACES = 32;       // faces per flux block (3 threads each)
+constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
+constexpr int FGEO = 24;             // reals per face geometry record
+
+template <typename T>
+struct DevMesh {
+    int64_t nc, nf;
+    const int32_t* nbr;    // [4][nc], -1 = none
+    const int32_t* cface;  // [4][nc] face * 2 + side (side 1 = right)
+    const double* inv_vol; // [nc]
+    const T* vol23;        // [nc] |Omega|^(2/3)
+    const T* vol43;        // [nc] |Omega|^(4/3)
+    const T* dr;           // [nc]
+    const T* mom2;         // [6][nc]
+    const T* cgp;          // [36][nc] the cell's face Gauss points about its centroid
+    const T* M1;           // [12][nc]
+    const T* M2;           // [144][nc]
+    const int32_t* flr;    // [2][nf]
+    const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
+};
+
+template <typename T>
+struct DevState {
+    double* Wd;   // [5][nc] master cell averages (FP64)
+    T* Wr;        // [5][nc] working copy (aliases Wd in FP64)
+    T* dW;        // [15][nc]
+    T* Ws;        // [5][nc] stage state W*
+    T* dWs;       // [15][nc]
+    double* S;    // [5][nc] saved stage-1 flux term
+    T* G;         // [15][nc] saved stage-1 gradient term
+    T* slopes;    // [nc][15]
+    T* poly;      // [nc][50]
+    T* rec;       // [nf][40]
+    double* ctrl; // [CTRL_N]
+    double* part; // [n_part_blocks][PART_N]
+    int32_t* err;
+};
+
+struct HostPhys {
+    double gamma, cfl, mu, eps_weno, tau_eps, tau_c;
+    int weno, order, smooth, viscous;
+};
+
+template <typename T>
+struct Launch {
+    // stage pieces
+    static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, cudaStream_t s);
+    static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
+                             const T* slopes, T* poly, int32_t* fallback, cudaStream_t s);
+    static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* poly, T* rec,
+                            const double* ctrl, double dt_override, int stage, cudaStream_t s);
+    static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
+    static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,
+                               cudaStream_t s);
+    static cudaError_t dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* W,
+                                   double* part, cudaStream_t s);
+    // conversions for diagnostics
+    static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
+    static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
+};
+
+cudaError_t launch_dt_finalize(const double* part, int nblk, double cfl, double* ctrl,
+                               cudaStream_t s);
+cudaError_t launch_set_control(double* ctrl, double dt_fixed, double t_end, int reset_time,
+                               cudaStream_t s);
+int update_blocks(int64_t nc);
+
+}  // namespace gks

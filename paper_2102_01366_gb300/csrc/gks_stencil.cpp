@@ -1,0 +1,232 @@
+// gks_stencil.cpp -- FP64 least-squares operators of the compact
+// reconstruction (Sec. 4.1 and Sec. 4.3), built once per mesh on the host.
+//
+// P1 (Eq. p1-stenci-condition): slopes b from the neighbours' averages in the
+// least-squares sense, M1 = R^-1 Q^T from a Householder QR of the offsets.
+//
+// P2 (Eqs. large-stenci-condition-1/2): P2 = Qbar_0 + sum_k a_k p^k with the
+// zero-mean basis of Eq. base (x, y, z, xx, xy, xz, yy, yz, zz about the
+// centroid).  The neighbours' averages are matched exactly, the neighbours'
+// averaged gradients in the least-squares sense.  Solved by the null-space
+// method: a QR of the constraint matrix splits a into a constrained part
+// and a free part, and the free part is the least-squares solution of the
+// projected gradient rows (a second QR).  Unknowns are scaled by powers of
+// h0 = |Omega|^(1/3) and gradient rows by h0 so that both QRs work on O(1)
+// entries; the result is unscaled before it is stored.
+#include <cmath>
+#include <cstring>
+
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+// Householder QR of A (m x n, m >= n, row-major).  On return Q (m x m) and
+// R (n x n, upper) satisfy A = Q[:, :n] R.
+void householder_qr(int m, int n, const double* A, double* Q, double* R) {
+    double W[16 * 16];
+    std::memcpy(W, A, sizeof(double) * m * n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Q[i * m + j] = i == j ? 1.0 : 0.0;
+    double v[16];
+    for (int k = 0; k < n; ++k) {
+        double norm = 0.0;
+        for (int i = k; i < m; ++i) norm += W[i * n + k] * W[i * n + k];
+        norm = std::sqrt(norm);
+        if (norm == 0.0) continue;
+        double alpha = W[k * n + k] > 0.0 ? -norm : norm;
+        for (int i = 0; i < m; ++i) v[i] = 0.0;
+        for (int i = k; i < m; ++i) v[i] = W[i * n + k];
+        v[k] -= alpha;
+        double vn = 0.0;
+        for (int i = k; i < m; ++i) vn += v[i] * v[i];
+        if (vn == 0.0) continue;
+        // W <- (I - 2 v v^T / vn) W
+        for (int j = k; j < n; ++j) {
+            double s = 0.0;
+            for (int i = k; i < m; ++i) s += v[i] * W[i * n + j];
+            s *= 2.0 / vn;
+            for (int i = k; i < m; ++i) W[i * n + j] -= s * v[i];
+        }
+        // Q <- Q (I - 2 v v^T / vn)
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int l = k; l < m; ++l) s += Q[i * m + l] * v[l];
+            s *= 2.0 / vn;
+            for (int l = k; l < m; ++l) Q[i * m + l] -= s * v[l];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) R[i * n + j] = j >= i ? W[i * n + j] : 0.0;
+}
+
+// condition proxy: smallest over largest |R_ii|
+double diag_ratio(int n, const double* R) {
+    double lo = INFINITY, hi = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double d = std::fabs(R[i * n + i]);
+        lo = std::fmin(lo, d);
+        hi = std::fmax(hi, d);
+    }
+    return hi > 0.0 ? lo / hi : 0.0;
+}
+
+// X (n x r) <- R^-1 X for upper-triangular R (n x n)
+void upper_solve(int n, const double* R, int r, double* X) {
+    for (int c = 0; c < r; ++c)
+        for (int i = n - 1; i >= 0; --i) {
+            double s = X[i * r + c];
+            for (int j = i + 1; j < n; ++j) s -= R[i * n + j] * X[j * r + c];
+            X[i * r + c] = s / R[i * n + i];
+        }
+}
+
+// X (n x r) <- R^-T X for upper-triangular R (n x n)
+void lower_solve_transposed(int n, const double* R, int r, double* X) {
+    for (int c = 0; c < r; ++c)
+        for (int i = 0; i < n; ++i) {
+            double s = X[i * r + c];
+            for (int j = 0; j < i; ++j) s -= R[j * n + i] * X[j * r + c];
+            X[i * r + c] = s / R[i * n + i];
+        }
+}
+
+const int PI_[6] = {0, 0, 0, 1, 1, 2};
+const int PJ_[6] = {0, 1, 2, 1, 2, 2};
+
+bool cell_stencil(const gks_mesh& m, int64_t c, double* M1, double* M2) {
+    int fl[4], nn = 0;
+    double d[4][3];
+    for (int f = 0; f < 4; ++f) {
+        int64_t nb = m.nbr[c * 4 + f];
+        if (nb < 0) continue;
+        for (int a = 0; a < 3; ++a)
+            d[nn][a] = (m.cen[nb * 3 + a] + (double)m.nbr_img[(c * 4 + f) * 3 + a] * m.period[a]) -
+                       m.cen[c * 3 + a];
+        fl[nn++] = f;
+    }
+    std::memset(M1, 0, sizeof(double) * 12);
+    std::memset(M2, 0, sizeof(double) * 144);
+    if (nn < 3) return false;
+    const double h0 = std::cbrt(m.vol[c]);
+
+    // ---- P1: min |A b - dq|, A rows d_f / h0 ----------------------------
+    {
+        double A[4 * 3], Q[16], R[9];
+        for (int r = 0; r < nn; ++r)
+            for (int a = 0; a < 3; ++a) A[r * 3 + a] = d[r][a] / h0;
+        householder_qr(nn, 3, A, Q, R);
+        if (diag_ratio(3, R) < 1e-12) return false;
+        double X[3 * 4];
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < nn; ++r) X[i * nn + r] = Q[r * nn + i];  // Q1^T
+        upper_solve(3, R, nn, X);
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < nn; ++r) M1[i * 4 + fl[r]] = X[i * nn + r] / h0;
+    }
+
+    // ---- P2: constrained least squares ----------------------------------
+    double sc[9];
+    for (int k = 0; k < 9; ++k) sc[k] = k < 3 ? h0 : h0 * h0;
+    const double* M0 = &m.mom2[c * 6];
+    double C[4 * 9];        // constraint rows (neighbour averages of the basis)
+    double B[12 * 9];       // gradient rows
+    const int nb_rows = 3 * nn;
+    for (int r = 0; r < nn; ++r) {
+        int64_t nb = m.nbr[c * 4 + fl[r]];
+        const double* Mn = &m.mom2[nb * 6];
+        for (int k = 0; k < 3; ++k) C[r * 9 + k] = d[r][k] / sc[k];
+        for (int q = 0; q < 6; ++q)
+            C[r * 9 + 3 + q] = (Mn[q] - M0[q] + d[r][PI_[q]] * d[r][PJ_[q]]) / sc[3 + q];
+        for (int l = 0; l < 3; ++l) {
+            double* row = &B[(3 * r + l) * 9];
+            for (int k = 0; k < 3; ++k) row[k] = (k == l ? h0 : 0.0) / sc[k];
+            for (int q = 0; q < 6; ++q) {
+                double g = (PI_[q] == l ? d[r][PJ_[q]] : 0.0) + (PJ_[q] == l ? d[r][PI_[q]] : 0.0);
+                row[3 + q] = h0 * g / sc[3 + q];
+            }
+        }
+    }
+    // QR of C^T (9 x nn)
+    double Ct[9 * 4], Qc[81], Rc[16];
+    for (int k = 0; k < 9; ++k)
+        for (int r = 0; r < nn; ++r) Ct[k * nn + r] = C[r * 9 + k];
+    householder_qr(9, nn, Ct, Qc, Rc);
+    if (diag_ratio(nn, Rc) < 1e-12) return false;
+    const int nz = 9 - nn;
+    // BQ2 (nb_rows x nz), BQ1 (nb_rows x nn)
+    double BQ2[12 * 6], BQ1[12 * 4];
+    for (int i = 0; i < nb_rows; ++i) {
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 9; ++k) s += B[i * 9 + k] * Qc[k * 9 + nn + j];
+            BQ2[i * nz + j] = s;
+        }
+        for (int j = 0; j < nn; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 9; ++k) s += B[i * 9 + k] * Qc[k * 9 + j];
+            BQ1[i * nn + j] = s;
+        }
+    }
+    double Qb[144], Rb[36];
+    householder_qr(nb_rows, nz, BQ2, Qb, Rb);
+    if (diag_ratio(nz, Rb) < 1e-12) return false;
+    // Z = Q2 Rb^-1 Qb1^T  (9 x nb_rows)
+    double Y[6 * 12];
+    for (int j = 0; j < nz; ++j)
+        for (int i = 0; i < nb_rows; ++i) Y[j * nb_rows + i] = Qb[i * nb_rows + j];
+    upper_solve(nz, Rb, nb_rows, Y);
+    double Z[9 * 12];
+    for (int k = 0; k < 9; ++k)
+        for (int i = 0; i < nb_rows; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < nz; ++j) s += Qc[k * 9 + nn + j] * Y[j * nb_rows + i];
+            Z[k * nb_rows + i] = s;
+        }
+    // X = Rc^-T (nn x nn) applied to the identity
+    double X[16];
+    for (int i = 0; i < nn; ++i)
+        for (int j = 0; j < nn; ++j) X[i * nn + j] = i == j ? 1.0 : 0.0;
+    lower_solve_transposed(nn, Rc, nn, X);
+    // Mq = Q1 X - Z BQ1 X  (9 x nn)
+    double BX[12 * 4];
+    for (int i = 0; i < nb_rows; ++i)
+        for (int j = 0; j < nn; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nn; ++l) s += BQ1[i * nn + l] * X[l * nn + j];
+            BX[i * nn + j] = s;
+        }
+    for (int k = 0; k < 9; ++k) {
+        for (int j = 0; j < nn; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nn; ++l) s += Qc[k * 9 + l] * X[l * nn + j];
+            for (int i = 0; i < nb_rows; ++i) s -= Z[k * nb_rows + i] * BX[i * nn + j];
+            M2[k * 16 + fl[j]] = s / sc[k];
+        }
+        for (int r = 0; r < nn; ++r)
+            for (int l = 0; l < 3; ++l)
+                M2[k * 16 + 4 + 3 * fl[r] + l] = Z[k * nb_rows + 3 * r + l] * h0 / sc[k];
+    }
+    return true;
+}
+
+}  // namespace
+
+gks_status build_stencils(gks_mesh& m) {
+    m.M1.assign((size_t)m.nc * 12, 0.0);
+    m.M2.assign((size_t)m.nc * 144, 0.0);
+    m.singular.assign((size_t)m.nc, 0);
+    m.n_singular = 0;
+    for (int64_t c = 0; c < m.nc; ++c) {
+        if (!cell_stencil(m, c, &m.M1[c * 12], &m.M2[c * 144])) {
+            m.singular[c] = 1;
+            ++m.n_singular;
+            std::memset(&m.M1[c * 12], 0, sizeof(double) * 12);
+            std::memset(&m.M2[c * 144], 0, sizeof(double) * 144);
+        }
+    }
+    m.has_stencils = true;
+    return GKS_OK;
+}
+
+}  // namespace gks

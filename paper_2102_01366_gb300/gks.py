@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libgks (include/gks.h), same names as the C ABI.
+
+Argument marshalling only: every step of the scheme runs in libgks.  PyTorch
+supplies device memory (the workspace and the state tensors) and the CUDA
+stream.  There is no fallback: if libgks.so is missing or fails to load, every
+entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgks.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gks.h")
+
+GKS_OK = 0
+STATUS = {0: "GKS_OK", -1: "GKS_E_ARG", -2: "GKS_E_MESH", -3: "GKS_E_STENCIL", -4: "GKS_E_STATE",
+          -5: "GKS_E_CUDA", -6: "GKS_E_TIMEOUT", -7: "GKS_E_NOMEM", -8: "GKS_E_UNSUPPORTED"}
+
+
+class GksError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s -> %s: %s" % (fn, STATUS.get(status, status), msg))
+        self.status = status
+
+
+class gks_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double),
+                ("eps_weno", C.c_double), ("tau_eps", C.c_double), ("tau_c", C.c_double),
+                ("weno", C.c_int32), ("order", C.c_int32), ("smooth_flux", C.c_int32),
+                ("viscous", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+_vp = C.c_void_p
+_i64p = C.POINTER(C.c_int64)
+
+
+def header_functions():
+    """Names of the functions declared in include/gks.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gks_[a-z0-9_]+)\s*\(", src)))
+
+
+def lib():
+    """Load libgks.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgks.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "gks_params_default": (None, [C.POINTER(gks_params)]),
+        "gks_last_error": (C.c_char_p, []),
+        "gks_mesh_create": (C.c_int32, [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.POINTER(_vp)]),
+        "gks_mesh_destroy": (None, [_vp]),
+        "gks_mesh_info": (C.c_int32, [_vp, _i64p, _i64p, _i64p]),
+        "gks_mesh_topology": (C.c_int32, [_vp] * 6),
+        "gks_mesh_geometry": (C.c_int32, [_vp] * 9),
+        "gks_stencil_build": (C.c_int32, [_vp, _i64p]),
+        "gks_mesh_stencils": (C.c_int32, [_vp, _vp, _vp]),
+        "gks_workspace_bytes": (C.c_size_t, [_vp, C.POINTER(gks_params)]),
+        "gks_state_create": (C.c_int32, [_vp, C.POINTER(gks_params), _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
+        "gks_state_destroy": (None, [_vp]),
+        "gks_init_state": (C.c_int32, [_vp, _vp, _vp]),
+        "gks_step": (C.c_int32, [_vp, C.c_int32, C.c_double, C.c_double]),
+        "gks_sync": (C.c_int32, [_vp]),
+        "gks_get_state": (C.c_int32, [_vp, _vp, _vp]),
+        "gks_get_time": (C.c_int32, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "gks_step_host": (C.c_int32, [_vp, _vp, _vp, C.c_int32, C.c_double, _vp, _vp]),
+        "gks_timestep": (C.c_int32, [_vp, C.POINTER(C.c_double)]),
+        "gks_step_timed": (C.c_int32, [_vp, C.c_int32, C.c_double, C.c_double, _vp, _vp]),
+        "gks_residual": (C.c_int32, [_vp, _vp]),
+        "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
+        "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != GKS_OK:
+        raise GksError(name, st, lib().gks_last_error().decode())
+    return st
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(_vp) if a is not None else None
+
+
+def params(gamma=1.4, cfl=1.0, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, weno=1, order=3,
+           smooth_flux=0, viscous=0, precision=0):
+    p = gks_params()
+    lib().gks_params_default(C.byref(p))
+    p.gamma, p.cfl, p.mu, p.eps_weno, p.tau_eps, p.tau_c = gamma, cfl, mu, eps_weno, tau_eps, tau_c
+    p.weno, p.order, p.smooth_flux, p.viscous, p.precision = weno, order, smooth_flux, viscous, precision
+    return p
+
+
+class Mesh:
+    """gks_mesh: connectivity, FP64 geometry and stencils (host object)."""
+
+    def __init__(self, mesh, build_stencils=True):
+        self._h = _vp()
+        xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+        tet = np.ascontiguousarray(mesh["tet"], dtype=np.int64)
+        shift = np.ascontiguousarray(mesh["shift"], dtype=np.int8)
+        period = np.ascontiguousarray(mesh["period"], dtype=np.float64)
+        _call("gks_mesh_create", _np_ptr(xyz), xyz.shape[0], _np_ptr(tet), _np_ptr(shift),
+              tet.shape[0], _np_ptr(period), C.byref(self._h))
+        nc, nf, nb = C.c_int64(), C.c_int64(), C.c_int64()
+        _call("gks_mesh_info", self._h, C.byref(nc), C.byref(nf), C.byref(nb))
+        self.nc, self.nf, self.n_boundary = nc.value, nf.value, nb.value
+        self.n_singular = None
+        if build_stencils:
+            ns = C.c_int64()
+            _call("gks_stencil_build", self._h, C.byref(ns))
+            self.n_singular = ns.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.gks_mesh_destroy(self._h)
+            self._h = _vp()
+
+    def topology(self):
+        nc, nf = self.nc, self.nf
+        out = dict(face_v=np.zeros((nf, 3), np.int64), face_lr=np.zeros((nf, 2), np.int64),
+                   nbr=np.zeros((nc, 4), np.int64), csr_face=np.zeros((nc, 4), np.int64),
+                   csr_sign=np.zeros((nc, 4), np.int8))
+        _call("gks_mesh_topology", self._h, *[_np_ptr(out[k]) for k in
+                                              ("face_v", "face_lr", "nbr", "csr_face", "csr_sign")])
+        return out
+
+    def geometry(self):
+        nc, nf = self.nc, self.nf
+        out = dict(vol=np.zeros(nc), cen=np.zeros((nc, 3)), mom2=np.zeros((nc, 6)), dr=np.zeros(nc),
+                   farea=np.zeros(nf), fnorm=np.zeros((nf, 3)), gp_l=np.zeros((nf, 3, 3)),
+                   gp_r=np.zeros((nf, 3, 3)))
+        _call("gks_mesh_geometry", self._h, *[_np_ptr(out[k]) for k in
+                                              ("vol", "cen", "mom2", "dr", "farea", "fnorm", "gp_l", "gp_r")])
+        return out
+
+    def stencils(self):
+        M1 = np.zeros((self.nc, 3, 4))
+        M2 = np.zeros((self.nc, 9, 16))
+        _call("gks_mesh_stencils", self._h, _np_ptr(M1), _np_ptr(M2))
+        return M1, M2
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class State:
+    """gks_state over a torch-allocated device workspace and a torch stream."""
+
+    def __init__(self, mesh: Mesh, p: gks_params, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.mesh = mesh
+        self.params = p
+        self.device = torch.device(device)
+        nbytes = lib().gks_workspace_bytes(mesh._h, C.byref(p))
+        if nbytes == 0:
+            raise GksError("gks_workspace_bytes", -1, lib().gks_last_error().decode())
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = self.workspace.data_ptr() + off
+        self.workspace_bytes = nbytes
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self._h = _vp()
+        with torch.cuda.device(self.device):
+            _call("gks_state_create", mesh._h, C.byref(p), C.c_void_p(self._ws_ptr), nbytes,
+                  C.c_void_p(self.stream.cuda_stream), C.byref(self._h))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.gks_state_destroy(self._h)
+            self._h = _vp()
+
+    # -- state --------------------------------------------------------------
+    def init(self, W, dW):
+        """W [5, nc], dW [15, nc] float64 (numpy or torch)."""
+        t = self.torch
+        W = t.as_tensor(np.ascontiguousarray(W) if isinstance(W, np.ndarray) else W,
+                        dtype=t.float64, device=self.device).contiguous()
+        dW = t.as_tensor(np.ascontiguousarray(dW) if isinstance(dW, np.ndarray) else dW,
+                         dtype=t.float64, device=self.device).contiguous()
+        assert W.shape == (5, self.mesh.nc) and dW.shape == (15, self.mesh.nc)
+        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        _call("gks_init_state", self._h, _dptr(W), _dptr(dW))
+        self._keep = (W, dW)  # alive until the stream has consumed them
+        self.sync()
+        self._keep = None
+
+    def step(self, nsteps=1, dt_fixed=0.0, t_end=0.0):
+        _call("gks_step", self._h, int(nsteps), float(dt_fixed), float(t_end))
+
+    def sync(self):
+        _call("gks_sync", self._h)
+
+    def get(self):
+        """(W [5, nc], dW [15, nc]) as float64 torch tensors."""
+        t = self.torch
+        W = t.empty((5, self.mesh.nc), dtype=t.float64, device=self.device)
+        dW = t.empty((15, self.mesh.nc), dtype=t.float64, device=self.device)
+        _call("gks_get_state", self._h, _dptr(W), _dptr(dW))
+        self.sync()
+        return W, dW
+
+    def time(self):
+        tt, dt = C.c_double(), C.c_double()
+        _call("gks_get_time", self._h, C.byref(tt), C.byref(dt))
+        return tt.value, dt.value
+
+    KERNELS = ("dt", "slopes", "recon", "flux1", "update1", "flux2", "update2")
+
+    def step_timed(self, nsteps=1, dt_fixed=0.0, t_end=0.0):
+        """Kernel-by-kernel steps with CUDA events between launches; returns
+        {kernel class: (total ms, launches)}."""
+        ms = np.zeros(len(self.KERNELS))
+        cnt = np.zeros(len(self.KERNELS), np.int64)
+        _call("gks_step_timed", self._h, int(nsteps), float(dt_fixed), float(t_end), _np_ptr(ms), _np_ptr(cnt))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNELS)}
+
+    def timestep(self):
+        dt = C.c_double()
+        _call("gks_timestep", self._h, C.byref(dt))
+        return dt.value
+
+    def residual(self):
+        out = np.zeros(5)
+        _call("gks_residual", self._h, _np_ptr(out))
+        return out
+
+    def step_host(self, W_host, dW_host, nsteps=1, dt_fixed=0.0, W_out=None, dW_out=None):
+        """Host buffers in and out (torch CPU tensors, pinned for async copies)."""
+        W_out = W_host if W_out is None else W_out
+        dW_out = dW_host if dW_out is None else dW_out
+        _call("gks_step_host", self._h, C.c_void_p(W_host.data_ptr()), C.c_void_p(dW_host.data_ptr()),
+              int(nsteps), float(dt_fixed), C.c_void_p(W_out.data_ptr()), C.c_void_p(dW_out.data_ptr()))
+        return W_out, dW_out
+
+    def run(self, nsteps=None, t_end=None, dt_fixed=0.0, chunk=64):
+        """Advance nsteps, or until t_end (polling the device time per chunk)."""
+        if t_end is None:
+            self.step(nsteps, dt_fixed, 0.0)
+            self.sync()
+            return self.time()[0]
+        while True:
+            self.step(chunk, dt_fixed, t_end)
+            self.sync()
+            tt, dt = self.time()
+            if tt >= t_end * (1 - 1e-14) or dt <= 0.0:
+                return tt
+
+    # -- diagnostics ----------------------------------------------------------
+    def debug_reconstruct(self):
+        t = self.torch
+        nc = self.mesh.nc
+        poly = t.empty((nc, 5, 10), dtype=t.float64, device=self.device)
+        slopes = t.empty((nc, 5, 3), dtype=t.float64, device=self.device)
+        fb = t.empty((nc,), dtype=t.int32, device=self.device)
+        _call("gks_debug_reconstruct", self._h, _dptr(poly), _dptr(slopes), _dptr(fb))
+        self.sync()
+        return poly, slopes, fb
+
+    def debug_face_records(self, dt, stage):
+        t = self.torch
+        rec = t.empty((self.mesh.nf, 40 if stage == 1 else 20), dtype=t.float64, device=self.device)
+        _call("gks_debug_face_records", self._h, float(dt), int(stage), _dptr(rec))
+        self.sync()
+        return rec

@@ -1,0 +1,95 @@
+"""The C-ABI library on the host (no GPU): every declared entry point is
+exported, and the host mesh setup reproduces the oracle's connectivity bit
+for bit, its FP64 geometry and its least-squares operators to rounding."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2102_01366_gb300 import gks
+from paper_2102_01366_gb300 import inputs as I
+
+MESHES = {
+    "periodic2": lambda: I.box_mesh((2, 2, 2), jitter=0.1, seed=1),
+    "periodic3_diag": lambda: I.box_mesh((3, 3, 4), jitter=0.1, seed=2, diagonal=(1, 1, -1)),
+    "sod_like": lambda: I.box_mesh((6, 2, 3), (1.0, 0.2, 0.3), (False, True, True), jitter=0.1, seed=3),
+    "uniform": lambda: I.box_mesh((3, 3, 3), jitter=0.0, seed=0),
+    "open_z": lambda: I.box_mesh((3, 3, 3), periodic=(True, True, False), jitter=0.1, seed=4),
+}
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2102_01366_gb300 import _build
+    _build.build()
+    return gks.lib()
+
+
+def test_every_declared_symbol_is_exported(built):
+    names = gks.header_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(built, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+def test_connectivity_bit_exact(built, oracle_mod, name):
+    mesh = MESHES[name]()
+    g = gks.Mesh(mesh)
+    o = oracle_mod.Mesh(mesh)
+    assert (g.nc, g.nf) == (o.nc, o.nf)
+    tg, to = g.topology(), o.topology()
+    for k in ("face_v", "face_lr", "nbr", "csr_face", "csr_sign"):
+        np.testing.assert_array_equal(tg[k], to[k], err_msg=k)
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+def test_geometry_matches_oracle(built, oracle_mod, name):
+    mesh = MESHES[name]()
+    gg, go = gks.Mesh(mesh).geometry(), oracle_mod.Mesh(mesh).geometry()
+    for k in gg:
+        scale = max(np.abs(go[k]).max(), 1e-300)
+        assert np.abs(gg[k] - go[k]).max() <= 1e-13 * scale, k
+    # the normals are fixed bit for bit by the orientation rule
+    assert (np.sign(gg["fnorm"]) == np.sign(go["fnorm"])).all()
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+def test_stencils_match_oracle(built, oracle_mod, name):
+    mesh = MESHES[name]()
+    g = gks.Mesh(mesh)
+    o = oracle_mod.Mesh(mesh)
+    assert g.n_singular == o.n_singular
+    M1g, M2g = g.stencils()
+    M1o, M2o = o.stencils()
+    # rows scale with powers of h: compare per row relative to the row size
+    for Mg, Mo in ((M1g, M1o), (M2g, M2o)):
+        scale = np.abs(Mo).max(axis=2, keepdims=True) + 1e-300
+        assert (np.abs(Mg - Mo) / scale).max() < 1e-10
+
+
+def test_rejects_bad_input(built):
+    mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=5)
+    bad = dict(mesh)
+    tet = mesh["tet"].copy()
+    tet[3, [1, 2]] = tet[3, [2, 1]]
+    bad["tet"] = tet
+    with pytest.raises(gks.GksError) as e:
+        gks.Mesh(bad)
+    assert e.value.status == -2
+    bad = dict(mesh)
+    tet = mesh["tet"].copy()
+    tet[0, 0] = 10 ** 9
+    bad["tet"] = tet
+    with pytest.raises(gks.GksError) as e:
+        gks.Mesh(bad)
+    assert e.value.status == -2
+    # state creation without a workspace fails before any device call
+    g = gks.Mesh(mesh)
+    p = gks.params()
+    assert gks.lib().gks_workspace_bytes(g._h, C.byref(p)) > 0
+    h = C.c_void_p()
+    st = gks.lib().gks_state_create(g._h, C.byref(p), None, 0, None, C.byref(h))
+    assert st == -7 and not h.value
+    p.order = 4
+    assert gks.lib().gks_workspace_bytes(g._h, C.byref(p)) == 0

@@ -1,0 +1,254 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances (normwise relative per component, max|gpu - oracle| / max|oracle|):
+FP64 path 1e-11 after 10 steps; FP32-bulk path 2e-5.  Connectivity is
+compared bit for bit on the host (test_abi_host)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2102_01366_gb300 import gks
+from paper_2102_01366_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-11, 1: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+    from paper_2102_01366_gb300 import _build
+    _build.build()
+    gks.lib()
+    return torch
+
+
+def _rel(a, b, axis=None):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.abs(b).max(axis=axis, keepdims=axis is not None)
+    scale = np.maximum(scale, 1e-300)
+    return (np.abs(a - b).max(axis=axis, keepdims=axis is not None) / scale).max()
+
+
+def _state_rel(Wg, Wo):
+    """max over components of the normwise relative error (rows = components)."""
+    return max(_rel(Wg[q], Wo[q]) for q in range(Wo.shape[0]))
+
+
+CASES = {
+    # name: (mesh factory, state factory, oracle params kwargs)
+    "sine_n3_linear": (lambda: I.box_mesh((3, 3, 3), jitter=0.1, seed=31, diagonal=(1, 1, -1)),
+                       lambda m: I.sine_wave_state(m), dict(weno=0)),
+    "sine_n3_weno": (lambda: I.box_mesh((3, 3, 3), jitter=0.1, seed=32),
+                     lambda m: I.sine_wave_state(m), dict(weno=1)),
+    "sine_n2_weno2": (lambda: I.box_mesh((2, 2, 2), jitter=0.1, seed=33),
+                      lambda m: I.sine_wave_state(m), dict(weno=1, order=2)),
+    "sod_small_weno": (lambda: I.box_mesh((12, 2, 2), (1.0, 1 / 6, 1 / 6), (False, True, True), jitter=0.1,
+                                          seed=34),
+                       lambda m: I.riemann_x_state(m), dict(weno=1)),
+    "sine_n3_smooth_viscous": (lambda: I.box_mesh((3, 3, 3), jitter=0.1, seed=35),
+                               lambda m: I.sine_wave_state(m), dict(weno=1, smooth_flux=1, viscous=1, mu=1e-3)),
+}
+
+
+def _setup(cuda, oracle_mod, name, precision):
+    mk, st, kw = CASES[name]
+    mesh = mk()
+    W, dW = st(mesh)
+    kw = dict(kw)
+    kw.setdefault("cfl", 0.5)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(precision=precision, **kw))
+    s.init(W, dW)
+    o = oracle_mod.Mesh(mesh)
+    return mesh, W, dW, s, o, oracle_mod.params(**kw)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_reconstruction_parity(cuda, oracle_mod, name, precision):
+    mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, precision)
+    poly_g, slopes_g, fb_g = [x.cpu().numpy() for x in s.debug_reconstruct()]
+    poly_o, slopes_o, fb_o = o.reconstruct(p, W, dW)
+    np.testing.assert_array_equal(fb_g, fb_o)
+    tol = TOL[precision]
+    for q in range(5):
+        # each coefficient family relative to its own size
+        for lo, hi in ((0, 1), (1, 4), (4, 10)):
+            if np.abs(poly_o[:, q, lo:hi]).max() > 1e-12:
+                assert _rel(poly_g[:, q, lo:hi], poly_o[:, q, lo:hi]) < tol * 10, (q, lo)
+    if p.weno or p.order == 2:
+        assert _rel(slopes_g, slopes_o) < tol * 10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("stage", [1, 2])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_face_record_parity(cuda, oracle_mod, name, stage, precision):
+    mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, precision)
+    dt = o.timestep(p, W)
+    rec_g = s.debug_face_records(dt, stage).cpu().numpy()
+    rec_o = o.face_records(p, W, dW, dt, stage)
+    # column groups: flux parts (5 each) and gradient parts (15 each)
+    groups = [(0, 5), (5, 10), (10, 25), (25, 40)] if stage == 1 else [(0, 5), (5, 20)]
+    for lo, hi in groups:
+        ref = rec_o[:, lo:hi]
+        scale = max(np.abs(ref).max(), 1e-300)
+        err = np.abs(rec_g[:, lo:hi] - ref).max() / scale
+        assert err < TOL[precision] * 10, (lo, hi, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_ten_steps_parity(cuda, oracle_mod, name, precision):
+    mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, precision)
+    Wo, dWo, t_o, n = o.run(p, W, dW, nsteps=10)
+    s.step(10)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    t_g, _ = s.time()
+    assert abs(t_g - t_o) <= 1e-12 * t_o
+    assert _state_rel(Wg, Wo) < TOL[precision], _state_rel(Wg, Wo)
+    # gradients: relative to the largest gradient of each component
+    for q in range(5):
+        ref = dWo[3 * q:3 * q + 3]
+        if np.abs(ref).max() > 1e-10:
+            assert _rel(dWg[3 * q:3 * q + 3], ref) < TOL[precision] * 10, q
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config1_sine_wave_ten_steps(cuda, oracle_mod, precision):
+    """The 3072-cell density wave (8^3 hexes x 6, jitter 0.1, linear
+    weights, full flux, CFL 0.5, 10 steps) in full."""
+    mesh, W, dW = I.sine_wave_case(n=8)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=0, cfl=0.5, precision=precision))
+    s.init(W, dW)
+    o = oracle_mod.Mesh(mesh)
+    Wo, dWo, t_o, _ = o.run(oracle_mod.params(weno=0, cfl=0.5), W, dW, nsteps=10)
+    s.step(10)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    assert _state_rel(Wg, Wo) < TOL[precision]
+    for q in range(5):
+        assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10
+    # accuracy against the exact solution is the same in both precisions
+    We, _ = I.sine_wave_state(mesh, t=t_o)
+    vol = g.geometry()["vol"]
+    l1_g = (vol * np.abs(Wg[0] - We[0])).sum() / vol.sum()
+    l1_o = (vol * np.abs(Wo[0] - We[0])).sum() / vol.sum()
+    assert abs(l1_g - l1_o) < 1e-3 * l1_o
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config2_sod_full_size_one_step(cuda, oracle_mod, precision):
+    """The 24,576-cell Sod tube (64 x 8 x 8 hexes x 6, WENO) at full size,
+    in the launch configuration the benchmark times: one step, every cell."""
+    mesh, W, dW = I.sod_case()
+    g = gks.Mesh(mesh)
+    assert (g.nc, g.nf, g.n_boundary) == (24576, 49280, 256)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+    s.init(W, dW)
+    o = oracle_mod.Mesh(mesh)
+    Wo, dWo, _, _ = o.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, nsteps=1)
+    s.step(1)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    assert _state_rel(Wg, Wo) < TOL[precision]
+    for q in (0, 1, 4):
+        assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10
+
+
+def test_time_step_rule_and_t_end(cuda, oracle_mod):
+    mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, "sod_small_weno", 0)
+    assert abs(s.timestep() - o.timestep(p, W)) <= 1e-14 * o.timestep(p, W)
+    dt0 = o.timestep(p, W)
+    t_end = 2.5 * dt0
+    t = s.run(t_end=t_end, chunk=4)
+    assert abs(t - t_end) < 1e-14
+    # steps at t = t_end are no-ops
+    Wa, _ = s.get()
+    s.step(3, 0.0, t_end)
+    s.sync()
+    Wb, _ = s.get()
+    assert cuda.equal(Wa, Wb)
+
+
+def test_free_stream_and_conservation_on_gpu(cuda):
+    mesh = I.box_mesh((4, 4, 4), jitter=0.1, seed=41)
+    g = gks.Mesh(mesh)
+    vol = g.geometry()["vol"]
+    for precision in (0, 1):
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+        W = np.empty((5, g.nc))
+        U = np.array([0.7, -0.2, 0.4])
+        W[0], W[1:4], W[4] = 1.1, (1.1 * U)[:, None], 2.0 / 0.4 + 0.5 * 1.1 * U @ U
+        s.init(W, np.zeros((15, g.nc)))
+        s.step(5)
+        s.sync()
+        Wg, dWg = [x.cpu().numpy() for x in s.get()]
+        tol = 1e-13 if precision == 0 else 1e-6
+        assert np.abs(Wg - W).max() < tol * 5
+        W2, dW2 = I.sine_wave_state(mesh)
+        s.init(W2, dW2)
+        s.step(5)
+        s.sync()
+        Wg, _ = [x.cpu().numpy() for x in s.get()]
+        tot0, tot1 = (W2 * vol).sum(1), (Wg * vol).sum(1)
+        ctol = 1e-13 if precision == 0 else 1e-7
+        assert np.abs(tot1 - tot0).max() < ctol * np.abs(tot0).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_buffer_entry_point_matches_device_path(cuda, precision):
+    mesh, W, dW = I.sine_wave_case(n=4)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+    s.init(W, dW)
+    s.step(3)
+    s.sync()
+    Wd, dWd = [x.cpu().numpy() for x in s.get()]
+    Wh = cuda.tensor(W).pin_memory()
+    dWh = cuda.tensor(dW).pin_memory()
+    s2 = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+    s2.step_host(Wh, dWh, nsteps=3)
+    np.testing.assert_array_equal(Wh.numpy(), Wd)
+    np.testing.assert_array_equal(dWh.numpy(), dWd)
+
+
+def test_bad_state_is_reported(cuda):
+    """A cell with negative pressure: the step runs (NaN arithmetic only, no
+    fault) and the device error flag surfaces as GKS_E_STATE."""
+    mesh, W, dW = I.sine_wave_case(n=3)
+    W = W.copy()
+    W[4, 5] = -1.0
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=0, cfl=0.5))
+    s.init(W, dW)
+    s.step(1, dt_fixed=1e-3)
+    with pytest.raises(gks.GksError) as e:
+        s.sync()
+    assert e.value.status == -4
+
+
+def test_residual_matches_state_change(cuda):
+    mesh, W, dW = I.sine_wave_case(n=3)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5))
+    s.init(W, dW)
+    s.step(2)
+    s.sync()
+    Wa, _ = s.get()
+    s.step(1)
+    s.sync()
+    Wb, _ = s.get()
+    _, dt = s.time()
+    r = s.residual()
+    ref = np.sqrt((((Wb - Wa).cpu().numpy() / dt) ** 2).mean(1))
+    np.testing.assert_allclose(r, ref, rtol=1e-10)
