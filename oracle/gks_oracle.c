@@ -1147,9 +1147,21 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                     for (int i = 0; i < 3; ++i) g[i][q] = gg[i];
                 }
             }
-            /* READING: an open boundary copies the interior state */
-            if (cl < 0) { memcpy(WL, WR, sizeof(WL)); memcpy(gL, gR, sizeof(gL)); }
-            if (cr < 0) { memcpy(WR, WL, sizeof(WR)); memcpy(gR, gL, sizeof(gR)); }
+            /* READING: the paper leaves open (outflow) boundaries unspecified.
+             * The ghost side of an open boundary face is the interior cell's
+             * average with zero gradient (zeroth-order extrapolation).  Copying
+             * the interior Gauss-point state, with or without its gradient,
+             * amplifies rounding noise without bound next to the boundary. */
+            for (int side = 0; side < 2; ++side) {
+                int64_t inner = side == 0 ? cr : cl;
+                if ((side == 0 ? cl : cr) >= 0) continue;
+                double* Wg = side == 0 ? WL : WR;
+                double (*gg)[5] = side == 0 ? gL : gR;
+                for (int q = 0; q < 5; ++q) {
+                    Wg[q] = W[q * nc + inner];
+                    gg[0][q] = gg[1][q] = gg[2][q] = 0.0;
+                }
+            }
             /* rotate into the local frame: components by T, directions by
              * its velocity block */
             double tWL[5], tWR[5], tgL[3][5], tgR[3][5];

@@ -481,12 +481,12 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     // stage 1 from (W^n, grad W^n)
     if (need_b && (e = Launch<T>::slopes(m, st.Wr, st.slopes, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
     // stage 2 from (W*, grad W*)
     if (need_b && (e = Launch<T>::slopes(m, st.Ws, st.slopes, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
     return Launch<T>::update2(m, p, st, q);
 }
 
@@ -558,7 +558,7 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             }
             if (e == cudaSuccess) e = Launch<T>::recon(m, p, W, dW, st.slopes, st.poly, nullptr, q);
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
-            if (e == cudaSuccess) e = Launch<T>::flux(m, p, st.poly, st.rec, st.ctrl, 0.0, stage, q);
+            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.ctrl, 0.0, stage, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
             if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
@@ -746,7 +746,7 @@ static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, d
                                  double* d_rec) {
     gks_status r = debug_recon_impl<T>(s, m, st, nullptr, nullptr, nullptr);
     if (r != GKS_OK) return r;
-    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.poly, st.rec, st.ctrl, dt, stage, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, st.ctrl, dt, stage, s->stream));
     GKS_CHECK_CUDA(Launch<T>::to_double(st.rec, d_rec, (stage == 1 ? 40 : 20) * m.nf, s->stream));
     return GKS_OK;
 }

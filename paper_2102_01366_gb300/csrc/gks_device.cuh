@@ -230,11 +230,16 @@ __device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& ful
 
 // Time-dependent kinetic solution at one Gauss point, face frame.
 //   Wl, Wr: states; gl[i][q], gr[i][q]: gradients (direction i, comp q)
-// Outputs Fh = int_0^{dt/2} F, F = int_0^dt F, W0 = W(0), Wdt = W(dt).
+// Outputs, each 5 long:
+//   Fh = int_0^{dt/2} F dt,  D = int_0^dt F dt - 2 Fh   (second-order part)
+//   W0 = W(0),               dW = W(dt) - W(0)
+// D and dW are formed from differences of the time coefficients, in which
+// the leading terms cancel exactly, instead of by subtracting the rounded
+// integrals (which loses about three digits in FP32).
 template <typename T>
 __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const T (*gl)[5],
-                                          const T* Wr, const T (*gr)[5], T dt, T* Fh, T* F,
-                                          T* W0, T* Wdt) {
+                                          const T* Wr, const T (*gr)[5], T dt, T* Fh, T* D,
+                                          T* W0, T* dW) {
     const Prim<T> L = to_prim(Wl, ph.gm1);
     const Prim<T> R = to_prim(Wr, ph.gm1);
 
@@ -254,26 +259,29 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     const T jump = d_abs((L.p - R.p) / (L.p + R.p)) * dt;
     const T tau_n = (ph.viscous ? ph.mu / C.p : ph.tau_eps * dt) + ph.tau_c * jump;
 
-    // -- time coefficients: integrals over [0, d] for d = dt/2, dt --
-    T k0[2], k1[2], q1[2], q2[2], q3[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const T d = h == 0 ? T(0.5) * dt : dt;
-        const T E = d_exp(-d / tau_n);
-        k0[h] = tau_n * (T(1) - E);                      // int e
-        k1[h] = tau_n * (tau_n * (T(1) - E) - d * E);    // int t e
-        q1[h] = d - k0[h];                               // int C1
-        q2[h] = k1[h] + tau * k0[h] - tau * d;           // int C2
-        q3[h] = T(0.5) * d * d - tau * d + tau * k0[h];  // int C3
-    }
-    const T Edt = d_exp(-dt / tau_n);
+    // -- time coefficients over [0, dt/2] and their dt-minus-twice-dt/2
+    //    differences (E = Eh^2) --
+    const T hd = T(0.5) * dt;
+    const T Eh = d_exp(-hd / tau_n);
+    const T E = Eh * Eh;
+    const T omh = T(1) - Eh;
+    const T k0 = tau_n * omh;                              // int_0^{dt/2} e
+    const T k1 = tau_n * (tau_n * omh - hd * Eh);          // int_0^{dt/2} t e
+    const T q1 = hd - k0;                                  // int C1
+    const T q2 = k1 + tau * k0 - tau * hd;                 // int C2
+    const T q3 = T(0.5) * hd * hd - tau * hd + tau * k0;   // int C3
+    const T dk0 = -tau_n * omh * omh;
+    const T dk1 = -tau_n * tau_n * omh * omh + tau_n * dt * Eh * omh;
+    const T dq1 = tau_n * omh * omh;
+    const T dq2 = dk1 + tau * dk0;
+    const T dq3 = T(0.25) * dt * dt + tau * dk0;
 
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         Fh[k] = T(0);
-        F[k] = T(0);
+        D[k] = T(0);
         W0[k] = T(0);
-        Wdt[k] = T(0);
+        dW[k] = T(0);
     }
     T dWc[3][5];
 #pragma unroll
@@ -296,23 +304,19 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
         for (int i = 0; i < 3; ++i) acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
         if (!ph.smooth) {
             // e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1), Eq. 2nd-flux
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                T* out = h == 0 ? Fh : F;
-                const T c0 = S.rho * k0[h];
-                const T c1 = -S.rho * (tau * k0[h] + k1[h]);
-                const T c2 = -S.rho * tau * k0[h];
-                acc_psi<1, 0, 0>(t, c0, out);
-                acc_grad<1>(t, a, c1, out);
-                acc_apsi<1, 0, 0>(t, A, c2, out);
-            }
-            // point values at t = 0 (e = 1) and t = dt (e = Edt)
+            acc_psi<1, 0, 0>(t, S.rho * k0, Fh);
+            acc_grad<1>(t, a, -S.rho * (tau * k0 + k1), Fh);
+            acc_apsi<1, 0, 0>(t, A, -S.rho * tau * k0, Fh);
+            acc_psi<1, 0, 0>(t, S.rho * dk0, D);
+            acc_grad<1>(t, a, -S.rho * (tau * dk0 + dk1), D);
+            acc_apsi<1, 0, 0>(t, A, -S.rho * tau * dk0, D);
+            // W(0) (e = 1) and W(dt) - W(0); the rho <psi> terms of the two
+            // sides add up to Wc and cancel against the C1 term below
             acc_psi<0, 0, 0>(t, S.rho, W0);
             acc_grad<0>(t, a, -S.rho * tau, W0);
             acc_apsi<0, 0, 0>(t, A, -S.rho * tau, W0);
-            acc_psi<0, 0, 0>(t, S.rho * Edt, Wdt);
-            acc_grad<0>(t, a, -S.rho * (tau + dt) * Edt, Wdt);
-            acc_apsi<0, 0, 0>(t, A, -S.rho * tau * Edt, Wdt);
+            acc_grad<0>(t, a, S.rho * (tau - (tau + dt) * E), dW);
+            acc_apsi<0, 0, 0>(t, A, S.rho * tau * (T(1) - E), dW);
         }
     }
 
@@ -324,36 +328,27 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
         state_slopes(C, t, ph.K, dWc, ac, Ac);
         if (ph.smooth) {
             // f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t, Eq. 2nd-smooth-flux
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                T* out = h == 0 ? Fh : F;
-                const T d = h == 0 ? T(0.5) * dt : dt;
-                acc_psi<1, 0, 0>(t, C.rho * d, out);
-                acc_grad<1>(t, ac, -C.rho * tau * d, out);
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * d * d - tau * d), out);
-            }
+            acc_psi<1, 0, 0>(t, C.rho * hd, Fh);
+            acc_grad<1>(t, ac, -C.rho * tau * hd, Fh);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * hd * hd - tau * hd), Fh);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho * T(0.25) * dt * dt, D);
 #pragma unroll
             for (int k = 0; k < 5; ++k) W0[k] = Wc[k];
             acc_grad<0>(t, ac, -C.rho * tau, W0);
             acc_apsi<0, 0, 0>(t, Ac, -C.rho * tau, W0);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) Wdt[k] = W0[k];
-            acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, Wdt);
+            acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, dW);
         } else {
             // C1 g^c + C2 a^c.u g^c + C3 A^c g^c, Eq. 2nd-flux
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                T* out = h == 0 ? Fh : F;
-                acc_psi<1, 0, 0>(t, C.rho * q1[h], out);
-                acc_grad<1>(t, ac, C.rho * q2[h], out);
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * q3[h], out);
-            }
-            // t = 0: C1 = C2 = C3 = 0.  t = dt:
-            const T C1 = T(1) - Edt, C2 = (dt + tau) * Edt - tau, C3 = dt - tau + tau * Edt;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) Wdt[k] += C1 * Wc[k];
-            acc_grad<0>(t, ac, C.rho * C2, Wdt);
-            acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, Wdt);
+            acc_psi<1, 0, 0>(t, C.rho * q1, Fh);
+            acc_grad<1>(t, ac, C.rho * q2, Fh);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho * q3, Fh);
+            acc_psi<1, 0, 0>(t, C.rho * dq1, D);
+            acc_grad<1>(t, ac, C.rho * dq2, D);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho * dq3, D);
+            // t = 0: C1 = C2 = C3 = 0.  t = dt: C2, C3 (C1 cancelled above)
+            const T C2 = (dt + tau) * E - tau, C3 = dt - tau + tau * E;
+            acc_grad<0>(t, ac, C.rho * C2, dW);
+            acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, dW);
         }
     }
 }

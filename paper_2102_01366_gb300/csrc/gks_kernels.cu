@@ -304,6 +304,7 @@ __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
 
 template <typename T, int NR>
 __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> ph,
+                                                          const T* __restrict__ Wavg,
                                                           const T* __restrict__ poly,
                                                           T* __restrict__ rec,
                                                           const double* __restrict__ ctrl,
@@ -330,19 +331,18 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
             const T X[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
             eval_poly(poly + (int64_t)Rc * 50, X, WR, gR);
         }
-        // open boundary: the missing side copies the interior state
-        if (L < 0) {
+        // open boundary: the missing side is the interior cell's average with
+        // zero gradient (zeroth-order extrapolation; the paper leaves outflow
+        // boundaries open, and copying the interior Gauss-point state is not
+        // stable)
+        if (L < 0 || Rc < 0) {
+            const int64_t in = L < 0 ? Rc : L;
+            T* Wg = L < 0 ? WL : WR;
+            T (*gg)[5] = L < 0 ? gL : gR;
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                WL[q] = WR[q];
-                gL[0][q] = gR[0][q]; gL[1][q] = gR[1][q]; gL[2][q] = gR[2][q];
-            }
-        }
-        if (Rc < 0) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                WR[q] = WL[q];
-                gR[0][q] = gL[0][q]; gR[1][q] = gL[1][q]; gR[2][q] = gL[2][q];
+                Wg[q] = Wavg[q * m.nc + in];
+                gg[0][q] = gg[1][q] = gg[2][q] = T(0);
             }
         }
         T Rm[3][3];
@@ -350,18 +350,19 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
         T tWL[5], tgL[3][5], tWR[5], tgR[3][5];
         to_local(Rm, WL, gL, tWL, tgL);
         to_local(Rm, WR, gR, tWR, tgR);
-        T Fh[5], F[5], W0[5], Wd[5];
-        gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, F, W0, Wd);
+        T Fh[5], D[5], W0[5], dWt[5];
+        gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, D, W0, dWt);
         to_global(Rm, Fh);
-        to_global(Rm, F);
+        to_global(Rm, D);
         to_global(Rm, W0);
-        to_global(Rm, Wd);
+        to_global(Rm, dWt);
         if (NR == 40) {
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
+                // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
                 mine[q] = w * Fh[q];
-                mine[5 + q] = w * (T(8.0 / 3.0) * Fh[q] - T(1.0 / 3.0) * F[q]);
-                const T ws = w * T(0.5) * (W0[q] + Wd[q]);
+                mine[5 + q] = w * (T(2) * Fh[q] - D[q] * T(1.0 / 3.0));
+                const T ws = w * (W0[q] + T(0.5) * dWt[q]);  // f* = f^n + dt/2 f_t^n
                 const T w0 = w * W0[q];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
@@ -372,8 +373,9 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                mine[q] = w * T(4.0 / 3.0) * (F[q] - T(2) * Fh[q]);
-                const T dg = w * (Wd[q] - W0[q]);
+                // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
+                mine[q] = w * T(4.0 / 3.0) * D[q];
+                const T dg = w * dWt[q];  // f^{n+1} = f^n + dt f_t^*
 #pragma unroll
                 for (int i = 0; i < 3; ++i) mine[5 + 3 * q + i] = dg * n[i];
             }
@@ -634,15 +636,15 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W,
 }
 
 template <typename T>
-cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* poly, T* rec,
+cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
                             const double* ctrl, double dt_override, int stage, cudaStream_t s) {
     if (m.nf == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
     const Phys<T> ph = make_phys<T>(p);
     if (stage == 1)
-        k_flux<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, poly, rec, ctrl, dt_override);
+        k_flux<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
     else
-        k_flux<T, 20><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, poly, rec, ctrl, dt_override);
+        k_flux<T, 20><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ struct Launch {
     static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, cudaStream_t s);
     static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
                              const T* slopes, T* poly, int32_t* fallback, cudaStream_t s);
-    static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* poly, T* rec,
+    static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
                             const double* ctrl, double dt_override, int stage, cudaStream_t s);
     static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
     static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,

@@ -113,7 +113,7 @@ def test_ten_steps_parity(cuda, oracle_mod, name, precision):
     s.sync()
     Wg, dWg = [x.cpu().numpy() for x in s.get()]
     t_g, _ = s.time()
-    assert abs(t_g - t_o) <= 1e-12 * t_o
+    assert abs(t_g - t_o) <= TOL[precision] * t_o
     assert _state_rel(Wg, Wo) < TOL[precision], _state_rel(Wg, Wo)
     # gradients: relative to the largest gradient of each component
     for q in range(5):

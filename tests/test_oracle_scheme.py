@@ -49,9 +49,9 @@ def test_conservation(oracle_mod, weno):
 
 def test_divergence_theorem_exact_for_linear_data(oracle_mod):
     """At t = 0 with linear data (reproduced exactly on both sides of every
-    face), the interface value is the field itself, so the face sums of
-    Eq. gauss-formula return the exact gradient in every cell, boundary
-    cells included."""
+    interior face), the interface value is the field itself, so the face
+    sums of Eq. gauss-formula return the exact gradient in every cell that
+    has no open-boundary face (there the ghost side is the cell average)."""
     mesh = I.box_mesh((5, 2, 2), (1.0, 0.4, 0.4), (False, True, True), jitter=0.1, seed=23)
     om = oracle_mod.Mesh(mesh)
     geo, top = om.geometry(), om.topology()
@@ -69,7 +69,9 @@ def test_divergence_theorem_exact_for_linear_data(oracle_mod):
     G0 /= geo["vol"][:, None]
     expect = np.zeros((om.nc, 15))
     expect[:, 0] = b
-    np.testing.assert_allclose(G0, expect, atol=1e-13)
+    inner = (top["nbr"] >= 0).all(1)
+    assert inner.sum() > 0.8 * om.nc
+    np.testing.assert_allclose(G0[inner], expect[inner], atol=1e-13)
 
 
 def _wave1d_state(mesh, t):
@@ -166,8 +168,8 @@ def test_face_records_for_linear_field_in_global_frame(oracle_mod):
     checked = 0
     for f in range(om.nf):
         l, r = top["face_lr"][f]
-        if (l >= 0 and not good[l]) or (r >= 0 and not good[r]):
-            continue
+        if l < 0 or r < 0 or not good[l] or not good[r]:
+            continue  # open-boundary faces see the cell average on the ghost side
         c = l if l >= 0 else r
         X = (geo["gp_l"][f] if l >= 0 else geo["gp_r"][f]) + geo["cen"][c]
         n = geo["fnorm"][f]
@@ -184,4 +186,21 @@ def test_face_records_for_linear_field_in_global_frame(oracle_mod):
         np.testing.assert_allclose(rec1[f, 0:5], Fh, rtol=1e-8, atol=1e-12)
         np.testing.assert_allclose(rec2[f, 5:20], dG.reshape(15), rtol=1e-7, atol=1e-12)
         checked += 1
-    assert checked > 0.8 * om.nf
+    assert checked > 0.7 * om.nf
+
+
+def test_open_boundary_is_stable(oracle_mod):
+    """Rounding-size noise on a uniform state next to open boundaries stays
+    bounded (the ghost side is the interior average with zero gradient);
+    copying the interior Gauss-point state instead grows it ~10^7-fold in
+    100 steps."""
+    nx = 16
+    mesh = I.box_mesh((nx, 2, 2), (1.0, 2.0 / nx, 2.0 / nx), (False, True, True), jitter=0.1, seed=6)
+    om = oracle_mod.Mesh(mesh)
+    rng = np.random.default_rng(0)
+    W0 = np.zeros((5, om.nc))
+    W0[0], W0[4] = 1.0, 2.5
+    W = W0 * (1 + 1e-7 * rng.standard_normal(W0.shape))
+    W[1:4] = 1e-7 * rng.standard_normal((3, om.nc))
+    W, dW, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5), W, np.zeros((15, om.nc)), nsteps=60)
+    assert np.abs(W - W0).max() < 1e-3
