@@ -40,8 +40,9 @@ METRIC = "Mcell-stage updates/s"
 WORKLOAD = "sod_tube_64x8x8_hex_x6_tets_24576_cells_weno3_cfl0.5"
 CPU_SAMPLE = dict(nx=16, nyz=4)  # same recipe, 1,536 cells: oracle per-cell cost is size independent
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-# per-launch algorithmic work of the dominant kernel (face flux); see the design doc
-FLUX_FLOPS_PER_GP = {"fp32": None, "fp64": None}
+# work of the dominant kernel (face flux) per Gauss point and stage, FP32 flop
+# (fadd + fmul + 2 ffma) counted by ncu on this workload (profiles/k_flux_fp32_*)
+FLUX_FLOPS_PER_GP = {"fp32": (6435.0, 5218.0)}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -293,7 +294,9 @@ def main():
     fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
     fpg = FLUX_FLOPS_PER_GP["fp32"]
     if fpg:
-        achieved = fpg * gps / (flux_ms / 1000.0) / 1e12
+        # both stage variants: total flop of the two launches over their total time
+        t_flux = (br["flux1"][0] + br["flux2"][0]) / max(1, br["flux1"][1])
+        achieved = (fpg[0] + fpg[1]) * gps / (t_flux / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_flux<float>",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % clk_mhz,
