@@ -207,6 +207,29 @@ gks_status gks_step_timed(gks_state* state, int32_t nsteps, double dt_fixed, dou
 /* Time step of the Sec. 5 rule for the current averages (host value). */
 gks_status gks_timestep(gks_state* state, double* dt);
 
+/* Largest number of cells gks_timestep_noalloc accepts, in blocks of 256. */
+#define GKS_NOALLOC_MAX_BLOCKS 8192
+
+/* The time step of gks_timestep without a gks_state and without any device
+ * allocation, for callers that are not allowed to allocate device memory
+ * (for example while a CUDA stream is being captured, or when another
+ * framework owns the device memory).  The paper has no counterpart: this is
+ * an interface convenience.
+ *   p       scheme parameters (gamma, cfl, mu, viscous are used)
+ *   d_W     device FP64 cell averages W[5][n_cell]
+ *   d_dr    device FP64 radii dr[n_cell] (gks_mesh_geometry's dr)
+ *   d_dt    device FP64 scalar receiving C_CFL * min over cells
+ *   stream  CUDA stream (cudaStream_t as void*; NULL = legacy default)
+ * Enqueues two small kernels and returns without synchronising.  Its
+ * scratch is a fixed device array of GKS_NOALLOC_MAX_BLOCKS doubles held by
+ * every GPU that loads the library; n_cell above 256 * that count is
+ * rejected with GKS_E_ARG.  The first call on a device resolves the array's
+ * address (cudaGetSymbolAddress) with that device current, so make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (unordered streams) race.  Allocates nothing, frees nothing. */
+gks_status gks_timestep_noalloc(const gks_params* p, const double* d_W, const double* d_dr,
+                                int64_t n_cell, double* d_dt, void* stream);
+
 /* Per-component root mean square over cells of (W(t) - W_prev) / dt_last,
  * where W_prev is the state before the last step (host out_l2[5];
  * synchronises). */

@@ -443,20 +443,6 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState
     }
 }
 
-template <typename T>
-__device__ __forceinline__ double local_dt(const T* Wv, T dr, const HostPhys& p) {
-    const double rho = (double)Wv[0];
-    const double u = (double)Wv[1] / rho, v = (double)Wv[2] / rho, w = (double)Wv[3] / rho;
-    const double pr = (p.gamma - 1.0) * ((double)Wv[4] - 0.5 * rho * (u * u + v * v + w * w));
-    const double a = sqrt(p.gamma * pr / rho);
-    double d = (double)dr / (sqrt(u * u + v * v + w * w) + a);
-    if (p.viscous && p.mu > 0.0) {
-        const double dv = (double)dr * (double)dr / (3.0 * p.mu / rho);
-        d = fmin(d, dv);
-    }
-    return d;
-}
-
 // deterministic block reduction of one min and five sums
 __device__ __forceinline__ void block_reduce_part(double mn, const double* sums, double* out) {
     __shared__ double smin[CELL_THREADS];

@@ -75,6 +75,24 @@ struct Launch {
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
 };
 
+// Local time-step limit of one cell (Sec. 5, Eq. time-step, without C_CFL):
+// dr / (|U| + a), and dr^2 / (3 nu) if viscous, from its averages Wv[5].
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ double local_dt(const T* Wv, T dr, const HostPhys& p) {
+    const double rho = (double)Wv[0];
+    const double u = (double)Wv[1] / rho, v = (double)Wv[2] / rho, w = (double)Wv[3] / rho;
+    const double pr = (p.gamma - 1.0) * ((double)Wv[4] - 0.5 * rho * (u * u + v * v + w * w));
+    const double a = sqrt(p.gamma * pr / rho);
+    double d = (double)dr / (sqrt(u * u + v * v + w * w) + a);
+    if (p.viscous && p.mu > 0.0) {
+        const double dv = (double)dr * (double)dr / (3.0 * p.mu / rho);
+        d = fmin(d, dv);
+    }
+    return d;
+}
+#endif
+
 cudaError_t launch_dt_finalize(const double* part, int nblk, double cfl, double* ctrl,
                                cudaStream_t s);
 cudaError_t launch_set_control(double* ctrl, double dt_fixed, double t_end, int reset_time,

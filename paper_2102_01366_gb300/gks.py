@@ -76,6 +76,7 @@ def lib():
         "gks_step_host": (C.c_int32, [_vp, _vp, _vp, C.c_int32, C.c_double, _vp, _vp]),
         "gks_timestep": (C.c_int32, [_vp, C.POINTER(C.c_double)]),
         "gks_step_timed": (C.c_int32, [_vp, C.c_int32, C.c_double, C.c_double, _vp, _vp]),
+        "gks_timestep_noalloc": (C.c_int32, [C.POINTER(gks_params), _vp, _vp, C.c_int64, _vp, _vp]),
         "gks_residual": (C.c_int32, [_vp, _vp]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
