@@ -287,7 +287,8 @@ def main():
     br = results["fp32"]["breakdown"]
     flux_ms = (br["flux1"][0] + br["flux2"][0]) / max(1, br["flux1"][1] + br["flux2"][1])
     total_ms = sum(v[0] for v in br.values())
-    launches_per_step = sum(v[1] for v in br.values()) / max(1, br["dt"][1]) + 1  # + control kernel
+    nst = max(1, br["flux1"][1])  # steps in the breakdown pass
+    launches_per_step = sum(v[1] for v in br.values()) / nst + 1  # + control kernel
     gps = 3 * g.nf
     peaks, peak_src = _peaks()
     clk_mhz = SM_MAX_MHZ
@@ -317,7 +318,7 @@ def main():
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32,
                           "fp32_vs_fp64_rel": fp32_vs_fp64},
         "fp32_speedup_over_fp64": value / value64,
-        "kernel_ms_per_step": {k: v[0] / max(1, br["dt"][1]) for k, v in br.items()},
+        "kernel_ms_per_step": {k: v[0] / nst for k, v in br.items() if v[1] > 0},
         "roofline": roof,
         "e2e": {"value": ws * nc * 2 / e2e_s / 1e6, "unit": METRIC,
                 "h2d_bytes_per_step": 20 * nc * 8, "d2h_bytes_per_step": 20 * nc * 8},

@@ -470,22 +470,27 @@ extern "C" gks_status gks_init_state(gks_state* s, const double* d_W, const doub
     return GKS_OK;
 }
 
-// one two-stage step (Sec. 3): enqueued on s->stream (captured into a graph)
+// one two-stage step (Sec. 3): enqueued on s->stream (captured into a graph).
+// The first kernel's block 0 first turns the per-block time-step minima left
+// by the previous update (or by gks_init_state) into this step's dt.
 template <typename T>
 static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     const HostPhys& p = s->phys;
     cudaStream_t q = s->stream;
     const bool need_b = p.weno || p.order == 2;
+    const typename Launch<T>::Finalize fin{st.part, update_blocks(m.nc), p.cfl, st.ctrl};
     cudaError_t e;
-    if ((e = launch_dt_finalize(st.part, update_blocks(m.nc), p.cfl, st.ctrl, q)) != cudaSuccess) return e;
     // stage 1 from (W^n, grad W^n)
-    if (need_b && (e = Launch<T>::slopes(m, st.Wr, st.slopes, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
+    if (need_b && (e = Launch<T>::slopes(m, st.Wr, st.slopes, &fin, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, nullptr, need_b ? nullptr : &fin, q)) !=
+        cudaSuccess)
+        return e;
     if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
     // stage 2 from (W*, grad W*)
-    if (need_b && (e = Launch<T>::slopes(m, st.Ws, st.slopes, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, st.slopes, st.poly, nullptr, q)) != cudaSuccess) return e;
+    if (need_b && (e = Launch<T>::slopes(m, st.Ws, st.slopes, nullptr, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, st.slopes, st.poly, nullptr, nullptr, q)) != cudaSuccess)
+        return e;
     if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
     return Launch<T>::update2(m, p, st, q);
 }
@@ -547,16 +552,17 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
         };
         cudaError_t e = cudaEventRecord(ev[ne], q);
         kid[ne++] = -1;
-        if (e == cudaSuccess) e = launch_dt_finalize(st.part, update_blocks(m.nc), p.cfl, st.ctrl, q);
-        if (e == cudaSuccess) e = mark(GKS_K_DT);
+        const typename Launch<T>::Finalize fin{st.part, update_blocks(m.nc), p.cfl, st.ctrl};
         for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
             const T* W = stage == 1 ? st.Wr : st.Ws;
             const T* dW = stage == 1 ? st.dW : st.dWs;
+            const bool fuse = stage == 1;
             if (need_b) {
-                e = Launch<T>::slopes(m, W, st.slopes, q);
+                e = Launch<T>::slopes(m, W, st.slopes, fuse ? &fin : nullptr, q);
                 if (e == cudaSuccess) e = mark(GKS_K_SLOPES);
             }
-            if (e == cudaSuccess) e = Launch<T>::recon(m, p, W, dW, st.slopes, st.poly, nullptr, q);
+            if (e == cudaSuccess)
+                e = Launch<T>::recon(m, p, W, dW, st.slopes, st.poly, nullptr, (fuse && !need_b) ? &fin : nullptr, q);
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
             if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.ctrl, 0.0, stage, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
@@ -706,10 +712,13 @@ extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
     GKS_CHECK_CUDA(cudaMemcpyAsync(part.data(), s->fp32 ? s->s32.part : s->s64.part, 8 * part.size(),
                                    cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    double ctrl[CTRL_N];
+    GKS_CHECK_CUDA(cudaMemcpy(ctrl, s->fp32 ? s->s32.ctrl : s->s64.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    const double dt = ctrl[CTRL_DT];
     for (int q = 0; q < 5; ++q) {
         double acc = 0.0;
         for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * PART_N + PART_RES + q];
-        out_l2[q] = std::sqrt(acc / (double)s->mesh->nc);
+        out_l2[q] = dt > 0.0 ? std::sqrt(acc / (double)s->mesh->nc) / dt : 0.0;
     }
     return GKS_OK;
 }
@@ -722,9 +731,9 @@ static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st,
     const HostPhys& p = s->phys;
     const bool need_b = p.weno || p.order == 2;
     const int64_t nc = m.nc;
-    if (need_b) GKS_CHECK_CUDA(Launch<T>::slopes(m, st.Wr, st.slopes, s->stream));
+    if (need_b) GKS_CHECK_CUDA(Launch<T>::slopes(m, st.Wr, st.slopes, nullptr, s->stream));
     else GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, d_fallback, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, d_fallback, nullptr, s->stream));
     if (d_poly) GKS_CHECK_CUDA(Launch<T>::to_double(st.poly, d_poly, 50 * nc, s->stream));
     if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
     return GKS_OK;

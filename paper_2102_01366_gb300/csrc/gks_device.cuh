@@ -353,4 +353,132 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     }
 }
 
+// The same kinetic solution with the work of one Gauss point split over a
+// lane pair (lanes 2j and 2j+1 of a warp, all 32 lanes active): lane "side"
+// owns the left (0) or right (1) initial state.  Each lane computes its side's
+// Maxwellian slopes and half-space moments; the interface equilibrium sums
+// and its slope sums are exchanged with one shuffle per value; both lanes
+// then form the equilibrium slopes, lane 0 adds the hydrodynamic part of Fh
+// (and of W0), lane 1 that of D and dW.  On return both lanes hold the totals.
+template <typename T>
+__device__ __forceinline__ T pair_sum(T v) {
+    return v + __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void gks_point_pair(const Phys<T>& ph, int side, const T* Ws, const T (*gs)[5],
+                                               T dt, T* Fh, T* D, T* W0, T* dW) {
+    const Prim<T> S = to_prim(Ws, ph.gm1);
+    const T p_other = __shfl_xor_sync(0xffffffffu, S.p, 1);
+    const int half = side == 0 ? +1 : -1;
+
+    // -- equilibrium state at the interface, Eq. new-equ-part (values) --
+    T Wc[5] = {T(0), T(0), T(0), T(0), T(0)};
+    Tab<T> t;
+    make_tab(t, S, ph.K, 0);
+    T a[3][5], A[5];
+    state_slopes(S, t, ph.K, gs, a, A);
+    make_half_u(t, S, half);
+    acc_psi<0, 0, 0>(t, S.rho, Wc);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Wc[k] = pair_sum(Wc[k]);
+    const Prim<T> C = to_prim(Wc, ph.gm1);
+
+    // -- collision times, Sec. 2.2 --
+    const T tau = ph.viscous ? ph.mu / C.p : T(0);
+    const T jump = d_abs((S.p - p_other) / (S.p + p_other)) * dt;
+    const T tau_n = (ph.viscous ? ph.mu / C.p : ph.tau_eps * dt) + ph.tau_c * jump;
+
+    // -- time coefficients (see gks_point) --
+    const T hd = T(0.5) * dt;
+    const T Eh = d_exp(-hd / tau_n);
+    const T E = Eh * Eh;
+    const T omh = T(1) - Eh;
+    const T k0 = tau_n * omh;
+    const T k1 = tau_n * (tau_n * omh - hd * Eh);
+    const T q1 = hd - k0;
+    const T q2 = k1 + tau * k0 - tau * hd;
+    const T q3 = T(0.5) * hd * hd - tau * hd + tau * k0;
+    const T dk0 = -tau_n * omh * omh;
+    const T dk1 = -tau_n * tau_n * omh * omh + tau_n * dt * Eh * omh;
+    const T dq1 = tau_n * omh * omh;
+    const T dq2 = dk1 + tau * dk0;
+    const T dq3 = T(0.25) * dt * dt + tau * dk0;
+
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Fh[k] = T(0);
+        D[k] = T(0);
+        W0[k] = T(0);
+        dW[k] = T(0);
+    }
+    // slope of the interface equilibrium, Eq. new-equ-part (gradients)
+    T dWc[3][5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dWc[i][k] = T(0);
+        acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
+    }
+    if (!ph.smooth) {
+        // this side's e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1)
+        acc_psi<1, 0, 0>(t, S.rho * k0, Fh);
+        acc_grad<1>(t, a, -S.rho * (tau * k0 + k1), Fh);
+        acc_apsi<1, 0, 0>(t, A, -S.rho * tau * k0, Fh);
+        acc_psi<1, 0, 0>(t, S.rho * dk0, D);
+        acc_grad<1>(t, a, -S.rho * (tau * dk0 + dk1), D);
+        acc_apsi<1, 0, 0>(t, A, -S.rho * tau * dk0, D);
+        acc_psi<0, 0, 0>(t, S.rho, W0);
+        acc_grad<0>(t, a, -S.rho * tau, W0);
+        acc_apsi<0, 0, 0>(t, A, -S.rho * tau, W0);
+        acc_grad<0>(t, a, S.rho * (tau - (tau + dt) * E), dW);
+        acc_apsi<0, 0, 0>(t, A, S.rho * tau * (T(1) - E), dW);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dWc[i][k] = pair_sum(dWc[i][k]);
+
+    // -- hydrodynamic (equilibrium) part, divided between the two lanes --
+    {
+        make_tab(t, C, ph.K, 0);
+        T ac[3][5], Ac[5];
+        state_slopes(C, t, ph.K, dWc, ac, Ac);
+        if (ph.smooth) {
+            if (side == 0) {
+                acc_psi<1, 0, 0>(t, C.rho * hd, Fh);
+                acc_grad<1>(t, ac, -C.rho * tau * hd, Fh);
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * hd * hd - tau * hd), Fh);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) W0[k] += Wc[k];
+                acc_grad<0>(t, ac, -C.rho * tau, W0);
+                acc_apsi<0, 0, 0>(t, Ac, -C.rho * tau, W0);
+            } else {
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * T(0.25) * dt * dt, D);
+                acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, dW);
+            }
+        } else {
+            if (side == 0) {
+                acc_psi<1, 0, 0>(t, C.rho * q1, Fh);
+                acc_grad<1>(t, ac, C.rho * q2, Fh);
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * q3, Fh);
+            } else {
+                acc_psi<1, 0, 0>(t, C.rho * dq1, D);
+                acc_grad<1>(t, ac, C.rho * dq2, D);
+                acc_apsi<1, 0, 0>(t, Ac, C.rho * dq3, D);
+                const T C2 = (dt + tau) * E - tau, C3 = dt - tau + tau * E;
+                acc_grad<0>(t, ac, C.rho * C2, dW);
+                acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, dW);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Fh[k] = pair_sum(Fh[k]);
+        D[k] = pair_sum(D[k]);
+        W0[k] = pair_sum(W0[k]);
+        dW[k] = pair_sum(dW[k]);
+    }
+}
+
 }  // namespace gks

@@ -30,114 +30,148 @@ struct ReconConst {
 };
 
 // --------------------------------------------------------------------------
-// reconstruction step 1
+// cell kernels: 5 lanes per cell (one per conservative component), 6 cells
+// per warp (lanes 30, 31 idle), CELLS_PER_BLOCK cells per 128-thread block
 // --------------------------------------------------------------------------
+// Global minimum of the per-block minima and the step's dt (run by one
+// whole block; deterministic).  Applies dt_fixed and t_end clipping.
+__device__ void finalize_dt_block(const double* __restrict__ part, int nblk, double cfl,
+                                  double* __restrict__ ctrl) {
+    __shared__ double smin[CELL_THREADS];
+    double mn = INFINITY;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) mn = fmin(mn, part[(int64_t)b * PART_N]);
+    smin[threadIdx.x] = mn;
+    __syncthreads();
+    for (int s = CELL_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double dt = ctrl[CTRL_DT_FIXED] > 0.0 ? ctrl[CTRL_DT_FIXED] : cfl * smin[0];
+        const double t_end = ctrl[CTRL_T_END];
+        if (t_end > 0.0) {
+            const double rem = t_end - ctrl[CTRL_T];
+            if (rem <= 1e-12 * t_end) {
+                dt = 0.0;
+                if (rem > 0.0) ctrl[CTRL_T] = t_end;
+            } else if (dt > rem) {
+                dt = rem;
+            }
+        }
+        if (!(dt > 0.0)) dt = 0.0;
+        ctrl[CTRL_DT] = dt;
+    }
+}
+
+template <typename T>
+struct FinArg {
+    const double* part;
+    int nblk;
+    double cfl;
+    double* ctrl;
+};
+
+struct CellLane {
+    int64_t c;    // cell (clamped to a valid cell on idle lanes)
+    int q;        // component
+    int base;     // lane of component 0 of this cell
+    bool active;  // lane carries a real (cell, component)
+};
+
+__device__ __forceinline__ CellLane cell_lane(int64_t nc) {
+    CellLane L;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int cl = lane / 5;
+    L.q = lane - 5 * cl;
+    L.base = lane - L.q;
+    const int64_t c = (int64_t)blockIdx.x * CELLS_PER_BLOCK + warp * 6 + cl;
+    L.active = lane < 30 && c < nc;
+    L.c = c < nc ? c : nc - 1;
+    return L;
+}
+
+// reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ W,
-                                                          T* __restrict__ slopes) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m.nc) return;
-    const int64_t nc = m.nc;
-    T Q0[5], b[5][3];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        Q0[q] = W[q * nc + c];
-        b[q][0] = b[q][1] = b[q][2] = T(0);
-    }
+                                                          T* __restrict__ slopes, FinArg<T> fin) {
+    if (fin.part && blockIdx.x == 0) finalize_dt_block(fin.part, fin.nblk, fin.cfl, fin.ctrl);
+    const CellLane cl = cell_lane(m.nc);
+    if (!cl.active) return;
+    const int64_t nc = m.nc, c = cl.c;
+    const int q = cl.q;
+    const T Q0 = W[q * nc + c];
+    T b0 = T(0), b1 = T(0), b2 = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + c];
         if (nb < 0) continue;
-        const T m0 = m.M1[(0 * 4 + f) * nc + c];
-        const T m1 = m.M1[(1 * 4 + f) * nc + c];
-        const T m2 = m.M1[(2 * 4 + f) * nc + c];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const T dq = W[q * nc + nb] - Q0[q];
-            b[q][0] += m0 * dq;
-            b[q][1] += m1 * dq;
-            b[q][2] += m2 * dq;
-        }
+        const T dq = W[q * nc + nb] - Q0;
+        b0 += m.M1[(0 * 4 + f) * nc + c] * dq;
+        b1 += m.M1[(1 * 4 + f) * nc + c] * dq;
+        b2 += m.M1[(2 * 4 + f) * nc + c] * dq;
     }
-    T* out = slopes + c * 15;
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) out[q * 3 + i] = b[q][i];
+    T* out = slopes + c * 15 + 3 * q;
+    out[0] = b0;
+    out[1] = b1;
+    out[2] = b2;
 }
 
-// --------------------------------------------------------------------------
-// reconstruction step 2
-// --------------------------------------------------------------------------
+// reconstruction step 2: P2 = M2 d, smoothness indicators, two-step beta_0,
+// nonlinear weights (Sec. 4.1-4.3), positivity at the cell's 12 face Gauss
+// points (Sec. 4.2); R written about the centroid in monomial form
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
                                                          const T* __restrict__ W,
                                                          const T* __restrict__ dW,
                                                          const T* __restrict__ slopes,
                                                          T* __restrict__ poly,
-                                                         int32_t* __restrict__ fallback) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m.nc) return;
-    const int64_t nc = m.nc;
+                                                         int32_t* __restrict__ fallback,
+                                                         FinArg<T> fin) {
+    if (fin.part && blockIdx.x == 0) finalize_dt_block(fin.part, fin.nblk, fin.cfl, fin.ctrl);
+    const CellLane cl = cell_lane(m.nc);
+    const int64_t nc = m.nc, c = cl.c;
+    const int q = cl.q;
     int nb[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
-    T Q0[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Q0[q] = W[q * nc + c];
+    const T Q0 = W[q * nc + c];
 
-    // data vectors [dQ_f (4); grad Q_{f,l} (12)] of all components
-    T d[5][16];
+    // data vector [dQ_f (4); grad Q_{f,l} (12)] of this component
+    T d[16];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool ok = nb[f] >= 0;
         const int64_t n = ok ? nb[f] : c;
+        d[f] = ok ? W[q * nc + n] - Q0 : T(0);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            d[q][f] = ok ? W[q * nc + n] - Q0[q] : T(0);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) d[q][4 + 3 * f + l] = ok ? dW[(3 * q + l) * nc + n] : T(0);
-        }
+        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? dW[(3 * q + l) * nc + n] : T(0);
     }
-    // P2 in the zero-mean basis: a = M2 d  (M2 streamed once, SoA, coalesced)
-    T a[5][9];
+    // P2 in the zero-mean basis of Eq. base: a = M2 d
+    T a[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
+        T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) a[q][k] = T(0);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const T mk = m.M2[(k * 16 + j) * nc + c];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) a[q][k] += mk * d[q][j];
-        }
+        for (int j = 0; j < 16; ++j) acc += m.M2[(k * 16 + j) * nc + c] * d[j];
+        a[k] = acc;
     }
-    T Mxx = m.mom2[0 * nc + c], Mxy = m.mom2[1 * nc + c], Mxz = m.mom2[2 * nc + c];
-    T Myy = m.mom2[3 * nc + c], Myz = m.mom2[4 * nc + c], Mzz = m.mom2[5 * nc + c];
+    const T Mxx = m.mom2[0 * nc + c], Mxy = m.mom2[1 * nc + c], Mxz = m.mom2[2 * nc + c];
+    const T Myy = m.mom2[3 * nc + c], Myz = m.mom2[4 * nc + c], Mzz = m.mom2[5 * nc + c];
 
-    // final R coefficients (basis form; the constant is Q0)
-    T R[5][9];
-    const bool need_b = rc.weno || rc.order == 2;
     const T g22 = T(100.0 / 111.0), g12 = T(10.0 / 111.0), g02 = T(1.0 / 111.0);
     const T g11 = T(10.0 / 11.0), g01 = T(1.0 / 11.0);
-    const T v23 = m.vol23[c], v43 = m.vol43[c];
+    T R[9];
+    T b[3] = {T(0), T(0), T(0)};
+    if (rc.weno || rc.order == 2) {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        T b[3] = {T(0), T(0), T(0)};
-        if (need_b) {
+        for (int i = 0; i < 3; ++i) b[i] = slopes[c * 15 + 3 * q + i];
+    }
+    if (!rc.weno) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) b[i] = slopes[c * 15 + 3 * q + i];
-        }
-        if (!rc.weno) {
-            if (rc.order == 2) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) R[q][k] = k < 3 ? b[k] : T(0);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) R[q][k] = a[q][k];
-            }
-            continue;
-        }
+        for (int k = 0; k < 9; ++k) R[k] = rc.order == 2 ? (k < 3 ? b[k] : T(0)) : a[k];
+    } else {
+        const T v23 = m.vol23[c], v43 = m.vol43[c];
         // smoothness indicators, Eq. smooth-indicator
         const T beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
         // two-step beta_0 from the neighbours' step-1 slopes, Eq. p0-non-linear-weight
@@ -172,68 +206,59 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
             const T sigma = pow43(d_abs(beta1 - beta0));
             const T r0 = sigma / (rc.eps + beta0), r1 = sigma / (rc.eps + beta1);
             const T w0 = g01 * (T(1) + r0 * r0), w1 = g11 * (T(1) + r1 * r1);
-            const T cl = (w1 / (w0 + w1)) / g11;
+            const T cl1 = (w1 / (w0 + w1)) / g11;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) R[q][k] = k < 3 ? cl * b[k] : T(0);
-            continue;
+            for (int k = 0; k < 9; ++k) R[k] = k < 3 ? cl1 * b[k] : T(0);
+        } else {
+            // Hessian rows of P2 and the integrals of its derivatives
+            const T H[3][3] = {{T(2) * a[3], a[4], a[5]}, {a[4], T(2) * a[6], a[7]}, {a[5], a[7], T(2) * a[8]}};
+            T first = T(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const T h0 = H[l][0], h1 = H[l][1], h2 = H[l][2];
+                const T hMh = h0 * (Mxx * h0 + Mxy * h1 + Mxz * h2) + h1 * (Mxy * h0 + Myy * h1 + Myz * h2) +
+                              h2 * (Mxz * h0 + Myz * h1 + Mzz * h2);
+                first += a[l] * a[l] + hMh;
+            }
+            const T second = H[0][0] * H[0][0] + a[4] * a[4] + a[5] * a[5] + H[1][1] * H[1][1] + a[7] * a[7] +
+                             H[2][2] * H[2][2];
+            const T beta2 = v23 * first + v43 * second;
+            // global smoothness indicator and nonlinear weights, Eq. non-linear-weight
+            const T sigma = pow43(T(0.5) * (d_abs(beta2 - beta1) + d_abs(beta2 - beta0)));
+            const T r0 = sigma / (rc.eps + beta0), r1 = sigma / (rc.eps + beta1), r2 = sigma / (rc.eps + beta2);
+            const T w0 = g02 * (T(1) + r0 * r0), w1 = g12 * (T(1) + r1 * r1), w2 = g22 * (T(1) + r2 * r2);
+            const T iw = T(1) / (w0 + w1 + w2);
+            const T c2 = (w2 * iw) / g22;
+            const T cb = (w1 * iw) / g11 - c2 * g12 / g11;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k] = c2 * a[k] + (k < 3 ? cb * b[k] : T(0));
         }
-        const T* aq = a[q];
-        // Hessian rows of P2 and the integrals of its derivatives
-        const T H[3][3] = {{T(2) * aq[3], aq[4], aq[5]},
-                           {aq[4], T(2) * aq[6], aq[7]},
-                           {aq[5], aq[7], T(2) * aq[8]}};
-        T first = T(0);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            const T h0 = H[l][0], h1 = H[l][1], h2 = H[l][2];
-            const T hMh = h0 * (Mxx * h0 + Mxy * h1 + Mxz * h2) + h1 * (Mxy * h0 + Myy * h1 + Myz * h2) +
-                          h2 * (Mxz * h0 + Myz * h1 + Mzz * h2);
-            first += aq[l] * aq[l] + hMh;
-        }
-        const T second = H[0][0] * H[0][0] + aq[4] * aq[4] + aq[5] * aq[5] + H[1][1] * H[1][1] +
-                         aq[7] * aq[7] + H[2][2] * H[2][2];
-        const T beta2 = v23 * first + v43 * second;
-        // global smoothness indicator and nonlinear weights, Eq. non-linear-weight
-        const T sigma = pow43(T(0.5) * (d_abs(beta2 - beta1) + d_abs(beta2 - beta0)));
-        const T r0 = sigma / (rc.eps + beta0), r1 = sigma / (rc.eps + beta1),
-                r2 = sigma / (rc.eps + beta2);
-        const T w0 = g02 * (T(1) + r0 * r0), w1 = g12 * (T(1) + r1 * r1), w2 = g22 * (T(1) + r2 * r2);
-        const T iw = T(1) / (w0 + w1 + w2);
-        const T c2 = (w2 * iw) / g22;
-        const T cb = (w1 * iw) / g11 - c2 * g12 / g11;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[q][k] = c2 * aq[k] + (k < 3 ? cb * b[k] : T(0));
     }
-
-    // constant term of the monomial form, then the positivity check at the
-    // 12 Gauss points of the cell's faces (Sec. 4.2)
-    T c0[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-        c0[q] = Q0[q] - (R[q][3] * Mxx + R[q][4] * Mxy + R[q][5] * Mxz + R[q][6] * Myy +
-                         R[q][7] * Myz + R[q][8] * Mzz);
+    // constant of the monomial form
+    const T c0 = Q0 - (R[3] * Mxx + R[4] * Mxy + R[5] * Mxz + R[6] * Myy + R[7] * Myz + R[8] * Mzz);
+    // positivity: the 5 lanes of the cell exchange their values at each point
     bool bad = false;
 #pragma unroll 1
     for (int g = 0; g < 12; ++g) {
         const T X = m.cgp[(g * 3 + 0) * nc + c];
         const T Y = m.cgp[(g * 3 + 1) * nc + c];
         const T Z = m.cgp[(g * 3 + 2) * nc + c];
-        T v[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-            v[q] = c0[q] + R[q][0] * X + R[q][1] * Y + R[q][2] * Z + R[q][3] * X * X + R[q][4] * X * Y +
-                   R[q][5] * X * Z + R[q][6] * Y * Y + R[q][7] * Y * Z + R[q][8] * Z * Z;
-        const T pr = rc.gm1 * (v[4] - T(0.5) * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0]);
-        if (!(v[0] > T(0)) || !(pr > T(0))) bad = true;
+        const T v = c0 + R[0] * X + R[1] * Y + R[2] * Z + R[3] * X * X + R[4] * X * Y + R[5] * X * Z +
+                    R[6] * Y * Y + R[7] * Y * Z + R[8] * Z * Z;
+        const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
+        const T m1 = __shfl_sync(0xffffffffu, v, cl.base + 1);
+        const T m2 = __shfl_sync(0xffffffffu, v, cl.base + 2);
+        const T m3 = __shfl_sync(0xffffffffu, v, cl.base + 3);
+        const T en = __shfl_sync(0xffffffffu, v, cl.base + 4);
+        const T pr = rc.gm1 * (en - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) / rho);
+        if (!(rho > T(0)) || !(pr > T(0))) bad = true;
     }
-    T* out = poly + c * 50;
+    if (!cl.active) return;
+    T* out = poly + c * 50 + q * 10;
+    out[0] = bad ? Q0 : c0;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        out[q * 10] = bad ? Q0[q] : c0[q];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) out[q * 10 + 1 + k] = bad ? T(0) : R[q][k];
-    }
-    if (fallback) fallback[c] = bad ? 1 : 0;
+    for (int k = 0; k < 9; ++k) out[1 + k] = bad ? T(0) : R[k];
+    if (fallback && q == 0) fallback[c] = bad ? 1 : 0;
 }
 
 // --------------------------------------------------------------------------
@@ -302,8 +327,9 @@ __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
     for (int i = 0; i < 3; ++i) v[1 + i] = Rm[0][i] * a + Rm[1][i] * b + Rm[2][i] * c;
 }
 
+// 6 threads per face: 3 Gauss points x 2 sides (a lane pair per point)
 template <typename T, int NR>
-__global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> ph,
+__global__ void __launch_bounds__(6 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> ph,
                                                           const T* __restrict__ Wavg,
                                                           const T* __restrict__ poly,
                                                           T* __restrict__ rec,
@@ -312,6 +338,106 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
     __shared__ T red[FLUX_FACES * 3 * NR];
     const double dtd = dt_override > 0.0 ? dt_override : ctrl[CTRL_DT];
     if (!(dtd > 0.0)) return;  // no-op step (grid-uniform)
+    const T dt = (T)dtd;
+    const int side = threadIdx.x & 1;
+    const int pt = threadIdx.x >> 1;  // Gauss point within the block
+    const int lf = pt / 3;
+    const int k = pt - 3 * lf;
+    const int64_t f0 = (int64_t)blockIdx.x * FLUX_FACES + lf;
+    const bool active = f0 < m.nf;
+    // inactive lanes of the last block compute a valid face and store nothing
+    // (the lane-pair shuffles need every lane of the warp)
+    const int64_t f = active ? f0 : m.nf - 1;
+    const int L = m.flr[f], Rc = m.flr[m.nf + f];
+    const T* geo = m.fgeo + f * FGEO;
+    const T n[3] = {geo[0], geo[1], geo[2]};
+    const T w = geo[3];
+    const int mine_cell = side == 0 ? L : Rc;
+    T Ws[5], gs[3][5];
+    if (mine_cell >= 0) {
+        const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
+        eval_poly(poly + (int64_t)mine_cell * 50, X, Ws, gs);
+    } else {
+        // open boundary: the missing side is the interior cell's average with
+        // zero gradient (zeroth-order extrapolation; the paper leaves outflow
+        // boundaries open, and copying the interior Gauss-point state is not
+        // stable)
+        const int64_t in = side == 0 ? Rc : L;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Ws[q] = Wavg[q * m.nc + in];
+            gs[0][q] = gs[1][q] = gs[2][q] = T(0);
+        }
+    }
+    T Rm[3][3];
+    face_frame(n, Rm);
+    T tW[5], tg[3][5];
+    to_local(Rm, Ws, gs, tW, tg);
+    T Fh[5], D[5], W0[5], dWt[5];
+    gks_point_pair(ph, side, tW, tg, dt, Fh, D, W0, dWt);
+    T* mine = red + (lf * 3 + k) * NR;
+    if (active) {
+        if (side == 0) {
+            to_global(Rm, Fh);
+            to_global(Rm, D);
+        } else {
+            to_global(Rm, W0);
+            to_global(Rm, dWt);
+        }
+        if (NR == 40) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (side == 0) {
+                    // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
+                    mine[q] = w * Fh[q];
+                    mine[5 + q] = w * (T(2) * Fh[q] - D[q] * T(1.0 / 3.0));
+                } else {
+                    const T ws = w * (W0[q] + T(0.5) * dWt[q]);  // f* = f^n + dt/2 f_t^n
+                    const T w0 = w * W0[q];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        mine[10 + 3 * q + i] = ws * n[i];
+                        mine[25 + 3 * q + i] = w0 * n[i];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (side == 0) {
+                    mine[q] = w * T(4.0 / 3.0) * D[q];  // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
+                } else {
+                    const T dg = w * dWt[q];  // f^{n+1} = f^n + dt f_t^*
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) mine[5 + 3 * q + i] = dg * n[i];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // sum the three Gauss points of each face; coalesced record store
+    const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
+    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 6 * FLUX_FACES) {
+        const int fl = idx / NR, j = idx - fl * NR;
+        if (base + fl < m.nf) {
+            const T* r = red + fl * 3 * NR + j;
+            rec[(base + fl) * NR + j] = (r[0] + r[NR]) + r[2 * NR];
+        }
+    }
+}
+
+// 3 threads per face, one Gauss point each (used for FP64, whose register
+// footprint leaves no room for the lane-pair split)
+template <typename T, int NR>
+__global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Phys<T> ph,
+                                                                 const T* __restrict__ Wavg,
+                                                                 const T* __restrict__ poly,
+                                                                 T* __restrict__ rec,
+                                                                 const double* __restrict__ ctrl,
+                                                                 double dt_override) {
+    __shared__ T red[FLUX_FACES * 3 * NR];
+    const double dtd = dt_override > 0.0 ? dt_override : ctrl[CTRL_DT];
+    if (!(dtd > 0.0)) return;
     const T dt = (T)dtd;
     const int lf = threadIdx.x / 3;
     const int k = threadIdx.x - 3 * lf;
@@ -323,26 +449,20 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
         const T n[3] = {geo[0], geo[1], geo[2]};
         const T w = geo[3];
         T WL[5], gL[3][5], WR[5], gR[3][5];
-        if (L >= 0) {
-            const T X[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
-            eval_poly(poly + (int64_t)L * 50, X, WL, gL);
-        }
-        if (Rc >= 0) {
-            const T X[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
-            eval_poly(poly + (int64_t)Rc * 50, X, WR, gR);
-        }
-        // open boundary: the missing side is the interior cell's average with
-        // zero gradient (zeroth-order extrapolation; the paper leaves outflow
-        // boundaries open, and copying the interior Gauss-point state is not
-        // stable)
-        if (L < 0 || Rc < 0) {
-            const int64_t in = L < 0 ? Rc : L;
-            T* Wg = L < 0 ? WL : WR;
-            T (*gg)[5] = L < 0 ? gL : gR;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                Wg[q] = Wavg[q * m.nc + in];
-                gg[0][q] = gg[1][q] = gg[2][q] = T(0);
+        for (int side = 0; side < 2; ++side) {
+            const int cell = side == 0 ? L : Rc;
+            T* Wv = side == 0 ? WL : WR;
+            T (*g)[5] = side == 0 ? gL : gR;
+            if (cell >= 0) {
+                const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
+                eval_poly(poly + (int64_t)cell * 50, X, Wv, g);
+            } else {
+                // open boundary: interior cell average, zero gradient
+                const int64_t in = side == 0 ? Rc : L;
+                for (int q = 0; q < 5; ++q) {
+                    Wv[q] = Wavg[q * m.nc + in];
+                    g[0][q] = g[1][q] = g[2][q] = T(0);
+                }
             }
         }
         T Rm[3][3];
@@ -356,33 +476,27 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
         to_global(Rm, D);
         to_global(Rm, W0);
         to_global(Rm, dWt);
-        if (NR == 40) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
                 mine[q] = w * Fh[q];
                 mine[5 + q] = w * (T(2) * Fh[q] - D[q] * T(1.0 / 3.0));
-                const T ws = w * (W0[q] + T(0.5) * dWt[q]);  // f* = f^n + dt/2 f_t^n
+                const T ws = w * (W0[q] + T(0.5) * dWt[q]);
                 const T w0 = w * W0[q];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     mine[10 + 3 * q + i] = ws * n[i];
                     mine[25 + 3 * q + i] = w0 * n[i];
                 }
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
+            } else {
                 mine[q] = w * T(4.0 / 3.0) * D[q];
-                const T dg = w * dWt[q];  // f^{n+1} = f^n + dt f_t^*
+                const T dg = w * dWt[q];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) mine[5 + 3 * q + i] = dg * n[i];
             }
         }
     }
     __syncthreads();
-    // sum the three Gauss points of each face; coalesced record store
     const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
     for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 3 * FLUX_FACES) {
         const int fl = idx / NR, j = idx - fl * NR;
@@ -394,76 +508,73 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
 }
 
 // --------------------------------------------------------------------------
-// cell updates
+// cell updates (5 lanes per cell)
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState<T> st) {
     const double dtd = st.ctrl[CTRL_DT];
     if (!(dtd > 0.0)) return;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m.nc) return;
-    const int64_t nc = m.nc;
-    CSum<T> fh[5], s1[5];
-    T gs[15], g0[15];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        fh[q].init();
-        s1[q].init();
-    }
-#pragma unroll
-    for (int j = 0; j < 15; ++j) gs[j] = g0[j] = T(0);
+    const CellLane cl = cell_lane(m.nc);
+    if (!cl.active) return;
+    const int64_t nc = m.nc, c = cl.c;
+    const int q = cl.q;
+    CSum<T> fh, s1;
+    fh.init();
+    s1.init();
+    T gs[3] = {T(0), T(0), T(0)}, g0[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int e = m.cface[f * nc + c];
         const T s = (e & 1) ? T(-1) : T(1);
         const T* r = st.rec + (int64_t)(e >> 1) * 40;
+        fh.add(s * r[q]);
+        s1.add(s * r[5 + q]);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            fh[q].add(s * r[q]);
-            s1[q].add(s * r[5 + q]);
-        }
-#pragma unroll
-        for (int j = 0; j < 15; ++j) {
-            gs[j] += s * r[10 + j];
-            g0[j] += s * r[25 + j];
+        for (int i = 0; i < 3; ++i) {
+            gs[i] += s * r[10 + 3 * q + i];
+            g0[i] += s * r[25 + 3 * q + i];
         }
     }
     const double iv = m.inv_vol[c];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        // W* = W^n - (1/|Omega|) sum s sum_k w Fh  (Eq. s2o4, first stage)
-        st.Ws[q * nc + c] = (T)(st.Wd[q * nc + c] - fh[q].value() * iv);
-        st.S[q * nc + c] = s1[q].value();
-    }
+    // W* = W^n - (1/|Omega|) sum s sum_k w Fh  (Eq. s2o4, first stage)
+    st.Ws[q * nc + c] = (T)(st.Wd[q * nc + c] - fh.value() * iv);
+    st.S[q * nc + c] = s1.value();
     const T ivr = (T)iv;
 #pragma unroll
-    for (int j = 0; j < 15; ++j) {
-        st.dWs[j * nc + c] = gs[j] * ivr;  // Eq. gauss-formula at t* (Eq. step-du)
-        st.G[j * nc + c] = g0[j];
+    for (int i = 0; i < 3; ++i) {
+        st.dWs[(3 * q + i) * nc + c] = gs[i] * ivr;  // Eq. gauss-formula at t* (Eq. step-du)
+        st.G[(3 * q + i) * nc + c] = g0[i];
     }
 }
 
-// deterministic block reduction of one min and five sums
+// deterministic block reduction of one min and five sums (warp shuffles,
+// then the 4 warp results in a fixed order)
 __device__ __forceinline__ void block_reduce_part(double mn, const double* sums, double* out) {
-    __shared__ double smin[CELL_THREADS];
-    __shared__ double ssum[5][CELL_THREADS];
-    const int t = threadIdx.x;
-    smin[t] = mn;
+    __shared__ double red[CELL_THREADS / 32][6];
+    double v[6] = {mn, sums[0], sums[1], sums[2], sums[3], sums[4]};
 #pragma unroll
-    for (int q = 0; q < 5; ++q) ssum[q][t] = sums[q];
-    __syncthreads();
-    for (int s = CELL_THREADS / 2; s > 0; s >>= 1) {
-        if (t < s) {
-            smin[t] = fmin(smin[t], smin[t + s]);
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmin(v[0], __shfl_down_sync(0xffffffffu, v[0], o));
 #pragma unroll
-            for (int q = 0; q < 5; ++q) ssum[q][t] += ssum[q][t + s];
-        }
-        __syncthreads();
+        for (int k = 1; k < 6; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     }
-    if (t == 0) {
-        out[PART_DTMIN] = smin[0];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) out[PART_RES + q] = ssum[q][0];
+        for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = red[0][k];
+        for (int w = 1; w < CELL_THREADS / 32; ++w) {
+            r[0] = fmin(r[0], red[w][0]);
+#pragma unroll
+            for (int k = 1; k < 6; ++k) r[k] += red[w][k];
+        }
+        out[PART_DTMIN] = r[0];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[PART_RES + q] = r[1 + q];
     }
 }
 
@@ -471,48 +582,49 @@ template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys p, DevState<T> st) {
     const double dtd = st.ctrl[CTRL_DT];
     if (!(dtd > 0.0)) return;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nc = m.nc;
+    const CellLane cl = cell_lane(m.nc);
+    const int64_t nc = m.nc, c = cl.c;
+    const int q = cl.q;
     double mn = INFINITY;
     double res[5] = {0, 0, 0, 0, 0};
-    if (c < nc) {
-        CSum<T> f2[5];
-        T dg[15];
+    CSum<T> f2;
+    f2.init();
+    T dg[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int q = 0; q < 5; ++q) f2[q].init();
+    for (int f = 0; f < 4; ++f) {
+        const int e = m.cface[f * nc + c];
+        const T s = (e & 1) ? T(-1) : T(1);
+        const T* r = st.rec + (int64_t)(e >> 1) * 20;
+        f2.add(s * r[q]);
 #pragma unroll
-        for (int j = 0; j < 15; ++j) dg[j] = T(0);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const int e = m.cface[f * nc + c];
-            const T s = (e & 1) ? T(-1) : T(1);
-            const T* r = st.rec + (int64_t)(e >> 1) * 20;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) f2[q].add(s * r[q]);
-#pragma unroll
-            for (int j = 0; j < 15; ++j) dg[j] += s * r[5 + j];
-        }
-        const double iv = m.inv_vol[c];
-        T Wn[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            // W^{n+1} |Omega| = W^n |Omega| - [dt F + dt^2/6 F_t](W^n)
-            //                   - [dt^2/3 F_t](W*)   (Eq. s2o4, second stage)
-            const double inc = ((st.S[q * nc + c] + (double)f2[q].hi) + (double)f2[q].lo) * iv;
-            const double wn = st.Wd[q * nc + c] - inc;
-            st.Wd[q * nc + c] = wn;
-            Wn[q] = (T)wn;
-            if ((void*)st.Wr != (void*)st.Wd) st.Wr[q * nc + c] = Wn[q];
-            const double r = inc / dtd;
-            res[q] = r * r;
-        }
+        for (int i = 0; i < 3; ++i) dg[i] += s * r[5 + 3 * q + i];
+    }
+    const double iv = m.inv_vol[c];
+    // W^{n+1} |Omega| = W^n |Omega| - [dt F + dt^2/6 F_t](W^n) - [dt^2/3 F_t](W*)
+    // (Eq. s2o4, second stage)
+    const double inc = ((st.S[q * nc + c] + (double)f2.hi) + (double)f2.lo) * iv;
+    const double wn = st.Wd[q * nc + c] - inc;
+    const T Wq = (T)wn;
+    if (cl.active) {
+        st.Wd[q * nc + c] = wn;
+        if ((void*)st.Wr != (void*)st.Wd) st.Wr[q * nc + c] = Wq;
         const T ivr = (T)iv;
 #pragma unroll
-        for (int j = 0; j < 15; ++j) st.dW[j * nc + c] = (st.G[j * nc + c] + dg[j]) * ivr;
-        const double pr = (p.gamma - 1.0) * ((double)Wn[4] - 0.5 * ((double)Wn[1] * Wn[1] + (double)Wn[2] * Wn[2] +
-                                                                    (double)Wn[3] * Wn[3]) / (double)Wn[0]);
-        if (!(Wn[0] > T(0)) || !(pr > 0.0)) atomicOr(st.err, ERR_STATE);
-        else mn = local_dt(Wn, m.dr[c], p);
+        for (int i = 0; i < 3; ++i)
+            st.dW[(3 * q + i) * nc + c] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
+        // squared increments; the residual divides by dt^2 on the host
+#pragma unroll
+        for (int k = 0; k < 5; ++k) res[k] = k == q ? inc * inc : 0.0;
+    }
+    // the cell's new state, gathered from its 5 lanes, for the positivity flag
+    // and the next step's local time-step limit
+    T Wn[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Wn[k] = __shfl_sync(0xffffffffu, Wq, cl.base + k);
+    if (cl.active && q == 0) {
+        const T pr = T(p.gamma - 1.0) * (Wn[4] - T(0.5) * (Wn[1] * Wn[1] + Wn[2] * Wn[2] + Wn[3] * Wn[3]) / Wn[0]);
+        if (!(Wn[0] > T(0)) || !(pr > T(0))) atomicOr(st.err, ERR_STATE);
+        else mn = (double)local_dt(Wn, m.dr[c], p);
     }
     block_reduce_part(mn, res, st.part + (int64_t)blockIdx.x * PART_N);
     if (blockIdx.x == 0 && threadIdx.x == 0) st.ctrl[CTRL_T] += dtd;
@@ -522,44 +634,21 @@ template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, HostPhys p,
                                                                const T* __restrict__ W,
                                                                double* __restrict__ part) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const CellLane cl = cell_lane(m.nc);
     double mn = INFINITY;
     double zero[5] = {0, 0, 0, 0, 0};
-    if (c < m.nc) {
+    if (cl.active && cl.q == 0) {
         T Wv[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + c];
-        mn = local_dt(Wv, m.dr[c], p);
+        for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + cl.c];
+        mn = (double)local_dt(Wv, m.dr[cl.c], p);
     }
     block_reduce_part(mn, zero, part + (int64_t)blockIdx.x * PART_N);
 }
 
-__global__ void k_dt_finalize(const double* __restrict__ part, int nblk, double cfl,
-                              double* __restrict__ ctrl) {
-    __shared__ double smin[256];
-    double mn = INFINITY;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) mn = fmin(mn, part[(int64_t)b * PART_N]);
-    smin[threadIdx.x] = mn;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double dt = ctrl[CTRL_DT_FIXED] > 0.0 ? ctrl[CTRL_DT_FIXED] : cfl * smin[0];
-        const double t_end = ctrl[CTRL_T_END];
-        if (t_end > 0.0) {
-            const double rem = t_end - ctrl[CTRL_T];
-            if (rem <= 1e-12 * t_end) {
-                dt = 0.0;
-                if (rem > 0.0) ctrl[CTRL_T] = t_end;
-            } else if (dt > rem) {
-                dt = rem;
-            }
-        }
-        if (!(dt > 0.0)) dt = 0.0;
-        ctrl[CTRL_DT] = dt;
-    }
+__global__ void __launch_bounds__(CELL_THREADS) k_dt_finalize(const double* __restrict__ part, int nblk,
+                                                                double cfl, double* __restrict__ ctrl) {
+    finalize_dt_block(part, nblk, cfl, ctrl);
 }
 
 __global__ void k_set_control(double* ctrl, double dt_fixed, double t_end, int reset) {
@@ -582,7 +671,7 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
-static inline unsigned cell_grid(int64_t nc) { return (unsigned)((nc + CELL_THREADS - 1) / CELL_THREADS); }
+static inline unsigned cell_grid(int64_t nc) { return (unsigned)((nc + CELLS_PER_BLOCK - 1) / CELLS_PER_BLOCK); }
 
 int update_blocks(int64_t nc) { return (int)cell_grid(nc); }
 
@@ -602,22 +691,34 @@ static Phys<T> make_phys(const HostPhys& p) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* W, T* slopes, cudaStream_t s) {
+static FinArg<T> fin_arg(const typename Launch<T>::Finalize* fin) {
+    FinArg<T> a;
+    a.part = fin ? fin->part : nullptr;
+    a.nblk = fin ? fin->nblk : 0;
+    a.cfl = fin ? fin->cfl : 0.0;
+    a.ctrl = fin ? fin->ctrl : nullptr;
+    return a;
+}
+
+template <typename T>
+cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
+                              cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_slopes<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, W, slopes);
+    k_slopes<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, W, slopes, fin_arg<T>(fin));
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
-                             const T* slopes, T* poly, int32_t* fallback, cudaStream_t s) {
+                             const T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+                             cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
     ReconConst<T> rc;
     rc.gm1 = (T)(p.gamma - 1.0);
     rc.eps = (T)p.eps_weno;
     rc.weno = p.weno;
     rc.order = p.order;
-    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, W, dW, slopes, poly, fallback);
+    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, W, dW, slopes, poly, fallback, fin_arg<T>(fin));
     return cudaGetLastError();
 }
 
@@ -627,10 +728,18 @@ cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, 
     if (m.nf == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
     const Phys<T> ph = make_phys<T>(p);
-    if (stage == 1)
-        k_flux<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
-    else
-        k_flux<T, 20><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+    if (sizeof(T) == 4) {
+        // FP32: a lane pair per Gauss point
+        if (stage == 1)
+            k_flux<T, 40><<<grid, 6 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        else
+            k_flux<T, 20><<<grid, 6 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+    } else {
+        if (stage == 1)
+            k_flux_single<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        else
+            k_flux_single<T, 20><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+    }
     return cudaGetLastError();
 }
 
@@ -672,7 +781,7 @@ cudaError_t Launch<T>::from_double(const double* in, T* out, int64_t n, cudaStre
 }
 
 cudaError_t launch_dt_finalize(const double* part, int nblk, double cfl, double* ctrl, cudaStream_t s) {
-    k_dt_finalize<<<1, 256, 0, s>>>(part, nblk, cfl, ctrl);
+    k_dt_finalize<<<1, CELL_THREADS, 0, s>>>(part, nblk, cfl, ctrl);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ enum { ERR_STATE = 1 };
 
 constexpr int FLUX_FACES = 32;       // faces per flux block (3 threads each)
 constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
+constexpr int CELLS_PER_BLOCK = 24;  // 4 warps x 6 cells, 5 lanes per cell
 constexpr int FGEO = 24;             // reals per face geometry record
 
 template <typename T>
@@ -60,9 +61,19 @@ struct HostPhys {
 template <typename T>
 struct Launch {
     // stage pieces
-    static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, cudaStream_t s);
+    // fin (may be NULL): block 0 first turns the per-block minima into the
+    // step's dt (the time-step rule's global minimum, t_end clipping)
+    struct Finalize {
+        const double* part;
+        int nblk;
+        double cfl;
+        double* ctrl;
+    };
+    static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
+                              cudaStream_t s);
     static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
-                             const T* slopes, T* poly, int32_t* fallback, cudaStream_t s);
+                             const T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+                             cudaStream_t s);
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
                             const double* ctrl, double dt_override, int stage, cudaStream_t s);
     static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
@@ -76,18 +87,20 @@ struct Launch {
 };
 
 // Local time-step limit of one cell (Sec. 5, Eq. time-step, without C_CFL):
-// dr / (|U| + a), and dr^2 / (3 nu) if viscous, from its averages Wv[5].
+// dr / (|U| + a), and dr^2 / (3 nu) if viscous, from its averages Wv[5],
+// in the working precision T.
 #ifdef __CUDACC__
 template <typename T>
-__device__ __forceinline__ double local_dt(const T* Wv, T dr, const HostPhys& p) {
-    const double rho = (double)Wv[0];
-    const double u = (double)Wv[1] / rho, v = (double)Wv[2] / rho, w = (double)Wv[3] / rho;
-    const double pr = (p.gamma - 1.0) * ((double)Wv[4] - 0.5 * rho * (u * u + v * v + w * w));
-    const double a = sqrt(p.gamma * pr / rho);
-    double d = (double)dr / (sqrt(u * u + v * v + w * w) + a);
+__device__ __forceinline__ T local_dt(const T* Wv, T dr, const HostPhys& p) {
+    const T ir = T(1) / Wv[0];
+    const T u = Wv[1] * ir, v = Wv[2] * ir, w = Wv[3] * ir;
+    const T q = u * u + v * v + w * w;
+    const T pr = T(p.gamma - 1.0) * (Wv[4] - T(0.5) * Wv[0] * q);
+    const T a = sqrt(T(p.gamma) * pr * ir);
+    T d = dr / (sqrt(q) + a);
     if (p.viscous && p.mu > 0.0) {
-        const double dv = (double)dr * (double)dr / (3.0 * p.mu / rho);
-        d = fmin(d, dv);
+        const T dv = dr * dr * Wv[0] / (T(3.0 * p.mu));
+        d = d < dv ? d : dv;
     }
     return d;
 }
