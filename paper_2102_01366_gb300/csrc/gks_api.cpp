@@ -237,7 +237,7 @@ Layout layout_workspace(int64_t nc, int64_t nf, bool fp32) {
     L.S = L.add(8 * 5 * nc);
     L.G = L.add(T * 15 * nc);
     L.slopes = L.add(T * 15 * nc);
-    L.poly = L.add(T * 50 * nc);
+    L.poly = L.add(T * POLY_STRIDE * nc);
     L.rec = L.add(T * 40 * nf);
     L.ctrl = L.add(8 * CTRL_N);
     L.part = L.add(8 * PART_N * nblk);
@@ -481,16 +481,11 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     const typename Launch<T>::Finalize fin{st.part, update_blocks(m.nc), p.cfl, st.ctrl};
     cudaError_t e;
     // stage 1 from (W^n, grad W^n)
-    if (need_b && (e = Launch<T>::slopes(m, st.Wr, st.slopes, &fin, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, nullptr, need_b ? nullptr : &fin, q)) !=
-        cudaSuccess)
-        return e;
+    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, nullptr, st.poly, nullptr, &fin, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
     // stage 2 from (W*, grad W*)
-    if (need_b && (e = Launch<T>::slopes(m, st.Ws, st.slopes, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, st.slopes, st.poly, nullptr, nullptr, q)) != cudaSuccess)
-        return e;
+    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, nullptr, st.poly, nullptr, nullptr, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
     return Launch<T>::update2(m, p, st, q);
 }
@@ -557,12 +552,8 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             const T* W = stage == 1 ? st.Wr : st.Ws;
             const T* dW = stage == 1 ? st.dW : st.dWs;
             const bool fuse = stage == 1;
-            if (need_b) {
-                e = Launch<T>::slopes(m, W, st.slopes, fuse ? &fin : nullptr, q);
-                if (e == cudaSuccess) e = mark(GKS_K_SLOPES);
-            }
             if (e == cudaSuccess)
-                e = Launch<T>::recon(m, p, W, dW, st.slopes, st.poly, nullptr, (fuse && !need_b) ? &fin : nullptr, q);
+                e = Launch<T>::recon(m, p, W, dW, nullptr, st.poly, nullptr, fuse ? &fin : nullptr, q);
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
             if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.ctrl, 0.0, stage, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
@@ -731,10 +722,10 @@ static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st,
     const HostPhys& p = s->phys;
     const bool need_b = p.weno || p.order == 2;
     const int64_t nc = m.nc;
-    if (need_b) GKS_CHECK_CUDA(Launch<T>::slopes(m, st.Wr, st.slopes, nullptr, s->stream));
-    else GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, st.slopes, st.poly, d_fallback, nullptr, s->stream));
-    if (d_poly) GKS_CHECK_CUDA(Launch<T>::to_double(st.poly, d_poly, 50 * nc, s->stream));
+    if (!need_b) GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, need_b ? st.slopes : nullptr, st.poly, d_fallback,
+                                    nullptr, s->stream));
+    if (d_poly) GKS_CHECK_CUDA(Launch<T>::poly_to_double(st.poly, d_poly, nc, s->stream));
     if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
     return GKS_OK;
 }

@@ -228,6 +228,74 @@ __device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& ful
     micro_slope(s, K, r, A);
 }
 
+// Time coefficients of Eq. 2nd-flux over [0, dt/2] (k0, k1 for the kinetic
+// factors e and t e; q1..q3 for C1..C3) and their "dt minus twice dt/2"
+// differences (dk*, dq*), with E = exp(-dt/tau_n) = Eh^2.
+template <typename T>
+struct TimeCoef {
+    T tau, tau_n, E;
+    T k0, k1, q1, q2, q3;
+    T dk0, dk1, dq1, dq2, dq3;
+};
+
+template <typename T>
+__device__ __forceinline__ TimeCoef<T> time_coefs(const Phys<T>& ph, T pl, T pr, T pc, T dt) {
+    TimeCoef<T> c;
+    c.tau = ph.viscous ? ph.mu / pc : T(0);
+    const T jump = d_abs((pl - pr) / (pl + pr)) * dt;
+    c.tau_n = (ph.viscous ? ph.mu / pc : ph.tau_eps * dt) + ph.tau_c * jump;
+    const T hd = T(0.5) * dt;
+    const T Eh = d_exp(-hd / c.tau_n);
+    c.E = Eh * Eh;
+    const T omh = T(1) - Eh;
+    const T tn = c.tau_n, tau = c.tau;
+    c.k0 = tn * omh;
+    c.k1 = tn * (tn * omh - hd * Eh);
+    c.q1 = hd - c.k0;
+    c.q2 = c.k1 + tau * c.k0 - tau * hd;
+    c.q3 = T(0.5) * hd * hd - tau * hd + tau * c.k0;
+    c.dk0 = -tn * omh * omh;
+    c.dk1 = -tn * tn * omh * omh + tn * dt * Eh * omh;
+    c.dq1 = tn * omh * omh;
+    c.dq2 = c.dk1 + tau * c.dk0;
+    c.dq3 = T(0.25) * dt * dt + tau * c.dk0;
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ void axpy5(T a, const T* x, T* y) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) y[k] += a * x[k];
+}
+
+// One side's initial-state (kinetic) part of Eq. 2nd-flux,
+//   e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1),
+// added to Fh, D, W0, dW.  Each velocity moment is formed once and scaled by
+// the time coefficients of all four outputs; the A terms carry a factor tau
+// and are skipped for inviscid flow.  Also returns this side's contributions
+// rho <psi> to W^c and rho <a_i psi> to its slopes (half space).
+template <typename T>
+__device__ __forceinline__ void kinetic_side(const Phys<T>& ph, const Prim<T>& S, const T (*g)[5], int half,
+                                             Tab<T>& t, T (*a)[5], T* A) {
+    const T ir = T(1) / S.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T b[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) b[k] = g[i][k] * ir;
+        micro_slope(S, ph.K, b, a[i]);
+    }
+    if (ph.viscous) {
+        make_tab(t, S, ph.K, 0);
+        T r[5] = {T(0), T(0), T(0), T(0), T(0)};
+        acc_grad<0>(t, a, T(-1), r);
+        micro_slope(S, ph.K, r, A);
+        make_half_u(t, S, half);
+    } else {
+        make_tab(t, S, ph.K, half);
+    }
+}
+
 // Time-dependent kinetic solution at one Gauss point, face frame.
 //   Wl, Wr: states; gl[i][q], gr[i][q]: gradients (direction i, comp q)
 // Outputs, each 5 long:
@@ -240,42 +308,7 @@ template <typename T>
 __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const T (*gl)[5],
                                           const T* Wr, const T (*gr)[5], T dt, T* Fh, T* D,
                                           T* W0, T* dW) {
-    const Prim<T> L = to_prim(Wl, ph.gm1);
-    const Prim<T> R = to_prim(Wr, ph.gm1);
-
-    // -- equilibrium state at the interface, Eq. new-equ-part (values) --
-    T Wc[5] = {T(0), T(0), T(0), T(0), T(0)};
-    {
-        Tab<T> t;
-        make_tab(t, L, ph.K, +1);
-        acc_psi<0, 0, 0>(t, L.rho, Wc);
-        make_tab(t, R, ph.K, -1);
-        acc_psi<0, 0, 0>(t, R.rho, Wc);
-    }
-    const Prim<T> C = to_prim(Wc, ph.gm1);
-
-    // -- collision times, Sec. 2.2 --
-    const T tau = ph.viscous ? ph.mu / C.p : T(0);
-    const T jump = d_abs((L.p - R.p) / (L.p + R.p)) * dt;
-    const T tau_n = (ph.viscous ? ph.mu / C.p : ph.tau_eps * dt) + ph.tau_c * jump;
-
-    // -- time coefficients over [0, dt/2] and their dt-minus-twice-dt/2
-    //    differences (E = Eh^2) --
-    const T hd = T(0.5) * dt;
-    const T Eh = d_exp(-hd / tau_n);
-    const T E = Eh * Eh;
-    const T omh = T(1) - Eh;
-    const T k0 = tau_n * omh;                              // int_0^{dt/2} e
-    const T k1 = tau_n * (tau_n * omh - hd * Eh);          // int_0^{dt/2} t e
-    const T q1 = hd - k0;                                  // int C1
-    const T q2 = k1 + tau * k0 - tau * hd;                 // int C2
-    const T q3 = T(0.5) * hd * hd - tau * hd + tau * k0;   // int C3
-    const T dk0 = -tau_n * omh * omh;
-    const T dk1 = -tau_n * tau_n * omh * omh + tau_n * dt * Eh * omh;
-    const T dq1 = tau_n * omh * omh;
-    const T dq2 = dk1 + tau * dk0;
-    const T dq3 = T(0.25) * dt * dt + tau * dk0;
-
+    const Prim<T> P[2] = {to_prim(Wl, ph.gm1), to_prim(Wr, ph.gm1)};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         Fh[k] = T(0);
@@ -283,83 +316,94 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
         W0[k] = T(0);
         dW[k] = T(0);
     }
+    // W^c from the half-space moments of both sides (Eq. new-equ-part)
+    T Wc[5] = {T(0), T(0), T(0), T(0), T(0)};
+    {
+        Tab<T> t;
+        make_tab(t, P[0], ph.K, +1);
+        acc_psi<0, 0, 0>(t, P[0].rho, Wc);
+        make_tab(t, P[1], ph.K, -1);
+        acc_psi<0, 0, 0>(t, P[1].rho, Wc);
+    }
+    const Prim<T> C = to_prim(Wc, ph.gm1);
+    const TimeCoef<T> tc = time_coefs(ph, P[0].p, P[1].p, C.p, dt);
+    const T tau = tc.tau;
     T dWc[3][5];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int k = 0; k < 5; ++k) dWc[i][k] = T(0);
-
-    // -- kinetic (initial-state) parts of the two sides --
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
-        const Prim<T> S = side == 0 ? L : R;
-        const T (*g)[5] = side == 0 ? gl : gr;
+        const Prim<T> S = P[side];
         Tab<T> t;
-        make_tab(t, S, ph.K, 0);
         T a[3][5], A[5];
-        state_slopes(S, t, ph.K, g, a, A);
-        make_half_u(t, S, side == 0 ? +1 : -1);
-        // slope of the interface equilibrium, Eq. new-equ-part (gradients)
+        kinetic_side(ph, S, side == 0 ? gl : gr, side == 0 ? +1 : -1, t, a, A);
 #pragma unroll
         for (int i = 0; i < 3; ++i) acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
-        if (!ph.smooth) {
-            // e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1), Eq. 2nd-flux
-            acc_psi<1, 0, 0>(t, S.rho * k0, Fh);
-            acc_grad<1>(t, a, -S.rho * (tau * k0 + k1), Fh);
-            acc_apsi<1, 0, 0>(t, A, -S.rho * tau * k0, Fh);
-            acc_psi<1, 0, 0>(t, S.rho * dk0, D);
-            acc_grad<1>(t, a, -S.rho * (tau * dk0 + dk1), D);
-            acc_apsi<1, 0, 0>(t, A, -S.rho * tau * dk0, D);
-            // W(0) (e = 1) and W(dt) - W(0); the rho <psi> terms of the two
-            // sides add up to Wc and cancel against the C1 term below
-            acc_psi<0, 0, 0>(t, S.rho, W0);
-            acc_grad<0>(t, a, -S.rho * tau, W0);
-            acc_apsi<0, 0, 0>(t, A, -S.rho * tau, W0);
-            acc_grad<0>(t, a, S.rho * (tau - (tau + dt) * E), dW);
-            acc_apsi<0, 0, 0>(t, A, S.rho * tau * (T(1) - E), dW);
+        if (ph.smooth) continue;
+        T mf0[5] = {0}, mf1[5] = {0}, mw0[5] = {0}, mw1[5] = {0};
+        acc_psi<1, 0, 0>(t, S.rho, mf0);
+        acc_grad<1>(t, a, S.rho, mf1);
+        acc_psi<0, 0, 0>(t, S.rho, mw0);
+        acc_grad<0>(t, a, S.rho, mw1);
+        axpy5(tc.k0, mf0, Fh);
+        axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
+        axpy5(tc.dk0, mf0, D);
+        axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
+        axpy5(T(1), mw0, W0);
+        axpy5(-tau, mw1, W0);
+        axpy5(tau - (tau + dt) * tc.E, mw1, dW);
+        if (ph.viscous) {
+            T mf2[5] = {0}, mw2[5] = {0};
+            acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
+            acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
+            axpy5(-tau * tc.k0, mf2, Fh);
+            axpy5(-tau * tc.dk0, mf2, D);
+            axpy5(-tau, mw2, W0);
+            axpy5(tau * (T(1) - tc.E), mw2, dW);
         }
     }
-
-    // -- hydrodynamic (equilibrium) part --
-    {
-        Tab<T> t;
-        make_tab(t, C, ph.K, 0);
-        T ac[3][5], Ac[5];
-        state_slopes(C, t, ph.K, dWc, ac, Ac);
-        if (ph.smooth) {
-            // f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t, Eq. 2nd-smooth-flux
-            acc_psi<1, 0, 0>(t, C.rho * hd, Fh);
-            acc_grad<1>(t, ac, -C.rho * tau * hd, Fh);
-            acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * hd * hd - tau * hd), Fh);
-            acc_apsi<1, 0, 0>(t, Ac, C.rho * T(0.25) * dt * dt, D);
+    // hydrodynamic (equilibrium) part: C1 g^c + C2 a^c.u g^c + C3 A^c g^c
+    Tab<T> t;
+    make_tab(t, C, ph.K, 0);
+    T ac[3][5], Ac[5];
+    state_slopes(C, t, ph.K, dWc, ac, Ac);
+    T mf0[5] = {0}, mf1[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+    acc_psi<1, 0, 0>(t, C.rho, mf0);
+    acc_grad<1>(t, ac, C.rho, mf1);
+    acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
+    acc_grad<0>(t, ac, C.rho, mw1);  // and rho <A^c psi> = -mw1 (Eq. co)
+    if (ph.smooth) {
+        // f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t, Eq. 2nd-smooth-flux
+        const T hd = T(0.5) * dt;
+        axpy5(hd, mf0, Fh);
+        axpy5(-tau * hd, mf1, Fh);
+        axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
+        axpy5(T(0.25) * dt * dt, mf2, D);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) W0[k] = Wc[k];
-            acc_grad<0>(t, ac, -C.rho * tau, W0);
-            acc_apsi<0, 0, 0>(t, Ac, -C.rho * tau, W0);
-            acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, dW);
-        } else {
-            // C1 g^c + C2 a^c.u g^c + C3 A^c g^c, Eq. 2nd-flux
-            acc_psi<1, 0, 0>(t, C.rho * q1, Fh);
-            acc_grad<1>(t, ac, C.rho * q2, Fh);
-            acc_apsi<1, 0, 0>(t, Ac, C.rho * q3, Fh);
-            acc_psi<1, 0, 0>(t, C.rho * dq1, D);
-            acc_grad<1>(t, ac, C.rho * dq2, D);
-            acc_apsi<1, 0, 0>(t, Ac, C.rho * dq3, D);
-            // t = 0: C1 = C2 = C3 = 0.  t = dt: C2, C3 (C1 cancelled above)
-            const T C2 = (dt + tau) * E - tau, C3 = dt - tau + tau * E;
-            acc_grad<0>(t, ac, C.rho * C2, dW);
-            acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, dW);
-        }
+        for (int k = 0; k < 5; ++k) W0[k] = Wc[k];  // tau terms cancel: <(a.u + A) psi> = 0
+        axpy5(-dt, mw1, dW);
+    } else {
+        axpy5(tc.q1, mf0, Fh);
+        axpy5(tc.q2, mf1, Fh);
+        axpy5(tc.q3, mf2, Fh);
+        axpy5(tc.dq1, mf0, D);
+        axpy5(tc.dq2, mf1, D);
+        axpy5(tc.dq3, mf2, D);
+        // t = dt: C2, C3 (C1 cancelled against the kinetic W0 terms)
+        const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
+        axpy5(C2 - C3, mw1, dW);
     }
 }
 
 // The same kinetic solution with the work of one Gauss point split over a
 // lane pair (lanes 2j and 2j+1 of a warp, all 32 lanes active): lane "side"
-// owns the left (0) or right (1) initial state.  Each lane computes its side's
-// Maxwellian slopes and half-space moments; the interface equilibrium sums
-// and its slope sums are exchanged with one shuffle per value; both lanes
-// then form the equilibrium slopes, lane 0 adds the hydrodynamic part of Fh
-// (and of W0), lane 1 that of D and dW.  On return both lanes hold the totals.
+// owns the left (0) or right (1) initial state and its kinetic part; the
+// interface equilibrium and its slopes are summed over the pair by shuffles;
+// both lanes form the equilibrium slopes, then lane 0 adds the C2 (a^c.u)
+// flux terms and lane 1 the C1 and C3 flux terms and the dW term.  On return
+// both lanes hold the totals.
 template <typename T>
 __device__ __forceinline__ T pair_sum(T v) {
     return v + __shfl_xor_sync(0xffffffffu, v, 1);
@@ -370,41 +414,19 @@ __device__ __forceinline__ void gks_point_pair(const Phys<T>& ph, int side, cons
                                                T dt, T* Fh, T* D, T* W0, T* dW) {
     const Prim<T> S = to_prim(Ws, ph.gm1);
     const T p_other = __shfl_xor_sync(0xffffffffu, S.p, 1);
-    const int half = side == 0 ? +1 : -1;
-
-    // -- equilibrium state at the interface, Eq. new-equ-part (values) --
-    T Wc[5] = {T(0), T(0), T(0), T(0), T(0)};
     Tab<T> t;
-    make_tab(t, S, ph.K, 0);
     T a[3][5], A[5];
-    state_slopes(S, t, ph.K, gs, a, A);
-    make_half_u(t, S, half);
-    acc_psi<0, 0, 0>(t, S.rho, Wc);
+    kinetic_side(ph, S, gs, side == 0 ? +1 : -1, t, a, A);
+    // W^c (Eq. new-equ-part): this side's half-space moments, summed over the pair
+    T mw0[5] = {T(0), T(0), T(0), T(0), T(0)};
+    acc_psi<0, 0, 0>(t, S.rho, mw0);
+    T Wc[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Wc[k] = pair_sum(Wc[k]);
+    for (int k = 0; k < 5; ++k) Wc[k] = pair_sum(mw0[k]);
     const Prim<T> C = to_prim(Wc, ph.gm1);
-
-    // -- collision times, Sec. 2.2 --
-    const T tau = ph.viscous ? ph.mu / C.p : T(0);
-    const T jump = d_abs((S.p - p_other) / (S.p + p_other)) * dt;
-    const T tau_n = (ph.viscous ? ph.mu / C.p : ph.tau_eps * dt) + ph.tau_c * jump;
-
-    // -- time coefficients (see gks_point) --
-    const T hd = T(0.5) * dt;
-    const T Eh = d_exp(-hd / tau_n);
-    const T E = Eh * Eh;
-    const T omh = T(1) - Eh;
-    const T k0 = tau_n * omh;
-    const T k1 = tau_n * (tau_n * omh - hd * Eh);
-    const T q1 = hd - k0;
-    const T q2 = k1 + tau * k0 - tau * hd;
-    const T q3 = T(0.5) * hd * hd - tau * hd + tau * k0;
-    const T dk0 = -tau_n * omh * omh;
-    const T dk1 = -tau_n * tau_n * omh * omh + tau_n * dt * Eh * omh;
-    const T dq1 = tau_n * omh * omh;
-    const T dq2 = dk1 + tau * dk0;
-    const T dq3 = T(0.25) * dt * dt + tau * dk0;
-
+    const T pl = side == 0 ? S.p : p_other, pr = side == 0 ? p_other : S.p;
+    const TimeCoef<T> tc = time_coefs(ph, pl, pr, C.p, dt);
+    const T tau = tc.tau;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         Fh[k] = T(0);
@@ -412,7 +434,6 @@ __device__ __forceinline__ void gks_point_pair(const Phys<T>& ph, int side, cons
         W0[k] = T(0);
         dW[k] = T(0);
     }
-    // slope of the interface equilibrium, Eq. new-equ-part (gradients)
     T dWc[3][5];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -421,55 +442,65 @@ __device__ __forceinline__ void gks_point_pair(const Phys<T>& ph, int side, cons
         acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
     }
     if (!ph.smooth) {
-        // this side's e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1)
-        acc_psi<1, 0, 0>(t, S.rho * k0, Fh);
-        acc_grad<1>(t, a, -S.rho * (tau * k0 + k1), Fh);
-        acc_apsi<1, 0, 0>(t, A, -S.rho * tau * k0, Fh);
-        acc_psi<1, 0, 0>(t, S.rho * dk0, D);
-        acc_grad<1>(t, a, -S.rho * (tau * dk0 + dk1), D);
-        acc_apsi<1, 0, 0>(t, A, -S.rho * tau * dk0, D);
-        acc_psi<0, 0, 0>(t, S.rho, W0);
-        acc_grad<0>(t, a, -S.rho * tau, W0);
-        acc_apsi<0, 0, 0>(t, A, -S.rho * tau, W0);
-        acc_grad<0>(t, a, S.rho * (tau - (tau + dt) * E), dW);
-        acc_apsi<0, 0, 0>(t, A, S.rho * tau * (T(1) - E), dW);
+        T mf0[5] = {0}, mf1[5] = {0}, mw1[5] = {0};
+        acc_psi<1, 0, 0>(t, S.rho, mf0);
+        acc_grad<1>(t, a, S.rho, mf1);
+        acc_grad<0>(t, a, S.rho, mw1);
+        axpy5(tc.k0, mf0, Fh);
+        axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
+        axpy5(tc.dk0, mf0, D);
+        axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
+        axpy5(T(1), mw0, W0);
+        axpy5(-tau, mw1, W0);
+        axpy5(tau - (tau + dt) * tc.E, mw1, dW);
+        if (ph.viscous) {
+            T mf2[5] = {0}, mw2[5] = {0};
+            acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
+            acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
+            axpy5(-tau * tc.k0, mf2, Fh);
+            axpy5(-tau * tc.dk0, mf2, D);
+            axpy5(-tau, mw2, W0);
+            axpy5(tau * (T(1) - tc.E), mw2, dW);
+        }
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int k = 0; k < 5; ++k) dWc[i][k] = pair_sum(dWc[i][k]);
 
-    // -- hydrodynamic (equilibrium) part, divided between the two lanes --
-    {
-        make_tab(t, C, ph.K, 0);
-        T ac[3][5], Ac[5];
-        state_slopes(C, t, ph.K, dWc, ac, Ac);
+    // hydrodynamic (equilibrium) part, moments divided between the lanes
+    make_tab(t, C, ph.K, 0);
+    T ac[3][5], Ac[5];
+    state_slopes(C, t, ph.K, dWc, ac, Ac);
+    if (side == 0) {
+        T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
+        acc_grad<1>(t, ac, C.rho, mf1);
         if (ph.smooth) {
-            if (side == 0) {
-                acc_psi<1, 0, 0>(t, C.rho * hd, Fh);
-                acc_grad<1>(t, ac, -C.rho * tau * hd, Fh);
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * (T(0.5) * hd * hd - tau * hd), Fh);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) W0[k] += Wc[k];
-                acc_grad<0>(t, ac, -C.rho * tau, W0);
-                acc_apsi<0, 0, 0>(t, Ac, -C.rho * tau, W0);
-            } else {
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * T(0.25) * dt * dt, D);
-                acc_apsi<0, 0, 0>(t, Ac, C.rho * dt, dW);
-            }
+            axpy5(-tau * T(0.5) * dt, mf1, Fh);
         } else {
-            if (side == 0) {
-                acc_psi<1, 0, 0>(t, C.rho * q1, Fh);
-                acc_grad<1>(t, ac, C.rho * q2, Fh);
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * q3, Fh);
-            } else {
-                acc_psi<1, 0, 0>(t, C.rho * dq1, D);
-                acc_grad<1>(t, ac, C.rho * dq2, D);
-                acc_apsi<1, 0, 0>(t, Ac, C.rho * dq3, D);
-                const T C2 = (dt + tau) * E - tau, C3 = dt - tau + tau * E;
-                acc_grad<0>(t, ac, C.rho * C2, dW);
-                acc_apsi<0, 0, 0>(t, Ac, C.rho * C3, dW);
-            }
+            axpy5(tc.q2, mf1, Fh);
+            axpy5(tc.dq2, mf1, D);
+        }
+    } else {
+        T mf0[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+        acc_psi<1, 0, 0>(t, C.rho, mf0);
+        acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
+        acc_grad<0>(t, ac, C.rho, mw1);  // rho <A^c psi> = -mw1 (Eq. co)
+        if (ph.smooth) {
+            const T hd = T(0.5) * dt;
+            axpy5(hd, mf0, Fh);
+            axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
+            axpy5(T(0.25) * dt * dt, mf2, D);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) W0[k] = Wc[k];  // tau terms cancel: <(a.u + A) psi> = 0
+            axpy5(-dt, mw1, dW);
+        } else {
+            axpy5(tc.q1, mf0, Fh);
+            axpy5(tc.q3, mf2, Fh);
+            axpy5(tc.dq1, mf0, D);
+            axpy5(tc.dq3, mf2, D);
+            const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
+            axpy5(C2 - C3, mw1, dW);
         }
     }
 #pragma unroll

@@ -117,21 +117,60 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
     out[2] = b2;
 }
 
-// reconstruction step 2: P2 = M2 d, smoothness indicators, two-step beta_0,
-// nonlinear weights (Sec. 4.1-4.3), positivity at the cell's 12 face Gauss
-// points (Sec. 4.2); R written about the centroid in monomial form
+// P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
+// b = M1 (Q_nb - Q_x) over the existing neighbours
+template <typename T>
+__device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ W, int64_t x, int q, T* b) {
+    const int64_t nc = m.nc;
+    const T Qx = W[q * nc + x];
+    b[0] = b[1] = b[2] = T(0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const int nb = m.nbr[f * nc + x];
+        if (nb < 0) continue;
+        const T dq = W[q * nc + nb] - Qx;
+        b[0] += m.M1[(0 * 4 + f) * nc + x] * dq;
+        b[1] += m.M1[(1 * 4 + f) * nc + x] * dq;
+        b[2] += m.M1[(2 * 4 + f) * nc + x] * dq;
+    }
+}
+
+// reconstruction (Sec. 4.1-4.3): the cell's own P1 slopes and, for the
+// two-step beta_0, its neighbours' P1 slopes (recomputed here: reconstruction
+// step 1 needs no separate pass); P2 = M2 d with M2 staged in shared memory;
+// smoothness indicators, nonlinear weights, positivity at the cell's 12 face
+// Gauss points (Sec. 4.2); R written about the centroid in monomial form
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
                                                          const T* __restrict__ W,
                                                          const T* __restrict__ dW,
-                                                         const T* __restrict__ slopes,
+                                                         T* __restrict__ slopes_out,
                                                          T* __restrict__ poly,
                                                          int32_t* __restrict__ fallback,
                                                          FinArg<T> fin) {
+    __shared__ T sM2[144][CELLS_PER_BLOCK];
+    __shared__ T sG[36][CELLS_PER_BLOCK];
     if (fin.part && blockIdx.x == 0) finalize_dt_block(fin.part, fin.nblk, fin.cfl, fin.ctrl);
-    const CellLane cl = cell_lane(m.nc);
-    const int64_t nc = m.nc, c = cl.c;
+    const int64_t nc = m.nc;
+    {
+        const int64_t cbase = (int64_t)blockIdx.x * CELLS_PER_BLOCK;
+        const int nloc = (int)min((int64_t)CELLS_PER_BLOCK, nc - cbase);
+        for (int idx = threadIdx.x; idx < 144 * CELLS_PER_BLOCK; idx += CELL_THREADS) {
+            const int row = idx / CELLS_PER_BLOCK, col = idx - row * CELLS_PER_BLOCK;
+            sM2[row][col] = col < nloc ? m.M2[row * nc + cbase + col] : T(0);
+        }
+        for (int idx = threadIdx.x; idx < 36 * CELLS_PER_BLOCK; idx += CELL_THREADS) {
+            const int row = idx / CELLS_PER_BLOCK, col = idx - row * CELLS_PER_BLOCK;
+            sG[row][col] = col < nloc ? m.cgp[row * nc + cbase + col] : T(0);
+        }
+    }
+    __syncthreads();
+    const CellLane cl = cell_lane(nc);
+    const int64_t c = cl.c;
     const int q = cl.q;
+    const int lc = (int)(c - (int64_t)blockIdx.x * CELLS_PER_BLOCK) < CELLS_PER_BLOCK
+                       ? (int)(c - (int64_t)blockIdx.x * CELLS_PER_BLOCK)
+                       : CELLS_PER_BLOCK - 1;
     int nb[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
@@ -153,7 +192,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     for (int k = 0; k < 9; ++k) {
         T acc = T(0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc += m.M2[(k * 16 + j) * nc + c] * d[j];
+        for (int j = 0; j < 16; ++j) acc += sM2[k * 16 + j][lc] * d[j];
         a[k] = acc;
     }
     const T Mxx = m.mom2[0 * nc + c], Mxy = m.mom2[1 * nc + c], Mxz = m.mom2[2 * nc + c];
@@ -164,8 +203,18 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     T R[9];
     T b[3] = {T(0), T(0), T(0)};
     if (rc.weno || rc.order == 2) {
+        // own P1 slope from the neighbour differences already loaded
 #pragma unroll
-        for (int i = 0; i < 3; ++i) b[i] = slopes[c * 15 + 3 * q + i];
+        for (int f = 0; f < 4; ++f) {
+            if (nb[f] < 0) continue;
+            b[0] += m.M1[(0 * 4 + f) * nc + c] * d[f];
+            b[1] += m.M1[(1 * 4 + f) * nc + c] * d[f];
+            b[2] += m.M1[(2 * 4 + f) * nc + c] * d[f];
+        }
+        if (slopes_out && cl.active) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) slopes_out[c * 15 + 3 * q + i] = b[i];
+        }
     }
     if (!rc.weno) {
 #pragma unroll
@@ -174,15 +223,15 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
         const T v23 = m.vol23[c], v43 = m.vol43[c];
         // smoothness indicators, Eq. smooth-indicator
         const T beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-        // two-step beta_0 from the neighbours' step-1 slopes, Eq. p0-non-linear-weight
+        // two-step beta_0 from the neighbours' P1 slopes, Eq. p0-non-linear-weight
         T b0j[4];
         int nn = 0;
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (nb[f] < 0) continue;
-            const T* s = slopes + (int64_t)nb[f] * 15 + 3 * q;
-            const T x = s[0], y = s[1], z = s[2];
-            b0j[nn++] = v23 * (x * x + y * y + z * z);
+            T bj[3];
+            p1_slope(m, W, nb[f], q, bj);
+            b0j[nn++] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
         }
         T beta0 = T(0);
         if (nn > 0) {
@@ -238,11 +287,11 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     const T c0 = Q0 - (R[3] * Mxx + R[4] * Mxy + R[5] * Mxz + R[6] * Myy + R[7] * Myz + R[8] * Mzz);
     // positivity: the 5 lanes of the cell exchange their values at each point
     bool bad = false;
-#pragma unroll 1
+#pragma unroll 4
     for (int g = 0; g < 12; ++g) {
-        const T X = m.cgp[(g * 3 + 0) * nc + c];
-        const T Y = m.cgp[(g * 3 + 1) * nc + c];
-        const T Z = m.cgp[(g * 3 + 2) * nc + c];
+        const T X = sG[g * 3 + 0][lc];
+        const T Y = sG[g * 3 + 1][lc];
+        const T Z = sG[g * 3 + 2][lc];
         const T v = c0 + R[0] * X + R[1] * Y + R[2] * Z + R[3] * X * X + R[4] * X * Y + R[5] * X * Z +
                     R[6] * Y * Y + R[7] * Y * Z + R[8] * Z * Z;
         const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
@@ -254,7 +303,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
         if (!(rho > T(0)) || !(pr > T(0))) bad = true;
     }
     if (!cl.active) return;
-    T* out = poly + c * 50 + q * 10;
+    T* out = poly + c * POLY_STRIDE + q * 10;
     out[0] = bad ? Q0 : c0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[1 + k] = bad ? T(0) : R[k];
@@ -266,15 +315,36 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
 // --------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T* val, T (*g)[5]) {
+    // the record is 16-byte aligned (POLY_STRIDE words): load it in vectors
+    T c[POLY_STRIDE];
+    if constexpr (sizeof(T) == 4) {
+        const float4* p4 = reinterpret_cast<const float4*>(P);
+#pragma unroll
+        for (int i = 0; i < POLY_STRIDE / 4; ++i) {
+            const float4 v = __ldg(p4 + i);
+            c[4 * i] = v.x;
+            c[4 * i + 1] = v.y;
+            c[4 * i + 2] = v.z;
+            c[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2* p2 = reinterpret_cast<const double2*>(P);
+#pragma unroll
+        for (int i = 0; i < POLY_STRIDE / 2; ++i) {
+            const double2 v = __ldg(p2 + i);
+            c[2 * i] = v.x;
+            c[2 * i + 1] = v.y;
+        }
+    }
     const T x = X[0], y = X[1], z = X[2];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        const T* c = P + q * 10;
-        val[q] = c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * x + c[5] * x * y + c[6] * x * z +
-                 c[7] * y * y + c[8] * y * z + c[9] * z * z;
-        g[0][q] = c[1] + T(2) * c[4] * x + c[5] * y + c[6] * z;
-        g[1][q] = c[2] + c[5] * x + T(2) * c[7] * y + c[8] * z;
-        g[2][q] = c[3] + c[6] * x + c[8] * y + T(2) * c[9] * z;
+        const T* cq = c + q * 10;
+        val[q] = cq[0] + cq[1] * x + cq[2] * y + cq[3] * z + cq[4] * x * x + cq[5] * x * y + cq[6] * x * z +
+                 cq[7] * y * y + cq[8] * y * z + cq[9] * z * z;
+        g[0][q] = cq[1] + T(2) * cq[4] * x + cq[5] * y + cq[6] * z;
+        g[1][q] = cq[2] + cq[5] * x + T(2) * cq[7] * y + cq[8] * z;
+        g[2][q] = cq[3] + cq[6] * x + cq[8] * y + T(2) * cq[9] * z;
     }
 }
 
@@ -327,36 +397,56 @@ __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
     for (int i = 0; i < 3; ++i) v[1 + i] = Rm[0][i] * a + Rm[1][i] * b + Rm[2][i] * c;
 }
 
-// 6 threads per face: 3 Gauss points x 2 sides (a lane pair per point)
+// Face flux with 6 threads per face: 3 Gauss points x 2 sides.  The two sides
+// of a Gauss point sit in different warps (warps 0-2 left, 3-5 right) so that
+// no warp diverges on the side; the interface equilibrium, its slopes and the
+// partial outputs are exchanged through shared memory:
+//   phase 1  own side: state at the point, face frame, slopes, rho <psi>+-
+//   phase 2  W^c, collision times; own kinetic part; rho <a_i psi>+-
+//   phase 3  equilibrium slopes; left warps add the C2 (a^c.u) flux terms,
+//            right warps the C1, C3 flux terms and the dW term
+//   phase 4  left warps finish the flux entries, right warps the gradient
+//            entries of the record; the 3 points of each face are summed.
+constexpr int FP_GP = 3 * FLUX_FACES;  // Gauss points per block (96)
+
 template <typename T, int NR>
-__global__ void __launch_bounds__(6 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> ph,
-                                                          const T* __restrict__ Wavg,
-                                                          const T* __restrict__ poly,
-                                                          T* __restrict__ rec,
-                                                          const double* __restrict__ ctrl,
-                                                          double dt_override) {
-    __shared__ T red[FLUX_FACES * 3 * NR];
+struct FluxSmem {
+    T w0[2][FP_GP][5];   // rho <psi>+- of each side
+    T p[2][FP_GP];       // pressure of each side
+    T dwc[2][FP_GP][15]; // rho <a_i psi>+- of each side
+    T out[2][FP_GP][20]; // partial Fh, D, W0, dW of each side
+    T red[FP_GP * NR];   // weighted record entries per Gauss point
+};
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(2 * FP_GP, 3) k_flux(DevMesh<T> m, Phys<T> ph,
+                                                     const T* __restrict__ Wavg,
+                                                     const T* __restrict__ poly,
+                                                     T* __restrict__ rec,
+                                                     const double* __restrict__ ctrl,
+                                                     double dt_override) {
+    __shared__ FluxSmem<T, NR> sm;
     const double dtd = dt_override > 0.0 ? dt_override : ctrl[CTRL_DT];
     if (!(dtd > 0.0)) return;  // no-op step (grid-uniform)
     const T dt = (T)dtd;
-    const int side = threadIdx.x & 1;
-    const int pt = threadIdx.x >> 1;  // Gauss point within the block
-    const int lf = pt / 3;
-    const int k = pt - 3 * lf;
+    const int side = threadIdx.x >= FP_GP ? 1 : 0;
+    const int g = threadIdx.x - side * FP_GP;  // Gauss point within the block
+    const int lf = g / 3;
+    const int k = g - 3 * lf;
     const int64_t f0 = (int64_t)blockIdx.x * FLUX_FACES + lf;
     const bool active = f0 < m.nf;
-    // inactive lanes of the last block compute a valid face and store nothing
-    // (the lane-pair shuffles need every lane of the warp)
-    const int64_t f = active ? f0 : m.nf - 1;
+    const int64_t f = active ? f0 : m.nf - 1;  // idle points compute a valid face, store nothing
     const int L = m.flr[f], Rc = m.flr[m.nf + f];
     const T* geo = m.fgeo + f * FGEO;
     const T n[3] = {geo[0], geo[1], geo[2]};
     const T w = geo[3];
-    const int mine_cell = side == 0 ? L : Rc;
+
+    // ---- phase 1 ----
+    const int mine = side == 0 ? L : Rc;
     T Ws[5], gs[3][5];
-    if (mine_cell >= 0) {
+    if (mine >= 0) {
         const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
-        eval_poly(poly + (int64_t)mine_cell * 50, X, Ws, gs);
+        eval_poly(poly + (int64_t)mine * POLY_STRIDE, X, Ws, gs);
     } else {
         // open boundary: the missing side is the interior cell's average with
         // zero gradient (zeroth-order extrapolation; the paper leaves outflow
@@ -373,54 +463,167 @@ __global__ void __launch_bounds__(6 * FLUX_FACES) k_flux(DevMesh<T> m, Phys<T> p
     face_frame(n, Rm);
     T tW[5], tg[3][5];
     to_local(Rm, Ws, gs, tW, tg);
+    const Prim<T> S = to_prim(tW, ph.gm1);
+    Tab<T> t;
+    T a[3][5], A[5];
+    kinetic_side(ph, S, tg, side == 0 ? +1 : -1, t, a, A);
+    T mw0[5] = {T(0), T(0), T(0), T(0), T(0)};
+    acc_psi<0, 0, 0>(t, S.rho, mw0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sm.w0[side][g][q] = mw0[q];
+    sm.p[side][g] = S.p;
+    __syncthreads();
+
+    // ---- phase 2 ----
+    T Wc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wc[q] = sm.w0[0][g][q] + sm.w0[1][g][q];
+    const Prim<T> C = to_prim(Wc, ph.gm1);
+    const TimeCoef<T> tc = time_coefs(ph, sm.p[0][g], sm.p[1][g], C.p, dt);
+    const T tau = tc.tau;
     T Fh[5], D[5], W0[5], dWt[5];
-    gks_point_pair(ph, side, tW, tg, dt, Fh, D, W0, dWt);
-    T* mine = red + (lf * 3 + k) * NR;
-    if (active) {
-        if (side == 0) {
-            to_global(Rm, Fh);
-            to_global(Rm, D);
-        } else {
-            to_global(Rm, W0);
-            to_global(Rm, dWt);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Fh[q] = D[q] = W0[q] = dWt[q] = T(0);
+    {
+        T dwc[3][5];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dwc[i][q] = T(0);
+            acc_apsi<0, 0, 0>(t, a[i], S.rho, dwc[i]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sm.dwc[side][g][5 * i + q] = dwc[i][q];
         }
-        if (NR == 40) {
+    }
+    if (!ph.smooth) {
+        T mf0[5] = {0}, mf1[5] = {0}, mw1[5] = {0};
+        acc_psi<1, 0, 0>(t, S.rho, mf0);
+        acc_grad<1>(t, a, S.rho, mf1);
+        acc_grad<0>(t, a, S.rho, mw1);
+        axpy5(tc.k0, mf0, Fh);
+        axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
+        axpy5(tc.dk0, mf0, D);
+        axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
+        axpy5(T(1), mw0, W0);
+        axpy5(-tau, mw1, W0);
+        axpy5(tau - (tau + dt) * tc.E, mw1, dWt);
+        if (ph.viscous) {
+            T mf2[5] = {0}, mw2[5] = {0};
+            acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
+            acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
+            axpy5(-tau * tc.k0, mf2, Fh);
+            axpy5(-tau * tc.dk0, mf2, D);
+            axpy5(-tau, mw2, W0);
+            axpy5(tau * (T(1) - tc.E), mw2, dWt);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3 ----
+    {
+        T dWc[3][5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (side == 0) {
-                    // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
-                    mine[q] = w * Fh[q];
-                    mine[5 + q] = w * (T(2) * Fh[q] - D[q] * T(1.0 / 3.0));
-                } else {
-                    const T ws = w * (W0[q] + T(0.5) * dWt[q]);  // f* = f^n + dt/2 f_t^n
-                    const T w0 = w * W0[q];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        mine[10 + 3 * q + i] = ws * n[i];
-                        mine[25 + 3 * q + i] = w0 * n[i];
-                    }
-                }
+            for (int q = 0; q < 5; ++q) dWc[i][q] = sm.dwc[0][g][5 * i + q] + sm.dwc[1][g][5 * i + q];
+        make_tab(t, C, ph.K, 0);
+        T ac[3][5], Ac[5];
+        state_slopes(C, t, ph.K, dWc, ac, Ac);
+        if (side == 0) {
+            T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
+            acc_grad<1>(t, ac, C.rho, mf1);
+            if (ph.smooth) {
+                axpy5(-tau * T(0.5) * dt, mf1, Fh);
+            } else {
+                axpy5(tc.q2, mf1, Fh);
+                axpy5(tc.dq2, mf1, D);
             }
         } else {
+            T mf0[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+            acc_psi<1, 0, 0>(t, C.rho, mf0);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
+            acc_grad<0>(t, ac, C.rho, mw1);  // rho <A^c psi> = -mw1 (Eq. co)
+            if (ph.smooth) {
+                const T hd = T(0.5) * dt;
+                axpy5(hd, mf0, Fh);
+                axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
+                axpy5(T(0.25) * dt * dt, mf2, D);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (side == 0) {
-                    mine[q] = w * T(4.0 / 3.0) * D[q];  // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
-                } else {
-                    const T dg = w * dWt[q];  // f^{n+1} = f^n + dt f_t^*
+                for (int q = 0; q < 5; ++q) W0[q] = Wc[q];  // tau terms cancel: <(a.u + A) psi> = 0
+                axpy5(-dt, mw1, dWt);
+            } else {
+                axpy5(tc.q1, mf0, Fh);
+                axpy5(tc.q3, mf2, Fh);
+                axpy5(tc.dq1, mf0, D);
+                axpy5(tc.dq3, mf2, D);
+                const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
+                axpy5(C2 - C3, mw1, dWt);
+            }
+        }
+    }
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) mine[5 + 3 * q + i] = dg * n[i];
+    for (int q = 0; q < 5; ++q) {
+        sm.out[side][g][q] = Fh[q];
+        sm.out[side][g][5 + q] = D[q];
+        sm.out[side][g][10 + q] = W0[q];
+        sm.out[side][g][15 + q] = dWt[q];
+    }
+    __syncthreads();
+
+    // ---- phase 4: left warps the flux entries, right warps the gradient entries
+    T* mine_rec = sm.red + g * NR;
+    if (side == 0) {
+        T Fs[5], Ds[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Fs[q] = sm.out[0][g][q] + sm.out[1][g][q];
+            Ds[q] = sm.out[0][g][5 + q] + sm.out[1][g][5 + q];
+        }
+        to_global(Rm, Fs);
+        to_global(Rm, Ds);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
+                // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
+                mine_rec[q] = w * Fs[q];
+                mine_rec[5 + q] = w * (T(2) * Fs[q] - Ds[q] * T(1.0 / 3.0));
+            } else {
+                mine_rec[q] = w * T(4.0 / 3.0) * Ds[q];  // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
+            }
+        }
+    } else {
+        T Zs[5], Ys[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Zs[q] = sm.out[0][g][10 + q] + sm.out[1][g][10 + q];
+            Ys[q] = sm.out[0][g][15 + q] + sm.out[1][g][15 + q];
+        }
+        to_global(Rm, Zs);
+        to_global(Rm, Ys);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
+                const T ws = w * (Zs[q] + T(0.5) * Ys[q]);  // f* = f^n + dt/2 f_t^n
+                const T w0 = w * Zs[q];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    mine_rec[10 + 3 * q + i] = ws * n[i];
+                    mine_rec[25 + 3 * q + i] = w0 * n[i];
                 }
+            } else {
+                const T dg = w * Ys[q];  // f^{n+1} = f^n + dt f_t^*
+#pragma unroll
+                for (int i = 0; i < 3; ++i) mine_rec[5 + 3 * q + i] = dg * n[i];
             }
         }
     }
     __syncthreads();
     // sum the three Gauss points of each face; coalesced record store
     const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
-    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 6 * FLUX_FACES) {
+    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 2 * FP_GP) {
         const int fl = idx / NR, j = idx - fl * NR;
         if (base + fl < m.nf) {
-            const T* r = red + fl * 3 * NR + j;
+            const T* r = sm.red + fl * 3 * NR + j;
             rec[(base + fl) * NR + j] = (r[0] + r[NR]) + r[2 * NR];
         }
     }
@@ -455,7 +658,7 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
             T (*g)[5] = side == 0 ? gL : gR;
             if (cell >= 0) {
                 const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
-                eval_poly(poly + (int64_t)cell * 50, X, Wv, g);
+                eval_poly(poly + (int64_t)cell * POLY_STRIDE, X, Wv, g);
             } else {
                 // open boundary: interior cell average, zero gradient
                 const int64_t in = side == 0 ? Rc : L;
@@ -547,11 +750,12 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState
     }
 }
 
-// deterministic block reduction of one min and five sums (warp shuffles,
-// then the 4 warp results in a fixed order)
-__device__ __forceinline__ void block_reduce_part(double mn, const double* sums, double* out) {
-    __shared__ double red[CELL_THREADS / 32][6];
-    double v[6] = {mn, sums[0], sums[1], sums[2], sums[3], sums[4]};
+// deterministic block reduction of one min and five sums in precision R
+// (warp shuffles, then the 4 warp results in a fixed order)
+template <typename R>
+__device__ __forceinline__ void block_reduce_part(R mn, const R* sums, double* out) {
+    __shared__ R red[CELL_THREADS / 32][6];
+    R v[6] = {mn, sums[0], sums[1], sums[2], sums[3], sums[4]};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         v[0] = fmin(v[0], __shfl_down_sync(0xffffffffu, v[0], o));
@@ -564,7 +768,7 @@ __device__ __forceinline__ void block_reduce_part(double mn, const double* sums,
         for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double r[6];
+        R r[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) r[k] = red[0][k];
         for (int w = 1; w < CELL_THREADS / 32; ++w) {
@@ -572,9 +776,9 @@ __device__ __forceinline__ void block_reduce_part(double mn, const double* sums,
 #pragma unroll
             for (int k = 1; k < 6; ++k) r[k] += red[w][k];
         }
-        out[PART_DTMIN] = r[0];
+        out[PART_DTMIN] = (double)r[0];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) out[PART_RES + q] = r[1 + q];
+        for (int q = 0; q < 5; ++q) out[PART_RES + q] = (double)r[1 + q];
     }
 }
 
@@ -585,8 +789,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     const CellLane cl = cell_lane(m.nc);
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
-    double mn = INFINITY;
-    double res[5] = {0, 0, 0, 0, 0};
+    T mn = T(INFINITY);
+    T res[5] = {T(0), T(0), T(0), T(0), T(0)};
     CSum<T> f2;
     f2.init();
     T dg[3] = {T(0), T(0), T(0)};
@@ -613,8 +817,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
         for (int i = 0; i < 3; ++i)
             st.dW[(3 * q + i) * nc + c] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
         // squared increments; the residual divides by dt^2 on the host
+        const T ti = (T)inc;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) res[k] = k == q ? inc * inc : 0.0;
+        for (int k = 0; k < 5; ++k) res[k] = k == q ? ti * ti : T(0);
     }
     // the cell's new state, gathered from its 5 lanes, for the positivity flag
     // and the next step's local time-step limit
@@ -624,9 +829,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     if (cl.active && q == 0) {
         const T pr = T(p.gamma - 1.0) * (Wn[4] - T(0.5) * (Wn[1] * Wn[1] + Wn[2] * Wn[2] + Wn[3] * Wn[3]) / Wn[0]);
         if (!(Wn[0] > T(0)) || !(pr > T(0))) atomicOr(st.err, ERR_STATE);
-        else mn = (double)local_dt(Wn, m.dr[c], p);
+        else mn = local_dt(Wn, m.dr[c], p);
     }
-    block_reduce_part(mn, res, st.part + (int64_t)blockIdx.x * PART_N);
+    block_reduce_part<T>(mn, res, st.part + (int64_t)blockIdx.x * PART_N);
     if (blockIdx.x == 0 && threadIdx.x == 0) st.ctrl[CTRL_T] += dtd;
 }
 
@@ -635,15 +840,15 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, Host
                                                                const T* __restrict__ W,
                                                                double* __restrict__ part) {
     const CellLane cl = cell_lane(m.nc);
-    double mn = INFINITY;
-    double zero[5] = {0, 0, 0, 0, 0};
+    T mn = T(INFINITY);
+    T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (cl.active && cl.q == 0) {
         T Wv[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + cl.c];
-        mn = (double)local_dt(Wv, m.dr[cl.c], p);
+        mn = local_dt(Wv, m.dr[cl.c], p);
     }
-    block_reduce_part(mn, zero, part + (int64_t)blockIdx.x * PART_N);
+    block_reduce_part<T>(mn, zero, part + (int64_t)blockIdx.x * PART_N);
 }
 
 __global__ void __launch_bounds__(CELL_THREADS) k_dt_finalize(const double* __restrict__ part, int nblk,
@@ -666,6 +871,12 @@ template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (B)in[i];
+}
+
+template <typename T>
+__global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, int64_t nc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 50; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[(i / 50) * POLY_STRIDE + i % 50];
 }
 
 // --------------------------------------------------------------------------
@@ -710,7 +921,7 @@ cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* W, T* slopes, const 
 
 template <typename T>
 cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
-                             const T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+                             T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
     ReconConst<T> rc;
@@ -728,12 +939,12 @@ cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, 
     if (m.nf == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
     const Phys<T> ph = make_phys<T>(p);
-    if (sizeof(T) == 4) {
-        // FP32: a lane pair per Gauss point
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the two sides of each Gauss point in separate warps
         if (stage == 1)
-            k_flux<T, 40><<<grid, 6 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            k_flux<T, 40><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
         else
-            k_flux<T, 20><<<grid, 6 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            k_flux<T, 20><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
     } else {
         if (stage == 1)
             k_flux_single<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
@@ -777,6 +988,14 @@ template <typename T>
 cudaError_t Launch<T>::from_double(const double* in, T* out, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_convert<double, T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    const int64_t n = nc * 50;
+    k_poly_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, nc);
     return cudaGetLastError();
 }
 

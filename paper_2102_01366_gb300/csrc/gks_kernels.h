@@ -18,6 +18,7 @@ constexpr int FLUX_FACES = 32;       // faces per flux block (3 threads each)
 constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
 constexpr int CELLS_PER_BLOCK = 24;  // 4 warps x 6 cells, 5 lanes per cell
 constexpr int FGEO = 24;             // reals per face geometry record
+constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record (50 used)
 
 template <typename T>
 struct DevMesh {
@@ -46,7 +47,7 @@ struct DevState {
     double* S;    // [5][nc] saved stage-1 flux term
     T* G;         // [15][nc] saved stage-1 gradient term
     T* slopes;    // [nc][15]
-    T* poly;      // [nc][50]
+    T* poly;      // [nc][POLY_STRIDE], 50 used
     T* rec;       // [nf][40]
     double* ctrl; // [CTRL_N]
     double* part; // [n_part_blocks][PART_N]
@@ -71,8 +72,10 @@ struct Launch {
     };
     static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
                               cudaStream_t s);
+    // slopes (may be NULL) receives the step-1 slopes, which the kernel
+    // computes itself (the neighbours' ones included)
     static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
-                             const T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+                             T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s);
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
                             const double* ctrl, double dt_override, int stage, cudaStream_t s);
@@ -84,6 +87,8 @@ struct Launch {
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
+    // padded reconstruction records [nc][POLY_STRIDE] -> compact FP64 [nc][50]
+    static cudaError_t poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s);
 };
 
 // Local time-step limit of one cell (Sec. 5, Eq. time-step, without C_CFL):
