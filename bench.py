@@ -41,8 +41,10 @@ WORKLOAD = "sod_tube_64x8x8_hex_x6_tets_24576_cells_weno3_cfl0.5"
 CPU_SAMPLE = dict(nx=16, nyz=4)  # same recipe, 1,536 cells: oracle per-cell cost is size independent
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # work of the dominant kernel (face flux) per Gauss point and stage, FP32 flop
-# (fadd + fmul + 2 ffma) counted by ncu on this workload (profiles/k_flux_fp32_*)
-FLUX_FLOPS_PER_GP = {"fp32": (6435.0, 5218.0)}
+# (fadd + fmul + 2 ffma) counted by ncu on this workload, and its DRAM bytes
+# per launch from the same capture (profiles/k_flux_fp32_sod24576.md)
+FLUX_FLOPS_PER_GP = {"fp32": (5016.0, 4913.0)}
+FLUX_DRAM_BYTES_PER_LAUNCH = 10.39e6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -299,7 +301,7 @@ def main():
         t_flux = (br["flux1"][0] + br["flux2"][0]) / max(1, br["flux1"][1])
         achieved = (fpg[0] + fpg[1]) * gps / (t_flux / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_flux<float>",
+                "frac": achieved / fp32_peak, "traffic": FLUX_DRAM_BYTES_PER_LAUNCH, "kernel": "k_flux<float>",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % clk_mhz,
                 "flux_ms_per_launch": flux_ms, "flux_share_of_step": sum(
                     br[k][0] for k in ("flux1", "flux2")) / total_ms}
