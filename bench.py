@@ -35,6 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2102_01366_gb300 import inputs as I  # noqa: E402
+from paper_2102_01366_gb300 import replicas  # noqa: E402
 
 METRIC = "Mcell-stage updates/s"
 WORKLOAD = "sod_tube_64x8x8_hex_x6_tets_24576_cells_weno3_cfl0.5"
@@ -113,23 +114,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
-def _barrier_max(torch, value, ws):
-    if ws == 1:
-        return value
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.barrier()
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
 def time_device(torch, s, steps, warmup, flush):
     """Per-step CUDA-event timing on the state's stream, L2 flushed between steps."""
     for _ in range(warmup):
@@ -179,7 +163,7 @@ def cpu_baseline(max_seconds=20.0, max_steps=40):
 
 
 def run_reference(args):
-    ws, rank, _ = _dist()
+    ws, rank, _ = replicas.world()
     if rank != 0:
         return
     from oracle import oracle as O
@@ -222,7 +206,7 @@ def main():
 
     import torch
     from paper_2102_01366_gb300 import _build, gks
-    ws, rank, local = _dist()
+    ws, rank, local = replicas.world()
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
@@ -257,7 +241,7 @@ def main():
             clocks = clk.summary()
         else:
             ms = time_device(torch, s, max(3, args.steps // 5), args.warmup, flush)
-        ms = _barrier_max(torch, ms, ws)
+        ms = replicas.max_over_ranks(ms)
         # kernel breakdown: same steps, kernel by kernel, events between launches
         s.init(W0, dW0)
         for _ in range(args.warmup):
@@ -281,7 +265,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         s.step_host(Wh, dWh, nsteps=1)
-    e2e_s = _barrier_max(torch, (time.perf_counter() - t0) / args.steps, ws)
+    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps)
 
     ms32 = results["fp32"]["ms"]
     value = ws * nc * 2 / (ms32 / 1000.0) / 1e6
