@@ -101,6 +101,23 @@ gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet
                            gks_mesh** out);
 void gks_mesh_destroy(gks_mesh* mesh);
 
+/* A batch of independent cases as one mesh (the disjoint union of their
+ * tetrahedra), each case with its own periods and its own time step and
+ * time (the time-step rule's minimum is taken per case).
+ *   tet_case[n_cell]  case id of each tetrahedron, ascending (cells grouped
+ *                     by case); NULL only when n_case == 1
+ *   period[n_case][3] periods of each case (NULL: none)
+ * Cells of different cases may not share a face (GKS_E_MESH).  Other
+ * arguments and the numbering rules as gks_mesh_create, which is the
+ * n_case = 1 case of this call. */
+gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_t* tet,
+                                 const int8_t* shift, int64_t n_cell, const int32_t* tet_case,
+                                 int32_t n_case, const double* period, gks_mesh** out);
+
+/* Number of cases and case_first_cell[n_case + 1] (first cell of each case
+ * and n_cell at the end; may be NULL). */
+gks_status gks_mesh_cases(const gks_mesh* mesh, int32_t* n_case, int64_t* case_first_cell);
+
 /* Counts: cells, faces, open boundary faces. Any output may be NULL. */
 gks_status gks_mesh_info(const gks_mesh* mesh, int64_t* n_cell, int64_t* n_face,
                          int64_t* n_boundary_face);
@@ -161,8 +178,9 @@ gks_status gks_init_state(gks_state* state, const double* d_W, const double* d_d
 
 /* Advances nsteps two-stage steps (Sec. 3).  dt_fixed > 0 fixes the step;
  * otherwise each step takes the time-step rule of Sec. 5 from the current
- * averages (a device-side reduction).  t_end > 0 clips the step so that the
- * time does not pass t_end (steps at t = t_end are no-ops).  The step
+ * averages (a device-side reduction, per case for a batch).  t_end > 0 clips
+ * each case's step so that its time does not pass t_end (steps of a case
+ * at t = t_end are no-ops).  The step
  * sequence is captured once into a CUDA graph per option set and replayed.
  * Returns after enqueueing; host outputs need gks_sync or gks_get_time. */
 gks_status gks_step(gks_state* state, int32_t nsteps, double dt_fixed, double t_end);
@@ -173,12 +191,17 @@ gks_status gks_sync(gks_state* state);
 /* Copies the current W, dW (FP64) to device arrays (either may be NULL). */
 gks_status gks_get_state(const gks_state* state, double* d_W, double* d_dW);
 
-/* Time and last step size (host values; synchronises). */
+/* Time and last step size of case 0 (host values; synchronises). */
 gks_status gks_get_time(gks_state* state, double* t, double* dt_last);
 
+/* Time and last step of every case, t[n_case] and dt_last[n_case] (host
+ * arrays, either may be NULL; synchronises). */
+gks_status gks_case_times(gks_state* state, double* t, double* dt_last);
+
 /* The same step through host buffers: copies h_W[5][nc], h_dW[15][nc] from
- * host memory (pinned for asynchronous copies), advances nsteps, and copies
- * the result to h_W_out, h_dW_out; synchronises.  In-place is allowed. */
+ * host memory (pinned for asynchronous copies), sets the time to 0 as
+ * gks_init_state does, advances nsteps, and copies the result to h_W_out,
+ * h_dW_out; synchronises.  In-place is allowed. */
 gks_status gks_step_host(gks_state* state, const double* h_W, const double* h_dW,
                          int32_t nsteps, double dt_fixed, double* h_W_out,
                          double* h_dW_out);

@@ -82,16 +82,16 @@ static gks_status check_params(const gks_params* p) {
 
 // ------------------------------------------------------------------ mesh --
 
-extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet,
-                                      const int8_t* shift, int64_t n_cell, const double* period,
-                                      gks_mesh** out) {
+extern "C" gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_t* tet,
+                                            const int8_t* shift, int64_t n_cell, const int32_t* tet_case,
+                                            int32_t n_case, const double* period, gks_mesh** out) {
     if (!out) { set_error("gks_mesh_create: out is NULL"); return GKS_E_ARG; }
     *out = nullptr;
-    if (!xyz || !tet || n_vert <= 0 || n_cell <= 0) {
-        set_error("gks_mesh_create: empty mesh or NULL arrays");
+    if (!xyz || !tet || n_vert <= 0 || n_cell <= 0 || n_case < 1 || (n_case > 1 && !tet_case)) {
+        set_error("gks_mesh_create: empty mesh, NULL arrays or bad case count");
         return GKS_E_ARG;
     }
-    if (n_cell >= ((int64_t)1 << 30) || n_vert >= ((int64_t)1 << 40)) {
+    if (n_cell >= ((int64_t)1 << 30) || n_vert >= ((int64_t)1 << 40) || n_case > (1 << 24)) {
         set_error("gks_mesh_create: mesh too large (cells and faces are indexed by int32)");
         return GKS_E_ARG;
     }
@@ -100,7 +100,31 @@ extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const i
     try {
         m->nv = n_vert;
         m->nc = n_cell;
-        for (int a = 0; a < 3; ++a) m->period[a] = period ? period[a] : 0.0;
+        m->ncase = n_case;
+        m->period.assign((size_t)n_case * 3, 0.0);
+        if (period) m->period.assign(period, period + (size_t)n_case * 3);
+        for (double v : m->period)
+            if (!(v >= 0.0)) {
+                set_error("gks_mesh_create: negative period");
+                delete m;
+                return GKS_E_ARG;
+            }
+        m->cell_case.assign((size_t)n_cell, 0);
+        if (tet_case) {
+            for (int64_t c = 0; c < n_cell; ++c) {
+                if (tet_case[c] < 0 || tet_case[c] >= n_case) {
+                    set_error("gks_mesh_create: case id out of range");
+                    delete m;
+                    return GKS_E_ARG;
+                }
+                if (c > 0 && tet_case[c] < tet_case[c - 1]) {
+                    set_error("gks_mesh_create: cells must be grouped by ascending case id");
+                    delete m;
+                    return GKS_E_ARG;
+                }
+                m->cell_case[c] = tet_case[c];
+            }
+        }
         m->xyz.assign(xyz, xyz + n_vert * 3);
         m->tet.assign(tet, tet + n_cell * 4);
         if (shift) m->shift.assign(shift, shift + n_cell * 12);
@@ -110,12 +134,6 @@ extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const i
                 set_error("gks_mesh_create: vertex id out of range");
                 delete m;
                 return GKS_E_MESH;
-            }
-        for (int a = 0; a < 3; ++a)
-            if (!(m->period[a] >= 0.0)) {
-                set_error("gks_mesh_create: negative period");
-                delete m;
-                return GKS_E_ARG;
             }
         gks_status st = build_mesh(*m);
         if (st != GKS_OK) { delete m; return st; }
@@ -133,6 +151,12 @@ extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const i
     return GKS_OK;
 }
 
+extern "C" gks_status gks_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet,
+                                      const int8_t* shift, int64_t n_cell, const double* period,
+                                      gks_mesh** out) {
+    return gks_mesh_create_cases(xyz, n_vert, tet, shift, n_cell, nullptr, 1, period, out);
+}
+
 extern "C" void gks_mesh_destroy(gks_mesh* mesh) { delete mesh; }
 
 extern "C" gks_status gks_mesh_info(const gks_mesh* m, int64_t* n_cell, int64_t* n_face,
@@ -141,6 +165,20 @@ extern "C" gks_status gks_mesh_info(const gks_mesh* m, int64_t* n_cell, int64_t*
     if (n_cell) *n_cell = m->nc;
     if (n_face) *n_face = m->nf;
     if (n_boundary_face) *n_boundary_face = m->nbf;
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_mesh_cases(const gks_mesh* m, int32_t* n_case, int64_t* case_first_cell) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    if (n_case) *n_case = m->ncase;
+    if (case_first_cell) {
+        int64_t c = 0;
+        for (int32_t k = 0; k < m->ncase; ++k) {
+            while (c < m->nc && m->cell_case[c] < k) ++c;
+            case_first_cell[k] = c;
+        }
+        case_first_cell[m->ncase] = m->nc;
+    }
     return GKS_OK;
 }
 
@@ -203,9 +241,9 @@ namespace {
 struct Layout {
     size_t total = 0;
     // mesh
-    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo;
+    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case;
     // state
-    size_t Wd, Wr, dW, Ws, dWs, S, G, slopes, poly, rec, ctrl, part, err, stage;
+    size_t Wd, Wr, dW, Ws, dWs, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -213,7 +251,7 @@ struct Layout {
     }
 };
 
-Layout layout_workspace(int64_t nc, int64_t nf, bool fp32) {
+Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     Layout L;
     const size_t T = fp32 ? 4 : 8;
     const size_t nblk = (size_t)update_blocks(nc);
@@ -229,6 +267,7 @@ Layout layout_workspace(int64_t nc, int64_t nf, bool fp32) {
     L.M2 = L.add(T * 144 * nc);
     L.flr = L.add(4 * 2 * nf);
     L.fgeo = L.add(T * FGEO * nf);
+    L.cell_case = L.add(4 * nc);
     L.Wd = L.add(8 * 5 * nc);
     L.Wr = fp32 ? L.add(T * 5 * nc) : L.Wd;
     L.dW = L.add(T * 15 * nc);
@@ -240,6 +279,9 @@ Layout layout_workspace(int64_t nc, int64_t nf, bool fp32) {
     L.poly = L.add(T * POLY_STRIDE * nc);
     L.rec = L.add(T * 40 * nf);
     L.ctrl = L.add(8 * CTRL_N);
+    L.case_t = L.add(8 * ncase);
+    L.case_dt = L.add(8 * ncase);
+    L.case_dtmin = L.add(8 * ncase);
     L.part = L.add(8 * PART_N * nblk);
     L.err = L.add(4);
     L.stage = L.add(8 * 15 * nc);
@@ -275,6 +317,8 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     const Layout& L = s->L;
     m.nc = s->mesh->nc;
     m.nf = s->mesh->nf;
+    m.ncase = s->mesh->ncase;
+    m.cell_case = at<int32_t>(s, L.cell_case);
     m.nbr = at<int32_t>(s, L.nbr);
     m.cface = at<int32_t>(s, L.cface);
     m.inv_vol = at<double>(s, L.inv_vol);
@@ -298,6 +342,9 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     st.poly = at<T>(s, L.poly);
     st.rec = at<T>(s, L.rec);
     st.ctrl = at<double>(s, L.ctrl);
+    st.case_t = at<double>(s, L.case_t);
+    st.case_dt = at<double>(s, L.case_dt);
+    st.case_dtmin = at<unsigned long long>(s, L.case_dtmin);
     st.part = at<double>(s, L.part);
     st.err = at<int32_t>(s, L.err);
 }
@@ -354,6 +401,7 @@ static gks_status upload_mesh(gks_state* s) {
     GKS_CHECK_CUDA(put(L.M2, M2.data(), sizeof(T) * M2.size()));
     GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
     GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
+    GKS_CHECK_CUDA(put(L.cell_case, g.cell_case.data(), 4 * g.cell_case.size()));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
@@ -362,7 +410,7 @@ static gks_status upload_mesh(gks_state* s) {
 
 extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
     if (!mesh || check_params(params) != GKS_OK) return 0;
-    return layout_workspace(mesh->nc, mesh->nf, params->precision == 1).total;
+    return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision == 1).total;
 }
 
 extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
@@ -375,7 +423,7 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     if (ps != GKS_OK) return ps;
     if (!mesh->has_stencils) { set_error("gks_state_create: stencils not built"); return GKS_E_STENCIL; }
     const bool fp32 = params->precision == 1;
-    Layout L = layout_workspace(mesh->nc, mesh->nf, fp32);
+    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32);
     if (!d_workspace || workspace_bytes < L.total) {
         set_error("gks_state_create: workspace missing or smaller than gks_workspace_bytes()");
         return GKS_E_NOMEM;
@@ -453,9 +501,9 @@ static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const 
         GKS_CHECK_CUDA(cudaMemcpyAsync(st.dW, d_dW, 8 * 15 * nc, cudaMemcpyDeviceToDevice, s->stream));
     else
         GKS_CHECK_CUDA(Launch<T>::from_double(d_dW, st.dW, 15 * nc, s->stream));
-    GKS_CHECK_CUDA(launch_set_control(st.ctrl, 0.0, 0.0, 1, s->stream));
+    GKS_CHECK_CUDA(launch_set_control(st.ctrl, st.case_t, st.case_dt, st.case_dtmin, m.ncase, 0.0, 0.0, 1, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, st.part, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.Wr, st.case_dtmin, s->stream));
     return GKS_OK;
 }
 
@@ -478,16 +526,24 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     const HostPhys& p = s->phys;
     cudaStream_t q = s->stream;
     const bool need_b = p.weno || p.order == 2;
-    const typename Launch<T>::Finalize fin{st.part, update_blocks(m.nc), p.cfl, st.ctrl};
+    const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
     cudaError_t e;
     // stage 1 from (W^n, grad W^n)
     if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, nullptr, st.poly, nullptr, &fin, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.ctrl, 0.0, 1, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.case_dt, 0.0, 1, q)) != cudaSuccess) return e;
     if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
     // stage 2 from (W*, grad W*)
     if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, nullptr, st.poly, nullptr, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.ctrl, 0.0, 2, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.case_dt, 0.0, 2, q)) != cudaSuccess) return e;
     return Launch<T>::update2(m, p, st, q);
+}
+
+static cudaError_t set_control(gks_state* s, double dt_fixed, double t_end, int reset) {
+    if (s->fp32)
+        return launch_set_control(s->s32.ctrl, s->s32.case_t, s->s32.case_dt, s->s32.case_dtmin, s->mesh->ncase,
+                                  dt_fixed, t_end, reset, s->stream);
+    return launch_set_control(s->s64.ctrl, s->s64.case_t, s->s64.case_dt, s->s64.case_dtmin, s->mesh->ncase,
+                              dt_fixed, t_end, reset, s->stream);
 }
 
 static gks_status build_graph(gks_state* s) {
@@ -519,8 +575,7 @@ extern "C" gks_status gks_step(gks_state* s, int32_t nsteps, double dt_fixed, do
         gks_status st = build_graph(s);
         if (st != GKS_OK) return st;
     }
-    double* ctrl = s->fp32 ? s->s32.ctrl : s->s64.ctrl;
-    GKS_CHECK_CUDA(launch_set_control(ctrl, dt_fixed, t_end, 0, s->stream));
+    GKS_CHECK_CUDA(set_control(s, dt_fixed, t_end, 0));
     for (int32_t i = 0; i < nsteps; ++i) GKS_CHECK_CUDA(cudaGraphLaunch(s->graph, s->stream));
     return GKS_OK;
 }
@@ -547,7 +602,7 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
         };
         cudaError_t e = cudaEventRecord(ev[ne], q);
         kid[ne++] = -1;
-        const typename Launch<T>::Finalize fin{st.part, update_blocks(m.nc), p.cfl, st.ctrl};
+        const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
         for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
             const T* W = stage == 1 ? st.Wr : st.Ws;
             const T* dW = stage == 1 ? st.dW : st.dWs;
@@ -555,7 +610,7 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             if (e == cudaSuccess)
                 e = Launch<T>::recon(m, p, W, dW, nullptr, st.poly, nullptr, fuse ? &fin : nullptr, q);
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
-            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.ctrl, 0.0, stage, q);
+            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.case_dt, 0.0, stage, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
             if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
@@ -586,8 +641,7 @@ extern "C" gks_status gks_step_timed(gks_state* s, int32_t nsteps, double dt_fix
     if (!s) { set_error("gks_step_timed: state is NULL"); return GKS_E_ARG; }
     if (!s->initialised) { set_error("gks_step_timed: state not initialised"); return GKS_E_STATE; }
     if (nsteps < 0) { set_error("gks_step_timed: negative nsteps"); return GKS_E_ARG; }
-    double* ctrl = s->fp32 ? s->s32.ctrl : s->s64.ctrl;
-    GKS_CHECK_CUDA(launch_set_control(ctrl, dt_fixed, t_end, 0, s->stream));
+    GKS_CHECK_CUDA(set_control(s, dt_fixed, t_end, 0));
     gks_status st = s->fp32 ? step_timed_impl<float>(s, s->m32, s->s32, nsteps, kernel_ms, launches)
                             : step_timed_impl<double>(s, s->m64, s->s64, nsteps, kernel_ms, launches);
     if (st != GKS_OK) return st;
@@ -628,13 +682,27 @@ extern "C" gks_status gks_get_state(const gks_state* cs, double* d_W, double* d_
     return GKS_OK;
 }
 
+extern "C" gks_status gks_case_times(gks_state* s, double* t, double* dt_last) {
+    if (!s) { set_error("gks_case_times: state is NULL"); return GKS_E_ARG; }
+    const size_t n = (size_t)s->mesh->ncase;
+    if (t)
+        GKS_CHECK_CUDA(cudaMemcpyAsync(t, s->fp32 ? s->s32.case_t : s->s64.case_t, 8 * n, cudaMemcpyDeviceToHost,
+                                       s->stream));
+    if (dt_last)
+        GKS_CHECK_CUDA(cudaMemcpyAsync(dt_last, s->fp32 ? s->s32.case_dt : s->s64.case_dt, 8 * n,
+                                       cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    return GKS_OK;
+}
+
 extern "C" gks_status gks_get_time(gks_state* s, double* t, double* dt_last) {
     if (!s) { set_error("gks_get_time: state is NULL"); return GKS_E_ARG; }
-    double c[CTRL_N];
-    GKS_CHECK_CUDA(cudaMemcpyAsync(c, s->fp32 ? s->s32.ctrl : s->s64.ctrl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    double c[2];
+    GKS_CHECK_CUDA(cudaMemcpyAsync(&c[0], s->fp32 ? s->s32.case_t : s->s64.case_t, 8, cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaMemcpyAsync(&c[1], s->fp32 ? s->s32.case_dt : s->s64.case_dt, 8, cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    if (t) *t = c[CTRL_T];
-    if (dt_last) *dt_last = c[CTRL_DT];
+    if (t) *t = c[0];
+    if (dt_last) *dt_last = c[1];
     return GKS_OK;
 }
 
@@ -652,7 +720,8 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
         GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
         GKS_CHECK_CUDA(Launch<T>::from_double(stage, st.dW, 15 * nc, s->stream));
     }
-    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, st.part, s->stream));
+    GKS_CHECK_CUDA(set_control(s, 0.0, 0.0, 1));
+    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.Wr, st.case_dtmin, s->stream));
     s->initialised = true;
     gks_status r = gks_step(s, nsteps, dt_fixed, 0.0);
     if (r != GKS_OK) return r;
@@ -703,13 +772,10 @@ extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
     GKS_CHECK_CUDA(cudaMemcpyAsync(part.data(), s->fp32 ? s->s32.part : s->s64.part, 8 * part.size(),
                                    cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    double ctrl[CTRL_N];
-    GKS_CHECK_CUDA(cudaMemcpy(ctrl, s->fp32 ? s->s32.ctrl : s->s64.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
-    const double dt = ctrl[CTRL_DT];
     for (int q = 0; q < 5; ++q) {
         double acc = 0.0;
         for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * PART_N + PART_RES + q];
-        out_l2[q] = dt > 0.0 ? std::sqrt(acc / (double)s->mesh->nc) / dt : 0.0;
+        out_l2[q] = std::sqrt(acc / (double)s->mesh->nc);
     }
     return GKS_OK;
 }
@@ -746,7 +812,7 @@ static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, d
                                  double* d_rec) {
     gks_status r = debug_recon_impl<T>(s, m, st, nullptr, nullptr, nullptr);
     if (r != GKS_OK) return r;
-    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, st.ctrl, dt, stage, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, nullptr, dt, stage, s->stream));
     GKS_CHECK_CUDA(Launch<T>::to_double(st.rec, d_rec, (stage == 1 ? 40 : 20) * m.nf, s->stream));
     return GKS_OK;
 }

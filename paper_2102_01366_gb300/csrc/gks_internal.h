@@ -11,7 +11,10 @@
 
 struct gks_mesh {
     int64_t nv = 0, nc = 0, nf = 0, nbf = 0;
-    double period[3] = {0, 0, 0};
+    int32_t ncase = 1;
+    std::vector<double> period;    // ncase*3, 0 on a non-periodic axis
+    std::vector<int32_t> cell_case;  // nc (all 0 for one case)
+    const double* per(int64_t c) const { return &period[(size_t)cell_case[c] * 3]; }
     std::vector<double> xyz;      // nv*3
     std::vector<int64_t> tet;     // nc*4
     std::vector<int8_t> shift;    // nc*12

@@ -33,43 +33,73 @@ struct ReconConst {
 // cell kernels: 5 lanes per cell (one per conservative component), 6 cells
 // per warp (lanes 30, 31 idle), CELLS_PER_BLOCK cells per 128-thread block
 // --------------------------------------------------------------------------
-// Global minimum of the per-block minima and the step's dt (run by one
-// whole block; deterministic).  Applies dt_fixed and t_end clipping.
-__device__ void finalize_dt_block(const double* __restrict__ part, int nblk, double cfl,
-                                  double* __restrict__ ctrl) {
-    __shared__ double smin[CELL_THREADS];
-    double mn = INFINITY;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) mn = fmin(mn, part[(int64_t)b * PART_N]);
-    smin[threadIdx.x] = mn;
-    __syncthreads();
-    for (int s = CELL_THREADS / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double dt = ctrl[CTRL_DT_FIXED] > 0.0 ? ctrl[CTRL_DT_FIXED] : cfl * smin[0];
-        const double t_end = ctrl[CTRL_T_END];
+// The step of every case from its minimum local limit (time-step rule of
+// Sec. 5), with dt_fixed and t_end clipping; advances the case times and
+// resets the minima for the next update.  One thread per case.
+__device__ void finalize_cases(unsigned long long* __restrict__ dtmin, double* __restrict__ case_t,
+                               double* __restrict__ case_dt, int32_t ncase, double cfl,
+                               const double* __restrict__ ctrl) {
+    const double dt_fixed = ctrl[CTRL_DT_FIXED], t_end = ctrl[CTRL_T_END];
+    for (int k = threadIdx.x; k < ncase; k += blockDim.x) {
+        const double mn = __longlong_as_double((long long)dtmin[k]);
+        double dt = dt_fixed > 0.0 ? dt_fixed : (mn < INFINITY ? cfl * mn : 0.0);
+        double t = case_t[k];
         if (t_end > 0.0) {
-            const double rem = t_end - ctrl[CTRL_T];
+            const double rem = t_end - t;
             if (rem <= 1e-12 * t_end) {
                 dt = 0.0;
-                if (rem > 0.0) ctrl[CTRL_T] = t_end;
+                if (rem > 0.0) t = t_end;
             } else if (dt > rem) {
                 dt = rem;
             }
         }
         if (!(dt > 0.0)) dt = 0.0;
-        ctrl[CTRL_DT] = dt;
+        case_dt[k] = dt;
+        case_t[k] = t + dt;
+        dtmin[k] = (unsigned long long)__double_as_longlong(INFINITY);
     }
 }
 
 template <typename T>
 struct FinArg {
-    const double* part;
-    int nblk;
+    unsigned long long* dtmin;
+    double* case_t;
+    double* case_dt;
+    int32_t ncase;
     double cfl;
-    double* ctrl;
+    const double* ctrl;
 };
+
+// per-case minimum of the local limits of the cells of a block: the block's
+// cells are contiguous and so are the cases, so its cases form runs; one
+// thread scans the 24 values and issues one atomicMin per run (the minimum
+// is exact, so the result does not depend on the order)
+__device__ void block_case_min(double v, int32_t cas, bool valid, int lc, unsigned long long* dtmin) {
+    __shared__ double sv[CELLS_PER_BLOCK];
+    __shared__ int32_t sc[CELLS_PER_BLOCK];
+    if (threadIdx.x < CELLS_PER_BLOCK) sc[threadIdx.x] = -1;
+    __syncthreads();
+    if (valid) {
+        sv[lc] = v;
+        sc[lc] = cas;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t cur = -1;
+        double mn = INFINITY;
+        for (int i = 0; i < CELLS_PER_BLOCK; ++i) {
+            if (sc[i] < 0) continue;
+            if (sc[i] != cur) {
+                if (cur >= 0 && mn < INFINITY)
+                    atomicMin(dtmin + cur, (unsigned long long)__double_as_longlong(mn));
+                cur = sc[i];
+                mn = INFINITY;
+            }
+            mn = fmin(mn, sv[i]);
+        }
+        if (cur >= 0 && mn < INFINITY) atomicMin(dtmin + cur, (unsigned long long)__double_as_longlong(mn));
+    }
+}
 
 struct CellLane {
     int64_t c;    // cell (clamped to a valid cell on idle lanes)
@@ -95,7 +125,7 @@ __device__ __forceinline__ CellLane cell_lane(int64_t nc) {
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ W,
                                                           T* __restrict__ slopes, FinArg<T> fin) {
-    if (fin.part && blockIdx.x == 0) finalize_dt_block(fin.part, fin.nblk, fin.cfl, fin.ctrl);
+    if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
     const CellLane cl = cell_lane(m.nc);
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
@@ -150,7 +180,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
                                                          FinArg<T> fin) {
     __shared__ T sM2[144][CELLS_PER_BLOCK];
     __shared__ T sG[36][CELLS_PER_BLOCK];
-    if (fin.part && blockIdx.x == 0) finalize_dt_block(fin.part, fin.nblk, fin.cfl, fin.ctrl);
+    if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
     const int64_t nc = m.nc;
     {
         const int64_t cbase = (int64_t)blockIdx.x * CELLS_PER_BLOCK;
@@ -426,9 +456,6 @@ __global__ void __launch_bounds__(2 * FP_GP, 3) k_flux(DevMesh<T> m, Phys<T> ph,
                                                      const double* __restrict__ ctrl,
                                                      double dt_override) {
     __shared__ FluxSmem<T, NR> sm;
-    const double dtd = dt_override > 0.0 ? dt_override : ctrl[CTRL_DT];
-    if (!(dtd > 0.0)) return;  // no-op step (grid-uniform)
-    const T dt = (T)dtd;
     const int side = threadIdx.x >= FP_GP ? 1 : 0;
     const int g = threadIdx.x - side * FP_GP;  // Gauss point within the block
     const int lf = g / 3;
@@ -437,6 +464,10 @@ __global__ void __launch_bounds__(2 * FP_GP, 3) k_flux(DevMesh<T> m, Phys<T> ph,
     const bool active = f0 < m.nf;
     const int64_t f = active ? f0 : m.nf - 1;  // idle points compute a valid face, store nothing
     const int L = m.flr[f], Rc = m.flr[m.nf + f];
+    // the face's case step; a finished case (dt = 0) computes with a dummy
+    // step and its cells ignore the record
+    const double dtc = ctrl ? ctrl[m.cell_case[L >= 0 ? L : Rc]] : dt_override;
+    const T dt = dtc > 0.0 ? (T)dtc : T(1);
     const T* geo = m.fgeo + f * FGEO;
     const T n[3] = {geo[0], geo[1], geo[2]};
     const T w = geo[3];
@@ -639,15 +670,14 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
                                                                  const double* __restrict__ ctrl,
                                                                  double dt_override) {
     __shared__ T red[FLUX_FACES * 3 * NR];
-    const double dtd = dt_override > 0.0 ? dt_override : ctrl[CTRL_DT];
-    if (!(dtd > 0.0)) return;
-    const T dt = (T)dtd;
     const int lf = threadIdx.x / 3;
     const int k = threadIdx.x - 3 * lf;
     const int64_t f = (int64_t)blockIdx.x * FLUX_FACES + lf;
     T* mine = red + (lf * 3 + k) * NR;
     if (f < m.nf) {
         const int L = m.flr[f], Rc = m.flr[m.nf + f];
+        const double dtc = ctrl ? ctrl[m.cell_case[L >= 0 ? L : Rc]] : dt_override;
+        const T dt = dtc > 0.0 ? (T)dtc : T(1);
         const T* geo = m.fgeo + f * FGEO;
         const T n[3] = {geo[0], geo[1], geo[2]};
         const T w = geo[3];
@@ -715,11 +745,10 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState<T> st) {
-    const double dtd = st.ctrl[CTRL_DT];
-    if (!(dtd > 0.0)) return;
     const CellLane cl = cell_lane(m.nc);
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
+    if (!(st.case_dt[m.cell_case[c]] > 0.0)) return;  // finished case
     const int q = cl.q;
     CSum<T> fh, s1;
     fh.init();
@@ -784,11 +813,12 @@ __device__ __forceinline__ void block_reduce_part(R mn, const R* sums, double* o
 
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys p, DevState<T> st) {
-    const double dtd = st.ctrl[CTRL_DT];
-    if (!(dtd > 0.0)) return;
     const CellLane cl = cell_lane(m.nc);
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
+    const int32_t cas = m.cell_case[c];
+    const double dtd = st.case_dt[cas];
+    const bool live = cl.active && dtd > 0.0;  // finished cases keep their state
     T mn = T(INFINITY);
     T res[5] = {T(0), T(0), T(0), T(0), T(0)};
     CSum<T> f2;
@@ -806,18 +836,18 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     const double iv = m.inv_vol[c];
     // W^{n+1} |Omega| = W^n |Omega| - [dt F + dt^2/6 F_t](W^n) - [dt^2/3 F_t](W*)
     // (Eq. s2o4, second stage)
-    const double inc = ((st.S[q * nc + c] + (double)f2.hi) + (double)f2.lo) * iv;
+    const double inc = live ? ((st.S[q * nc + c] + (double)f2.hi) + (double)f2.lo) * iv : 0.0;
     const double wn = st.Wd[q * nc + c] - inc;
     const T Wq = (T)wn;
-    if (cl.active) {
+    if (live) {
         st.Wd[q * nc + c] = wn;
         if ((void*)st.Wr != (void*)st.Wd) st.Wr[q * nc + c] = Wq;
         const T ivr = (T)iv;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
             st.dW[(3 * q + i) * nc + c] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
-        // squared increments; the residual divides by dt^2 on the host
-        const T ti = (T)inc;
+        // squared rates of change (W^{n+1} - W^n) / dt for the residual
+        const T ti = (T)inc / (T)dtd;
 #pragma unroll
         for (int k = 0; k < 5; ++k) res[k] = k == q ? ti * ti : T(0);
     }
@@ -826,13 +856,16 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     T Wn[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) Wn[k] = __shfl_sync(0xffffffffu, Wq, cl.base + k);
-    if (cl.active && q == 0) {
+    const bool lead = cl.active && q == 0;
+    if (lead) {
         const T pr = T(p.gamma - 1.0) * (Wn[4] - T(0.5) * (Wn[1] * Wn[1] + Wn[2] * Wn[2] + Wn[3] * Wn[3]) / Wn[0]);
         if (!(Wn[0] > T(0)) || !(pr > T(0))) atomicOr(st.err, ERR_STATE);
         else mn = local_dt(Wn, m.dr[c], p);
     }
-    block_reduce_part<T>(mn, res, st.part + (int64_t)blockIdx.x * PART_N);
-    if (blockIdx.x == 0 && threadIdx.x == 0) st.ctrl[CTRL_T] += dtd;
+    const int lc = (int)(c - (int64_t)blockIdx.x * CELLS_PER_BLOCK);
+    block_case_min((double)mn, cas, lead && lc >= 0 && lc < CELLS_PER_BLOCK && mn < T(INFINITY), lc, st.case_dtmin);
+    T mn_unused = T(INFINITY);
+    block_reduce_part<T>(mn_unused, res, st.part + (int64_t)blockIdx.x * PART_N);
 }
 
 template <typename T>
@@ -851,20 +884,34 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, Host
     block_reduce_part<T>(mn, zero, part + (int64_t)blockIdx.x * PART_N);
 }
 
-__global__ void __launch_bounds__(CELL_THREADS) k_dt_finalize(const double* __restrict__ part, int nblk,
-                                                                double cfl, double* __restrict__ ctrl) {
-    finalize_dt_block(part, nblk, cfl, ctrl);
+template <typename T>
+__global__ void __launch_bounds__(CELL_THREADS) k_init_dtmin(DevMesh<T> m, HostPhys p, const T* __restrict__ W,
+                                                              unsigned long long* __restrict__ dtmin) {
+    const CellLane cl = cell_lane(m.nc);
+    const bool lead = cl.active && cl.q == 0;
+    double mn = INFINITY;
+    if (lead) {
+        T Wv[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + cl.c];
+        mn = (double)local_dt(Wv, m.dr[cl.c], p);
+    }
+    const int lc = (int)(cl.c - (int64_t)blockIdx.x * CELLS_PER_BLOCK);
+    block_case_min(mn, m.cell_case[cl.c], lead && lc >= 0 && lc < CELLS_PER_BLOCK && mn < INFINITY, lc, dtmin);
 }
 
-__global__ void k_set_control(double* ctrl, double dt_fixed, double t_end, int reset) {
-    if (threadIdx.x == 0) {
+__global__ void k_set_control(double* ctrl, double* case_t, double* case_dt, unsigned long long* dtmin,
+                              int32_t ncase, double dt_fixed, double t_end, int reset) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
         ctrl[CTRL_DT_FIXED] = dt_fixed;
         ctrl[CTRL_T_END] = t_end;
-        if (reset) {
-            ctrl[CTRL_T] = 0.0;
-            ctrl[CTRL_DT] = 0.0;
-        }
     }
+    if (reset)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncase; k += gridDim.x * blockDim.x) {
+            case_t[k] = 0.0;
+            case_dt[k] = 0.0;
+            dtmin[k] = (unsigned long long)__double_as_longlong(INFINITY);
+        }
 }
 
 template <typename A, typename B>
@@ -904,8 +951,10 @@ static Phys<T> make_phys(const HostPhys& p) {
 template <typename T>
 static FinArg<T> fin_arg(const typename Launch<T>::Finalize* fin) {
     FinArg<T> a;
-    a.part = fin ? fin->part : nullptr;
-    a.nblk = fin ? fin->nblk : 0;
+    a.dtmin = fin ? fin->dtmin : nullptr;
+    a.case_t = fin ? fin->case_t : nullptr;
+    a.case_dt = fin ? fin->case_dt : nullptr;
+    a.ncase = fin ? fin->ncase : 0;
     a.cfl = fin ? fin->cfl : 0.0;
     a.ctrl = fin ? fin->ctrl : nullptr;
     return a;
@@ -936,6 +985,7 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W,
 template <typename T>
 cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
                             const double* ctrl, double dt_override, int stage, cudaStream_t s) {
+    // ctrl is the per-case step array (NULL: dt_override everywhere)
     if (m.nf == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
     const Phys<T> ph = make_phys<T>(p);
@@ -978,6 +1028,14 @@ cudaError_t Launch<T>::dt_partials(const DevMesh<T>& m, const HostPhys& p, const
 }
 
 template <typename T>
+cudaError_t Launch<T>::init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* W,
+                                  unsigned long long* case_dtmin, cudaStream_t s) {
+    if (m.nc == 0) return cudaSuccess;
+    k_init_dtmin<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, W, case_dtmin);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::to_double(const T* in, double* out, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_convert<T, double><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, n);
@@ -999,14 +1057,11 @@ cudaError_t Launch<T>::poly_to_double(const T* in, double* out, int64_t nc, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_dt_finalize(const double* part, int nblk, double cfl, double* ctrl, cudaStream_t s) {
-    k_dt_finalize<<<1, CELL_THREADS, 0, s>>>(part, nblk, cfl, ctrl);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_set_control(double* ctrl, double dt_fixed, double t_end, int reset_time,
-                               cudaStream_t s) {
-    k_set_control<<<1, 32, 0, s>>>(ctrl, dt_fixed, t_end, reset_time);
+cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt, unsigned long long* case_dtmin,
+                               int32_t ncase, double dt_fixed, double t_end, int reset_time, cudaStream_t s) {
+    const int grid = reset_time ? (int)((ncase + 255) / 256 < 1024 ? (ncase + 255) / 256 : 1024) : 1;
+    k_set_control<<<grid < 1 ? 1 : grid, 256, 0, s>>>(ctrl, case_t, case_dt, case_dtmin, ncase, dt_fixed,
+                                                      t_end, reset_time);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record (50
 template <typename T>
 struct DevMesh {
     int64_t nc, nf;
+    int32_t ncase;
+    const int32_t* cell_case;  // [nc] case of each cell (ascending)
     const int32_t* nbr;    // [4][nc], -1 = none
     const int32_t* cface;  // [4][nc] face * 2 + side (side 1 = right)
     const double* inv_vol; // [nc]
@@ -49,8 +51,11 @@ struct DevState {
     T* slopes;    // [nc][15]
     T* poly;      // [nc][POLY_STRIDE], 50 used
     T* rec;       // [nf][40]
-    double* ctrl; // [CTRL_N]
-    double* part; // [n_part_blocks][PART_N]
+    double* ctrl; // [CTRL_N] global controls (dt_fixed, t_end)
+    double* case_t;   // [ncase] time of each case
+    double* case_dt;  // [ncase] step of each case for the current step
+    unsigned long long* case_dtmin;  // [ncase] bits of the minimum local dt (atomicMin)
+    double* part; // [n_part_blocks][PART_N] residual sums per block
     int32_t* err;
 };
 
@@ -65,10 +70,12 @@ struct Launch {
     // fin (may be NULL): block 0 first turns the per-block minima into the
     // step's dt (the time-step rule's global minimum, t_end clipping)
     struct Finalize {
-        const double* part;
-        int nblk;
+        unsigned long long* dtmin;
+        double* case_t;
+        double* case_dt;
+        int32_t ncase;
         double cfl;
-        double* ctrl;
+        const double* ctrl;
     };
     static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
                               cudaStream_t s);
@@ -77,13 +84,17 @@ struct Launch {
     static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
                              T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s);
+    // case_dt: per-case step (NULL: dt_override for every face)
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
-                            const double* ctrl, double dt_override, int stage, cudaStream_t s);
+                            const double* case_dt, double dt_override, int stage, cudaStream_t s);
     static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
     static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,
                                cudaStream_t s);
     static cudaError_t dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* W,
                                    double* part, cudaStream_t s);
+    // per-case minima of the local limits of W into case_dtmin (reset first)
+    static cudaError_t init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* W,
+                                  unsigned long long* case_dtmin, cudaStream_t s);
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
@@ -111,10 +122,11 @@ __device__ __forceinline__ T local_dt(const T* Wv, T dr, const HostPhys& p) {
 }
 #endif
 
-cudaError_t launch_dt_finalize(const double* part, int nblk, double cfl, double* ctrl,
-                               cudaStream_t s);
-cudaError_t launch_set_control(double* ctrl, double dt_fixed, double t_end, int reset_time,
-                               cudaStream_t s);
+// sets dt_fixed and t_end; with reset_time also zeroes the case times and
+// steps and sets the case minima to +inf
+cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt,
+                               unsigned long long* case_dtmin, int32_t ncase, double dt_fixed,
+                               double t_end, int reset_time, cudaStream_t s);
 int update_blocks(int64_t nc);
 
 }  // namespace gks

@@ -77,7 +77,6 @@ inline void vsub(const double* a, const double* b, double* c) {
 
 gks_status build_mesh(gks_mesh& m) {
     const int64_t nc = m.nc;
-    const double* P = m.period;
     // ---- match faces -------------------------------------------------
     std::unordered_map<FaceKey, int64_t, FaceKeyHash> index;
     index.reserve((size_t)(nc * 3));
@@ -147,6 +146,11 @@ gks_status build_mesh(gks_mesh& m) {
                                       {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}};
     for (int64_t fi = 0; fi < nf; ++fi) {
         const FaceEntry& e = faces[(size_t)fi];
+        const double* P = m.per(e.side[0].cell);
+        if (e.count == 2 && m.cell_case[e.side[1].cell] != m.cell_case[e.side[0].cell]) {
+            set_error("gks_mesh_create: cells of different cases share a face");
+            return GKS_E_MESH;
+        }
         double x[3][3];
         for (int a = 0; a < 3; ++a) {
             x[0][a] = m.xyz[e.key.v[0] * 3 + a];
@@ -224,6 +228,7 @@ gks_status build_mesh(gks_mesh& m) {
     m.mom2.assign((size_t)nc * 6, 0.0);
     m.dr.assign((size_t)nc, 0.0);
     for (int64_t c = 0; c < nc; ++c) {
+        const double* P = m.per(c);
         double x[4][3];
         for (int v = 0; v < 4; ++v) {
             int64_t id = m.tet[c * 4 + v];
@@ -262,6 +267,7 @@ gks_status build_mesh(gks_mesh& m) {
         for (int lr = 0; lr < 2; ++lr) {
             int64_t c = m.face_lr[fi * 2 + lr];
             if (c < 0) continue;
+            const double* P = m.per(c);
             double* out = lr == 0 ? &m.gp_l[fi * 9] : &m.gp_r[fi * 9];
             for (int k = 0; k < 3; ++k)
                 for (int a = 0; a < 3; ++a)

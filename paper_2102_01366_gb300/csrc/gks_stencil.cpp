@@ -13,8 +13,10 @@
 // projected gradient rows (a second QR).  Unknowns are scaled by powers of
 // h0 = |Omega|^(1/3) and gradient rows by h0 so that both QRs work on O(1)
 // entries; the result is unscaled before it is stored.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "gks_internal.h"
 
@@ -101,7 +103,7 @@ bool cell_stencil(const gks_mesh& m, int64_t c, double* M1, double* M2) {
         int64_t nb = m.nbr[c * 4 + f];
         if (nb < 0) continue;
         for (int a = 0; a < 3; ++a)
-            d[nn][a] = (m.cen[nb * 3 + a] + (double)m.nbr_img[(c * 4 + f) * 3 + a] * m.period[a]) -
+            d[nn][a] = (m.cen[nb * 3 + a] + (double)m.nbr_img[(c * 4 + f) * 3 + a] * m.per(c)[a]) -
                        m.cen[c * 3 + a];
         fl[nn++] = f;
     }
@@ -216,15 +218,26 @@ gks_status build_stencils(gks_mesh& m) {
     m.M1.assign((size_t)m.nc * 12, 0.0);
     m.M2.assign((size_t)m.nc * 144, 0.0);
     m.singular.assign((size_t)m.nc, 0);
-    m.n_singular = 0;
-    for (int64_t c = 0; c < m.nc; ++c) {
-        if (!cell_stencil(m, c, &m.M1[c * 12], &m.M2[c * 144])) {
-            m.singular[c] = 1;
-            ++m.n_singular;
-            std::memset(&m.M1[c * 12], 0, sizeof(double) * 12);
-            std::memset(&m.M2[c * 144], 0, sizeof(double) * 144);
+    // independent per cell: split the cells over the host's hardware threads
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nthr = std::min<int64_t>((int64_t)hw, std::max<int64_t>(1, m.nc / 4096));
+    auto work = [&](int64_t lo, int64_t hi) {
+        for (int64_t c = lo; c < hi; ++c) {
+            if (!cell_stencil(m, c, &m.M1[c * 12], &m.M2[c * 144])) {
+                m.singular[c] = 1;
+                std::memset(&m.M1[c * 12], 0, sizeof(double) * 12);
+                std::memset(&m.M2[c * 144], 0, sizeof(double) * 144);
+            }
         }
-    }
+    };
+    std::vector<std::thread> pool;
+    const int64_t chunk = (m.nc + nthr - 1) / nthr;
+    for (int64_t t = 1; t < nthr; ++t)
+        pool.emplace_back(work, std::min(m.nc, t * chunk), std::min(m.nc, (t + 1) * chunk));
+    work(0, std::min(m.nc, chunk));
+    for (auto& th : pool) th.join();
+    m.n_singular = 0;
+    for (int64_t c = 0; c < m.nc; ++c) m.n_singular += m.singular[c];
     m.has_stencils = true;
     return GKS_OK;
 }

@@ -59,6 +59,10 @@ def lib():
         "gks_params_default": (None, [C.POINTER(gks_params)]),
         "gks_last_error": (C.c_char_p, []),
         "gks_mesh_create": (C.c_int32, [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.POINTER(_vp)]),
+        "gks_mesh_create_cases": (C.c_int32, [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp,
+                                              C.POINTER(_vp)]),
+        "gks_mesh_cases": (C.c_int32, [_vp, C.POINTER(C.c_int32), _vp]),
+        "gks_case_times": (C.c_int32, [_vp, _vp, _vp]),
         "gks_mesh_destroy": (None, [_vp]),
         "gks_mesh_info": (C.c_int32, [_vp, _i64p, _i64p, _i64p]),
         "gks_mesh_topology": (C.c_int32, [_vp] * 6),
@@ -118,11 +122,21 @@ class Mesh:
         tet = np.ascontiguousarray(mesh["tet"], dtype=np.int64)
         shift = np.ascontiguousarray(mesh["shift"], dtype=np.int8)
         period = np.ascontiguousarray(mesh["period"], dtype=np.float64)
-        _call("gks_mesh_create", _np_ptr(xyz), xyz.shape[0], _np_ptr(tet), _np_ptr(shift),
-              tet.shape[0], _np_ptr(period), C.byref(self._h))
+        if "case" in mesh:
+            case = np.ascontiguousarray(mesh["case"], dtype=np.int32)
+            _call("gks_mesh_create_cases", _np_ptr(xyz), xyz.shape[0], _np_ptr(tet), _np_ptr(shift),
+                  tet.shape[0], _np_ptr(case), int(mesh["ncase"]), _np_ptr(period), C.byref(self._h))
+        else:
+            _call("gks_mesh_create", _np_ptr(xyz), xyz.shape[0], _np_ptr(tet), _np_ptr(shift),
+                  tet.shape[0], _np_ptr(period), C.byref(self._h))
         nc, nf, nb = C.c_int64(), C.c_int64(), C.c_int64()
         _call("gks_mesh_info", self._h, C.byref(nc), C.byref(nf), C.byref(nb))
         self.nc, self.nf, self.n_boundary = nc.value, nf.value, nb.value
+        ncase = C.c_int32()
+        _call("gks_mesh_cases", self._h, C.byref(ncase), None)
+        self.ncase = ncase.value
+        self.case_first = np.zeros(self.ncase + 1, np.int64)
+        _call("gks_mesh_cases", self._h, C.byref(ncase), _np_ptr(self.case_first))
         self.n_singular = None
         if build_stencils:
             ns = C.c_int64()
@@ -235,6 +249,13 @@ class State:
         _call("gks_step_timed", self._h, int(nsteps), float(dt_fixed), float(t_end), _np_ptr(ms), _np_ptr(cnt))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNELS)}
 
+    def case_times(self):
+        """(t[ncase], dt_last[ncase]) of every case."""
+        t = np.zeros(self.mesh.ncase)
+        dt = np.zeros(self.mesh.ncase)
+        _call("gks_case_times", self._h, _np_ptr(t), _np_ptr(dt))
+        return t, dt
+
     def timestep(self):
         dt = C.c_double()
         _call("gks_timestep", self._h, C.byref(dt))
@@ -262,9 +283,9 @@ class State:
         while True:
             self.step(chunk, dt_fixed, t_end)
             self.sync()
-            tt, dt = self.time()
-            if tt >= t_end * (1 - 1e-14) or dt <= 0.0:
-                return tt
+            tt, dt = self.case_times()
+            if (tt >= t_end * (1 - 1e-14)).all() or (dt <= 0.0).all():
+                return float(tt.min())
 
     # -- diagnostics ----------------------------------------------------------
     def debug_reconstruct(self):

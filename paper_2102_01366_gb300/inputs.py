@@ -373,3 +373,63 @@ def sod_case(nx=64, nyz=8, jitter=0.1, seed=2):
     mesh = box_mesh((nx, nyz, nyz), (1.0, 0.1, 0.1), (False, True, True), jitter, seed)
     W, dW = riemann_x_state(mesh)
     return mesh, W, dW
+
+
+# --------------------------------------------------------------------------
+# batches of independent cases (one mesh, disjoint components)
+# --------------------------------------------------------------------------
+
+def batch_mesh(meshes):
+    """Disjoint union of meshes: vertex ids offset, cells grouped by case.
+    Adds ``case`` (int32 per tet) and per-case ``period`` [ncase, 3]."""
+    xyz, tet, shift, case, period = [], [], [], [], []
+    off = 0
+    for k, m in enumerate(meshes):
+        xyz.append(m["xyz"])
+        tet.append(m["tet"] + off)
+        shift.append(m["shift"])
+        case.append(np.full(m["tet"].shape[0], k, dtype=np.int32))
+        period.append(m["period"])
+        off += m["xyz"].shape[0]
+    return {"xyz": np.concatenate(xyz), "tet": np.concatenate(tet), "shift": np.concatenate(shift),
+            "case": np.concatenate(case), "period": np.stack(period), "ncase": len(meshes),
+            "case_cells": np.array([m["tet"].shape[0] for m in meshes])}
+
+
+def riemann_slab_state(mesh, inner=(1.0, 1.0), outer=(0.125, 0.1), mach=1.0, x0=0.25, x1=0.75,
+                       gamma=1.4):
+    """Periodic planar Riemann data: (rho, p) = inner on x0 <= x < x1 and outer
+    elsewhere, both moving along x at Ma times the inner sound speed; exact
+    volume fractions of the two planes per cell, zero gradients."""
+    verts = tet_vertices(mesh)
+    frac_in = _neg_fraction(verts[:, :, 0] - x1) - _neg_fraction(verts[:, :, 0] - x0)
+    u = mach * math.sqrt(gamma * inner[1] / inner[0])
+    def cons(rho, p):
+        return _prim_to_cons(np.array(rho), np.array([u, 0.0, 0.0]), np.array(p), gamma)
+    wi, wo = cons(*inner), cons(*outer)
+    W = frac_in[None, :] * wi[:, None] + (1.0 - frac_in)[None, :] * wo[:, None]
+    return np.ascontiguousarray(W), np.zeros((15, W.shape[1]))
+
+
+def batch_cases(n_cases=48, n_range=(8, 40), seed=5, jitter=0.1, quad_order=3):
+    """Independent periodic unit cubes of n^3 hexes x 6 tets, n uniform in
+    n_range (seeded); each case a density wave or a planar Riemann problem
+    moving at a Mach number uniform in [0.5, 3].  Returns (batch mesh,
+    W, dW, case descriptions)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    meshes, Ws, dWs, desc = [], [], [], []
+    for k in range(n_cases):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        kind = "sine" if rng.random() < 0.5 else "riemann"
+        mach = float(rng.uniform(0.5, 3.0))
+        m = box_mesh((n, n, n), (1.0, 1.0, 1.0), (True, True, True), jitter, seed * 1000 + k,
+                     diagonal=(1, 1, -1))
+        if kind == "sine":
+            W, dW = sine_wave_state(m, order=quad_order)
+        else:
+            W, dW = riemann_slab_state(m, mach=mach)
+        meshes.append(m)
+        Ws.append(W)
+        dWs.append(dW)
+        desc.append({"n": n, "kind": kind, "mach": mach if kind == "riemann" else None})
+    return batch_mesh(meshes), np.concatenate(Ws, axis=1), np.concatenate(dWs, axis=1), desc, meshes

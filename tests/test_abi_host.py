@@ -93,3 +93,27 @@ def test_rejects_bad_input(built):
     assert st == -7 and not h.value
     p.order = 4
     assert gks.lib().gks_workspace_bytes(g._h, C.byref(p)) == 0
+
+
+def test_batch_connectivity_matches_each_case(built, oracle_mod):
+    """A batch is the disjoint union of its cases: per case, the connectivity
+    equals the oracle's for that case alone (cell ids offset by the case's
+    first cell); faces never join cells of different cases."""
+    batch, W, dW, desc, meshes = I.batch_cases(n_cases=4, n_range=(2, 4), seed=3)
+    g = gks.Mesh(batch)
+    assert g.ncase == 4 and g.case_first[-1] == g.nc
+    top = g.topology()
+    for k, m in enumerate(meshes):
+        to = oracle_mod.Mesh(m).topology()
+        c0, c1 = g.case_first[k], g.case_first[k + 1]
+        nb = top["nbr"][c0:c1]
+        np.testing.assert_array_equal(np.where(nb >= 0, nb - c0, nb), to["nbr"])
+        np.testing.assert_array_equal(top["csr_sign"][c0:c1], to["csr_sign"])
+    lr = top["face_lr"]
+    case_of = np.searchsorted(g.case_first, np.arange(g.nc), side="right") - 1
+    assert (case_of[lr[:, 0]] == case_of[lr[:, 1]]).all()
+    # cases must be grouped in ascending order
+    bad = dict(batch)
+    bad["case"] = batch["case"][::-1].copy()
+    with pytest.raises(gks.GksError):
+        gks.Mesh(bad)
