@@ -162,6 +162,27 @@ def cpu_baseline(max_seconds=20.0, max_steps=40):
                       "FP64 C oracle, 1 thread" % (n, om.nc)}
 
 
+def batched_leg(torch, gks, args, flush):
+    """Many independent periodic cases of uneven size in one mesh (each with
+    its own time step), FP32 bulk, one CUDA graph per step for the batch."""
+    t0 = time.perf_counter()
+    batch, W, dW, desc, _ = I.batch_cases(n_cases=args.batch_cases, n_range=(8, 40), seed=5)
+    g = gks.Mesh(batch)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    s.init(W, dW)
+    setup_s = time.perf_counter() - t0
+    steps = max(5, args.steps // 5)
+    ms = time_device(torch, s, steps, args.warmup, flush)
+    ms = replicas.max_over_ranks(ms)
+    t, dt = s.case_times()
+    return {"workload": "%d periodic cubes of 8^3..40^3 hexes x 6 tets (seed 5), density waves and "
+                        "Riemann slabs at Mach 0.5-3, WENO, FP32 bulk, per-case dt" % args.batch_cases,
+            "cells": g.nc, "faces": g.nf, "cases": g.ncase, "steps": steps, "ms_per_step": ms,
+            "value": replicas.world()[0] * g.nc * 2 / (ms / 1000.0) / 1e6, "unit": METRIC,
+            "dt_range": [float(dt.min()), float(dt.max())], "host_setup_s": setup_s,
+            "l2": "inputs larger than L2 (plus the flush)"}
+
+
 def run_reference(args):
     ws, rank, _ = replicas.world()
     if rank != 0:
@@ -200,6 +221,8 @@ def main():
                     help="only the FP32 timed steps (for profilers); no accuracy, e2e or CPU legs")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of --profile-case")
+    ap.add_argument("--batch-cases", type=int, default=48,
+                    help="independent cases of the batched leg (0: skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -312,6 +335,8 @@ def main():
         "clocks": clocks,
         "peaks": {"source": peak_src, **{k: peaks[k] for k in ("hbm_gbs", "bf16_tflops") if k in peaks}},
     }
+    if args.batch_cases > 0:
+        line["batched"] = batched_leg(torch, gks, args, flush)
     if rank == 0 and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

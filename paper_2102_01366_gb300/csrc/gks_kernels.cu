@@ -85,19 +85,24 @@ __device__ void block_case_min(double v, int32_t cas, bool valid, int lc, unsign
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // an update only when it can lower the current minimum: most blocks
+        // then issue no atomic at all
+        auto commit = [&](int32_t k, double v) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            if (b < *((volatile unsigned long long*)(dtmin + k))) atomicMin(dtmin + k, b);
+        };
         int32_t cur = -1;
         double mn = INFINITY;
         for (int i = 0; i < CELLS_PER_BLOCK; ++i) {
             if (sc[i] < 0) continue;
             if (sc[i] != cur) {
-                if (cur >= 0 && mn < INFINITY)
-                    atomicMin(dtmin + cur, (unsigned long long)__double_as_longlong(mn));
+                if (cur >= 0 && mn < INFINITY) commit(cur, mn);
                 cur = sc[i];
                 mn = INFINITY;
             }
             mn = fmin(mn, sv[i]);
         }
-        if (cur >= 0 && mn < INFINITY) atomicMin(dtmin + cur, (unsigned long long)__double_as_longlong(mn));
+        if (cur >= 0 && mn < INFINITY) commit(cur, mn);
     }
 }
 

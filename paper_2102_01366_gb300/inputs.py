@@ -189,13 +189,25 @@ def sine_wave_fields(x, t=0.0, amp=0.2, k=2.0 * math.pi, u=(1.0, 1.0, 1.0),
     return W, dW
 
 
-def sine_wave_state(mesh, t=0.0, order=5, **kw):
-    """Cell averages of W and of grad W for the density wave at time t."""
+def sine_wave_state(mesh, t=0.0, order=5, amp=0.2, k=2.0 * math.pi, u=(1.0, 1.0, 1.0), p=1.0,
+                    gamma=1.4):
+    """Cell averages of W and of grad W for the density wave at time t.  Every
+    conservative variable is affine in rho, so only the averages of
+    sin(k s) and cos(k s), s = x + y + z - (u1+u2+u3) t, are integrated."""
+    c = u[0] + u[1] + u[2]
+
     def f(x):
-        W, dW = sine_wave_fields(x, t=t, **kw)
-        return np.concatenate([W, dW], axis=-1)
+        sarg = k * (x[..., 0] + x[..., 1] + x[..., 2] - c * t)
+        return np.stack([np.sin(sarg), np.cos(sarg)], axis=-1)
+
     avg = cell_average(mesh, f, order=order)
-    return np.ascontiguousarray(avg[:, :5].T), np.ascontiguousarray(avg[:, 5:].T)
+    rho = 1.0 + amp * avg[:, 0]
+    drho = amp * k * avg[:, 1]
+    dqdrho = np.array([1.0, u[0], u[1], u[2], 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)])
+    W = dqdrho[:, None] * rho[None, :]
+    W[4] += p / (gamma - 1.0)
+    dW = np.repeat((dqdrho[:, None] * drho[None, :]), 3, axis=0)
+    return np.ascontiguousarray(W), np.ascontiguousarray(dW)
 
 
 def _neg_fraction(d):
