@@ -171,6 +171,7 @@ def batched_leg(torch, gks, args, flush):
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
     s.init(W, dW)
     setup_s = time.perf_counter() - t0
+    tuned = s.autotune(steps=5, cache=False)
     steps = max(5, args.steps // 5)
     ms = time_device(torch, s, steps, args.warmup, flush)
     ms = replicas.max_over_ranks(ms)
@@ -180,6 +181,7 @@ def batched_leg(torch, gks, args, flush):
             "cells": g.nc, "faces": g.nf, "cases": g.ncase, "steps": steps, "ms_per_step": ms,
             "value": replicas.world()[0] * g.nc * 2 / (ms / 1000.0) / 1e6, "unit": METRIC,
             "dt_range": [float(dt.min()), float(dt.max())], "host_setup_s": setup_s,
+            "autotuned_variant": tuned["variant"], "variant_ms": tuned["ms_per_step"],
             "l2": "inputs larger than L2 (plus the flush)"}
 
 
@@ -258,6 +260,7 @@ def main():
     for name, prec in (("fp64", 0), ("fp32", 1)):
         s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
         s.init(W0, dW0)
+        tuned = s.autotune(steps=10, cache=False)  # restores the state
         if name == "fp32":
             with ClockSampler(local) as clk:
                 ms = time_device(torch, s, args.steps, args.warmup, flush)
@@ -271,7 +274,7 @@ def main():
             s.step(1)
         s.sync()
         br = s.step_timed(max(3, args.steps // 5 if name == "fp64" else args.steps))
-        results[name] = {"ms": ms, "breakdown": br}
+        results[name] = {"ms": ms, "breakdown": br, "variant": tuned["variant"]}
     # equal-L1 comparison at t = 0.2 (untimed)
     l1_64, W64 = l1_at(torch, gks, mesh, W0, dW0, 0, 0.2)
     l1_32, W32 = l1_at(torch, gks, mesh, W0, dW0, 1, 0.2)
@@ -324,6 +327,8 @@ def main():
                    "l2": "flushed between timed steps (512 MB write)", "graph": "one CUDA graph per step",
                    "replicas": ws},
         "fp64": {"value": value64, "ms_per_step": results["fp64"]["ms"], "dtype": "f64"},
+        "autotuned_variant": {"fp32": results["fp32"]["variant"], "fp64": results["fp64"]["variant"],
+                              "meaning": "[face_order, flux_blocks_per_SM]"},
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32,
                           "fp32_vs_fp64_rel": fp32_vs_fp64},
         "fp32_speedup_over_fp64": value / value64,

@@ -241,7 +241,7 @@ namespace {
 struct Layout {
     size_t total = 0;
     // mesh
-    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case;
+    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case, perm;
     // state
     size_t Wd, Wr, dW, Ws, dWs, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
@@ -268,6 +268,7 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     L.flr = L.add(4 * 2 * nf);
     L.fgeo = L.add(T * FGEO * nf);
     L.cell_case = L.add(4 * nc);
+    L.perm = L.add(4 * nf);
     L.Wd = L.add(8 * 5 * nc);
     L.Wr = fp32 ? L.add(T * 5 * nc) : L.Wd;
     L.dW = L.add(T * 15 * nc);
@@ -284,7 +285,8 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     L.case_dtmin = L.add(8 * ncase);
     L.part = L.add(8 * PART_N * nblk);
     L.err = L.add(4);
-    L.stage = L.add(8 * 15 * nc);
+    // scratch: host-buffer staging, time-step partials, autotune snapshot
+    L.stage = L.add(8 * (20 * nc + 3 * ncase + CTRL_N + 1));
     return L;
 }
 
@@ -305,6 +307,8 @@ struct gks_state {
     DevState<float> s32;
     cudaGraphExec_t graph = nullptr;
     bool initialised = false;
+    int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
+    int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
 };
 
 template <typename T>
@@ -349,21 +353,74 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     st.err = at<int32_t>(s, L.err);
 }
 
+// Device face order: canonical (0) or grouped by left cell (1).  perm maps a
+// device face index to its canonical index; the cell-to-face list, the face
+// arrays and the records use device indices.
+static std::vector<int32_t> face_permutation(const gks_mesh& g, int order) {
+    std::vector<int32_t> perm((size_t)g.nf);
+    for (int64_t f = 0; f < g.nf; ++f) perm[f] = (int32_t)f;
+    if (order == 1) {
+        auto key = [&](int32_t f) {
+            const int64_t l = g.face_lr[f * 2], r = g.face_lr[f * 2 + 1];
+            return std::make_pair(l >= 0 ? l : r, (int64_t)f);
+        };
+        std::sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
+    }
+    return perm;
+}
+
 template <typename T>
-static gks_status upload_mesh(gks_state* s) {
+static gks_status upload_faces(gks_state* s) {
     const gks_mesh& g = *s->mesh;
     const int64_t nc = g.nc, nf = g.nf;
     const Layout& L = s->L;
-    std::vector<int32_t> nbr(4 * nc), cface(4 * nc), flr(2 * nf);
+    const std::vector<int32_t> perm = face_permutation(g, s->face_order);
+    std::vector<int32_t> inv((size_t)nf);
+    for (int64_t d = 0; d < nf; ++d) inv[perm[d]] = (int32_t)d;
+    std::vector<int32_t> cface(4 * nc), flr(2 * nf);
+    std::vector<T> fgeo(FGEO * nf, T(0));
+    for (int64_t c = 0; c < nc; ++c)
+        for (int f = 0; f < 4; ++f) {
+            const int64_t fi = g.csr_face[c * 4 + f];
+            const bool left = g.csr_sign[c * 4 + f] > 0;
+            cface[f * nc + c] = (int32_t)((int64_t)inv[fi] * 2 + (left ? 0 : 1));
+        }
+    for (int64_t d = 0; d < nf; ++d) {
+        const int64_t f = perm[d];
+        flr[d] = (int32_t)g.face_lr[f * 2];
+        flr[nf + d] = (int32_t)g.face_lr[f * 2 + 1];
+        T* r = &fgeo[d * FGEO];
+        for (int a = 0; a < 3; ++a) r[a] = (T)g.fnorm[f * 3 + a];
+        r[3] = (T)(g.farea[f] / 3.0);
+        for (int k = 0; k < 9; ++k) {
+            r[4 + k] = (T)g.gp_l[f * 9 + k];
+            r[13 + k] = (T)g.gp_r[f * 9 + k];
+        }
+    }
+    auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+        return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    GKS_CHECK_CUDA(put(L.cface, cface.data(), 4 * cface.size()));
+    GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
+    GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
+    GKS_CHECK_CUDA(put(L.perm, perm.data(), 4 * perm.size()));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
+    return GKS_OK;
+}
+
+template <typename T>
+static gks_status upload_mesh(gks_state* s) {
+    const gks_mesh& g = *s->mesh;
+    const int64_t nc = g.nc;
+    const Layout& L = s->L;
+    std::vector<int32_t> nbr(4 * nc);
     std::vector<double> inv_vol(nc);
-    std::vector<T> vol23(nc), vol43(nc), dr(nc), mom2(6 * nc), cgp(36 * nc), M1(12 * nc), M2(144 * nc),
-        fgeo(FGEO * nf, T(0));
+    std::vector<T> vol23(nc), vol43(nc), dr(nc), mom2(6 * nc), cgp(36 * nc), M1(12 * nc), M2(144 * nc);
     for (int64_t c = 0; c < nc; ++c) {
         for (int f = 0; f < 4; ++f) {
             nbr[f * nc + c] = (int32_t)g.nbr[c * 4 + f];
             const int64_t fi = g.csr_face[c * 4 + f];
             const bool left = g.csr_sign[c * 4 + f] > 0;
-            cface[f * nc + c] = (int32_t)(fi * 2 + (left ? 0 : 1));
             const double* gp = left ? &g.gp_l[fi * 9] : &g.gp_r[fi * 9];
             for (int k = 0; k < 9; ++k) cgp[(f * 9 + k) * nc + c] = (T)gp[k];
         }
@@ -375,22 +432,10 @@ static gks_status upload_mesh(gks_state* s) {
         for (int k = 0; k < 12; ++k) M1[k * nc + c] = (T)g.M1[c * 12 + k];
         for (int k = 0; k < 144; ++k) M2[k * nc + c] = (T)g.M2[c * 144 + k];
     }
-    for (int64_t f = 0; f < nf; ++f) {
-        flr[f] = (int32_t)g.face_lr[f * 2];
-        flr[nf + f] = (int32_t)g.face_lr[f * 2 + 1];
-        T* r = &fgeo[f * FGEO];
-        for (int a = 0; a < 3; ++a) r[a] = (T)g.fnorm[f * 3 + a];
-        r[3] = (T)(g.farea[f] / 3.0);
-        for (int k = 0; k < 9; ++k) {
-            r[4 + k] = (T)g.gp_l[f * 9 + k];
-            r[13 + k] = (T)g.gp_r[f * 9 + k];
-        }
-    }
     auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
     };
     GKS_CHECK_CUDA(put(L.nbr, nbr.data(), 4 * nbr.size()));
-    GKS_CHECK_CUDA(put(L.cface, cface.data(), 4 * cface.size()));
     GKS_CHECK_CUDA(put(L.inv_vol, inv_vol.data(), 8 * inv_vol.size()));
     GKS_CHECK_CUDA(put(L.vol23, vol23.data(), sizeof(T) * vol23.size()));
     GKS_CHECK_CUDA(put(L.vol43, vol43.data(), sizeof(T) * vol43.size()));
@@ -399,13 +444,11 @@ static gks_status upload_mesh(gks_state* s) {
     GKS_CHECK_CUDA(put(L.cgp, cgp.data(), sizeof(T) * cgp.size()));
     GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(T) * M1.size()));
     GKS_CHECK_CUDA(put(L.M2, M2.data(), sizeof(T) * M2.size()));
-    GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
-    GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
     GKS_CHECK_CUDA(put(L.cell_case, g.cell_case.data(), 4 * g.cell_case.size()));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
-    return GKS_OK;
+    return upload_faces<T>(s);
 }
 
 extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
@@ -530,11 +573,11 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     cudaError_t e;
     // stage 1 from (W^n, grad W^n)
     if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, nullptr, st.poly, nullptr, &fin, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.case_dt, 0.0, 1, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.case_dt, 0.0, 1, q, s->flux_variant)) != cudaSuccess) return e;
     if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
     // stage 2 from (W*, grad W*)
     if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, nullptr, st.poly, nullptr, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.case_dt, 0.0, 2, q)) != cudaSuccess) return e;
+    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.case_dt, 0.0, 2, q, s->flux_variant)) != cudaSuccess) return e;
     return Launch<T>::update2(m, p, st, q);
 }
 
@@ -610,7 +653,7 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             if (e == cudaSuccess)
                 e = Launch<T>::recon(m, p, W, dW, nullptr, st.poly, nullptr, fuse ? &fin : nullptr, q);
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
-            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.case_dt, 0.0, stage, q);
+            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
             if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
@@ -812,8 +855,9 @@ static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, d
                                  double* d_rec) {
     gks_status r = debug_recon_impl<T>(s, m, st, nullptr, nullptr, nullptr);
     if (r != GKS_OK) return r;
-    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, nullptr, dt, stage, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::to_double(st.rec, d_rec, (stage == 1 ? 40 : 20) * m.nf, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, nullptr, dt, stage, s->stream, s->flux_variant));
+    GKS_CHECK_CUDA(Launch<T>::rec_to_double(st.rec, at<int32_t>(s, s->L.perm), d_rec, m.nf, stage == 1 ? 40 : 20,
+                                            s->stream));
     return GKS_OK;
 }
 
@@ -826,4 +870,87 @@ extern "C" gks_status gks_debug_face_records(gks_state* s, double dt, int32_t st
     if (st != GKS_OK) return st;
     if (s->own_stream) return gks_sync(s);
     return GKS_OK;
+}
+
+// ------------------------------------------------------------- variants --
+
+extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, int32_t flux_blocks) {
+    if (!s) { set_error("gks_state_set_variant: state is NULL"); return GKS_E_ARG; }
+    if ((face_order != 0 && face_order != 1) || (flux_blocks != 2 && flux_blocks != 3)) {
+        set_error("gks_state_set_variant: face_order must be 0 or 1 and flux_blocks 2 or 3");
+        return GKS_E_ARG;
+    }
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->flux_variant = flux_blocks == 3 ? 1 : 0;
+    if (face_order != s->face_order) {
+        s->face_order = face_order;
+        gks_status st = s->fp32 ? upload_faces<float>(s) : upload_faces<double>(s);
+        if (st != GKS_OK) return st;
+    }
+    return GKS_OK;
+}
+
+template <typename T>
+static gks_status snapshot(gks_state* s, DevState<T>& st, bool save) {
+    const int64_t nc = s->mesh->nc, nk = s->mesh->ncase;
+    char* base = s->ws + s->L.stage;
+    struct Item { void* dev; size_t bytes; };
+    const Item items[] = {{st.Wd, 8 * 5 * (size_t)nc},
+                          {st.dW, sizeof(T) * 15 * (size_t)nc},
+                          {st.case_t, 8 * (size_t)nk},
+                          {st.case_dt, 8 * (size_t)nk},
+                          {st.case_dtmin, 8 * (size_t)nk},
+                          {st.ctrl, 8 * (size_t)CTRL_N}};
+    size_t off = 0;
+    for (const Item& it : items) {
+        void* dst = save ? (void*)(base + off) : it.dev;
+        const void* src = save ? it.dev : (const void*)(base + off);
+        GKS_CHECK_CUDA(cudaMemcpyAsync(dst, src, it.bytes, cudaMemcpyDeviceToDevice, s->stream));
+        off += it.bytes;
+    }
+    if (!save && (void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_order, int32_t* flux_blocks,
+                                   double* ms_per_step) {
+    if (!s || steps < 1) { set_error("gks_autotune: NULL state or steps < 1"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("gks_autotune: state not initialised"); return GKS_E_STATE; }
+    const int orders[4] = {0, 1, 0, 1}, blocks[4] = {3, 3, 2, 2};
+    const int nvar = s->fp32 ? 4 : 2;  // the FP64 flux has a single variant
+    gks_status r = s->fp32 ? snapshot<float>(s, s->s32, true) : snapshot<double>(s, s->s64, true);
+    if (r != GKS_OK) return r;
+    double best = INFINITY;
+    int bi = 0;
+    cudaEvent_t e0, e1;
+    GKS_CHECK_CUDA(cudaEventCreate(&e0));
+    GKS_CHECK_CUDA(cudaEventCreate(&e1));
+    for (int v = 0; v < nvar && r == GKS_OK; ++v) {
+        r = gks_state_set_variant(s, orders[v], blocks[v]);
+        if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
+        if (r == GKS_OK) r = gks_step(s, 1, 0.0, 0.0);  // graph capture + warm-up
+        if (r != GKS_OK) break;
+        cudaEventRecord(e0, s->stream);
+        r = gks_step(s, steps, 0.0, 0.0);
+        cudaEventRecord(e1, s->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { set_error("gks_autotune: event"); r = GKS_E_CUDA; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[v] = per;
+        if (per < best) { best = per; bi = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != GKS_OK) return r;
+    r = gks_state_set_variant(s, orders[bi], blocks[bi]);
+    if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
+    if (r != GKS_OK) return r;
+    GKS_CHECK_CUDA(cudaMemsetAsync(s->fp32 ? (void*)s->s32.err : (void*)s->s64.err, 0, 4, s->stream));
+    if (face_order) *face_order = orders[bi];
+    if (flux_blocks) *flux_blocks = blocks[bi];
+    return gks_sync(s);
 }

@@ -453,8 +453,8 @@ struct FluxSmem {
     T red[FP_GP * NR];   // weighted record entries per Gauss point
 };
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(2 * FP_GP, 3) k_flux(DevMesh<T> m, Phys<T> ph,
+template <typename T, int NR, int MINB>
+__global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
                                                      const T* __restrict__ Wavg,
                                                      const T* __restrict__ poly,
                                                      T* __restrict__ rec,
@@ -926,6 +926,15 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
 }
 
 template <typename T>
+__global__ void k_rec_out(const T* __restrict__ rec, const int32_t* __restrict__ perm, double* __restrict__ out,
+                          int64_t nf, int nr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf * nr; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = i / nr;
+        out[(int64_t)perm[d] * nr + (i - d * nr)] = (double)rec[i];
+    }
+}
+
+template <typename T>
 __global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, int64_t nc) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 50; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (double)in[(i / 50) * POLY_STRIDE + i % 50];
@@ -989,17 +998,26 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W,
 
 template <typename T>
 cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
-                            const double* ctrl, double dt_override, int stage, cudaStream_t s) {
+                            const double* ctrl, double dt_override, int stage, cudaStream_t s, int variant) {
     // ctrl is the per-case step array (NULL: dt_override everywhere)
     if (m.nf == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
     const Phys<T> ph = make_phys<T>(p);
     if constexpr (sizeof(T) == 4) {
-        // FP32: the two sides of each Gauss point in separate warps
-        if (stage == 1)
-            k_flux<T, 40><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
-        else
-            k_flux<T, 20><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        // FP32: the two sides of each Gauss point in separate warps; variant
+        // 1 trades registers for occupancy (3 blocks per SM), variant 0 keeps
+        // 2 blocks per SM without spills
+        if (variant == 1) {
+            if (stage == 1)
+                k_flux<T, 40, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            else
+                k_flux<T, 20, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        } else {
+            if (stage == 1)
+                k_flux<T, 40, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            else
+                k_flux<T, 20, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        }
     } else {
         if (stage == 1)
             k_flux_single<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
@@ -1051,6 +1069,15 @@ template <typename T>
 cudaError_t Launch<T>::from_double(const double* in, T* out, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_convert<double, T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::rec_to_double(const T* rec, const int32_t* perm, double* out, int64_t nf, int nr,
+                                     cudaStream_t s) {
+    if (nf == 0) return cudaSuccess;
+    const int64_t n = nf * nr;
+    k_rec_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(rec, perm, out, nf, nr);
     return cudaGetLastError();
 }
 

@@ -85,8 +85,10 @@ struct Launch {
                              T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s);
     // case_dt: per-case step (NULL: dt_override for every face)
+    // variant: 1 = 3 blocks per SM (FP32), 0 = 2 blocks per SM; ignored in FP64
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
-                            const double* case_dt, double dt_override, int stage, cudaStream_t s);
+                            const double* case_dt, double dt_override, int stage, cudaStream_t s,
+                            int variant = 1);
     static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
     static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,
                                cudaStream_t s);
@@ -98,6 +100,9 @@ struct Launch {
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
+    // face records in device order -> FP64 in canonical order (perm: device -> canonical)
+    static cudaError_t rec_to_double(const T* rec, const int32_t* perm, double* out, int64_t nf, int nr,
+                                     cudaStream_t s);
     // padded reconstruction records [nc][POLY_STRIDE] -> compact FP64 [nc][50]
     static cudaError_t poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s);
 };

@@ -84,6 +84,8 @@ def lib():
         "gks_residual": (C.c_int32, [_vp, _vp]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
+        "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32]),
+        "gks_autotune": (C.c_int32, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -286,6 +288,54 @@ class State:
             tt, dt = self.case_times()
             if (tt >= t_end * (1 - 1e-14)).all() or (dt <= 0.0).all():
                 return float(tt.min())
+
+    # -- tuning ----------------------------------------------------------------
+    def set_variant(self, face_order, flux_blocks):
+        _call("gks_state_set_variant", self._h, int(face_order), int(flux_blocks))
+        self.variant = (int(face_order), int(flux_blocks))
+
+    def _tune_key(self):
+        p = self.params
+        name = self.torch.cuda.get_device_name(self.device)
+        return "%s|nc=%d|nf=%d|ncase=%d|prec=%d|weno=%d|order=%d|smooth=%d|visc=%d" % (
+            name, self.mesh.nc, self.mesh.nf, self.mesh.ncase, p.precision, p.weno, p.order,
+            p.smooth_flux, p.viscous)
+
+    def autotune(self, steps=10, cache=None):
+        """Choose the fastest execution variant for this mesh and options by
+        timing them (gks_autotune); results are cached in a JSON file keyed by
+        GPU name, mesh size and options (``cache``: path, None for the default
+        ~/.cache/paper_2102_01366_gb300/autotune.json, False for no cache)."""
+        import json
+        if cache is None:
+            cache = os.environ.get("GKS_AUTOTUNE_CACHE", os.path.join(
+                os.path.expanduser("~"), ".cache", "paper_2102_01366_gb300", "autotune.json"))
+        key = self._tune_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                table = json.load(open(cache))
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            fo, fb = table[key]["variant"]
+            self.set_variant(fo, fb)
+            return dict(table[key], cached=True)
+        fo, fb = C.c_int32(), C.c_int32()
+        ms = np.zeros(4)
+        _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), _np_ptr(ms))
+        self.variant = (fo.value, fb.value)
+        res = {"variant": [fo.value, fb.value], "ms_per_step": ms.tolist()}
+        if cache:
+            try:
+                os.makedirs(os.path.dirname(cache), exist_ok=True)
+                table[key] = res
+                tmp = cache + ".tmp%d" % os.getpid()
+                json.dump(table, open(tmp, "w"), indent=1)
+                os.replace(tmp, cache)
+            except OSError:
+                pass
+        return dict(res, cached=False)
 
     # -- diagnostics ----------------------------------------------------------
     def debug_reconstruct(self):

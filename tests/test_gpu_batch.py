@@ -59,3 +59,50 @@ def test_batch_t_end_per_case(cuda):
     s.sync()
     Wb, _ = s.get()
     assert cuda.equal(Wa, Wb)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_variants_give_identical_results(cuda, precision):
+    """Execution variants change speed only.  The face order leaves every
+    face's arithmetic unchanged: bit-identical state.  The two FP32 flux
+    occupancy variants are separately optimised instantiations of the same
+    code (the compiler may contract differently): equal to the FP32
+    tolerance."""
+    mesh, W, dW = I.sod_case(nx=16, nyz=3)
+    g = gks.Mesh(mesh)
+    res = {}
+    for fo, fb in ((0, 3), (1, 3), (0, 2), (1, 2)):
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+        s.set_variant(fo, fb)
+        s.init(W, dW)
+        s.step(3)
+        s.sync()
+        res[(fo, fb)] = [x.cpu() for x in s.get()] + [s.debug_face_records(1e-3, 1).cpu()]
+    for fb in (3, 2):
+        for a, b in zip(res[(0, fb)], res[(1, fb)]):
+            assert cuda.equal(a, b)
+    for a, b in zip(res[(0, 3)], res[(0, 2)]):
+        if precision == 0:
+            assert cuda.equal(a, b)
+        else:
+            assert float((a - b).abs().max() / b.abs().max()) < 2e-5
+
+
+def test_autotune_restores_state(cuda, tmp_path):
+    batch, W, dW, desc, meshes = I.batch_cases(n_cases=3, n_range=(3, 5), seed=11)
+    g = gks.Mesh(batch)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    s.init(W, dW)
+    s.step(2)
+    s.sync()
+    before = [x.clone() for x in s.get()]
+    tb = s.case_times()
+    res = s.autotune(steps=3, cache=str(tmp_path / "tune.json"))
+    assert res["variant"][0] in (0, 1) and res["variant"][1] in (2, 3) and not res["cached"]
+    after = s.get()
+    assert cuda.equal(before[0], after[0]) and cuda.equal(before[1], after[1])
+    np.testing.assert_array_equal(tb[0], s.case_times()[0])
+    # a second state on the same mesh reads the cache
+    s2 = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    s2.init(W, dW)
+    assert s2.autotune(steps=3, cache=str(tmp_path / "tune.json"))["cached"]
