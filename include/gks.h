@@ -260,21 +260,26 @@ gks_status gks_residual(gks_state* state, double* out_l2);
 
 /* ---------------------------------------------------- tuning variants -- */
 
-/* Execution variant of a state (results are identical, only speed differs):
+/* Execution variant of a state (the same arithmetic, only speed differs):
  *   face_order   0 = faces in canonical order, 1 = grouped by left cell
  *   flux_blocks  resident flux blocks per SM, 3 (more warps, fewer registers)
  *                or 2 (no register spills); FP32 only, ignored in FP64
- * Re-uploads the face arrays when the order changes; the next gks_step
- * captures a new graph. */
-gks_status gks_state_set_variant(gks_state* state, int32_t face_order, int32_t flux_blocks);
+ *   slopes_pass  0 = reconstruction step 1 (the P1 slopes, Sec. 4.3) is
+ *                recomputed inside step 2 for each neighbour, 1 = a separate
+ *                pass stores every cell's slopes first (WENO only)
+ * Returns GKS_E_ARG for any other value.  Re-uploads the face arrays when the
+ * order changes; the next gks_step captures a new graph. */
+gks_status gks_state_set_variant(gks_state* state, int32_t face_order, int32_t flux_blocks,
+                                 int32_t slopes_pass);
 
 /* Times every variant for `steps` steps on this state's own mesh and data,
  * keeps the fastest, and restores the state (averages, gradients, case times)
  * to what it was before the call.  Outputs (may be NULL): the chosen
- * face_order and flux_blocks, and ms_per_step[4] of the variants in the order
- * (0,3), (1,3), (0,2), (1,2) (2 entries in FP64).  Synchronises. */
+ * face_order, flux_blocks and slopes_pass, and ms_per_step[8] of variant
+ * v = face_order + 2 slopes_pass + 4 (3 - flux_blocks) (the first 4 entries
+ * only in FP64, whose flux has one form).  Synchronises. */
 gks_status gks_autotune(gks_state* state, int32_t steps, int32_t* face_order, int32_t* flux_blocks,
-                        double* ms_per_step);
+                        int32_t* slopes_pass, double* ms_per_step);
 
 /* ------------------------------------------------------- diagnostics -- */
 

@@ -243,7 +243,7 @@ struct Layout {
     // mesh
     size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case, perm;
     // state
-    size_t Wd, Wr, dW, Ws, dWs, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
+    size_t Wd, X, Xs, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -270,10 +270,8 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     L.cell_case = L.add(4 * nc);
     L.perm = L.add(4 * nf);
     L.Wd = L.add(8 * 5 * nc);
-    L.Wr = fp32 ? L.add(T * 5 * nc) : L.Wd;
-    L.dW = L.add(T * 15 * nc);
-    L.Ws = L.add(T * 5 * nc);
-    L.dWs = L.add(T * 15 * nc);
+    L.X = L.add(T * XS * nc);
+    L.Xs = L.add(T * XS * nc);
     L.S = L.add(8 * 5 * nc);
     L.G = L.add(T * 15 * nc);
     L.slopes = L.add(T * 15 * nc);
@@ -286,7 +284,8 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     L.part = L.add(8 * PART_N * nblk);
     L.err = L.add(4);
     // scratch: host-buffer staging, time-step partials, autotune snapshot
-    L.stage = L.add(8 * (20 * nc + 3 * ncase + CTRL_N + 1));
+    // (FP64 averages and the working state: 25 doubles a cell at most)
+    L.stage = L.add(8 * (25 * nc + 3 * ncase + CTRL_N + 1));
     return L;
 }
 
@@ -309,6 +308,7 @@ struct gks_state {
     bool initialised = false;
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
+    int slopes_pass = 0;   // 1: reconstruction step 1 as its own pass
 };
 
 template <typename T>
@@ -336,10 +336,8 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.flr = at<int32_t>(s, L.flr);
     m.fgeo = at<T>(s, L.fgeo);
     st.Wd = at<double>(s, L.Wd);
-    st.Wr = at<T>(s, L.Wr);
-    st.dW = at<T>(s, L.dW);
-    st.Ws = at<T>(s, L.Ws);
-    st.dWs = at<T>(s, L.dWs);
+    st.X = at<T>(s, L.X);
+    st.Xs = at<T>(s, L.Xs);
     st.S = at<double>(s, L.S);
     st.G = at<T>(s, L.G);
     st.slopes = at<T>(s, L.slopes);
@@ -539,14 +537,10 @@ static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const 
                             const double* d_dW) {
     const int64_t nc = m.nc;
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
-    if ((void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
-    if (sizeof(T) == 8)
-        GKS_CHECK_CUDA(cudaMemcpyAsync(st.dW, d_dW, 8 * 15 * nc, cudaMemcpyDeviceToDevice, s->stream));
-    else
-        GKS_CHECK_CUDA(Launch<T>::from_double(d_dW, st.dW, 15 * nc, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, d_dW, st.X, nc, s->stream));
     GKS_CHECK_CUDA(launch_set_control(st.ctrl, st.case_t, st.case_dt, st.case_dtmin, m.ncase, 0.0, 0.0, 1, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.Wr, st.case_dtmin, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
     return GKS_OK;
 }
 
@@ -561,6 +555,20 @@ extern "C" gks_status gks_init_state(gks_state* s, const double* d_W, const doub
     return GKS_OK;
 }
 
+// reconstruction of one stage (Sec. 4.3): step 1 as its own pass when the
+// variant asks for it and the scheme needs the slopes, else fused into step 2
+template <typename T>
+static cudaError_t enqueue_recon(gks_state* s, DevMesh<T>& m, DevState<T>& st, const T* X,
+                                 const typename Launch<T>::Finalize* fin) {
+    const HostPhys& p = s->phys;
+    if (s->slopes_pass && p.weno) {
+        cudaError_t e = Launch<T>::slopes(m, X, st.slopes, fin, s->stream);
+        if (e != cudaSuccess) return e;
+        return Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, s->stream);
+    }
+    return Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, fin, s->stream);
+}
+
 // one two-stage step (Sec. 3): enqueued on s->stream (captured into a graph).
 // The first kernel's block 0 first turns the per-block time-step minima left
 // by the previous update (or by gks_init_state) into this step's dt.
@@ -568,17 +576,17 @@ template <typename T>
 static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     const HostPhys& p = s->phys;
     cudaStream_t q = s->stream;
-    const bool need_b = p.weno || p.order == 2;
     const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
     cudaError_t e;
-    // stage 1 from (W^n, grad W^n)
-    if ((e = Launch<T>::recon(m, p, st.Wr, st.dW, nullptr, st.poly, nullptr, &fin, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Wr, st.poly, st.rec, st.case_dt, 0.0, 1, q, s->flux_variant)) != cudaSuccess) return e;
-    if ((e = Launch<T>::update1(m, st, q)) != cudaSuccess) return e;
-    // stage 2 from (W*, grad W*)
-    if ((e = Launch<T>::recon(m, p, st.Ws, st.dWs, nullptr, st.poly, nullptr, nullptr, q)) != cudaSuccess) return e;
-    if ((e = Launch<T>::flux(m, p, st.Ws, st.poly, st.rec, st.case_dt, 0.0, 2, q, s->flux_variant)) != cudaSuccess) return e;
-    return Launch<T>::update2(m, p, st, q);
+    for (int stage = 1; stage <= 2; ++stage) {
+        // stage 1 from (W^n, grad W^n), stage 2 from (W*, grad W*)
+        const T* X = stage == 1 ? st.X : st.Xs;
+        if ((e = enqueue_recon(s, m, st, X, stage == 1 ? &fin : nullptr)) != cudaSuccess) return e;
+        if ((e = Launch<T>::flux(m, p, X, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant)) != cudaSuccess)
+            return e;
+        if ((e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static cudaError_t set_control(gks_state* s, double dt_fixed, double t_end, int reset) {
@@ -629,7 +637,6 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
                                   double* kernel_ms, int64_t* launches) {
     const HostPhys& p = s->phys;
     cudaStream_t q = s->stream;
-    const bool need_b = p.weno || p.order == 2;
     const int nev = 16;
     cudaEvent_t ev[nev];
     for (int i = 0; i < nev; ++i) GKS_CHECK_CUDA(cudaEventCreate(&ev[i]));
@@ -647,13 +654,17 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
         kid[ne++] = -1;
         const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
         for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
-            const T* W = stage == 1 ? st.Wr : st.Ws;
-            const T* dW = stage == 1 ? st.dW : st.dWs;
-            const bool fuse = stage == 1;
-            if (e == cudaSuccess)
-                e = Launch<T>::recon(m, p, W, dW, nullptr, st.poly, nullptr, fuse ? &fin : nullptr, q);
+            const T* X = stage == 1 ? st.X : st.Xs;
+            const typename Launch<T>::Finalize* f = stage == 1 ? &fin : nullptr;
+            if (s->slopes_pass && p.weno) {
+                if (e == cudaSuccess) e = Launch<T>::slopes(m, X, st.slopes, f, q);
+                if (e == cudaSuccess) e = mark(GKS_K_SLOPES);
+                if (e == cudaSuccess) e = Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, q);
+            } else if (e == cudaSuccess) {
+                e = Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, f, q);
+            }
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
-            if (e == cudaSuccess) e = Launch<T>::flux(m, p, W, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant);
+            if (e == cudaSuccess) e = Launch<T>::flux(m, p, X, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
             if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
@@ -706,12 +717,7 @@ extern "C" gks_status gks_sync(gks_state* s) {
 template <typename T>
 static gks_status get_impl(gks_state* s, DevState<T>& st, int64_t nc, double* d_W, double* d_dW) {
     if (d_W) GKS_CHECK_CUDA(cudaMemcpyAsync(d_W, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
-    if (d_dW) {
-        if (sizeof(T) == 8)
-            GKS_CHECK_CUDA(cudaMemcpyAsync(d_dW, st.dW, 8 * 15 * nc, cudaMemcpyDeviceToDevice, s->stream));
-        else
-            GKS_CHECK_CUDA(Launch<T>::to_double(st.dW, d_dW, 15 * nc, s->stream));
-    }
+    if (d_dW) GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, d_dW, nc, s->stream));
     return GKS_OK;
 }
 
@@ -756,25 +762,16 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     const int64_t nc = m.nc;
     double* stage = at<double>(s, s->L.stage);
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
-    if ((void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
-    if (sizeof(T) == 8) {
-        GKS_CHECK_CUDA(cudaMemcpyAsync(st.dW, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
-    } else {
-        GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
-        GKS_CHECK_CUDA(Launch<T>::from_double(stage, st.dW, 15 * nc, s->stream));
-    }
+    GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
     GKS_CHECK_CUDA(set_control(s, 0.0, 0.0, 1));
-    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.Wr, st.case_dtmin, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
     s->initialised = true;
     gks_status r = gks_step(s, nsteps, dt_fixed, 0.0);
     if (r != GKS_OK) return r;
     GKS_CHECK_CUDA(cudaMemcpyAsync(h_W_out, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToHost, s->stream));
-    if (sizeof(T) == 8) {
-        GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, st.dW, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
-    } else {
-        GKS_CHECK_CUDA(Launch<T>::to_double(st.dW, stage, 15 * nc, s->stream));
-        GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, stage, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
-    }
+    GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, stage, nc, s->stream));
+    GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, stage, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
     return gks_sync(s);
 }
 
@@ -792,7 +789,7 @@ template <typename T>
 static gks_status timestep_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, double* dt) {
     const int nblk = update_blocks(m.nc);
     double* tmp = at<double>(s, s->L.stage);  // scratch for the partials
-    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.Wr, tmp, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::dt_partials(m, s->phys, st.X, tmp, s->stream));
     std::vector<double> part((size_t)nblk * PART_N);
     GKS_CHECK_CUDA(cudaMemcpyAsync(part.data(), tmp, 8 * part.size(), cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
@@ -832,7 +829,7 @@ static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st,
     const bool need_b = p.weno || p.order == 2;
     const int64_t nc = m.nc;
     if (!need_b) GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.Wr, st.dW, need_b ? st.slopes : nullptr, st.poly, d_fallback,
+    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.X, nullptr, need_b ? st.slopes : nullptr, st.poly, d_fallback,
                                     nullptr, s->stream));
     if (d_poly) GKS_CHECK_CUDA(Launch<T>::poly_to_double(st.poly, d_poly, nc, s->stream));
     if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
@@ -855,7 +852,7 @@ static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, d
                                  double* d_rec) {
     gks_status r = debug_recon_impl<T>(s, m, st, nullptr, nullptr, nullptr);
     if (r != GKS_OK) return r;
-    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.Wr, st.poly, st.rec, nullptr, dt, stage, s->stream, s->flux_variant));
+    GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.X, st.poly, st.rec, nullptr, dt, stage, s->stream, s->flux_variant));
     GKS_CHECK_CUDA(Launch<T>::rec_to_double(st.rec, at<int32_t>(s, s->L.perm), d_rec, m.nf, stage == 1 ? 40 : 20,
                                             s->stream));
     return GKS_OK;
@@ -874,10 +871,12 @@ extern "C" gks_status gks_debug_face_records(gks_state* s, double dt, int32_t st
 
 // ------------------------------------------------------------- variants --
 
-extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, int32_t flux_blocks) {
+extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, int32_t flux_blocks,
+                                            int32_t slopes_pass) {
     if (!s) { set_error("gks_state_set_variant: state is NULL"); return GKS_E_ARG; }
-    if ((face_order != 0 && face_order != 1) || (flux_blocks != 2 && flux_blocks != 3)) {
-        set_error("gks_state_set_variant: face_order must be 0 or 1 and flux_blocks 2 or 3");
+    if ((face_order != 0 && face_order != 1) || (flux_blocks != 2 && flux_blocks != 3) ||
+        (slopes_pass != 0 && slopes_pass != 1)) {
+        set_error("gks_state_set_variant: face_order and slopes_pass must be 0 or 1, flux_blocks 2 or 3");
         return GKS_E_ARG;
     }
     if (s->graph) {
@@ -885,6 +884,7 @@ extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, in
         s->graph = nullptr;
     }
     s->flux_variant = flux_blocks == 3 ? 1 : 0;
+    s->slopes_pass = slopes_pass;
     if (face_order != s->face_order) {
         s->face_order = face_order;
         gks_status st = s->fp32 ? upload_faces<float>(s) : upload_faces<double>(s);
@@ -899,7 +899,7 @@ static gks_status snapshot(gks_state* s, DevState<T>& st, bool save) {
     char* base = s->ws + s->L.stage;
     struct Item { void* dev; size_t bytes; };
     const Item items[] = {{st.Wd, 8 * 5 * (size_t)nc},
-                          {st.dW, sizeof(T) * 15 * (size_t)nc},
+                          {st.X, sizeof(T) * XS * (size_t)nc},
                           {st.case_t, 8 * (size_t)nk},
                           {st.case_dt, 8 * (size_t)nk},
                           {st.case_dtmin, 8 * (size_t)nk},
@@ -911,16 +911,21 @@ static gks_status snapshot(gks_state* s, DevState<T>& st, bool save) {
         GKS_CHECK_CUDA(cudaMemcpyAsync(dst, src, it.bytes, cudaMemcpyDeviceToDevice, s->stream));
         off += it.bytes;
     }
-    if (!save && (void*)st.Wr != (void*)st.Wd) GKS_CHECK_CUDA(Launch<T>::from_double(st.Wd, st.Wr, 5 * nc, s->stream));
     return GKS_OK;
 }
 
 extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_order, int32_t* flux_blocks,
-                                   double* ms_per_step) {
+                                   int32_t* slopes_pass, double* ms_per_step) {
     if (!s || steps < 1) { set_error("gks_autotune: NULL state or steps < 1"); return GKS_E_ARG; }
     if (!s->initialised) { set_error("gks_autotune: state not initialised"); return GKS_E_STATE; }
-    const int orders[4] = {0, 1, 0, 1}, blocks[4] = {3, 3, 2, 2};
-    const int nvar = s->fp32 ? 4 : 2;  // the FP64 flux has a single variant
+    // variant v: face order v & 1, slopes pass (v >> 1) & 1, flux blocks 3 - (v >> 2)
+    int orders[8], passes[8], blocks[8];
+    for (int v = 0; v < 8; ++v) {
+        orders[v] = v & 1;
+        passes[v] = (v >> 1) & 1;
+        blocks[v] = 3 - (v >> 2);
+    }
+    const int nvar = s->fp32 ? 8 : 4;  // the FP64 flux has a single variant
     gks_status r = s->fp32 ? snapshot<float>(s, s->s32, true) : snapshot<double>(s, s->s64, true);
     if (r != GKS_OK) return r;
     double best = INFINITY;
@@ -929,7 +934,7 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
     GKS_CHECK_CUDA(cudaEventCreate(&e0));
     GKS_CHECK_CUDA(cudaEventCreate(&e1));
     for (int v = 0; v < nvar && r == GKS_OK; ++v) {
-        r = gks_state_set_variant(s, orders[v], blocks[v]);
+        r = gks_state_set_variant(s, orders[v], blocks[v], passes[v]);
         if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
         if (r == GKS_OK) r = gks_step(s, 1, 0.0, 0.0);  // graph capture + warm-up
         if (r != GKS_OK) break;
@@ -946,11 +951,12 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != GKS_OK) return r;
-    r = gks_state_set_variant(s, orders[bi], blocks[bi]);
+    r = gks_state_set_variant(s, orders[bi], blocks[bi], passes[bi]);
     if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
     if (r != GKS_OK) return r;
     GKS_CHECK_CUDA(cudaMemsetAsync(s->fp32 ? (void*)s->s32.err : (void*)s->s64.err, 0, 4, s->stream));
     if (face_order) *face_order = orders[bi];
     if (flux_blocks) *flux_blocks = blocks[bi];
+    if (slopes_pass) *slopes_pass = passes[bi];
     return gks_sync(s);
 }

@@ -128,20 +128,20 @@ __device__ __forceinline__ CellLane cell_lane(int64_t nc) {
 
 // reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3
 template <typename T>
-__global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ W,
+__global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ X,
                                                           T* __restrict__ slopes, FinArg<T> fin) {
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
     const CellLane cl = cell_lane(m.nc);
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
-    const T Q0 = W[q * nc + c];
+    const T Q0 = X[c * XS + q];
     T b0 = T(0), b1 = T(0), b2 = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + c];
         if (nb < 0) continue;
-        const T dq = W[q * nc + nb] - Q0;
+        const T dq = X[(int64_t)nb * XS + q] - Q0;
         b0 += m.M1[(0 * 4 + f) * nc + c] * dq;
         b1 += m.M1[(1 * 4 + f) * nc + c] * dq;
         b2 += m.M1[(2 * 4 + f) * nc + c] * dq;
@@ -155,15 +155,15 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
 // P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
 // b = M1 (Q_nb - Q_x) over the existing neighbours
 template <typename T>
-__device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ W, int64_t x, int q, T* b) {
+__device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ X, int64_t x, int q, T* b) {
     const int64_t nc = m.nc;
-    const T Qx = W[q * nc + x];
+    const T Qx = X[x * XS + q];
     b[0] = b[1] = b[2] = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + x];
         if (nb < 0) continue;
-        const T dq = W[q * nc + nb] - Qx;
+        const T dq = X[(int64_t)nb * XS + q] - Qx;
         b[0] += m.M1[(0 * 4 + f) * nc + x] * dq;
         b[1] += m.M1[(1 * 4 + f) * nc + x] * dq;
         b[2] += m.M1[(2 * 4 + f) * nc + x] * dq;
@@ -177,8 +177,8 @@ __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restric
 // Gauss points (Sec. 4.2); R written about the centroid in monomial form
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
-                                                         const T* __restrict__ W,
-                                                         const T* __restrict__ dW,
+                                                         const T* __restrict__ X,
+                                                         const T* __restrict__ slopes_in,
                                                          T* __restrict__ slopes_out,
                                                          T* __restrict__ poly,
                                                          int32_t* __restrict__ fallback,
@@ -209,17 +209,17 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     int nb[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
-    const T Q0 = W[q * nc + c];
+    const T Q0 = X[c * XS + q];
 
     // data vector [dQ_f (4); grad Q_{f,l} (12)] of this component
     T d[16];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool ok = nb[f] >= 0;
-        const int64_t n = ok ? nb[f] : c;
-        d[f] = ok ? W[q * nc + n] - Q0 : T(0);
+        const T* xn = X + (ok ? (int64_t)nb[f] : c) * XS;
+        d[f] = ok ? xn[q] - Q0 : T(0);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? dW[(3 * q + l) * nc + n] : T(0);
+        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? xn[5 + 3 * q + l] : T(0);
     }
     // P2 in the zero-mean basis of Eq. base: a = M2 d
     T a[9];
@@ -265,7 +265,14 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
         for (int f = 0; f < 4; ++f) {
             if (nb[f] < 0) continue;
             T bj[3];
-            p1_slope(m, W, nb[f], q, bj);
+            if (slopes_in) {
+                const T* sj = slopes_in + (int64_t)nb[f] * 15 + 3 * q;
+                bj[0] = sj[0];
+                bj[1] = sj[1];
+                bj[2] = sj[2];
+            } else {
+                p1_slope(m, X, nb[f], q, bj);
+            }
             b0j[nn++] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
         }
         T beta0 = T(0);
@@ -324,11 +331,11 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     bool bad = false;
 #pragma unroll 4
     for (int g = 0; g < 12; ++g) {
-        const T X = sG[g * 3 + 0][lc];
-        const T Y = sG[g * 3 + 1][lc];
-        const T Z = sG[g * 3 + 2][lc];
-        const T v = c0 + R[0] * X + R[1] * Y + R[2] * Z + R[3] * X * X + R[4] * X * Y + R[5] * X * Z +
-                    R[6] * Y * Y + R[7] * Y * Z + R[8] * Z * Z;
+        const T gx = sG[g * 3 + 0][lc];
+        const T gy = sG[g * 3 + 1][lc];
+        const T gz = sG[g * 3 + 2][lc];
+        const T v = c0 + R[0] * gx + R[1] * gy + R[2] * gz + R[3] * gx * gx + R[4] * gx * gy + R[5] * gx * gz +
+                    R[6] * gy * gy + R[7] * gy * gz + R[8] * gz * gz;
         const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
         const T m1 = __shfl_sync(0xffffffffu, v, cl.base + 1);
         const T m2 = __shfl_sync(0xffffffffu, v, cl.base + 2);
@@ -491,7 +498,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         const int64_t in = side == 0 ? Rc : L;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            Ws[q] = Wavg[q * m.nc + in];
+            Ws[q] = Wavg[in * XS + q];
             gs[0][q] = gs[1][q] = gs[2][q] = T(0);
         }
     }
@@ -698,7 +705,7 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
                 // open boundary: interior cell average, zero gradient
                 const int64_t in = side == 0 ? Rc : L;
                 for (int q = 0; q < 5; ++q) {
-                    Wv[q] = Wavg[q * m.nc + in];
+                    Wv[q] = Wavg[in * XS + q];
                     g[0][q] = g[1][q] = g[2][q] = T(0);
                 }
             }
@@ -773,13 +780,14 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState
         }
     }
     const double iv = m.inv_vol[c];
+    T* xs = st.Xs + c * XS;
     // W* = W^n - (1/|Omega|) sum s sum_k w Fh  (Eq. s2o4, first stage)
-    st.Ws[q * nc + c] = (T)(st.Wd[q * nc + c] - fh.value() * iv);
+    xs[q] = (T)(st.Wd[q * nc + c] - fh.value() * iv);
     st.S[q * nc + c] = s1.value();
     const T ivr = (T)iv;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        st.dWs[(3 * q + i) * nc + c] = gs[i] * ivr;  // Eq. gauss-formula at t* (Eq. step-du)
+        xs[5 + 3 * q + i] = gs[i] * ivr;  // Eq. gauss-formula at t* (Eq. step-du)
         st.G[(3 * q + i) * nc + c] = g0[i];
     }
 }
@@ -846,11 +854,11 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     const T Wq = (T)wn;
     if (live) {
         st.Wd[q * nc + c] = wn;
-        if ((void*)st.Wr != (void*)st.Wd) st.Wr[q * nc + c] = Wq;
+        T* x = st.X + c * XS;
+        x[q] = Wq;
         const T ivr = (T)iv;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            st.dW[(3 * q + i) * nc + c] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
+        for (int i = 0; i < 3; ++i) x[5 + 3 * q + i] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
         // squared rates of change (W^{n+1} - W^n) / dt for the residual
         const T ti = (T)inc / (T)dtd;
 #pragma unroll
@@ -875,7 +883,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
 
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, HostPhys p,
-                                                               const T* __restrict__ W,
+                                                               const T* __restrict__ X,
                                                                double* __restrict__ part) {
     const CellLane cl = cell_lane(m.nc);
     T mn = T(INFINITY);
@@ -883,14 +891,14 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, Host
     if (cl.active && cl.q == 0) {
         T Wv[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + cl.c];
+        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * XS + q];
         mn = local_dt(Wv, m.dr[cl.c], p);
     }
     block_reduce_part<T>(mn, zero, part + (int64_t)blockIdx.x * PART_N);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CELL_THREADS) k_init_dtmin(DevMesh<T> m, HostPhys p, const T* __restrict__ W,
+__global__ void __launch_bounds__(CELL_THREADS) k_init_dtmin(DevMesh<T> m, HostPhys p, const T* __restrict__ X,
                                                               unsigned long long* __restrict__ dtmin) {
     const CellLane cl = cell_lane(m.nc);
     const bool lead = cl.active && cl.q == 0;
@@ -898,7 +906,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_init_dtmin(DevMesh<T> m, HostP
     if (lead) {
         T Wv[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wv[q] = W[q * m.nc + cl.c];
+        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * XS + q];
         mn = (double)local_dt(Wv, m.dr[cl.c], p);
     }
     const int lc = (int)(cl.c - (int64_t)blockIdx.x * CELLS_PER_BLOCK);
@@ -923,6 +931,23 @@ template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (B)in[i];
+}
+
+template <typename T>
+__global__ void k_pack(const double* __restrict__ W, const double* __restrict__ dW, T* __restrict__ X, int64_t nc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * XS; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / XS;
+        const int j = (int)(i - c * XS);
+        X[i] = (T)(j < 5 ? W[j * nc + c] : dW[(j - 5) * nc + c]);
+    }
+}
+
+template <typename T>
+__global__ void k_unpack_grad(const T* __restrict__ X, double* __restrict__ dW, int64_t nc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 15; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / nc, c = i - j * nc;
+        dW[i] = (double)X[c * XS + 5 + j];
+    }
 }
 
 template <typename T>
@@ -975,15 +1000,15 @@ static FinArg<T> fin_arg(const typename Launch<T>::Finalize* fin) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
+cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* X, T* slopes, const Finalize* fin,
                               cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_slopes<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, W, slopes, fin_arg<T>(fin));
+    k_slopes<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, X, slopes, fin_arg<T>(fin));
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
+cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* slopes_in,
                              T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
@@ -992,7 +1017,7 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* W,
     rc.eps = (T)p.eps_weno;
     rc.weno = p.weno;
     rc.order = p.order;
-    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, W, dW, slopes, poly, fallback, fin_arg<T>(fin));
+    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback, fin_arg<T>(fin));
     return cudaGetLastError();
 }
 
@@ -1043,18 +1068,34 @@ cudaError_t Launch<T>::update2(const DevMesh<T>& m, const HostPhys& p, const Dev
 }
 
 template <typename T>
-cudaError_t Launch<T>::dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* W,
+cudaError_t Launch<T>::dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* X,
                                    double* part, cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_dt_partials<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, W, part);
+    k_dt_partials<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, X, part);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* W,
+cudaError_t Launch<T>::init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* X,
                                   unsigned long long* case_dtmin, cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_init_dtmin<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, W, case_dtmin);
+    k_init_dtmin<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, X, case_dtmin);
+    return cudaGetLastError();
+}
+
+static inline unsigned ew_grid(int64_t n) { return (unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192); }
+
+template <typename T>
+cudaError_t Launch<T>::pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_pack<T><<<ew_grid(nc * XS), 256, 0, s>>>(W, dW, X, nc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_unpack_grad<T><<<ew_grid(nc * 15), 256, 0, s>>>(X, dW, nc);
     return cudaGetLastError();
 }
 

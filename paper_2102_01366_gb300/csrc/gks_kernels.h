@@ -19,6 +19,7 @@ constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
 constexpr int CELLS_PER_BLOCK = 24;  // 4 warps x 6 cells, 5 lanes per cell
 constexpr int FGEO = 24;             // reals per face geometry record
 constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record (50 used)
+constexpr int XS = 20;               // reals per cell working-state record: W (5), grad W (15, 3q+i)
 
 template <typename T>
 struct DevMesh {
@@ -42,10 +43,8 @@ struct DevMesh {
 template <typename T>
 struct DevState {
     double* Wd;   // [5][nc] master cell averages (FP64)
-    T* Wr;        // [5][nc] working copy (aliases Wd in FP64)
-    T* dW;        // [15][nc]
-    T* Ws;        // [5][nc] stage state W*
-    T* dWs;       // [15][nc]
+    T* X;         // [nc][XS] working state W^n, grad W^n (cell-major for neighbour gathers)
+    T* Xs;        // [nc][XS] stage state W*, grad W*
     double* S;    // [5][nc] saved stage-1 flux term
     T* G;         // [15][nc] saved stage-1 gradient term
     T* slopes;    // [nc][15]
@@ -77,26 +76,31 @@ struct Launch {
         double cfl;
         const double* ctrl;
     };
-    static cudaError_t slopes(const DevMesh<T>& m, const T* W, T* slopes, const Finalize* fin,
+    static cudaError_t slopes(const DevMesh<T>& m, const T* X, T* slopes, const Finalize* fin,
                               cudaStream_t s);
-    // slopes (may be NULL) receives the step-1 slopes, which the kernel
-    // computes itself (the neighbours' ones included)
-    static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* dW,
-                             T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+    // slopes_in (may be NULL): the step-1 slopes of every cell from a slopes
+    // pass; without it the kernel computes its own and its neighbours' slopes.
+    // slopes_out (may be NULL) receives the cell's own step-1 slopes.
+    static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* slopes_in,
+                             T* slopes_out, T* poly, int32_t* fallback, const Finalize* fin,
                              cudaStream_t s);
     // case_dt: per-case step (NULL: dt_override for every face)
     // variant: 1 = 3 blocks per SM (FP32), 0 = 2 blocks per SM; ignored in FP64
-    static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
+    static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* poly, T* rec,
                             const double* case_dt, double dt_override, int stage, cudaStream_t s,
                             int variant = 1);
     static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
     static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,
                                cudaStream_t s);
-    static cudaError_t dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* W,
+    static cudaError_t dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* X,
                                    double* part, cudaStream_t s);
-    // per-case minima of the local limits of W into case_dtmin (reset first)
-    static cudaError_t init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* W,
+    // per-case minima of the local limits of X into case_dtmin (reset first)
+    static cudaError_t init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* X,
                                   unsigned long long* case_dtmin, cudaStream_t s);
+    // X = [W | grad W] per cell from FP64 component-major W[5][nc], dW[15][nc]
+    static cudaError_t pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s);
+    // FP64 component-major dW[15][nc] from X
+    static cudaError_t unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s);
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);

@@ -84,8 +84,9 @@ def lib():
         "gks_residual": (C.c_int32, [_vp, _vp]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
-        "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32]),
-        "gks_autotune": (C.c_int32, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _vp]),
+        "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+        "gks_autotune": (C.c_int32, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -290,9 +291,9 @@ class State:
                 return float(tt.min())
 
     # -- tuning ----------------------------------------------------------------
-    def set_variant(self, face_order, flux_blocks):
-        _call("gks_state_set_variant", self._h, int(face_order), int(flux_blocks))
-        self.variant = (int(face_order), int(flux_blocks))
+    def set_variant(self, face_order, flux_blocks, slopes_pass=0):
+        _call("gks_state_set_variant", self._h, int(face_order), int(flux_blocks), int(slopes_pass))
+        self.variant = (int(face_order), int(flux_blocks), int(slopes_pass))
 
     def _tune_key(self):
         p = self.params
@@ -317,15 +318,15 @@ class State:
                 table = json.load(open(cache))
             except (OSError, ValueError):
                 table = {}
-        if key in table:
-            fo, fb = table[key]["variant"]
-            self.set_variant(fo, fb)
+        if key in table and len(table[key].get("variant", ())) == 3:
+            self.set_variant(*table[key]["variant"])
             return dict(table[key], cached=True)
-        fo, fb = C.c_int32(), C.c_int32()
-        ms = np.zeros(4)
-        _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), _np_ptr(ms))
-        self.variant = (fo.value, fb.value)
-        res = {"variant": [fo.value, fb.value], "ms_per_step": ms.tolist()}
+        fo, fb, sp = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = np.zeros(8)
+        _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), C.byref(sp), _np_ptr(ms))
+        nvar = 8 if self.params.precision == 1 else 4
+        self.variant = (fo.value, fb.value, sp.value)
+        res = {"variant": list(self.variant), "ms_per_step": ms[:nvar].tolist()}
         if cache:
             try:
                 os.makedirs(os.path.dirname(cache), exist_ok=True)

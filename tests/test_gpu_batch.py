@@ -66,26 +66,36 @@ def test_variants_give_identical_results(cuda, precision):
     """Execution variants change speed only.  The face order leaves every
     face's arithmetic unchanged: bit-identical state.  The two FP32 flux
     occupancy variants are separately optimised instantiations of the same
-    code (the compiler may contract differently): equal to the FP32
-    tolerance."""
+    code (the compiler may contract differently), and so are the fused and
+    the separate slopes passes: equal to the working precision's tolerance."""
     mesh, W, dW = I.sod_case(nx=16, nyz=3)
     g = gks.Mesh(mesh)
     res = {}
-    for fo, fb in ((0, 3), (1, 3), (0, 2), (1, 2)):
+    for v in ((0, 3, 0), (1, 3, 0), (0, 2, 0), (1, 2, 0), (0, 3, 1), (1, 2, 1)):
         s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
-        s.set_variant(fo, fb)
+        s.set_variant(*v)
         s.init(W, dW)
         s.step(3)
         s.sync()
-        res[(fo, fb)] = [x.cpu() for x in s.get()] + [s.debug_face_records(1e-3, 1).cpu()]
+        res[v] = [x.cpu() for x in s.get()] + [s.debug_face_records(1e-3, 1).cpu()]
     for fb in (3, 2):
-        for a, b in zip(res[(0, fb)], res[(1, fb)]):
+        for a, b in zip(res[(0, fb, 0)], res[(1, fb, 0)]):
             assert cuda.equal(a, b)
-    for a, b in zip(res[(0, 3)], res[(0, 2)]):
-        if precision == 0:
-            assert cuda.equal(a, b)
-        else:
-            assert float((a - b).abs().max() / b.abs().max()) < 2e-5
+    tol = 1e-13 if precision == 0 else 2e-5
+    for other in ((0, 2, 0), (0, 3, 1), (1, 2, 1)):
+        for a, b in zip(res[(0, 3, 0)], res[other]):
+            if precision == 0 and other[2] == 0:
+                assert cuda.equal(a, b)
+            else:
+                assert float((a - b).abs().max() / b.abs().max()) < tol, other
+
+
+def test_set_variant_rejects_bad_values(cuda):
+    mesh, W, dW = I.sod_case(nx=8, nyz=2)
+    s = gks.State(gks.Mesh(mesh), gks.params(weno=1))
+    for bad in ((2, 3, 0), (0, 4, 0), (0, 3, 2)):
+        st = gks.lib().gks_state_set_variant(s._h, *bad)
+        assert st == -1, bad  # GKS_E_ARG
 
 
 def test_autotune_restores_state(cuda, tmp_path):
@@ -98,7 +108,9 @@ def test_autotune_restores_state(cuda, tmp_path):
     before = [x.clone() for x in s.get()]
     tb = s.case_times()
     res = s.autotune(steps=3, cache=str(tmp_path / "tune.json"))
-    assert res["variant"][0] in (0, 1) and res["variant"][1] in (2, 3) and not res["cached"]
+    fo, fb, sp = res["variant"]
+    assert fo in (0, 1) and fb in (2, 3) and sp in (0, 1) and not res["cached"]
+    assert len(res["ms_per_step"]) == 8 and min(res["ms_per_step"]) > 0
     after = s.get()
     assert cuda.equal(before[0], after[0]) and cuda.equal(before[1], after[1])
     np.testing.assert_array_equal(tb[0], s.case_times()[0])
