@@ -59,6 +59,8 @@ struct ora_mesh {
     /* stencils */
     double *M1, *M2;
     int64_t n_singular;
+    /* boundary kind of each face (ORA_BC_*), meaningful on boundary faces */
+    int8_t* bkind;      /* [nf] */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -220,6 +222,7 @@ static int build_topology(ora_mesh* m, char* err, int errlen) {
     m->nf = nf;
     m->face_v = (int64_t*)malloc(sizeof(int64_t) * 3 * nf);
     m->face_lr = (int64_t*)malloc(sizeof(int64_t) * 2 * nf);
+    m->bkind = (int8_t*)calloc((size_t)nf, sizeof(int8_t));
     m->farea = (double*)calloc((size_t)nf, sizeof(double));
     m->fnorm = (double*)calloc((size_t)nf * 3, sizeof(double));
     m->gp_l = (double*)calloc((size_t)nf * 9, sizeof(double));
@@ -515,6 +518,17 @@ ora_mesh* ora_mesh_build(const double* xyz, int64_t nv, const int64_t* tet,
     return m;
 }
 
+int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
+    for (int64_t c = 0; c < m->nc; ++c)
+        for (int f = 0; f < 4; ++f) {
+            if (m->nbr[c * 4 + f] >= 0) continue;
+            int8_t k = kind[c * 4 + f];
+            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL) return -1;
+            m->bkind[m->csr_face[c * 4 + f]] = k;
+        }
+    return 0;
+}
+
 void ora_mesh_free(ora_mesh* m) {
     if (!m) return;
     free(m->xyz); free(m->tet); free(m->shift);
@@ -522,7 +536,7 @@ void ora_mesh_free(ora_mesh* m) {
     free(m->csr_face); free(m->csr_sign);
     free(m->vol); free(m->cen); free(m->mom2); free(m->dr);
     free(m->farea); free(m->fnorm); free(m->gp_l); free(m->gp_r);
-    free(m->M1); free(m->M2);
+    free(m->M1); free(m->M2); free(m->bkind);
     free(m);
 }
 
@@ -1154,12 +1168,25 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
              * amplifies rounding noise without bound next to the boundary. */
             for (int side = 0; side < 2; ++side) {
                 int64_t inner = side == 0 ? cr : cl;
-                if ((side == 0 ? cl : cr) >= 0) continue;
+                if ((side == 0 ? cl : cr) >= 0 || m->bkind[f] != ORA_BC_OPEN) continue;
                 double* Wg = side == 0 ? WL : WR;
                 double (*gg)[5] = side == 0 ? gL : gR;
                 for (int q = 0; q < 5; ++q) {
                     Wg[q] = W[q * nc + inner];
                     gg[0][q] = gg[1][q] = gg[2][q] = 0.0;
+                }
+            }
+            /* a slip wall's ghost is built from the interior Gauss-point
+             * state after the rotation (below); give the missing side the
+             * interior values so the rotation leaves them defined */
+            int wall = (cl < 0 || cr < 0) && m->bkind[f] == ORA_BC_SLIP_WALL;
+            if (wall) {
+                if (cl < 0) {
+                    memcpy(WL, WR, sizeof WL);
+                    memcpy(gL, gR, sizeof gL);
+                } else {
+                    memcpy(WR, WL, sizeof WR);
+                    memcpy(gR, gL, sizeof gR);
                 }
             }
             /* rotate into the local frame: components by T, directions by
@@ -1180,6 +1207,20 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                     tgL[j][a] = sl;
                     tgR[j][a] = sr;
                 }
+            if (wall) {
+                /* Sec. 4.4, slip wall, in the face frame (x1 along n): the
+                 * ghost copies rho, rho U2, rho U3, rho E and reverses rho U1;
+                 * of the x1-derivatives only that of rho U1 is kept, the
+                 * others change sign; of the x2- and x3-derivatives only
+                 * those of rho U1 change sign. */
+                double* gW = cl < 0 ? tWL : tWR;
+                double (*gg)[5] = cl < 0 ? tgL : tgR;
+                gW[1] = -gW[1];
+                for (int a = 0; a < 5; ++a)
+                    if (a != 1) gg[0][a] = -gg[0][a];
+                gg[1][1] = -gg[1][1];
+                gg[2][1] = -gg[2][1];
+            }
             double tFh[5], tF[5], tW0[5], tWdt[5];
             ora_gp_flux(p, tWL, &tgL[0][0], tWR, &tgR[0][0], dt, tFh, tF, tW0, tWdt);
             /* back to the global frame with T^-1 = T^T (Eq. flux-local-to-global) */

@@ -56,6 +56,8 @@ def lib():
         L.ora_mesh_build.restype = C.c_void_p
         L.ora_mesh_build.argtypes = [_dp, C.c_int64, _ip, _bp, C.c_int64, _dp, C.c_char_p, C.c_int]
         L.ora_mesh_free.argtypes = [C.c_void_p]
+        L.ora_mesh_set_boundary.restype = C.c_int
+        L.ora_mesh_set_boundary.argtypes = [C.c_void_p, _bp]
         for fn in ("ora_mesh_nc", "ora_mesh_nf", "ora_mesh_n_singular"):
             getattr(L, fn).restype = C.c_int64
             getattr(L, fn).argtypes = [C.c_void_p]
@@ -93,6 +95,15 @@ class Mesh:
         self.nc = L.ora_mesh_nc(self._h)
         self.nf = L.ora_mesh_nf(self._h)
         self.n_singular = L.ora_mesh_n_singular(self._h)
+        if mesh.get("bkind") is not None:
+            self.set_boundary(mesh["bkind"])
+
+    def set_boundary(self, kind):
+        """kind[nc][4]: 0 open, 1 slip wall, per local face (read on boundary
+        faces only)."""
+        kind = np.ascontiguousarray(kind, dtype=np.int8).reshape(self.nc, 4)
+        if lib().ora_mesh_set_boundary(self._h, kind) != 0:
+            raise ValueError("oracle mesh: invalid boundary kind")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -364,6 +364,98 @@ def riemann_x_exact_density(mesh, t, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.
     return cell_average(mesh, f, order=order)[:, 0]
 
 
+def wall_kinds(mesh, axes):
+    """Boundary kind per local face, int8 [nc, 4] (face f is opposite tet
+    vertex f): 1 (slip wall) where the face lies on an end plane of one of the
+    non-periodic ``axes`` (the planes are the extreme vertex coordinates; the
+    generator jitters end-plane vertices only tangentially), else 0 (open)."""
+    xyz = mesh["xyz"]
+    tet = mesh["tet"]
+    kind = np.zeros(tet.shape, dtype=np.int8)
+    for a in axes:
+        if mesh["period"][..., a].any():
+            raise ValueError("axis %d is periodic" % a)
+        coord = xyz[tet, a]  # [nc, 4]
+        for plane in (xyz[:, a].min(), xyz[:, a].max()):
+            on = coord == plane
+            for f in range(4):
+                others = [v for v in range(4) if v != f]
+                kind[on[:, others].all(axis=1), f] = 1
+    return kind
+
+
+def wall_reflection_exact_density(mesh, t, state=(1.0, 1.0, 1.0), length=1.0, gamma=1.4,
+                                  order=6):
+    """Uniform gas (rho, u, p) moving along x between slip walls at x = 0 and
+    x = length: at the right wall a shock reflects, at the left wall a
+    rarefaction opens.  Each is the Riemann problem between the gas and its
+    mirror image; the two fans are separated while the rarefaction head
+    (u + c) t and the shock have not met.  Cell averages of the exact density
+    at time t."""
+    rho, u, p = state
+    gas, mirror = (rho, u, p), (rho, -u, p)
+    ps, _ = exact_riemann(gas, mirror, gamma)
+    c = math.sqrt(gamma * p / rho)
+    shock = u - c * math.sqrt((gamma + 1) / (2 * gamma) * ps / p + (gamma - 1) / (2 * gamma))
+    if (u + c) * t >= length + shock * t:
+        raise ValueError("the two wall waves have met before t")
+
+    def f(x):
+        xx = x[..., 0]
+        r_left, _, _ = sample_riemann(xx / t, mirror, gas, gamma)
+        r_right, _, _ = sample_riemann((xx - length) / t, gas, mirror, gamma)
+        return np.where(xx < 0.5 * length, r_left, r_right)[..., None]
+    return cell_average(mesh, f, order=order)[:, 0]
+
+
+def shu_osher_state(mesh, gamma=1.4, order=3):
+    """Shu-Osher data along x on [0, 10] (Sec. 5.2): (3.857134, 2.629369,
+    10.33333) for x <= 1, (1 + 0.2 sin 5x, 0, 1) beyond; cell averages by
+    quadrature (collapsed Gauss of the given order), gradients of the smooth
+    part by the same quadrature, zero in cells the jump cuts."""
+    left = np.array([3.857134, 2.629369, 10.33333])
+
+    def prim(x):
+        xx = x[..., 0]
+        rho = np.where(xx <= 1.0, left[0], 1.0 + 0.2 * np.sin(5.0 * xx))
+        u = np.where(xx <= 1.0, left[1], 0.0)
+        p = np.where(xx <= 1.0, left[2], 1.0)
+        return rho, u, p
+
+    def cons(x):
+        rho, u, p = prim(x)
+        z = np.zeros_like(rho)
+        return np.stack([rho, rho * u, z, z, p / (gamma - 1.0) + 0.5 * rho * u * u], axis=-1)
+    W = cell_average(mesh, cons, order=order).T.copy()
+    # gradients: only rho and rho E vary in the smooth part (d/dx of the
+    # sine), and U = 0 there
+    def grad(x):
+        xx = x[..., 0]
+        out = np.zeros(xx.shape + (15,))
+        out[..., 0] = np.where(xx <= 1.0, 0.0, 0.2 * 5.0 * np.cos(5.0 * xx))  # d rho / dx
+        return out
+    dW = cell_average(mesh, grad, order=order).T.copy()
+    verts = tet_vertices(mesh)
+    cut = (verts[:, :, 0].min(axis=1) < 1.0) & (verts[:, :, 0].max(axis=1) > 1.0)
+    dW[:, cut] = 0.0
+    return np.ascontiguousarray(W), np.ascontiguousarray(dW)
+
+
+def blast_wave_state(mesh, gamma=1.4):
+    """Woodward-Colella blast wave on [0, 1] (Sec. 5.2): rho = 1, u = 0 and
+    p = 1000 | 0.01 | 100 split at x = 0.1 and 0.9; exact volume fractions of
+    the two planes per cell, zero gradients."""
+    verts = tet_vertices(mesh)
+    f_left = _neg_fraction(verts[:, :, 0] - 0.1)
+    f_right = 1.0 - _neg_fraction(verts[:, :, 0] - 0.9)
+    f_mid = 1.0 - f_left - f_right
+    E = (1000.0 * f_left + 0.01 * f_mid + 100.0 * f_right) / (gamma - 1.0)
+    W = np.zeros((5, verts.shape[0]))
+    W[0] = 1.0
+    W[4] = E
+    return W, np.zeros((15, W.shape[1]))
+
+
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
@@ -391,6 +483,35 @@ def sod_case(nx=64, nyz=8, jitter=0.1, seed=2):
 # batches of independent cases (one mesh, disjoint components)
 # --------------------------------------------------------------------------
 
+def wall_reflection_case(nx=64, nyz=4, state=(1.0, 1.0, 1.0), jitter=0.1, seed=3):
+    """Uniform gas moving along x in [0,1] x [0,nyz/nx]^2 (cubic hexahedra)
+    between slip walls at x = 0 and 1, y and z periodic; nx x nyz x nyz
+    hexes x 6 tets."""
+    w = nyz / nx
+    mesh = box_mesh((nx, nyz, nyz), (1.0, w, w), (False, True, True), jitter, seed)
+    mesh["bkind"] = wall_kinds(mesh, (0,))
+    W, dW = riemann_x_state(mesh, left=state, right=state)
+    return mesh, W, dW
+
+
+def shu_osher_case(nx=200, nyz=2, jitter=0.0, seed=4):
+    """Shu-Osher problem (Sec. 5.2) on [0,10]x[0,0.1]^2, nx x nyz x nyz hexes
+    x 6 tets, y, z periodic, x ends open."""
+    mesh = box_mesh((nx, nyz, nyz), (10.0, 0.1, 0.1), (False, True, True), jitter, seed)
+    W, dW = shu_osher_state(mesh)
+    return mesh, W, dW
+
+
+def blast_wave_case(nx=200, nyz=2, jitter=0.0, seed=6):
+    """Woodward-Colella blast wave (Sec. 5.2) on [0,1]x[0,0.01]^2 with
+    reflecting (slip-wall) ends, nx x nyz x nyz hexes x 6 tets, y, z
+    periodic."""
+    mesh = box_mesh((nx, nyz, nyz), (1.0, 0.01, 0.01), (False, True, True), jitter, seed)
+    mesh["bkind"] = wall_kinds(mesh, (0,))
+    W, dW = blast_wave_state(mesh)
+    return mesh, W, dW
+
+
 def batch_mesh(meshes):
     """Disjoint union of meshes: vertex ids offset, cells grouped by case.
     Adds ``case`` (int32 per tet) and per-case ``period`` [ncase, 3]."""
@@ -403,9 +524,13 @@ def batch_mesh(meshes):
         case.append(np.full(m["tet"].shape[0], k, dtype=np.int32))
         period.append(m["period"])
         off += m["xyz"].shape[0]
-    return {"xyz": np.concatenate(xyz), "tet": np.concatenate(tet), "shift": np.concatenate(shift),
-            "case": np.concatenate(case), "period": np.stack(period), "ncase": len(meshes),
-            "case_cells": np.array([m["tet"].shape[0] for m in meshes])}
+    out = {"xyz": np.concatenate(xyz), "tet": np.concatenate(tet), "shift": np.concatenate(shift),
+           "case": np.concatenate(case), "period": np.stack(period), "ncase": len(meshes),
+           "case_cells": np.array([m["tet"].shape[0] for m in meshes])}
+    if any(m.get("bkind") is not None for m in meshes):
+        out["bkind"] = np.concatenate([m["bkind"] if m.get("bkind") is not None
+                                       else np.zeros(m["tet"].shape, np.int8) for m in meshes])
+    return out
 
 
 def riemann_slab_state(mesh, inner=(1.0, 1.0), outer=(0.125, 0.1), mach=1.0, x0=0.25, x1=0.75,
