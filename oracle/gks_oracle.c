@@ -61,6 +61,8 @@ struct ora_mesh {
     int64_t n_singular;
     /* boundary kind of each face (ORA_BC_*), meaningful on boundary faces */
     int8_t* bkind;      /* [nf] */
+    /* the fixed boundary state: a copy of W[5][nc], dW[15][nc] (or NULL) */
+    double *fixW, *fixdW;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -523,10 +525,19 @@ int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
         for (int f = 0; f < 4; ++f) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             int8_t k = kind[c * 4 + f];
-            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL) return -1;
+            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED) return -1;
             m->bkind[m->csr_face[c * 4 + f]] = k;
         }
     return 0;
+}
+
+void ora_mesh_set_fixed_state(ora_mesh* m, const double* W, const double* dW) {
+    free(m->fixW);
+    free(m->fixdW);
+    m->fixW = (double*)malloc(sizeof(double) * 5 * m->nc);
+    m->fixdW = (double*)malloc(sizeof(double) * 15 * m->nc);
+    memcpy(m->fixW, W, sizeof(double) * 5 * m->nc);
+    memcpy(m->fixdW, dW, sizeof(double) * 15 * m->nc);
 }
 
 void ora_mesh_free(ora_mesh* m) {
@@ -536,7 +547,7 @@ void ora_mesh_free(ora_mesh* m) {
     free(m->csr_face); free(m->csr_sign);
     free(m->vol); free(m->cen); free(m->mom2); free(m->dr);
     free(m->farea); free(m->fnorm); free(m->gp_l); free(m->gp_r);
-    free(m->M1); free(m->M2); free(m->bkind);
+    free(m->M1); free(m->M2); free(m->bkind); free(m->fixW); free(m->fixdW);
     free(m);
 }
 
@@ -1137,6 +1148,10 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                      const double* dW, double dt, int stage, double* rec) {
     const int64_t nc = m->nc;
     const int nrec = stage == 1 ? 40 : 20;
+    if (!m->fixW)
+        for (int64_t f = 0; f < m->nf; ++f)
+            if ((m->face_lr[f * 2] < 0 || m->face_lr[f * 2 + 1] < 0) && m->bkind[f] == ORA_BC_FIXED)
+                return -1; /* a fixed boundary without its state */
     double* poly_ = (double*)malloc(sizeof(double) * nc * 50);
     ora_reconstruct(m, p, W, dW, poly_, NULL, NULL);
     for (int64_t f = 0; f < m->nf; ++f) {
@@ -1174,6 +1189,25 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                 for (int q = 0; q < 5; ++q) {
                     Wg[q] = W[q * nc + inner];
                     gg[0][q] = gg[1][q] = gg[2][q] = 0.0;
+                }
+            }
+            /* a fixed boundary's ghost is the fixed state of the interior
+             * cell (its average and gradient) extended linearly to the
+             * Gauss point, with that gradient: a prescribed profile carried
+             * past the boundary (the Shu-Osher right end, Sec. 5.2; a far
+             * field, Sec. 5) */
+            for (int side = 0; side < 2; ++side) {
+                int64_t inner = side == 0 ? cr : cl;
+                if ((side == 0 ? cl : cr) >= 0 || m->bkind[f] != ORA_BC_FIXED) continue;
+                const double* X = side == 0 ? &m->gp_r[f * 9 + k * 3] : &m->gp_l[f * 9 + k * 3];
+                double* Wg = side == 0 ? WL : WR;
+                double (*gg)[5] = side == 0 ? gL : gR;
+                for (int q = 0; q < 5; ++q) {
+                    Wg[q] = m->fixW[q * nc + inner];
+                    for (int i = 0; i < 3; ++i) {
+                        gg[i][q] = m->fixdW[(3 * q + i) * nc + inner];
+                        Wg[q] += gg[i][q] * X[i];
+                    }
                 }
             }
             /* a slip wall's ghost is built from the interior Gauss-point
@@ -1297,7 +1331,10 @@ int ora_step(const ora_mesh* m, const ora_params* p, double* W, double* dW,
     double* dWs = (double*)malloc(sizeof(double) * nc * 15);
     double* S = (double*)malloc(sizeof(double) * nc * 5);
     double* G = (double*)malloc(sizeof(double) * nc * 15);
-    ora_face_records(m, p, W, dW, dt, 1, rec1);
+    if (ora_face_records(m, p, W, dW, dt, 1, rec1) != 0) {
+        free(rec1); free(rec2); free(Ws); free(dWs); free(S); free(G);
+        return -1;
+    }
     for (int64_t c = 0; c < nc; ++c) {
         double fh[5] = {0}, s[5] = {0}, gs[15] = {0}, g0[15] = {0};
         for (int f = 0; f < 4; ++f) {

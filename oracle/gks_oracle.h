@@ -38,12 +38,16 @@ ora_mesh* ora_mesh_build(const double* xyz, int64_t nv, const int64_t* tet,
 void ora_mesh_free(ora_mesh* m);
 
 /* Boundary condition of the boundary faces (faces with one cell). */
-enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1 };
+enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2 };
 /* kind[nc][4]: the condition of local face f (opposite vertex f) of cell c,
  * read only where that face is on the boundary.  Default: all open.
  * Returns -1 (mesh unchanged only up to the offending face) on a value
  * that is not one of ORA_BC_*. */
 int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind);
+/* The state a fixed boundary (ORA_BC_FIXED) holds: W[5][nc], dW[15][nc] of
+ * the cells (read at the interior cell of each fixed face; copied).  Face
+ * records and steps return -1 while a fixed face has no state. */
+void ora_mesh_set_fixed_state(ora_mesh* m, const double* W, const double* dW);
 int64_t ora_mesh_nc(const ora_mesh* m);
 int64_t ora_mesh_nf(const ora_mesh* m);
 int64_t ora_mesh_n_singular(const ora_mesh* m);

@@ -58,6 +58,7 @@ def lib():
         L.ora_mesh_free.argtypes = [C.c_void_p]
         L.ora_mesh_set_boundary.restype = C.c_int
         L.ora_mesh_set_boundary.argtypes = [C.c_void_p, _bp]
+        L.ora_mesh_set_fixed_state.argtypes = [C.c_void_p, _dp, _dp]
         for fn in ("ora_mesh_nc", "ora_mesh_nf", "ora_mesh_n_singular"):
             getattr(L, fn).restype = C.c_int64
             getattr(L, fn).argtypes = [C.c_void_p]
@@ -97,6 +98,8 @@ class Mesh:
         self.n_singular = L.ora_mesh_n_singular(self._h)
         if mesh.get("bkind") is not None:
             self.set_boundary(mesh["bkind"])
+        if mesh.get("fixed_state") is not None:
+            self.set_fixed_state(*mesh["fixed_state"])
 
     def set_boundary(self, kind):
         """kind[nc][4]: 0 open, 1 slip wall, per local face (read on boundary
@@ -104,6 +107,11 @@ class Mesh:
         kind = np.ascontiguousarray(kind, dtype=np.int8).reshape(self.nc, 4)
         if lib().ora_mesh_set_boundary(self._h, kind) != 0:
             raise ValueError("oracle mesh: invalid boundary kind")
+
+    def set_fixed_state(self, W, dW):
+        """The state fixed boundaries (kind 2) hold: W[5][nc], dW[15][nc]."""
+        lib().ora_mesh_set_fixed_state(self._h, np.ascontiguousarray(W, dtype=np.float64),
+                                       np.ascontiguousarray(dW, dtype=np.float64))
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -144,8 +152,9 @@ class Mesh:
 
     def face_records(self, p, W, dW, dt, stage):
         rec = np.zeros((self.nf, 40 if stage == 1 else 20))
-        lib().ora_face_records(self._h, C.byref(p), np.ascontiguousarray(W, dtype=np.float64),
-                               np.ascontiguousarray(dW, dtype=np.float64), dt, stage, rec)
+        if lib().ora_face_records(self._h, C.byref(p), np.ascontiguousarray(W, dtype=np.float64),
+                                  np.ascontiguousarray(dW, dtype=np.float64), dt, stage, rec) != 0:
+            raise ValueError("oracle: a fixed boundary face has no state")
         return rec
 
     def timestep(self, p, W):
@@ -156,7 +165,8 @@ class Mesh:
         W = np.array(W, dtype=np.float64, order="C", copy=True)
         dW = np.array(dW, dtype=np.float64, order="C", copy=True)
         used = C.c_double(0.0)
-        lib().ora_step(self._h, C.byref(p), W, dW, float(dt), C.byref(used))
+        if lib().ora_step(self._h, C.byref(p), W, dW, float(dt), C.byref(used)) != 0:
+            raise ValueError("oracle: a fixed boundary face has no state")
         return W, dW, used.value
 
     def run(self, p, W, dW, nsteps=None, t_end=None, dt=0.0):

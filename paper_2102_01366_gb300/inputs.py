@@ -364,24 +364,32 @@ def riemann_x_exact_density(mesh, t, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.
     return cell_average(mesh, f, order=order)[:, 0]
 
 
-def wall_kinds(mesh, axes):
+BC_OPEN, BC_SLIP_WALL, BC_FIXED = 0, 1, 2
+
+
+def boundary_kinds(mesh, spec):
     """Boundary kind per local face, int8 [nc, 4] (face f is opposite tet
-    vertex f): 1 (slip wall) where the face lies on an end plane of one of the
-    non-periodic ``axes`` (the planes are the extreme vertex coordinates; the
-    generator jitters end-plane vertices only tangentially), else 0 (open)."""
+    vertex f).  ``spec`` maps (axis, "lo" | "hi") to a kind for the faces on
+    that end plane of a non-periodic axis (the planes are the extreme vertex
+    coordinates; the generator jitters end-plane vertices only tangentially);
+    every other face gets BC_OPEN."""
     xyz = mesh["xyz"]
     tet = mesh["tet"]
     kind = np.zeros(tet.shape, dtype=np.int8)
-    for a in axes:
+    for (a, end), k in spec.items():
         if mesh["period"][..., a].any():
             raise ValueError("axis %d is periodic" % a)
-        coord = xyz[tet, a]  # [nc, 4]
-        for plane in (xyz[:, a].min(), xyz[:, a].max()):
-            on = coord == plane
-            for f in range(4):
-                others = [v for v in range(4) if v != f]
-                kind[on[:, others].all(axis=1), f] = 1
+        plane = xyz[:, a].min() if end == "lo" else xyz[:, a].max()
+        on = xyz[tet, a] == plane  # [nc, 4]
+        for f in range(4):
+            others = [v for v in range(4) if v != f]
+            kind[on[:, others].all(axis=1), f] = k
     return kind
+
+
+def wall_kinds(mesh, axes):
+    """Slip walls (BC_SLIP_WALL) on both end planes of the given axes."""
+    return boundary_kinds(mesh, {(a, e): BC_SLIP_WALL for a in axes for e in ("lo", "hi")})
 
 
 def wall_reflection_exact_density(mesh, t, state=(1.0, 1.0, 1.0), length=1.0, gamma=1.4,
@@ -496,9 +504,13 @@ def wall_reflection_case(nx=64, nyz=4, state=(1.0, 1.0, 1.0), jitter=0.1, seed=3
 
 def shu_osher_case(nx=200, nyz=2, jitter=0.0, seed=4):
     """Shu-Osher problem (Sec. 5.2) on [0,10]x[0,0.1]^2, nx x nyz x nyz hexes
-    x 6 tets, y, z periodic, x ends open."""
+    x 6 tets, y, z periodic.  Left end open (the supersonic inflow keeps its
+    state), right end fixed to the initial profile (the wave profile carried
+    past the boundary); ``fixed_state`` is that initial state."""
     mesh = box_mesh((nx, nyz, nyz), (10.0, 0.1, 0.1), (False, True, True), jitter, seed)
+    mesh["bkind"] = boundary_kinds(mesh, {(0, "hi"): BC_FIXED})
     W, dW = shu_osher_state(mesh)
+    mesh["fixed_state"] = (W, dW)
     return mesh, W, dW
 
 

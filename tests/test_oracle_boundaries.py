@@ -1,11 +1,20 @@
-"""Slip walls (Sec. 4.4) in the oracle, pinned by what the mirror image
+"""Boundary faces in the oracle.
+
+Slip walls (Sec. 4.4), pinned by what the mirror image
 across a wall fixes independently of the oracle's formulas: no mass, energy
 or tangential momentum crosses a wall (the ghost is the exact mirror of the
 interior state at every Gauss point), a gas at rest in a closed box stays at
 rest, a closed box conserves mass, energy and the tangential momenta, and a
 gas moving between two walls reproduces the exact reflected-shock /
 wall-rarefaction solution (each wave the Riemann problem between the gas and
-its mirror image) with an error that falls under refinement."""
+its mirror image) with an error that falls under refinement.
+
+Fixed boundaries (a prescribed state carried past the boundary: the
+Shu-Osher right end of Sec. 5.2, a far field), pinned by a stationary
+contact: a linear density profile at rest under uniform pressure is an exact
+steady solution that the scheme reproduces to round-off when the ghost holds
+the profile's value and gradient at each Gauss point, and visibly does not
+with open ends."""
 import numpy as np
 import pytest
 
@@ -108,3 +117,50 @@ def test_wall_reflection_against_exact_solution(oracle_mod):
         l1.append(float((np.abs(W1[0] - exact) * vol).sum() / vol.sum()))
     assert l1[0] < 0.03, l1
     assert l1[1] < 0.8 * l1[0], l1
+
+
+def _contact(seed=51):
+    mesh = I.box_mesh((6, 2, 2), (1.0, 1 / 3, 1 / 3), (False, True, True), jitter=0.1, seed=seed)
+
+    def lin(x):
+        rho = 1.0 + 0.3 * x[..., 0]
+        z = np.zeros_like(rho)
+        return np.stack([rho, z, z, z, np.full_like(rho, 1.0 / 0.4)], axis=-1)
+    W = I.cell_average(mesh, lin, order=3).T.copy()
+    dW = np.zeros((15, W.shape[1]))
+    dW[0] = 0.3
+    return mesh, W, dW
+
+
+@pytest.mark.parametrize("weno", [0, 1])
+def test_fixed_boundary_keeps_a_stationary_contact(oracle_mod, weno):
+    mesh, W, dW = _contact()
+    change = {}
+    for kind in (I.BC_OPEN, I.BC_FIXED):
+        m = dict(mesh)
+        m["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
+        m["fixed_state"] = (W, dW)
+        om = oracle_mod.Mesh(m)
+        W1, dW1, _, _ = om.run(oracle_mod.params(weno=weno, cfl=0.5), W, dW, nsteps=3)
+        change[kind] = (np.abs(W1 - W).max(), np.abs(dW1 - dW).max())
+    assert change[I.BC_FIXED][0] < 1e-14 and change[I.BC_FIXED][1] < 1e-12, change
+    assert change[I.BC_OPEN][0] > 1e-3, change
+
+
+def test_uniform_flow_through_fixed_boundaries(oracle_mod):
+    mesh = I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=52)
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_FIXED, (0, "hi"): I.BC_FIXED})
+    W, dW = I.riemann_x_state(mesh, left=(1.2, 1.5, 0.8), right=(1.2, 1.5, 0.8))
+    mesh["fixed_state"] = (W, dW)
+    om = oracle_mod.Mesh(mesh)
+    W1, dW1, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, nsteps=3)
+    assert np.abs(W1 - W).max() < 1e-13
+    assert np.abs(dW1).max() < 1e-11
+
+
+def test_fixed_boundary_needs_its_state(oracle_mod):
+    mesh, W, dW = _contact()
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "hi"): I.BC_FIXED})
+    om = oracle_mod.Mesh(mesh)
+    with pytest.raises(ValueError):
+        om.step(oracle_mod.params(weno=1), W, dW)
