@@ -114,6 +114,35 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
                                  const int8_t* shift, int64_t n_cell, const int32_t* tet_case,
                                  int32_t n_case, const double* period, gks_mesh** out);
 
+/* Boundary conditions of the boundary faces (faces with one cell):
+ *   GKS_BC_OPEN       ghost side = the interior cell's average with zero
+ *                     gradient (outflow by zeroth-order extrapolation; the
+ *                     default)
+ *   GKS_BC_SLIP_WALL  Sec. 4.4 slip wall: at each Gauss point the ghost is
+ *                     the mirror image of the interior reconstruction in the
+ *                     face frame (normal momentum reversed; normal derivatives
+ *                     reversed except that of the normal momentum; tangential
+ *                     derivatives of the normal momentum reversed)
+ *   GKS_BC_FIXED      a prescribed state carried past the boundary (the
+ *                     Shu-Osher right end of Sec. 5.2; a far field): the
+ *                     ghost at each Gauss point is the interior cell's fixed
+ *                     state, its average plus its gradient times the offset
+ *                     from the centroid, with that gradient.  The fixed state
+ *                     is the state given to gks_init_state (or gks_step_host)
+ *                     and holds until the next such call; a mesh with fixed
+ *                     faces needs 20 more working-precision reals a cell of
+ *                     workspace.
+ * The interior reconstruction of a boundary cell is the one-sided one of
+ * Sec. 4.4 (no constraint for these kinds): the cell's stencil simply lacks
+ * the missing neighbour. */
+enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2 };
+
+/* kind[n_cell][4] (host): the condition of local face f (the face opposite
+ * tet vertex f) of each cell, read only where that face is a boundary face.
+ * Applies to states created afterwards (and to gks_workspace_bytes).  GKS_E_ARG on a NULL argument or an
+ * unknown kind on a boundary face (the mesh keeps its previous kinds). */
+gks_status gks_mesh_set_boundary(gks_mesh* mesh, const int8_t* kind);
+
 /* Number of cases and case_first_cell[n_case + 1] (first cell of each case
  * and n_cell at the end; may be NULL). */
 gks_status gks_mesh_cases(const gks_mesh* mesh, int32_t* n_case, int64_t* case_first_cell);

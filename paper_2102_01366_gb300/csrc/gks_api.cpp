@@ -168,6 +168,24 @@ extern "C" gks_status gks_mesh_info(const gks_mesh* m, int64_t* n_cell, int64_t*
     return GKS_OK;
 }
 
+extern "C" gks_status gks_mesh_set_boundary(gks_mesh* m, const int8_t* kind) {
+    if (!m || !kind) { set_error("gks_mesh_set_boundary: NULL argument"); return GKS_E_ARG; }
+    std::vector<int8_t> bk((size_t)m->nf, 0);
+    for (int64_t c = 0; c < m->nc; ++c)
+        for (int f = 0; f < 4; ++f) {
+            if (m->nbr[c * 4 + f] >= 0) continue;
+            const int8_t k = kind[c * 4 + f];
+            if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED) {
+                set_error("gks_mesh_set_boundary: unknown kind " + std::to_string((int)k) + " at cell " +
+                          std::to_string(c) + " face " + std::to_string(f));
+                return GKS_E_ARG;
+            }
+            bk[(size_t)m->csr_face[c * 4 + f]] = k;
+        }
+    m->bkind.swap(bk);
+    return GKS_OK;
+}
+
 extern "C" gks_status gks_mesh_cases(const gks_mesh* m, int32_t* n_case, int64_t* case_first_cell) {
     if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
     if (n_case) *n_case = m->ncase;
@@ -243,7 +261,7 @@ struct Layout {
     // mesh
     size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case, perm;
     // state
-    size_t Wd, X, Xs, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
+    size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -251,7 +269,13 @@ struct Layout {
     }
 };
 
-Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
+bool has_fixed(const gks_mesh& m) {
+    for (int64_t f = 0; f < m.nf; ++f)
+        if (m.bkind[f] == GKS_BC_FIXED) return true;
+    return false;
+}
+
+Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool fixed) {
     Layout L;
     const size_t T = fp32 ? 4 : 8;
     const size_t nblk = (size_t)update_blocks(nc);
@@ -272,6 +296,7 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32) {
     L.Wd = L.add(8 * 5 * nc);
     L.X = L.add(T * XS * nc);
     L.Xs = L.add(T * XS * nc);
+    L.X0 = fixed ? L.add(T * XS * nc) : 0;  // state held by fixed boundary faces
     L.S = L.add(8 * 5 * nc);
     L.G = L.add(T * 15 * nc);
     L.slopes = L.add(T * 15 * nc);
@@ -335,6 +360,7 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.M2 = at<T>(s, L.M2);
     m.flr = at<int32_t>(s, L.flr);
     m.fgeo = at<T>(s, L.fgeo);
+    m.fixed = L.X0 ? at<T>(s, L.X0) : nullptr;
     st.Wd = at<double>(s, L.Wd);
     st.X = at<T>(s, L.X);
     st.Xs = at<T>(s, L.Xs);
@@ -385,8 +411,10 @@ static gks_status upload_faces(gks_state* s) {
         }
     for (int64_t d = 0; d < nf; ++d) {
         const int64_t f = perm[d];
-        flr[d] = (int32_t)g.face_lr[f * 2];
-        flr[nf + d] = (int32_t)g.face_lr[f * 2 + 1];
+        // a boundary face's missing side carries its kind: -1 - GKS_BC_*
+        const int32_t miss = -1 - (int32_t)g.bkind[f];
+        flr[d] = g.face_lr[f * 2] >= 0 ? (int32_t)g.face_lr[f * 2] : miss;
+        flr[nf + d] = g.face_lr[f * 2 + 1] >= 0 ? (int32_t)g.face_lr[f * 2 + 1] : miss;
         T* r = &fgeo[d * FGEO];
         for (int a = 0; a < 3; ++a) r[a] = (T)g.fnorm[f * 3 + a];
         r[3] = (T)(g.farea[f] / 3.0);
@@ -451,7 +479,7 @@ static gks_status upload_mesh(gks_state* s) {
 
 extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
     if (!mesh || check_params(params) != GKS_OK) return 0;
-    return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision == 1).total;
+    return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision == 1, has_fixed(*mesh)).total;
 }
 
 extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
@@ -464,7 +492,7 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     if (ps != GKS_OK) return ps;
     if (!mesh->has_stencils) { set_error("gks_state_create: stencils not built"); return GKS_E_STENCIL; }
     const bool fp32 = params->precision == 1;
-    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32);
+    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32, has_fixed(*mesh));
     if (!d_workspace || workspace_bytes < L.total) {
         set_error("gks_state_create: workspace missing or smaller than gks_workspace_bytes()");
         return GKS_E_NOMEM;
@@ -538,6 +566,8 @@ static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const 
     const int64_t nc = m.nc;
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, d_dW, st.X, nc, s->stream));
+    if (m.fixed)  // fixed boundaries hold the initial state
+        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(launch_set_control(st.ctrl, st.case_t, st.case_dt, st.case_dtmin, m.ncase, 0.0, 0.0, 1, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
@@ -764,6 +794,8 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
     GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
+    if (m.fixed)
+        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(set_control(s, 0.0, 0.0, 1));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
     s->initialised = true;

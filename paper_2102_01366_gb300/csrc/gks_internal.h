@@ -25,6 +25,7 @@ struct gks_mesh {
     std::vector<int32_t> nbr_img;    // nc*12 image shift, own frame -> neighbour
     std::vector<int64_t> csr_face;   // nc*4
     std::vector<int8_t> csr_sign;    // nc*4
+    std::vector<int8_t> bkind;       // nf, GKS_BC_* of boundary faces (0 elsewhere)
     // FP64 geometry
     std::vector<double> vol, cen, mom2, dr;       // nc, nc*3, nc*6, nc
     std::vector<double> farea, fnorm, gp_l, gp_r; // nf, nf*3, nf*9, nf*9

@@ -432,6 +432,40 @@ __device__ __forceinline__ void to_local(const T (*Rm)[3], const T* W, const T (
     }
 }
 
+// Slip-wall ghost (Sec. 4.4) of a state already in the face frame (x1 along
+// the normal): the mirror image across the wall.  rho U1 changes sign; of the
+// x1-derivatives all but that of rho U1 change sign; of the x2-, x3-derivatives
+// only those of rho U1 do.
+template <typename T>
+__device__ __forceinline__ void slip_wall_ghost(T* Wt, T (*gt)[5]) {
+    Wt[1] = -Wt[1];
+    gt[0][0] = -gt[0][0];
+    gt[0][2] = -gt[0][2];
+    gt[0][3] = -gt[0][3];
+    gt[0][4] = -gt[0][4];
+    gt[1][1] = -gt[1][1];
+    gt[2][1] = -gt[2][1];
+}
+
+// device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
+constexpr int FLR_OPEN = -1, FLR_SLIP_WALL = -2, FLR_FIXED = -3;
+
+// fixed boundary: the interior cell's fixed state (average and gradient)
+// extended linearly to the point X (relative to the cell's centroid)
+template <typename T>
+__device__ __forceinline__ void fixed_ghost(const T* __restrict__ x0, const T* X, T* W, T (*g)[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        T v = x0[q];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[i][q] = x0[5 + 3 * q + i];
+            v += g[i][q] * X[i];
+        }
+        W[q] = v;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
     const T a = v[1], b = v[2], c = v[3];
@@ -486,10 +520,19 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 
     // ---- phase 1 ----
     const int mine = side == 0 ? L : Rc;
+    const bool wall = mine == FLR_SLIP_WALL;
     T Ws[5], gs[3][5];
-    if (mine >= 0) {
-        const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
-        eval_poly(poly + (int64_t)mine * POLY_STRIDE, X, Ws, gs);
+    if (mine >= 0 || wall) {
+        // a wall side starts from the interior cell's value at the point
+        const int src = mine >= 0 ? side : 1 - side;
+        const int64_t cell = mine >= 0 ? mine : (side == 0 ? Rc : L);
+        const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+        eval_poly(poly + cell * POLY_STRIDE, X, Ws, gs);
+    } else if (mine == FLR_FIXED) {
+        const int64_t in = side == 0 ? Rc : L;
+        const int src = 1 - side;
+        const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+        fixed_ghost(m.fixed + in * XS, X, Ws, gs);
     } else {
         // open boundary: the missing side is the interior cell's average with
         // zero gradient (zeroth-order extrapolation; the paper leaves outflow
@@ -506,6 +549,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     face_frame(n, Rm);
     T tW[5], tg[3][5];
     to_local(Rm, Ws, gs, tW, tg);
+    if (wall) slip_wall_ghost(tW, tg);
     const Prim<T> S = to_prim(tW, ph.gm1);
     Tab<T> t;
     T a[3][5], A[5];
@@ -698,9 +742,17 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
             const int cell = side == 0 ? L : Rc;
             T* Wv = side == 0 ? WL : WR;
             T (*g)[5] = side == 0 ? gL : gR;
-            if (cell >= 0) {
-                const T X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
-                eval_poly(poly + (int64_t)cell * POLY_STRIDE, X, Wv, g);
+            if (cell >= 0 || cell == FLR_SLIP_WALL) {
+                // a wall side starts from the interior cell's value at the point
+                const int src = cell >= 0 ? side : 1 - side;
+                const int64_t c = cell >= 0 ? cell : (side == 0 ? Rc : L);
+                const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+                eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
+            } else if (cell == FLR_FIXED) {
+                const int64_t in = side == 0 ? Rc : L;
+                const int src = 1 - side;
+                const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+                fixed_ghost(m.fixed + in * XS, X, Wv, g);
             } else {
                 // open boundary: interior cell average, zero gradient
                 const int64_t in = side == 0 ? Rc : L;
@@ -715,6 +767,8 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
         T tWL[5], tgL[3][5], tWR[5], tgR[3][5];
         to_local(Rm, WL, gL, tWL, tgL);
         to_local(Rm, WR, gR, tWR, tgR);
+        if (L == FLR_SLIP_WALL) slip_wall_ghost(tWL, tgL);
+        if (Rc == FLR_SLIP_WALL) slip_wall_ghost(tWR, tgR);
         T Fh[5], D[5], W0[5], dWt[5];
         gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, D, W0, dWt);
         to_global(Rm, Fh);

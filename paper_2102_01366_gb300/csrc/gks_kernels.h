@@ -38,6 +38,7 @@ struct DevMesh {
     const T* M2;           // [144][nc]
     const int32_t* flr;    // [2][nf]
     const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
+    const T* fixed;        // [nc][XS] state held by fixed boundary faces (NULL: none)
 };
 
 template <typename T>

@@ -128,6 +128,7 @@ gks_status build_mesh(gks_mesh& m) {
     m.nf = nf;
     m.face_v.assign((size_t)nf * 3, 0);
     m.face_lr.assign((size_t)nf * 2, -1);
+    m.bkind.assign((size_t)nf, 0);
     m.nbr.assign((size_t)nc * 4, -1);
     m.nbr_img.assign((size_t)nc * 12, 0);
     m.csr_face.assign((size_t)nc * 4, -1);

@@ -62,6 +62,7 @@ def lib():
         "gks_mesh_create_cases": (C.c_int32, [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp,
                                               C.POINTER(_vp)]),
         "gks_mesh_cases": (C.c_int32, [_vp, C.POINTER(C.c_int32), _vp]),
+        "gks_mesh_set_boundary": (C.c_int32, [_vp, _vp]),
         "gks_case_times": (C.c_int32, [_vp, _vp, _vp]),
         "gks_mesh_destroy": (None, [_vp]),
         "gks_mesh_info": (C.c_int32, [_vp, _i64p, _i64p, _i64p]),
@@ -141,10 +142,18 @@ class Mesh:
         self.case_first = np.zeros(self.ncase + 1, np.int64)
         _call("gks_mesh_cases", self._h, C.byref(ncase), _np_ptr(self.case_first))
         self.n_singular = None
+        if mesh.get("bkind") is not None:
+            self.set_boundary(mesh["bkind"])
         if build_stencils:
             ns = C.c_int64()
             _call("gks_stencil_build", self._h, C.byref(ns))
             self.n_singular = ns.value
+
+    def set_boundary(self, kind):
+        """kind[nc][4] (GKS_BC_OPEN 0, GKS_BC_SLIP_WALL 1) per local face; read
+        on boundary faces only; applies to states created afterwards."""
+        kind = np.ascontiguousarray(kind, dtype=np.int8).reshape(self.nc, 4)
+        _call("gks_mesh_set_boundary", self._h, _np_ptr(kind))
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value and _lib is not None:

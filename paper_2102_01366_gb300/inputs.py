@@ -504,11 +504,12 @@ def wall_reflection_case(nx=64, nyz=4, state=(1.0, 1.0, 1.0), jitter=0.1, seed=3
 
 def shu_osher_case(nx=200, nyz=2, jitter=0.0, seed=4):
     """Shu-Osher problem (Sec. 5.2) on [0,10]x[0,0.1]^2, nx x nyz x nyz hexes
-    x 6 tets, y, z periodic.  Left end open (the supersonic inflow keeps its
-    state), right end fixed to the initial profile (the wave profile carried
-    past the boundary); ``fixed_state`` is that initial state."""
+    x 6 tets, y, z periodic.  Both x ends fixed to the initial state: on the
+    left the supersonic inflow (every characteristic enters, so holding the
+    inflow state is the non-reflecting condition), on the right the wave
+    profile carried past the boundary; ``fixed_state`` is that state."""
     mesh = box_mesh((nx, nyz, nyz), (10.0, 0.1, 0.1), (False, True, True), jitter, seed)
-    mesh["bkind"] = boundary_kinds(mesh, {(0, "hi"): BC_FIXED})
+    mesh["bkind"] = boundary_kinds(mesh, {(0, "lo"): BC_FIXED, (0, "hi"): BC_FIXED})
     W, dW = shu_osher_state(mesh)
     mesh["fixed_state"] = (W, dW)
     return mesh, W, dW
