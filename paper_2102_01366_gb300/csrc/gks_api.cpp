@@ -259,7 +259,7 @@ namespace {
 struct Layout {
     size_t total = 0;
     // mesh
-    size_t nbr, cface, inv_vol, vol23, vol43, dr, mom2, cgp, M1, M2, flr, fgeo, cell_case, perm;
+    size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, cell_case, perm;
     // state
     size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
@@ -282,13 +282,9 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool f
     L.nbr = L.add(4 * 4 * nc);
     L.cface = L.add(4 * 4 * nc);
     L.inv_vol = L.add(8 * nc);
-    L.vol23 = L.add(T * nc);
-    L.vol43 = L.add(T * nc);
     L.dr = L.add(T * nc);
-    L.mom2 = L.add(T * 6 * nc);
-    L.cgp = L.add(T * 36 * nc);
     L.M1 = L.add(T * 12 * nc);
-    L.M2 = L.add(T * 144 * nc);
+    L.tile = L.add(T * TILE_ROWS * CELLS_PER_BLOCK * nblk);
     L.flr = L.add(4 * 2 * nf);
     L.fgeo = L.add(T * FGEO * nf);
     L.cell_case = L.add(4 * nc);
@@ -351,13 +347,9 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.nbr = at<int32_t>(s, L.nbr);
     m.cface = at<int32_t>(s, L.cface);
     m.inv_vol = at<double>(s, L.inv_vol);
-    m.vol23 = at<T>(s, L.vol23);
-    m.vol43 = at<T>(s, L.vol43);
     m.dr = at<T>(s, L.dr);
-    m.mom2 = at<T>(s, L.mom2);
-    m.cgp = at<T>(s, L.cgp);
     m.M1 = at<T>(s, L.M1);
-    m.M2 = at<T>(s, L.M2);
+    m.tile = at<T>(s, L.tile);
     m.flr = at<int32_t>(s, L.flr);
     m.fgeo = at<T>(s, L.fgeo);
     m.fixed = L.X0 ? at<T>(s, L.X0) : nullptr;
@@ -441,35 +433,39 @@ static gks_status upload_mesh(gks_state* s) {
     const Layout& L = s->L;
     std::vector<int32_t> nbr(4 * nc);
     std::vector<double> inv_vol(nc);
-    std::vector<T> vol23(nc), vol43(nc), dr(nc), mom2(6 * nc), cgp(36 * nc), M1(12 * nc), M2(144 * nc);
+    const int64_t nblk = update_blocks(nc);
+    std::vector<T> dr(nc), M1(12 * nc);
+    // per-block tile [blk][TILE_ROWS][CELLS_PER_BLOCK], zero past the last cell
+    std::vector<T> tile((size_t)nblk * TILE_ROWS * CELLS_PER_BLOCK, T(0));
     for (int64_t c = 0; c < nc; ++c) {
+        T* tc = &tile[(size_t)(c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK];
+        auto put_row = [&](int row, double v) { tc[(size_t)row * CELLS_PER_BLOCK] = (T)v; };
         for (int f = 0; f < 4; ++f) {
             nbr[f * nc + c] = (int32_t)g.nbr[c * 4 + f];
             const int64_t fi = g.csr_face[c * 4 + f];
             const bool left = g.csr_sign[c * 4 + f] > 0;
             const double* gp = left ? &g.gp_l[fi * 9] : &g.gp_r[fi * 9];
-            for (int k = 0; k < 9; ++k) cgp[(f * 9 + k) * nc + c] = (T)gp[k];
+            for (int k = 0; k < 9; ++k) put_row(TILE_G + f * 9 + k, gp[k]);
         }
         inv_vol[c] = 1.0 / g.vol[c];
-        vol23[c] = (T)std::pow(g.vol[c], 2.0 / 3.0);
-        vol43[c] = (T)std::pow(g.vol[c], 4.0 / 3.0);
+        put_row(TILE_V23, std::pow(g.vol[c], 2.0 / 3.0));
+        put_row(TILE_V43, std::pow(g.vol[c], 4.0 / 3.0));
         dr[c] = (T)g.dr[c];
-        for (int q = 0; q < 6; ++q) mom2[q * nc + c] = (T)g.mom2[c * 6 + q];
-        for (int k = 0; k < 12; ++k) M1[k * nc + c] = (T)g.M1[c * 12 + k];
-        for (int k = 0; k < 144; ++k) M2[k * nc + c] = (T)g.M2[c * 144 + k];
+        for (int q = 0; q < 6; ++q) put_row(TILE_MOM + q, g.mom2[c * 6 + q]);
+        for (int k = 0; k < 12; ++k) {
+            M1[k * nc + c] = (T)g.M1[c * 12 + k];
+            put_row(TILE_M1 + k, g.M1[c * 12 + k]);
+        }
+        for (int k = 0; k < 144; ++k) put_row(TILE_M2 + k, g.M2[c * 144 + k]);
     }
     auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
     };
     GKS_CHECK_CUDA(put(L.nbr, nbr.data(), 4 * nbr.size()));
     GKS_CHECK_CUDA(put(L.inv_vol, inv_vol.data(), 8 * inv_vol.size()));
-    GKS_CHECK_CUDA(put(L.vol23, vol23.data(), sizeof(T) * vol23.size()));
-    GKS_CHECK_CUDA(put(L.vol43, vol43.data(), sizeof(T) * vol43.size()));
     GKS_CHECK_CUDA(put(L.dr, dr.data(), sizeof(T) * dr.size()));
-    GKS_CHECK_CUDA(put(L.mom2, mom2.data(), sizeof(T) * mom2.size()));
-    GKS_CHECK_CUDA(put(L.cgp, cgp.data(), sizeof(T) * cgp.size()));
     GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(T) * M1.size()));
-    GKS_CHECK_CUDA(put(L.M2, M2.data(), sizeof(T) * M2.size()));
+    GKS_CHECK_CUDA(put(L.tile, tile.data(), sizeof(T) * tile.size()));
     GKS_CHECK_CUDA(put(L.cell_case, g.cell_case.data(), 4 * g.cell_case.size()));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
@@ -594,9 +590,9 @@ static cudaError_t enqueue_recon(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     if (s->slopes_pass && p.weno) {
         cudaError_t e = Launch<T>::slopes(m, X, st.slopes, fin, s->stream);
         if (e != cudaSuccess) return e;
-        return Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, s->stream);
+        return Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, st.err, s->stream);
     }
-    return Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, fin, s->stream);
+    return Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, fin, st.err, s->stream);
 }
 
 // one two-stage step (Sec. 3): enqueued on s->stream (captured into a graph).
@@ -689,9 +685,10 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             if (s->slopes_pass && p.weno) {
                 if (e == cudaSuccess) e = Launch<T>::slopes(m, X, st.slopes, f, q);
                 if (e == cudaSuccess) e = mark(GKS_K_SLOPES);
-                if (e == cudaSuccess) e = Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, q);
+                if (e == cudaSuccess)
+                    e = Launch<T>::recon(m, p, X, st.slopes, nullptr, st.poly, nullptr, nullptr, st.err, q);
             } else if (e == cudaSuccess) {
-                e = Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, f, q);
+                e = Launch<T>::recon(m, p, X, nullptr, nullptr, st.poly, nullptr, f, st.err, q);
             }
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
             if (e == cudaSuccess) e = Launch<T>::flux(m, p, X, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant);
@@ -737,6 +734,10 @@ extern "C" gks_status gks_sync(gks_state* s) {
     int32_t err = 0;
     GKS_CHECK_CUDA(cudaMemcpyAsync(&err, s->fp32 ? s->s32.err : s->s64.err, 4, cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    if (err & ERR_TIMEOUT) {
+        set_error("a bounded device wait (reconstruction tile copy) gave up");
+        return GKS_E_TIMEOUT;
+    }
     if (err & ERR_STATE) {
         set_error("non-positive density or pressure in an updated cell average");
         return GKS_E_STATE;
@@ -862,7 +863,7 @@ static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st,
     const int64_t nc = m.nc;
     if (!need_b) GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
     GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.X, nullptr, need_b ? st.slopes : nullptr, st.poly, d_fallback,
-                                    nullptr, s->stream));
+                                    nullptr, st.err, s->stream));
     if (d_poly) GKS_CHECK_CUDA(Launch<T>::poly_to_double(st.poly, d_poly, nc, s->stream));
     if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
     return GKS_OK;

@@ -23,6 +23,52 @@
 
 namespace gks {
 
+// ---- bulk copy global -> shared with an mbarrier (sm_90+ async proxy) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also announces the bytes the copy will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait for phase `parity`: false if it gave up (each try_wait
+// already suspends for a while, so the bound is far beyond any copy time)
+constexpr int MBAR_TRIES = 1 << 16;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int i = 0; i < MBAR_TRIES; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 template <typename T>
 struct ReconConst {
     T gm1, eps;
@@ -171,8 +217,10 @@ __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restric
 }
 
 // reconstruction (Sec. 4.1-4.3): the cell's own P1 slopes and, for the
-// two-step beta_0, its neighbours' P1 slopes (recomputed here: reconstruction
-// step 1 needs no separate pass); P2 = M2 d with M2 staged in shared memory;
+// two-step beta_0, its neighbours' P1 slopes (recomputed here, or read from
+// a slopes pass); P2 = M2 d with the block's static data (M2, Gauss points,
+// M1, moments) brought into shared memory by one bulk copy that overlaps the
+// neighbour gathers;
 // smoothness indicators, nonlinear weights, positivity at the cell's 12 face
 // Gauss points (Sec. 4.2); R written about the centroid in monomial form
 template <typename T>
@@ -182,24 +230,19 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
                                                          T* __restrict__ slopes_out,
                                                          T* __restrict__ poly,
                                                          int32_t* __restrict__ fallback,
-                                                         FinArg<T> fin) {
-    __shared__ T sM2[144][CELLS_PER_BLOCK];
-    __shared__ T sG[36][CELLS_PER_BLOCK];
+                                                         FinArg<T> fin, int32_t* __restrict__ err) {
+    __shared__ alignas(128) T sT[TILE_ROWS][CELLS_PER_BLOCK];
+    __shared__ alignas(8) unsigned long long bar;
+    constexpr unsigned TILE_BYTES = TILE_ROWS * CELLS_PER_BLOCK * sizeof(T);
+    static_assert(TILE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();  // the barrier exists before anyone waits on it
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, TILE_BYTES);
+        bulk_load(&sT[0][0], m.tile + (int64_t)blockIdx.x * TILE_ROWS * CELLS_PER_BLOCK, TILE_BYTES, &bar);
+    }
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
     const int64_t nc = m.nc;
-    {
-        const int64_t cbase = (int64_t)blockIdx.x * CELLS_PER_BLOCK;
-        const int nloc = (int)min((int64_t)CELLS_PER_BLOCK, nc - cbase);
-        for (int idx = threadIdx.x; idx < 144 * CELLS_PER_BLOCK; idx += CELL_THREADS) {
-            const int row = idx / CELLS_PER_BLOCK, col = idx - row * CELLS_PER_BLOCK;
-            sM2[row][col] = col < nloc ? m.M2[row * nc + cbase + col] : T(0);
-        }
-        for (int idx = threadIdx.x; idx < 36 * CELLS_PER_BLOCK; idx += CELL_THREADS) {
-            const int row = idx / CELLS_PER_BLOCK, col = idx - row * CELLS_PER_BLOCK;
-            sG[row][col] = col < nloc ? m.cgp[row * nc + cbase + col] : T(0);
-        }
-    }
-    __syncthreads();
     const CellLane cl = cell_lane(nc);
     const int64_t c = cl.c;
     const int q = cl.q;
@@ -221,17 +264,21 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
 #pragma unroll
         for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? xn[5 + 3 * q + l] : T(0);
     }
+    // the tile has landed (all threads wait; a give-up is reported, and the
+    // values computed from an incomplete tile are never trusted by the host)
+    const bool tile_ok = mbar_wait(&bar, 0);
+    if (!tile_ok && (threadIdx.x & 31) == 0) atomicOr(err, ERR_TIMEOUT);
     // P2 in the zero-mean basis of Eq. base: a = M2 d
     T a[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         T acc = T(0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc += sM2[k * 16 + j][lc] * d[j];
+        for (int j = 0; j < 16; ++j) acc += sT[TILE_M2 + k * 16 + j][lc] * d[j];
         a[k] = acc;
     }
-    const T Mxx = m.mom2[0 * nc + c], Mxy = m.mom2[1 * nc + c], Mxz = m.mom2[2 * nc + c];
-    const T Myy = m.mom2[3 * nc + c], Myz = m.mom2[4 * nc + c], Mzz = m.mom2[5 * nc + c];
+    const T Mxx = sT[TILE_MOM + 0][lc], Mxy = sT[TILE_MOM + 1][lc], Mxz = sT[TILE_MOM + 2][lc];
+    const T Myy = sT[TILE_MOM + 3][lc], Myz = sT[TILE_MOM + 4][lc], Mzz = sT[TILE_MOM + 5][lc];
 
     const T g22 = T(100.0 / 111.0), g12 = T(10.0 / 111.0), g02 = T(1.0 / 111.0);
     const T g11 = T(10.0 / 11.0), g01 = T(1.0 / 11.0);
@@ -242,9 +289,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (nb[f] < 0) continue;
-            b[0] += m.M1[(0 * 4 + f) * nc + c] * d[f];
-            b[1] += m.M1[(1 * 4 + f) * nc + c] * d[f];
-            b[2] += m.M1[(2 * 4 + f) * nc + c] * d[f];
+            b[0] += sT[TILE_M1 + 0 * 4 + f][lc] * d[f];
+            b[1] += sT[TILE_M1 + 1 * 4 + f][lc] * d[f];
+            b[2] += sT[TILE_M1 + 2 * 4 + f][lc] * d[f];
         }
         if (slopes_out && cl.active) {
 #pragma unroll
@@ -255,7 +302,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = rc.order == 2 ? (k < 3 ? b[k] : T(0)) : a[k];
     } else {
-        const T v23 = m.vol23[c], v43 = m.vol43[c];
+        const T v23 = sT[TILE_V23][lc], v43 = sT[TILE_V43][lc];
         // smoothness indicators, Eq. smooth-indicator
         const T beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
         // two-step beta_0 from the neighbours' P1 slopes, Eq. p0-non-linear-weight
@@ -331,9 +378,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     bool bad = false;
 #pragma unroll 4
     for (int g = 0; g < 12; ++g) {
-        const T gx = sG[g * 3 + 0][lc];
-        const T gy = sG[g * 3 + 1][lc];
-        const T gz = sG[g * 3 + 2][lc];
+        const T gx = sT[TILE_G + g * 3 + 0][lc];
+        const T gy = sT[TILE_G + g * 3 + 1][lc];
+        const T gz = sT[TILE_G + g * 3 + 2][lc];
         const T v = c0 + R[0] * gx + R[1] * gy + R[2] * gz + R[3] * gx * gx + R[4] * gx * gy + R[5] * gx * gz +
                     R[6] * gy * gy + R[7] * gy * gz + R[8] * gz * gz;
         const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
@@ -344,6 +391,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
         const T pr = rc.gm1 * (en - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) / rho);
         if (!(rho > T(0)) || !(pr > T(0))) bad = true;
     }
+    if (!tile_ok) mbar_wait(&bar, 0);  // a late copy lands before the block exits
     if (!cl.active) return;
     T* out = poly + c * POLY_STRIDE + q * 10;
     out[0] = bad ? Q0 : c0;
@@ -1063,7 +1111,7 @@ cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* X, T* slopes, const 
 
 template <typename T>
 cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* slopes_in,
-                             T* slopes, T* poly, int32_t* fallback, const Finalize* fin,
+                             T* slopes, T* poly, int32_t* fallback, const Finalize* fin, int32_t* err,
                              cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
     ReconConst<T> rc;
@@ -1071,7 +1119,8 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X,
     rc.eps = (T)p.eps_weno;
     rc.weno = p.weno;
     rc.order = p.order;
-    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback, fin_arg<T>(fin));
+    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback, fin_arg<T>(fin),
+                                                        err);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ enum { CTRL_T = 0, CTRL_DT = 1, CTRL_DT_FIXED = 2, CTRL_T_END = 3, CTRL_N = 8 };
 // per-block partial results of the update / time-step kernels
 enum { PART_DTMIN = 0, PART_RES = 1, PART_N = 6 };
 // device error flags
-enum { ERR_STATE = 1 };
+enum { ERR_STATE = 1, ERR_TIMEOUT = 2 };
 
 constexpr int FLUX_FACES = 32;       // faces per flux block (3 threads each)
 constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
@@ -20,6 +20,12 @@ constexpr int CELLS_PER_BLOCK = 24;  // 4 warps x 6 cells, 5 lanes per cell
 constexpr int FGEO = 24;             // reals per face geometry record
 constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record (50 used)
 constexpr int XS = 20;               // reals per cell working-state record: W (5), grad W (15, 3q+i)
+// Per-block tile of the reconstruction's static cell data, one contiguous
+// [TILE_ROWS][CELLS_PER_BLOCK] record per block of cells, loaded into shared
+// memory by one bulk copy: M2 (144 rows), the cell's 12 face Gauss points
+// about its centroid (36), M1 (12), central second moments (6), |Omega|^(2/3),
+// |Omega|^(4/3).
+enum { TILE_M2 = 0, TILE_G = 144, TILE_M1 = 180, TILE_MOM = 192, TILE_V23 = 198, TILE_V43 = 199, TILE_ROWS = 200 };
 
 template <typename T>
 struct DevMesh {
@@ -29,13 +35,9 @@ struct DevMesh {
     const int32_t* nbr;    // [4][nc], -1 = none
     const int32_t* cface;  // [4][nc] face * 2 + side (side 1 = right)
     const double* inv_vol; // [nc]
-    const T* vol23;        // [nc] |Omega|^(2/3)
-    const T* vol43;        // [nc] |Omega|^(4/3)
     const T* dr;           // [nc]
-    const T* mom2;         // [6][nc]
-    const T* cgp;          // [36][nc] the cell's face Gauss points about its centroid
     const T* M1;           // [12][nc]
-    const T* M2;           // [144][nc]
+    const T* tile;         // [blocks][TILE_ROWS][CELLS_PER_BLOCK] reconstruction data
     const int32_t* flr;    // [2][nf]
     const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
     const T* fixed;        // [nc][XS] state held by fixed boundary faces (NULL: none)
@@ -82,9 +84,11 @@ struct Launch {
     // slopes_in (may be NULL): the step-1 slopes of every cell from a slopes
     // pass; without it the kernel computes its own and its neighbours' slopes.
     // slopes_out (may be NULL) receives the cell's own step-1 slopes.
+    // err: ERR_TIMEOUT is or-ed in if a block's bounded wait for its tile
+    // gave up
     static cudaError_t recon(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* slopes_in,
                              T* slopes_out, T* poly, int32_t* fallback, const Finalize* fin,
-                             cudaStream_t s);
+                             int32_t* err, cudaStream_t s);
     // case_dt: per-case step (NULL: dt_override for every face)
     // variant: 1 = 3 blocks per SM (FP32), 0 = 2 blocks per SM; ignored in FP64
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* poly, T* rec,
