@@ -1,0 +1,530 @@
+// gks_flux.cu -- face flux kernels (Sec. 2.2, 3, 4.4, 4.5), sm_103a, FP64 and
+// FP32-bulk instantiations.
+//
+//   k_flux         face-ordered, 6 threads per face (3 Gauss points x 2
+//                  sides): R of both cells at the Gauss points, face frame,
+//                  kinetic solution (Eq. 2nd-flux with the equilibrium state
+//                  of Eq. new-equ-part), weighted face record of the stage
+//                  (Sec. 3 Eqs. linear-system, s2o4, step-du); FP32
+//   k_flux_single  the same with one thread per Gauss point; FP64
+//
+// Boundary faces take their ghost side from the face's kind (Sec. 4.4 slip
+// wall, a fixed state, or zeroth-order extrapolation).
+#include <cuda_runtime.h>
+
+#include "gks_device.cuh"
+#include "gks_kernels.h"
+
+namespace gks {
+
+// --------------------------------------------------------------------------
+// face flux
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T* val, T (*g)[5]) {
+    // the record is 16-byte aligned (POLY_STRIDE words): load it in vectors
+    T c[POLY_STRIDE];
+    if constexpr (sizeof(T) == 4) {
+        const float4* p4 = reinterpret_cast<const float4*>(P);
+#pragma unroll
+        for (int i = 0; i < POLY_STRIDE / 4; ++i) {
+            const float4 v = __ldg(p4 + i);
+            c[4 * i] = v.x;
+            c[4 * i + 1] = v.y;
+            c[4 * i + 2] = v.z;
+            c[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2* p2 = reinterpret_cast<const double2*>(P);
+#pragma unroll
+        for (int i = 0; i < POLY_STRIDE / 2; ++i) {
+            const double2 v = __ldg(p2 + i);
+            c[2 * i] = v.x;
+            c[2 * i + 1] = v.y;
+        }
+    }
+    const T x = X[0], y = X[1], z = X[2];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const T* cq = c + q * 10;
+        val[q] = cq[0] + cq[1] * x + cq[2] * y + cq[3] * z + cq[4] * x * x + cq[5] * x * y + cq[6] * x * z +
+                 cq[7] * y * y + cq[8] * y * z + cq[9] * z * z;
+        g[0][q] = cq[1] + T(2) * cq[4] * x + cq[5] * y + cq[6] * z;
+        g[1][q] = cq[2] + cq[5] * x + T(2) * cq[7] * y + cq[8] * z;
+        g[2][q] = cq[3] + cq[6] * x + cq[8] * y + T(2) * cq[9] * z;
+    }
+}
+
+// rows of the face frame: n, t1, t2 (Eq. rotate-matrix-3d; n1 = -1 uses the
+// reflection diag(-1, -1, 1) of the velocity block)
+template <typename T>
+__device__ __forceinline__ void face_frame(const T* n, T (*Rm)[3]) {
+    const T n1 = n[0], n2 = n[1], n3 = n[2];
+    Rm[0][0] = n1;
+    Rm[0][1] = n2;
+    Rm[0][2] = n3;
+    if (n1 == T(-1)) {
+        Rm[1][0] = T(0); Rm[1][1] = T(-1); Rm[1][2] = T(0);
+        Rm[2][0] = T(0); Rm[2][1] = T(0); Rm[2][2] = T(1);
+        return;
+    }
+    const T r = T(1) / (T(1) + n1);
+    Rm[1][0] = -n2;
+    Rm[1][1] = n1 + n3 * n3 * r;
+    Rm[1][2] = -n2 * n3 * r;
+    Rm[2][0] = -n3;
+    Rm[2][1] = -n2 * n3 * r;
+    Rm[2][2] = T(1) - n3 * n3 * r;
+}
+
+template <typename T>
+__device__ __forceinline__ void to_local(const T (*Rm)[3], const T* W, const T (*g)[5], T* Wt,
+                                         T (*gt)[5]) {
+    Wt[0] = W[0];
+    Wt[4] = W[4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Wt[1 + j] = Rm[j][0] * W[1] + Rm[j][1] * W[2] + Rm[j][2] * W[3];
+    // directions first: h_j = sum_i R_ji g_i, then the momentum components
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T h[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) h[q] = Rm[j][0] * g[0][q] + Rm[j][1] * g[1][q] + Rm[j][2] * g[2][q];
+        gt[j][0] = h[0];
+        gt[j][4] = h[4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gt[j][1 + k] = Rm[k][0] * h[1] + Rm[k][1] * h[2] + Rm[k][2] * h[3];
+    }
+}
+
+// Slip-wall ghost (Sec. 4.4) of a state already in the face frame (x1 along
+// the normal): the mirror image across the wall.  rho U1 changes sign; of the
+// x1-derivatives all but that of rho U1 change sign; of the x2-, x3-derivatives
+// only those of rho U1 do.
+template <typename T>
+__device__ __forceinline__ void slip_wall_ghost(T* Wt, T (*gt)[5]) {
+    Wt[1] = -Wt[1];
+    gt[0][0] = -gt[0][0];
+    gt[0][2] = -gt[0][2];
+    gt[0][3] = -gt[0][3];
+    gt[0][4] = -gt[0][4];
+    gt[1][1] = -gt[1][1];
+    gt[2][1] = -gt[2][1];
+}
+
+// device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
+constexpr int FLR_SLIP_WALL = -2, FLR_FIXED = -3;  // -1: open
+
+// fixed boundary: the interior cell's fixed state (average and gradient)
+// extended linearly to the point X (relative to the cell's centroid)
+template <typename T>
+__device__ __forceinline__ void fixed_ghost(const T* __restrict__ x0, const T* X, T* W, T (*g)[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        T v = x0[q];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[i][q] = x0[5 + 3 * q + i];
+            v += g[i][q] * X[i];
+        }
+        W[q] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
+    const T a = v[1], b = v[2], c = v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[1 + i] = Rm[0][i] * a + Rm[1][i] * b + Rm[2][i] * c;
+}
+
+// Face flux with 6 threads per face: 3 Gauss points x 2 sides.  The two sides
+// of a Gauss point sit in different warps (warps 0-2 left, 3-5 right) so that
+// no warp diverges on the side; the interface equilibrium, its slopes and the
+// partial outputs are exchanged through shared memory:
+//   phase 1  own side: state at the point, face frame, slopes, rho <psi>+-
+//   phase 2  W^c, collision times; own kinetic part; rho <a_i psi>+-
+//   phase 3  equilibrium slopes; left warps add the C2 (a^c.u) flux terms,
+//            right warps the C1, C3 flux terms and the dW term
+//   phase 4  left warps finish the flux entries, right warps the gradient
+//            entries of the record; the 3 points of each face are summed.
+constexpr int FP_GP = 3 * FLUX_FACES;  // Gauss points per block (96)
+
+template <typename T, int NR>
+struct FluxSmem {
+    T w0[2][FP_GP][5];   // rho <psi>+- of each side
+    T p[2][FP_GP];       // pressure of each side
+    T dwc[2][FP_GP][15]; // rho <a_i psi>+- of each side
+    T out[2][FP_GP][20]; // partial Fh, D, W0, dW of each side
+    T red[FP_GP * NR];   // weighted record entries per Gauss point
+};
+
+template <typename T, int NR, int MINB>
+__global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
+                                                     const T* __restrict__ Wavg,
+                                                     const T* __restrict__ poly,
+                                                     T* __restrict__ rec,
+                                                     const double* __restrict__ ctrl,
+                                                     double dt_override) {
+    __shared__ FluxSmem<T, NR> sm;
+    const int side = threadIdx.x >= FP_GP ? 1 : 0;
+    const int g = threadIdx.x - side * FP_GP;  // Gauss point within the block
+    const int lf = g / 3;
+    const int k = g - 3 * lf;
+    const int64_t f0 = (int64_t)blockIdx.x * FLUX_FACES + lf;
+    const bool active = f0 < m.nf;
+    const int64_t f = active ? f0 : m.nf - 1;  // idle points compute a valid face, store nothing
+    const int L = m.flr[f], Rc = m.flr[m.nf + f];
+    // the face's case step; a finished case (dt = 0) computes with a dummy
+    // step and its cells ignore the record
+    const double dtc = ctrl ? ctrl[m.cell_case[L >= 0 ? L : Rc]] : dt_override;
+    const T dt = dtc > 0.0 ? (T)dtc : T(1);
+    const T* geo = m.fgeo + f * FGEO;
+    const T n[3] = {geo[0], geo[1], geo[2]};
+    const T w = geo[3];
+
+    // ---- phase 1 ----
+    const int mine = side == 0 ? L : Rc;
+    const bool wall = mine == FLR_SLIP_WALL;
+    T Ws[5], gs[3][5];
+    if (mine >= 0 || wall) {
+        // a wall side starts from the interior cell's value at the point
+        const int src = mine >= 0 ? side : 1 - side;
+        const int64_t cell = mine >= 0 ? mine : (side == 0 ? Rc : L);
+        const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+        eval_poly(poly + cell * POLY_STRIDE, X, Ws, gs);
+    } else if (mine == FLR_FIXED) {
+        const int64_t in = side == 0 ? Rc : L;
+        const int src = 1 - side;
+        const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+        fixed_ghost(m.fixed + in * XS, X, Ws, gs);
+    } else {
+        // open boundary: the missing side is the interior cell's average with
+        // zero gradient (zeroth-order extrapolation; the paper leaves outflow
+        // boundaries open, and copying the interior Gauss-point state is not
+        // stable)
+        const int64_t in = side == 0 ? Rc : L;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Ws[q] = Wavg[in * XS + q];
+            gs[0][q] = gs[1][q] = gs[2][q] = T(0);
+        }
+    }
+    T Rm[3][3];
+    face_frame(n, Rm);
+    T tW[5], tg[3][5];
+    to_local(Rm, Ws, gs, tW, tg);
+    if (wall) slip_wall_ghost(tW, tg);
+    const Prim<T> S = to_prim(tW, ph.gm1);
+    Tab<T> t;
+    T a[3][5], A[5];
+    kinetic_side(ph, S, tg, side == 0 ? +1 : -1, t, a, A);
+    T mw0[5] = {T(0), T(0), T(0), T(0), T(0)};
+    acc_psi<0, 0, 0>(t, S.rho, mw0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sm.w0[side][g][q] = mw0[q];
+    sm.p[side][g] = S.p;
+    __syncthreads();
+
+    // ---- phase 2 ----
+    T Wc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wc[q] = sm.w0[0][g][q] + sm.w0[1][g][q];
+    const Prim<T> C = to_prim(Wc, ph.gm1);
+    const TimeCoef<T> tc = time_coefs(ph, sm.p[0][g], sm.p[1][g], C.p, dt);
+    const T tau = tc.tau;
+    T Fh[5], D[5], W0[5], dWt[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Fh[q] = D[q] = W0[q] = dWt[q] = T(0);
+    {
+        T dwc[3][5];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dwc[i][q] = T(0);
+            acc_apsi<0, 0, 0>(t, a[i], S.rho, dwc[i]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sm.dwc[side][g][5 * i + q] = dwc[i][q];
+        }
+    }
+    if (!ph.smooth) {
+        T mf0[5] = {0}, mf1[5] = {0}, mw1[5] = {0};
+        acc_psi<1, 0, 0>(t, S.rho, mf0);
+        acc_grad<1>(t, a, S.rho, mf1);
+        acc_grad<0>(t, a, S.rho, mw1);
+        axpy5(tc.k0, mf0, Fh);
+        axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
+        axpy5(tc.dk0, mf0, D);
+        axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
+        axpy5(T(1), mw0, W0);
+        axpy5(-tau, mw1, W0);
+        axpy5(tau - (tau + dt) * tc.E, mw1, dWt);
+        if (ph.viscous) {
+            T mf2[5] = {0}, mw2[5] = {0};
+            acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
+            acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
+            axpy5(-tau * tc.k0, mf2, Fh);
+            axpy5(-tau * tc.dk0, mf2, D);
+            axpy5(-tau, mw2, W0);
+            axpy5(tau * (T(1) - tc.E), mw2, dWt);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3 ----
+    {
+        T dWc[3][5];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dWc[i][q] = sm.dwc[0][g][5 * i + q] + sm.dwc[1][g][5 * i + q];
+        make_tab(t, C, ph.K, 0);
+        T ac[3][5], Ac[5];
+        state_slopes(C, t, ph.K, dWc, ac, Ac);
+        if (side == 0) {
+            T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
+            acc_grad<1>(t, ac, C.rho, mf1);
+            if (ph.smooth) {
+                axpy5(-tau * T(0.5) * dt, mf1, Fh);
+            } else {
+                axpy5(tc.q2, mf1, Fh);
+                axpy5(tc.dq2, mf1, D);
+            }
+        } else {
+            T mf0[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+            acc_psi<1, 0, 0>(t, C.rho, mf0);
+            acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
+            acc_grad<0>(t, ac, C.rho, mw1);  // rho <A^c psi> = -mw1 (Eq. co)
+            if (ph.smooth) {
+                const T hd = T(0.5) * dt;
+                axpy5(hd, mf0, Fh);
+                axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
+                axpy5(T(0.25) * dt * dt, mf2, D);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) W0[q] = Wc[q];  // tau terms cancel: <(a.u + A) psi> = 0
+                axpy5(-dt, mw1, dWt);
+            } else {
+                axpy5(tc.q1, mf0, Fh);
+                axpy5(tc.q3, mf2, Fh);
+                axpy5(tc.dq1, mf0, D);
+                axpy5(tc.dq3, mf2, D);
+                const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
+                axpy5(C2 - C3, mw1, dWt);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        sm.out[side][g][q] = Fh[q];
+        sm.out[side][g][5 + q] = D[q];
+        sm.out[side][g][10 + q] = W0[q];
+        sm.out[side][g][15 + q] = dWt[q];
+    }
+    __syncthreads();
+
+    // ---- phase 4: left warps the flux entries, right warps the gradient entries
+    T* mine_rec = sm.red + g * NR;
+    if (side == 0) {
+        T Fs[5], Ds[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Fs[q] = sm.out[0][g][q] + sm.out[1][g][q];
+            Ds[q] = sm.out[0][g][5 + q] + sm.out[1][g][5 + q];
+        }
+        to_global(Rm, Fs);
+        to_global(Rm, Ds);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
+                // dt L + dt^2/6 L_t = 8/3 Fh - 1/3 F = 2 Fh - D / 3 (Eqs. linear-system, s2o4)
+                mine_rec[q] = w * Fs[q];
+                mine_rec[5 + q] = w * (T(2) * Fs[q] - Ds[q] * T(1.0 / 3.0));
+            } else {
+                mine_rec[q] = w * T(4.0 / 3.0) * Ds[q];  // dt^2/3 L_t(W*) = 4/3 (F* - 2 Fh*)
+            }
+        }
+    } else {
+        T Zs[5], Ys[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Zs[q] = sm.out[0][g][10 + q] + sm.out[1][g][10 + q];
+            Ys[q] = sm.out[0][g][15 + q] + sm.out[1][g][15 + q];
+        }
+        to_global(Rm, Zs);
+        to_global(Rm, Ys);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
+                const T ws = w * (Zs[q] + T(0.5) * Ys[q]);  // f* = f^n + dt/2 f_t^n
+                const T w0 = w * Zs[q];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    mine_rec[10 + 3 * q + i] = ws * n[i];
+                    mine_rec[25 + 3 * q + i] = w0 * n[i];
+                }
+            } else {
+                const T dg = w * Ys[q];  // f^{n+1} = f^n + dt f_t^*
+#pragma unroll
+                for (int i = 0; i < 3; ++i) mine_rec[5 + 3 * q + i] = dg * n[i];
+            }
+        }
+    }
+    __syncthreads();
+    // sum the three Gauss points of each face; coalesced record store
+    const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
+    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 2 * FP_GP) {
+        const int fl = idx / NR, j = idx - fl * NR;
+        if (base + fl < m.nf) {
+            const T* r = sm.red + fl * 3 * NR + j;
+            rec[(base + fl) * NR + j] = (r[0] + r[NR]) + r[2 * NR];
+        }
+    }
+}
+
+// 3 threads per face, one Gauss point each (used for FP64, whose register
+// footprint leaves no room for the lane-pair split)
+template <typename T, int NR>
+__global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Phys<T> ph,
+                                                                 const T* __restrict__ Wavg,
+                                                                 const T* __restrict__ poly,
+                                                                 T* __restrict__ rec,
+                                                                 const double* __restrict__ ctrl,
+                                                                 double dt_override) {
+    __shared__ T red[FLUX_FACES * 3 * NR];
+    const int lf = threadIdx.x / 3;
+    const int k = threadIdx.x - 3 * lf;
+    const int64_t f = (int64_t)blockIdx.x * FLUX_FACES + lf;
+    T* mine = red + (lf * 3 + k) * NR;
+    if (f < m.nf) {
+        const int L = m.flr[f], Rc = m.flr[m.nf + f];
+        const double dtc = ctrl ? ctrl[m.cell_case[L >= 0 ? L : Rc]] : dt_override;
+        const T dt = dtc > 0.0 ? (T)dtc : T(1);
+        const T* geo = m.fgeo + f * FGEO;
+        const T n[3] = {geo[0], geo[1], geo[2]};
+        const T w = geo[3];
+        T WL[5], gL[3][5], WR[5], gR[3][5];
+        for (int side = 0; side < 2; ++side) {
+            const int cell = side == 0 ? L : Rc;
+            T* Wv = side == 0 ? WL : WR;
+            T (*g)[5] = side == 0 ? gL : gR;
+            if (cell >= 0 || cell == FLR_SLIP_WALL) {
+                // a wall side starts from the interior cell's value at the point
+                const int src = cell >= 0 ? side : 1 - side;
+                const int64_t c = cell >= 0 ? cell : (side == 0 ? Rc : L);
+                const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+                eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
+            } else if (cell == FLR_FIXED) {
+                const int64_t in = side == 0 ? Rc : L;
+                const int src = 1 - side;
+                const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+                fixed_ghost(m.fixed + in * XS, X, Wv, g);
+            } else {
+                // open boundary: interior cell average, zero gradient
+                const int64_t in = side == 0 ? Rc : L;
+                for (int q = 0; q < 5; ++q) {
+                    Wv[q] = Wavg[in * XS + q];
+                    g[0][q] = g[1][q] = g[2][q] = T(0);
+                }
+            }
+        }
+        T Rm[3][3];
+        face_frame(n, Rm);
+        T tWL[5], tgL[3][5], tWR[5], tgR[3][5];
+        to_local(Rm, WL, gL, tWL, tgL);
+        to_local(Rm, WR, gR, tWR, tgR);
+        if (L == FLR_SLIP_WALL) slip_wall_ghost(tWL, tgL);
+        if (Rc == FLR_SLIP_WALL) slip_wall_ghost(tWR, tgR);
+        T Fh[5], D[5], W0[5], dWt[5];
+        gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, D, W0, dWt);
+        to_global(Rm, Fh);
+        to_global(Rm, D);
+        to_global(Rm, W0);
+        to_global(Rm, dWt);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (NR == 40) {
+                mine[q] = w * Fh[q];
+                mine[5 + q] = w * (T(2) * Fh[q] - D[q] * T(1.0 / 3.0));
+                const T ws = w * (W0[q] + T(0.5) * dWt[q]);
+                const T w0 = w * W0[q];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    mine[10 + 3 * q + i] = ws * n[i];
+                    mine[25 + 3 * q + i] = w0 * n[i];
+                }
+            } else {
+                mine[q] = w * T(4.0 / 3.0) * D[q];
+                const T dg = w * dWt[q];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) mine[5 + 3 * q + i] = dg * n[i];
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
+    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 3 * FLUX_FACES) {
+        const int fl = idx / NR, j = idx - fl * NR;
+        if (base + fl < m.nf) {
+            const T* r = red + fl * 3 * NR + j;
+            rec[(base + fl) * NR + j] = (r[0] + r[NR]) + r[2 * NR];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// launcher
+// --------------------------------------------------------------------------
+template <typename T>
+static Phys<T> make_phys(const HostPhys& p) {
+    Phys<T> ph;
+    ph.gamma = (T)p.gamma;
+    ph.gm1 = (T)(p.gamma - 1.0);
+    ph.K = (T)((5.0 - 3.0 * p.gamma) / (p.gamma - 1.0));
+    ph.tau_eps = (T)p.tau_eps;
+    ph.tau_c = (T)p.tau_c;
+    ph.mu = (T)p.mu;
+    ph.eps_w = (T)p.eps_weno;
+    ph.viscous = p.viscous;
+    ph.smooth = p.smooth;
+    return ph;
+}
+
+
+template <typename T>
+cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, const T* poly, T* rec,
+                            const double* ctrl, double dt_override, int stage, cudaStream_t s, int variant) {
+    // ctrl is the per-case step array (NULL: dt_override everywhere)
+    if (m.nf == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((m.nf + FLUX_FACES - 1) / FLUX_FACES);
+    const Phys<T> ph = make_phys<T>(p);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the two sides of each Gauss point in separate warps; variant
+        // 1 trades registers for occupancy (3 blocks per SM), variant 0 keeps
+        // 2 blocks per SM without spills
+        if (variant == 1) {
+            if (stage == 1)
+                k_flux<T, 40, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            else
+                k_flux<T, 20, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        } else {
+            if (stage == 1)
+                k_flux<T, 40, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+            else
+                k_flux<T, 20, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        }
+    } else {
+        if (stage == 1)
+            k_flux_single<T, 40><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+        else
+            k_flux_single<T, 20><<<grid, 3 * FLUX_FACES, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+    }
+    return cudaGetLastError();
+}
+
+
+template cudaError_t Launch<double>::flux(const DevMesh<double>&, const HostPhys&, const double*, const double*,
+                                          double*, const double*, double, int, cudaStream_t, int);
+template cudaError_t Launch<float>::flux(const DevMesh<float>&, const HostPhys&, const float*, const float*,
+                                         float*, const double*, double, int, cudaStream_t, int);
+
+}  // namespace gks
