@@ -42,10 +42,11 @@ WORKLOAD = "sod_tube_64x8x8_hex_x6_tets_24576_cells_weno3_cfl0.5"
 CPU_SAMPLE = dict(nx=16, nyz=4)  # same recipe, 1,536 cells: oracle per-cell cost is size independent
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # work of the dominant kernel (face flux) per Gauss point and stage, FP32 flop
-# (fadd + fmul + 2 ffma) counted by ncu on this workload, and its DRAM bytes
-# per launch from the same capture (profiles/k_flux_fp32_sod24576.md)
-FLUX_FLOPS_PER_GP = {"fp32": (5016.0, 4913.0)}
-FLUX_DRAM_BYTES_PER_LAUNCH = 10.39e6
+# (fadd + fmul + 2 ffma) counted by ncu on this workload (147,840 Gauss points
+# a launch), and its DRAM bytes per stage-1 launch from the same capture (the
+# flux kernel's summary under profiles/)
+FLUX_FLOPS_PER_GP = {"fp32": (4746.6, 4643.3)}
+FLUX_DRAM_BYTES_PER_LAUNCH = 10.46e6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -223,6 +224,9 @@ def main():
                     help="only the FP32 timed steps (for profilers); no accuracy, e2e or CPU legs")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of --profile-case")
+    ap.add_argument("--variant", default="auto",
+                    help="execution variant of --profile-case: face_order,flux_blocks,slopes_pass "
+                         "(e.g. 1,3,1) or auto (tuned as in the full run)")
     ap.add_argument("--batch-cases", type=int, default=48,
                     help="independent cases of the batched leg (0: skip it)")
     args = ap.parse_args()
@@ -251,9 +255,14 @@ def main():
         prec = 1 if args.precision == "fp32" else 0
         s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
         s.init(W0, dW0)
+        if args.variant == "auto":
+            s.autotune(steps=10, cache=False)
+        else:
+            s.set_variant(*[int(v) for v in args.variant.split(",")])
         ms = time_device(torch, s, args.steps, args.warmup, flush)
         if rank == 0:
-            print(json.dumps({"profile_case": WORKLOAD, "precision": args.precision, "ms_per_step": ms}))
+            print(json.dumps({"profile_case": WORKLOAD, "precision": args.precision, "variant": s.variant,
+                              "ms_per_step": ms}))
         return
 
     results = {}
@@ -328,7 +337,7 @@ def main():
                    "replicas": ws},
         "fp64": {"value": value64, "ms_per_step": results["fp64"]["ms"], "dtype": "f64"},
         "autotuned_variant": {"fp32": results["fp32"]["variant"], "fp64": results["fp64"]["variant"],
-                              "meaning": "[face_order, flux_blocks_per_SM]"},
+                              "meaning": "[face_order, flux_blocks_per_SM, slopes_pass]"},
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32,
                           "fp32_vs_fp64_rel": fp32_vs_fp64},
         "fp32_speedup_over_fp64": value / value64,

@@ -197,6 +197,7 @@ class State:
         self.torch = torch
         self.mesh = mesh
         self.params = p
+        self.variant = (0, 3, 0)  # the library default: canonical faces, 3 flux blocks per SM, fused slopes
         self.device = torch.device(device)
         nbytes = lib().gks_workspace_bytes(mesh._h, C.byref(p))
         if nbytes == 0:
