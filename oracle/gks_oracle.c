@@ -525,7 +525,8 @@ int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
         for (int f = 0; f < 4; ++f) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             int8_t k = kind[c * 4 + f];
-            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED) return -1;
+            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED && k != ORA_BC_NOSLIP_WALL)
+                return -1;
             m->bkind[m->csr_face[c * 4 + f]] = k;
         }
     return 0;
@@ -1213,7 +1214,8 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
             /* a slip wall's ghost is built from the interior Gauss-point
              * state after the rotation (below); give the missing side the
              * interior values so the rotation leaves them defined */
-            int wall = (cl < 0 || cr < 0) && m->bkind[f] == ORA_BC_SLIP_WALL;
+            int wall = (cl < 0 || cr < 0) &&
+                       (m->bkind[f] == ORA_BC_SLIP_WALL || m->bkind[f] == ORA_BC_NOSLIP_WALL);
             if (wall) {
                 if (cl < 0) {
                     memcpy(WL, WR, sizeof WL);
@@ -1249,11 +1251,23 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                  * those of rho U1 change sign. */
                 double* gW = cl < 0 ? tWL : tWR;
                 double (*gg)[5] = cl < 0 ? tgL : tgR;
-                gW[1] = -gW[1];
-                for (int a = 0; a < 5; ++a)
-                    if (a != 1) gg[0][a] = -gg[0][a];
-                gg[1][1] = -gg[1][1];
-                gg[2][1] = -gg[2][1];
+                if (m->bkind[f] == ORA_BC_SLIP_WALL) {
+                    gW[1] = -gW[1];
+                    for (int a = 0; a < 5; ++a)
+                        if (a != 1) gg[0][a] = -gg[0][a];
+                    gg[1][1] = -gg[1][1];
+                    gg[2][1] = -gg[2][1];
+                } else {
+                    /* Sec. 4.4, non-slip adiabatic wall (at rest): the ghost
+                     * keeps rho and rho E and reverses all three momenta;
+                     * every derivative of the momenta is kept, every
+                     * derivative of rho and of rho E changes sign. */
+                    for (int a = 1; a <= 3; ++a) gW[a] = -gW[a];
+                    for (int j = 0; j < 3; ++j) {
+                        gg[j][0] = -gg[j][0];
+                        gg[j][4] = -gg[j][4];
+                    }
+                }
             }
             double tFh[5], tF[5], tW0[5], tWdt[5];
             ora_gp_flux(p, tWL, &tgL[0][0], tWR, &tgR[0][0], dt, tFh, tF, tW0, tWdt);

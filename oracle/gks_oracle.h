@@ -38,7 +38,7 @@ ora_mesh* ora_mesh_build(const double* xyz, int64_t nv, const int64_t* tet,
 void ora_mesh_free(ora_mesh* m);
 
 /* Boundary condition of the boundary faces (faces with one cell). */
-enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2 };
+enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2, ORA_BC_NOSLIP_WALL = 3 };
 /* kind[nc][4]: the condition of local face f (opposite vertex f) of cell c,
  * read only where that face is on the boundary.  Default: all open.
  * Returns -1 (mesh unchanged only up to the offending face) on a value

@@ -364,7 +364,7 @@ def riemann_x_exact_density(mesh, t, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.
     return cell_average(mesh, f, order=order)[:, 0]
 
 
-BC_OPEN, BC_SLIP_WALL, BC_FIXED = 0, 1, 2
+BC_OPEN, BC_SLIP_WALL, BC_FIXED, BC_NOSLIP_WALL = 0, 1, 2, 3
 
 
 def boundary_kinds(mesh, spec):
@@ -490,6 +490,48 @@ def sod_case(nx=64, nyz=8, jitter=0.1, seed=2):
 # --------------------------------------------------------------------------
 # batches of independent cases (one mesh, disjoint components)
 # --------------------------------------------------------------------------
+
+def shear_decay_state(mesh, amp=0.05, rho=1.0, p=1.0, length=1.0, gamma=1.4, order=4):
+    """Tangential shear v = amp sin(pi x / length) (along y) in a gas of
+    uniform density and pressure: cell averages of W and of grad W."""
+    k = math.pi / length
+
+    def cons(x):
+        s = np.sin(k * x[..., 0])
+        v = amp * s
+        z = np.zeros_like(v)
+        return np.stack([np.full_like(v, rho), z, rho * v, z, p / (gamma - 1.0) + 0.5 * rho * v * v], axis=-1)
+
+    def grad(x):
+        s, c = np.sin(k * x[..., 0]), np.cos(k * x[..., 0])
+        out = np.zeros(x.shape[:-1] + (15,))
+        out[..., 3 * 2 + 0] = rho * amp * k * c              # d(rho v)/dx
+        out[..., 3 * 4 + 0] = rho * amp * amp * k * s * c    # d(rho E)/dx
+        return out
+    W = cell_average(mesh, cons, order=order).T.copy()
+    dW = cell_average(mesh, grad, order=order).T.copy()
+    return np.ascontiguousarray(W), np.ascontiguousarray(dW)
+
+
+def shear_decay_amplitude(mesh, W, length=1.0, vol=None):
+    """Least-squares amplitude of rho v against sin(pi x / length) over the
+    cells (volume weighted, cell averages of the sine by quadrature)."""
+    s = cell_average(mesh, lambda x: np.sin(math.pi / length * x[..., 0])[..., None], order=4)[:, 0]
+    if vol is None:
+        vol = np.ones_like(s)
+    return float((vol * W[2] * s).sum() / (vol * s * s).sum())
+
+
+def shear_decay_case(nx=16, nyz=2, amp=0.05, jitter=0.1, seed=7):
+    """Decaying shear between no-slip adiabatic walls at x = 0 and 1 (y, z
+    periodic, cubic hexahedra, nx x nyz x nyz hexes x 6 tets).  For a viscous
+    gas at low Mach number v = amp sin(pi x) exp(-nu pi^2 t), nu = mu / rho."""
+    w = nyz / nx
+    mesh = box_mesh((nx, nyz, nyz), (1.0, w, w), (False, True, True), jitter, seed)
+    mesh["bkind"] = boundary_kinds(mesh, {(0, "lo"): BC_NOSLIP_WALL, (0, "hi"): BC_NOSLIP_WALL})
+    W, dW = shear_decay_state(mesh, amp=amp)
+    return mesh, W, dW
+
 
 def wall_reflection_case(nx=64, nyz=4, state=(1.0, 1.0, 1.0), jitter=0.1, seed=3):
     """Uniform gas moving along x in [0,1] x [0,nyz/nx]^2 (cubic hexahedra)

@@ -15,6 +15,8 @@ contact: a linear density profile at rest under uniform pressure is an exact
 steady solution that the scheme reproduces to round-off when the ghost holds
 the profile's value and gradient at each Gauss point, and visibly does not
 with open ends."""
+import math
+
 import numpy as np
 import pytest
 
@@ -164,3 +166,64 @@ def test_fixed_boundary_needs_its_state(oracle_mod):
     om = oracle_mod.Mesh(mesh)
     with pytest.raises(ValueError):
         om.step(oracle_mod.params(weno=1), W, dW)
+
+
+# ---------------------------------------------------------------- no-slip --
+# Non-slip adiabatic walls at rest (Sec. 4.4): the ghost is the interior
+# state reflected through the Gauss point with the velocity reversed, so the
+# interface distribution carries no mass and no energy through the wall
+# while the viscous solver supplies the wall shear.  Pinned by those fluxes,
+# exact conservation of mass and energy in a closed box, and the decay rate
+# of a viscous shear wave between two walls (v = A sin(pi x) e^{-nu pi^2 t}).
+
+def _noslip_box(nx=4, nyz=2, seed=33):
+    mesh = I.box_mesh((nx, nyz, nyz), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=seed)
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL, (0, "hi"): I.BC_NOSLIP_WALL})
+    return mesh
+
+
+@pytest.mark.parametrize("stage", [1, 2])
+@pytest.mark.parametrize("viscous", [0, 1])
+def test_no_mass_or_energy_through_a_noslip_wall(oracle_mod, stage, viscous):
+    mesh = _noslip_box()
+    W, dW = _smooth_state(mesh)
+    om = oracle_mod.Mesh(mesh)
+    top = om.topology()
+    rec = om.face_records(oracle_mod.params(weno=1, viscous=viscous, mu=0.01), W, dW, 2e-3, stage)
+    wall = (top["face_lr"] < 0).any(axis=1)
+    scale = np.abs(rec[:, :5]).max()
+    for b in ((0, 5) if stage == 1 else (0,)):
+        F = rec[wall, b:b + 5]
+        assert np.abs(F[:, 0]).max() < 1e-14 * scale  # mass
+        assert np.abs(F[:, 4]).max() < 1e-14 * scale  # energy
+
+
+def test_noslip_closed_box_conserves_mass_and_energy(oracle_mod):
+    mesh = _noslip_box()
+    W, dW = _smooth_state(mesh)
+    om = oracle_mod.Mesh(mesh)
+    vol = om.geometry()["vol"]
+    W1, _, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.01), W, dW, nsteps=4)
+    tot0, tot1 = (W * vol).sum(1), (W1 * vol).sum(1)
+    for q in (0, 4):
+        assert abs(tot1[q] - tot0[q]) < 1e-14 * abs(tot0[q]), q
+    # the walls take momentum out (shear and pressure)
+    assert np.abs(tot1[1:4] - tot0[1:4]).max() > 1e-6
+
+
+def test_shear_wave_decays_at_the_viscous_rate(oracle_mod):
+    """8 cells across, mu = 0.002 (mean free path ~ 2e-3 of the gap, so the
+    BGK gas is in the Navier-Stokes regime), t = 2: the amplitude falls by
+    3.9 %, and the computed decrement matches nu pi^2 t to 1 %; the inviscid
+    solver keeps nearly all of the amplitude."""
+    mesh, W, dW = I.shear_decay_case(nx=8, nyz=2)
+    om = oracle_mod.Mesh(mesh)
+    vol = om.geometry()["vol"]
+    A0 = I.shear_decay_amplitude(mesh, W, vol=vol)
+    exact = A0 * math.exp(-0.002 * math.pi ** 2 * 2.0)
+    W1, _, t, _ = om.run(oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.002), W, dW, t_end=2.0)
+    A1 = I.shear_decay_amplitude(mesh, W1, vol=vol)
+    assert abs(A1 - exact) < 0.01 * (A0 - exact), (A0, A1, exact)
+    W2, _, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, t_end=2.0)
+    A2 = I.shear_decay_amplitude(mesh, W2, vol=vol)
+    assert A2 - exact > 0.5 * (A0 - exact), (A0, A2, exact)
