@@ -132,10 +132,17 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
  *                     and holds until the next such call; a mesh with fixed
  *                     faces needs 20 more working-precision reals a cell of
  *                     workspace.
+ *   GKS_BC_NOSLIP_WALL Sec. 4.4 non-slip adiabatic wall at rest: the ghost
+ *                     keeps rho and rho E and reverses the three momenta at
+ *                     each Gauss point; all derivatives of the momenta are
+ *                     kept, all derivatives of rho and rho E reversed
+ *                     (impermeable, no heat flux; the wall shear comes from
+ *                     the viscous solver, params.viscous = 1)
  * The interior reconstruction of a boundary cell is the one-sided one of
- * Sec. 4.4 (no constraint for these kinds): the cell's stencil simply lacks
- * the missing neighbour. */
-enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2 };
+ * Sec. 4.4 without constraint rows (for the non-slip wall the paper adds the
+ * wall velocity as a constraint; this library does not): the cell's stencil
+ * simply lacks the missing neighbour. */
+enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2, GKS_BC_NOSLIP_WALL = 3 };
 
 /* kind[n_cell][4] (host): the condition of local face f (the face opposite
  * tet vertex f) of each cell, read only where that face is a boundary face.

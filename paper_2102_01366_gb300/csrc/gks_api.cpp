@@ -175,7 +175,7 @@ extern "C" gks_status gks_mesh_set_boundary(gks_mesh* m, const int8_t* kind) {
         for (int f = 0; f < 4; ++f) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             const int8_t k = kind[c * 4 + f];
-            if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED) {
+            if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED && k != GKS_BC_NOSLIP_WALL) {
                 set_error("gks_mesh_set_boundary: unknown kind " + std::to_string((int)k) + " at cell " +
                           std::to_string(c) + " face " + std::to_string(f));
                 return GKS_E_ARG;

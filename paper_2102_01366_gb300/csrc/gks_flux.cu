@@ -112,8 +112,23 @@ __device__ __forceinline__ void slip_wall_ghost(T* Wt, T (*gt)[5]) {
     gt[2][1] = -gt[2][1];
 }
 
+// Non-slip adiabatic wall at rest (Sec. 4.4) in the face frame: rho and rho E
+// kept, the three momenta reversed; every derivative of the momenta kept,
+// every derivative of rho and rho E reversed.
+template <typename T>
+__device__ __forceinline__ void noslip_wall_ghost(T* Wt, T (*gt)[5]) {
+    Wt[1] = -Wt[1];
+    Wt[2] = -Wt[2];
+    Wt[3] = -Wt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        gt[j][0] = -gt[j][0];
+        gt[j][4] = -gt[j][4];
+    }
+}
+
 // device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
-constexpr int FLR_SLIP_WALL = -2, FLR_FIXED = -3;  // -1: open
+constexpr int FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4;  // -1: open
 
 // fixed boundary: the interior cell's fixed state (average and gradient)
 // extended linearly to the point X (relative to the cell's centroid)
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 
     // ---- phase 1 ----
     const int mine = side == 0 ? L : Rc;
-    const bool wall = mine == FLR_SLIP_WALL;
+    const bool wall = mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL;
     T Ws[5], gs[3][5];
     if (mine >= 0 || wall) {
         // a wall side starts from the interior cell's value at the point
@@ -214,7 +229,8 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     face_frame(n, Rm);
     T tW[5], tg[3][5];
     to_local(Rm, Ws, gs, tW, tg);
-    if (wall) slip_wall_ghost(tW, tg);
+    if (mine == FLR_SLIP_WALL) slip_wall_ghost(tW, tg);
+    if (mine == FLR_NOSLIP_WALL) noslip_wall_ghost(tW, tg);
     const Prim<T> S = to_prim(tW, ph.gm1);
     Tab<T> t;
     T a[3][5], A[5];
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
             const int cell = side == 0 ? L : Rc;
             T* Wv = side == 0 ? WL : WR;
             T (*g)[5] = side == 0 ? gL : gR;
-            if (cell >= 0 || cell == FLR_SLIP_WALL) {
+            if (cell >= 0 || cell == FLR_SLIP_WALL || cell == FLR_NOSLIP_WALL) {
                 // a wall side starts from the interior cell's value at the point
                 const int src = cell >= 0 ? side : 1 - side;
                 const int64_t c = cell >= 0 ? cell : (side == 0 ? Rc : L);
@@ -434,6 +450,8 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
         to_local(Rm, WR, gR, tWR, tgR);
         if (L == FLR_SLIP_WALL) slip_wall_ghost(tWL, tgL);
         if (Rc == FLR_SLIP_WALL) slip_wall_ghost(tWR, tgR);
+        if (L == FLR_NOSLIP_WALL) noslip_wall_ghost(tWL, tgL);
+        if (Rc == FLR_NOSLIP_WALL) noslip_wall_ghost(tWR, tgR);
         T Fh[5], D[5], W0[5], dWt[5];
         gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, D, W0, dWt);
         to_global(Rm, Fh);

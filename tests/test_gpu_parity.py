@@ -65,6 +65,11 @@ CASES = {
     "wall_reflection_weno": (lambda: I.wall_reflection_case(nx=8, nyz=2)[0],
                              lambda m: I.riemann_x_state(m, left=(1.0, 1.0, 1.0), right=(1.0, 1.0, 1.0)),
                              dict(weno=1)),
+    # non-slip adiabatic walls, viscous solver
+    "noslip_box_viscous": (lambda: _noslip(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1,
+                                                      seed=38)),
+                           lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.6, -0.3, 0.2)),
+                           dict(weno=1, viscous=1, mu=0.01)),
     # both ends fixed to the initial state (inflow state, wave profile)
     "shu_osher_small_weno": (lambda: I.shu_osher_case(nx=20, nyz=2, jitter=0.1)[0],
                              lambda m: I.shu_osher_state(m), dict(weno=1)),
@@ -73,6 +78,11 @@ CASES = {
 
 def _walled(mesh):
     mesh["bkind"] = I.wall_kinds(mesh, (0,))
+    return mesh
+
+
+def _noslip(mesh):
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL, (0, "hi"): I.BC_NOSLIP_WALL})
     return mesh
 
 

@@ -102,6 +102,25 @@ def test_fixed_ends_keep_a_stationary_contact(cuda, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_shear_wave_between_noslip_walls(cuda, precision):
+    """Viscous shear wave v = A sin(pi x) between non-slip adiabatic walls,
+    32 cells across (24,576 tets), mu = 0.002, to t = 2: the decrement of the
+    amplitude matches nu pi^2 t to 0.2 % (the oracle's 8-cell run: 1 %), mass
+    and total energy are conserved (impermeable, adiabatic walls at rest)."""
+    mesh, W, dW = I.shear_decay_case(nx=32, nyz=4)
+    g, Wg, _, t = _run(mesh, W, dW, 2.0, precision, weno=1, cfl=0.5, viscous=1, mu=0.002)
+    assert abs(t - 2.0) < 1e-12
+    vol = g.geometry()["vol"]
+    A0 = I.shear_decay_amplitude(mesh, W, vol=vol)
+    A1 = I.shear_decay_amplitude(mesh, Wg, vol=vol)
+    exact = A0 * math.exp(-0.002 * math.pi ** 2 * 2.0)
+    assert abs(A1 - exact) < 2e-3 * (A0 - exact), (A0, A1, exact)
+    tol = 1e-12 if precision == 0 else 1e-6
+    for q in (0, 4):
+        assert abs((Wg[q] * vol).sum() - (W[q] * vol).sum()) < tol * abs((W[q] * vol).sum()), q
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_shu_osher(cuda, precision):
     """Sec. 5.2 (a), 6 x 200 x 2 x 2 cells, third order, to t = 1.8.  The
     Mach-3 shock (speed 3.549 into the gas at rest) sits near x = 7.39; ahead
