@@ -212,9 +212,11 @@ __device__ __forceinline__ void micro_slope(const Prim<T>& s, T K, const T* b, T
 
 // Slopes a_x, a_y, a_z and A of a Maxwellian with conservative gradients
 // g[i][q] (Eq. co): <a_i psi> = g_i / rho, <(A + sum_i a_i u_i) psi> = 0.
+// r (may be NULL) receives <A psi> = -sum_i <(a_i . psi) u_i psi>, which
+// the flux needs again (rho <A psi> is the W-rate of the equilibrium part).
 template <typename T>
 __device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& full, T K,
-                                             const T (*g)[5], T (*a)[5], T* A) {
+                                             const T (*g)[5], T (*a)[5], T* A, T* r_out = nullptr) {
     const T ir = T(1) / s.rho;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -226,6 +228,9 @@ __device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& ful
     T r[5] = {T(0), T(0), T(0), T(0), T(0)};
     acc_grad<0>(full, a, T(-1), r);
     micro_slope(s, K, r, A);
+    if (r_out)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r_out[k] = r[k];
 }
 
 // Time coefficients of Eq. 2nd-flux over [0, dt/2] (k0, k1 for the kinetic
@@ -367,13 +372,14 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     // hydrodynamic (equilibrium) part: C1 g^c + C2 a^c.u g^c + C3 A^c g^c
     Tab<T> t;
     make_tab(t, C, ph.K, 0);
-    T ac[3][5], Ac[5];
-    state_slopes(C, t, ph.K, dWc, ac, Ac);
-    T mf0[5] = {0}, mf1[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+    T ac[3][5], Ac[5], rA[5];
+    state_slopes(C, t, ph.K, dWc, ac, Ac, rA);
+    T mf0[5] = {0}, mf1[5] = {0}, mf2[5] = {0}, mw1[5];
     acc_psi<1, 0, 0>(t, C.rho, mf0);
     acc_grad<1>(t, ac, C.rho, mf1);
     acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
-    acc_grad<0>(t, ac, C.rho, mw1);  // and rho <A^c psi> = -mw1 (Eq. co)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) mw1[k] = -C.rho * rA[k];  // rho sum_i <(a_i . psi) u_i psi> (Eq. co)
     if (ph.smooth) {
         // f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t, Eq. 2nd-smooth-flux
         const T hd = T(0.5) * dt;
@@ -397,119 +403,5 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     }
 }
 
-// The same kinetic solution with the work of one Gauss point split over a
-// lane pair (lanes 2j and 2j+1 of a warp, all 32 lanes active): lane "side"
-// owns the left (0) or right (1) initial state and its kinetic part; the
-// interface equilibrium and its slopes are summed over the pair by shuffles;
-// both lanes form the equilibrium slopes, then lane 0 adds the C2 (a^c.u)
-// flux terms and lane 1 the C1 and C3 flux terms and the dW term.  On return
-// both lanes hold the totals.
-template <typename T>
-__device__ __forceinline__ T pair_sum(T v) {
-    return v + __shfl_xor_sync(0xffffffffu, v, 1);
-}
-
-template <typename T>
-__device__ __forceinline__ void gks_point_pair(const Phys<T>& ph, int side, const T* Ws, const T (*gs)[5],
-                                               T dt, T* Fh, T* D, T* W0, T* dW) {
-    const Prim<T> S = to_prim(Ws, ph.gm1);
-    const T p_other = __shfl_xor_sync(0xffffffffu, S.p, 1);
-    Tab<T> t;
-    T a[3][5], A[5];
-    kinetic_side(ph, S, gs, side == 0 ? +1 : -1, t, a, A);
-    // W^c (Eq. new-equ-part): this side's half-space moments, summed over the pair
-    T mw0[5] = {T(0), T(0), T(0), T(0), T(0)};
-    acc_psi<0, 0, 0>(t, S.rho, mw0);
-    T Wc[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) Wc[k] = pair_sum(mw0[k]);
-    const Prim<T> C = to_prim(Wc, ph.gm1);
-    const T pl = side == 0 ? S.p : p_other, pr = side == 0 ? p_other : S.p;
-    const TimeCoef<T> tc = time_coefs(ph, pl, pr, C.p, dt);
-    const T tau = tc.tau;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        Fh[k] = T(0);
-        D[k] = T(0);
-        W0[k] = T(0);
-        dW[k] = T(0);
-    }
-    T dWc[3][5];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) dWc[i][k] = T(0);
-        acc_apsi<0, 0, 0>(t, a[i], S.rho, dWc[i]);
-    }
-    if (!ph.smooth) {
-        T mf0[5] = {0}, mf1[5] = {0}, mw1[5] = {0};
-        acc_psi<1, 0, 0>(t, S.rho, mf0);
-        acc_grad<1>(t, a, S.rho, mf1);
-        acc_grad<0>(t, a, S.rho, mw1);
-        axpy5(tc.k0, mf0, Fh);
-        axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
-        axpy5(tc.dk0, mf0, D);
-        axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
-        axpy5(T(1), mw0, W0);
-        axpy5(-tau, mw1, W0);
-        axpy5(tau - (tau + dt) * tc.E, mw1, dW);
-        if (ph.viscous) {
-            T mf2[5] = {0}, mw2[5] = {0};
-            acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
-            acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
-            axpy5(-tau * tc.k0, mf2, Fh);
-            axpy5(-tau * tc.dk0, mf2, D);
-            axpy5(-tau, mw2, W0);
-            axpy5(tau * (T(1) - tc.E), mw2, dW);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) dWc[i][k] = pair_sum(dWc[i][k]);
-
-    // hydrodynamic (equilibrium) part, moments divided between the lanes
-    make_tab(t, C, ph.K, 0);
-    T ac[3][5], Ac[5];
-    state_slopes(C, t, ph.K, dWc, ac, Ac);
-    if (side == 0) {
-        T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
-        acc_grad<1>(t, ac, C.rho, mf1);
-        if (ph.smooth) {
-            axpy5(-tau * T(0.5) * dt, mf1, Fh);
-        } else {
-            axpy5(tc.q2, mf1, Fh);
-            axpy5(tc.dq2, mf1, D);
-        }
-    } else {
-        T mf0[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
-        acc_psi<1, 0, 0>(t, C.rho, mf0);
-        acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
-        acc_grad<0>(t, ac, C.rho, mw1);  // rho <A^c psi> = -mw1 (Eq. co)
-        if (ph.smooth) {
-            const T hd = T(0.5) * dt;
-            axpy5(hd, mf0, Fh);
-            axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
-            axpy5(T(0.25) * dt * dt, mf2, D);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) W0[k] = Wc[k];  // tau terms cancel: <(a.u + A) psi> = 0
-            axpy5(-dt, mw1, dW);
-        } else {
-            axpy5(tc.q1, mf0, Fh);
-            axpy5(tc.q3, mf2, Fh);
-            axpy5(tc.dq1, mf0, D);
-            axpy5(tc.dq3, mf2, D);
-            const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
-            axpy5(C2 - C3, mw1, dW);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        Fh[k] = pair_sum(Fh[k]);
-        D[k] = pair_sum(D[k]);
-        W0[k] = pair_sum(W0[k]);
-        dW[k] = pair_sum(dW[k]);
-    }
-}
 
 }  // namespace gks

@@ -159,7 +159,8 @@ __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
 // partial outputs are exchanged through shared memory:
 //   phase 1  own side: state at the point, face frame, slopes, rho <psi>+-
 //   phase 2  W^c, collision times; own kinetic part; rho <a_i psi>+-
-//   phase 3  equilibrium slopes; left warps add the C2 (a^c.u) flux terms,
+//   phase 3  right warps form the equilibrium slopes (once per point) and
+//            share a^c; then left warps add the C2 (a^c.u) flux terms,
 //            right warps the C1, C3 flux terms and the dW term
 //   phase 4  left warps finish the flux entries, right warps the gradient
 //            entries of the record; the 3 points of each face are summed.
@@ -170,6 +171,7 @@ struct FluxSmem {
     T w0[2][FP_GP][5];   // rho <psi>+- of each side
     T p[2][FP_GP];       // pressure of each side
     T dwc[2][FP_GP][15]; // rho <a_i psi>+- of each side
+    T ac[FP_GP][15];     // equilibrium slopes a^c_i (formed once, by the right warps)
     T out[2][FP_GP][20]; // partial Fh, D, W0, dW of each side
     T red[FP_GP * NR];   // weighted record entries per Gauss point
 };
@@ -289,15 +291,27 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 
     // ---- phase 3 ----
     {
-        T dWc[3][5];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) dWc[i][q] = sm.dwc[0][g][5 * i + q] + sm.dwc[1][g][5 * i + q];
         make_tab(t, C, ph.K, 0);
-        T ac[3][5], Ac[5];
-        state_slopes(C, t, ph.K, dWc, ac, Ac);
+        T ac[3][5], Ac[5], rA[5];
+        if (side == 1) {
+            // the equilibrium slopes, once per point (Eq. co for g^c)
+            T dWc[3][5];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) dWc[i][q] = sm.dwc[0][g][5 * i + q] + sm.dwc[1][g][5 * i + q];
+            state_slopes(C, t, ph.K, dWc, ac, Ac, rA);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
+        }
+        __syncthreads();
         if (side == 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) ac[i][q] = sm.ac[g][5 * i + q];
             T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
             acc_grad<1>(t, ac, C.rho, mf1);
             if (ph.smooth) {
@@ -307,10 +321,11 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
                 axpy5(tc.dq2, mf1, D);
             }
         } else {
-            T mf0[5] = {0}, mf2[5] = {0}, mw1[5] = {0};
+            T mf0[5] = {0}, mf2[5] = {0}, mw1[5];
             acc_psi<1, 0, 0>(t, C.rho, mf0);
             acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
-            acc_grad<0>(t, ac, C.rho, mw1);  // rho <A^c psi> = -mw1 (Eq. co)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) mw1[q] = -C.rho * rA[q];  // rho sum_i <(a_i . psi) u_i psi> (Eq. co)
             if (ph.smooth) {
                 const T hd = T(0.5) * dt;
                 axpy5(hd, mf0, Fh);
