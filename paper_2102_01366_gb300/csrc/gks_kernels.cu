@@ -25,7 +25,8 @@ namespace gks {
 // per-case minimum of the local limits of the cells of a block: the block's
 // cells are contiguous and so are the cases, so its cases form runs; one
 // thread scans the 24 values and issues one atomicMin per run (the minimum
-// is exact, so the result does not depend on the order)
+// is exact, so the result does not depend on the order; the result of the
+// atomic is not used, so it does not stall the thread)
 __device__ void block_case_min(double v, int32_t cas, bool valid, int lc, unsigned long long* dtmin) {
     __shared__ double sv[CELLS_PER_BLOCK];
     __shared__ int32_t sc[CELLS_PER_BLOCK];
@@ -37,11 +38,9 @@ __device__ void block_case_min(double v, int32_t cas, bool valid, int lc, unsign
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // an update only when it can lower the current minimum: most blocks
-        // then issue no atomic at all
+        // positive doubles order like their bit patterns
         auto commit = [&](int32_t k, double v) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-            if (b < *((volatile unsigned long long*)(dtmin + k))) atomicMin(dtmin + k, b);
+            atomicMin(dtmin + k, (unsigned long long)__double_as_longlong(v));
         };
         int32_t cur = -1;
         double mn = INFINITY;
