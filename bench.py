@@ -45,8 +45,8 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # (fadd + fmul + 2 ffma) counted by ncu on this workload (147,840 Gauss points
 # a launch), and its DRAM bytes per stage-1 launch from the same capture (the
 # flux kernel's summary under profiles/)
-FLUX_FLOPS_PER_GP = {"fp32": (4746.6, 4643.3)}
-FLUX_DRAM_BYTES_PER_LAUNCH = 10.46e6
+FLUX_FLOPS_PER_GP = {"fp32": (4216.6, 4114.3)}
+FLUX_DRAM_BYTES_PER_LAUNCH = 10.42e6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
