@@ -117,3 +117,11 @@ def test_batch_connectivity_matches_each_case(built, oracle_mod):
     bad["case"] = batch["case"][::-1].copy()
     with pytest.raises(gks.GksError):
         gks.Mesh(bad)
+
+
+def test_empty_mesh_is_rejected(built):
+    mesh = {"xyz": np.zeros((0, 3)), "tet": np.zeros((0, 4), np.int64), "shift": np.zeros((0, 4, 3), np.int8),
+            "period": np.zeros(3)}
+    with pytest.raises(gks.GksError) as e:
+        gks.Mesh(mesh)
+    assert e.value.status == -1
