@@ -294,6 +294,29 @@ gks_status gks_timestep_noalloc(const gks_params* p, const double* d_W, const do
  * synchronises). */
 gks_status gks_residual(gks_state* state, double* out_l2);
 
+/* -------------------------------------------------------------- adjoint -- */
+
+/* The paper differentiates nothing: this is the reverse (adjoint) mode of one
+ * step, for gradients of an output of a run with respect to its initial
+ * state.  Given the adjoint of the step's result, (lamW [5][nc], lamdW
+ * [15][nc]) = d J / d (W^{n+1}, grad W^{n+1}), it returns d J / d (W^n,
+ * grad W^n) in (lamW_out, lamdW_out), with the time step frozen at dt: the
+ * transpose of the step's Jacobian at (d_W, d_dW) applied to (lamW, lamdW).
+ * It first recomputes the step's two reconstructions from (d_W, d_dW), so a
+ * run of N steps back-propagates from the N saved (or recomputed) states.
+ * Supported: FP64 states (precision 0) with linear reconstruction weights
+ * (weno = 0, order 3), full or smooth flux, Euler or viscous, single-case
+ * meshes without boundary faces; GKS_E_UNSUPPORTED otherwise, and also when a
+ * cell of either stage falls back to a constant reconstruction (the
+ * positivity branch, whose derivative this does not build).  All arrays are
+ * device FP64; d_scratch (gks_adjoint_workspace_bytes) is caller-allocated
+ * device memory.  On return the state is initialised at (d_W, d_dW) with its
+ * time reset.  Synchronises. */
+size_t gks_adjoint_workspace_bytes(const gks_state* state);
+gks_status gks_adjoint_step(gks_state* state, double dt, const double* d_W, const double* d_dW,
+                            const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
+                            double* d_lamdW_out, void* d_scratch, size_t scratch_bytes);
+
 /* ---------------------------------------------------- tuning variants -- */
 
 /* Execution variant of a state (the same arithmetic, only speed differs):

@@ -1,0 +1,341 @@
+// gks_adjoint.cu -- reverse (adjoint) sweep of one two-stage step, FP64.
+//
+// Given the adjoint of the step's result, (lambda W^{n+1}, lambda grad
+// W^{n+1}), these kernels return the adjoint of its start, (lambda W^n,
+// lambda grad W^n): the transpose of the step's Jacobian applied to a vector,
+// with the time step frozen.  Every part of the step but the kinetic solution
+// at a Gauss point is linear in the working state (the linear-weight
+// reconstruction, the evaluation of R at the Gauss points, the face frame
+// rotations, the stage records of Eqs. linear-system and s2o4, the update of
+// averages and of gradients by Eq. gauss-formula); those are transposed by
+// hand, each as a gather so that no two threads write one location.  The
+// kinetic solution (Eq. 2nd-flux with Eq. new-equ-part) is differentiated in
+// forward mode: the same templated point code runs on Dual numbers, one
+// input direction a pass (40 passes a point: wider Duals multiply the code
+// the compiler has to schedule), and each Jacobian column is contracted with
+// the output adjoints at once.
+//
+//   k_adj_src2 / k_adj_src1  per-cell adjoints of the face-record sums
+//   k_adj_flux<NR>           per face: record adjoints -> adjoints of both
+//                            cells' reconstruction coefficients
+//   k_adj_gather_poly        per cell: sum over its four faces
+//   k_adj_recon_local        per cell: transpose of a = M2 d and of the
+//                            monomial constant
+//   k_adj_recon_gather       per cell: adjoint of its working state from its
+//                            own and its neighbours' stencil adjoints
+//   k_adj_final              the three paths into (W^n, grad W^n)
+#include <cuda_runtime.h>
+
+#include "gks_cells.cuh"
+#include "gks_device.cuh"
+#include "gks_dual.cuh"
+#include "gks_face.cuh"
+#include "gks_kernels.h"
+
+namespace gks {
+
+constexpr int ADW = 1;           // directions per forward-mode pass
+constexpr int ADJ_IN = 40;       // inputs of the point solution: WL, gL, WR, gR (face frame)
+constexpr int ADJ_THREADS = 64;  // threads (faces) per block of k_adj_flux
+
+// stage 2 records: [sum w 4/3 D (5) | sum w dW n (15)]; the cell sums enter
+// W^{n+1} = W^n - (S + sum s rec[0:5]) / |Omega| and
+// grad W^{n+1} = (G + sum s rec[5:20]) / |Omega|
+__global__ void k_adj_src2(DevMesh<double> m, const double* __restrict__ lW, const double* __restrict__ ldW,
+                           double* __restrict__ src) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    const double iv = m.inv_vol[c];
+    double* o = src + c * 20;
+    for (int q = 0; q < 5; ++q) o[q] = -lW[q * m.nc + c] * iv;
+    for (int j = 0; j < 15; ++j) o[5 + j] = ldW[j * m.nc + c] * iv;
+}
+
+// stage 1 records: [sum w Fh | sum w (2 Fh - D/3) | sum w W* n | sum w W0 n];
+// they enter W* = W^n - sum s rec[0:5] / |Omega|, S = sum s rec[5:10] (into
+// W^{n+1} with -1/|Omega|), grad W* = sum s rec[10:25] / |Omega| and
+// G = sum s rec[25:40] (into grad W^{n+1} with 1/|Omega|)
+__global__ void k_adj_src1(DevMesh<double> m, const double* __restrict__ lW, const double* __restrict__ ldW,
+                           const double* __restrict__ lXs, double* __restrict__ src) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    const double iv = m.inv_vol[c];
+    const double* xs = lXs + c * XS;
+    double* o = src + c * 40;
+    for (int q = 0; q < 5; ++q) {
+        o[q] = -xs[q] * iv;
+        o[5 + q] = -lW[q * m.nc + c] * iv;
+    }
+    for (int j = 0; j < 15; ++j) {
+        o[10 + j] = xs[5 + j] * iv;
+        o[25 + j] = ldW[j * m.nc + c] * iv;
+    }
+}
+
+// adjoint of eval_poly: lc += (d val / d c)^T lv + (d g / d c)^T lg
+__device__ __forceinline__ void eval_poly_adj(const double* X, const double* lv, const double (*lg)[5],
+                                              double* lc) {
+    const double x = X[0], y = X[1], z = X[2];
+    for (int q = 0; q < 5; ++q) {
+        double* c = lc + q * 10;
+        const double v = lv[q], g0 = lg[0][q], g1 = lg[1][q], g2 = lg[2][q];
+        c[0] += v;
+        c[1] += v * x + g0;
+        c[2] += v * y + g1;
+        c[3] += v * z + g2;
+        c[4] += v * x * x + 2.0 * x * g0;
+        c[5] += v * x * y + y * g0 + x * g1;
+        c[6] += v * x * z + z * g0 + x * g2;
+        c[7] += v * y * y + 2.0 * y * g1;
+        c[8] += v * y * z + z * g1 + y * g2;
+        c[9] += v * z * z + 2.0 * z * g2;
+    }
+}
+
+// adjoint of to_local: (lW, lg) global from (lWt, lgt) in the face frame
+__device__ __forceinline__ void to_local_adj(const double (*Rm)[3], const double* lWt, const double (*lgt)[5],
+                                             double* lW, double (*lg)[5]) {
+    lW[0] = lWt[0];
+    lW[4] = lWt[4];
+    for (int i = 0; i < 3; ++i) lW[1 + i] = Rm[0][i] * lWt[1] + Rm[1][i] * lWt[2] + Rm[2][i] * lWt[3];
+    double lh[3][5];
+    for (int j = 0; j < 3; ++j) {
+        lh[j][0] = lgt[j][0];
+        lh[j][4] = lgt[j][4];
+        for (int l = 0; l < 3; ++l)
+            lh[j][1 + l] = Rm[0][l] * lgt[j][1] + Rm[1][l] * lgt[j][2] + Rm[2][l] * lgt[j][3];
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int q = 0; q < 5; ++q) lg[i][q] = Rm[0][i] * lh[0][q] + Rm[1][i] * lh[1][q] + Rm[2][i] * lh[2][q];
+}
+
+// the momentum block of a global vector in the face frame (the adjoint of
+// to_global)
+__device__ __forceinline__ void rotate_in(const double (*Rm)[3], double* v) {
+    const double a = v[1], b = v[2], c = v[3];
+    for (int j = 0; j < 3; ++j) v[1 + j] = Rm[j][0] * a + Rm[j][1] * b + Rm[j][2] * c;
+}
+
+// One thread per face (interior faces only).  For each Gauss point: the
+// point's inputs are re-evaluated from the stored reconstruction, the output
+// adjoints follow from the record adjoints (the transposed record formulas of
+// the stage), the point solution is differentiated in forward mode and its
+// Jacobian contracted with them, and the result is carried back through the
+// rotations and the evaluation at the point into lpf[f][side][5][10].
+template <int NR>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_flux(DevMesh<double> m, Phys<double> ph,
+                                                          const double* __restrict__ poly,
+                                                          const double* __restrict__ src, double dt,
+                                                          double* __restrict__ lpf) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.nf) return;
+    const int L = m.flr[f], R = m.flr[m.nf + f];
+    const double* geo = m.fgeo + f * FGEO;
+    const double n[3] = {geo[0], geo[1], geo[2]};
+    const double w = geo[3];
+    double Rm[3][3];
+    face_frame(n, Rm);
+    // record adjoints: the left cell adds the record, the right one subtracts it
+    double lr[NR];
+    for (int j = 0; j < NR; ++j) lr[j] = src[(int64_t)L * NR + j] - src[(int64_t)R * NR + j];
+    // output adjoints of every point (global frame, then face frame)
+    double lFh[5], lD[5], lW0[5], ldWt[5];
+    for (int q = 0; q < 5; ++q) {
+        double sn0 = 0.0, sn1 = 0.0;
+        if (NR == 40) {
+            for (int i = 0; i < 3; ++i) {
+                sn0 += n[i] * lr[10 + 3 * q + i];
+                sn1 += n[i] * lr[25 + 3 * q + i];
+            }
+            lFh[q] = w * (lr[q] + 2.0 * lr[5 + q]);
+            lD[q] = -w * (1.0 / 3.0) * lr[5 + q];
+            lW0[q] = w * (sn0 + sn1);
+            ldWt[q] = 0.5 * w * sn0;
+        } else {
+            for (int i = 0; i < 3; ++i) sn0 += n[i] * lr[5 + 3 * q + i];
+            lFh[q] = 0.0;
+            lD[q] = w * (4.0 / 3.0) * lr[q];
+            lW0[q] = 0.0;
+            ldWt[q] = w * sn0;
+        }
+    }
+    rotate_in(Rm, lFh);
+    rotate_in(Rm, lD);
+    rotate_in(Rm, lW0);
+    rotate_in(Rm, ldWt);
+
+    Phys<Dual<ADW>> pd;
+    pd.gamma = ph.gamma;
+    pd.gm1 = ph.gm1;
+    pd.K = ph.K;
+    pd.tau_eps = ph.tau_eps;
+    pd.tau_c = ph.tau_c;
+    pd.mu = ph.mu;
+    pd.eps_w = ph.eps_w;
+    pd.viscous = ph.viscous;
+    pd.smooth = ph.smooth;
+
+    double lpL[50], lpR[50];
+    for (int j = 0; j < 50; ++j) lpL[j] = lpR[j] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double XL[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
+        const double XR[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
+        double WL[5], gL[3][5], WR[5], gR[3][5];
+        eval_poly(poly + (int64_t)L * POLY_STRIDE, XL, WL, gL);
+        eval_poly(poly + (int64_t)R * POLY_STRIDE, XR, WR, gR);
+        double x[ADJ_IN];
+        to_local(Rm, WL, gL, x, reinterpret_cast<double (*)[5]>(x + 5));
+        to_local(Rm, WR, gR, x + 20, reinterpret_cast<double (*)[5]>(x + 25));
+        double lx[ADJ_IN];
+        for (int p = 0; p < ADJ_IN / ADW; ++p) {
+            Dual<ADW> in[ADJ_IN];
+            for (int j = 0; j < ADJ_IN; ++j) {
+                in[j] = Dual<ADW>(x[j]);
+                if (j / ADW == p) in[j].d[j % ADW] = 1.0;
+            }
+            Dual<ADW> Fh[5], D[5], W0[5], dW[5];
+            gks_point(pd, in, reinterpret_cast<const Dual<ADW>(*)[5]>(in + 5), in + 20,
+                      reinterpret_cast<const Dual<ADW>(*)[5]>(in + 25), Dual<ADW>(dt), Fh, D, W0, dW);
+            for (int j = 0; j < ADW; ++j) {
+                double acc = 0.0;
+                for (int q = 0; q < 5; ++q)
+                    acc += lFh[q] * Fh[q].d[j] + lD[q] * D[q].d[j] + lW0[q] * W0[q].d[j] + ldWt[q] * dW[q].d[j];
+                lx[p * ADW + j] = acc;
+            }
+        }
+        double lWL[5], lgL[3][5], lWR[5], lgR[3][5];
+        to_local_adj(Rm, lx, reinterpret_cast<const double (*)[5]>(lx + 5), lWL, lgL);
+        to_local_adj(Rm, lx + 20, reinterpret_cast<const double (*)[5]>(lx + 25), lWR, lgR);
+        eval_poly_adj(XL, lWL, lgL, lpL);
+        eval_poly_adj(XR, lWR, lgR, lpR);
+    }
+    double* o = lpf + f * 100;
+    for (int j = 0; j < 50; ++j) {
+        o[j] = lpL[j];
+        o[50 + j] = lpR[j];
+    }
+}
+
+// adjoint of a cell's reconstruction coefficients: the sum over its faces
+__global__ void k_adj_gather_poly(DevMesh<double> m, const double* __restrict__ lpf, double* __restrict__ lp) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    double acc[50];
+    for (int j = 0; j < 50; ++j) acc[j] = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        const int e = m.cface[f * m.nc + c];
+        const double* src = lpf + (int64_t)(e >> 1) * 100 + (e & 1) * 50;
+        for (int j = 0; j < 50; ++j) acc[j] += src[j];
+    }
+    for (int j = 0; j < 50; ++j) lp[c * 50 + j] = acc[j];
+}
+
+// Transpose of the linear-weight reconstruction of one cell (Sec. 4.1):
+// R = a = M2 d, c0 = Q0 - sum_k R_k M_k (second moments), with
+// d = [Q_nb - Q0 (4); grad Q_nb (12)].  Writes ld[c][q][16] = M2^T lambda_a
+// and own[c][q] = lambda_c0 - sum over existing neighbours of ld[c][q][f].
+__global__ void k_adj_recon_local(DevMesh<double> m, const double* __restrict__ lp, double* __restrict__ ld,
+                                  double* __restrict__ own) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t c = idx / 5;
+    const int q = (int)(idx - c * 5);
+    const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
+    auto T_ = [&](int row) { return tile[(int64_t)row * CELLS_PER_BLOCK]; };
+    const double* l = lp + c * 50 + q * 10;
+    const double lc0 = l[0];
+    double la[9];
+    for (int k = 0; k < 9; ++k) la[k] = l[1 + k];
+    for (int k = 3; k < 9; ++k) la[k] -= lc0 * T_(TILE_MOM + (k - 3));
+    double* o = ld + (c * 5 + q) * 16;
+    double s = 0.0;
+    for (int j = 0; j < 16; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += T_(TILE_M2 + k * 16 + j) * la[k];
+        o[j] = acc;
+    }
+    for (int f = 0; f < 4; ++f)
+        if (m.nbr[f * m.nc + c] >= 0) s += o[f];
+    own[c * 5 + q] = lc0 - s;
+}
+
+// adjoint of a cell's working state [W (5), grad W (15)]: its own part and,
+// from each neighbour n, the entries of n's stencil adjoint in the slot that
+// points back to this cell across the shared face (rev[f][c])
+__global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__ rev,
+                                   const double* __restrict__ ld, const double* __restrict__ own,
+                                   double* __restrict__ lX) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t c = idx / 5;
+    const int q = (int)(idx - c * 5);
+    double lq = own[c * 5 + q];
+    double lg[3] = {0.0, 0.0, 0.0};
+    for (int f = 0; f < 4; ++f) {
+        const int n = m.nbr[f * m.nc + c];
+        if (n < 0) continue;
+        const int r = rev[f * m.nc + c];
+        const double* o = ld + ((int64_t)n * 5 + q) * 16;
+        lq += o[r];
+        for (int l = 0; l < 3; ++l) lg[l] += o[4 + 3 * r + l];
+    }
+    double* x = lX + c * XS;
+    x[q] = lq;
+    for (int l = 0; l < 3; ++l) x[5 + 3 * q + l] = lg[l];
+}
+
+// lambda W^n = lambda W^{n+1} (the update's pass-through) + lambda W* (the
+// stage-1 pass-through) + the stage-1 reconstruction's; lambda grad W^n from
+// the stage-1 reconstruction alone
+__global__ void k_adj_final(DevMesh<double> m, const double* __restrict__ lW, const double* __restrict__ lXs,
+                            const double* __restrict__ lX1, double* __restrict__ oW, double* __restrict__ odW) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    for (int q = 0; q < 5; ++q) oW[q * m.nc + c] = lW[q * m.nc + c] + lXs[c * XS + q] + lX1[c * XS + q];
+    for (int j = 0; j < 15; ++j) odW[j * m.nc + c] = lX1[c * XS + 5 + j];
+}
+
+// --------------------------------------------------------------------------
+// launcher
+// --------------------------------------------------------------------------
+static inline unsigned grid_of(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+static Phys<double> phys64(const HostPhys& p) {
+    Phys<double> ph;
+    ph.gamma = p.gamma;
+    ph.gm1 = p.gamma - 1.0;
+    ph.K = (5.0 - 3.0 * p.gamma) / (p.gamma - 1.0);
+    ph.tau_eps = p.tau_eps;
+    ph.tau_c = p.tau_c;
+    ph.mu = p.mu;
+    ph.eps_w = p.eps_weno;
+    ph.viscous = p.viscous;
+    ph.smooth = p.smooth;
+    return ph;
+}
+
+// The reverse sweep proper; the forward intermediates (poly1, poly2) come from
+// a forward recomputation by the caller.
+cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,
+                            const double* lW, const double* ldW, double* oW, double* odW, cudaStream_t s) {
+    const Phys<double> ph = phys64(p);
+    const int B = 128;
+    cudaError_t e;
+    // stage 2
+    k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
+    k_adj_flux<20><<<grid_of(m.nf, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lpf);
+    k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
+    k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
+    k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lXs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // stage 1
+    k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
+    k_adj_flux<40><<<grid_of(m.nf, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lpf);
+    k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
+    k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
+    k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lX1);
+    k_adj_final<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, b.lXs, b.lX1, oW, odW);
+    return cudaGetLastError();
+}
+
+}  // namespace gks

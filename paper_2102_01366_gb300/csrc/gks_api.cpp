@@ -853,6 +853,115 @@ extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
     return GKS_OK;
 }
 
+// --------------------------------------------------------------- adjoint --
+
+namespace {
+struct AdjLayout {
+    size_t poly1, src, lpf, lp, ld, own, lXs, lX1, rev, fallback, total = 0;
+    size_t add(size_t bytes) {
+        size_t off = total;
+        total += (bytes + 255) & ~(size_t)255;
+        return off;
+    }
+};
+
+AdjLayout adj_layout(int64_t nc, int64_t nf) {
+    AdjLayout L;
+    L.poly1 = L.add(8 * POLY_STRIDE * nc);
+    L.src = L.add(8 * 40 * nc);
+    L.lpf = L.add(8 * 100 * nf);
+    L.lp = L.add(8 * 50 * nc);
+    L.ld = L.add(8 * 80 * nc);
+    L.own = L.add(8 * 5 * nc);
+    L.lXs = L.add(8 * XS * nc);
+    L.lX1 = L.add(8 * XS * nc);
+    L.rev = L.add(4 * nc);
+    L.fallback = L.add(4 * 2 * nc);
+    return L;
+}
+}  // namespace
+
+extern "C" size_t gks_adjoint_workspace_bytes(const gks_state* s) {
+    if (!s) return 0;
+    return adj_layout(s->mesh->nc, s->mesh->nf).total;
+}
+
+extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_W, const double* d_dW,
+                                       const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
+                                       double* d_lamdW_out, void* d_scratch, size_t scratch_bytes) {
+    if (!s || !d_W || !d_dW || !d_lamW || !d_lamdW || !d_lamW_out || !d_lamdW_out || !d_scratch) {
+        set_error("gks_adjoint_step: NULL argument");
+        return GKS_E_ARG;
+    }
+    if (!(dt > 0.0) || !std::isfinite(dt)) { set_error("gks_adjoint_step: dt must be positive"); return GKS_E_ARG; }
+    const gks_mesh& g = *s->mesh;
+    const AdjLayout A = adj_layout(g.nc, g.nf);
+    if (scratch_bytes < A.total) {
+        set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
+        return GKS_E_NOMEM;
+    }
+    if (s->fp32 || s->params.weno != 0 || s->params.order != 3 || g.nbf != 0 || g.ncase != 1) {
+        set_error("gks_adjoint_step: needs an FP64 state with linear weights (weno 0, order 3) on a "
+                  "single-case mesh without boundary faces");
+        return GKS_E_UNSUPPORTED;
+    }
+    order_after_caller(s);
+    DevMesh<double>& m = s->m64;
+    DevState<double>& st = s->s64;
+    const int64_t nc = g.nc;
+    char* base = static_cast<char*>(d_scratch);
+    // reverse face slots: rev[f][c] = the local face of neighbour n = nbr(c, f)
+    // that is the same face
+    std::vector<int8_t> rev((size_t)4 * nc, 0);
+    for (int64_t c = 0; c < nc; ++c)
+        for (int f = 0; f < 4; ++f) {
+            const int64_t n = g.nbr[c * 4 + f];
+            if (n < 0) continue;
+            const int64_t fi = g.csr_face[c * 4 + f];
+            for (int r = 0; r < 4; ++r)
+                if (g.csr_face[n * 4 + r] == fi) rev[(size_t)f * nc + c] = (int8_t)r;
+        }
+    GKS_CHECK_CUDA(cudaMemcpyAsync(base + A.rev, rev.data(), rev.size(), cudaMemcpyHostToDevice, s->stream));
+    // forward recomputation of the step's two reconstructions with the frozen dt
+    gks_status r = init_impl<double>(s, m, st, d_W, d_dW);
+    if (r != GKS_OK) return r;
+    s->initialised = true;
+    const double dth = dt;
+    GKS_CHECK_CUDA(cudaMemcpyAsync(st.case_dt, &dth, 8, cudaMemcpyHostToDevice, s->stream));
+    int32_t* fb = reinterpret_cast<int32_t*>(base + A.fallback);
+    double* poly1 = reinterpret_cast<double*>(base + A.poly1);
+    GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.X, nullptr, nullptr, st.poly, fb, nullptr, st.err,
+                                         s->stream));
+    GKS_CHECK_CUDA(cudaMemcpyAsync(poly1, st.poly, 8 * POLY_STRIDE * nc, cudaMemcpyDeviceToDevice, s->stream));
+    GKS_CHECK_CUDA(Launch<double>::flux(m, s->phys, st.X, st.poly, st.rec, st.case_dt, 0.0, 1, s->stream,
+                                        s->flux_variant));
+    GKS_CHECK_CUDA(Launch<double>::update1(m, st, s->stream));
+    GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.Xs, nullptr, nullptr, st.poly, fb + nc, nullptr, st.err,
+                                         s->stream));
+    std::vector<int32_t> flags((size_t)2 * nc);
+    GKS_CHECK_CUDA(cudaMemcpyAsync(flags.data(), fb, 8 * nc, cudaMemcpyDeviceToHost, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    for (int32_t v : flags)
+        if (v) {
+            set_error("gks_adjoint_step: a cell falls back to a constant reconstruction (positivity branch)");
+            return GKS_E_UNSUPPORTED;
+        }
+    AdjBuffers b;
+    b.poly1 = poly1;
+    b.poly2 = st.poly;
+    b.src = reinterpret_cast<double*>(base + A.src);
+    b.lpf = reinterpret_cast<double*>(base + A.lpf);
+    b.lp = reinterpret_cast<double*>(base + A.lp);
+    b.ld = reinterpret_cast<double*>(base + A.ld);
+    b.own = reinterpret_cast<double*>(base + A.own);
+    b.lXs = reinterpret_cast<double*>(base + A.lXs);
+    b.lX1 = reinterpret_cast<double*>(base + A.lX1);
+    b.rev = reinterpret_cast<const int8_t*>(base + A.rev);
+    b.fallback = fb;
+    GKS_CHECK_CUDA(adjoint_reverse(m, s->phys, dt, b, d_lamW, d_lamdW, d_lamW_out, d_lamdW_out, s->stream));
+    return gks_sync(s);
+}
+
 // ----------------------------------------------------------- diagnostics --
 
 template <typename T>

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "gks_device.cuh"
+#include "gks_face.cuh"
 #include "gks_kernels.h"
 
 namespace gks {
@@ -20,83 +21,6 @@ namespace gks {
 // --------------------------------------------------------------------------
 // face flux
 // --------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T* val, T (*g)[5]) {
-    // the record is 16-byte aligned (POLY_STRIDE words): load it in vectors
-    T c[POLY_STRIDE];
-    if constexpr (sizeof(T) == 4) {
-        const float4* p4 = reinterpret_cast<const float4*>(P);
-#pragma unroll
-        for (int i = 0; i < POLY_STRIDE / 4; ++i) {
-            const float4 v = __ldg(p4 + i);
-            c[4 * i] = v.x;
-            c[4 * i + 1] = v.y;
-            c[4 * i + 2] = v.z;
-            c[4 * i + 3] = v.w;
-        }
-    } else {
-        const double2* p2 = reinterpret_cast<const double2*>(P);
-#pragma unroll
-        for (int i = 0; i < POLY_STRIDE / 2; ++i) {
-            const double2 v = __ldg(p2 + i);
-            c[2 * i] = v.x;
-            c[2 * i + 1] = v.y;
-        }
-    }
-    const T x = X[0], y = X[1], z = X[2];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const T* cq = c + q * 10;
-        val[q] = cq[0] + cq[1] * x + cq[2] * y + cq[3] * z + cq[4] * x * x + cq[5] * x * y + cq[6] * x * z +
-                 cq[7] * y * y + cq[8] * y * z + cq[9] * z * z;
-        g[0][q] = cq[1] + T(2) * cq[4] * x + cq[5] * y + cq[6] * z;
-        g[1][q] = cq[2] + cq[5] * x + T(2) * cq[7] * y + cq[8] * z;
-        g[2][q] = cq[3] + cq[6] * x + cq[8] * y + T(2) * cq[9] * z;
-    }
-}
-
-// rows of the face frame: n, t1, t2 (Eq. rotate-matrix-3d; n1 = -1 uses the
-// reflection diag(-1, -1, 1) of the velocity block)
-template <typename T>
-__device__ __forceinline__ void face_frame(const T* n, T (*Rm)[3]) {
-    const T n1 = n[0], n2 = n[1], n3 = n[2];
-    Rm[0][0] = n1;
-    Rm[0][1] = n2;
-    Rm[0][2] = n3;
-    if (n1 == T(-1)) {
-        Rm[1][0] = T(0); Rm[1][1] = T(-1); Rm[1][2] = T(0);
-        Rm[2][0] = T(0); Rm[2][1] = T(0); Rm[2][2] = T(1);
-        return;
-    }
-    const T r = T(1) / (T(1) + n1);
-    Rm[1][0] = -n2;
-    Rm[1][1] = n1 + n3 * n3 * r;
-    Rm[1][2] = -n2 * n3 * r;
-    Rm[2][0] = -n3;
-    Rm[2][1] = -n2 * n3 * r;
-    Rm[2][2] = T(1) - n3 * n3 * r;
-}
-
-template <typename T>
-__device__ __forceinline__ void to_local(const T (*Rm)[3], const T* W, const T (*g)[5], T* Wt,
-                                         T (*gt)[5]) {
-    Wt[0] = W[0];
-    Wt[4] = W[4];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Wt[1 + j] = Rm[j][0] * W[1] + Rm[j][1] * W[2] + Rm[j][2] * W[3];
-    // directions first: h_j = sum_i R_ji g_i, then the momentum components
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        T h[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) h[q] = Rm[j][0] * g[0][q] + Rm[j][1] * g[1][q] + Rm[j][2] * g[2][q];
-        gt[j][0] = h[0];
-        gt[j][4] = h[4];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gt[j][1 + k] = Rm[k][0] * h[1] + Rm[k][1] * h[2] + Rm[k][2] * h[3];
-    }
-}
-
 // Slip-wall ghost (Sec. 4.4) of a state already in the face frame (x1 along
 // the normal): the mirror image across the wall.  rho U1 changes sign; of the
 // x1-derivatives all but that of rho U1 change sign; of the x2-, x3-derivatives
@@ -146,12 +70,6 @@ __device__ __forceinline__ void fixed_ghost(const T* __restrict__ x0, const T* X
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
-    const T a = v[1], b = v[2], c = v[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[1 + i] = Rm[0][i] * a + Rm[1][i] * b + Rm[2][i] * c;
-}
 
 // Face flux with 6 threads per face: 3 Gauss points x 2 sides.  The two sides
 // of a Gauss point sit in different warps (warps 0-2 left, 3-5 right) so that

@@ -136,6 +136,24 @@ __device__ __forceinline__ T local_dt(const T* Wv, T dr, const HostPhys& p) {
 }
 #endif
 
+// Device buffers of the adjoint sweep (FP64): the two stages' reconstruction
+// records, the per-cell record adjoints (up to 40), the per-face adjoints of
+// both cells' reconstruction coefficients [nf][2][50], their per-cell sums
+// [nc][50], stencil adjoints [nc][5][16] and own parts [nc][5], the working
+// state adjoints of the stage and of the step [nc][XS], the reverse face
+// slots [4][nc] and the positivity-fallback flags of both stages [2][nc].
+struct AdjBuffers {
+    const double* poly1;
+    const double* poly2;
+    double *src, *lpf, *lp, *ld, *own, *lXs, *lX1;
+    const int8_t* rev;
+    int32_t* fallback;
+};
+// lambda (W^n, grad W^n) from lambda (W^{n+1}, grad W^{n+1}) for one step
+// with the frozen time step dt (public [component][cell] FP64 layouts)
+cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,
+                            const double* lW, const double* ldW, double* oW, double* odW, cudaStream_t s);
+
 // sets dt_fixed and t_end; with reset_time also zeroes the case times and
 // steps and sets the case minima to +inf
 cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt,

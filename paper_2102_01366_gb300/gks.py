@@ -83,6 +83,8 @@ def lib():
         "gks_step_timed": (C.c_int32, [_vp, C.c_int32, C.c_double, C.c_double, _vp, _vp]),
         "gks_timestep_noalloc": (C.c_int32, [C.POINTER(gks_params), _vp, _vp, C.c_int64, _vp, _vp]),
         "gks_residual": (C.c_int32, [_vp, _vp]),
+        "gks_adjoint_workspace_bytes": (C.c_size_t, [_vp]),
+        "gks_adjoint_step": (C.c_int32, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
         "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32]),
@@ -279,6 +281,23 @@ class State:
         _call("gks_residual", self._h, _np_ptr(out))
         return out
 
+    def adjoint_step(self, W, dW, lamW, lamdW, dt):
+        """Adjoint of one step at (W, dW) with the frozen step dt
+        (gks_adjoint_step): returns d J / d (W, dW) given d J / d (W', dW') of
+        the step's result.  All [5|15, nc] float64 CUDA tensors; the state is
+        left initialised at (W, dW)."""
+        t = self.torch
+        args = [t.as_tensor(x, dtype=t.float64, device=self.device).contiguous() for x in (W, dW, lamW, lamdW)]
+        oW = t.empty((5, self.mesh.nc), dtype=t.float64, device=self.device)
+        odW = t.empty((15, self.mesh.nc), dtype=t.float64, device=self.device)
+        nbytes = lib().gks_adjoint_workspace_bytes(self._h)
+        if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nbytes:
+            self._adj_ws = t.empty(nbytes, dtype=t.uint8, device=self.device)
+        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        _call("gks_adjoint_step", self._h, float(dt), *[_dptr(x) for x in args], _dptr(oW), _dptr(odW),
+              _dptr(self._adj_ws), nbytes)
+        return oW, odW
+
     def step_host(self, W_host, dW_host, nsteps=1, dt_fixed=0.0, W_out=None, dW_out=None):
         """Host buffers in and out (torch CPU tensors, pinned for async copies)."""
         W_out = W_host if W_out is None else W_out
@@ -365,3 +384,29 @@ class State:
         _call("gks_debug_face_records", self._h, float(dt), int(stage), _dptr(rec))
         self.sync()
         return rec
+
+
+def make_step_function(state, dt):
+    """A torch.autograd.Function for one step of ``state`` with the frozen
+    step dt: forward runs gks_step from (W, dW), backward gks_adjoint_step
+    (the forward state is recomputed, so only each step's input is kept).
+    Chaining N applications differentiates an N-step run."""
+    torch = state.torch
+
+    class _Step(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, W, dW):
+            state.init(W.detach(), dW.detach())
+            state.step(1, float(dt), 0.0)
+            Wn, dWn = state.get()
+            ctx.start = (W.detach().clone(), dW.detach().clone())
+            return Wn, dWn
+
+        @staticmethod
+        def backward(ctx, gW, gdW):
+            W, dW = ctx.start
+            gW = torch.zeros_like(W) if gW is None else gW
+            gdW = torch.zeros_like(dW) if gdW is None else gdW
+            return state.adjoint_step(W, dW, gW, gdW, dt)
+
+    return _Step.apply
