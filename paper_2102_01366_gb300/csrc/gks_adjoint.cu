@@ -16,8 +16,12 @@
 // the output adjoints at once.
 //
 //   k_adj_src2 / k_adj_src1  per-cell adjoints of the face-record sums
-//   k_adj_flux<NR>           per face: record adjoints -> adjoints of both
-//                            cells' reconstruction coefficients
+//   k_adj_point<NR>          per (face, Gauss point, input): one column of
+//                            the point solution's Jacobian against the
+//                            output adjoints
+//   k_adj_face_back          per face: rotations and evaluation at the
+//                            points transposed -> adjoints of both cells'
+//                            reconstruction coefficients
 //   k_adj_gather_poly        per cell: sum over its four faces
 //   k_adj_recon_local        per cell: transpose of a = M2 d and of the
 //                            monomial constant
@@ -36,7 +40,7 @@ namespace gks {
 
 constexpr int ADW = 1;           // directions per forward-mode pass
 constexpr int ADJ_IN = 40;       // inputs of the point solution: WL, gL, WR, gR (face frame)
-constexpr int ADJ_THREADS = 64;  // threads (faces) per block of k_adj_flux
+constexpr int ADJ_THREADS = 64;  // threads per block of k_adj_point
 
 // stage 2 records: [sum w 4/3 D (5) | sum w dW n (15)]; the cell sums enter
 // W^{n+1} = W^n - (S + sum s rec[0:5]) / |Omega| and
@@ -116,30 +120,22 @@ __device__ __forceinline__ void rotate_in(const double (*Rm)[3], double* v) {
     for (int j = 0; j < 3; ++j) v[1 + j] = Rm[j][0] * a + Rm[j][1] * b + Rm[j][2] * c;
 }
 
-// One thread per face (interior faces only).  For each Gauss point: the
-// point's inputs are re-evaluated from the stored reconstruction, the output
-// adjoints follow from the record adjoints (the transposed record formulas of
-// the stage), the point solution is differentiated in forward mode and its
-// Jacobian contracted with them, and the result is carried back through the
-// rotations and the evaluation at the point into lpf[f][side][5][10].
+// The point's inputs in the face frame (WL, gL, WR, gR: 40 values) from the
+// stored reconstruction, and the output adjoints of the point (face frame)
+// from the record adjoints (the transposed record formulas of the stage).
 template <int NR>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_flux(DevMesh<double> m, Phys<double> ph,
-                                                          const double* __restrict__ poly,
-                                                          const double* __restrict__ src, double dt,
-                                                          double* __restrict__ lpf) {
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= m.nf) return;
+__device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const double* __restrict__ poly,
+                                                const double* __restrict__ src, int64_t f, int k,
+                                                double (*Rm)[3], double* x, double* lFh, double* lD,
+                                                double* lW0, double* ldWt) {
     const int L = m.flr[f], R = m.flr[m.nf + f];
     const double* geo = m.fgeo + f * FGEO;
     const double n[3] = {geo[0], geo[1], geo[2]};
     const double w = geo[3];
-    double Rm[3][3];
     face_frame(n, Rm);
     // record adjoints: the left cell adds the record, the right one subtracts it
     double lr[NR];
     for (int j = 0; j < NR; ++j) lr[j] = src[(int64_t)L * NR + j] - src[(int64_t)R * NR + j];
-    // output adjoints of every point (global frame, then face frame)
-    double lFh[5], lD[5], lW0[5], ldWt[5];
     for (int q = 0; q < 5; ++q) {
         double sn0 = 0.0, sn1 = 0.0;
         if (NR == 40) {
@@ -163,7 +159,32 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_flux(DevMesh<double> m, Phy
     rotate_in(Rm, lD);
     rotate_in(Rm, lW0);
     rotate_in(Rm, ldWt);
+    if (x) {
+        const double XL[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
+        const double XR[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
+        double WL[5], gL[3][5], WR[5], gR[3][5];
+        eval_poly(poly + (int64_t)L * POLY_STRIDE, XL, WL, gL);
+        eval_poly(poly + (int64_t)R * POLY_STRIDE, XR, WR, gR);
+        to_local(Rm, WL, gL, x, reinterpret_cast<double (*)[5]>(x + 5));
+        to_local(Rm, WR, gR, x + 20, reinterpret_cast<double (*)[5]>(x + 25));
+    }
+}
 
+// One thread per (face, Gauss point, input direction) of interior faces: the
+// point solution differentiated in forward mode along one input and the
+// column contracted with the output adjoints: lx[f][k][j] = (J^T lambda)_j.
+template <int NR>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Phys<double> ph,
+                                                           const double* __restrict__ poly,
+                                                           const double* __restrict__ src, double dt,
+                                                           double* __restrict__ lx) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.nf * 3 * ADJ_IN) return;
+    const int64_t f = t / (3 * ADJ_IN);
+    const int rem = (int)(t - f * 3 * ADJ_IN);
+    const int k = rem / ADJ_IN, j = rem - k * ADJ_IN;
+    double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
+    adj_point_setup<NR>(m, poly, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
     Phys<Dual<ADW>> pd;
     pd.gamma = ph.gamma;
     pd.gm1 = ph.gm1;
@@ -174,38 +195,37 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_flux(DevMesh<double> m, Phy
     pd.eps_w = ph.eps_w;
     pd.viscous = ph.viscous;
     pd.smooth = ph.smooth;
+    Dual<ADW> in[ADJ_IN];
+    for (int i = 0; i < ADJ_IN; ++i) in[i] = Dual<ADW>(x[i]);
+    in[j].d[0] = 1.0;
+    Dual<ADW> Fh[5], D[5], W0[5], dW[5];
+    gks_point(pd, in, reinterpret_cast<const Dual<ADW>(*)[5]>(in + 5), in + 20,
+              reinterpret_cast<const Dual<ADW>(*)[5]>(in + 25), Dual<ADW>(dt), Fh, D, W0, dW);
+    double acc = 0.0;
+    for (int q = 0; q < 5; ++q)
+        acc += lFh[q] * Fh[q].d[0] + lD[q] * D[q].d[0] + lW0[q] * W0[q].d[0] + ldWt[q] * dW[q].d[0];
+    lx[t] = acc;
+}
 
+// One thread per face: the input adjoints of its three points carried back
+// through the rotations and the evaluation at the points into
+// lpf[f][side][5][10].
+__global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.nf) return;
+    const double* geo = m.fgeo + f * FGEO;
+    const double n[3] = {geo[0], geo[1], geo[2]};
+    double Rm[3][3];
+    face_frame(n, Rm);
     double lpL[50], lpR[50];
     for (int j = 0; j < 50; ++j) lpL[j] = lpR[j] = 0.0;
     for (int k = 0; k < 3; ++k) {
+        const double* l = lx + (f * 3 + k) * ADJ_IN;
         const double XL[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
         const double XR[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
-        double WL[5], gL[3][5], WR[5], gR[3][5];
-        eval_poly(poly + (int64_t)L * POLY_STRIDE, XL, WL, gL);
-        eval_poly(poly + (int64_t)R * POLY_STRIDE, XR, WR, gR);
-        double x[ADJ_IN];
-        to_local(Rm, WL, gL, x, reinterpret_cast<double (*)[5]>(x + 5));
-        to_local(Rm, WR, gR, x + 20, reinterpret_cast<double (*)[5]>(x + 25));
-        double lx[ADJ_IN];
-        for (int p = 0; p < ADJ_IN / ADW; ++p) {
-            Dual<ADW> in[ADJ_IN];
-            for (int j = 0; j < ADJ_IN; ++j) {
-                in[j] = Dual<ADW>(x[j]);
-                if (j / ADW == p) in[j].d[j % ADW] = 1.0;
-            }
-            Dual<ADW> Fh[5], D[5], W0[5], dW[5];
-            gks_point(pd, in, reinterpret_cast<const Dual<ADW>(*)[5]>(in + 5), in + 20,
-                      reinterpret_cast<const Dual<ADW>(*)[5]>(in + 25), Dual<ADW>(dt), Fh, D, W0, dW);
-            for (int j = 0; j < ADW; ++j) {
-                double acc = 0.0;
-                for (int q = 0; q < 5; ++q)
-                    acc += lFh[q] * Fh[q].d[j] + lD[q] * D[q].d[j] + lW0[q] * W0[q].d[j] + ldWt[q] * dW[q].d[j];
-                lx[p * ADW + j] = acc;
-            }
-        }
         double lWL[5], lgL[3][5], lWR[5], lgR[3][5];
-        to_local_adj(Rm, lx, reinterpret_cast<const double (*)[5]>(lx + 5), lWL, lgL);
-        to_local_adj(Rm, lx + 20, reinterpret_cast<const double (*)[5]>(lx + 25), lWR, lgR);
+        to_local_adj(Rm, l, reinterpret_cast<const double (*)[5]>(l + 5), lWL, lgL);
+        to_local_adj(Rm, l + 20, reinterpret_cast<const double (*)[5]>(l + 25), lWR, lgR);
         eval_poly_adj(XL, lWL, lgL, lpL);
         eval_poly_adj(XR, lWR, lgR, lpR);
     }
@@ -323,14 +343,16 @@ cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double 
     cudaError_t e;
     // stage 2
     k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
-    k_adj_flux<20><<<grid_of(m.nf, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lpf);
+    k_adj_point<20><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
     k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
     k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lXs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 1
     k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
-    k_adj_flux<40><<<grid_of(m.nf, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lpf);
+    k_adj_point<40><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
     k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
     k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lX1);

@@ -857,7 +857,7 @@ extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
 
 namespace {
 struct AdjLayout {
-    size_t poly1, src, lpf, lp, ld, own, lXs, lX1, rev, fallback, total = 0;
+    size_t poly1, src, lx, lpf, lp, ld, own, lXs, lX1, rev, fallback, total = 0;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -869,6 +869,7 @@ AdjLayout adj_layout(int64_t nc, int64_t nf) {
     AdjLayout L;
     L.poly1 = L.add(8 * POLY_STRIDE * nc);
     L.src = L.add(8 * 40 * nc);
+    L.lx = L.add(8 * 120 * nf);
     L.lpf = L.add(8 * 100 * nf);
     L.lp = L.add(8 * 50 * nc);
     L.ld = L.add(8 * 80 * nc);
@@ -950,6 +951,7 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     b.poly1 = poly1;
     b.poly2 = st.poly;
     b.src = reinterpret_cast<double*>(base + A.src);
+    b.lx = reinterpret_cast<double*>(base + A.lx);
     b.lpf = reinterpret_cast<double*>(base + A.lpf);
     b.lp = reinterpret_cast<double*>(base + A.lp);
     b.ld = reinterpret_cast<double*>(base + A.ld);

@@ -138,14 +138,15 @@ __device__ __forceinline__ T local_dt(const T* Wv, T dr, const HostPhys& p) {
 
 // Device buffers of the adjoint sweep (FP64): the two stages' reconstruction
 // records, the per-cell record adjoints (up to 40), the per-face adjoints of
-// both cells' reconstruction coefficients [nf][2][50], their per-cell sums
+// both cells' reconstruction coefficients [nf][2][50] (through the point
+// input adjoints [nf][3][40]), their per-cell sums
 // [nc][50], stencil adjoints [nc][5][16] and own parts [nc][5], the working
 // state adjoints of the stage and of the step [nc][XS], the reverse face
 // slots [4][nc] and the positivity-fallback flags of both stages [2][nc].
 struct AdjBuffers {
     const double* poly1;
     const double* poly2;
-    double *src, *lpf, *lp, *ld, *own, *lXs, *lX1;
+    double *src, *lx, *lpf, *lp, *ld, *own, *lXs, *lX1;
     const int8_t* rev;
     int32_t* fallback;
 };
