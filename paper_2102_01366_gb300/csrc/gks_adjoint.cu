@@ -10,15 +10,18 @@
 // averages and of gradients by Eq. gauss-formula); those are transposed by
 // hand, each as a gather so that no two threads write one location.  The
 // kinetic solution (Eq. 2nd-flux with Eq. new-equ-part) is differentiated in
-// forward mode: the same templated point code runs on Dual numbers, one
-// input direction a pass (40 passes a point: wider Duals multiply the code
-// the compiler has to schedule), and each Jacobian column is contracted with
-// the output adjoints at once.
+// reverse mode for inviscid flow (gks_point_adj.cuh, about three point
+// evaluations of work); with viscosity it is differentiated in forward mode:
+// the same templated point code runs on Dual numbers, one input direction a
+// pass (40 passes a point), and each Jacobian column is contracted with the
+// output adjoints at once.
 //
 //   k_adj_src2 / k_adj_src1  per-cell adjoints of the face-record sums
-//   k_adj_point<NR>          per (face, Gauss point, input): one column of
-//                            the point solution's Jacobian against the
-//                            output adjoints
+//   k_adj_point_rev<NR>      per (face, Gauss point), inviscid: the point
+//                            solution's adjoint in reverse mode
+//   k_adj_point<NR>          per (face, Gauss point, input), viscous: one
+//                            column of the point solution's Jacobian (forward
+//                            mode) against the output adjoints
 //   k_adj_face_back          per face: rotations and evaluation at the
 //                            points transposed -> adjoints of both cells'
 //                            reconstruction coefficients
@@ -35,6 +38,7 @@
 #include "gks_dual.cuh"
 #include "gks_face.cuh"
 #include "gks_kernels.h"
+#include "gks_point_adj.cuh"
 
 namespace gks {
 
@@ -207,6 +211,28 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Ph
     lx[t] = acc;
 }
 
+// One thread per (face, Gauss point) of interior faces, inviscid flow: the
+// point solution's adjoint in reverse mode (gks_point_adj), lx[f][k][0:40].
+template <int NR>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m, Phys<double> ph,
+                                                               const double* __restrict__ poly,
+                                                               const double* __restrict__ src, double dt,
+                                                               double* __restrict__ lx) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.nf * 3) return;
+    const int64_t f = t / 3;
+    const int k = (int)(t - f * 3);
+    double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
+    adj_point_setup<NR>(m, poly, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
+    double* l = lx + t * ADJ_IN;
+    double lin[ADJ_IN];
+    for (int i = 0; i < ADJ_IN; ++i) lin[i] = 0.0;
+    gks_point_adj(ph, x, reinterpret_cast<const double (*)[5]>(x + 5), x + 20,
+                  reinterpret_cast<const double (*)[5]>(x + 25), dt, lFh, lD, lW0, ldWt, lin,
+                  reinterpret_cast<double (*)[5]>(lin + 5), lin + 20, reinterpret_cast<double (*)[5]>(lin + 25));
+    for (int i = 0; i < ADJ_IN; ++i) l[i] = lin[i];
+}
+
 // One thread per face: the input adjoints of its three points carried back
 // through the rotations and the evaluation at the points into
 // lpf[f][side][5][10].
@@ -343,7 +369,10 @@ cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double 
     cudaError_t e;
     // stage 2
     k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
-    k_adj_point<20><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
+    if (ph.viscous)
+        k_adj_point<20><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
+    else
+        k_adj_point_rev<20><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
     k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
     k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
@@ -351,7 +380,10 @@ cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 1
     k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
-    k_adj_point<40><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
+    if (ph.viscous)
+        k_adj_point<40><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
+    else
+        k_adj_point_rev<40><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
     k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
     k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);

@@ -1,0 +1,475 @@
+// gks_point_adj.cuh -- reverse-mode (adjoint) derivative of the kinetic
+// solution at one Gauss point, FP64, for inviscid flow (tau = 0).
+//
+// gks_point_adj recomputes the forward quantities of gks_point (the two
+// half-space moment tables, the interface equilibrium, the time coefficients,
+// the micro-slopes of both sides and of the equilibrium) and then carries the
+// output adjoints (of Fh, D, W0, dW) back through each of them in reverse
+// order: every building block of gks_device.cuh has its transpose here
+// (adj_*).  The moment sums are multilinear in the tables' one-dimensional
+// moments; their adjoints go through adj_G, which distributes the adjoint of
+// one product <u^P><v^Q><w^R> over its three factors.
+#pragma once
+
+#include "gks_device.cuh"
+
+namespace gks {
+
+using TabD = Tab<double>;
+
+__device__ __forceinline__ void tab_zero(TabD& t) {
+    for (int k = 0; k < 7; ++k) t.u[k] = t.v[k] = t.w[k] = 0.0;
+    t.xi2 = t.xi4 = 0.0;
+}
+
+// adjoint of G = u[P] v[Q] w[R]
+template <int P, int Q, int R>
+__device__ __forceinline__ void adj_G(const TabD& t, TabD& lt, double lam) {
+    lt.u[P] += lam * t.v[Q] * t.w[R];
+    lt.v[Q] += lam * t.u[P] * t.w[R];
+    lt.w[R] += lam * t.u[P] * t.v[Q];
+}
+
+// adjoint of Em<P,Q,R> = (G(P+2) + G(Q+2) + G(R+2) + xi2 G) / 2
+template <int P, int Q, int R>
+__device__ __forceinline__ void adj_E(const TabD& t, TabD& lt, double lam) {
+    const double h = 0.5 * lam;
+    adj_G<P + 2, Q, R>(t, lt, h);
+    adj_G<P, Q + 2, R>(t, lt, h);
+    adj_G<P, Q, R + 2>(t, lt, h);
+    adj_G<P, Q, R>(t, lt, h * t.xi2);
+    lt.xi2 += h * Gm<P, Q, R>(t);
+}
+
+// adjoint of E2m<P,Q,R>
+template <int P, int Q, int R>
+__device__ __forceinline__ void adj_E2(const TabD& t, TabD& lt, double lam) {
+    const double q = 0.25 * lam;
+    adj_G<P + 4, Q, R>(t, lt, q);
+    adj_G<P, Q + 4, R>(t, lt, q);
+    adj_G<P, Q, R + 4>(t, lt, q);
+    adj_G<P, Q, R>(t, lt, q * t.xi4);
+    lt.xi4 += q * Gm<P, Q, R>(t);
+    adj_G<P + 2, Q + 2, R>(t, lt, 2.0 * q);
+    adj_G<P + 2, Q, R + 2>(t, lt, 2.0 * q);
+    adj_G<P, Q + 2, R + 2>(t, lt, 2.0 * q);
+    adj_G<P + 2, Q, R>(t, lt, 2.0 * q * t.xi2);
+    adj_G<P, Q + 2, R>(t, lt, 2.0 * q * t.xi2);
+    adj_G<P, Q, R + 2>(t, lt, 2.0 * q * t.xi2);
+    lt.xi2 += 2.0 * q * (Gm<P + 2, Q, R>(t) + Gm<P, Q + 2, R>(t) + Gm<P, Q, R + 2>(t));
+}
+
+// adjoint of acc_psi<P,Q,R>(t, c, out): out += c <psi u^P v^Q w^R>
+template <int P, int Q, int R>
+__device__ __forceinline__ void adj_acc_psi(const TabD& t, double c, const double* lo, TabD& lt, double& lc) {
+    lc += lo[0] * Gm<P, Q, R>(t) + lo[1] * Gm<P + 1, Q, R>(t) + lo[2] * Gm<P, Q + 1, R>(t) +
+          lo[3] * Gm<P, Q, R + 1>(t) + lo[4] * Em<P, Q, R>(t);
+    adj_G<P, Q, R>(t, lt, c * lo[0]);
+    adj_G<P + 1, Q, R>(t, lt, c * lo[1]);
+    adj_G<P, Q + 1, R>(t, lt, c * lo[2]);
+    adj_G<P, Q, R + 1>(t, lt, c * lo[3]);
+    adj_E<P, Q, R>(t, lt, c * lo[4]);
+}
+
+// adjoint of acc_apsi<P,Q,R>(t, a, c, out): out_k += sum_j c a_j M_kj with the
+// symmetric moment matrix M_kj = <psi_k psi_j u^P v^Q w^R>
+template <int P, int Q, int R>
+__device__ __forceinline__ void adj_acc_apsi(const TabD& t, const double* a, double c, const double* lo,
+                                             TabD& lt, double* la, double& lc) {
+    double M[5][5];
+    M[0][0] = Gm<P, Q, R>(t);
+    M[0][1] = M[1][0] = Gm<P + 1, Q, R>(t);
+    M[0][2] = M[2][0] = Gm<P, Q + 1, R>(t);
+    M[0][3] = M[3][0] = Gm<P, Q, R + 1>(t);
+    M[0][4] = M[4][0] = Em<P, Q, R>(t);
+    M[1][1] = Gm<P + 2, Q, R>(t);
+    M[1][2] = M[2][1] = Gm<P + 1, Q + 1, R>(t);
+    M[1][3] = M[3][1] = Gm<P + 1, Q, R + 1>(t);
+    M[1][4] = M[4][1] = Em<P + 1, Q, R>(t);
+    M[2][2] = Gm<P, Q + 2, R>(t);
+    M[2][3] = M[3][2] = Gm<P, Q + 1, R + 1>(t);
+    M[2][4] = M[4][2] = Em<P, Q + 1, R>(t);
+    M[3][3] = Gm<P, Q, R + 2>(t);
+    M[3][4] = M[4][3] = Em<P, Q, R + 1>(t);
+    M[4][4] = E2m<P, Q, R>(t);
+    double ca[5];
+    for (int j = 0; j < 5; ++j) ca[j] = c * a[j];
+    for (int j = 0; j < 5; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < 5; ++k) s += lo[k] * M[k][j];
+        la[j] += c * s;
+        lc += a[j] * s;
+    }
+    // adjoint of each distinct entry: lo_k ca_j + lo_j ca_k off the diagonal
+    auto e = [&](int k, int j) { return k == j ? lo[k] * ca[k] : lo[k] * ca[j] + lo[j] * ca[k]; };
+    adj_G<P, Q, R>(t, lt, e(0, 0));
+    adj_G<P + 1, Q, R>(t, lt, e(0, 1));
+    adj_G<P, Q + 1, R>(t, lt, e(0, 2));
+    adj_G<P, Q, R + 1>(t, lt, e(0, 3));
+    adj_E<P, Q, R>(t, lt, e(0, 4));
+    adj_G<P + 2, Q, R>(t, lt, e(1, 1));
+    adj_G<P + 1, Q + 1, R>(t, lt, e(1, 2));
+    adj_G<P + 1, Q, R + 1>(t, lt, e(1, 3));
+    adj_E<P + 1, Q, R>(t, lt, e(1, 4));
+    adj_G<P, Q + 2, R>(t, lt, e(2, 2));
+    adj_G<P, Q + 1, R + 1>(t, lt, e(2, 3));
+    adj_E<P, Q + 1, R>(t, lt, e(2, 4));
+    adj_G<P, Q, R + 2>(t, lt, e(3, 3));
+    adj_E<P, Q, R + 1>(t, lt, e(3, 4));
+    adj_E2<P, Q, R>(t, lt, e(4, 4));
+}
+
+// adjoint of acc_grad<P>(t, a, c, out)
+template <int P>
+__device__ __forceinline__ void adj_acc_grad(const TabD& t, const double (*a)[5], double c, const double* lo,
+                                             TabD& lt, double (*la)[5], double& lc) {
+    adj_acc_apsi<P + 1, 0, 0>(t, a[0], c, lo, lt, la[0], lc);
+    adj_acc_apsi<P, 1, 0>(t, a[1], c, lo, lt, la[1], lc);
+    adj_acc_apsi<P, 0, 1>(t, a[2], c, lo, lt, la[2], lc);
+}
+
+// adjoints of a primitive state, in the fields of Prim
+struct PrimAdj {
+    double rho = 0.0, u = 0.0, v = 0.0, w = 0.0, lam = 0.0, p = 0.0;
+};
+
+// adjoint of the moment recursion m[k+2] = U m[k+1] + (k+1) h m[k]
+__device__ __forceinline__ void adj_recur(const double* m, double U, double h, double* lm, double& lU,
+                                          double& lh) {
+    for (int k = 4; k >= 0; --k) {
+        const double l = lm[k + 2];
+        lU += l * m[k + 1];
+        lm[k + 1] += l * U;
+        lh += l * (double)(k + 1) * m[k];
+        lm[k] += l * (double)(k + 1) * h;
+    }
+}
+
+// adjoint of make_tab(t, s, K, half): the table's adjoint lt into the state's
+__device__ __forceinline__ void adj_make_tab(const TabD& t, const Prim<double>& s, double K, int half,
+                                             const TabD& lt, PrimAdj& ls) {
+    const double h = 0.5 / s.lam;
+    double lh = K * lt.xi2 + 2.0 * (K * K + 2.0 * K) * h * lt.xi4;
+    double lu[7], lv[7], lw[7];
+    for (int k = 0; k < 7; ++k) {
+        lu[k] = lt.u[k];
+        lv[k] = lt.v[k];
+        lw[k] = lt.w[k];
+    }
+    adj_recur(t.u, s.u, h, lu, ls.u, lh);
+    adj_recur(t.v, s.v, h, lv, ls.v, lh);
+    adj_recur(t.w, s.w, h, lw, ls.w, lh);
+    ls.v += lv[1];
+    ls.w += lw[1];
+    if (half == 0) {
+        ls.u += lu[1];
+    } else {
+        const double sg = half > 0 ? 1.0 : -1.0;
+        const double sl = sqrt(s.lam);
+        const double e = exp(-s.lam * s.u * s.u);
+        const double c = 0.5 * 0.56418958354775628695;  // 1 / (2 sqrt(pi))
+        // u1 = U u0 + sg c e / sl
+        ls.u += lu[1] * t.u[0];
+        lu[0] += lu[1] * s.u;
+        ls.u += lu[1] * sg * c * e * (-2.0 * s.lam * s.u) / sl;
+        ls.lam += lu[1] * sg * c * e * (-s.u * s.u / sl - 0.5 / (s.lam * sl));
+        // u0 = erfc(x) / 2 with x = -sg sl U;  d erfc / dx = -2/sqrt(pi) exp(-x^2)
+        const double du0dx = -0.56418958354775628695 * e;
+        ls.u += lu[0] * du0dx * (-sg * sl);
+        ls.lam += lu[0] * du0dx * (-sg * s.u * 0.5 / sl);
+    }
+    ls.lam += lh * (-0.5 / (s.lam * s.lam));
+}
+
+// adjoint of to_prim(W, gm1): the primitive adjoint ls into lW
+__device__ __forceinline__ void adj_to_prim(const double* W, double gm1, const Prim<double>& s,
+                                            const PrimAdj& ls, double* lW) {
+    double lp = ls.p, lrho = ls.rho;
+    lrho += ls.lam * 0.5 / s.p;
+    lp += ls.lam * (-0.5 * s.rho / (s.p * s.p));
+    double lu = ls.u, lv = ls.v, lw = ls.w;
+    lW[4] += gm1 * lp;
+    lW[1] += -0.5 * gm1 * lp * s.u;
+    lW[2] += -0.5 * gm1 * lp * s.v;
+    lW[3] += -0.5 * gm1 * lp * s.w;
+    lu += -0.5 * gm1 * lp * W[1];
+    lv += -0.5 * gm1 * lp * W[2];
+    lw += -0.5 * gm1 * lp * W[3];
+    const double ir = 1.0 / W[0];
+    lW[1] += lu * ir;
+    lW[2] += lv * ir;
+    lW[3] += lw * ir;
+    const double lir = lu * W[1] + lv * W[2] + lw * W[3];
+    lW[0] += lrho - lir * ir * ir;
+}
+
+// adjoint of micro_slope(s, K, b, a): la into ls and lb
+__device__ __forceinline__ void adj_micro_slope(const Prim<double>& s, double K, const double* b,
+                                                const double* la_in, PrimAdj& ls, double* lb) {
+    // forward
+    const double q = s.u * s.u + s.v * s.v + s.w * s.w;
+    const double e = q + (K + 3.0) * 0.5 / s.lam;
+    const double r1 = b[1] - s.u * b[0], r2 = b[2] - s.v * b[0], r3 = b[3] - s.w * b[0];
+    const double r4 = 2.0 * b[4] - e * b[0];
+    const double kap = 4.0 * s.lam * s.lam / (K + 3.0);
+    const double S = s.u * r1 + s.v * r2 + s.w * r3;
+    const double a4 = kap * (r4 - 2.0 * S);
+    const double tl = 2.0 * s.lam;
+    const double a1 = tl * r1 - s.u * a4, a2 = tl * r2 - s.v * a4, a3 = tl * r3 - s.w * a4;
+    // reverse
+    double la1 = la_in[1], la2 = la_in[2], la3 = la_in[3], la4 = la_in[4];
+    const double la0 = la_in[0];
+    double le = 0.0, ltl = 0.0, lr1 = 0.0, lr2 = 0.0, lr3 = 0.0, lr4 = 0.0;
+    // a0 = b0 - u a1 - v a2 - w a3 - a4 e / 2
+    lb[0] += la0;
+    ls.u += -la0 * a1;
+    la1 += -la0 * s.u;
+    ls.v += -la0 * a2;
+    la2 += -la0 * s.v;
+    ls.w += -la0 * a3;
+    la3 += -la0 * s.w;
+    la4 += -0.5 * la0 * e;
+    le += -0.5 * la0 * a4;
+    // a_i = tl r_i - u_i a4
+    ltl += la1 * r1 + la2 * r2 + la3 * r3;
+    lr1 += la1 * tl;
+    lr2 += la2 * tl;
+    lr3 += la3 * tl;
+    ls.u += -la1 * a4;
+    ls.v += -la2 * a4;
+    ls.w += -la3 * a4;
+    la4 += -(la1 * s.u + la2 * s.v + la3 * s.w);
+    ls.lam += 2.0 * ltl;
+    // a4 = kap (r4 - 2 S)
+    const double lkap = la4 * (r4 - 2.0 * S);
+    lr4 += la4 * kap;
+    const double lS = -2.0 * kap * la4;
+    ls.u += lS * r1;
+    ls.v += lS * r2;
+    ls.w += lS * r3;
+    lr1 += lS * s.u;
+    lr2 += lS * s.v;
+    lr3 += lS * s.w;
+    ls.lam += lkap * 8.0 * s.lam / (K + 3.0);
+    // r4 = 2 b4 - e b0, r_i = b_i - u_i b0
+    lb[4] += 2.0 * lr4;
+    le += -lr4 * b[0];
+    lb[0] += -lr4 * e - lr1 * s.u - lr2 * s.v - lr3 * s.w;
+    lb[1] += lr1;
+    lb[2] += lr2;
+    lb[3] += lr3;
+    ls.u += -lr1 * b[0];
+    ls.v += -lr2 * b[0];
+    ls.w += -lr3 * b[0];
+    // e = q + (K + 3) / (2 lam)
+    ls.lam += le * (-(K + 3.0) * 0.5 / (s.lam * s.lam));
+    ls.u += 2.0 * s.u * le;
+    ls.v += 2.0 * s.v * le;
+    ls.w += 2.0 * s.w * le;
+}
+
+// Adjoint of gks_point for tau = 0 (inviscid): output adjoints lFh, lD, lW0,
+// ldW (face frame) into the input adjoints lWl, lgl, lWr, lgr (accumulated).
+__device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const double (*gl)[5],
+                              const double* Wr, const double (*gr)[5], double dt, const double* lFh,
+                              const double* lD, const double* lW0, const double* ldW, double* lWl,
+                              double (*lgl)[5], double* lWr, double (*lgr)[5]) {
+    const double K = ph.K;
+    const double* Win[2] = {Wl, Wr};
+    const double (*gin[2])[5] = {gl, gr};
+    // ---- forward recomputation ----
+    Prim<double> P[2];
+    TabD th[2];
+    double Wc[5] = {0, 0, 0, 0, 0};
+    for (int s = 0; s < 2; ++s) {
+        P[s] = to_prim(Win[s], ph.gm1);
+        make_tab(th[s], P[s], K, s == 0 ? +1 : -1);
+        acc_psi<0, 0, 0>(th[s], P[s].rho, Wc);
+    }
+    const Prim<double> C = to_prim(Wc, ph.gm1);
+    const TimeCoef<double> tc = time_coefs(ph, P[0].p, P[1].p, C.p, dt);
+    double a[2][3][5];
+    double dWc[3][5] = {};
+    for (int s = 0; s < 2; ++s) {
+        const double ir = 1.0 / P[s].rho;
+        for (int i = 0; i < 3; ++i) {
+            double b[5];
+            for (int k = 0; k < 5; ++k) b[k] = gin[s][i][k] * ir;
+            micro_slope(P[s], K, b, a[s][i]);
+            acc_apsi<0, 0, 0>(th[s], a[s][i], P[s].rho, dWc[i]);
+        }
+    }
+    TabD tf;
+    make_tab(tf, C, K, 0);
+    double ac[3][5], Ac[5], rA[5], bc[3][5];
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 5; ++k) bc[i][k] = dWc[i][k] / C.rho;
+        micro_slope(C, K, bc[i], ac[i]);
+    }
+    for (int k = 0; k < 5; ++k) rA[k] = 0.0;
+    acc_grad<0>(tf, ac, -1.0, rA);
+    micro_slope(C, K, rA, Ac);
+    const double hd = 0.5 * dt;
+
+    // ---- reverse ----
+    TabD ltf;
+    tab_zero(ltf);
+    PrimAdj lC;
+    double lCrho = 0.0;  // adjoint of the rho factor of the equilibrium sums
+    double lWc[5] = {0, 0, 0, 0, 0};
+    double lac[3][5] = {}, lAc[5] = {0, 0, 0, 0, 0}, lrA[5] = {0, 0, 0, 0, 0};
+    // time-coefficient adjoints
+    double lk0 = 0, lk1 = 0, ldk0 = 0, ldk1 = 0, lq1 = 0, ldq1 = 0, lE = 0;
+    double lmf0[5], lmf1[5], lmf2[5], lmw1[5];
+    if (ph.smooth) {
+        for (int k = 0; k < 5; ++k) {
+            lmf0[k] = hd * lFh[k];
+            lmf1[k] = 0.0;
+            lmf2[k] = 0.5 * hd * hd * lFh[k] + 0.25 * dt * dt * lD[k];
+            lmw1[k] = -dt * ldW[k];
+            lWc[k] += lW0[k];
+        }
+    } else {
+        const double C23 = dt * (tc.E - 1.0);
+        for (int k = 0; k < 5; ++k) {
+            lmf0[k] = tc.q1 * lFh[k] + tc.dq1 * lD[k];
+            lmf1[k] = tc.q2 * lFh[k] + tc.dq2 * lD[k];
+            lmf2[k] = tc.q3 * lFh[k] + tc.dq3 * lD[k];
+            lmw1[k] = C23 * ldW[k];
+        }
+        // the coefficients' own adjoints need the sums: recompute them
+        double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mw1[5];
+        acc_psi<1, 0, 0>(tf, C.rho, mf0);
+        acc_grad<1>(tf, ac, C.rho, mf1);
+        for (int k = 0; k < 5; ++k) mw1[k] = -C.rho * rA[k];
+        for (int k = 0; k < 5; ++k) {
+            lq1 += lFh[k] * mf0[k];
+            ldq1 += lD[k] * mf0[k];
+            lk1 += lFh[k] * mf1[k];   // q2 = k1 (tau = 0)
+            ldk1 += lD[k] * mf1[k];   // dq2 = dk1
+            lE += dt * ldW[k] * mw1[k];
+        }
+        // q3, dq3 depend on dt only (tau = 0)
+    }
+    // mw1 = -rho_c rA
+    for (int k = 0; k < 5; ++k) {
+        lCrho += -lmw1[k] * rA[k];
+        lrA[k] += -C.rho * lmw1[k];
+    }
+    // mf2 = acc_apsi<1,0,0>(tf, Ac, rho_c); mf1 = acc_grad<1>(tf, ac, rho_c); mf0 = acc_psi<1>(tf, rho_c)
+    adj_acc_apsi<1, 0, 0>(tf, Ac, C.rho, lmf2, ltf, lAc, lCrho);
+    adj_acc_grad<1>(tf, ac, C.rho, lmf1, ltf, lac, lCrho);
+    adj_acc_psi<1, 0, 0>(tf, C.rho, lmf0, ltf, lCrho);
+    // Ac = micro_slope(C, K, rA)
+    adj_micro_slope(C, K, rA, lAc, lC, lrA);
+    // rA = -sum_i <(ac_i . psi) u_i psi>
+    {
+        double lunused = 0.0;
+        adj_acc_grad<0>(tf, ac, -1.0, lrA, ltf, lac, lunused);
+    }
+    // ac_i = micro_slope(C, K, dWc_i / rho_c)
+    double ldWc[3][5] = {};
+    for (int i = 0; i < 3; ++i) {
+        double lb[5] = {0, 0, 0, 0, 0};
+        adj_micro_slope(C, K, bc[i], lac[i], lC, lb);
+        for (int k = 0; k < 5; ++k) {
+            ldWc[i][k] += lb[k] / C.rho;
+            lC.rho += -lb[k] * dWc[i][k] / (C.rho * C.rho);
+        }
+    }
+    adj_make_tab(tf, C, K, 0, ltf, lC);
+    lC.rho += lCrho;
+
+    // time coefficients (tau = 0): k0, k1, dk0, dk1, q1, dq1, E from tau_n
+    TabD lth[2];
+    PrimAdj lP[2];
+    double la[2][3][5] = {};
+    for (int s = 0; s < 2; ++s) {
+        tab_zero(lth[s]);
+        double lrho = 0.0;
+        if (!ph.smooth) {
+            double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mw1[5] = {0, 0, 0, 0, 0};
+            acc_psi<1, 0, 0>(th[s], P[s].rho, mf0);
+            acc_grad<1>(th[s], a[s], P[s].rho, mf1);
+            acc_grad<0>(th[s], a[s], P[s].rho, mw1);
+            double lmf0s[5], lmf1s[5], lmw0s[5], lmw1s[5];
+            for (int k = 0; k < 5; ++k) {
+                lmf0s[k] = tc.k0 * lFh[k] + tc.dk0 * lD[k];
+                lmf1s[k] = -tc.k1 * lFh[k] - tc.dk1 * lD[k];
+                lmw0s[k] = lW0[k];
+                lmw1s[k] = -dt * tc.E * ldW[k];
+                lk0 += lFh[k] * mf0[k];
+                lk1 += -lFh[k] * mf1[k];
+                ldk0 += lD[k] * mf0[k];
+                ldk1 += -lD[k] * mf1[k];
+                lE += -dt * ldW[k] * mw1[k];
+            }
+            adj_acc_psi<1, 0, 0>(th[s], P[s].rho, lmf0s, lth[s], lrho);
+            adj_acc_grad<1>(th[s], a[s], P[s].rho, lmf1s, lth[s], la[s], lrho);
+            adj_acc_psi<0, 0, 0>(th[s], P[s].rho, lmw0s, lth[s], lrho);
+            adj_acc_grad<0>(th[s], a[s], P[s].rho, lmw1s, lth[s], la[s], lrho);
+        }
+        // dWc_i += acc_apsi<0,0,0>(th, a_i, rho)
+        for (int i = 0; i < 3; ++i) adj_acc_apsi<0, 0, 0>(th[s], a[s][i], P[s].rho, ldWc[i], lth[s], la[s][i], lrho);
+        // a_i = micro_slope(P, K, g_i / rho)
+        double (*lg)[5] = s == 0 ? lgl : lgr;
+        const double ir = 1.0 / P[s].rho;
+        for (int i = 0; i < 3; ++i) {
+            double b[5], lb[5] = {0, 0, 0, 0, 0};
+            for (int k = 0; k < 5; ++k) b[k] = gin[s][i][k] * ir;
+            adj_micro_slope(P[s], K, b, la[s][i], lP[s], lb);
+            for (int k = 0; k < 5; ++k) {
+                lg[i][k] += lb[k] * ir;
+                lrho += -lb[k] * gin[s][i][k] * ir * ir;
+            }
+        }
+        lP[s].rho += lrho;
+    }
+    // time coefficients -> tau_n -> the two pressures
+    if (!ph.smooth) {
+        const double tn = tc.tau_n;
+        const double Eh = sqrt(tc.E);
+        const double omh = 1.0 - Eh;
+        lk0 += -lq1;                  // q1 = hd - k0
+        double ltn = 0.0, lEh = 0.0, lomh = 0.0;
+        // k0 = tn omh
+        ltn += lk0 * omh;
+        lomh += lk0 * tn;
+        // k1 = tn (tn omh - hd Eh)
+        ltn += lk1 * (2.0 * tn * omh - hd * Eh);
+        lomh += lk1 * tn * tn;
+        lEh += lk1 * (-tn * hd);
+        // dk0 = -tn omh^2
+        ltn += ldk0 * (-omh * omh);
+        lomh += ldk0 * (-2.0 * tn * omh);
+        // dk1 = -tn^2 omh^2 + tn dt Eh omh
+        ltn += ldk1 * (-2.0 * tn * omh * omh + dt * Eh * omh);
+        lomh += ldk1 * (-2.0 * tn * tn * omh + tn * dt * Eh);
+        lEh += ldk1 * tn * dt * omh;
+        // dq1 = tn omh^2
+        ltn += ldq1 * omh * omh;
+        lomh += ldq1 * 2.0 * tn * omh;
+        // E = Eh^2, omh = 1 - Eh, Eh = exp(-hd / tn)
+        lEh += 2.0 * Eh * lE - lomh;
+        ltn += lEh * Eh * hd / (tn * tn);
+        // tn = tau_eps dt + tau_c |x| dt, x = (pl - pr) / (pl + pr)
+        const double pl = P[0].p, pr = P[1].p;
+        const double x = (pl - pr) / (pl + pr);
+        const double sx = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+        const double lx = ltn * ph.tau_c * dt * sx;
+        const double den = (pl + pr) * (pl + pr);
+        lP[0].p += lx * 2.0 * pr / den;
+        lP[1].p += lx * (-2.0 * pl) / den;
+    }
+    // C = to_prim(Wc)
+    adj_to_prim(Wc, ph.gm1, C, lC, lWc);
+    // Wc = sum_s acc_psi<0,0,0>(th_s, rho_s)
+    for (int s = 0; s < 2; ++s) adj_acc_psi<0, 0, 0>(th[s], P[s].rho, lWc, lth[s], lP[s].rho);
+    // the half-space tables and the primitive states
+    for (int s = 0; s < 2; ++s) {
+        adj_make_tab(th[s], P[s], K, s == 0 ? +1 : -1, lth[s], lP[s]);
+        adj_to_prim(Win[s], ph.gm1, P[s], lP[s], s == 0 ? lWl : lWr);
+    }
+}
+
+}  // namespace gks

@@ -44,12 +44,14 @@ def _dot(a, b):
     return float(sum((np.asarray(x) * np.asarray(y)).sum() for x, y in zip(a, b)))
 
 
-@pytest.mark.parametrize("smooth", [0, 1])
-def test_adjoint_matches_finite_differences(cuda, oracle_mod, smooth):
+@pytest.mark.parametrize("smooth,viscous", [(0, 0), (1, 0), (0, 1)])
+def test_adjoint_matches_finite_differences(cuda, oracle_mod, smooth, viscous):
+    """Inviscid runs take the reverse-mode point adjoint, the viscous run the
+    forward-mode one."""
     torch = cuda
     mesh, W, dW, rng = _case()
     g = gks.Mesh(mesh)
-    kw = dict(weno=0, cfl=0.5, smooth_flux=smooth)
+    kw = dict(weno=0, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
     s = gks.State(g, gks.params(precision=0, **kw))
     o = oracle_mod.Mesh(mesh)
     p = oracle_mod.params(**kw)
