@@ -186,6 +186,45 @@ def batched_leg(torch, gks, args, flush):
             "l2": "inputs larger than L2 (plus the flush)"}
 
 
+def adjoint_leg(torch, gks, args):
+    """Cost of the adjoint step against the forward step it differentiates:
+    the isentropic vortex on the periodic 64^3 x 6 box (1,572,864 cells),
+    FP64, linear weights, the time step frozen.  Both are timed end to end
+    (the adjoint call includes its forward recomputation and host set-up)."""
+    mesh, W, dW = I.isentropic_vortex_case(n=64, order=2)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=0, cfl=0.5, precision=0))
+    s.init(W, dW)
+    dt = s.timestep()
+    Wt, dWt = torch.tensor(W, device="cuda"), torch.tensor(dW, device="cuda")
+    # the adjoint of the total kinetic energy sum |rho U|^2 / (2 rho) after the step
+    lam_W = torch.zeros_like(Wt)
+    lam_W[1:4] = Wt[1:4] / Wt[0]
+    lam_W[0] = -0.5 * (Wt[1:4] ** 2).sum(0) / Wt[0] ** 2
+    lam_dW = torch.zeros_like(dWt)
+    reps = 3
+    for _ in range(max(1, args.warmup // 2)):
+        s.step(1, dt, 0.0)
+        s.sync()
+        s.adjoint_step(Wt, dWt, lam_W, lam_dW, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s.init(Wt, dWt)
+        s.step(1, dt, 0.0)
+        s.sync()
+    fwd = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s.adjoint_step(Wt, dWt, lam_W, lam_dW, dt)
+    torch.cuda.synchronize()
+    adj = (time.perf_counter() - t0) / reps
+    return {"workload": "isentropic vortex (strength 5, Ma 0.5 along the diagonal), periodic [0,10]^3, "
+                        "64^3 hexes x 6 tets = %d cells, FP64, linear weights, dt frozen" % g.nc,
+            "forward_ms": fwd * 1e3, "adjoint_ms": adj * 1e3, "adjoint_over_forward": adj / fwd,
+            "timing": "wall clock of the library calls, %d each after warm-up (forward: init + step)" % reps}
+
+
 def run_reference(args):
     ws, rank, _ = replicas.world()
     if rank != 0:
@@ -229,6 +268,7 @@ def main():
                          "(e.g. 1,3,1) or auto (tuned as in the full run)")
     ap.add_argument("--batch-cases", type=int, default=48,
                     help="independent cases of the batched leg (0: skip it)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -351,6 +391,8 @@ def main():
     }
     if args.batch_cases > 0:
         line["batched"] = batched_leg(torch, gks, args, flush)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(torch, gks, args)
     if rank == 0 and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -330,6 +330,23 @@ __global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__
     for (int l = 0; l < 3; ++l) x[5 + 3 * q + l] = lg[l];
 }
 
+// or of the positivity-fallback flags of both stages into *any
+__global__ void k_adj_any(const int32_t* __restrict__ flags, int64_t n, int32_t* __restrict__ any) {
+    int32_t v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v |= flags[i];
+    v = __reduce_or_sync(0xffffffffu, v);
+    if (v && (threadIdx.x & 31) == 0) atomicOr(any, v);
+}
+
+cudaError_t adjoint_any_fallback(const int32_t* flags, int64_t n, int32_t* any, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(any, 0, 4, s);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    k_adj_any<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(flags, n, any);
+    return cudaGetLastError();
+}
+
 // lambda W^n = lambda W^{n+1} (the update's pass-through) + lambda W* (the
 // stage-1 pass-through) + the stage-1 reconstruction's; lambda grad W^n from
 // the stage-1 reconstruction alone

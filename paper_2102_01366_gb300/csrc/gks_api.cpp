@@ -330,6 +330,7 @@ struct gks_state {
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
     int slopes_pass = 0;   // 1: reconstruction step 1 as its own pass
+    std::vector<int8_t> adj_rev;  // reverse face slots of the adjoint (built on first use)
 };
 
 template <typename T>
@@ -877,7 +878,7 @@ AdjLayout adj_layout(int64_t nc, int64_t nf) {
     L.lXs = L.add(8 * XS * nc);
     L.lX1 = L.add(8 * XS * nc);
     L.rev = L.add(4 * nc);
-    L.fallback = L.add(4 * 2 * nc);
+    L.fallback = L.add(4 * 2 * nc + 4);  // flags of both stages, then their or
     return L;
 }
 }  // namespace
@@ -913,15 +914,18 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     char* base = static_cast<char*>(d_scratch);
     // reverse face slots: rev[f][c] = the local face of neighbour n = nbr(c, f)
     // that is the same face
-    std::vector<int8_t> rev((size_t)4 * nc, 0);
-    for (int64_t c = 0; c < nc; ++c)
-        for (int f = 0; f < 4; ++f) {
-            const int64_t n = g.nbr[c * 4 + f];
-            if (n < 0) continue;
-            const int64_t fi = g.csr_face[c * 4 + f];
-            for (int r = 0; r < 4; ++r)
-                if (g.csr_face[n * 4 + r] == fi) rev[(size_t)f * nc + c] = (int8_t)r;
-        }
+    std::vector<int8_t>& rev = s->adj_rev;
+    if (rev.size() != (size_t)4 * nc) {
+        rev.assign((size_t)4 * nc, 0);
+        for (int64_t c = 0; c < nc; ++c)
+            for (int f = 0; f < 4; ++f) {
+                const int64_t n = g.nbr[c * 4 + f];
+                if (n < 0) continue;
+                const int64_t fi = g.csr_face[c * 4 + f];
+                for (int r = 0; r < 4; ++r)
+                    if (g.csr_face[n * 4 + r] == fi) rev[(size_t)f * nc + c] = (int8_t)r;
+            }
+    }
     GKS_CHECK_CUDA(cudaMemcpyAsync(base + A.rev, rev.data(), rev.size(), cudaMemcpyHostToDevice, s->stream));
     // forward recomputation of the step's two reconstructions with the frozen dt
     gks_status r = init_impl<double>(s, m, st, d_W, d_dW);
@@ -939,14 +943,14 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     GKS_CHECK_CUDA(Launch<double>::update1(m, st, s->stream));
     GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.Xs, nullptr, nullptr, st.poly, fb + nc, nullptr, st.err,
                                          s->stream));
-    std::vector<int32_t> flags((size_t)2 * nc);
-    GKS_CHECK_CUDA(cudaMemcpyAsync(flags.data(), fb, 8 * nc, cudaMemcpyDeviceToHost, s->stream));
+    int32_t any = 0;
+    GKS_CHECK_CUDA(adjoint_any_fallback(fb, 2 * nc, fb + 2 * nc, s->stream));
+    GKS_CHECK_CUDA(cudaMemcpyAsync(&any, fb + 2 * nc, 4, cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    for (int32_t v : flags)
-        if (v) {
-            set_error("gks_adjoint_step: a cell falls back to a constant reconstruction (positivity branch)");
-            return GKS_E_UNSUPPORTED;
-        }
+    if (any) {
+        set_error("gks_adjoint_step: a cell falls back to a constant reconstruction (positivity branch)");
+        return GKS_E_UNSUPPORTED;
+    }
     AdjBuffers b;
     b.poly1 = poly1;
     b.poly2 = st.poly;

@@ -533,6 +533,49 @@ def shear_decay_case(nx=16, nyz=2, amp=0.05, jitter=0.1, seed=7):
     return mesh, W, dW
 
 
+def isentropic_vortex_fields(x, length=10.0, strength=5.0, mach=0.5, gamma=1.4):
+    """Conservative variables of an isentropic vortex (axis along z through
+    the box centre, core radius 1) on a free stream of Mach number `mach`
+    along (1,1,1)/sqrt(3), rho_inf = 1, p_inf = 1/gamma (c_inf = 1): the
+    swirl u_theta = strength/(2 pi) r exp((1 - r^2)/2) and the temperature
+    T = p/rho = 1/gamma - (gamma-1)/gamma strength^2/(8 pi^2) exp(1 - r^2) of
+    the radial momentum balance, with rho = (gamma T)^(1/(gamma-1))."""
+    c = 0.5 * length
+    dx, dy = x[..., 0] - c, x[..., 1] - c
+    r2 = dx * dx + dy * dy
+    k = strength / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    ui = mach / math.sqrt(3.0)
+    u = ui - k * dy
+    v = ui + k * dx
+    w = np.full_like(u, ui)
+    T = 1.0 / gamma - (gamma - 1.0) / gamma * strength ** 2 / (8.0 * math.pi ** 2) * np.exp(1.0 - r2)
+    rho = (gamma * T) ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)],
+                    axis=-1)
+
+
+def isentropic_vortex_case(n=64, length=10.0, strength=5.0, mach=0.5, jitter=0.1, seed=8, order=3):
+    """The isentropic vortex on the periodic box [0, length]^3, n^3 hexes x 6
+    tets: cell averages of W by quadrature, cell-averaged gradients by
+    quadrature of central differences of the field (step 1e-5 length)."""
+    mesh = box_mesh((n, n, n), (length,) * 3, (True, True, True), jitter, seed)
+    f = lambda x: isentropic_vortex_fields(x, length, strength, mach)
+    W = cell_average(mesh, f, order=order).T.copy()
+    h = 1e-5 * length
+
+    def grad(x):
+        out = np.empty(x.shape[:-1] + (15,))
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = h
+            d = (f(x + e) - f(x - e)) / (2.0 * h)
+            out[..., i::3] = d
+        return out
+    dW = cell_average(mesh, grad, order=order).T.copy()
+    return mesh, np.ascontiguousarray(W), np.ascontiguousarray(dW)
+
+
 def wall_reflection_case(nx=64, nyz=4, state=(1.0, 1.0, 1.0), jitter=0.1, seed=3):
     """Uniform gas moving along x in [0,1] x [0,nyz/nx]^2 (cubic hexahedra)
     between slip walls at x = 0 and 1, y and z periodic; nx x nyz x nyz

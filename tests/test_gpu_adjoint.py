@@ -137,3 +137,21 @@ def test_unsupported_configurations_are_rejected(cuda):
     with pytest.raises(gks.GksError) as e:
         s.adjoint_step(*argso, 1e-3)
     assert e.value.status == -8
+
+
+def test_positivity_fallback_is_rejected(cuda):
+    """A near-vacuum cell makes its reconstruction fall back to the average
+    (the positivity branch, whose derivative is not built): rejected."""
+    torch = cuda
+    mesh, W, dW, _ = _case()
+    W = W.copy()
+    W[4, 0] = 0.5 * (W[1, 0] ** 2 + W[2, 0] ** 2 + W[3, 0] ** 2) / W[0, 0] + 1e-6
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=0, cfl=0.5))
+    s.init(W, dW)
+    fb = s.debug_reconstruct()[2].cpu().numpy()
+    assert fb.any()
+    args = [torch.tensor(x, device="cuda") for x in (W, dW, np.zeros_like(W), np.zeros_like(dW))]
+    with pytest.raises(gks.GksError) as e:
+        s.adjoint_step(*args, 1e-4)
+    assert e.value.status == -8
