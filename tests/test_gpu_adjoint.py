@@ -155,3 +155,51 @@ def test_positivity_fallback_is_rejected(cuda):
     with pytest.raises(gks.GksError) as e:
         s.adjoint_step(*args, 1e-4)
     assert e.value.status == -8
+
+
+def test_mach_number_gradient_of_the_vortex(cuda):
+    """dJ/dMa for J = total kinetic energy after 4 steps of the isentropic
+    vortex (periodic 6^3 x 6 box): the chained adjoint gives dJ/d(W0, dW0),
+    the derivative of the initial state with respect to the free-stream Mach
+    number comes from the input generator (central difference of the cell
+    averages, which are linear in the free-stream velocity), and the product
+    matches a central difference of J(Ma) through the forward runs."""
+    torch = cuda
+    n, ma, hm = 6, 0.5, 1e-5
+
+    def case(m):
+        return I.isentropic_vortex_case(n=n, mach=m, order=3)
+    mesh, W, dW = case(ma)
+    g = gks.Mesh(mesh)
+    vol = torch.tensor(g.geometry()["vol"], device="cuda")
+    s = gks.State(g, gks.params(precision=0, weno=0, cfl=0.5))
+    s.init(W, dW)
+    dt = s.timestep()
+
+    def energy_of(Wc):
+        return (vol * (Wc[1:4] ** 2).sum(0) / (2.0 * Wc[0])).sum()
+
+    def run(W0, dW0):
+        Wc, dWc = torch.tensor(W0, device="cuda"), torch.tensor(dW0, device="cuda")
+        states = []
+        for _ in range(4):
+            states.append((Wc, dWc))
+            s.init(Wc, dWc)
+            s.step(1, dt, 0.0)
+            Wc, dWc = s.get()
+        return Wc, states
+
+    Wn, states = run(W, dW)
+    lam_W = torch.zeros_like(Wn)
+    lam_W[1:4] = vol * Wn[1:4] / Wn[0]
+    lam_W[0] = -0.5 * vol * (Wn[1:4] ** 2).sum(0) / Wn[0] ** 2
+    lam_dW = torch.zeros((15, g.nc), dtype=torch.float64, device="cuda")
+    for Wc, dWc in reversed(states):
+        lam_W, lam_dW = s.adjoint_step(Wc, dWc, lam_W, lam_dW, dt)
+    _, Wp, dWp = case(ma + hm)
+    _, Wm, dWm = case(ma - hm)
+    dW0 = (Wp - Wm) / (2 * hm)
+    ddW0 = (dWp - dWm) / (2 * hm)
+    ad = float((lam_W.cpu().numpy() * dW0).sum() + (lam_dW.cpu().numpy() * ddW0).sum())
+    fd = (float(energy_of(run(Wp, dWp)[0])) - float(energy_of(run(Wm, dWm)[0]))) / (2 * hm)
+    assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
