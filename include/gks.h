@@ -304,8 +304,9 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * transpose of the step's Jacobian at (d_W, d_dW) applied to (lamW, lamdW).
  * It first recomputes the step's two reconstructions from (d_W, d_dW), so a
  * run of N steps back-propagates from the N saved (or recomputed) states.
- * Supported: FP64 states (precision 0) with linear reconstruction weights
- * (weno = 0, order 3), full or smooth flux, Euler or viscous, single-case
+ * Supported: FP64 states (precision 0) with the third-order reconstruction
+ * (order 3) with linear or WENO weights (the weights are differentiated,
+ * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
  * meshes without boundary faces; GKS_E_UNSUPPORTED otherwise, and also when a
  * cell of either stage falls back to a constant reconstruction (the
  * positivity branch, whose derivative this does not build).  All arrays are

@@ -27,7 +27,9 @@
 //                            reconstruction coefficients
 //   k_adj_gather_poly        per cell: sum over its four faces
 //   k_adj_recon_local        per cell: transpose of a = M2 d and of the
-//                            monomial constant
+//                            monomial constant (linear weights)
+//   k_adj_recon_weno         the same with the nonlinear WENO weights, and
+//   k_adj_slopes             the neighbours' P1 slopes those weights use
 //   k_adj_recon_gather       per cell: adjoint of its working state from its
 //                            own and its neighbours' stencil adjoints
 //   k_adj_final              the three paths into (W^n, grad W^n)
@@ -305,12 +307,238 @@ __global__ void k_adj_recon_local(DevMesh<double> m, const double* __restrict__ 
     own[c * 5 + q] = lc0 - s;
 }
 
+// P1 slope of cell x for component q from the working state X (the
+// reconstruction's step 1, Sec. 4.3)
+__device__ __forceinline__ void adj_p1_slope(const DevMesh<double>& m, const double* __restrict__ X, int64_t x,
+                                             int q, double* b) {
+    const int64_t nc = m.nc;
+    const double Qx = X[x * XS + q];
+    b[0] = b[1] = b[2] = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        const int nb = m.nbr[f * nc + x];
+        if (nb < 0) continue;
+        const double dq = X[(int64_t)nb * XS + q] - Qx;
+        for (int i = 0; i < 3; ++i) b[i] += m.M1[(i * 4 + f) * nc + x] * dq;
+    }
+}
+
+__device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// Transpose of the third-order multi-resolution WENO reconstruction of one
+// cell and component (Sec. 4.2, 4.3): R = c2 a + cb b with the nonlinear
+// weights of beta_0 (two-step, from the neighbours' P1 slopes), beta_1, beta_2;
+// c0 = Q0 - sum_k R_k M_k.  The weights are recomputed from the stage's
+// working state X and differentiated (|x|' = sign x, (x^{4/3})' = 4/3 x^{1/3}).
+// Writes ld[c][q][16] (adjoint of the stencil data d), lbn[c][q][f][3] (of
+// the neighbours' slopes as this cell uses them) and own[c][q] (of Q0 through
+// c0 and the differences d[0:4]).
+__global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __restrict__ X,
+                                 const double* __restrict__ lp, double* __restrict__ ld,
+                                 double* __restrict__ lbn, double* __restrict__ own) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t c = idx / 5, nc = m.nc;
+    const int q = (int)(idx - c * 5);
+    const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
+    auto T_ = [&](int row) { return tile[(int64_t)row * CELLS_PER_BLOCK]; };
+    int nb[4];
+    for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
+    const double Q0 = X[c * XS + q];
+    double d[16];
+    for (int f = 0; f < 4; ++f) {
+        const bool ok = nb[f] >= 0;
+        const double* xn = X + (ok ? (int64_t)nb[f] : c) * XS;
+        d[f] = ok ? xn[q] - Q0 : 0.0;
+        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? xn[5 + 3 * q + l] : 0.0;
+    }
+    double a[9];
+    for (int k = 0; k < 9; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < 16; ++j) acc += T_(TILE_M2 + k * 16 + j) * d[j];
+        a[k] = acc;
+    }
+    double Mm[6];
+    for (int k = 0; k < 6; ++k) Mm[k] = T_(TILE_MOM + k);
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int f = 0; f < 4; ++f) {
+        if (nb[f] < 0) continue;
+        for (int i = 0; i < 3; ++i) b[i] += T_(TILE_M1 + i * 4 + f) * d[f];
+    }
+    const double v23 = T_(TILE_V23), v43 = T_(TILE_V43);
+    const double g22 = 100.0 / 111.0, g12 = 10.0 / 111.0, g02 = 1.0 / 111.0, g11 = 10.0 / 11.0;
+    // forward: beta_1, beta_0 (two-step), beta_2, sigma, weights
+    const double beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    double bj[4][3], b0j[4];
+    int slot[4], nn = 0;
+    for (int f = 0; f < 4; ++f) {
+        if (nb[f] < 0) continue;
+        adj_p1_slope(m, X, nb[f], q, bj[nn]);
+        b0j[nn] = v23 * (bj[nn][0] * bj[nn][0] + bj[nn][1] * bj[nn][1] + bj[nn][2] * bj[nn][2]);
+        slot[nn++] = f;
+    }
+    double beta0 = 0.0, s1 = 0.0, ws = 0.0, accb = 0.0, sum = 0.0, w1j[4];
+    int npair = 0;
+    if (nn > 0) {
+        for (int j = 0; j < nn; ++j)
+            for (int k = 0; k < j; ++k) {
+                sum += fabs(b0j[j] - b0j[k]);
+                ++npair;
+            }
+        s1 = npair ? pow43(sum / npair) : 0.0;
+        for (int j = 0; j < nn; ++j) {
+            w1j[j] = 1.0 + s1 / (eps + b0j[j]);
+            ws += w1j[j];
+            accb += w1j[j] * b0j[j];
+        }
+        beta0 = accb / ws;
+    }
+    const double H[3][3] = {{2.0 * a[3], a[4], a[5]}, {a[4], 2.0 * a[6], a[7]}, {a[5], a[7], 2.0 * a[8]}};
+    const double MM[3][3] = {{Mm[0], Mm[1], Mm[2]}, {Mm[1], Mm[3], Mm[4]}, {Mm[2], Mm[4], Mm[5]}};
+    double first = 0.0, MH[3][3];
+    for (int l = 0; l < 3; ++l) {
+        for (int i = 0; i < 3; ++i) MH[l][i] = MM[i][0] * H[l][0] + MM[i][1] * H[l][1] + MM[i][2] * H[l][2];
+        first += a[l] * a[l] + H[l][0] * MH[l][0] + H[l][1] * MH[l][1] + H[l][2] * MH[l][2];
+    }
+    const double second = H[0][0] * H[0][0] + a[4] * a[4] + a[5] * a[5] + H[1][1] * H[1][1] + a[7] * a[7] +
+                          H[2][2] * H[2][2];
+    const double beta2 = v23 * first + v43 * second;
+    const double z = 0.5 * (fabs(beta2 - beta1) + fabs(beta2 - beta0));
+    const double sigma = pow43(z);
+    const double bet[3] = {beta0, beta1, beta2}, gam[3] = {g02, g12, g22};
+    double r[3], w[3];
+    for (int k = 0; k < 3; ++k) {
+        r[k] = sigma / (eps + bet[k]);
+        w[k] = gam[k] * (1.0 + r[k] * r[k]);
+    }
+    const double iw = 1.0 / (w[0] + w[1] + w[2]);
+    const double c2 = (w[2] * iw) / g22;
+    const double cb = (w[1] * iw) / g11 - c2 * g12 / g11;
+    double R[9];
+    for (int k = 0; k < 9; ++k) R[k] = c2 * a[k] + (k < 3 ? cb * b[k] : 0.0);
+
+    // reverse
+    const double* l = lp + c * 50 + q * 10;
+    const double lc0 = l[0];
+    double lR[9];
+    for (int k = 0; k < 9; ++k) lR[k] = l[1 + k];
+    for (int k = 3; k < 9; ++k) lR[k] -= lc0 * Mm[k - 3];
+    double la[9], lb[3], lc2 = 0.0, lcb = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        la[k] = c2 * lR[k];
+        lc2 += lR[k] * a[k];
+    }
+    for (int i = 0; i < 3; ++i) {
+        lb[i] = cb * lR[i];
+        lcb += lR[i] * b[i];
+    }
+    // c2 = w2 iw / g22, cb = w1 iw / g11 - c2 g12 / g11
+    const double lc2t = lc2 - lcb * g12 / g11;
+    double lw[3] = {0.0, lcb * iw / g11, lc2t * iw / g22};
+    const double liw = lc2t * w[2] / g22 + lcb * w[1] / g11;
+    const double lS = -liw * iw * iw;
+    double lbet[3] = {0.0, 0.0, 0.0}, lsig = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        lw[k] += lS;
+        const double lr = lw[k] * gam[k] * 2.0 * r[k];
+        lsig += lr / (eps + bet[k]);
+        lbet[k] += -lr * sigma / ((eps + bet[k]) * (eps + bet[k]));
+    }
+    // sigma = z^{4/3}, z = (|b2 - b1| + |b2 - b0|) / 2
+    const double lz = lsig * (4.0 / 3.0) * cbrt(z);
+    const double s21 = sgn(beta2 - beta1), s20 = sgn(beta2 - beta0);
+    lbet[2] += 0.5 * lz * (s21 + s20);
+    lbet[1] += -0.5 * lz * s21;
+    lbet[0] += -0.5 * lz * s20;
+    // beta_2 = v23 first + v43 second
+    const double lfirst = v23 * lbet[2], lsecond = v43 * lbet[2];
+    double lH[3][3];
+    for (int l2 = 0; l2 < 3; ++l2) {
+        la[l2] += 2.0 * a[l2] * lfirst;
+        for (int i = 0; i < 3; ++i) lH[l2][i] = 2.0 * MH[l2][i] * lfirst;
+    }
+    lH[0][0] += 2.0 * H[0][0] * lsecond;
+    lH[1][1] += 2.0 * H[1][1] * lsecond;
+    lH[2][2] += 2.0 * H[2][2] * lsecond;
+    la[4] += 2.0 * a[4] * lsecond;
+    la[5] += 2.0 * a[5] * lsecond;
+    la[7] += 2.0 * a[7] * lsecond;
+    la[3] += 2.0 * lH[0][0];
+    la[4] += lH[0][1] + lH[1][0];
+    la[5] += lH[0][2] + lH[2][0];
+    la[6] += 2.0 * lH[1][1];
+    la[7] += lH[1][2] + lH[2][1];
+    la[8] += 2.0 * lH[2][2];
+    // beta_1 = v23 |b|^2
+    for (int i = 0; i < 3; ++i) lb[i] += 2.0 * v23 * b[i] * lbet[1];
+    // beta_0 = sum w1j b0j / sum w1j, w1j = 1 + s1 / (eps + b0j), s1 = (sum / npair)^{4/3}
+    double lbj[4][3];
+    for (int j = 0; j < 4; ++j) lbj[j][0] = lbj[j][1] = lbj[j][2] = 0.0;
+    if (nn > 0) {
+        const double lacc = lbet[0] / ws, lws = -lbet[0] * accb / (ws * ws);
+        double lb0[4], ls1 = 0.0;
+        for (int j = 0; j < nn; ++j) {
+            const double lwj = lacc * b0j[j] + lws;
+            lb0[j] = lacc * w1j[j] - lwj * s1 / ((eps + b0j[j]) * (eps + b0j[j]));
+            ls1 += lwj / (eps + b0j[j]);
+        }
+        if (npair) {
+            const double lsum = ls1 * (4.0 / 3.0) * cbrt(sum / npair) / npair;
+            for (int j = 0; j < nn; ++j)
+                for (int k = 0; k < nn; ++k)
+                    if (k != j) lb0[j] += lsum * sgn(b0j[j] - b0j[k]);
+        }
+        for (int j = 0; j < nn; ++j)
+            for (int i = 0; i < 3; ++i) lbj[j][i] = 2.0 * v23 * bj[j][i] * lb0[j];
+    }
+    // a = M2 d, b = M1 d[0:4]
+    double* o = ld + (c * 5 + q) * 16;
+    double s = 0.0;
+    for (int j = 0; j < 16; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += T_(TILE_M2 + k * 16 + j) * la[k];
+        if (j < 4 && nb[j] >= 0)
+            for (int i = 0; i < 3; ++i) acc += T_(TILE_M1 + i * 4 + j) * lb[i];
+        o[j] = acc;
+        if (j < 4 && nb[j] >= 0) s += acc;
+    }
+    own[c * 5 + q] = lc0 - s;
+    double* ob = lbn + (c * 5 + q) * 12;
+    for (int j = 0; j < 12; ++j) ob[j] = 0.0;
+    for (int j = 0; j < nn; ++j)
+        for (int i = 0; i < 3; ++i) ob[3 * slot[j] + i] = lbj[j][i];
+}
+
+// Adjoint of the neighbours' P1 slopes, per cell n and component: the slope
+// adjoints the cells around n hold for n's slope (lbn, in the slot that
+// points back to n) are summed, then carried through n's slope operator:
+// lds[n][q][f] is the adjoint of Q_nbr(n, f) - Q_n.
+__global__ void k_adj_slopes(DevMesh<double> m, const int8_t* __restrict__ rev, const double* __restrict__ lbn,
+                             double* __restrict__ lds) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t n = idx / 5, nc = m.nc;
+    const int q = (int)(idx - n * 5);
+    double ls[3] = {0.0, 0.0, 0.0};
+    for (int f = 0; f < 4; ++f) {
+        const int c = m.nbr[f * nc + n];
+        if (c < 0) continue;
+        const double* src = lbn + ((int64_t)c * 5 + q) * 12 + 3 * rev[f * nc + n];
+        for (int i = 0; i < 3; ++i) ls[i] += src[i];
+    }
+    double* o = lds + (n * 5 + q) * 4;
+    for (int f = 0; f < 4; ++f)
+        o[f] = m.nbr[f * nc + n] >= 0
+                   ? m.M1[(0 * 4 + f) * nc + n] * ls[0] + m.M1[(1 * 4 + f) * nc + n] * ls[1] +
+                         m.M1[(2 * 4 + f) * nc + n] * ls[2]
+                   : 0.0;
+}
+
 // adjoint of a cell's working state [W (5), grad W (15)]: its own part and,
 // from each neighbour n, the entries of n's stencil adjoint in the slot that
 // points back to this cell across the shared face (rev[f][c])
 __global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__ rev,
-                                   const double* __restrict__ ld, const double* __restrict__ own,
-                                   double* __restrict__ lX) {
+                                   const double* __restrict__ ld, const double* __restrict__ lds,
+                                   const double* __restrict__ own, double* __restrict__ lX) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m.nc * 5) return;
     const int64_t c = idx / 5;
@@ -324,6 +552,7 @@ __global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__
         const double* o = ld + ((int64_t)n * 5 + q) * 16;
         lq += o[r];
         for (int l = 0; l < 3; ++l) lg[l] += o[4 + 3 * r + l];
+        if (lds) lq += lds[((int64_t)n * 5 + q) * 4 + r] - lds[(c * 5 + q) * 4 + f];
     }
     double* x = lX + c * XS;
     x[q] = lq;
@@ -377,34 +606,53 @@ static Phys<double> phys64(const HostPhys& p) {
     return ph;
 }
 
-// The reverse sweep proper; the forward intermediates (poly1, poly2) come from
-// a forward recomputation by the caller.
+// transpose of one stage's reconstruction: lp (per-cell coefficient
+// adjoints) into lX, from the stage's working state X
+static void recon_back(const DevMesh<double>& m, const HostPhys& p, const AdjBuffers& b, const double* X,
+                       double* lX, cudaStream_t s) {
+    const int B = 128;
+    if (p.weno) {
+        k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, b.ld, b.lbn, b.own);
+        k_adj_slopes<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.lbn, b.lds);
+        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.lds, b.own, lX);
+    } else {
+        k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
+        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, nullptr, b.own, lX);
+    }
+}
+
+// transpose of one stage's face flux: the record adjoints in b.src into the
+// per-cell reconstruction-coefficient adjoints b.lp
+template <int NR>
+static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const AdjBuffers& b, const double* poly,
+                      double dt, cudaStream_t s) {
+    const int B = 128;
+    if (ph.viscous)
+        k_adj_point<NR><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, b.src, dt, b.lx);
+    else
+        k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, b.src, dt, b.lx);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
+    k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
+}
+
+// The reverse sweep proper; the forward intermediates (the two stages'
+// working states X1, X2 and reconstructions poly1, poly2) come from a forward
+// recomputation by the caller.
 cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,
-                            const double* lW, const double* ldW, double* oW, double* odW, cudaStream_t s) {
+                            const double* X1, const double* X2, const double* lW, const double* ldW, double* oW,
+                            double* odW, cudaStream_t s) {
     const Phys<double> ph = phys64(p);
     const int B = 128;
     cudaError_t e;
     // stage 2
     k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
-    if (ph.viscous)
-        k_adj_point<20><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
-    else
-        k_adj_point_rev<20><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly2, b.src, dt, b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
-    k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
-    k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
-    k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lXs);
+    flux_back<20>(m, ph, b, b.poly2, dt, s);
+    recon_back(m, p, b, X2, b.lXs, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 1
     k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
-    if (ph.viscous)
-        k_adj_point<40><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
-    else
-        k_adj_point_rev<40><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, b.poly1, b.src, dt, b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
-    k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
-    k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
-    k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.own, b.lX1);
+    flux_back<40>(m, ph, b, b.poly1, dt, s);
+    recon_back(m, p, b, X1, b.lX1, s);
     k_adj_final<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, b.lXs, b.lX1, oW, odW);
     return cudaGetLastError();
 }

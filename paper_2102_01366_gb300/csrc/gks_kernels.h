@@ -147,6 +147,7 @@ struct AdjBuffers {
     const double* poly1;
     const double* poly2;
     double *src, *lx, *lpf, *lp, *ld, *own, *lXs, *lX1;
+    double *lbn, *lds;  // WENO only: neighbour-slope adjoints [nc][5][4][3], [nc][5][4]
     const int8_t* rev;
     int32_t* fallback;
 };
@@ -155,7 +156,8 @@ cudaError_t adjoint_any_fallback(const int32_t* flags, int64_t n, int32_t* any, 
 // lambda (W^n, grad W^n) from lambda (W^{n+1}, grad W^{n+1}) for one step
 // with the frozen time step dt (public [component][cell] FP64 layouts)
 cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,
-                            const double* lW, const double* ldW, double* oW, double* odW, cudaStream_t s);
+                            const double* X1, const double* X2, const double* lW, const double* ldW, double* oW,
+                            double* odW, cudaStream_t s);
 
 // sets dt_fixed and t_end; with reset_time also zeroes the case times and
 // steps and sets the case minima to +inf

@@ -31,9 +31,12 @@ def cuda():
     return torch
 
 
-def _case(seed=61):
-    mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=seed)
-    W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
+def _case(seed=61, state="sine"):
+    mesh = I.box_mesh((3, 3, 3) if state == "sine" else (4, 3, 3), jitter=0.1, seed=seed)
+    if state == "sine":
+        W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
+    else:  # a moving density and pressure slab: far-from-linear WENO weights
+        W, dW = I.riemann_slab_state(mesh, inner=(1.0, 1.0), outer=(0.5, 0.6), mach=0.8)
     rng = np.random.Generator(np.random.PCG64(seed))
     W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
     dW = dW + 0.05 * rng.standard_normal(dW.shape)
@@ -44,14 +47,19 @@ def _dot(a, b):
     return float(sum((np.asarray(x) * np.asarray(y)).sum() for x, y in zip(a, b)))
 
 
-@pytest.mark.parametrize("smooth,viscous", [(0, 0), (1, 0), (0, 1)])
-def test_adjoint_matches_finite_differences(cuda, oracle_mod, smooth, viscous):
+@pytest.mark.parametrize("weno,smooth,viscous,state", [(0, 0, 0, "sine"), (0, 1, 0, "sine"), (0, 0, 1, "sine"),
+                                                       (1, 0, 0, "sine"), (1, 0, 0, "slab")])
+def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, viscous, state):
     """Inviscid runs take the reverse-mode point adjoint, the viscous run the
-    forward-mode one."""
+    forward-mode one; weno = 1 differentiates the nonlinear weights (on the
+    slab they move the gradient by ~10 % from the linear-weight one).  The
+    slab's many |x| terms (pairs of smoothness indicators, pressure jumps)
+    sit close to their kinks, so its differences use a smaller step."""
     torch = cuda
-    mesh, W, dW, rng = _case()
+    mesh, W, dW, rng = _case(state=state)
+    H = 1e-6 if state == "sine" else 1e-7
     g = gks.Mesh(mesh)
-    kw = dict(weno=0, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
+    kw = dict(weno=weno, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
     s = gks.State(g, gks.params(precision=0, **kw))
     o = oracle_mod.Mesh(mesh)
     p = oracle_mod.params(**kw)
@@ -126,7 +134,7 @@ def test_unsupported_configurations_are_rejected(cuda):
     mesh, W, dW, _ = _case()
     g = gks.Mesh(mesh)
     args = [torch.tensor(x, device="cuda") for x in (W, dW, np.zeros_like(W), np.zeros_like(dW))]
-    for kw in (dict(weno=1, precision=0), dict(weno=0, precision=1)):
+    for kw in (dict(weno=1, order=2, precision=0), dict(weno=0, precision=1)):
         s = gks.State(g, gks.params(cfl=0.5, **kw))
         with pytest.raises(gks.GksError) as e:
             s.adjoint_step(*args, 1e-3)
