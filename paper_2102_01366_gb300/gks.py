@@ -410,3 +410,61 @@ def make_step_function(state, dt):
             return state.adjoint_step(W, dW, gW, gdW, dt)
 
     return _Step.apply
+
+
+def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=20, primal_precision=0):
+    """Gradient of loss(W_N) after N steps of frozen step dt with respect to
+    the initial (W0, dW0), by the adjoint with checkpointing: the primal run
+    keeps every `checkpoint_every`-th state (in FP64, on the device), the
+    reverse sweep recomputes each segment from its checkpoint in FP64 and
+    applies gks_adjoint_step backwards through it, so the memory is one
+    segment plus the checkpoints.
+
+    loss: a torch function of the final W [5, nc] (FP64 tensor) returning a
+    scalar.  primal_precision 1 runs the primal in FP32 bulk (the checkpoints
+    are its FP64 master states); the reverse sweep is FP64 either way, so the
+    gradient then belongs to FP64 segments restarted from FP32-run
+    checkpoints.  Returns (loss value, dJ/dW0, dJ/d dW0)."""
+    import torch
+    if not isinstance(mesh, Mesh):
+        mesh = Mesh(mesh)
+    p64 = gks_params()
+    C.memmove(C.byref(p64), C.byref(params), C.sizeof(gks_params))
+    p64.precision = 0
+    s64 = State(mesh, p64)
+    primal = s64
+    if primal_precision:
+        pp = gks_params()
+        C.memmove(C.byref(pp), C.byref(params), C.sizeof(gks_params))
+        pp.precision = 1
+        primal = State(mesh, pp)
+    W = torch.as_tensor(np.ascontiguousarray(W0) if isinstance(W0, np.ndarray) else W0,
+                        dtype=torch.float64, device="cuda")
+    dW = torch.as_tensor(np.ascontiguousarray(dW0) if isinstance(dW0, np.ndarray) else dW0,
+                         dtype=torch.float64, device="cuda")
+    checkpoints = {0: (W.clone(), dW.clone())}
+    primal.init(W, dW)
+    for n in range(1, nsteps + 1):
+        primal.step(1, float(dt), 0.0)
+        if n % checkpoint_every == 0 and n < nsteps:
+            checkpoints[n] = primal.get()
+    primal.sync()
+    Wn, _ = primal.get()
+    Wn = Wn.clone().requires_grad_(True)
+    J = loss(Wn)
+    J.backward()
+    lam_W = Wn.grad.detach().clone()
+    lam_dW = torch.zeros((15, mesh.nc), dtype=torch.float64, device="cuda")
+    starts = sorted(checkpoints)
+    for k in reversed(range(len(starts))):
+        n0 = starts[k]
+        n1 = starts[k + 1] if k + 1 < len(starts) else nsteps
+        Wc, dWc = checkpoints[n0]
+        segment = [(Wc, dWc)]
+        s64.init(Wc, dWc)
+        for _ in range(n0 + 1, n1):
+            s64.step(1, float(dt), 0.0)
+            segment.append(s64.get())
+        for Ws, dWs in reversed(segment):
+            lam_W, lam_dW = s64.adjoint_step(Ws, dWs, lam_W, lam_dW, dt)
+    return float(J.detach()), lam_W, lam_dW

@@ -211,3 +211,28 @@ def test_mach_number_gradient_of_the_vortex(cuda):
     ad = float((lam_W.cpu().numpy() * dW0).sum() + (lam_dW.cpu().numpy() * ddW0).sum())
     fd = (float(energy_of(run(Wp, dWp)[0])) - float(energy_of(run(Wm, dWm)[0]))) / (2 * hm)
     assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
+
+
+def test_checkpointed_gradient(cuda):
+    """Six steps with a checkpoint every 2 give the same gradient as a
+    checkpoint every step (the recomputation is exact in FP64); an FP32-bulk
+    primal run with FP64 checkpoints gives a gradient within 1e-3 of it."""
+    torch = cuda
+    mesh, W, dW, _ = _case(seed=64)
+    g = gks.Mesh(mesh)
+    p = gks.params(weno=1, cfl=0.5)
+    s = gks.State(g, p)
+    s.init(W, dW)
+    dt = s.timestep()
+    vol = torch.tensor(g.geometry()["vol"], device="cuda")
+
+    def loss(Wn):
+        return (vol * (Wn[1:4] ** 2).sum(0) / (2.0 * Wn[0])).sum()
+
+    J1, gW1, gdW1 = gks.checkpointed_gradient(g, p, W, dW, 6, dt, loss, checkpoint_every=1)
+    J2, gW2, gdW2 = gks.checkpointed_gradient(g, p, W, dW, 6, dt, loss, checkpoint_every=2)
+    assert J1 == J2
+    assert torch.equal(gW1, gW2) and torch.equal(gdW1, gdW2)
+    J3, gW3, _ = gks.checkpointed_gradient(g, p, W, dW, 6, dt, loss, checkpoint_every=2, primal_precision=1)
+    assert abs(J3 - J1) < 1e-5 * abs(J1)
+    assert float((gW3 - gW1).abs().max() / gW1.abs().max()) < 1e-3
