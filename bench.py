@@ -269,6 +269,8 @@ def main():
     ap.add_argument("--batch-cases", type=int, default=48,
                     help="independent cases of the batched leg (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="only two adjoint steps on the periodic 16^3 x 6 density wave (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -290,6 +292,20 @@ def main():
     g = gks.Mesh(mesh)
     nc = g.nc
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    if args.profile_adjoint:
+        mesh_a, Wa, dWa = I.sine_wave_case(n=16)
+        ga = gks.Mesh(mesh_a)
+        sa = gks.State(ga, gks.params(weno=0, cfl=0.5, precision=0))
+        sa.init(Wa, dWa)
+        dta = sa.timestep()
+        Wt, dWt = torch.tensor(Wa, device="cuda"), torch.tensor(dWa, device="cuda")
+        for _ in range(2):
+            sa.adjoint_step(Wt, dWt, torch.ones_like(Wt), torch.ones_like(dWt), dta)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_adjoint": "density wave 16^3 x 6 = %d cells, FP64, linear weights" % ga.nc}))
+        return
 
     if args.profile_case:
         prec = 1 if args.precision == "fp32" else 0

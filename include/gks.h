@@ -307,7 +307,8 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * Supported: FP64 states (precision 0) with the third-order reconstruction
  * (order 3) with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
- * meshes without boundary faces; GKS_E_UNSUPPORTED otherwise, and also when a
+ * meshes, periodic or with open, slip-wall or non-slip-wall boundary faces
+ * (not fixed-state ones); GKS_E_UNSUPPORTED otherwise, and also when a
  * cell of either stage falls back to a constant reconstruction (the
  * positivity branch, whose derivative this does not build).  All arrays are
  * device FP64; d_scratch (gks_adjoint_workspace_bytes) is caller-allocated

@@ -131,17 +131,19 @@ __device__ __forceinline__ void rotate_in(const double (*Rm)[3], double* v) {
 // from the record adjoints (the transposed record formulas of the stage).
 template <int NR>
 __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const double* __restrict__ poly,
-                                                const double* __restrict__ src, int64_t f, int k,
-                                                double (*Rm)[3], double* x, double* lFh, double* lD,
-                                                double* lW0, double* ldWt) {
+                                                const double* __restrict__ Xavg, const double* __restrict__ src,
+                                                int64_t f, int k, double (*Rm)[3], double* x, double* lFh,
+                                                double* lD, double* lW0, double* ldWt) {
     const int L = m.flr[f], R = m.flr[m.nf + f];
     const double* geo = m.fgeo + f * FGEO;
     const double n[3] = {geo[0], geo[1], geo[2]};
     const double w = geo[3];
     face_frame(n, Rm);
     // record adjoints: the left cell adds the record, the right one subtracts it
+    // (a boundary face has one cell)
     double lr[NR];
-    for (int j = 0; j < NR; ++j) lr[j] = src[(int64_t)L * NR + j] - src[(int64_t)R * NR + j];
+    for (int j = 0; j < NR; ++j)
+        lr[j] = (L >= 0 ? src[(int64_t)L * NR + j] : 0.0) - (R >= 0 ? src[(int64_t)R * NR + j] : 0.0);
     for (int q = 0; q < 5; ++q) {
         double sn0 = 0.0, sn1 = 0.0;
         if (NR == 40) {
@@ -166,13 +168,32 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
     rotate_in(Rm, lW0);
     rotate_in(Rm, ldWt);
     if (x) {
-        const double XL[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
-        const double XR[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
-        double WL[5], gL[3][5], WR[5], gR[3][5];
-        eval_poly(poly + (int64_t)L * POLY_STRIDE, XL, WL, gL);
-        eval_poly(poly + (int64_t)R * POLY_STRIDE, XR, WR, gR);
-        to_local(Rm, WL, gL, x, reinterpret_cast<double (*)[5]>(x + 5));
-        to_local(Rm, WR, gR, x + 20, reinterpret_cast<double (*)[5]>(x + 25));
+        // each side's state in the face frame, as the forward flux forms it
+        for (int side = 0; side < 2; ++side) {
+            const int cell = side == 0 ? L : R;
+            const int in = side == 0 ? R : L;
+            double* xs = x + 20 * side;
+            double (*gs)[5] = reinterpret_cast<double (*)[5]>(xs + 5);
+            double Wv[5], g[3][5];
+            if (cell == FLR_OPEN) {
+                // open: the interior cell's average, zero gradient
+                for (int q = 0; q < 5; ++q) {
+                    Wv[q] = Xavg[(int64_t)in * XS + q];
+                    g[0][q] = g[1][q] = g[2][q] = 0.0;
+                }
+                to_local(Rm, Wv, g, xs, gs);
+                continue;
+            }
+            // a real side, or a wall side from the interior cell at the point
+            const int src_side = cell >= 0 ? side : 1 - side;
+            const int64_t c = cell >= 0 ? cell : in;
+            const double X[3] = {geo[4 + 9 * src_side + 3 * k], geo[5 + 9 * src_side + 3 * k],
+                                 geo[6 + 9 * src_side + 3 * k]};
+            eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
+            to_local(Rm, Wv, g, xs, gs);
+            if (cell == FLR_SLIP_WALL) slip_wall_ghost(xs, gs);
+            if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(xs, gs);
+        }
     }
 }
 
@@ -182,6 +203,7 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
 template <int NR>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Phys<double> ph,
                                                            const double* __restrict__ poly,
+                                                           const double* __restrict__ Xavg,
                                                            const double* __restrict__ src, double dt,
                                                            double* __restrict__ lx) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -190,7 +212,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Ph
     const int rem = (int)(t - f * 3 * ADJ_IN);
     const int k = rem / ADJ_IN, j = rem - k * ADJ_IN;
     double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
-    adj_point_setup<NR>(m, poly, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
+    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
     Phys<Dual<ADW>> pd;
     pd.gamma = ph.gamma;
     pd.gm1 = ph.gm1;
@@ -218,6 +240,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Ph
 template <int NR>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m, Phys<double> ph,
                                                                const double* __restrict__ poly,
+                                                               const double* __restrict__ Xavg,
                                                                const double* __restrict__ src, double dt,
                                                                double* __restrict__ lx) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,7 +248,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
     const int64_t f = t / 3;
     const int k = (int)(t - f * 3);
     double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
-    adj_point_setup<NR>(m, poly, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
+    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
     double* l = lx + t * ADJ_IN;
     double lin[ADJ_IN];
     for (int i = 0; i < ADJ_IN; ++i) lin[i] = 0.0;
@@ -238,30 +261,53 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
 // One thread per face: the input adjoints of its three points carried back
 // through the rotations and the evaluation at the points into
 // lpf[f][side][5][10].
-__global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf) {
+// A wall side's adjoint (the mirror is its own transpose) joins the interior
+// side's at the same point; an open side's goes to the interior cell's
+// average, lwo[f][5] (zero on every other face).
+__global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf,
+                                double* __restrict__ lwo) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= m.nf) return;
+    const int L = m.flr[f], R = m.flr[m.nf + f];
     const double* geo = m.fgeo + f * FGEO;
     const double n[3] = {geo[0], geo[1], geo[2]};
     double Rm[3][3];
     face_frame(n, Rm);
-    double lpL[50], lpR[50];
-    for (int j = 0; j < 50; ++j) lpL[j] = lpR[j] = 0.0;
+    double lp[2][50], lw[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < 50; ++j) lp[0][j] = lp[1][j] = 0.0;
     for (int k = 0; k < 3; ++k) {
-        const double* l = lx + (f * 3 + k) * ADJ_IN;
-        const double XL[3] = {geo[4 + 3 * k], geo[5 + 3 * k], geo[6 + 3 * k]};
-        const double XR[3] = {geo[13 + 3 * k], geo[14 + 3 * k], geo[15 + 3 * k]};
-        double lWL[5], lgL[3][5], lWR[5], lgR[3][5];
-        to_local_adj(Rm, l, reinterpret_cast<const double (*)[5]>(l + 5), lWL, lgL);
-        to_local_adj(Rm, l + 20, reinterpret_cast<const double (*)[5]>(l + 25), lWR, lgR);
-        eval_poly_adj(XL, lWL, lgL, lpL);
-        eval_poly_adj(XR, lWR, lgR, lpR);
+        double l[ADJ_IN];
+        for (int i = 0; i < ADJ_IN; ++i) l[i] = lx[(f * 3 + k) * ADJ_IN + i];
+        for (int side = 0; side < 2; ++side) {
+            const int cell = side == 0 ? L : R;
+            if (cell >= 0) continue;
+            double* ls = l + 20 * side;
+            double (*lg)[5] = reinterpret_cast<double (*)[5]>(ls + 5);
+            double* li = l + 20 * (1 - side);
+            if (cell == FLR_OPEN) {
+                double lW[5], lgg[3][5];
+                to_local_adj(Rm, ls, lg, lW, lgg);
+                for (int q = 0; q < 5; ++q) lw[q] += lW[q];
+            } else {
+                if (cell == FLR_SLIP_WALL) slip_wall_ghost(ls, lg);
+                if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(ls, lg);
+                for (int i = 0; i < 20; ++i) li[i] += ls[i];
+            }
+        }
+        for (int side = 0; side < 2; ++side) {
+            if ((side == 0 ? L : R) < 0) continue;
+            const double X[3] = {geo[4 + 9 * side + 3 * k], geo[5 + 9 * side + 3 * k], geo[6 + 9 * side + 3 * k]};
+            double lW[5], lg[3][5];
+            to_local_adj(Rm, l + 20 * side, reinterpret_cast<const double (*)[5]>(l + 20 * side + 5), lW, lg);
+            eval_poly_adj(X, lW, lg, lp[side]);
+        }
     }
     double* o = lpf + f * 100;
     for (int j = 0; j < 50; ++j) {
-        o[j] = lpL[j];
-        o[50 + j] = lpR[j];
+        o[j] = lp[0][j];
+        o[50 + j] = lp[1][j];
     }
+    for (int q = 0; q < 5; ++q) lwo[f * 5 + q] = lw[q];
 }
 
 // adjoint of a cell's reconstruction coefficients: the sum over its faces
@@ -413,8 +459,6 @@ __global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __
     const double iw = 1.0 / (w[0] + w[1] + w[2]);
     const double c2 = (w[2] * iw) / g22;
     const double cb = (w[1] * iw) / g11 - c2 * g12 / g11;
-    double R[9];
-    for (int k = 0; k < 9; ++k) R[k] = c2 * a[k] + (k < 3 ? cb * b[k] : 0.0);
 
     // reverse
     const double* l = lp + c * 50 + q * 10;
@@ -538,12 +582,19 @@ __global__ void k_adj_slopes(DevMesh<double> m, const int8_t* __restrict__ rev, 
 // points back to this cell across the shared face (rev[f][c])
 __global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__ rev,
                                    const double* __restrict__ ld, const double* __restrict__ lds,
-                                   const double* __restrict__ own, double* __restrict__ lX) {
+                                   const double* __restrict__ own, const double* __restrict__ lwo,
+                                   double* __restrict__ lX) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m.nc * 5) return;
     const int64_t c = idx / 5;
     const int q = (int)(idx - c * 5);
     double lq = own[c * 5 + q];
+    // open faces of this cell: their ghost is this cell's average
+    for (int f = 0; f < 4; ++f) {
+        const int e = m.cface[f * m.nc + c];
+        const int64_t face = e >> 1;
+        if (m.flr[(int64_t)(1 - (e & 1)) * m.nf + face] == FLR_OPEN) lq += lwo[face * 5 + q];
+    }
     double lg[3] = {0.0, 0.0, 0.0};
     for (int f = 0; f < 4; ++f) {
         const int n = m.nbr[f * m.nc + c];
@@ -614,10 +665,10 @@ static void recon_back(const DevMesh<double>& m, const HostPhys& p, const AdjBuf
     if (p.weno) {
         k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, b.ld, b.lbn, b.own);
         k_adj_slopes<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.lbn, b.lds);
-        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.lds, b.own, lX);
+        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.lds, b.own, b.lwo, lX);
     } else {
         k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
-        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, nullptr, b.own, lX);
+        k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, nullptr, b.own, b.lwo, lX);
     }
 }
 
@@ -625,13 +676,14 @@ static void recon_back(const DevMesh<double>& m, const HostPhys& p, const AdjBuf
 // per-cell reconstruction-coefficient adjoints b.lp
 template <int NR>
 static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const AdjBuffers& b, const double* poly,
-                      double dt, cudaStream_t s) {
+                      const double* X, double dt, cudaStream_t s) {
     const int B = 128;
     if (ph.viscous)
-        k_adj_point<NR><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, b.src, dt, b.lx);
+        k_adj_point<NR><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
+                                                                                        b.lx);
     else
-        k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, b.src, dt, b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf);
+        k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt, b.lx);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }
 
@@ -646,12 +698,12 @@ cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double 
     cudaError_t e;
     // stage 2
     k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
-    flux_back<20>(m, ph, b, b.poly2, dt, s);
+    flux_back<20>(m, ph, b, b.poly2, X2, dt, s);
     recon_back(m, p, b, X2, b.lXs, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 1
     k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
-    flux_back<40>(m, ph, b, b.poly1, dt, s);
+    flux_back<40>(m, ph, b, b.poly1, X1, dt, s);
     recon_back(m, p, b, X1, b.lX1, s);
     k_adj_final<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, b.lXs, b.lX1, oW, odW);
     return cudaGetLastError();

@@ -858,7 +858,7 @@ extern "C" gks_status gks_residual(gks_state* s, double* out_l2) {
 
 namespace {
 struct AdjLayout {
-    size_t poly1, src, lx, lpf, lp, ld, own, lXs, lX1, lbn, lds, rev, fallback, total = 0;
+    size_t poly1, src, lx, lpf, lp, ld, own, lXs, lX1, lbn, lds, lwo, rev, fallback, total = 0;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -879,6 +879,7 @@ AdjLayout adj_layout(int64_t nc, int64_t nf) {
     L.lX1 = L.add(8 * XS * nc);
     L.lbn = L.add(8 * 60 * nc);
     L.lds = L.add(8 * 20 * nc);
+    L.lwo = L.add(8 * 5 * nf);
     L.rev = L.add(4 * nc);
     L.fallback = L.add(4 * 2 * nc + 4);  // flags of both stages, then their or
     return L;
@@ -904,9 +905,9 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    if (s->fp32 || s->params.order != 3 || g.nbf != 0 || g.ncase != 1) {
+    if (s->fp32 || s->params.order != 3 || g.ncase != 1 || has_fixed(g)) {
         set_error("gks_adjoint_step: needs an FP64 state with the third-order reconstruction on a "
-                  "single-case mesh without boundary faces");
+                  "single-case mesh without fixed-state boundary faces");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);
@@ -966,6 +967,7 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     b.lX1 = reinterpret_cast<double*>(base + A.lX1);
     b.lbn = reinterpret_cast<double*>(base + A.lbn);
     b.lds = reinterpret_cast<double*>(base + A.lds);
+    b.lwo = reinterpret_cast<double*>(base + A.lwo);
     b.rev = reinterpret_cast<const int8_t*>(base + A.rev);
     b.fallback = fb;
     GKS_CHECK_CUDA(adjoint_reverse(m, s->phys, dt, b, st.X, st.Xs, d_lamW, d_lamdW, d_lamW_out, d_lamdW_out,

@@ -1,6 +1,7 @@
 // gks_face.cuh -- per-Gauss-point pieces of the face flux shared by the flux
 // kernels and their adjoint: the reconstruction evaluated at a point, the
-// face frame (Eq. rotate-matrix-3d) and the rotations into and out of it.
+// face frame (Eq. rotate-matrix-3d), the rotations into and out of it, and
+// the ghost states of boundary faces (Sec. 4.4).
 #pragma once
 
 #include "gks_kernels.h"
@@ -89,6 +90,55 @@ __device__ __forceinline__ void to_global(const T (*Rm)[3], T* v) {
     const T a = v[1], b = v[2], c = v[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) v[1 + i] = Rm[0][i] * a + Rm[1][i] * b + Rm[2][i] * c;
+}
+
+// Slip-wall ghost (Sec. 4.4) of a state already in the face frame (x1 along
+// the normal): the mirror image across the wall.  rho U1 changes sign; of the
+// x1-derivatives all but that of rho U1 change sign; of the x2-, x3-derivatives
+// only those of rho U1 do.
+template <typename T>
+__device__ __forceinline__ void slip_wall_ghost(T* Wt, T (*gt)[5]) {
+    Wt[1] = -Wt[1];
+    gt[0][0] = -gt[0][0];
+    gt[0][2] = -gt[0][2];
+    gt[0][3] = -gt[0][3];
+    gt[0][4] = -gt[0][4];
+    gt[1][1] = -gt[1][1];
+    gt[2][1] = -gt[2][1];
+}
+
+// Non-slip adiabatic wall at rest (Sec. 4.4) in the face frame: rho and rho E
+// kept, the three momenta reversed; every derivative of the momenta kept,
+// every derivative of rho and rho E reversed.
+template <typename T>
+__device__ __forceinline__ void noslip_wall_ghost(T* Wt, T (*gt)[5]) {
+    Wt[1] = -Wt[1];
+    Wt[2] = -Wt[2];
+    Wt[3] = -Wt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        gt[j][0] = -gt[j][0];
+        gt[j][4] = -gt[j][4];
+    }
+}
+
+// device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
+inline constexpr int FLR_OPEN = -1, FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4;
+
+// fixed boundary: the interior cell's fixed state (average and gradient)
+// extended linearly to the point X (relative to the cell's centroid)
+template <typename T>
+__device__ __forceinline__ void fixed_ghost(const T* __restrict__ x0, const T* X, T* W, T (*g)[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        T v = x0[q];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[i][q] = x0[5 + 3 * q + i];
+            v += g[i][q] * X[i];
+        }
+        W[q] = v;
+    }
 }
 
 }  // namespace gks

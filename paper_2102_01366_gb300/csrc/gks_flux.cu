@@ -21,54 +21,6 @@ namespace gks {
 // --------------------------------------------------------------------------
 // face flux
 // --------------------------------------------------------------------------
-// Slip-wall ghost (Sec. 4.4) of a state already in the face frame (x1 along
-// the normal): the mirror image across the wall.  rho U1 changes sign; of the
-// x1-derivatives all but that of rho U1 change sign; of the x2-, x3-derivatives
-// only those of rho U1 do.
-template <typename T>
-__device__ __forceinline__ void slip_wall_ghost(T* Wt, T (*gt)[5]) {
-    Wt[1] = -Wt[1];
-    gt[0][0] = -gt[0][0];
-    gt[0][2] = -gt[0][2];
-    gt[0][3] = -gt[0][3];
-    gt[0][4] = -gt[0][4];
-    gt[1][1] = -gt[1][1];
-    gt[2][1] = -gt[2][1];
-}
-
-// Non-slip adiabatic wall at rest (Sec. 4.4) in the face frame: rho and rho E
-// kept, the three momenta reversed; every derivative of the momenta kept,
-// every derivative of rho and rho E reversed.
-template <typename T>
-__device__ __forceinline__ void noslip_wall_ghost(T* Wt, T (*gt)[5]) {
-    Wt[1] = -Wt[1];
-    Wt[2] = -Wt[2];
-    Wt[3] = -Wt[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        gt[j][0] = -gt[j][0];
-        gt[j][4] = -gt[j][4];
-    }
-}
-
-// device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
-constexpr int FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4;  // -1: open
-
-// fixed boundary: the interior cell's fixed state (average and gradient)
-// extended linearly to the point X (relative to the cell's centroid)
-template <typename T>
-__device__ __forceinline__ void fixed_ghost(const T* __restrict__ x0, const T* X, T* W, T (*g)[5]) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        T v = x0[q];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            g[i][q] = x0[5 + 3 * q + i];
-            v += g[i][q] * X[i];
-        }
-        W[q] = v;
-    }
-}
 
 
 // Face flux with 6 threads per face: 3 Gauss points x 2 sides.  The two sides

@@ -148,6 +148,7 @@ struct AdjBuffers {
     const double* poly2;
     double *src, *lx, *lpf, *lp, *ld, *own, *lXs, *lX1;
     double *lbn, *lds;  // WENO only: neighbour-slope adjoints [nc][5][4][3], [nc][5][4]
+    double* lwo;        // open-face ghost adjoints [nf][5]
     const int8_t* rev;
     int32_t* fallback;
 };

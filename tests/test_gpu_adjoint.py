@@ -32,10 +32,18 @@ def cuda():
 
 
 def _case(seed=61, state="sine"):
-    mesh = I.box_mesh((3, 3, 3) if state == "sine" else (4, 3, 3), jitter=0.1, seed=seed)
-    if state == "sine":
+    if state in ("open", "slip", "noslip"):
+        # open ends or walls on x, y and z periodic; a smooth moving state
+        mesh = I.box_mesh((4, 3, 3), (1.0, 0.75, 0.75), (False, True, True), jitter=0.1, seed=seed)
+        if state != "open":
+            kind = I.BC_SLIP_WALL if state == "slip" else I.BC_NOSLIP_WALL
+            mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
+        W, dW = I.sine_wave_state(mesh, k=8.0 * np.pi / 3.0, u=(0.6, 0.5, -0.3))
+    elif state == "sine":
+        mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=seed)
         W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
     else:  # a moving density and pressure slab: far-from-linear WENO weights
+        mesh = I.box_mesh((4, 3, 3), jitter=0.1, seed=seed)
         W, dW = I.riemann_slab_state(mesh, inner=(1.0, 1.0), outer=(0.5, 0.6), mach=0.8)
     rng = np.random.Generator(np.random.PCG64(seed))
     W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
@@ -48,16 +56,18 @@ def _dot(a, b):
 
 
 @pytest.mark.parametrize("weno,smooth,viscous,state", [(0, 0, 0, "sine"), (0, 1, 0, "sine"), (0, 0, 1, "sine"),
-                                                       (1, 0, 0, "sine"), (1, 0, 0, "slab")])
+                                                       (1, 0, 0, "sine"), (1, 0, 0, "slab"), (1, 0, 0, "open"),
+                                                       (1, 0, 0, "slip"), (0, 0, 1, "noslip")])
 def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, viscous, state):
     """Inviscid runs take the reverse-mode point adjoint, the viscous run the
     forward-mode one; weno = 1 differentiates the nonlinear weights (on the
-    slab they move the gradient by ~10 % from the linear-weight one).  The
+    slab they move the gradient by ~10 % from the linear-weight one); open
+    ends and slip and non-slip walls take their ghosts' adjoints.  The
     slab's many |x| terms (pairs of smoothness indicators, pressure jumps)
     sit close to their kinks, so its differences use a smaller step."""
     torch = cuda
     mesh, W, dW, rng = _case(state=state)
-    H = 1e-6 if state == "sine" else 1e-7
+    H = 1e-7 if state == "slab" else 1e-6
     g = gks.Mesh(mesh)
     kw = dict(weno=weno, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
     s = gks.State(g, gks.params(precision=0, **kw))
@@ -139,8 +149,8 @@ def test_unsupported_configurations_are_rejected(cuda):
         with pytest.raises(gks.GksError) as e:
             s.adjoint_step(*args, 1e-3)
         assert e.value.status == -8  # GKS_E_UNSUPPORTED
-    open_mesh, Wo, dWo = I.sod_case(nx=8, nyz=2)
-    s = gks.State(gks.Mesh(open_mesh), gks.params(weno=0, cfl=0.5))
+    fixed_mesh, Wo, dWo = I.shu_osher_case(nx=8, nyz=2)  # fixed-state ends
+    s = gks.State(gks.Mesh(fixed_mesh), gks.params(weno=0, cfl=0.5))
     argso = [torch.tensor(x, device="cuda") for x in (Wo, dWo, np.zeros_like(Wo), np.zeros_like(dWo))]
     with pytest.raises(gks.GksError) as e:
         s.adjoint_step(*argso, 1e-3)
