@@ -46,6 +46,13 @@ struct FluxSmem {
     T red[FP_GP * NR];   // weighted record entries per Gauss point
 };
 
+// The two warps that hold the two sides of the same 32 Gauss points (warp w
+// and warp w + 3) exchange through shared memory only with each other, so
+// they meet at a named barrier of their own instead of the whole block's.
+__device__ __forceinline__ void pair_barrier(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (g >> 5)), "r"(64) : "memory");
+}
+
 template <typename T, int NR, int MINB>
 __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
                                                      const T* __restrict__ Wavg,
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 #pragma unroll
     for (int q = 0; q < 5; ++q) sm.w0[side][g][q] = mw0[q];
     sm.p[side][g] = S.p;
-    __syncthreads();
+    pair_barrier(g);
 
     // ---- phase 2 ----
     T Wc[5];
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             axpy5(tau * (T(1) - tc.E), mw2, dWt);
         }
     }
-    __syncthreads();
+    pair_barrier(g);
 
     // ---- phase 3 ----
     {
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 #pragma unroll
                 for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
         }
-        __syncthreads();
+        pair_barrier(g);
         if (side == 0) {
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         sm.out[side][g][10 + q] = W0[q];
         sm.out[side][g][15 + q] = dWt[q];
     }
-    __syncthreads();
+    pair_barrier(g);
 
     // ---- phase 4: left warps the flux entries, right warps the gradient entries
     T* mine_rec = sm.red + g * NR;
