@@ -10,18 +10,12 @@
 // averages and of gradients by Eq. gauss-formula); those are transposed by
 // hand, each as a gather so that no two threads write one location.  The
 // kinetic solution (Eq. 2nd-flux with Eq. new-equ-part) is differentiated in
-// reverse mode for inviscid flow (gks_point_adj.cuh, about three point
-// evaluations of work); with viscosity it is differentiated in forward mode:
-// the same templated point code runs on Dual numbers, one input direction a
-// pass (40 passes a point), and each Jacobian column is contracted with the
-// output adjoints at once.
+// reverse mode (gks_point_adj.cuh, about three point evaluations of work),
+// inviscid or viscous.
 //
 //   k_adj_src2 / k_adj_src1  per-cell adjoints of the face-record sums
-//   k_adj_point_rev<NR>      per (face, Gauss point), inviscid: the point
-//                            solution's adjoint in reverse mode
-//   k_adj_point<NR>          per (face, Gauss point, input), viscous: one
-//                            column of the point solution's Jacobian (forward
-//                            mode) against the output adjoints
+//   k_adj_point_rev<NR>      per (face, Gauss point): the point solution's
+//                            adjoint in reverse mode
 //   k_adj_face_back          per face: rotations and evaluation at the
 //                            points transposed -> adjoints of both cells'
 //                            reconstruction coefficients
@@ -37,16 +31,14 @@
 
 #include "gks_cells.cuh"
 #include "gks_device.cuh"
-#include "gks_dual.cuh"
 #include "gks_face.cuh"
 #include "gks_kernels.h"
 #include "gks_point_adj.cuh"
 
 namespace gks {
 
-constexpr int ADW = 1;           // directions per forward-mode pass
 constexpr int ADJ_IN = 40;       // inputs of the point solution: WL, gL, WR, gR (face frame)
-constexpr int ADJ_THREADS = 64;  // threads per block of k_adj_point
+constexpr int ADJ_THREADS = 64;  // threads per block of k_adj_point_rev
 
 // stage 2 records: [sum w 4/3 D (5) | sum w dW n (15)]; the cell sums enter
 // W^{n+1} = W^n - (S + sum s rec[0:5]) / |Omega| and
@@ -197,46 +189,8 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
     }
 }
 
-// One thread per (face, Gauss point, input direction) of interior faces: the
-// point solution differentiated in forward mode along one input and the
-// column contracted with the output adjoints: lx[f][k][j] = (J^T lambda)_j.
-template <int NR>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_point(DevMesh<double> m, Phys<double> ph,
-                                                           const double* __restrict__ poly,
-                                                           const double* __restrict__ Xavg,
-                                                           const double* __restrict__ src, double dt,
-                                                           double* __restrict__ lx) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.nf * 3 * ADJ_IN) return;
-    const int64_t f = t / (3 * ADJ_IN);
-    const int rem = (int)(t - f * 3 * ADJ_IN);
-    const int k = rem / ADJ_IN, j = rem - k * ADJ_IN;
-    double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
-    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
-    Phys<Dual<ADW>> pd;
-    pd.gamma = ph.gamma;
-    pd.gm1 = ph.gm1;
-    pd.K = ph.K;
-    pd.tau_eps = ph.tau_eps;
-    pd.tau_c = ph.tau_c;
-    pd.mu = ph.mu;
-    pd.eps_w = ph.eps_w;
-    pd.viscous = ph.viscous;
-    pd.smooth = ph.smooth;
-    Dual<ADW> in[ADJ_IN];
-    for (int i = 0; i < ADJ_IN; ++i) in[i] = Dual<ADW>(x[i]);
-    in[j].d[0] = 1.0;
-    Dual<ADW> Fh[5], D[5], W0[5], dW[5];
-    gks_point(pd, in, reinterpret_cast<const Dual<ADW>(*)[5]>(in + 5), in + 20,
-              reinterpret_cast<const Dual<ADW>(*)[5]>(in + 25), Dual<ADW>(dt), Fh, D, W0, dW);
-    double acc = 0.0;
-    for (int q = 0; q < 5; ++q)
-        acc += lFh[q] * Fh[q].d[0] + lD[q] * D[q].d[0] + lW0[q] * W0[q].d[0] + ldWt[q] * dW[q].d[0];
-    lx[t] = acc;
-}
-
-// One thread per (face, Gauss point) of interior faces, inviscid flow: the
-// point solution's adjoint in reverse mode (gks_point_adj), lx[f][k][0:40].
+// One thread per (face, Gauss point) of interior faces: the point
+// solution's adjoint in reverse mode (gks_point_adj), lx[f][k][0:40].
 template <int NR>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m, Phys<double> ph,
                                                                const double* __restrict__ poly,
@@ -678,11 +632,7 @@ template <int NR>
 static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const AdjBuffers& b, const double* poly,
                       const double* X, double dt, cudaStream_t s) {
     const int B = 128;
-    if (ph.viscous)
-        k_adj_point<NR><<<grid_of(m.nf * 3 * ADJ_IN, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
-                                                                                        b.lx);
-    else
-        k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt, b.lx);
+    k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt, b.lx);
     k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }

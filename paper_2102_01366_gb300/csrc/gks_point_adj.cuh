@@ -1,9 +1,10 @@
 // gks_point_adj.cuh -- reverse-mode (adjoint) derivative of the kinetic
-// solution at one Gauss point, FP64, for inviscid flow (tau = 0).
+// solution at one Gauss point, FP64, inviscid or viscous.
 //
 // gks_point_adj recomputes the forward quantities of gks_point (the two
 // half-space moment tables, the interface equilibrium, the time coefficients,
-// the micro-slopes of both sides and of the equilibrium) and then carries the
+// the micro-slopes of both sides and of the equilibrium, and with viscosity
+// each side's time slope A from its full table) and then carries the
 // output adjoints (of Fh, D, W0, dW) back through each of them in reverse
 // order: every building block of gks_device.cuh has its transpose here
 // (adj_*).  The moment sums are multilinear in the tables' one-dimensional
@@ -268,13 +269,15 @@ __device__ __forceinline__ void adj_micro_slope(const Prim<double>& s, double K,
     ls.w += 2.0 * s.w * le;
 }
 
-// Adjoint of gks_point for tau = 0 (inviscid): output adjoints lFh, lD, lW0,
-// ldW (face frame) into the input adjoints lWl, lgl, lWr, lgr (accumulated).
+// Adjoint of gks_point: output adjoints lFh, lD, lW0, ldW (face frame) into
+// the input adjoints lWl, lgl, lWr, lgr (accumulated).  Inviscid (tau = 0)
+// and viscous (tau = mu / p_c, with the A terms of each side) alike.
 __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const double (*gl)[5],
                               const double* Wr, const double (*gr)[5], double dt, const double* lFh,
                               const double* lD, const double* lW0, const double* ldW, double* lWl,
                               double (*lgl)[5], double* lWr, double (*lgr)[5]) {
     const double K = ph.K;
+    const bool visc = ph.viscous != 0, smooth = ph.smooth != 0;
     const double* Win[2] = {Wl, Wr};
     const double (*gin[2])[5] = {gl, gr};
     // ---- forward recomputation ----
@@ -288,8 +291,10 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
     }
     const Prim<double> C = to_prim(Wc, ph.gm1);
     const TimeCoef<double> tc = time_coefs(ph, P[0].p, P[1].p, C.p, dt);
-    double a[2][3][5];
+    const double tau = tc.tau;
+    double a[2][3][5], As[2][5], rs[2][5];
     double dWc[3][5] = {};
+    TabD tfs[2];  // full tables of the two sides (viscous only)
     for (int s = 0; s < 2; ++s) {
         const double ir = 1.0 / P[s].rho;
         for (int i = 0; i < 3; ++i) {
@@ -297,6 +302,12 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
             for (int k = 0; k < 5; ++k) b[k] = gin[s][i][k] * ir;
             micro_slope(P[s], K, b, a[s][i]);
             acc_apsi<0, 0, 0>(th[s], a[s][i], P[s].rho, dWc[i]);
+        }
+        if (visc && !smooth) {
+            make_tab(tfs[s], P[s], K, 0);
+            for (int k = 0; k < 5; ++k) rs[s][k] = 0.0;
+            acc_grad<0>(tfs[s], a[s], -1.0, rs[s]);
+            micro_slope(P[s], K, rs[s], As[s]);
         }
     }
     TabD tf;
@@ -318,16 +329,24 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
     double lCrho = 0.0;  // adjoint of the rho factor of the equilibrium sums
     double lWc[5] = {0, 0, 0, 0, 0};
     double lac[3][5] = {}, lAc[5] = {0, 0, 0, 0, 0}, lrA[5] = {0, 0, 0, 0, 0};
-    // time-coefficient adjoints
-    double lk0 = 0, lk1 = 0, ldk0 = 0, ldk1 = 0, lq1 = 0, ldq1 = 0, lE = 0;
+    // adjoints of the time coefficients and of tau
+    double lk0 = 0, lk1 = 0, ldk0 = 0, ldk1 = 0, lq1 = 0, lq2 = 0, lq3 = 0, ldq1 = 0, ldq2 = 0, ldq3 = 0;
+    double lE = 0, ltau = 0;
+    // equilibrium sums (recomputed for the coefficient adjoints)
+    double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mf2[5] = {0, 0, 0, 0, 0}, mw1[5];
+    acc_psi<1, 0, 0>(tf, C.rho, mf0);
+    acc_grad<1>(tf, ac, C.rho, mf1);
+    acc_apsi<1, 0, 0>(tf, Ac, C.rho, mf2);
+    for (int k = 0; k < 5; ++k) mw1[k] = -C.rho * rA[k];
     double lmf0[5], lmf1[5], lmf2[5], lmw1[5];
-    if (ph.smooth) {
+    if (smooth) {
         for (int k = 0; k < 5; ++k) {
             lmf0[k] = hd * lFh[k];
-            lmf1[k] = 0.0;
-            lmf2[k] = 0.5 * hd * hd * lFh[k] + 0.25 * dt * dt * lD[k];
+            lmf1[k] = -tau * hd * lFh[k];
+            lmf2[k] = (0.5 * hd * hd - tau * hd) * lFh[k] + 0.25 * dt * dt * lD[k];
             lmw1[k] = -dt * ldW[k];
             lWc[k] += lW0[k];
+            ltau += -hd * lFh[k] * (mf1[k] + mf2[k]);
         }
     } else {
         const double C23 = dt * (tc.E - 1.0);
@@ -336,38 +355,28 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
             lmf1[k] = tc.q2 * lFh[k] + tc.dq2 * lD[k];
             lmf2[k] = tc.q3 * lFh[k] + tc.dq3 * lD[k];
             lmw1[k] = C23 * ldW[k];
-        }
-        // the coefficients' own adjoints need the sums: recompute them
-        double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mw1[5];
-        acc_psi<1, 0, 0>(tf, C.rho, mf0);
-        acc_grad<1>(tf, ac, C.rho, mf1);
-        for (int k = 0; k < 5; ++k) mw1[k] = -C.rho * rA[k];
-        for (int k = 0; k < 5; ++k) {
             lq1 += lFh[k] * mf0[k];
+            lq2 += lFh[k] * mf1[k];
+            lq3 += lFh[k] * mf2[k];
             ldq1 += lD[k] * mf0[k];
-            lk1 += lFh[k] * mf1[k];   // q2 = k1 (tau = 0)
-            ldk1 += lD[k] * mf1[k];   // dq2 = dk1
+            ldq2 += lD[k] * mf1[k];
+            ldq3 += lD[k] * mf2[k];
             lE += dt * ldW[k] * mw1[k];
         }
-        // q3, dq3 depend on dt only (tau = 0)
     }
     // mw1 = -rho_c rA
     for (int k = 0; k < 5; ++k) {
         lCrho += -lmw1[k] * rA[k];
         lrA[k] += -C.rho * lmw1[k];
     }
-    // mf2 = acc_apsi<1,0,0>(tf, Ac, rho_c); mf1 = acc_grad<1>(tf, ac, rho_c); mf0 = acc_psi<1>(tf, rho_c)
     adj_acc_apsi<1, 0, 0>(tf, Ac, C.rho, lmf2, ltf, lAc, lCrho);
     adj_acc_grad<1>(tf, ac, C.rho, lmf1, ltf, lac, lCrho);
     adj_acc_psi<1, 0, 0>(tf, C.rho, lmf0, ltf, lCrho);
-    // Ac = micro_slope(C, K, rA)
     adj_micro_slope(C, K, rA, lAc, lC, lrA);
-    // rA = -sum_i <(ac_i . psi) u_i psi>
     {
         double lunused = 0.0;
         adj_acc_grad<0>(tf, ac, -1.0, lrA, ltf, lac, lunused);
     }
-    // ac_i = micro_slope(C, K, dWc_i / rho_c)
     double ldWc[3][5] = {};
     for (int i = 0; i < 3; ++i) {
         double lb[5] = {0, 0, 0, 0, 0};
@@ -380,38 +389,62 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
     adj_make_tab(tf, C, K, 0, ltf, lC);
     lC.rho += lCrho;
 
-    // time coefficients (tau = 0): k0, k1, dk0, dk1, q1, dq1, E from tau_n
+    // the two sides: kinetic parts (full flux), their sums, slopes and tables
     TabD lth[2];
     PrimAdj lP[2];
     double la[2][3][5] = {};
     for (int s = 0; s < 2; ++s) {
         tab_zero(lth[s]);
-        double lrho = 0.0;
-        if (!ph.smooth) {
-            double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mw1[5] = {0, 0, 0, 0, 0};
-            acc_psi<1, 0, 0>(th[s], P[s].rho, mf0);
-            acc_grad<1>(th[s], a[s], P[s].rho, mf1);
-            acc_grad<0>(th[s], a[s], P[s].rho, mw1);
-            double lmf0s[5], lmf1s[5], lmw0s[5], lmw1s[5];
-            for (int k = 0; k < 5; ++k) {
-                lmf0s[k] = tc.k0 * lFh[k] + tc.dk0 * lD[k];
-                lmf1s[k] = -tc.k1 * lFh[k] - tc.dk1 * lD[k];
-                lmw0s[k] = lW0[k];
-                lmw1s[k] = -dt * tc.E * ldW[k];
-                lk0 += lFh[k] * mf0[k];
-                lk1 += -lFh[k] * mf1[k];
-                ldk0 += lD[k] * mf0[k];
-                ldk1 += -lD[k] * mf1[k];
-                lE += -dt * ldW[k] * mw1[k];
+        double lrho = 0.0, lA[5] = {0, 0, 0, 0, 0};
+        if (!smooth) {
+            double kf0[5] = {0, 0, 0, 0, 0}, kf1[5] = {0, 0, 0, 0, 0}, kw0[5] = {0, 0, 0, 0, 0},
+                   kw1[5] = {0, 0, 0, 0, 0}, kf2[5] = {0, 0, 0, 0, 0}, kw2[5] = {0, 0, 0, 0, 0};
+            acc_psi<1, 0, 0>(th[s], P[s].rho, kf0);
+            acc_grad<1>(th[s], a[s], P[s].rho, kf1);
+            acc_psi<0, 0, 0>(th[s], P[s].rho, kw0);
+            acc_grad<0>(th[s], a[s], P[s].rho, kw1);
+            if (visc) {
+                acc_apsi<1, 0, 0>(th[s], As[s], P[s].rho, kf2);
+                acc_apsi<0, 0, 0>(th[s], As[s], P[s].rho, kw2);
             }
-            adj_acc_psi<1, 0, 0>(th[s], P[s].rho, lmf0s, lth[s], lrho);
-            adj_acc_grad<1>(th[s], a[s], P[s].rho, lmf1s, lth[s], la[s], lrho);
-            adj_acc_psi<0, 0, 0>(th[s], P[s].rho, lmw0s, lth[s], lrho);
-            adj_acc_grad<0>(th[s], a[s], P[s].rho, lmw1s, lth[s], la[s], lrho);
+            double lkf0[5], lkf1[5], lkw0[5], lkw1[5], lkf2[5], lkw2[5];
+            const double cw1 = tau - (tau + dt) * tc.E, cw2 = tau * (1.0 - tc.E);
+            for (int k = 0; k < 5; ++k) {
+                // Fh += k0 f0 - (tau k0 + k1) f1 - tau k0 f2; D alike with dk;
+                // W0 += w0 - tau w1 - tau w2; dW += cw1 w1 + cw2 w2
+                lkf0[k] = tc.k0 * lFh[k] + tc.dk0 * lD[k];
+                lkf1[k] = -(tau * tc.k0 + tc.k1) * lFh[k] - (tau * tc.dk0 + tc.dk1) * lD[k];
+                lkf2[k] = -tau * tc.k0 * lFh[k] - tau * tc.dk0 * lD[k];
+                lkw0[k] = lW0[k];
+                lkw1[k] = -tau * lW0[k] + cw1 * ldW[k];
+                lkw2[k] = -tau * lW0[k] + cw2 * ldW[k];
+                lk0 += lFh[k] * (kf0[k] - tau * kf1[k] - tau * kf2[k]);
+                lk1 += -lFh[k] * kf1[k];
+                ldk0 += lD[k] * (kf0[k] - tau * kf1[k] - tau * kf2[k]);
+                ldk1 += -lD[k] * kf1[k];
+                ltau += -lFh[k] * tc.k0 * (kf1[k] + kf2[k]) - lD[k] * tc.dk0 * (kf1[k] + kf2[k]) -
+                        lW0[k] * (kw1[k] + kw2[k]) + ldW[k] * ((1.0 - tc.E) * (kw1[k] + kw2[k]));
+                lE += ldW[k] * (-(tau + dt) * kw1[k] - tau * kw2[k]);
+            }
+            adj_acc_psi<1, 0, 0>(th[s], P[s].rho, lkf0, lth[s], lrho);
+            adj_acc_grad<1>(th[s], a[s], P[s].rho, lkf1, lth[s], la[s], lrho);
+            adj_acc_psi<0, 0, 0>(th[s], P[s].rho, lkw0, lth[s], lrho);
+            adj_acc_grad<0>(th[s], a[s], P[s].rho, lkw1, lth[s], la[s], lrho);
+            if (visc) {
+                adj_acc_apsi<1, 0, 0>(th[s], As[s], P[s].rho, lkf2, lth[s], lA, lrho);
+                adj_acc_apsi<0, 0, 0>(th[s], As[s], P[s].rho, lkw2, lth[s], lA, lrho);
+            }
         }
-        // dWc_i += acc_apsi<0,0,0>(th, a_i, rho)
+        if (visc && !smooth) {
+            // A = micro_slope(P, K, r), r = -sum_i <(a_i . psi) u_i psi> over the full table
+            double lr[5] = {0, 0, 0, 0, 0}, lunused = 0.0;
+            TabD ltfs;
+            tab_zero(ltfs);
+            adj_micro_slope(P[s], K, rs[s], lA, lP[s], lr);
+            adj_acc_grad<0>(tfs[s], a[s], -1.0, lr, ltfs, la[s], lunused);
+            adj_make_tab(tfs[s], P[s], K, 0, ltfs, lP[s]);
+        }
         for (int i = 0; i < 3; ++i) adj_acc_apsi<0, 0, 0>(th[s], a[s][i], P[s].rho, ldWc[i], lth[s], la[s][i], lrho);
-        // a_i = micro_slope(P, K, g_i / rho)
         double (*lg)[5] = s == 0 ? lgl : lgr;
         const double ir = 1.0 / P[s].rho;
         for (int i = 0; i < 3; ++i) {
@@ -425,34 +458,35 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
         }
         lP[s].rho += lrho;
     }
-    // time coefficients -> tau_n -> the two pressures
-    if (!ph.smooth) {
+    // time coefficients -> tau_n, tau -> the pressures
+    if (!smooth) {
+        // q1 = hd - k0; q2 = k1 + tau k0 - tau hd; q3 = hd^2/2 - tau hd + tau k0;
+        // dq1 = tn omh^2; dq2 = dk1 + tau dk0; dq3 = dt^2/4 + tau dk0
+        lk0 += -lq1 + tau * lq2 + tau * lq3;
+        lk1 += lq2;
+        ltau += (tc.k0 - hd) * (lq2 + lq3) + tc.dk0 * (ldq2 + ldq3);
+        ldk1 += ldq2;
+        ldk0 += tau * (ldq2 + ldq3);
         const double tn = tc.tau_n;
         const double Eh = sqrt(tc.E);
         const double omh = 1.0 - Eh;
-        lk0 += -lq1;                  // q1 = hd - k0
         double ltn = 0.0, lEh = 0.0, lomh = 0.0;
-        // k0 = tn omh
         ltn += lk0 * omh;
         lomh += lk0 * tn;
-        // k1 = tn (tn omh - hd Eh)
         ltn += lk1 * (2.0 * tn * omh - hd * Eh);
         lomh += lk1 * tn * tn;
         lEh += lk1 * (-tn * hd);
-        // dk0 = -tn omh^2
         ltn += ldk0 * (-omh * omh);
         lomh += ldk0 * (-2.0 * tn * omh);
-        // dk1 = -tn^2 omh^2 + tn dt Eh omh
         ltn += ldk1 * (-2.0 * tn * omh * omh + dt * Eh * omh);
         lomh += ldk1 * (-2.0 * tn * tn * omh + tn * dt * Eh);
         lEh += ldk1 * tn * dt * omh;
-        // dq1 = tn omh^2
         ltn += ldq1 * omh * omh;
         lomh += ldq1 * 2.0 * tn * omh;
-        // E = Eh^2, omh = 1 - Eh, Eh = exp(-hd / tn)
         lEh += 2.0 * Eh * lE - lomh;
         ltn += lEh * Eh * hd / (tn * tn);
-        // tn = tau_eps dt + tau_c |x| dt, x = (pl - pr) / (pl + pr)
+        // tn = (viscous ? tau : tau_eps dt) + tau_c |x| dt, x = (pl - pr) / (pl + pr)
+        if (visc) ltau += ltn;
         const double pl = P[0].p, pr = P[1].p;
         const double x = (pl - pr) / (pl + pr);
         const double sx = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
@@ -461,11 +495,10 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
         lP[0].p += lx * 2.0 * pr / den;
         lP[1].p += lx * (-2.0 * pl) / den;
     }
-    // C = to_prim(Wc)
+    // tau = mu / p_c (viscous)
+    if (visc) lC.p += -ltau * ph.mu / (C.p * C.p);
     adj_to_prim(Wc, ph.gm1, C, lC, lWc);
-    // Wc = sum_s acc_psi<0,0,0>(th_s, rho_s)
     for (int s = 0; s < 2; ++s) adj_acc_psi<0, 0, 0>(th[s], P[s].rho, lWc, lth[s], lP[s].rho);
-    // the half-space tables and the primitive states
     for (int s = 0; s < 2; ++s) {
         adj_make_tab(th[s], P[s], K, s == 0 ? +1 : -1, lth[s], lP[s]);
         adj_to_prim(Win[s], ph.gm1, P[s], lP[s], s == 0 ? lWl : lWr);

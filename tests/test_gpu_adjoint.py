@@ -56,12 +56,14 @@ def _dot(a, b):
 
 
 @pytest.mark.parametrize("weno,smooth,viscous,state", [(0, 0, 0, "sine"), (0, 1, 0, "sine"), (0, 0, 1, "sine"),
-                                                       (1, 0, 0, "sine"), (1, 0, 0, "slab"), (1, 0, 0, "open"),
+                                                       (0, 1, 1, "sine"), (1, 0, 0, "sine"), (1, 0, 0, "slab"),
+                                                       (1, 0, 1, "slab"), (1, 0, 0, "open"), (1, 0, 1, "open"),
                                                        (1, 0, 0, "slip"), (0, 0, 1, "noslip")])
 def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, viscous, state):
-    """Inviscid runs take the reverse-mode point adjoint, the viscous run the
-    forward-mode one; weno = 1 differentiates the nonlinear weights (on the
-    slab they move the gradient by ~10 % from the linear-weight one); open
+    """Viscous runs carry tau = mu / p_c and each side's time slope A
+    through the reverse-mode point adjoint; weno = 1 differentiates the
+    nonlinear weights (on the slab they move the gradient by ~10 % from the
+    linear-weight one); open
     ends and slip and non-slip walls take their ghosts' adjoints.  The
     slab's many |x| terms (pairs of smoothness indicators, pressure jumps)
     sit close to their kinks, so its differences use a smaller step."""
