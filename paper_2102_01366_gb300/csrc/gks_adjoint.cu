@@ -191,7 +191,7 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
 
 // One thread per (face, Gauss point) of interior faces: the point
 // solution's adjoint in reverse mode (gks_point_adj), lx[f][k][0:40].
-template <int NR>
+template <int NR, bool VISC>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m, Phys<double> ph,
                                                                const double* __restrict__ poly,
                                                                const double* __restrict__ Xavg,
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
     double* l = lx + t * ADJ_IN;
     double lin[ADJ_IN];
     for (int i = 0; i < ADJ_IN; ++i) lin[i] = 0.0;
-    gks_point_adj(ph, x, reinterpret_cast<const double (*)[5]>(x + 5), x + 20,
+    gks_point_adj<VISC>(ph, x, reinterpret_cast<const double (*)[5]>(x + 5), x + 20,
                   reinterpret_cast<const double (*)[5]>(x + 25), dt, lFh, lD, lW0, ldWt, lin,
                   reinterpret_cast<double (*)[5]>(lin + 5), lin + 20, reinterpret_cast<double (*)[5]>(lin + 25));
     for (int i = 0; i < ADJ_IN; ++i) l[i] = lin[i];
@@ -632,7 +632,12 @@ template <int NR>
 static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const AdjBuffers& b, const double* poly,
                       const double* X, double dt, cudaStream_t s) {
     const int B = 128;
-    k_adj_point_rev<NR><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt, b.lx);
+    if (ph.viscous)
+        k_adj_point_rev<NR, true><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
+                                                                                       b.lx);
+    else
+        k_adj_point_rev<NR, false><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
+                                                                                        b.lx);
     k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }

@@ -271,13 +271,16 @@ __device__ __forceinline__ void adj_micro_slope(const Prim<double>& s, double K,
 
 // Adjoint of gks_point: output adjoints lFh, lD, lW0, ldW (face frame) into
 // the input adjoints lWl, lgl, lWr, lgr (accumulated).  Inviscid (tau = 0)
-// and viscous (tau = mu / p_c, with the A terms of each side) alike.
+// and viscous (tau = mu / p_c, with the A terms of each side) alike; VISC
+// must equal ph.viscous (the inviscid instance keeps no viscous state).
+template <bool VISC>
 __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const double (*gl)[5],
                               const double* Wr, const double (*gr)[5], double dt, const double* lFh,
                               const double* lD, const double* lW0, const double* ldW, double* lWl,
                               double (*lgl)[5], double* lWr, double (*lgr)[5]) {
     const double K = ph.K;
-    const bool visc = ph.viscous != 0, smooth = ph.smooth != 0;
+    constexpr bool visc = VISC;
+    const bool smooth = ph.smooth != 0;
     const double* Win[2] = {Wl, Wr};
     const double (*gin[2])[5] = {gl, gr};
     // ---- forward recomputation ----
