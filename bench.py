@@ -225,6 +225,48 @@ def adjoint_leg(torch, gks, args):
             "timing": "wall clock of the library calls, %d each after warm-up (forward: init + step)" % reps}
 
 
+def sphere_leg(torch, gks, args, flush):
+    """Viscous flow past a sphere, Re 100 on the diameter, Ma 0.2: the O-type
+    shell of 64 radial (ratio 1.08) x 96 polar x 192 azimuthal hexes x 6
+    tets (3 on the pole rows) = 7,004,160 cells, far field at r = 20, flat
+    faces (the split mirrored in theta on the southern half), WENO,
+    started from the free stream.  The first steps are timed
+    in FP32 bulk and in FP64 (CUDA events per step, L2 flushed), and the two
+    states are compared after the same steps."""
+    t0 = time.perf_counter()
+    mesh, W, dW, mu = I.sphere_case()
+    g = gks.Mesh(mesh)
+    setup_s = time.perf_counter() - t0
+    kw = dict(weno=1, cfl=0.5, viscous=1, mu=mu)
+    out = {"workload": "sphere Re 100 Ma 0.2, O-type shell 64 x 96 x 192 hexes x 6 tets (3 on pole rows), "
+                       "r 0.5..20, radial ratio 1.08, flat faces, WENO, viscous (mu 0.002), from the free stream",
+           "cells": g.nc, "faces": g.nf, "boundary_faces": g.n_boundary, "host_setup_s": setup_s}
+    states = {}
+    for name, prec, steps in (("fp32", 1, max(5, args.steps // 5)), ("fp64", 0, 3)):
+        s = gks.State(g, gks.params(precision=prec, **kw))
+        s.init(W, dW)
+        if prec == 1:
+            s.autotune(steps=3, cache=False)
+        ms = replicas.max_over_ranks(time_device(torch, s, steps, min(args.warmup, 3), flush))
+        t, _ = s.time()
+        out[name] = {"ms_per_step": ms, "value": replicas.world()[0] * g.nc * 2 / (ms / 1000.0) / 1e6,
+                     "steps_timed": steps, "t": t, "variant": list(s.variant)}
+        s.init(W, dW)
+        s.step(3)
+        s.sync()
+        states[name] = s.get()[0].cpu().numpy()
+        del s
+        torch.cuda.empty_cache()
+    # differences after the same 3 steps, each component against its free-stream
+    # scale (rho, rho |U|, rho |U|, rho |U|, rho E)
+    a, b = states["fp32"], states["fp64"]
+    scale = [W[0, 0], W[1, 0], W[1, 0], W[1, 0], W[4, 0]]
+    out["fp32_vs_fp64_after_3_steps"] = {n: float(np.abs(a[q] - b[q]).max() / scale[q])
+                                         for q, n in enumerate(("rho", "rho_u", "rho_v", "rho_w", "rho_E"))}
+    out["unit"] = METRIC
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = replicas.world()
     if rank != 0:
@@ -269,6 +311,7 @@ def main():
     ap.add_argument("--batch-cases", type=int, default=48,
                     help="independent cases of the batched leg (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
+    ap.add_argument("--no-sphere", action="store_true", help="skip the 7M-cell viscous sphere leg")
     ap.add_argument("--profile-adjoint", action="store_true",
                     help="only two adjoint steps on the periodic 16^3 x 6 density wave (for profilers)")
     args = ap.parse_args()
@@ -409,6 +452,8 @@ def main():
         line["batched"] = batched_leg(torch, gks, args, flush)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(torch, gks, args)
+    if not args.no_sphere:
+        line["sphere"] = sphere_leg(torch, gks, args, flush)
     if rank == 0 and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

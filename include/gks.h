@@ -63,7 +63,9 @@ typedef struct gks_params {
     double eps_weno;     /* epsilon of the nonlinear weights, Sec. 4.2 (paper: 1e-8) */
     double tau_eps;      /* epsilon of the numerical collision time, Sec. 2.2 (0.01) */
     double tau_c;        /* C of the numerical collision time, Sec. 2.2 (1) */
-    int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2); 1: nonlinear */
+    int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2; at order 3 a
+                            boundary cell takes the least-squares first-order fit to
+                            its P2 stencil's data, Sec. 4.4); 1: nonlinear */
     int32_t order;       /* 3: R^3rd (Eq. final_weno_expression-3rd); 2: R^2nd */
     int32_t smooth_flux; /* 0: full solver Eq. 2nd-flux; 1: smooth Eq. 2nd-smooth-flux */
     int32_t viscous;     /* 0: Euler, tau = 0; 1: tau = mu / p (Sec. 2.2) */

@@ -58,6 +58,7 @@ struct ora_mesh {
     double *farea, *fnorm, *gp_l, *gp_r;
     /* stencils */
     double *M1, *M2;
+    double* M2L;  /* [nc][3][16]: boundary cells' first-order fit (Sec. 4.4), else 0 */
     int64_t n_singular;
     /* boundary kind of each face (ORA_BC_*), meaningful on boundary faces */
     int8_t* bkind;      /* [nf] */
@@ -399,6 +400,7 @@ static void neighbour_offset(const ora_mesh* m, int64_t c, int f, double d[3]) {
 static void build_stencils(ora_mesh* m) {
     m->M1 = (double*)calloc((size_t)m->nc * 12, sizeof(double));
     m->M2 = (double*)calloc((size_t)m->nc * 144, sizeof(double));
+    m->M2L = (double*)calloc((size_t)m->nc * 48, sizeof(double));
     m->n_singular = 0;
     for (int64_t c = 0; c < m->nc; ++c) {
         int faces[4], nn = 0;
@@ -486,6 +488,25 @@ static void build_stencils(ora_mesh* m) {
         }
         for (int k = 0; k < 9; ++k)
             for (int j = 0; j < 16; ++j) m->M2[c * 144 + k * 16 + j] = R[k * 16 + j] / sc[k];
+
+        /* Sec. 4.4: a boundary cell of the linear-weight (smooth)
+         * reconstruction uses a first-order polynomial fitted to its P2
+         * stencil in the least-squares sense.  READING: the rows are the
+         * neighbours' averages (d_r . b = dQ_r) and averaged gradients
+         * (b = grad Q_r, each scaled by h0 as in the P2 system), unweighted;
+         * solved here by the normal equations. */
+        if (nn == 3) {
+            double G[9] = {0}, H[3 * 16] = {0};
+            for (int r = 0; r < nn; ++r) {
+                for (int i = 0; i < 3; ++i) {
+                    for (int j = 0; j < 3; ++j) G[i * 3 + j] += d[r][i] * d[r][j] + (i == j ? h0 * h0 : 0.0);
+                    H[i * 16 + faces[r]] = d[r][i];
+                    H[i * 16 + 4 + 3 * faces[r] + i] = h0 * h0;
+                }
+            }
+            if (gauss_solve(3, 16, G, H, &pmin, &pmax) == 0 && pmin >= 1e-12 * pmax)
+                memcpy(&m->M2L[c * 48], H, sizeof(double) * 48);
+        }
     }
 }
 
@@ -548,7 +569,7 @@ void ora_mesh_free(ora_mesh* m) {
     free(m->csr_face); free(m->csr_sign);
     free(m->vol); free(m->cen); free(m->mom2); free(m->dr);
     free(m->farea); free(m->fnorm); free(m->gp_l); free(m->gp_r);
-    free(m->M1); free(m->M2); free(m->bkind); free(m->fixW); free(m->fixdW);
+    free(m->M1); free(m->M2); free(m->M2L); free(m->bkind); free(m->fixW); free(m->fixdW);
     free(m);
 }
 
@@ -705,10 +726,21 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
             double P1[10] = {Q0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             double P2[10] = {Q0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int i = 0; i < 3; ++i) P1[1 + i] = b[(c * 5 + q) * 3 + i];
-            for (int k = 0; k < 9; ++k) {
-                double s = 0.0;
-                for (int j = 0; j < 16; ++j) s += m->M2[c * 144 + k * 16 + j] * data[j];
-                P2[1 + k] = s;
+            int boundary = 0;
+            for (int f = 0; f < 4; ++f) boundary |= m->nbr[c * 4 + f] < 0;
+            if (boundary && !p->weno && p->order == 3) {
+                /* Sec. 4.4: the first-order least-squares fit instead of P2 */
+                for (int k = 0; k < 3; ++k) {
+                    double s = 0.0;
+                    for (int j = 0; j < 16; ++j) s += m->M2L[c * 48 + k * 16 + j] * data[j];
+                    P2[1 + k] = s;
+                }
+            } else {
+                for (int k = 0; k < 9; ++k) {
+                    double s = 0.0;
+                    for (int j = 0; j < 16; ++j) s += m->M2[c * 144 + k * 16 + j] * data[j];
+                    P2[1 + k] = s;
+                }
             }
             double Rb[10];
             if (!p->weno) {

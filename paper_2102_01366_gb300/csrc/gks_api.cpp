@@ -438,6 +438,9 @@ static gks_status upload_mesh(gks_state* s) {
     std::vector<T> dr(nc), M1(12 * nc);
     // per-block tile [blk][TILE_ROWS][CELLS_PER_BLOCK], zero past the last cell
     std::vector<T> tile((size_t)nblk * TILE_ROWS * CELLS_PER_BLOCK, T(0));
+    // Sec. 4.4: with linear weights a boundary cell's third-order step is the
+    // least-squares first-order fit to its P2 stencil
+    const bool linear_boundary = !s->params.weno && s->params.order == 3;
     for (int64_t c = 0; c < nc; ++c) {
         T* tc = &tile[(size_t)(c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK];
         auto put_row = [&](int row, double v) { tc[(size_t)row * CELLS_PER_BLOCK] = (T)v; };
@@ -457,7 +460,13 @@ static gks_status upload_mesh(gks_state* s) {
             M1[k * nc + c] = (T)g.M1[c * 12 + k];
             put_row(TILE_M1 + k, g.M1[c * 12 + k]);
         }
-        for (int k = 0; k < 144; ++k) put_row(TILE_M2 + k, g.M2[c * 144 + k]);
+        const double* M2c = &g.M2[c * 144];
+        double M2lin[144];
+        if (linear_boundary && !g.singular[c] &&
+            (g.nbr[c * 4] < 0 || g.nbr[c * 4 + 1] < 0 || g.nbr[c * 4 + 2] < 0 || g.nbr[c * 4 + 3] < 0) &&
+            cell_linear_fit(g, c, M2lin))
+            M2c = M2lin;
+        for (int k = 0; k < 144; ++k) put_row(TILE_M2 + k, M2c[k]);
     }
     auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);

@@ -40,4 +40,5 @@ namespace gks {
 void set_error(const std::string& msg);
 gks_status build_mesh(gks_mesh& m);      // topology + geometry
 gks_status build_stencils(gks_mesh& m);  // M1, M2
+bool cell_linear_fit(const gks_mesh& m, int64_t c, double* M2);  // boundary cells, linear weights
 }  // namespace gks

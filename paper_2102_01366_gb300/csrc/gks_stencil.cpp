@@ -214,6 +214,49 @@ bool cell_stencil(const gks_mesh& m, int64_t c, double* M1, double* M2) {
 
 }  // namespace
 
+// Sec. 4.4, boundary cells of the linear-weight (smooth) reconstruction: a
+// first-order polynomial fitted to the P2 stencil's data by least squares,
+// the neighbours' averages (rows d_f . b = dQ_f) and averaged gradients
+// (rows b = grad Q_f), each gradient row scaled by h0 = |Omega|^(1/3) as in
+// the P2 system.  Written into the 9 x 16 layout of M2 (the quadratic rows
+// zero); false when the cell has fewer than 3 neighbours or the fit is
+// singular.
+bool cell_linear_fit(const gks_mesh& m, int64_t c, double* M2) {
+    int fl[4], nn = 0;
+    double d[4][3];
+    for (int f = 0; f < 4; ++f) {
+        int64_t nb = m.nbr[c * 4 + f];
+        if (nb < 0) continue;
+        for (int a = 0; a < 3; ++a)
+            d[nn][a] = (m.cen[nb * 3 + a] + (double)m.nbr_img[(c * 4 + f) * 3 + a] * m.per(c)[a]) -
+                       m.cen[c * 3 + a];
+        fl[nn++] = f;
+    }
+    std::memset(M2, 0, sizeof(double) * 144);
+    if (nn < 3) return false;
+    const double h0 = std::cbrt(m.vol[c]);
+    // unknown y = h0 b; rows: (d_f / h0) . y = dQ_f, then y_l = h0 dQ_f/dx_l
+    const int rows = 4 * nn;
+    double A[16 * 3], Q[256], R[9];
+    for (int r = 0; r < nn; ++r)
+        for (int a = 0; a < 3; ++a) A[r * 3 + a] = d[r][a] / h0;
+    for (int r = 0; r < nn; ++r)
+        for (int l = 0; l < 3; ++l)
+            for (int a = 0; a < 3; ++a) A[(nn + 3 * r + l) * 3 + a] = a == l ? 1.0 : 0.0;
+    householder_qr(rows, 3, A, Q, R);
+    if (diag_ratio(3, R) < 1e-12) return false;
+    double X[3 * 16];
+    for (int i = 0; i < 3; ++i)
+        for (int r = 0; r < rows; ++r) X[i * rows + r] = Q[r * rows + i];  // Q1^T
+    upper_solve(3, R, rows, X);
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < nn; ++r) {
+            M2[k * 16 + fl[r]] = X[k * rows + r] / h0;
+            for (int l = 0; l < 3; ++l) M2[k * 16 + 4 + 3 * fl[r] + l] = X[k * rows + nn + 3 * r + l];
+        }
+    return true;
+}
+
 gks_status build_stencils(gks_mesh& m) {
     m.M1.assign((size_t)m.nc * 12, 0.0);
     m.M2.assign((size_t)m.nc * 144, 0.0);

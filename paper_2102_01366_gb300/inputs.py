@@ -673,3 +673,107 @@ def batch_cases(n_cases=48, n_range=(8, 40), seed=5, jitter=0.1, quad_order=3,
         dWs.append(dW)
         desc.append({"n": n, "kind": kind, "mach": mach if kind == "riemann" else None})
     return batch_mesh(meshes), np.concatenate(Ws, axis=1), np.concatenate(dWs, axis=1), desc, meshes
+
+
+def sphere_shell_mesh(nr=64, ntheta=96, nphi=192, r0=0.5, r1=20.0, ratio=1.08):
+    """O-type mesh of the shell r0 <= r <= r1 around a sphere of diameter
+    2 r0 (the viscous sphere of Sec. 5.3): nr radial layers with radii in
+    geometric progression (ratio between successive spacings), ntheta polar
+    and nphi azimuthal divisions, every (r, theta, phi) hexahedron cut into
+    the 6 Kuhn tetrahedra in index space.  On the two rows of hexahedra
+    touching a pole the azimuthal edge on the axis collapses to a point;
+    the 3 Kuhn tetrahedra that contain such an edge are degenerate and are
+    left out, so those rows carry 3 tetrahedra per hexahedron:
+    nc = 6 nr (ntheta - 2) nphi + 3 nr 2 nphi.  Faces are flat (the
+    sphere is represented by its inscribed polyhedron); the split is
+    mirrored in theta on the southern half so that both poles are alike
+    (the split of each theta = const face is unchanged by the mirror, so
+    the two halves stay conforming); no periodic axis
+    (the seam at phi = 2 pi reuses the vertices at phi = 0).  bkind marks
+    the faces on r = r0 as non-slip walls and those on r = r1 as fixed
+    (far-field) faces.  Cells are ordered with phi fastest, then theta,
+    then r."""
+    q = float(ratio)
+    s = np.arange(nr + 1, dtype=np.float64)
+    frac = s / nr if q == 1.0 else (q ** s - 1.0) / (q ** nr - 1.0)
+    rad = r0 + (r1 - r0) * frac
+    th = math.pi * np.arange(ntheta + 1) / ntheta
+    ph = 2.0 * math.pi * np.arange(nphi) / nphi
+    npole = nr + 1
+    # vertex ids: north poles, south poles, then (i, j = 1..ntheta-1, k)
+    nv = 2 * npole + npole * (ntheta - 1) * nphi
+    xyz = np.empty((nv, 3))
+    xyz[:npole] = np.stack([np.zeros(npole), np.zeros(npole), rad], axis=1)
+    xyz[npole:2 * npole] = np.stack([np.zeros(npole), np.zeros(npole), -rad], axis=1)
+    I, J, K = np.meshgrid(np.arange(npole), np.arange(1, ntheta), np.arange(nphi), indexing="ij")
+    R, T, P = rad[I], th[J], ph[K]
+    xyz[2 * npole:] = np.stack([R * np.sin(T) * np.cos(P), R * np.sin(T) * np.sin(P), R * np.cos(T)],
+                               axis=-1).reshape(-1, 3)
+    vrad = np.empty(nv, dtype=np.int64)
+    vrad[:npole] = np.arange(npole)
+    vrad[npole:2 * npole] = np.arange(npole)
+    vrad[2 * npole:] = I.ravel()
+
+    def vid(i, j, k):
+        k = k % nphi
+        mid = 2 * npole + (i * (ntheta - 1) + (j - 1)) * nphi + k
+        return np.where(j == 0, i, np.where(j == ntheta, npole + i, mid))
+
+    hi, hj, hk = np.meshgrid(np.arange(nr), np.arange(ntheta), np.arange(nphi), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()  # phi fastest
+    nh = hi.size
+    # southern half: the split mirrored in theta, so that both poles carry
+    # the same pattern (the unmirrored split leaves the south-pole cells
+    # with nearly dependent stencils)
+    south = hj >= (ntheta + 1) // 2
+    tets = np.empty((nh, 6, 4), dtype=np.int64)
+    for t, perm in enumerate(KUHN_PERMS):
+        o = [0, 0, 0]
+        offs = [list(o)]
+        for a in perm:
+            o[a] += 1
+            offs.append(list(o))
+        for v, (oi, oj, ok) in enumerate(offs):
+            tets[:, t, v] = vid(hi + oi, hj + np.where(south, 1 - oj, oj), hk + ok)
+    tets = tets.reshape(-1, 4)
+    srt = np.sort(tets, axis=1)
+    keep = (srt[:, 1:] != srt[:, :-1]).all(axis=1)
+    tets = tets[keep]
+    # positive orientation
+    x = xyz[tets]
+    vol = np.einsum("ij,ij->i", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
+    neg = vol < 0.0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    nc = tets.shape[0]
+    kind = np.zeros((nc, 4), dtype=np.int8)
+    tr = vrad[tets]
+    for f in range(4):
+        others = [v for v in range(4) if v != f]
+        kind[(tr[:, others] == 0).all(axis=1), f] = BC_NOSLIP_WALL
+        kind[(tr[:, others] == nr).all(axis=1), f] = BC_FIXED
+    return {
+        "xyz": xyz,
+        "tet": tets,
+        "shift": np.zeros((nc, 4, 3), dtype=np.int8),
+        "period": np.zeros(3),
+        "bkind": kind,
+        "n": (nr, ntheta, nphi),
+        "radii": (float(r0), float(r1)),
+    }
+
+
+def sphere_case(nr=64, ntheta=96, nphi=192, r0=0.5, r1=20.0, ratio=1.08, mach=0.2, reynolds=100.0,
+                gamma=1.4):
+    """Viscous flow past a sphere of diameter D = 2 r0 (Sec. 5.3): the shell
+    mesh of sphere_shell_mesh started impulsively from the free stream
+    (rho = 1, p = 1/gamma so that c = 1, U = (mach, 0, 0)), zero gradients;
+    the far-field faces hold that state.  Returns (mesh, W, dW, mu) with the
+    constant viscosity mu = rho U D / Re."""
+    mesh = sphere_shell_mesh(nr, ntheta, nphi, r0, r1, ratio)
+    nc = mesh["tet"].shape[0]
+    p = 1.0 / gamma
+    w = np.array([1.0, mach, 0.0, 0.0, p / (gamma - 1.0) + 0.5 * mach * mach])
+    W = np.ascontiguousarray(np.repeat(w[:, None], nc, axis=1))
+    dW = np.zeros((15, nc))
+    mesh["fixed_state"] = (W, dW)
+    return mesh, W, dW, mach * 2.0 * r0 / reynolds

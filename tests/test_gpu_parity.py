@@ -70,10 +70,28 @@ CASES = {
                                                       seed=38)),
                            lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.6, -0.3, 0.2)),
                            dict(weno=1, viscous=1, mu=0.01)),
+    # the sphere's O-type shell (pole rows of 3 tets per hexahedron), non-slip
+    # wall at r = 0.5, far field held at r = 1.5, viscous, a perturbed free
+    # stream; with linear weights the wall cells take the first-order fit
+    "sphere_shell_linear_viscous": (lambda: I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08),
+                                    lambda m: I.sine_wave_state(m, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4),
+                                    dict(weno=0, viscous=1, mu=0.01)),
+    "sphere_shell_weno_viscous": (lambda: I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08),
+                                  lambda m: I.sine_wave_state(m, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4),
+                                  dict(weno=1, viscous=1, mu=0.01)),
     # both ends fixed to the initial state (inflow state, wave profile)
     "shu_osher_small_weno": (lambda: I.shu_osher_case(nx=20, nyz=2, jitter=0.1)[0],
                              lambda m: I.shu_osher_state(m), dict(weno=1)),
 }
+
+
+# Cases whose step amplifies rounding: on the coarse shell (22.5 degrees
+# between neighbouring wall faces) the third-order WENO wall cells grow a
+# 1e-15 relative perturbation of the start to 3e-13 after 5 steps and 1e-10
+# after 10 in the oracle itself (the same run twice, once perturbed; with
+# linear weights it stays at 8e-15), so two implementations can agree to the
+# stated tolerance only over the first steps; those cases compare fewer.
+STEPS = {"sphere_shell_weno_viscous": 4}
 
 
 def _walled(mesh):
@@ -142,8 +160,9 @@ def test_face_record_parity(cuda, oracle_mod, name, stage, precision):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_ten_steps_parity(cuda, oracle_mod, name, precision):
     mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, precision)
-    Wo, dWo, t_o, n = o.run(p, W, dW, nsteps=10)
-    s.step(10)
+    nsteps = STEPS.get(name, 10)
+    Wo, dWo, t_o, n = o.run(p, W, dW, nsteps=nsteps)
+    s.step(nsteps)
     s.sync()
     Wg, dWg = [x.cpu().numpy() for x in s.get()]
     t_g, _ = s.time()

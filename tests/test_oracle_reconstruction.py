@@ -51,6 +51,32 @@ def _expected_monomial(cen, c0, g, H):
     return out
 
 
+def _boundary_fit(om, avg, grad, period=1.0):
+    """For every cell with a missing neighbour: the gradient b minimising
+    sum_r (d_r . b - dQ_r)^2 + h0^2 |b - grad Q_r|^2 over its neighbours r
+    (d_r the centroid offset, minimal periodic image of the unit box),
+    by numpy's least-squares solver."""
+    geo = om.geometry()
+    cen, vol = geo["cen"], geo["vol"]
+    nbr = om.topology()["nbr"]
+    out = np.full((om.nc, 3), np.nan)
+    for c in np.nonzero((nbr < 0).any(axis=1))[0]:
+        h0 = np.cbrt(vol[c])
+        rows, rhs = [], []
+        for nb in nbr[c][nbr[c] >= 0]:
+            d = cen[nb] - cen[c]
+            d -= period * np.round(d / period)
+            rows.append(d)
+            rhs.append(avg[nb] - avg[c])
+            for l in range(3):
+                e = np.zeros(3)
+                e[l] = h0
+                rows.append(e)
+                rhs.append(h0 * grad[nb, l])
+        out[c] = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+    return out
+
+
 @pytest.mark.parametrize("periodic", [(False, True, True), (True, True, False)])
 @pytest.mark.parametrize("weno", [0, 1])
 def test_quadratic_field_reproduced(oracle_mod, periodic, weno):
@@ -69,8 +95,15 @@ def test_quadratic_field_reproduced(oracle_mod, periodic, weno):
     assert not fb.any()
     exp = _expected_monomial(om.geometry()["cen"], 0.3, g, H)
     if weno == 0:
-        # P2 is exact for any quadratic (interior and boundary cells)
-        np.testing.assert_allclose(poly[:, 1, :], exp, atol=1e-10)
+        # P2 is exact for any quadratic in the interior; a boundary cell takes
+        # the least-squares first-order fit to its P2 stencil (Sec. 4.4)
+        nbr = om.topology()["nbr"]
+        inner = (nbr >= 0).all(axis=1)
+        assert inner.any() and (~inner).any()
+        np.testing.assert_allclose(poly[inner, 1, :], exp[inner], atol=1e-10)
+        np.testing.assert_allclose(poly[~inner, 1, 0], avg[~inner], atol=1e-12)
+        np.testing.assert_array_equal(poly[~inner, 1, 4:], 0.0)
+        np.testing.assert_allclose(poly[~inner, 1, 1:4], _boundary_fit(om, avg, grad)[~inner], atol=1e-10)
     else:
         # nonlinear weights only reproduce linear data exactly; check the
         # linear case below, here only that the mean is kept
