@@ -226,7 +226,7 @@ def adjoint_leg(torch, gks, args):
 
 
 def sphere_leg(torch, gks, args, flush):
-    """Viscous flow past a sphere, Re 100 on the diameter, Ma 0.2: the O-type
+    """Viscous flow past a sphere, Re 100 on the diameter, Ma 0.2, Pr 0.72: the O-type
     shell of 64 radial (ratio 1.08) x 96 polar x 192 azimuthal hexes x 6
     tets (3 on the pole rows) = 7,004,160 cells, far field at r = 20, flat
     faces (the split mirrored in theta on the southern half), WENO,
@@ -237,9 +237,9 @@ def sphere_leg(torch, gks, args, flush):
     mesh, W, dW, mu = I.sphere_case()
     g = gks.Mesh(mesh)
     setup_s = time.perf_counter() - t0
-    kw = dict(weno=1, cfl=0.5, viscous=1, mu=mu)
+    kw = dict(weno=1, cfl=0.5, viscous=1, mu=mu, prandtl=0.72)
     out = {"workload": "sphere Re 100 Ma 0.2, O-type shell 64 x 96 x 192 hexes x 6 tets (3 on pole rows), "
-                       "r 0.5..20, radial ratio 1.08, flat faces, WENO, viscous (mu 0.002), from the free stream",
+                       "r 0.5..20, radial ratio 1.08, flat faces, WENO, viscous (mu 0.002, Pr 0.72), from the free stream",
            "cells": g.nc, "faces": g.nf, "boundary_faces": g.n_boundary, "host_setup_s": setup_s}
     states = {}
     for name, prec, steps in (("fp32", 1, max(5, args.steps // 5)), ("fp64", 0, 3)):

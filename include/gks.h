@@ -63,6 +63,8 @@ typedef struct gks_params {
     double eps_weno;     /* epsilon of the nonlinear weights, Sec. 4.2 (paper: 1e-8) */
     double tau_eps;      /* epsilon of the numerical collision time, Sec. 2.2 (0.01) */
     double tau_c;        /* C of the numerical collision time, Sec. 2.2 (1) */
+    double prandtl;      /* Prandtl number of the viscous solver (BGK gives 1; other
+                            values correct the heat flux, Pr fix below); 1 default */
     int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2; at order 3 a
                             boundary cell takes the least-squares first-order fit to
                             its P2 stencil's data, Sec. 4.4); 1: nonlinear */
@@ -76,7 +78,16 @@ typedef struct gks_params {
 } gks_params;
 
 /* Fills the paper's defaults: gamma 1.4, cfl 1, mu 0, eps_weno 1e-8,
- * tau_eps 0.01, tau_c 1, weno 1, order 3, full flux, Euler, FP64. */
+ * tau_eps 0.01, tau_c 1, prandtl 1, weno 1, order 3, full flux, Euler, FP64.
+ *
+ * Pr fix (viscous = 1, prandtl != 1): the BGK model fixes Pr = 1 (Sec. 2);
+ * the energy entries of the time-integrated flux get (1/Pr - 1) q, with q
+ * the time integral of the heat flux (1/2) int (u1 - U1) |u - U|^2 f dXi of
+ * the interface distribution of Eq. 2nd-flux (xi included), U the velocity
+ * of the interface equilibrium state in the face frame.  The paper names
+ * no formula; this is the correction of the gas-kinetic literature it cites
+ * for the Navier-Stokes solver.  Not differentiated: gks_adjoint_step
+ * rejects it. */
 void gks_params_default(gks_params* p);
 
 typedef struct gks_mesh gks_mesh;   /* opaque, library-owned host object */

@@ -990,6 +990,15 @@ static void slopes_of_state(const mtab* full, const prim* st, const double dW[3]
     micro_slope(full, r, A);
 }
 
+/* Pr fix of one interval's flux F given its state integral IW = int psi f:
+ * F_E += prf q, q = F_E - U.F_m + |U|^2/2 F_rho - U1 (IW_E - U.IW_m + |U|^2/2 IW_rho) */
+static void heat_flux_fix(double prf, const double U[3], const double IW[5], double F[5]) {
+    double uu = 0.5 * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    double qf = F[4] - (U[0] * F[1] + U[1] * F[2] + U[2] * F[3]) + uu * F[0];
+    double qw = IW[4] - (U[0] * IW[1] + U[1] * IW[2] + U[2] * IW[3]) + uu * IW[0];
+    F[4] += prf * (qf - U[0] * qw);
+}
+
 void ora_gp_flux(const ora_params* p, const double* Wl, const double* dWl_,
                  const double* Wr, const double* dWr_, double dt, double* Fh,
                  double* F, double* W0, double* Wdt) {
@@ -1058,13 +1067,26 @@ void ora_gp_flux(const ora_params* p, const double* Wl, const double* dWl_,
     grad_term(&hr, ar, 0, 0, 0, r_wa);
     psi_moments(&hr, &pAr, r_wA);
 
+    /* Pr fix (viscous, Pr != 1): the energy flux over [0, d] gains
+     * (1/Pr - 1) q, q = int_0^d int (u1 - U1) (|u - U|^2 + xi^2)/2 f, U the
+     * interface equilibrium velocity.  The paper names no formula (BGK has
+     * Pr = 1, Sec. 2); READING: the heat-flux correction of the gas-kinetic
+     * Navier-Stokes solver, applied to the time-integrated flux.  Since
+     * (u1 - U1)|c|^2/2 = u1 eps - u1 U.u + u1 |U|^2/2 - U1 (eps - U.u + |U|^2/2),
+     * q follows from the interval's flux and its state integral IW. */
+    const double prf = p->viscous ? 1.0 / p->prandtl - 1.0 : 0.0;
+    double IW[2][5];
+
     if (p->smooth_flux) {
         /* Eq. 2nd-smooth-flux: f = g^c - tau (a^c.u + A^c) g^c + A^c g^c t */
         for (int h = 0; h < 2; ++h) {
             double d = h == 0 ? 0.5 * dt : dt;
             double* out = h == 0 ? Fh : F;
-            for (int k = 0; k < 5; ++k)
+            for (int k = 0; k < 5; ++k) {
                 out[k] = C.rho * (d * c_f[k] - tau * d * (c_fa[k] + c_fA[k]) + 0.5 * d * d * c_fA[k]);
+                IW[h][k] = C.rho * (d * c_w[k] - tau * d * (c_wa[k] + c_wA[k]) + 0.5 * d * d * c_wA[k]);
+            }
+            if (prf != 0.0) heat_flux_fix(prf, C.U, IW[h], out);
         }
         for (int h = 0; h < 2; ++h) {
             double t = h == 0 ? 0.0 : dt;
@@ -1086,10 +1108,15 @@ void ora_gp_flux(const ora_params* p, const double* Wl, const double* dWl_,
         double q2 = k1 + tau * k0 - tau * d;           /* int C2 */
         double q3 = 0.5 * d * d - tau * d + tau * k0;  /* int C3 */
         double* out = h == 0 ? Fh : F;
-        for (int k = 0; k < 5; ++k)
+        for (int k = 0; k < 5; ++k) {
             out[k] = C.rho * (q1 * c_f[k] + q2 * c_fa[k] + q3 * c_fA[k]) +
                      L.rho * (k0 * l_f[k] - (tau * k0 + k1) * l_fa[k] - tau * k0 * l_fA[k]) +
                      R.rho * (k0 * r_f[k] - (tau * k0 + k1) * r_fa[k] - tau * k0 * r_fA[k]);
+            IW[h][k] = C.rho * (q1 * c_w[k] + q2 * c_wa[k] + q3 * c_wA[k]) +
+                       L.rho * (k0 * l_w[k] - (tau * k0 + k1) * l_wa[k] - tau * k0 * l_wA[k]) +
+                       R.rho * (k0 * r_w[k] - (tau * k0 + k1) * r_wa[k] - tau * k0 * r_wA[k]);
+        }
+        if (prf != 0.0) heat_flux_fix(prf, C.U, IW[h], out);
     }
     /* point values of f at t = 0 and t = dt */
     for (int h = 0; h < 2; ++h) {

@@ -25,6 +25,7 @@ typedef struct {
     int32_t order;     /* 3: third-order R, 2: second-order R (Eq. of R^2nd) */
     int32_t smooth_flux; /* 0: full solver (2nd-flux), 1: smooth solver */
     int32_t viscous;   /* 0: Euler (tau = 0), 1: tau = mu / p */
+    double prandtl;    /* viscous only: Pr != 1 corrects the heat flux (Pr fix) */
 } ora_params;
 
 typedef struct ora_mesh ora_mesh;

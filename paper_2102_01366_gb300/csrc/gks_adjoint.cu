@@ -608,6 +608,7 @@ static Phys<double> phys64(const HostPhys& p) {
     ph.eps_w = p.eps_weno;
     ph.viscous = p.viscous;
     ph.smooth = p.smooth;
+    ph.prf = p.prf;
     return ph;
 }
 

@@ -45,6 +45,7 @@ extern "C" void gks_params_default(gks_params* p) {
     p->eps_weno = 1e-8;
     p->tau_eps = 0.01;
     p->tau_c = 1.0;
+    p->prandtl = 1.0;
     p->weno = 1;
     p->order = 3;
     p->smooth_flux = 0;
@@ -59,8 +60,8 @@ static gks_status check_params(const gks_params* p) {
         return GKS_E_ARG;
     }
     if (!(p->cfl > 0.0) || !(p->eps_weno > 0.0) || !(p->tau_eps >= 0.0) || !(p->tau_c >= 0.0) ||
-        !(p->mu >= 0.0)) {
-        set_error("cfl, eps_weno must be positive; tau_eps, tau_c, mu non-negative");
+        !(p->mu >= 0.0) || !(p->prandtl > 0.0)) {
+        set_error("cfl, eps_weno, prandtl must be positive; tau_eps, tau_c, mu non-negative");
         return GKS_E_ARG;
     }
     if ((p->weno != 0 && p->weno != 1) || (p->order != 2 && p->order != 3) ||
@@ -518,7 +519,8 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     s->mesh = mesh;
     s->params = *params;
     s->phys = HostPhys{params->gamma, params->cfl, params->mu, params->eps_weno, params->tau_eps,
-                       params->tau_c, params->weno, params->order, params->smooth_flux, params->viscous};
+                       params->tau_c, params->weno, params->order, params->smooth_flux, params->viscous,
+                       params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0};
     s->fp32 = fp32;
     s->ws = static_cast<char*>(d_workspace);
     s->L = L;
@@ -914,7 +916,7 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    if (s->fp32 || s->params.order != 3 || g.ncase != 1 || has_fixed(g)) {
+    if (s->fp32 || s->params.order != 3 || g.ncase != 1 || has_fixed(g) || s->phys.prf != 0.0) {
         set_error("gks_adjoint_step: needs an FP64 state with the third-order reconstruction on a "
                   "single-case mesh without fixed-state boundary faces");
         return GKS_E_UNSUPPORTED;

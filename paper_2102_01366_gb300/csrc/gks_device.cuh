@@ -63,6 +63,7 @@ struct Phys {
     T gamma, gm1, K;     // K internal degrees of freedom
     T tau_eps, tau_c, mu;
     T eps_w;
+    T prf;               // Pr fix: 1/Pr - 1 (0 without it)
     int viscous, smooth;
 };
 
@@ -273,6 +274,19 @@ __device__ __forceinline__ void axpy5(T a, const T* x, T* y) {
     for (int k = 0; k < 5; ++k) y[k] += a * x[k];
 }
 
+// Pr fix of the energy flux over one time interval: F_E += (1/Pr - 1) q with
+// q = int (u1 - U1) (|u - U|^2 + xi^2) / 2 f, expanded into the flux F and the
+// state integral IW = int psi f over the same interval (U the interface
+// equilibrium velocity, face frame):
+//   q = F_E - U.F_m + |U|^2/2 F_rho - U1 (IW_E - U.IW_m + |U|^2/2 IW_rho)
+template <typename T>
+__device__ __forceinline__ void prandtl_fix(T prf, const T* U, const T* IW, T* F) {
+    const T uu = T(0.5) * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    const T qf = F[4] - (U[0] * F[1] + U[1] * F[2] + U[2] * F[3]) + uu * F[0];
+    const T qw = IW[4] - (U[0] * IW[1] + U[1] * IW[2] + U[2] * IW[3]) + uu * IW[0];
+    F[4] += prf * (qf - U[0] * qw);
+}
+
 // One side's initial-state (kinetic) part of Eq. 2nd-flux,
 //   e^{-t/tau_n} g [1 - (tau + t) a.u - tau A] H(+-u1),
 // added to Fh, D, W0, dW.  Each velocity moment is formed once and scaled by
@@ -333,6 +347,12 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     const Prim<T> C = to_prim(Wc, ph.gm1);
     const TimeCoef<T> tc = time_coefs(ph, P[0].p, P[1].p, C.p, dt);
     const T tau = tc.tau;
+    // state integrals over [0, dt/2] and their "dt minus twice" differences,
+    // for the Pr fix only
+    const bool prfix = ph.prf != T(0);
+    T IWh[5], IWd[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) IWh[k] = IWd[k] = T(0);
     T dWc[3][5];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -359,6 +379,12 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
         axpy5(T(1), mw0, W0);
         axpy5(-tau, mw1, W0);
         axpy5(tau - (tau + dt) * tc.E, mw1, dW);
+        if (prfix) {
+            axpy5(tc.k0, mw0, IWh);
+            axpy5(-(tau * tc.k0 + tc.k1), mw1, IWh);
+            axpy5(tc.dk0, mw0, IWd);
+            axpy5(-(tau * tc.dk0 + tc.dk1), mw1, IWd);
+        }
         if (ph.viscous) {
             T mf2[5] = {0}, mw2[5] = {0};
             acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
@@ -367,6 +393,10 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
             axpy5(-tau * tc.dk0, mf2, D);
             axpy5(-tau, mw2, W0);
             axpy5(tau * (T(1) - tc.E), mw2, dW);
+            if (prfix) {
+                axpy5(-tau * tc.k0, mw2, IWh);
+                axpy5(-tau * tc.dk0, mw2, IWd);
+            }
         }
     }
     // hydrodynamic (equilibrium) part: C1 g^c + C2 a^c.u g^c + C3 A^c g^c
@@ -390,6 +420,13 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
 #pragma unroll
         for (int k = 0; k < 5; ++k) W0[k] = Wc[k];  // tau terms cancel: <(a.u + A) psi> = 0
         axpy5(-dt, mw1, dW);
+        if (prfix) {
+            // int psi f over [0, dt/2] = hd W^c - hd^2/2 rho <(a^c.u) psi> (the
+            // A^c moments are minus the a^c.u ones); the difference -dt^2/4 of it
+            axpy5(hd, Wc, IWh);
+            axpy5(-T(0.5) * hd * hd, mw1, IWh);
+            axpy5(-T(0.25) * dt * dt, mw1, IWd);
+        }
     } else {
         axpy5(tc.q1, mf0, Fh);
         axpy5(tc.q2, mf1, Fh);
@@ -400,6 +437,17 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
         // t = dt: C2, C3 (C1 cancelled against the kinetic W0 terms)
         const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
         axpy5(C2 - C3, mw1, dW);
+        if (prfix) {
+            axpy5(tc.q1, Wc, IWh);
+            axpy5(tc.q2 - tc.q3, mw1, IWh);
+            axpy5(tc.dq1, Wc, IWd);
+            axpy5(tc.dq2 - tc.dq3, mw1, IWd);
+        }
+    }
+    if (prfix) {
+        const T U[3] = {C.u, C.v, C.w};
+        prandtl_fix(ph.prf, U, IWh, Fh);
+        prandtl_fix(ph.prf, U, IWd, D);
     }
 }
 

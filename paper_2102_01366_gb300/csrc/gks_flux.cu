@@ -53,7 +53,7 @@ __device__ __forceinline__ void pair_barrier(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + (g >> 5)), "r"(64) : "memory");
 }
 
-template <typename T, int NR, int MINB>
+template <typename T, int NR, int MINB, bool PRF>
 __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
                                                      const T* __restrict__ Wavg,
                                                      const T* __restrict__ poly,
@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         axpy5(T(1), mw0, W0);
         axpy5(-tau, mw1, W0);
         axpy5(tau - (tau + dt) * tc.E, mw1, dWt);
+        T mw2[5] = {T(0), T(0), T(0), T(0), T(0)};
         if (ph.viscous) {
-            T mf2[5] = {0}, mw2[5] = {0};
+            T mf2[5] = {0};
             acc_apsi<1, 0, 0>(t, A, S.rho, mf2);
             acc_apsi<0, 0, 0>(t, A, S.rho, mw2);
             axpy5(-tau * tc.k0, mf2, Fh);
@@ -163,6 +164,19 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             axpy5(-tau, mw2, W0);
             axpy5(tau * (T(1) - tc.E), mw2, dWt);
         }
+        if (PRF) {
+            // this side's state integrals for the Pr fix, parked in its own
+            // output slots until phase 3 ends
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                sm.out[side][g][q] = tc.k0 * mw0[q] - (tau * tc.k0 + tc.k1) * mw1[q] - tau * tc.k0 * mw2[q];
+                sm.out[side][g][5 + q] =
+                    tc.dk0 * mw0[q] - (tau * tc.dk0 + tc.dk1) * mw1[q] - tau * tc.dk0 * mw2[q];
+            }
+        }
+    } else if (PRF) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) sm.out[side][g][q] = T(0);
     }
     pair_barrier(g);
 
@@ -184,6 +198,13 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
                 for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
         }
         pair_barrier(g);
+        // Pr fix: the state integrals move to this side's (now unused) slope
+        // slots; the right side adds the equilibrium part below
+        T IW[10];
+        if (PRF) {
+#pragma unroll
+            for (int q = 0; q < 10; ++q) IW[q] = sm.out[side][g][q];
+        }
         if (side == 0) {
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -211,6 +232,13 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 #pragma unroll
                 for (int q = 0; q < 5; ++q) W0[q] = Wc[q];  // tau terms cancel: <(a.u + A) psi> = 0
                 axpy5(-dt, mw1, dWt);
+                if (PRF) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        IW[q] += hd * Wc[q] - T(0.5) * hd * hd * mw1[q];
+                        IW[5 + q] += -T(0.25) * dt * dt * mw1[q];
+                    }
+                }
             } else {
                 axpy5(tc.q1, mf0, Fh);
                 axpy5(tc.q3, mf2, Fh);
@@ -218,7 +246,18 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
                 axpy5(tc.dq3, mf2, D);
                 const T C2 = (dt + tau) * tc.E - tau, C3 = dt - tau + tau * tc.E;
                 axpy5(C2 - C3, mw1, dWt);
+                if (PRF) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        IW[q] += tc.q1 * Wc[q] + (tc.q2 - tc.q3) * mw1[q];
+                        IW[5 + q] += tc.dq1 * Wc[q] + (tc.dq2 - tc.dq3) * mw1[q];
+                    }
+                }
             }
+        }
+        if (PRF) {
+#pragma unroll
+            for (int q = 0; q < 10; ++q) sm.dwc[side][g][q] = IW[q];
         }
     }
 #pragma unroll
@@ -238,6 +277,18 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         for (int q = 0; q < 5; ++q) {
             Fs[q] = sm.out[0][g][q] + sm.out[1][g][q];
             Ds[q] = sm.out[0][g][5 + q] + sm.out[1][g][5 + q];
+        }
+        if (PRF) {
+            T IWh[5], IWd[5], Wc[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                IWh[q] = sm.dwc[0][g][q] + sm.dwc[1][g][q];
+                IWd[q] = sm.dwc[0][g][5 + q] + sm.dwc[1][g][5 + q];
+                Wc[q] = sm.w0[0][g][q] + sm.w0[1][g][q];
+            }
+            const T U[3] = {Wc[1] / Wc[0], Wc[2] / Wc[0], Wc[3] / Wc[0]};
+            prandtl_fix(ph.prf, U, IWh, Fs);
+            prandtl_fix(ph.prf, U, IWd, Ds);
         }
         to_global(Rm, Fs);
         to_global(Rm, Ds);
@@ -396,6 +447,7 @@ static Phys<T> make_phys(const HostPhys& p) {
     ph.eps_w = (T)p.eps_weno;
     ph.viscous = p.viscous;
     ph.smooth = p.smooth;
+    ph.prf = (T)p.prf;
     return ph;
 }
 
@@ -410,17 +462,19 @@ cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, 
     if constexpr (sizeof(T) == 4) {
         // FP32: the two sides of each Gauss point in separate warps; variant
         // 1 trades registers for occupancy (3 blocks per SM), variant 0 keeps
-        // 2 blocks per SM without spills
+        // 2 blocks per SM without spills; the Pr fix has its own instances
+        const bool prf = p.prf != 0.0;
+        auto go = [&](auto kernel) { kernel<<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override); };
         if (variant == 1) {
             if (stage == 1)
-                k_flux<T, 40, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+                prf ? go(k_flux<T, 40, 3, true>) : go(k_flux<T, 40, 3, false>);
             else
-                k_flux<T, 20, 3><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+                prf ? go(k_flux<T, 20, 3, true>) : go(k_flux<T, 20, 3, false>);
         } else {
             if (stage == 1)
-                k_flux<T, 40, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+                prf ? go(k_flux<T, 40, 2, true>) : go(k_flux<T, 40, 2, false>);
             else
-                k_flux<T, 20, 2><<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override);
+                prf ? go(k_flux<T, 20, 2, true>) : go(k_flux<T, 20, 2, false>);
         }
     } else {
         if (stage == 1)

@@ -149,7 +149,8 @@ def test_unsupported_configurations_are_rejected(cuda):
     mesh, W, dW, _ = _case()
     g = gks.Mesh(mesh)
     args = [torch.tensor(x, device="cuda") for x in (W, dW, np.zeros_like(W), np.zeros_like(dW))]
-    for kw in (dict(weno=1, order=2, precision=0), dict(weno=0, precision=1)):
+    for kw in (dict(weno=1, order=2, precision=0), dict(weno=0, precision=1),
+               dict(weno=0, precision=0, viscous=1, mu=0.01, prandtl=0.72)):
         s = gks.State(g, gks.params(cfl=0.5, **kw))
         with pytest.raises(gks.GksError) as e:
             s.adjoint_step(*args, 1e-3)

@@ -93,7 +93,7 @@ def _time_integrals(f, d, tau_n):
     return tot
 
 
-def brute_force(Wl, dWl, Wr, dWr, dt, viscous=False, mu=0.0, tau_eps=0.01, tau_c=1.0):
+def brute_force(Wl, dWl, Wr, dWr, dt, viscous=False, mu=0.0, tau_eps=0.01, tau_c=1.0, prandtl=1.0):
     rl, Ul, pl, laml = _prim(Wl)
     rr, Ur, pr, lamr = _prim(Wr)
     al, Al = _slopes(Wl, dWl)
@@ -119,6 +119,11 @@ def brute_force(Wl, dWl, Wr, dWr, dt, viscous=False, mu=0.0, tau_eps=0.01, tau_c
         out = {}
         for name, extra in (("F", nodes[0]), ("W", np.ones_like(nodes[0]))):
             out[name] = ((P * w) @ extra, (P * w) @ (au * extra), (P * w) @ (Av * extra))
+        # heat flux density (u1 - U1) (|u - U|^2 + xi^2) / 2 about the
+        # interface equilibrium velocity (a scalar moment)
+        c = [nodes[i] - Uc[i] for i in range(3)]
+        qv = c[0] * 0.5 * (c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + nodes[3])
+        out["Q"] = (w @ qv, w @ (au * qv), w @ (Av * qv))
         return out
 
     mc = pieces(nc_, wc, Pc, ac, Ac)
@@ -137,6 +142,12 @@ def brute_force(Wl, dWl, Wr, dWr, dt, viscous=False, mu=0.0, tau_eps=0.01, tau_c
 
     Fh = _time_integrals(lambda t: f_moments("F", t), 0.5 * dt, tau_n)
     F = _time_integrals(lambda t: f_moments("F", t), dt, tau_n)
+    if viscous and prandtl != 1.0:
+        # the energy flux gains (1/Pr - 1) times the time integral of the heat flux
+        Fh = Fh.copy()
+        F = F.copy()
+        Fh[4] += (1.0 / prandtl - 1.0) * _time_integrals(lambda t: f_moments("Q", t), 0.5 * dt, tau_n)
+        F[4] += (1.0 / prandtl - 1.0) * _time_integrals(lambda t: f_moments("Q", t), dt, tau_n)
     return Fh, F, f_moments("W", 0.0), f_moments("W", dt)
 
 
@@ -163,6 +174,57 @@ def test_flux_matches_brute_force_quadrature(oracle_mod, seed, viscous):
     for g, r, name in zip(got, ref, ("Fh", "F", "W0", "Wdt")):
         scale = np.abs(r).max()
         assert np.abs(g - r).max() < 1e-11 * scale, (name, g, r)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_prandtl_fix_matches_brute_force_quadrature(oracle_mod, seed):
+    """Pr = 0.72: the energy flux gains (1/Pr - 1) times the time integral of
+    the heat flux of the interface distribution, here integrated directly
+    from its definition over velocity space and time."""
+    rng = np.random.default_rng(seed)
+    Wl, dWl = _random_state(rng)
+    Wr, dWr = _random_state(rng)
+    dt, mu = 0.02, 2e-3
+    got = oracle_mod.gp_flux(oracle_mod.params(viscous=1, mu=mu, prandtl=0.72), Wl, dWl, Wr, dWr, dt)
+    base = oracle_mod.gp_flux(oracle_mod.params(viscous=1, mu=mu), Wl, dWl, Wr, dWr, dt)
+    ref = brute_force(Wl, dWl, Wr, dWr, dt, viscous=True, mu=mu, prandtl=0.72)
+    for g, r, name in zip(got, ref, ("Fh", "F", "W0", "Wdt")):
+        scale = np.abs(r).max()
+        assert np.abs(g - r).max() < 1e-11 * scale, (name, g, r)
+    # only the energy flux moves, and by a visible amount
+    for i in (0, 1):
+        np.testing.assert_array_equal(got[i][:4], base[i][:4])
+        assert abs(got[i][4] - base[i][4]) > 1e-6 * abs(base[i][4])
+    np.testing.assert_array_equal(got[2], base[2])
+    np.testing.assert_array_equal(got[3], base[3])
+
+
+@pytest.mark.parametrize("U", [(0.0, 0.0, 0.0), (0.4, -0.3, 0.2)])
+def test_prandtl_fix_scales_the_fourier_heat_flux(oracle_mod, U):
+    """Gas with uniform pressure and velocity and a linear temperature
+    T = p / rho = T0 + s x1 (R = 1), smooth solver: the energy flux over
+    [0, d] is the convected energy plus the Fourier heat flux
+    -kappa s d with kappa = mu c_p / Pr, c_p = gamma / (gamma - 1) (the BGK
+    model alone gives Pr = 1).  Holds for a moving gas too (the correction
+    measures the heat flux about the gas velocity)."""
+    p0, T0, s_, mu, dt = 1.0, 1.2, 0.3, 2e-3, 0.01
+    U = np.array(U)
+    rho = p0 / T0
+    drho = -p0 * s_ / T0 ** 2
+    W = np.array([rho, rho * U[0], rho * U[1], rho * U[2], p0 / (GAMMA - 1) + 0.5 * rho * U @ U])
+    dW = np.zeros((3, 5))
+    dW[0] = [drho, drho * U[0], drho * U[1], drho * U[2], 0.5 * drho * U @ U]
+    cp = GAMMA / (GAMMA - 1.0)
+    F = {}
+    for pr in (1.0, 0.72):
+        F[pr] = oracle_mod.gp_flux(oracle_mod.params(viscous=1, mu=mu, smooth_flux=1, prandtl=pr),
+                                   W, dW, W, dW, dt)
+    for i, d in ((0, 0.5 * dt), (1, dt)):
+        if not U.any():
+            np.testing.assert_allclose(F[1.0][i][4], -mu * cp * s_ * d, rtol=1e-12)
+            np.testing.assert_allclose(F[0.72][i][4], -mu * cp * s_ * d / 0.72, rtol=1e-12)
+        np.testing.assert_allclose(F[0.72][i][4] - F[1.0][i][4], (1 / 0.72 - 1) * (-mu * cp * s_ * d),
+                                   rtol=1e-10)
 
 
 def test_uniform_flow_gives_euler_flux(oracle_mod):
