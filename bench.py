@@ -225,6 +225,77 @@ def adjoint_leg(torch, gks, args):
             "timing": "wall clock of the library calls, %d each after warm-up (forward: init + step)" % reps}
 
 
+def adjoint_chain_leg(torch, gks, args):
+    """Gradients through 200 frozen-dt steps of the isentropic vortex on the
+    periodic 64^3 x 6 box (1,572,864 cells, linear weights), checkpointed
+    every 20 steps, of J = total kinetic energy at the end: with respect to
+    the free-stream Mach number (chain rule through the input generator's
+    central difference, exact for its quadratic dependence) and along a
+    random direction of the initial density field (velocity and pressure
+    held).  The adjoint runs with the FP32 primal (FP64 checkpoints, FP64
+    reverse sweep) and with the FP64 primal; central differences of FP64
+    forward runs check both."""
+    nsteps, every, ma, hm = 200, 20, 0.5, 1e-6
+    case = lambda m: I.isentropic_vortex_case(n=64, mach=m, order=2)
+    mesh, W, dW = case(ma)
+    _, Wp, dWp = case(ma + hm)
+    _, Wm, dWm = case(ma - hm)
+    dW_dma, ddW_dma = (Wp - Wm) / (2 * hm), (dWp - dWm) / (2 * hm)
+    g = gks.Mesh(mesh)
+    vol = torch.tensor(g.geometry()["vol"], device="cuda")
+    prm = gks.params(weno=0, cfl=0.5, precision=0)
+    s = gks.State(g, prm)
+    s.init(W, dW)
+    dt = s.timestep()
+
+    def energy(Wc):
+        return (vol * (Wc[1:4] ** 2).sum(0) / (2.0 * Wc[0])).sum()
+
+    def forward(W0, dW0):
+        s.init(W0, dW0)
+        s.step(nsteps, dt, 0.0)
+        s.sync()
+        return float(energy(s.get()[0]))
+
+    rng = np.random.Generator(np.random.PCG64(17))
+    d = rng.standard_normal(g.nc)  # O(1): a 1e-6 step then moves J well above its rounding
+    U = W[1:4] / W[0]
+    gm1 = 0.4  # gamma - 1 of the vortex case
+    pres = gm1 * (W[4] - 0.5 * (W[1:4] ** 2).sum(0) / W[0])
+
+    def with_rho(rho):
+        return np.concatenate([rho[None], rho[None] * U, (pres / gm1 + 0.5 * rho * (U ** 2).sum(0))[None]])
+    dW_drho = with_rho(W[0] + 1.0 * d) - with_rho(W[0])  # linear in rho: the directional change
+    out = {"workload": "isentropic vortex, periodic 64^3 hexes x 6 tets = %d cells, linear weights, "
+                       "%d steps of dt %.4g frozen, checkpoint every %d" % (g.nc, nsteps, dt, every),
+           "loss": "total kinetic energy at the end"}
+    t0 = time.perf_counter()
+    fd_ma = (forward(Wp, dWp) - forward(Wm, dWm)) / (2 * hm)
+    hr = 1e-6
+    fd_rho = (forward(W + hr * dW_drho, dW) - forward(W - hr * dW_drho, dW)) / (2 * hr)
+    out["fd_seconds"] = time.perf_counter() - t0
+    out["fd"] = {"dJ_dMa": fd_ma, "dJ_drho_along_d": fd_rho}
+    for name, prec in (("fp32_primal", 1), ("fp64_primal", 0)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, lW, ldW = gks.checkpointed_gradient(g, prm, W, dW, nsteps, dt, energy, checkpoint_every=every,
+                                               primal_precision=prec)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        lW, ldW = lW.cpu().numpy(), ldW.cpu().numpy()
+        ad_ma = float((lW * dW_dma).sum() + (ldW * ddW_dma).sum())
+        ad_rho = float((lW * dW_drho).sum())
+        out[name] = {"J": J, "dJ_dMa": ad_ma, "dJ_drho_along_d": ad_rho,
+                     "rel_err_dMa": abs(ad_ma - fd_ma) / abs(fd_ma),
+                     "rel_err_drho": abs(ad_rho - fd_rho) / abs(fd_rho), "seconds": el}
+    # cost against the primal alone
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    forward(W, dW)
+    out["fp64_forward_seconds"] = time.perf_counter() - t0
+    return out
+
+
 def sphere_leg(torch, gks, args, flush):
     """Viscous flow past a sphere, Re 100 on the diameter, Ma 0.2, Pr 0.72: the O-type
     shell of 64 radial (ratio 1.08) x 96 polar x 192 azimuthal hexes x 6
@@ -312,6 +383,8 @@ def main():
                     help="independent cases of the batched leg (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     ap.add_argument("--no-sphere", action="store_true", help="skip the 7M-cell viscous sphere leg")
+    ap.add_argument("--adjoint-chain", action="store_true",
+                    help="also run the 200-step checkpointed gradient of the 64^3 vortex (minutes)")
     ap.add_argument("--profile-adjoint", action="store_true",
                     help="only two adjoint steps on the periodic 16^3 x 6 density wave (for profilers)")
     args = ap.parse_args()
@@ -454,6 +527,8 @@ def main():
         line["adjoint"] = adjoint_leg(torch, gks, args)
     if not args.no_sphere:
         line["sphere"] = sphere_leg(torch, gks, args, flush)
+    if args.adjoint_chain:
+        line["adjoint_chain"] = adjoint_chain_leg(torch, gks, args)
     if rank == 0 and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
