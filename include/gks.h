@@ -321,9 +321,10 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * (order 3) with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
  * meshes, periodic or with open, slip-wall or non-slip-wall boundary faces
- * (not fixed-state ones); GKS_E_UNSUPPORTED otherwise, and also when a
- * cell of either stage falls back to a constant reconstruction (the
- * positivity branch, whose derivative this does not build).  All arrays are
+ * (not fixed-state ones), Pr = 1; GKS_E_UNSUPPORTED otherwise.  A cell that
+ * falls back to its average (the positivity check of Sec. 4.3) passes the
+ * adjoint of its constant to its own average only; the fallback decision is
+ * held fixed (piecewise derivative).  All arrays are
  * device FP64; d_scratch (gks_adjoint_workspace_bytes) is caller-allocated
  * device memory.  On return the state is initialised at (d_W, d_dW) with its
  * time reset.  Synchronises. */

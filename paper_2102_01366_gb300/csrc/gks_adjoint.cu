@@ -278,16 +278,34 @@ __global__ void k_adj_gather_poly(DevMesh<double> m, const double* __restrict__ 
     for (int j = 0; j < 50; ++j) lp[c * 50 + j] = acc[j];
 }
 
+// A cell whose reconstruction fell back to its average (the positivity
+// check, Sec. 4.3: R = P0, zero slopes) passes only the adjoint of its
+// constant on to its own average; nothing reaches the stencil data or the
+// neighbours' slopes.  The fallback decision itself is piecewise constant.
+__device__ __forceinline__ void fallback_back(const double* __restrict__ lp, int64_t c, int q,
+                                              double* __restrict__ ld, double* __restrict__ lbn,
+                                              double* __restrict__ own) {
+    double* o = ld + (c * 5 + q) * 16;
+    for (int j = 0; j < 16; ++j) o[j] = 0.0;
+    if (lbn)
+        for (int j = 0; j < 12; ++j) lbn[(c * 5 + q) * 12 + j] = 0.0;
+    own[c * 5 + q] = lp[c * 50 + q * 10];
+}
+
 // Transpose of the linear-weight reconstruction of one cell (Sec. 4.1):
 // R = a = M2 d, c0 = Q0 - sum_k R_k M_k (second moments), with
 // d = [Q_nb - Q0 (4); grad Q_nb (12)].  Writes ld[c][q][16] = M2^T lambda_a
 // and own[c][q] = lambda_c0 - sum over existing neighbours of ld[c][q][f].
-__global__ void k_adj_recon_local(DevMesh<double> m, const double* __restrict__ lp, double* __restrict__ ld,
-                                  double* __restrict__ own) {
+__global__ void k_adj_recon_local(DevMesh<double> m, const double* __restrict__ lp, const int32_t* __restrict__ fb,
+                                  double* __restrict__ ld, double* __restrict__ own) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m.nc * 5) return;
     const int64_t c = idx / 5;
     const int q = (int)(idx - c * 5);
+    if (fb[c]) {
+        fallback_back(lp, c, q, ld, nullptr, own);
+        return;
+    }
     const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
     auto T_ = [&](int row) { return tile[(int64_t)row * CELLS_PER_BLOCK]; };
     const double* l = lp + c * 50 + q * 10;
@@ -333,12 +351,16 @@ __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.
 // the neighbours' slopes as this cell uses them) and own[c][q] (of Q0 through
 // c0 and the differences d[0:4]).
 __global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __restrict__ X,
-                                 const double* __restrict__ lp, double* __restrict__ ld,
-                                 double* __restrict__ lbn, double* __restrict__ own) {
+                                 const double* __restrict__ lp, const int32_t* __restrict__ fb,
+                                 double* __restrict__ ld, double* __restrict__ lbn, double* __restrict__ own) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m.nc * 5) return;
     const int64_t c = idx / 5, nc = m.nc;
     const int q = (int)(idx - c * 5);
+    if (fb[c]) {
+        fallback_back(lp, c, q, ld, lbn, own);
+        return;
+    }
     const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
     auto T_ = [&](int row) { return tile[(int64_t)row * CELLS_PER_BLOCK]; };
     int nb[4];
@@ -564,23 +586,6 @@ __global__ void k_adj_recon_gather(DevMesh<double> m, const int8_t* __restrict__
     for (int l = 0; l < 3; ++l) x[5 + 3 * q + l] = lg[l];
 }
 
-// or of the positivity-fallback flags of both stages into *any
-__global__ void k_adj_any(const int32_t* __restrict__ flags, int64_t n, int32_t* __restrict__ any) {
-    int32_t v = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v |= flags[i];
-    v = __reduce_or_sync(0xffffffffu, v);
-    if (v && (threadIdx.x & 31) == 0) atomicOr(any, v);
-}
-
-cudaError_t adjoint_any_fallback(const int32_t* flags, int64_t n, int32_t* any, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(any, 0, 4, s);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-    k_adj_any<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(flags, n, any);
-    return cudaGetLastError();
-}
-
 // lambda W^n = lambda W^{n+1} (the update's pass-through) + lambda W* (the
 // stage-1 pass-through) + the stage-1 reconstruction's; lambda grad W^n from
 // the stage-1 reconstruction alone
@@ -615,14 +620,15 @@ static Phys<double> phys64(const HostPhys& p) {
 // transpose of one stage's reconstruction: lp (per-cell coefficient
 // adjoints) into lX, from the stage's working state X
 static void recon_back(const DevMesh<double>& m, const HostPhys& p, const AdjBuffers& b, const double* X,
+                       const int32_t* fb,
                        double* lX, cudaStream_t s) {
     const int B = 128;
     if (p.weno) {
-        k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, b.ld, b.lbn, b.own);
+        k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, fb, b.ld, b.lbn, b.own);
         k_adj_slopes<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.lbn, b.lds);
         k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.lds, b.own, b.lwo, lX);
     } else {
-        k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, b.ld, b.own);
+        k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, fb, b.ld, b.own);
         k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, nullptr, b.own, b.lwo, lX);
     }
 }
@@ -655,12 +661,12 @@ cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double 
     // stage 2
     k_adj_src2<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.src);
     flux_back<20>(m, ph, b, b.poly2, X2, dt, s);
-    recon_back(m, p, b, X2, b.lXs, s);
+    recon_back(m, p, b, X2, b.fallback + m.nc, b.lXs, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 1
     k_adj_src1<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, ldW, b.lXs, b.src);
     flux_back<40>(m, ph, b, b.poly1, X1, dt, s);
-    recon_back(m, p, b, X1, b.lX1, s);
+    recon_back(m, p, b, X1, b.fallback, b.lX1, s);
     k_adj_final<<<grid_of(m.nc, B), B, 0, s>>>(m, lW, b.lXs, b.lX1, oW, odW);
     return cudaGetLastError();
 }

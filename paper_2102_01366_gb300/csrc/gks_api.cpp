@@ -892,7 +892,7 @@ AdjLayout adj_layout(int64_t nc, int64_t nf) {
     L.lds = L.add(8 * 20 * nc);
     L.lwo = L.add(8 * 5 * nf);
     L.rev = L.add(4 * nc);
-    L.fallback = L.add(4 * 2 * nc + 4);  // flags of both stages, then their or
+    L.fallback = L.add(4 * 2 * nc);  // positivity-fallback flags of both stages
     return L;
 }
 }  // namespace
@@ -957,14 +957,6 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     GKS_CHECK_CUDA(Launch<double>::update1(m, st, s->stream));
     GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.Xs, nullptr, nullptr, st.poly, fb + nc, nullptr, st.err,
                                          s->stream));
-    int32_t any = 0;
-    GKS_CHECK_CUDA(adjoint_any_fallback(fb, 2 * nc, fb + 2 * nc, s->stream));
-    GKS_CHECK_CUDA(cudaMemcpyAsync(&any, fb + 2 * nc, 4, cudaMemcpyDeviceToHost, s->stream));
-    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    if (any) {
-        set_error("gks_adjoint_step: a cell falls back to a constant reconstruction (positivity branch)");
-        return GKS_E_UNSUPPORTED;
-    }
     AdjBuffers b;
     b.poly1 = poly1;
     b.poly2 = st.poly;

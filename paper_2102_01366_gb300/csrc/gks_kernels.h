@@ -153,8 +153,6 @@ struct AdjBuffers {
     const int8_t* rev;
     int32_t* fallback;
 };
-// *any = the or of flags[0:n] (cleared first)
-cudaError_t adjoint_any_fallback(const int32_t* flags, int64_t n, int32_t* any, cudaStream_t s);
 // lambda (W^n, grad W^n) from lambda (W^{n+1}, grad W^{n+1}) for one step
 // with the frozen time step dt (public [component][cell] FP64 layouts)
 cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,
