@@ -317,8 +317,8 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * transpose of the step's Jacobian at (d_W, d_dW) applied to (lamW, lamdW).
  * It first recomputes the step's two reconstructions from (d_W, d_dW), so a
  * run of N steps back-propagates from the N saved (or recomputed) states.
- * Supported: FP64 states (precision 0) with the third-order reconstruction
- * (order 3) with linear or WENO weights (the weights are differentiated,
+ * Supported: FP64 states (precision 0) with the third- or second-order
+ * reconstruction with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
  * meshes, periodic or with open, slip-wall or non-slip-wall boundary faces
  * (not fixed-state ones), Pr = 1; GKS_E_UNSUPPORTED otherwise.  A cell that

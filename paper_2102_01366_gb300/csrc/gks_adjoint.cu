@@ -342,6 +342,73 @@ __device__ __forceinline__ void adj_p1_slope(const DevMesh<double>& m, const dou
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
+// beta_0 of the two-step reconstruction (Eq. p0-non-linear-weight): the
+// neighbours' P1 slopes b_j, beta_0j = |Omega|^{2/3} |b_j|^2, weights
+// w1j = 1 + s1 / (eps + beta_0j) with s1 the 4/3 power of the mean pairwise
+// |beta_0j - beta_0k|, beta_0 = sum w1j beta_0j / sum w1j; kept for the reverse.
+struct Beta0 {
+    double bj[4][3], b0j[4], w1j[4];
+    double s1, ws, accb, sum, beta;
+    int slot[4], nn, npair;
+};
+
+__device__ __forceinline__ void beta0_forward(const DevMesh<double>& m, const double* __restrict__ X,
+                                              const int* nb, int q, double v23, double eps, Beta0& B) {
+    B.nn = 0;
+    for (int f = 0; f < 4; ++f) {
+        if (nb[f] < 0) continue;
+        adj_p1_slope(m, X, nb[f], q, B.bj[B.nn]);
+        const double* bj = B.bj[B.nn];
+        B.b0j[B.nn] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
+        B.slot[B.nn++] = f;
+    }
+    B.beta = B.s1 = B.ws = B.accb = B.sum = 0.0;
+    B.npair = 0;
+    if (B.nn > 0) {
+        for (int j = 0; j < B.nn; ++j)
+            for (int k = 0; k < j; ++k) {
+                B.sum += fabs(B.b0j[j] - B.b0j[k]);
+                ++B.npair;
+            }
+        B.s1 = B.npair ? pow43(B.sum / B.npair) : 0.0;
+        for (int j = 0; j < B.nn; ++j) {
+            B.w1j[j] = 1.0 + B.s1 / (eps + B.b0j[j]);
+            B.ws += B.w1j[j];
+            B.accb += B.w1j[j] * B.b0j[j];
+        }
+        B.beta = B.accb / B.ws;
+    }
+}
+
+// adjoint of beta_0 into the adjoints of the neighbours' slopes lbj[j][3]
+__device__ __forceinline__ void beta0_backward(const Beta0& B, double lbeta0, double v23, double eps,
+                                               double (*lbj)[3]) {
+    for (int j = 0; j < 4; ++j) lbj[j][0] = lbj[j][1] = lbj[j][2] = 0.0;
+    if (B.nn == 0) return;
+    const double lacc = lbeta0 / B.ws, lws = -lbeta0 * B.accb / (B.ws * B.ws);
+    double lb0[4], ls1 = 0.0;
+    for (int j = 0; j < B.nn; ++j) {
+        const double lwj = lacc * B.b0j[j] + lws;
+        lb0[j] = lacc * B.w1j[j] - lwj * B.s1 / ((eps + B.b0j[j]) * (eps + B.b0j[j]));
+        ls1 += lwj / (eps + B.b0j[j]);
+    }
+    if (B.npair) {
+        const double lsum = ls1 * (4.0 / 3.0) * cbrt(B.sum / B.npair) / B.npair;
+        for (int j = 0; j < B.nn; ++j)
+            for (int k = 0; k < B.nn; ++k)
+                if (k != j) lb0[j] += lsum * sgn(B.b0j[j] - B.b0j[k]);
+    }
+    for (int j = 0; j < B.nn; ++j)
+        for (int i = 0; i < 3; ++i) lbj[j][i] = 2.0 * v23 * B.bj[j][i] * lb0[j];
+}
+
+// the neighbours' slope adjoints into lbn[f][3] (zero for missing neighbours)
+__device__ __forceinline__ void store_lbn(const Beta0& B, const double (*lbj)[3], double* __restrict__ ob) {
+    for (int j = 0; j < 12; ++j) ob[j] = 0.0;
+    for (int j = 0; j < B.nn; ++j)
+        for (int i = 0; i < 3; ++i) ob[3 * B.slot[j] + i] = lbj[j][i];
+}
+
 // Transpose of the third-order multi-resolution WENO reconstruction of one
 // cell and component (Sec. 4.2, 4.3): R = c2 a + cb b with the nonlinear
 // weights of beta_0 (two-step, from the neighbours' P1 slopes), beta_1, beta_2;
@@ -390,30 +457,9 @@ __global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __
     const double g22 = 100.0 / 111.0, g12 = 10.0 / 111.0, g02 = 1.0 / 111.0, g11 = 10.0 / 11.0;
     // forward: beta_1, beta_0 (two-step), beta_2, sigma, weights
     const double beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-    double bj[4][3], b0j[4];
-    int slot[4], nn = 0;
-    for (int f = 0; f < 4; ++f) {
-        if (nb[f] < 0) continue;
-        adj_p1_slope(m, X, nb[f], q, bj[nn]);
-        b0j[nn] = v23 * (bj[nn][0] * bj[nn][0] + bj[nn][1] * bj[nn][1] + bj[nn][2] * bj[nn][2]);
-        slot[nn++] = f;
-    }
-    double beta0 = 0.0, s1 = 0.0, ws = 0.0, accb = 0.0, sum = 0.0, w1j[4];
-    int npair = 0;
-    if (nn > 0) {
-        for (int j = 0; j < nn; ++j)
-            for (int k = 0; k < j; ++k) {
-                sum += fabs(b0j[j] - b0j[k]);
-                ++npair;
-            }
-        s1 = npair ? pow43(sum / npair) : 0.0;
-        for (int j = 0; j < nn; ++j) {
-            w1j[j] = 1.0 + s1 / (eps + b0j[j]);
-            ws += w1j[j];
-            accb += w1j[j] * b0j[j];
-        }
-        beta0 = accb / ws;
-    }
+    Beta0 B0;
+    beta0_forward(m, X, nb, q, v23, eps, B0);
+    const double beta0 = B0.beta;
     const double H[3][3] = {{2.0 * a[3], a[4], a[5]}, {a[4], 2.0 * a[6], a[7]}, {a[5], a[7], 2.0 * a[8]}};
     const double MM[3][3] = {{Mm[0], Mm[1], Mm[2]}, {Mm[1], Mm[3], Mm[4]}, {Mm[2], Mm[4], Mm[5]}};
     double first = 0.0, MH[3][3];
@@ -490,26 +536,8 @@ __global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __
     la[8] += 2.0 * lH[2][2];
     // beta_1 = v23 |b|^2
     for (int i = 0; i < 3; ++i) lb[i] += 2.0 * v23 * b[i] * lbet[1];
-    // beta_0 = sum w1j b0j / sum w1j, w1j = 1 + s1 / (eps + b0j), s1 = (sum / npair)^{4/3}
     double lbj[4][3];
-    for (int j = 0; j < 4; ++j) lbj[j][0] = lbj[j][1] = lbj[j][2] = 0.0;
-    if (nn > 0) {
-        const double lacc = lbet[0] / ws, lws = -lbet[0] * accb / (ws * ws);
-        double lb0[4], ls1 = 0.0;
-        for (int j = 0; j < nn; ++j) {
-            const double lwj = lacc * b0j[j] + lws;
-            lb0[j] = lacc * w1j[j] - lwj * s1 / ((eps + b0j[j]) * (eps + b0j[j]));
-            ls1 += lwj / (eps + b0j[j]);
-        }
-        if (npair) {
-            const double lsum = ls1 * (4.0 / 3.0) * cbrt(sum / npair) / npair;
-            for (int j = 0; j < nn; ++j)
-                for (int k = 0; k < nn; ++k)
-                    if (k != j) lb0[j] += lsum * sgn(b0j[j] - b0j[k]);
-        }
-        for (int j = 0; j < nn; ++j)
-            for (int i = 0; i < 3; ++i) lbj[j][i] = 2.0 * v23 * bj[j][i] * lb0[j];
-    }
+    beta0_backward(B0, lbet[0], v23, eps, lbj);
     // a = M2 d, b = M1 d[0:4]
     double* o = ld + (c * 5 + q) * 16;
     double s = 0.0;
@@ -522,10 +550,113 @@ __global__ void k_adj_recon_weno(DevMesh<double> m, double eps, const double* __
         if (j < 4 && nb[j] >= 0) s += acc;
     }
     own[c * 5 + q] = lc0 - s;
-    double* ob = lbn + (c * 5 + q) * 12;
-    for (int j = 0; j < 12; ++j) ob[j] = 0.0;
-    for (int j = 0; j < nn; ++j)
-        for (int i = 0; i < 3; ++i) ob[3 * slot[j] + i] = lbj[j][i];
+    store_lbn(B0, lbj, lbn + (c * 5 + q) * 12);
+}
+
+// Transpose of the second-order WENO reconstruction R^2nd (Eq.
+// final_weno_expression-2nd) of one cell and component: R = Q0 + cb b.x with
+// cb = (w1 / (w0 + w1)) / g11, w0, w1 from beta_0 (two-step) and beta_1,
+// sigma = |beta_1 - beta_0|^{4/3}.  Same outputs as k_adj_recon_weno.
+__global__ void k_adj_recon_weno2(DevMesh<double> m, double eps, const double* __restrict__ X,
+                                  const double* __restrict__ lp, const int32_t* __restrict__ fb,
+                                  double* __restrict__ ld, double* __restrict__ lbn, double* __restrict__ own) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t c = idx / 5, nc = m.nc;
+    const int q = (int)(idx - c * 5);
+    if (fb[c]) {
+        fallback_back(lp, c, q, ld, lbn, own);
+        return;
+    }
+    const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
+    auto T_ = [&](int row) { return tile[(int64_t)row * CELLS_PER_BLOCK]; };
+    int nb[4];
+    for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
+    const double Q0 = X[c * XS + q];
+    double d[4];
+    for (int f = 0; f < 4; ++f) d[f] = nb[f] >= 0 ? X[(int64_t)nb[f] * XS + q] - Q0 : 0.0;
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int f = 0; f < 4; ++f) {
+        if (nb[f] < 0) continue;
+        for (int i = 0; i < 3; ++i) b[i] += T_(TILE_M1 + i * 4 + f) * d[f];
+    }
+    const double v23 = T_(TILE_V23);
+    const double g01 = 1.0 / 11.0, g11 = 10.0 / 11.0;
+    const double beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    Beta0 B0;
+    beta0_forward(m, X, nb, q, v23, eps, B0);
+    const double beta0 = B0.beta;
+    const double z = fabs(beta1 - beta0);
+    const double sigma = pow43(z);
+    const double bet[2] = {beta0, beta1}, gam[2] = {g01, g11};
+    double r[2], w[2];
+    for (int k = 0; k < 2; ++k) {
+        r[k] = sigma / (eps + bet[k]);
+        w[k] = gam[k] * (1.0 + r[k] * r[k]);
+    }
+    const double wsum = w[0] + w[1];
+    const double cb = w[1] / (wsum * g11);
+
+    // reverse: only the constant and the linear coefficients of R are nonzero
+    const double* l = lp + c * 50 + q * 10;
+    const double lc0 = l[0];
+    double lb[3], lcb = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        lb[i] = cb * l[1 + i];
+        lcb += l[1 + i] * b[i];
+    }
+    double lw[2];
+    const double lwsum = -lcb * w[1] / (wsum * wsum * g11);
+    lw[0] = lwsum;
+    lw[1] = lwsum + lcb / (wsum * g11);
+    double lbet[2] = {0.0, 0.0}, lsig = 0.0;
+    for (int k = 0; k < 2; ++k) {
+        const double lr = lw[k] * gam[k] * 2.0 * r[k];
+        lsig += lr / (eps + bet[k]);
+        lbet[k] += -lr * sigma / ((eps + bet[k]) * (eps + bet[k]));
+    }
+    const double lz = lsig * (4.0 / 3.0) * cbrt(z);
+    const double s10 = sgn(beta1 - beta0);
+    lbet[1] += lz * s10;
+    lbet[0] -= lz * s10;
+    for (int i = 0; i < 3; ++i) lb[i] += 2.0 * v23 * b[i] * lbet[1];
+    double lbj[4][3];
+    beta0_backward(B0, lbet[0], v23, eps, lbj);
+    double* o = ld + (c * 5 + q) * 16;
+    double s = 0.0;
+    for (int j = 0; j < 16; ++j) o[j] = 0.0;
+    for (int j = 0; j < 4; ++j) {
+        if (nb[j] < 0) continue;
+        for (int i = 0; i < 3; ++i) o[j] += T_(TILE_M1 + i * 4 + j) * lb[i];
+        s += o[j];
+    }
+    own[c * 5 + q] = lc0 - s;
+    store_lbn(B0, lbj, lbn + (c * 5 + q) * 12);
+}
+
+// Transpose of the second-order reconstruction with linear weights: R = P1,
+// the step-1 slope b = M1 d[0:4].
+__global__ void k_adj_recon_p1(DevMesh<double> m, const double* __restrict__ lp, const int32_t* __restrict__ fb,
+                               double* __restrict__ ld, double* __restrict__ own) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.nc * 5) return;
+    const int64_t c = idx / 5;
+    const int q = (int)(idx - c * 5);
+    if (fb[c]) {
+        fallback_back(lp, c, q, ld, nullptr, own);
+        return;
+    }
+    const double* tile = m.tile + (c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK;
+    const double* l = lp + c * 50 + q * 10;
+    double* o = ld + (c * 5 + q) * 16;
+    double s = 0.0;
+    for (int j = 0; j < 16; ++j) o[j] = 0.0;
+    for (int j = 0; j < 4; ++j) {
+        if (m.nbr[j * m.nc + c] < 0) continue;
+        for (int i = 0; i < 3; ++i) o[j] += tile[(int64_t)(TILE_M1 + i * 4 + j) * CELLS_PER_BLOCK] * l[1 + i];
+        s += o[j];
+    }
+    own[c * 5 + q] = l[0] - s;
 }
 
 // Adjoint of the neighbours' P1 slopes, per cell n and component: the slope
@@ -624,11 +755,17 @@ static void recon_back(const DevMesh<double>& m, const HostPhys& p, const AdjBuf
                        double* lX, cudaStream_t s) {
     const int B = 128;
     if (p.weno) {
-        k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, fb, b.ld, b.lbn, b.own);
+        if (p.order == 2)
+            k_adj_recon_weno2<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, fb, b.ld, b.lbn, b.own);
+        else
+            k_adj_recon_weno<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, p.eps_weno, X, b.lp, fb, b.ld, b.lbn, b.own);
         k_adj_slopes<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.lbn, b.lds);
         k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, b.lds, b.own, b.lwo, lX);
     } else {
-        k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, fb, b.ld, b.own);
+        if (p.order == 2)
+            k_adj_recon_p1<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, fb, b.ld, b.own);
+        else
+            k_adj_recon_local<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.lp, fb, b.ld, b.own);
         k_adj_recon_gather<<<grid_of(m.nc * 5, B), B, 0, s>>>(m, b.rev, b.ld, nullptr, b.own, b.lwo, lX);
     }
 }

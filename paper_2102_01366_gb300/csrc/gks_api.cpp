@@ -916,9 +916,9 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    if (s->fp32 || s->params.order != 3 || g.ncase != 1 || has_fixed(g) || s->phys.prf != 0.0) {
-        set_error("gks_adjoint_step: needs an FP64 state with the third-order reconstruction on a "
-                  "single-case mesh without fixed-state boundary faces");
+    if (s->fp32 || g.ncase != 1 || has_fixed(g) || s->phys.prf != 0.0) {
+        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh without fixed-state "
+                  "boundary faces, Pr = 1");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);
