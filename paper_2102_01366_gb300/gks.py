@@ -154,8 +154,9 @@ class Mesh:
             self.n_singular = ns.value
 
     def set_boundary(self, kind):
-        """kind[nc][4] (GKS_BC_OPEN 0, GKS_BC_SLIP_WALL 1) per local face; read
-        on boundary faces only; applies to states created afterwards."""
+        """kind[nc][4] per local face (GKS_BC_OPEN 0, GKS_BC_SLIP_WALL 1,
+        GKS_BC_FIXED 2, GKS_BC_NOSLIP_WALL 3); read on boundary faces only;
+        applies to states created afterwards."""
         kind = np.ascontiguousarray(kind, dtype=np.int8).reshape(self.nc, 4)
         _call("gks_mesh_set_boundary", self._h, _np_ptr(kind))
 
