@@ -142,7 +142,9 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
  *                     state, its average plus its gradient times the offset
  *                     from the centroid, with that gradient.  The fixed state
  *                     is the state given to gks_init_state (or gks_step_host)
- *                     and holds until the next such call; a mesh with fixed
+ *                     and holds until the next such call, unless
+ *                     gks_set_fixed_state has set it: then it holds through
+ *                     every later initialisation; a mesh with fixed
  *                     faces needs 20 more working-precision reals a cell of
  *                     workspace.
  *   GKS_BC_NOSLIP_WALL Sec. 4.4 non-slip adiabatic wall at rest: the ghost
@@ -220,6 +222,15 @@ gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
                             void* d_workspace, size_t workspace_bytes, void* stream,
                             gks_state** out);
 void gks_state_destroy(gks_state* state);
+
+/* Sets the state that fixed boundary faces (GKS_BC_FIXED) hold, from device
+ * arrays W[5][nc], dW[15][nc] (FP64; read at the interior cell of each fixed
+ * face), independently of the evolving state: later gks_init_state and
+ * gks_step_host calls no longer overwrite it.  A run of steps that each
+ * re-initialise the state (gradients over chained steps) then sees the same
+ * boundary as one long run.  GKS_E_ARG on NULL or on a mesh without fixed
+ * faces.  Synchronises. */
+gks_status gks_set_fixed_state(gks_state* state, const double* d_W, const double* d_dW);
 
 /* Sets the cell averages and gradients from device arrays W[5][nc],
  * dW[15][nc] (FP64) and the time to 0. */
@@ -320,8 +331,10 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * Supported: FP64 states (precision 0) with the third- or second-order
  * reconstruction with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
- * meshes, periodic or with open, slip-wall or non-slip-wall boundary faces
- * (not fixed-state ones), Pr = 1; GKS_E_UNSUPPORTED otherwise.  A cell that
+ * meshes, periodic or with open, slip-wall, non-slip-wall or fixed-state
+ * boundary faces (the last only with a fixed state set by
+ * gks_set_fixed_state: it is then a constant of the step), Pr = 1;
+ * GKS_E_UNSUPPORTED otherwise.  A cell that
  * falls back to its average (the positivity check of Sec. 4.3) passes the
  * adjoint of its constant to its own average only; the fallback decision is
  * held fixed (piecewise derivative).  All arrays are

@@ -176,6 +176,14 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
                 to_local(Rm, Wv, g, xs, gs);
                 continue;
             }
+            if (cell == FLR_FIXED) {
+                // fixed: the interior cell's fixed state carried to the point
+                const int si = 1 - side;
+                const double X[3] = {geo[4 + 9 * si + 3 * k], geo[5 + 9 * si + 3 * k], geo[6 + 9 * si + 3 * k]};
+                fixed_ghost(m.fixed + (int64_t)in * XS, X, Wv, g);
+                to_local(Rm, Wv, g, xs, gs);
+                continue;
+            }
             // a real side, or a wall side from the interior cell at the point
             const int src_side = cell >= 0 ? side : 1 - side;
             const int64_t c = cell >= 0 ? cell : in;
@@ -242,6 +250,8 @@ __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx
                 double lW[5], lgg[3][5];
                 to_local_adj(Rm, ls, lg, lW, lgg);
                 for (int q = 0; q < 5; ++q) lw[q] += lW[q];
+            } else if (cell == FLR_FIXED) {
+                // a set fixed state is a constant of the step: nothing flows back
             } else {
                 if (cell == FLR_SLIP_WALL) slip_wall_ghost(ls, lg);
                 if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(ls, lg);

@@ -328,6 +328,7 @@ struct gks_state {
     DevState<float> s32;
     cudaGraphExec_t graph = nullptr;
     bool initialised = false;
+    bool fixed_pinned = false;  // gks_set_fixed_state was called: initialisations keep the fixed state
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
     int slopes_pass = 0;   // 1: reconstruction step 1 as its own pass
@@ -574,11 +575,25 @@ static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const 
     const int64_t nc = m.nc;
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, d_dW, st.X, nc, s->stream));
-    if (m.fixed)  // fixed boundaries hold the initial state
+    if (m.fixed && !s->fixed_pinned)  // fixed boundaries hold the initial state
         GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(launch_set_control(st.ctrl, st.case_t, st.case_dt, st.case_dtmin, m.ncase, 0.0, 0.0, 1, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_set_fixed_state(gks_state* s, const double* d_W, const double* d_dW) {
+    if (!s || !d_W || !d_dW) { set_error("gks_set_fixed_state: NULL argument"); return GKS_E_ARG; }
+    if (!has_fixed(*s->mesh)) { set_error("gks_set_fixed_state: the mesh has no fixed boundary faces"); return GKS_E_ARG; }
+    order_after_caller(s);
+    const int64_t nc = s->mesh->nc;
+    if (s->fp32)
+        GKS_CHECK_CUDA(Launch<float>::pack(d_W, d_dW, const_cast<float*>(s->m32.fixed), nc, s->stream));
+    else
+        GKS_CHECK_CUDA(Launch<double>::pack(d_W, d_dW, const_cast<double*>(s->m64.fixed), nc, s->stream));
+    s->fixed_pinned = true;
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
     return GKS_OK;
 }
 
@@ -807,7 +822,7 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
     GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
-    if (m.fixed)
+    if (m.fixed && !s->fixed_pinned)
         GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(set_control(s, 0.0, 0.0, 1));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
@@ -916,9 +931,9 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    if (s->fp32 || g.ncase != 1 || has_fixed(g) || s->phys.prf != 0.0) {
-        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh without fixed-state "
-                  "boundary faces, Pr = 1");
+    if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned) || s->phys.prf != 0.0) {
+        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh, Pr = 1, and on a mesh "
+                  "with fixed-state faces a fixed state set by gks_set_fixed_state");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);

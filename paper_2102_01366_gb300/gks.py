@@ -85,6 +85,7 @@ def lib():
         "gks_timestep_noalloc": (C.c_int32, [C.POINTER(gks_params), _vp, _vp, C.c_int64, _vp, _vp]),
         "gks_residual": (C.c_int32, [_vp, _vp]),
         "gks_adjoint_workspace_bytes": (C.c_size_t, [_vp]),
+        "gks_set_fixed_state": (C.c_int32, [_vp, _vp, _vp]),
         "gks_adjoint_step": (C.c_int32, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
@@ -283,6 +284,14 @@ class State:
         out = np.zeros(5)
         _call("gks_residual", self._h, _np_ptr(out))
         return out
+
+    def set_fixed_state(self, W, dW):
+        """The state fixed boundary faces hold from now on, [5|15, nc] FP64
+        (gks_set_fixed_state); later init() calls keep it."""
+        t = self.torch
+        args = [t.as_tensor(x, dtype=t.float64, device=self.device).contiguous() for x in (W, dW)]
+        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        _call("gks_set_fixed_state", self._h, *[_dptr(x) for x in args])
 
     def adjoint_step(self, W, dW, lamW, lamdW, dt):
         """Adjoint of one step at (W, dW) with the frozen step dt

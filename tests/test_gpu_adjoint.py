@@ -32,11 +32,11 @@ def cuda():
 
 
 def _case(seed=61, state="sine"):
-    if state in ("open", "slip", "noslip"):
-        # open ends or walls on x, y and z periodic; a smooth moving state
+    if state in ("open", "slip", "noslip", "fixed"):
+        # open, wall or fixed-state ends on x, y and z periodic; a smooth moving state
         mesh = I.box_mesh((4, 3, 3), (1.0, 0.75, 0.75), (False, True, True), jitter=0.1, seed=seed)
         if state != "open":
-            kind = I.BC_SLIP_WALL if state == "slip" else I.BC_NOSLIP_WALL
+            kind = {"slip": I.BC_SLIP_WALL, "noslip": I.BC_NOSLIP_WALL, "fixed": I.BC_FIXED}[state]
             mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
         W, dW = I.sine_wave_state(mesh, k=8.0 * np.pi / 3.0, u=(0.6, 0.5, -0.3))
     elif state == "sine":
@@ -58,13 +58,15 @@ def _dot(a, b):
 @pytest.mark.parametrize("weno,smooth,viscous,state", [(0, 0, 0, "sine"), (0, 1, 0, "sine"), (0, 0, 1, "sine"),
                                                        (0, 1, 1, "sine"), (1, 0, 0, "sine"), (1, 0, 0, "slab"),
                                                        (1, 0, 1, "slab"), (1, 0, 0, "open"), (1, 0, 1, "open"),
-                                                       (1, 0, 0, "slip"), (0, 0, 1, "noslip")])
+                                                       (1, 0, 0, "slip"), (0, 0, 1, "noslip"), (1, 0, 0, "fixed"),
+                                                       (0, 0, 1, "fixed")])
 def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, viscous, state):
     """Viscous runs carry tau = mu / p_c and each side's time slope A
     through the reverse-mode point adjoint; weno = 1 differentiates the
     nonlinear weights (on the slab they move the gradient by ~10 % from the
     linear-weight one); open
-    ends and slip and non-slip walls take their ghosts' adjoints.  The
+    ends and slip and non-slip walls take their ghosts' adjoints; fixed ends
+    hold a state set once (gks_set_fixed_state), a constant of the step.  The
     slab's many |x| terms (pairs of smoothness indicators, pressure jumps)
     sit close to their kinks, and so do some of the viscous WENO runs'
     (on the open box the difference quotient moves by 1.5e-6 between
@@ -76,6 +78,11 @@ def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, visc
     g = gks.Mesh(mesh)
     kw = dict(weno=weno, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
     s = gks.State(g, gks.params(precision=0, **kw))
+    if state == "fixed":
+        # the boundary state, set apart from the (perturbed) initialisations
+        Wf, dWf = W * (1.0 + 0.02 * rng.standard_normal(W.shape)), 0.5 * dW
+        s.set_fixed_state(Wf, dWf)
+        mesh["fixed_state"] = (Wf, dWf)
     o = oracle_mod.Mesh(mesh)
     p = oracle_mod.params(**kw)
     dt = 0.5 * o.timestep(p, W)
