@@ -86,8 +86,7 @@ typedef struct gks_params {
  * the interface distribution of Eq. 2nd-flux (xi included), U the velocity
  * of the interface equilibrium state in the face frame.  The paper names
  * no formula; this is the correction of the gas-kinetic literature it cites
- * for the Navier-Stokes solver.  Not differentiated: gks_adjoint_step
- * rejects it. */
+ * for the Navier-Stokes solver; gks_adjoint_step differentiates it. */
 void gks_params_default(gks_params* p);
 
 typedef struct gks_mesh gks_mesh;   /* opaque, library-owned host object */
@@ -333,8 +332,8 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
  * meshes, periodic or with open, slip-wall, non-slip-wall or fixed-state
  * boundary faces (the last only with a fixed state set by
- * gks_set_fixed_state: it is then a constant of the step), Pr = 1;
- * GKS_E_UNSUPPORTED otherwise.  A cell that
+ * gks_set_fixed_state: it is then a constant of the step), any Prandtl
+ * number; GKS_E_UNSUPPORTED otherwise.  A cell that
  * falls back to its average (the positivity check of Sec. 4.3) passes the
  * adjoint of its constant to its own average only; the fallback decision is
  * held fixed (piecewise derivative).  All arrays are

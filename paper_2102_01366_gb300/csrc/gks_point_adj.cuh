@@ -275,8 +275,8 @@ __device__ __forceinline__ void adj_micro_slope(const Prim<double>& s, double K,
 // must equal ph.viscous (the inviscid instance keeps no viscous state).
 template <bool VISC>
 __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const double (*gl)[5],
-                              const double* Wr, const double (*gr)[5], double dt, const double* lFh,
-                              const double* lD, const double* lW0, const double* ldW, double* lWl,
+                              const double* Wr, const double (*gr)[5], double dt, const double* lFh_out,
+                              const double* lD_out, const double* lW0, const double* ldW, double* lWl,
                               double (*lgl)[5], double* lWr, double (*lgr)[5]) {
     const double K = ph.K;
     constexpr bool visc = VISC;
@@ -324,23 +324,86 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
     acc_grad<0>(tf, ac, -1.0, rA);
     micro_slope(C, K, rA, Ac);
     const double hd = 0.5 * dt;
-
-    // ---- reverse ----
-    TabD ltf;
-    tab_zero(ltf);
-    PrimAdj lC;
-    double lCrho = 0.0;  // adjoint of the rho factor of the equilibrium sums
-    double lWc[5] = {0, 0, 0, 0, 0};
-    double lac[3][5] = {}, lAc[5] = {0, 0, 0, 0, 0}, lrA[5] = {0, 0, 0, 0, 0};
-    // adjoints of the time coefficients and of tau
-    double lk0 = 0, lk1 = 0, ldk0 = 0, ldk1 = 0, lq1 = 0, lq2 = 0, lq3 = 0, ldq1 = 0, ldq2 = 0, ldq3 = 0;
-    double lE = 0, ltau = 0;
     // equilibrium sums (recomputed for the coefficient adjoints)
     double mf0[5] = {0, 0, 0, 0, 0}, mf1[5] = {0, 0, 0, 0, 0}, mf2[5] = {0, 0, 0, 0, 0}, mw1[5];
     acc_psi<1, 0, 0>(tf, C.rho, mf0);
     acc_grad<1>(tf, ac, C.rho, mf1);
     acc_apsi<1, 0, 0>(tf, Ac, C.rho, mf2);
     for (int k = 0; k < 5; ++k) mw1[k] = -C.rho * rA[k];
+
+    // ---- reverse ----
+    // Pr fix (viscous): F_E += prf (qf - U1 qw) on Fh and D, with
+    // qf = F_E - U.F_m + |U|^2/2 F_rho, qw the same of the state integral IW
+    // and U = U^c.  Its transpose turns the output adjoints into those of the
+    // uncorrected Fh, D, of IWh, IWd and of U^c.
+    double lFh[5], lD[5], lIWh[5] = {0, 0, 0, 0, 0}, lIWd[5] = {0, 0, 0, 0, 0}, lU[3] = {0, 0, 0};
+    for (int k = 0; k < 5; ++k) {
+        lFh[k] = lFh_out[k];
+        lD[k] = lD_out[k];
+    }
+    const bool prfix = VISC && ph.prf != 0.0;
+    if (prfix) {
+        // forward: the uncorrected Fh, D and the state integrals IWh, IWd
+        double F[2][5], IW[2][5];
+        for (int k = 0; k < 5; ++k) {
+            if (smooth) {
+                F[0][k] = hd * mf0[k] - tau * hd * mf1[k] + (0.5 * hd * hd - tau * hd) * mf2[k];
+                F[1][k] = 0.25 * dt * dt * mf2[k];
+                IW[0][k] = hd * Wc[k] - 0.5 * hd * hd * mw1[k];
+                IW[1][k] = -0.25 * dt * dt * mw1[k];
+            } else {
+                F[0][k] = tc.q1 * mf0[k] + tc.q2 * mf1[k] + tc.q3 * mf2[k];
+                F[1][k] = tc.dq1 * mf0[k] + tc.dq2 * mf1[k] + tc.dq3 * mf2[k];
+                IW[0][k] = tc.q1 * Wc[k] + (tc.q2 - tc.q3) * mw1[k];
+                IW[1][k] = tc.dq1 * Wc[k] + (tc.dq2 - tc.dq3) * mw1[k];
+            }
+        }
+        if (!smooth)
+            for (int s = 0; s < 2; ++s) {
+                double kf0[5] = {0, 0, 0, 0, 0}, kf1[5] = {0, 0, 0, 0, 0}, kf2[5] = {0, 0, 0, 0, 0},
+                       kw0[5] = {0, 0, 0, 0, 0}, kw1[5] = {0, 0, 0, 0, 0}, kw2[5] = {0, 0, 0, 0, 0};
+                acc_psi<1, 0, 0>(th[s], P[s].rho, kf0);
+                acc_grad<1>(th[s], a[s], P[s].rho, kf1);
+                acc_apsi<1, 0, 0>(th[s], As[s], P[s].rho, kf2);
+                acc_psi<0, 0, 0>(th[s], P[s].rho, kw0);
+                acc_grad<0>(th[s], a[s], P[s].rho, kw1);
+                acc_apsi<0, 0, 0>(th[s], As[s], P[s].rho, kw2);
+                for (int k = 0; k < 5; ++k) {
+                    F[0][k] += tc.k0 * kf0[k] - (tau * tc.k0 + tc.k1) * kf1[k] - tau * tc.k0 * kf2[k];
+                    F[1][k] += tc.dk0 * kf0[k] - (tau * tc.dk0 + tc.dk1) * kf1[k] - tau * tc.dk0 * kf2[k];
+                    IW[0][k] += tc.k0 * kw0[k] - (tau * tc.k0 + tc.k1) * kw1[k] - tau * tc.k0 * kw2[k];
+                    IW[1][k] += tc.dk0 * kw0[k] - (tau * tc.dk0 + tc.dk1) * kw1[k] - tau * tc.dk0 * kw2[k];
+                }
+            }
+        const double U[3] = {C.u, C.v, C.w};
+        const double uu = 0.5 * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+        const double gq[5] = {uu, -U[0], -U[1], -U[2], 1.0};  // d q / d (F or IW)
+        for (int h = 0; h < 2; ++h) {
+            double* lF = h == 0 ? lFh : lD;
+            double* lIW = h == 0 ? lIWh : lIWd;
+            const double l = ph.prf * lF[4];
+            const double qw = IW[h][4] - (U[0] * IW[h][1] + U[1] * IW[h][2] + U[2] * IW[h][3]) + uu * IW[h][0];
+            for (int j = 0; j < 3; ++j)
+                lU[j] += l * (-F[h][1 + j] + U[j] * F[h][0] - (j == 0 ? qw : 0.0) -
+                              U[0] * (-IW[h][1 + j] + U[j] * IW[h][0]));
+            for (int k = 0; k < 5; ++k) {
+                lF[k] += l * gq[k];
+                lIW[k] += -U[0] * l * gq[k];
+            }
+        }
+    }
+    TabD ltf;
+    tab_zero(ltf);
+    PrimAdj lC;
+    lC.u += lU[0];
+    lC.v += lU[1];
+    lC.w += lU[2];
+    double lCrho = 0.0;  // adjoint of the rho factor of the equilibrium sums
+    double lWc[5] = {0, 0, 0, 0, 0};
+    double lac[3][5] = {}, lAc[5] = {0, 0, 0, 0, 0}, lrA[5] = {0, 0, 0, 0, 0};
+    // adjoints of the time coefficients and of tau
+    double lk0 = 0, lk1 = 0, ldk0 = 0, ldk1 = 0, lq1 = 0, lq2 = 0, lq3 = 0, ldq1 = 0, ldq2 = 0, ldq3 = 0;
+    double lE = 0, ltau = 0;
     double lmf0[5], lmf1[5], lmf2[5], lmw1[5];
     if (smooth) {
         for (int k = 0; k < 5; ++k) {
@@ -350,6 +413,9 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
             lmw1[k] = -dt * ldW[k];
             lWc[k] += lW0[k];
             ltau += -hd * lFh[k] * (mf1[k] + mf2[k]);
+            // Pr fix: IWh = hd W^c - hd^2/2 mw1, IWd = -dt^2/4 mw1
+            lWc[k] += hd * lIWh[k];
+            lmw1[k] += -0.5 * hd * hd * lIWh[k] - 0.25 * dt * dt * lIWd[k];
         }
     } else {
         const double C23 = dt * (tc.E - 1.0);
@@ -365,6 +431,15 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
             ldq2 += lD[k] * mf1[k];
             ldq3 += lD[k] * mf2[k];
             lE += dt * ldW[k] * mw1[k];
+            // Pr fix: IWh = q1 W^c + (q2 - q3) mw1, IWd with the d-coefficients
+            lWc[k] += tc.q1 * lIWh[k] + tc.dq1 * lIWd[k];
+            lmw1[k] += (tc.q2 - tc.q3) * lIWh[k] + (tc.dq2 - tc.dq3) * lIWd[k];
+            lq1 += lIWh[k] * Wc[k];
+            lq2 += lIWh[k] * mw1[k];
+            lq3 -= lIWh[k] * mw1[k];
+            ldq1 += lIWd[k] * Wc[k];
+            ldq2 += lIWd[k] * mw1[k];
+            ldq3 -= lIWd[k] * mw1[k];
         }
     }
     // mw1 = -rho_c rA
@@ -428,6 +503,15 @@ __device__ void gks_point_adj(const Phys<double>& ph, const double* Wl, const do
                 ltau += -lFh[k] * tc.k0 * (kf1[k] + kf2[k]) - lD[k] * tc.dk0 * (kf1[k] + kf2[k]) -
                         lW0[k] * (kw1[k] + kw2[k]) + ldW[k] * ((1.0 - tc.E) * (kw1[k] + kw2[k]));
                 lE += ldW[k] * (-(tau + dt) * kw1[k] - tau * kw2[k]);
+                // Pr fix: this side's part of IWh, IWd (k- and dk-coefficients)
+                lkw0[k] += tc.k0 * lIWh[k] + tc.dk0 * lIWd[k];
+                lkw1[k] += -(tau * tc.k0 + tc.k1) * lIWh[k] - (tau * tc.dk0 + tc.dk1) * lIWd[k];
+                lkw2[k] += -tau * tc.k0 * lIWh[k] - tau * tc.dk0 * lIWd[k];
+                lk0 += lIWh[k] * (kw0[k] - tau * kw1[k] - tau * kw2[k]);
+                lk1 -= lIWh[k] * kw1[k];
+                ldk0 += lIWd[k] * (kw0[k] - tau * kw1[k] - tau * kw2[k]);
+                ldk1 -= lIWd[k] * kw1[k];
+                ltau += -(lIWh[k] * tc.k0 + lIWd[k] * tc.dk0) * (kw1[k] + kw2[k]);
             }
             adj_acc_psi<1, 0, 0>(th[s], P[s].rho, lkf0, lth[s], lrho);
             adj_acc_grad<1>(th[s], a[s], P[s].rho, lkf1, lth[s], la[s], lrho);
