@@ -142,6 +142,46 @@ def test_prandtl_fix_adjoint(cuda, oracle_mod, weno, smooth, state):
     assert abs(_dot(lam, jv_ora) - rhs) < 1e-6 * abs(rhs), (_dot(lam, jv_ora), rhs)
 
 
+@pytest.mark.parametrize("weno", [0, 1])
+def test_sphere_shell_adjoint(cuda, oracle_mod, weno):
+    """The viscous sphere's configuration on a 1,080-cell shell: non-slip
+    wall (with the linear weights' first-order wall cells or WENO), far
+    field held at a set state, Pr = 0.72, pole wedges; one step's adjoint
+    against central differences of the GPU and oracle forward maps."""
+    torch = cuda
+    mesh = I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08)
+    W, dW = I.sine_wave_state(mesh, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4)
+    rng = np.random.Generator(np.random.PCG64(71))
+    W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
+    dW = dW + 0.05 * rng.standard_normal(dW.shape)
+    mesh["fixed_state"] = (W, dW)
+    H = 1e-7 if weno else 1e-6
+    g = gks.Mesh(mesh)
+    kw = dict(weno=weno, cfl=0.5, viscous=1, mu=0.01, prandtl=0.72)
+    s = gks.State(g, gks.params(precision=0, **kw))
+    s.set_fixed_state(W, dW)
+    o = oracle_mod.Mesh(mesh)
+    p = oracle_mod.params(**kw)
+    dt = 0.5 * o.timestep(p, W)
+    lam = (rng.standard_normal(W.shape), rng.standard_normal(dW.shape))
+    v = (rng.standard_normal(W.shape) * np.abs(W).max(axis=1, keepdims=True),
+         rng.standard_normal(dW.shape) * np.abs(dW).max())
+
+    def gpu_step(Wx, dWx):
+        s.init(Wx, dWx)
+        s.step(1, dt, 0.0)
+        return [x.cpu().numpy() for x in s.get()]
+
+    jv_gpu = [(a - b) / (2 * H) for a, b in zip(gpu_step(W + H * v[0], dW + H * v[1]),
+                                                 gpu_step(W - H * v[0], dW - H * v[1]))]
+    op, om = o.step(p, W + H * v[0], dW + H * v[1], dt), o.step(p, W - H * v[0], dW - H * v[1], dt)
+    jv_ora = [(op[0] - om[0]) / (2 * H), (op[1] - om[1]) / (2 * H)]
+    lW, ldW = s.adjoint_step(torch.tensor(W), torch.tensor(dW), torch.tensor(lam[0]), torch.tensor(lam[1]), dt)
+    rhs = _dot((lW.cpu().numpy(), ldW.cpu().numpy()), v)
+    assert abs(_dot(lam, jv_gpu) - rhs) < 1e-6 * abs(rhs), (_dot(lam, jv_gpu), rhs)
+    assert abs(_dot(lam, jv_ora) - rhs) < 1e-6 * abs(rhs), (_dot(lam, jv_ora), rhs)
+
+
 @pytest.mark.parametrize("weno,state", [(0, "sine"), (1, "sine"), (1, "slab")])
 def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
     """R^2nd (Eq. final_weno_expression-2nd): linear weights give R = P1, the
