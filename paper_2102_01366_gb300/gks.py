@@ -424,6 +424,31 @@ def make_step_function(state, dt):
     return _Step.apply
 
 
+def wall_pressure_force(mesh, kinds, gamma=1.4, wall=(1, 3), device="cuda"):
+    """A differentiable output for gradients: the pressure force on the wall
+    faces, sum over faces of p A n, with p the pressure of the adjacent
+    cell's average and n the face's unit normal pointing out of the fluid
+    (first order in the cell size).  mesh: a Mesh; kinds[nc][4] the boundary
+    kinds per local face (wall = slip 1 and non-slip 3 by default).  Returns
+    a torch function of W [5, nc] (FP64) giving the 3-vector."""
+    import torch
+    top, geo = mesh.topology(), mesh.geometry()
+    kinds = np.asarray(kinds).reshape(mesh.nc, 4)
+    on = (top["nbr"] < 0) & np.isin(kinds, wall)
+    cells, lf = np.nonzero(on)
+    faces = top["csr_face"][cells, lf]
+    sign = top["csr_sign"][cells, lf].astype(np.float64)
+    an = geo["farea"][faces, None] * geo["fnorm"][faces] * sign[:, None]
+    cells_t = torch.as_tensor(cells, device=device)
+    an_t = torch.as_tensor(an, device=device)
+
+    def force(W):
+        Wc = W[:, cells_t]
+        p = (gamma - 1.0) * (Wc[4] - 0.5 * (Wc[1:4] ** 2).sum(0) / Wc[0])
+        return (p[:, None] * an_t).sum(0)
+    return force
+
+
 def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=20, primal_precision=0):
     """Gradient of loss(W_N) after N steps of frozen step dt with respect to
     the initial (W0, dW0), by the adjoint with checkpointing: the primal run

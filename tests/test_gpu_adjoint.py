@@ -182,6 +182,52 @@ def test_sphere_shell_adjoint(cuda, oracle_mod, weno):
     assert abs(_dot(lam, jv_ora) - rhs) < 1e-6 * abs(rhs), (_dot(lam, jv_ora), rhs)
 
 
+def test_wall_force_gradient_on_the_sphere_shell(cuda):
+    """J = x-component of the pressure force on the sphere (gks.wall_pressure_force)
+    after 3 steps of the viscous shell (WENO, Pr 0.72, far field held at a
+    set state); dJ/d rho_0 along a random direction (velocity and pressure
+    held) by the chained adjoint, against a central difference of the
+    forward runs."""
+    torch = cuda
+    mesh = I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08)
+    W, dW = I.sine_wave_state(mesh, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4)
+    rng = np.random.Generator(np.random.PCG64(73))
+    W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(precision=0, weno=1, cfl=0.5, viscous=1, mu=0.01, prandtl=0.72))
+    s.set_fixed_state(W, dW)
+    s.init(W, dW)
+    dt = 0.5 * s.timestep()
+    force = gks.wall_pressure_force(g, mesh["bkind"])
+
+    def run(W0):
+        Wc, dWc = torch.tensor(W0, device="cuda"), torch.tensor(dW, device="cuda")
+        states = []
+        for _ in range(3):
+            states.append((Wc, dWc))
+            s.init(Wc, dWc)
+            s.step(1, dt, 0.0)
+            Wc, dWc = s.get()
+        return Wc, states
+
+    Wn, states = run(W)
+    Wn = Wn.clone().requires_grad_(True)
+    J = force(Wn)[0]
+    J.backward()
+    lam_W = Wn.grad.detach().clone()
+    lam_dW = torch.zeros((15, g.nc), dtype=torch.float64, device="cuda")
+    for Wc, dWc in reversed(states):
+        lam_W, lam_dW = s.adjoint_step(Wc, dWc, lam_W, lam_dW, dt)
+    d = rng.standard_normal(g.nc)
+    U = W[1:4] / W[0]
+    dW0 = np.concatenate([d[None], d[None] * U, 0.5 * d[None] * (U ** 2).sum(0)[None]])
+    ad = float((lam_W.cpu().numpy() * dW0).sum())
+    h = 1e-7
+    with torch.no_grad():
+        fd = (float(force(run(W + h * dW0)[0])[0]) - float(force(run(W - h * dW0)[0])[0])) / (2 * h)
+    assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
+
+
 @pytest.mark.parametrize("weno,state", [(0, "sine"), (1, "sine"), (1, "slab")])
 def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
     """R^2nd (Eq. final_weno_expression-2nd): linear weights give R = P1, the
