@@ -1,0 +1,269 @@
+"""FP64 CPU restatement of one two-stage step in plain PyTorch operations, so
+that torch.autograd gives the step's exact reverse sweep on the CPU.
+
+TEST INFRASTRUCTURE ONLY: the tests use it as a second, independent check of
+the library's adjoint (gks_adjoint_step); nothing in the product imports it.
+
+Scope: third-order reconstruction with linear weights (R = P^2 = M2 d, Sec.
+4.1), the full gas-kinetic solver for the Euler equations (tau = 0, Eq.
+2nd-flux with the equilibrium state of Eq. new-equ-part), periodic meshes,
+the S2O4 step of Sec. 3 with the linear flux fit (Eqs. linear-system, s2o4)
+and the cell-averaged gradients from the divergence theorem (Eq.
+gauss-formula).  Geometry, connectivity and the stencil operators M2 come
+from the C oracle (they do not depend on the state); everything that does
+is written here afresh: the face frame, the Maxwellian moments as products
+of one-dimensional moments (sparse polynomials in u, v, w, xi^2), the
+micro-slopes by a 5x5 linear solve, the time integrals of the distribution,
+the stage sums."""
+import math
+
+import numpy as np
+import torch
+
+PAIRS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+# ----------------------------------------------------------- polynomials --
+# a polynomial in (u, v, w, s = xi^2) is a dict {(a, b, c, d): coefficient}
+
+def _pmul(p, q):
+    out = {}
+    for ka, ca in p.items():
+        for kb, cb in q.items():
+            k = (ka[0] + kb[0], ka[1] + kb[1], ka[2] + kb[2], ka[3] + kb[3])
+            out[k] = out[k] + ca * cb if k in out else ca * cb
+    return out
+
+
+def _padd(p, q):
+    out = dict(p)
+    for k, c in q.items():
+        out[k] = out[k] + c if k in out else c
+    return out
+
+
+_PSI = [{(0, 0, 0, 0): 1.0}, {(1, 0, 0, 0): 1.0}, {(0, 1, 0, 0): 1.0}, {(0, 0, 1, 0): 1.0},
+        {(2, 0, 0, 0): 0.5, (0, 2, 0, 0): 0.5, (0, 0, 2, 0): 0.5, (0, 0, 0, 1): 0.5}]
+_U = [{(1, 0, 0, 0): 1.0}, {(0, 1, 0, 0): 1.0}, {(0, 0, 1, 0): 1.0}]
+
+
+def _slope_poly(a):
+    """a . psi for a [N, 5]"""
+    out = {}
+    for k in range(5):
+        out = _padd(out, {key: c * a[:, k] for key, c in _PSI[k].items()})
+    return out
+
+
+# ------------------------------------------------------ Maxwellian moments --
+class _Moments:
+    """Normalised moments <u^a v^b w^c xi^2d> of a Maxwellian (U, lam), with
+    u restricted to u > 0 (half = +1), u < 0 (-1) or free (0)."""
+
+    def __init__(self, U, lam, K, half, order=8):
+        h = 0.5 / lam
+        self.tab = []
+        for axis in range(3):
+            m = [None] * (order + 1)
+            Ua = U[:, axis]
+            if axis == 0 and half != 0:
+                sg = float(half)
+                m[0] = 0.5 * torch.special.erfc(-sg * torch.sqrt(lam) * Ua)
+                m[1] = Ua * m[0] + sg * torch.exp(-lam * Ua * Ua) / (2.0 * torch.sqrt(math.pi * lam))
+            else:
+                m[0] = torch.ones_like(Ua)
+                m[1] = Ua
+            for n in range(order - 1):
+                m[n + 2] = Ua * m[n + 1] + (n + 1) * h * m[n]
+            self.tab.append(m)
+        self.xi = [torch.ones_like(lam), K * h, (K * K + 2.0 * K) * h * h, K * (K + 2.0) * (K + 4.0) * h ** 3]
+
+    def of(self, poly):
+        tot = 0.0
+        for (a, b, c, d), coef in poly.items():
+            tot = tot + coef * self.tab[0][a] * self.tab[1][b] * self.tab[2][c] * self.xi[d]
+        return tot
+
+    def psi(self, poly):
+        """the 5-vector <poly psi_k>, [N, 5]"""
+        return torch.stack([self.of(_pmul(poly, _PSI[k])) for k in range(5)], dim=1)
+
+    def gram(self):
+        """<psi_k psi_j>, [N, 5, 5]"""
+        rows = [self.psi(_PSI[k]) for k in range(5)]
+        return torch.stack(rows, dim=1)
+
+
+def _prim(W, gamma):
+    rho = W[:, 0]
+    U = W[:, 1:4] / rho[:, None]
+    p = (gamma - 1.0) * (W[:, 4] - 0.5 * rho * (U * U).sum(1))
+    return rho, U, p, rho / (2.0 * p)
+
+
+def _slopes(full, rho, dW):
+    """micro-slopes a_i (<(a_i . psi) psi> = dW_i / rho) and A
+    (<(A + sum_i a_i u_i) . psi> = 0) by direct solves; dW [N, 3, 5]"""
+    G = full.gram()
+    a = [torch.linalg.solve(G, dW[:, i] / rho[:, None]) for i in range(3)]
+    rhs = 0.0
+    for i in range(3):
+        rhs = rhs + full.psi(_pmul(_U[i], _slope_poly(a[i])))
+    A = torch.linalg.solve(G, -rhs)
+    return a, A
+
+
+def point_flux(Wl, gl, Wr, gr, dt, gamma=1.4, tau_eps=0.01, tau_c=1.0):
+    """Euler kinetic solution at N points in the face frame (x1 along the
+    normal): states [N, 5], gradients [N, 3, 5] (d/dx_i).  Returns the flux
+    integrals over [0, dt/2] and [0, dt] and the states at t = 0 and dt."""
+    K = (5.0 - 3.0 * gamma) / (gamma - 1.0)
+    rl, Ul, pl, laml = _prim(Wl, gamma)
+    rr, Ur, pr, lamr = _prim(Wr, gamma)
+    fl, fr = _Moments(Ul, laml, K, 0), _Moments(Ur, lamr, K, 0)
+    hl, hr = _Moments(Ul, laml, K, +1), _Moments(Ur, lamr, K, -1)
+    al, _ = _slopes(fl, rl, gl)
+    ar, _ = _slopes(fr, rr, gr)
+    one = {(0, 0, 0, 0): 1.0}
+    Wc = rl[:, None] * hl.psi(one) + rr[:, None] * hr.psi(one)
+    dWc = torch.stack([rl[:, None] * hl.psi(_slope_poly(al[i])) + rr[:, None] * hr.psi(_slope_poly(ar[i]))
+                       for i in range(3)], dim=1)
+    rc, Uc, pc, lamc = _prim(Wc, gamma)
+    fc = _Moments(Uc, lamc, K, 0)
+    ac, Ac = _slopes(fc, rc, dWc)
+    tau_n = (tau_eps + tau_c * torch.abs((pl - pr) / (pl + pr))) * dt
+
+    def au(a):  # sum_i (a_i . psi) u_i
+        out = {}
+        for i in range(3):
+            out = _padd(out, _pmul(_U[i], _slope_poly(a[i])))
+        return out
+    u1 = _U[0]
+    c_f, c_fa, c_fA = fc.psi(u1), fc.psi(_pmul(u1, au(ac))), fc.psi(_pmul(u1, _slope_poly(Ac)))
+    c_wa, c_wA = fc.psi(au(ac)), fc.psi(_slope_poly(Ac))
+    c_w = fc.psi(one)
+    sides = [(rl, hl, al), (rr, hr, ar)]
+    kin = [(r[:, None], h.psi(u1), h.psi(_pmul(u1, au(a))), h.psi(one), h.psi(au(a))) for r, h, a in sides]
+
+    def flux(d):
+        E = torch.exp(-d / tau_n)[:, None]
+        tn = tau_n[:, None]
+        k0 = tn * (1.0 - E)
+        k1 = tn * tn * (1.0 - E) - tn * d * E
+        out = rc[:, None] * ((d - k0) * c_f + k1 * c_fa + 0.5 * d * d * c_fA)
+        for r, f0, f1, _, _ in kin:
+            out = out + r * (k0 * f0 - k1 * f1)
+        return out
+
+    def state(t):
+        e = torch.exp(-t / tau_n)[:, None]
+        out = rc[:, None] * ((1.0 - e) * c_w + t * e * c_wa + t * c_wA)
+        for r, _, _, w0, w1 in kin:
+            out = out + r * (e * w0 - t * e * w1)
+        return out
+    return flux(0.5 * dt), flux(dt), state(0.0), state(dt)
+
+
+# -------------------------------------------------------------- the step --
+def _frame(n):
+    """rows (n, t1, t2), a right-handed orthonormal frame per face, [nf, 3, 3]"""
+    e = torch.zeros_like(n)
+    use_x = n[:, 0].abs() < 0.9
+    e[use_x, 0] = 1.0
+    e[~use_x, 1] = 1.0
+    t1 = e - (e * n).sum(1, keepdim=True) * n
+    t1 = t1 / torch.linalg.norm(t1, dim=1, keepdim=True)
+    t2 = torch.cross(n, t1, dim=1)
+    return torch.stack([n, t1, t2], dim=1)
+
+
+class Step:
+    """One step on an oracle mesh (periodic), linear weights, Euler."""
+
+    def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0):
+        geo, top = om.geometry(), om.topology()
+        _, M2 = om.stencils()
+        t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
+        self.vol, self.mom = t(geo["vol"]), t(geo["mom2"])
+        self.area, self.n = t(geo["farea"]), t(geo["fnorm"])
+        self.gpl, self.gpr = t(geo["gp_l"]), t(geo["gp_r"])
+        self.lr = torch.as_tensor(top["face_lr"])
+        self.nbr = torch.as_tensor(top["nbr"])
+        self.M2 = t(M2)
+        if (self.nbr < 0).any():
+            raise ValueError("periodic meshes only")
+        self.R = _frame(self.n)
+        self.gamma, self.tau_eps, self.tau_c = gamma, tau_eps, tau_c
+
+    def _recon(self, W, dW):
+        """a = M2 d per cell and component: [nc, 5, 9] (linear weights)"""
+        Q0 = W.T                                   # [nc, 5]
+        Qn = W.T[self.nbr]                         # [nc, 4, 5]
+        G = dW.T.reshape(-1, 5, 3)[self.nbr]       # [nc, 4, 5, 3]
+        d = torch.cat([(Qn - Q0[:, None, :]).permute(0, 2, 1),                   # [nc, 5, 4]
+                       G.permute(0, 2, 1, 3).reshape(-1, 5, 12)], dim=2)          # [nc, 5, 12]
+        return torch.einsum("ckj,cqj->cqk", self.M2, d), Q0
+
+    def _eval(self, a, Q0, cells, X):
+        """value [F, 5] and gradient [F, 3, 5] of R of `cells` at offsets X [F, 3]"""
+        a, Q0, M = a[cells], Q0[cells], self.mom[cells]
+        val = Q0 + torch.einsum("fqk,fk->fq", a[:, :, :3], X)
+        grad = a[:, :, :3].permute(0, 2, 1).clone()
+        for q, (i, j) in enumerate(PAIRS):
+            val = val + a[:, :, 3 + q] * (X[:, i] * X[:, j] - M[:, q])[:, None]
+            grad[:, i, :] = grad[:, i, :] + a[:, :, 3 + q] * X[:, j][:, None]
+            grad[:, j, :] = grad[:, j, :] + a[:, :, 3 + q] * X[:, i][:, None]
+        return val, grad
+
+    def _to_local(self, R, W, g):
+        m = torch.einsum("fij,fj->fi", R, W[:, 1:4])
+        Wl = torch.cat([W[:, :1], m, W[:, 4:]], dim=1)
+        gx = torch.einsum("fij,fjq->fiq", R, g)                       # derivative index
+        gm = torch.einsum("fij,fkj->fki", R, gx[:, :, 1:4])            # momentum components
+        gl = torch.cat([gx[:, :, :1], gm, gx[:, :, 4:]], dim=2)
+        return Wl, gl
+
+    def _to_global(self, R, F):
+        m = torch.einsum("fji,fj->fi", R, F[:, 1:4])
+        return torch.cat([F[:, :1], m, F[:, 4:]], dim=1)
+
+    def _faces(self, W, dW, dt):
+        """per face: sum_k w_k of Fh, F, W(0) n, W(dt) n (global frame)"""
+        a, Q0 = self._recon(W, dW)
+        L, Rr = self.lr[:, 0], self.lr[:, 1]
+        w = self.area / 3.0
+        out = [0.0, 0.0, 0.0, 0.0]
+        for k in range(3):
+            vl, gl = self._eval(a, Q0, L, self.gpl[:, k])
+            vr, gr = self._eval(a, Q0, Rr, self.gpr[:, k])
+            Wl, gll = self._to_local(self.R, vl, gl)
+            Wr, grl = self._to_local(self.R, vr, gr)
+            Fh, F, W0, Wt = point_flux(Wl, gll, Wr, grl, dt, self.gamma, self.tau_eps, self.tau_c)
+            res = [self._to_global(self.R, x) for x in (Fh, F, W0, Wt)]
+            for j in range(4):
+                out[j] = out[j] + w[:, None] * res[j]
+        return out
+
+    def _cell_sum(self, per_face):
+        """sum over each cell's faces with s = +1 as left cell, -1 as right; [nc, ...]"""
+        nc = self.vol.shape[0]
+        shape = (nc,) + tuple(per_face.shape[1:])
+        out = torch.zeros(shape, dtype=per_face.dtype)
+        out = out.index_add(0, self.lr[:, 0], per_face)
+        return out.index_add(0, self.lr[:, 1], -per_face)
+
+    def __call__(self, W, dW, dt):
+        """(W [5, nc], dW [15, nc]) -> (W^{n+1}, grad W^{n+1}) with the step dt"""
+        n = self.n
+        vol = self.vol[:, None]
+        Fh, F, W0, Wt = self._faces(W, dW, dt)
+        Ws = W.T - self._cell_sum(Fh) / vol
+        half = 0.5 * (W0 + Wt)
+        gs = self._cell_sum(half[:, :, None] * n[:, None, :]) / vol[:, :, None]
+        S = self._cell_sum(8.0 / 3.0 * Fh - 1.0 / 3.0 * F)
+        G = self._cell_sum(W0[:, :, None] * n[:, None, :])
+        dWs = gs.reshape(-1, 15).T
+        Fh2, F2, W02, Wt2 = self._faces(Ws.T, dWs, dt)
+        Wn = W.T - (S + self._cell_sum(4.0 / 3.0 * (F2 - 2.0 * Fh2))) / vol
+        gn = (G + self._cell_sum((Wt2 - W02)[:, :, None] * n[:, None, :])) / vol[:, :, None]
+        return Wn.T, gn.reshape(-1, 15).T

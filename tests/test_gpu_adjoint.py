@@ -261,6 +261,30 @@ def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
     assert abs(_dot(lam, jv_ora) - rhs) < 1e-6 * abs(rhs), (_dot(lam, jv_ora), rhs)
 
 
+@pytest.mark.parametrize("seed", [61, 62])
+def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, seed):
+    """The adjoint against an FP64 CPU reverse sweep: torch.autograd through
+    the plain-PyTorch restatement of the step (oracle/torch_step.py, itself
+    pinned to the C oracle's step), linear weights, Euler, full flux,
+    periodic mesh.  Both are exact derivatives, so they agree to rounding,
+    every entry of d J / d (W, grad W)."""
+    import torch
+    from oracle import torch_step as TS
+    mesh, W, dW, rng = _case(seed=seed)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(precision=0, weno=0, cfl=0.5))
+    o = oracle_mod.Mesh(mesh)
+    dt = 0.5 * o.timestep(oracle_mod.params(weno=0, cfl=0.5), W)
+    lam = (rng.standard_normal(W.shape), rng.standard_normal(dW.shape))
+    lW, ldW = s.adjoint_step(torch.tensor(W), torch.tensor(dW), torch.tensor(lam[0]), torch.tensor(lam[1]), dt)
+    Wt = torch.tensor(W, requires_grad=True)
+    dWt = torch.tensor(dW, requires_grad=True)
+    Wn, dWn = TS.Step(o)(Wt, dWt, dt)
+    ((Wn * torch.tensor(lam[0])).sum() + (dWn * torch.tensor(lam[1])).sum()).backward()
+    for gpu, cpu in ((lW.cpu().numpy(), Wt.grad.numpy()), (ldW.cpu().numpy(), dWt.grad.numpy())):
+        assert np.abs(gpu - cpu).max() < 1e-11 * np.abs(cpu).max(), np.abs(gpu - cpu).max() / np.abs(cpu).max()
+
+
 def test_kinetic_energy_gradient_through_three_steps(cuda, oracle_mod):
     """J = sum |Omega| |rho U|^2 / (2 rho) after 3 steps; dJ/d rho_0 (initial
     cell-average density, U and p held) by autograd over the chained step

@@ -204,3 +204,26 @@ def test_open_boundary_is_stable(oracle_mod):
     W[1:4] = 1e-7 * rng.standard_normal((3, om.nc))
     W, dW, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5), W, np.zeros((15, om.nc)), nsteps=60)
     assert np.abs(W - W0).max() < 1e-3
+
+
+def test_torch_restatement_matches_the_oracle_step(oracle_mod):
+    """oracle/torch_step.py (the step in plain PyTorch CPU operations, for the
+    autograd reverse sweep that checks the library's adjoint) reproduces the
+    C oracle's step on a jittered periodic mesh: linear weights, Euler, full
+    flux."""
+    import torch
+    from oracle import torch_step as TS
+    mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=61)
+    W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
+    rng = np.random.Generator(np.random.PCG64(61))
+    W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
+    dW = dW + 0.05 * rng.standard_normal(dW.shape)
+    o = oracle_mod.Mesh(mesh)
+    p = oracle_mod.params(weno=0, cfl=0.5)
+    dt = 0.5 * o.timestep(p, W)
+    Wo, dWo, _ = o.step(p, W, dW, dt)
+    Wt, dWt = TS.Step(o)(torch.tensor(W), torch.tensor(dW), dt)
+    for q in range(5):
+        assert np.abs(Wt.numpy()[q] - Wo[q]).max() < 1e-14 * np.abs(Wo[q]).max()
+        ref = dWo[3 * q:3 * q + 3]
+        assert np.abs(dWt.numpy()[3 * q:3 * q + 3] - ref).max() < 1e-12 * np.abs(ref).max()
