@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY: the tests use it as a second, independent check of
 the library's adjoint (gks_adjoint_step); nothing in the product imports it.
 
 Scope: third-order reconstruction with linear weights (R = P^2 = M2 d, Sec.
-4.1), the full gas-kinetic solver for the Euler equations (tau = 0, Eq.
-2nd-flux with the equilibrium state of Eq. new-equ-part), periodic meshes,
+4.1), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
+Eq. new-equ-part) or the smooth one (Eq. 2nd-smooth-flux), Euler (tau = 0) or
+Navier-Stokes (tau = mu / p_c, Sec. 2.2) with the heat-flux correction for a
+Prandtl number other than 1 (the reading of the oracle), periodic meshes,
 the S2O4 step of Sec. 3 with the linear flux fit (Eqs. linear-system, s2o4)
 and the cell-averaged gradients from the divergence theorem (Eq.
 gauss-formula).  Geometry, connectivity and the stencil operators M2 come
@@ -113,17 +115,18 @@ def _slopes(full, rho, dW):
     return a, A
 
 
-def point_flux(Wl, gl, Wr, gr, dt, gamma=1.4, tau_eps=0.01, tau_c=1.0):
-    """Euler kinetic solution at N points in the face frame (x1 along the
-    normal): states [N, 5], gradients [N, 3, 5] (d/dx_i).  Returns the flux
-    integrals over [0, dt/2] and [0, dt] and the states at t = 0 and dt."""
+def point_flux(Wl, gl, Wr, gr, dt, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False,
+               prandtl=1.0):
+    """Kinetic solution at N points in the face frame (x1 along the normal):
+    states [N, 5], gradients [N, 3, 5] (d/dx_i).  Returns the flux integrals
+    over [0, dt/2] and [0, dt] and the states at t = 0 and dt."""
     K = (5.0 - 3.0 * gamma) / (gamma - 1.0)
     rl, Ul, pl, laml = _prim(Wl, gamma)
     rr, Ur, pr, lamr = _prim(Wr, gamma)
     fl, fr = _Moments(Ul, laml, K, 0), _Moments(Ur, lamr, K, 0)
     hl, hr = _Moments(Ul, laml, K, +1), _Moments(Ur, lamr, K, -1)
-    al, _ = _slopes(fl, rl, gl)
-    ar, _ = _slopes(fr, rr, gr)
+    al, Al = _slopes(fl, rl, gl)
+    ar, Ar = _slopes(fr, rr, gr)
     one = {(0, 0, 0, 0): 1.0}
     Wc = rl[:, None] * hl.psi(one) + rr[:, None] * hr.psi(one)
     dWc = torch.stack([rl[:, None] * hl.psi(_slope_poly(al[i])) + rr[:, None] * hr.psi(_slope_poly(ar[i]))
@@ -131,7 +134,10 @@ def point_flux(Wl, gl, Wr, gr, dt, gamma=1.4, tau_eps=0.01, tau_c=1.0):
     rc, Uc, pc, lamc = _prim(Wc, gamma)
     fc = _Moments(Uc, lamc, K, 0)
     ac, Ac = _slopes(fc, rc, dWc)
-    tau_n = (tau_eps + tau_c * torch.abs((pl - pr) / (pl + pr))) * dt
+    jump = tau_c * torch.abs((pl - pr) / (pl + pr)) * dt
+    tau = mu / pc if viscous else torch.zeros_like(pc)
+    tau_n = tau + jump if viscous else tau_eps * dt + jump
+    tau = tau[:, None]
 
     def au(a):  # sum_i (a_i . psi) u_i
         out = {}
@@ -142,26 +148,47 @@ def point_flux(Wl, gl, Wr, gr, dt, gamma=1.4, tau_eps=0.01, tau_c=1.0):
     c_f, c_fa, c_fA = fc.psi(u1), fc.psi(_pmul(u1, au(ac))), fc.psi(_pmul(u1, _slope_poly(Ac)))
     c_wa, c_wA = fc.psi(au(ac)), fc.psi(_slope_poly(Ac))
     c_w = fc.psi(one)
-    sides = [(rl, hl, al), (rr, hr, ar)]
-    kin = [(r[:, None], h.psi(u1), h.psi(_pmul(u1, au(a))), h.psi(one), h.psi(au(a))) for r, h, a in sides]
+    sides = [(rl, hl, al, Al), (rr, hr, ar, Ar)]
+    kin = [(r[:, None], h.psi(u1), h.psi(_pmul(u1, au(a))), h.psi(_pmul(u1, _slope_poly(A))), h.psi(one),
+            h.psi(au(a)), h.psi(_slope_poly(A))) for r, h, a, A in sides]
+    rcc = rc[:, None]
 
     def flux(d):
+        """int_0^d of the flux and of the state (the latter for the Pr fix)"""
+        if smooth:
+            F = rcc * (d * c_f - tau * d * (c_fa + c_fA) + 0.5 * d * d * c_fA)
+            IW = rcc * (d * c_w - tau * d * (c_wa + c_wA) + 0.5 * d * d * c_wA)
+            return F, IW
         E = torch.exp(-d / tau_n)[:, None]
         tn = tau_n[:, None]
         k0 = tn * (1.0 - E)
         k1 = tn * tn * (1.0 - E) - tn * d * E
-        out = rc[:, None] * ((d - k0) * c_f + k1 * c_fa + 0.5 * d * d * c_fA)
-        for r, f0, f1, _, _ in kin:
-            out = out + r * (k0 * f0 - k1 * f1)
-        return out
+        q1, q2, q3 = d - k0, k1 + tau * k0 - tau * d, 0.5 * d * d - tau * d + tau * k0
+        F = rcc * (q1 * c_f + q2 * c_fa + q3 * c_fA)
+        IW = rcc * (q1 * c_w + q2 * c_wa + q3 * c_wA)
+        for r, f0, f1, f2, w0, w1, w2 in kin:
+            F = F + r * (k0 * f0 - (tau * k0 + k1) * f1 - tau * k0 * f2)
+            IW = IW + r * (k0 * w0 - (tau * k0 + k1) * w1 - tau * k0 * w2)
+        return F, IW
+
+    def fixed(F, IW):
+        if not (viscous and prandtl != 1.0):
+            return F
+        # F_E += (1/Pr - 1) q, q the heat flux about U^c (expanded into F and IW)
+        uu = 0.5 * (Uc * Uc).sum(1)
+        qf = F[:, 4] - (Uc * F[:, 1:4]).sum(1) + uu * F[:, 0]
+        qw = IW[:, 4] - (Uc * IW[:, 1:4]).sum(1) + uu * IW[:, 0]
+        return torch.cat([F[:, :4], (F[:, 4] + (1.0 / prandtl - 1.0) * (qf - Uc[:, 0] * qw))[:, None]], dim=1)
 
     def state(t):
+        if smooth:
+            return rcc * (c_w - tau * (c_wa + c_wA) + t * c_wA)
         e = torch.exp(-t / tau_n)[:, None]
-        out = rc[:, None] * ((1.0 - e) * c_w + t * e * c_wa + t * c_wA)
-        for r, _, _, w0, w1 in kin:
-            out = out + r * (e * w0 - t * e * w1)
+        out = rcc * ((1.0 - e) * c_w + ((t + tau) * e - tau) * c_wa + (t - tau + tau * e) * c_wA)
+        for r, _, _, _, w0, w1, w2 in kin:
+            out = out + r * (e * w0 - (tau + t) * e * w1 - tau * e * w2)
         return out
-    return flux(0.5 * dt), flux(dt), state(0.0), state(dt)
+    return fixed(*flux(0.5 * dt)), fixed(*flux(dt)), state(0.0), state(dt)
 
 
 # -------------------------------------------------------------- the step --
@@ -178,9 +205,9 @@ def _frame(n):
 
 
 class Step:
-    """One step on an oracle mesh (periodic), linear weights, Euler."""
+    """One step on an oracle mesh (periodic), linear weights."""
 
-    def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0):
+    def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0):
         geo, top = om.geometry(), om.topology()
         _, M2 = om.stencils()
         t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
@@ -193,7 +220,8 @@ class Step:
         if (self.nbr < 0).any():
             raise ValueError("periodic meshes only")
         self.R = _frame(self.n)
-        self.gamma, self.tau_eps, self.tau_c = gamma, tau_eps, tau_c
+        self.kw = dict(gamma=gamma, tau_eps=tau_eps, tau_c=tau_c, mu=mu, viscous=viscous, smooth=smooth,
+                       prandtl=prandtl)
 
     def _recon(self, W, dW):
         """a = M2 d per cell and component: [nc, 5, 9] (linear weights)"""
@@ -238,7 +266,7 @@ class Step:
             vr, gr = self._eval(a, Q0, Rr, self.gpr[:, k])
             Wl, gll = self._to_local(self.R, vl, gl)
             Wr, grl = self._to_local(self.R, vr, gr)
-            Fh, F, W0, Wt = point_flux(Wl, gll, Wr, grl, dt, self.gamma, self.tau_eps, self.tau_c)
+            Fh, F, W0, Wt = point_flux(Wl, gll, Wr, grl, dt, **self.kw)
             res = [self._to_global(self.R, x) for x in (Fh, F, W0, Wt)]
             for j in range(4):
                 out[j] = out[j] + w[:, None] * res[j]
