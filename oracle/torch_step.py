@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY: the tests use it as a second, independent check of
 the library's adjoint (gks_adjoint_step); nothing in the product imports it.
 
 Scope: third-order reconstruction with linear weights (R = P^2 = M2 d, Sec.
-4.1), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
+4.1) or the multi-resolution WENO weights of Sec. 4.2-4.3 (beta_0 by the
+two-step construction from the neighbours' P1 slopes), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
 Eq. new-equ-part) or the smooth one (Eq. 2nd-smooth-flux), Euler (tau = 0) or
 Navier-Stokes (tau = mu / p_c, Sec. 2.2) with the heat-flux correction for a
 Prandtl number other than 1 (the reading of the oracle), periodic meshes,
@@ -207,9 +208,11 @@ def _frame(n):
 class Step:
     """One step on an oracle mesh (periodic), linear weights."""
 
-    def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0):
+    def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0,
+                 weno=False, eps=1e-8):
         geo, top = om.geometry(), om.topology()
-        _, M2 = om.stencils()
+        M1, M2 = om.stencils()
+        self.weno, self.eps = weno, eps
         t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
         self.vol, self.mom = t(geo["vol"]), t(geo["mom2"])
         self.area, self.n = t(geo["farea"]), t(geo["fnorm"])
@@ -217,6 +220,7 @@ class Step:
         self.lr = torch.as_tensor(top["face_lr"])
         self.nbr = torch.as_tensor(top["nbr"])
         self.M2 = t(M2)
+        self.M1 = t(M1)
         if (self.nbr < 0).any():
             raise ValueError("periodic meshes only")
         self.R = _frame(self.n)
@@ -224,13 +228,57 @@ class Step:
                        prandtl=prandtl)
 
     def _recon(self, W, dW):
-        """a = M2 d per cell and component: [nc, 5, 9] (linear weights)"""
+        """R's coefficients a in the zero-mean basis per cell and component,
+        [nc, 5, 9]: P2 = M2 d (linear weights), or the WENO combination"""
         Q0 = W.T                                   # [nc, 5]
         Qn = W.T[self.nbr]                         # [nc, 4, 5]
         G = dW.T.reshape(-1, 5, 3)[self.nbr]       # [nc, 4, 5, 3]
-        d = torch.cat([(Qn - Q0[:, None, :]).permute(0, 2, 1),                   # [nc, 5, 4]
-                       G.permute(0, 2, 1, 3).reshape(-1, 5, 12)], dim=2)          # [nc, 5, 12]
-        return torch.einsum("ckj,cqj->cqk", self.M2, d), Q0
+        dq = (Qn - Q0[:, None, :]).permute(0, 2, 1)                                   # [nc, 5, 4]
+        d = torch.cat([dq, G.permute(0, 2, 1, 3).reshape(-1, 5, 12)], dim=2)          # [nc, 5, 16]
+        a = torch.einsum("ckj,cqj->cqk", self.M2, d)
+        if not self.weno:
+            return a, Q0
+        return self._weno(a, dq), Q0
+
+    def _weno(self, a, dq):
+        """Sec. 4.2-4.3: smoothness indicators of P1 (slopes b = M1 dQ), P2 and
+        the two-step beta_0 (the neighbours' P1 slopes weighted by 1 +
+        sigma1 / (eps + beta_0j)), nonlinear weights gamma (1 + (sigma /
+        (eps + beta))^2), R = w2 p2 + w1 p1 + w0 p0 (readings R3-R6, R13)"""
+        eps = self.eps
+        v = self.vol[:, None]
+        b = torch.einsum("cij,cqj->cqi", self.M1, dq)                                   # [nc, 5, 3]
+        beta1 = v ** (2.0 / 3.0) * (b * b).sum(2)
+        b0j = v[:, :, None] ** (2.0 / 3.0) * (b[self.nbr] * b[self.nbr]).sum(3).permute(0, 2, 1)  # [nc, 5, 4]
+        pair = 0.0
+        for j in range(4):
+            for k in range(j):
+                pair = pair + torch.abs(b0j[:, :, j] - b0j[:, :, k])
+        s1 = (pair / 6.0) ** (4.0 / 3.0)
+        w1 = 1.0 + s1[:, :, None] / (eps + b0j)
+        beta0 = (w1 * b0j).sum(2) / w1.sum(2)
+        # beta_2 from the exact integrals of the quadratic over the cell
+        lin = a[:, :, :3]
+        H = torch.zeros(a.shape[0], 5, 3, 3, dtype=a.dtype)
+        for q, (i, j) in enumerate(PAIRS):
+            H[:, :, i, j] = H[:, :, i, j] + a[:, :, 3 + q]
+            H[:, :, j, i] = H[:, :, j, i] + a[:, :, 3 + q]
+        Mm = torch.zeros(a.shape[0], 3, 3, dtype=a.dtype)
+        for q, (i, j) in enumerate(PAIRS):
+            Mm[:, i, j] = self.mom[:, q]
+            Mm[:, j, i] = self.mom[:, q]
+        first = (lin * lin).sum(2) + torch.einsum("cqij,cjk,cqik->cq", H, Mm, H)
+        second = sum(H[:, :, i, j] ** 2 for i in range(3) for j in range(i, 3))
+        beta2 = v ** (2.0 / 3.0) * first + v ** (4.0 / 3.0) * second
+        sigma = (0.5 * (torch.abs(beta2 - beta1) + torch.abs(beta2 - beta0))) ** (4.0 / 3.0)
+        g2, g1, g0 = 100.0 / 111.0, 10.0 / 111.0, 1.0 / 111.0
+        w = [g * (1.0 + (sigma / (eps + beta)) ** 2) for g, beta in ((g0, beta0), (g1, beta1), (g2, beta2))]
+        ws = w[0] + w[1] + w[2]
+        g11, g01 = 10.0 / 11.0, 1.0 / 11.0
+        # p0 = Q0, p1 = (P1 - g01 P0) / g11, p2 = (P2 - g1 p1 - g0 p0) / g2; the constants all Q0
+        p1 = torch.cat([b / g11, torch.zeros_like(a[:, :, 3:])], dim=2)
+        p2 = (a - g1 * p1) / g2
+        return (w[2] / ws)[:, :, None] * p2 + (w[1] / ws)[:, :, None] * p1
 
     def _eval(self, a, Q0, cells, X):
         """value [F, 5] and gradient [F, 3, 5] of R of `cells` at offsets X [F, 3]"""

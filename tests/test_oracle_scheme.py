@@ -206,13 +206,14 @@ def test_open_boundary_is_stable(oracle_mod):
     assert np.abs(W - W0).max() < 1e-3
 
 
-@pytest.mark.parametrize("viscous,smooth,prandtl", [(0, 0, 1.0), (0, 1, 1.0), (1, 0, 1.0), (1, 1, 1.0),
-                                                   (1, 0, 0.72)])
-def test_torch_restatement_matches_the_oracle_step(oracle_mod, viscous, smooth, prandtl):
+@pytest.mark.parametrize("weno,viscous,smooth,prandtl", [(0, 0, 0, 1.0), (0, 0, 1, 1.0), (0, 1, 0, 1.0),
+                                                        (0, 1, 1, 1.0), (0, 1, 0, 0.72), (1, 0, 0, 1.0),
+                                                        (1, 1, 0, 0.72)])
+def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, smooth, prandtl):
     """oracle/torch_step.py (the step in plain PyTorch CPU operations, for the
     autograd reverse sweep that checks the library's adjoint) reproduces the
-    C oracle's step on a jittered periodic mesh: linear weights, full or
-    smooth flux, Euler or Navier-Stokes, with the Pr fix."""
+    C oracle's step on a jittered periodic mesh: linear or WENO weights,
+    full or smooth flux, Euler or Navier-Stokes, with the Pr fix."""
     import torch
     from oracle import torch_step as TS
     mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=61)
@@ -222,10 +223,10 @@ def test_torch_restatement_matches_the_oracle_step(oracle_mod, viscous, smooth, 
     dW = dW + 0.05 * rng.standard_normal(dW.shape)
     o = oracle_mod.Mesh(mesh)
     kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl)
-    p = oracle_mod.params(weno=0, cfl=0.5, **kw)
+    p = oracle_mod.params(weno=weno, cfl=0.5, **kw)
     dt = 0.5 * o.timestep(p, W)
     Wo, dWo, _ = o.step(p, W, dW, dt)
-    st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl)
+    st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl, weno=bool(weno))
     Wt, dWt = st(torch.tensor(W), torch.tensor(dW), dt)
     for q in range(5):
         assert np.abs(Wt.numpy()[q] - Wo[q]).max() < 1e-14 * np.abs(Wo[q]).max()
