@@ -9,7 +9,10 @@ Scope: third-order reconstruction with linear weights (R = P^2 = M2 d, Sec.
 two-step construction from the neighbours' P1 slopes), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
 Eq. new-equ-part) or the smooth one (Eq. 2nd-smooth-flux), Euler (tau = 0) or
 Navier-Stokes (tau = mu / p_c, Sec. 2.2) with the heat-flux correction for a
-Prandtl number other than 1 (the reading of the oracle), periodic meshes,
+Prandtl number other than 1 (the reading of the oracle), periodic meshes or
+boundary faces that are open, slip or non-slip walls or fixed (Sec. 4.4 and
+the oracle's readings: one-sided stencils, the linear-weight boundary cells'
+least-squares first-order fit, the ghosts at the Gauss points),
 the S2O4 step of Sec. 3 with the linear flux fit (Eqs. linear-system, s2o4)
 and the cell-averaged gradients from the divergence theorem (Eq.
 gauss-formula).  Geometry, connectivity and the stencil operators M2 come
@@ -205,11 +208,16 @@ def _frame(n):
     return torch.stack([n, t1, t2], dim=1)
 
 
+OPEN, SLIP, FIXED, NOSLIP = 0, 1, 2, 3
+
+
 class Step:
-    """One step on an oracle mesh (periodic), linear weights."""
+    """One step on an oracle mesh.  kinds[nc][4]: boundary kind per local face
+    (read on boundary faces); fixed = (W [5, nc], dW [15, nc]) the state that
+    fixed faces hold."""
 
     def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0,
-                 weno=False, eps=1e-8):
+                 weno=False, eps=1e-8, kinds=None, fixed=None):
         geo, top = om.geometry(), om.topology()
         M1, M2 = om.stencils()
         self.weno, self.eps = weno, eps
@@ -221,8 +229,27 @@ class Step:
         self.nbr = torch.as_tensor(top["nbr"])
         self.M2 = t(M2)
         self.M1 = t(M1)
-        if (self.nbr < 0).any():
-            raise ValueError("periodic meshes only")
+        nc, nf = self.vol.shape[0], self.n.shape[0]
+        # boundary faces: the kind of each (from the interior cell's local face)
+        self.fkind = torch.full((nf,), -1, dtype=torch.int64)
+        csr_face, csr_sign = top["csr_face"], top["csr_sign"]
+        nbr = top["nbr"]
+        if (nbr < 0).any():
+            kinds = np.zeros((nc, 4), np.int64) if kinds is None else np.asarray(kinds).reshape(nc, 4)
+            cells, lf = np.nonzero(nbr < 0)
+            self.fkind[torch.as_tensor(csr_face[cells, lf])] = torch.as_tensor(kinds[cells, lf].astype(np.int64))
+        self.bcell = torch.as_tensor((nbr < 0).any(axis=1))
+        self.nmask = torch.as_tensor(nbr >= 0, dtype=torch.float64)        # [nc, 4]
+        self.nbr_safe = torch.where(self.nbr >= 0, self.nbr, torch.arange(nc)[:, None])
+        # centroid offsets to the neighbours (periodic images from the face geometry)
+        off = np.zeros((nc, 4, 3))
+        gl, gr = geo["gp_l"][:, 0], geo["gp_r"][:, 0]
+        for f in range(4):
+            fi = csr_face[:, f]
+            d = np.where((csr_sign[:, f] > 0)[:, None], gl[fi] - gr[fi], gr[fi] - gl[fi])
+            off[:, f] = np.where((nbr[:, f] >= 0)[:, None], d, 0.0)
+        self.off = t(off)
+        self.fixed = None if fixed is None else (t(fixed[0]).T, t(fixed[1]).T.reshape(-1, 5, 3))
         self.R = _frame(self.n)
         self.kw = dict(gamma=gamma, tau_eps=tau_eps, tau_c=tau_c, mu=mu, viscous=viscous, smooth=smooth,
                        prandtl=prandtl)
@@ -231,14 +258,28 @@ class Step:
         """R's coefficients a in the zero-mean basis per cell and component,
         [nc, 5, 9]: P2 = M2 d (linear weights), or the WENO combination"""
         Q0 = W.T                                   # [nc, 5]
-        Qn = W.T[self.nbr]                         # [nc, 4, 5]
-        G = dW.T.reshape(-1, 5, 3)[self.nbr]       # [nc, 4, 5, 3]
-        dq = (Qn - Q0[:, None, :]).permute(0, 2, 1)                                   # [nc, 5, 4]
+        m = self.nmask
+        Qn = W.T[self.nbr_safe]                    # [nc, 4, 5] (a missing neighbour reads the cell itself)
+        G = dW.T.reshape(-1, 5, 3)[self.nbr_safe] * m[:, :, None, None]                 # [nc, 4, 5, 3]
+        dq = ((Qn - Q0[:, None, :]) * m[:, :, None]).permute(0, 2, 1)                   # [nc, 5, 4]
         d = torch.cat([dq, G.permute(0, 2, 1, 3).reshape(-1, 5, 12)], dim=2)          # [nc, 5, 16]
         a = torch.einsum("ckj,cqj->cqk", self.M2, d)
         if not self.weno:
+            if self.bcell.any():
+                a = torch.where(self.bcell[:, None, None], self._linear_fit(dq, G), a)
             return a, Q0
         return self._weno(a, dq), Q0
+
+    def _linear_fit(self, dq, G):
+        """Sec. 4.4 with linear weights: a boundary cell's first-order
+        least-squares fit to its neighbours' averages (d_r . b = dQ_r) and
+        averaged gradients (h0 b = h0 grad Q_r), [nc, 5, 9]"""
+        h2 = self.vol ** (2.0 / 3.0)
+        m, off = self.nmask, self.off
+        A = torch.einsum("cr,cri,crj->cij", m, off, off) + (m.sum(1) * h2)[:, None, None] * torch.eye(3)
+        rhs = torch.einsum("cri,cqr->cqi", off, dq) + h2[:, None, None] * G.sum(1)      # [nc, 5, 3]
+        b = torch.linalg.solve(A[:, None], rhs[..., None])[..., 0]
+        return torch.cat([b, torch.zeros(b.shape[0], 5, 6, dtype=b.dtype)], dim=2)
 
     def _weno(self, a, dq):
         """Sec. 4.2-4.3: smoothness indicators of P1 (slopes b = M1 dQ), P2 and
@@ -249,13 +290,16 @@ class Step:
         v = self.vol[:, None]
         b = torch.einsum("cij,cqj->cqi", self.M1, dq)                                   # [nc, 5, 3]
         beta1 = v ** (2.0 / 3.0) * (b * b).sum(2)
-        b0j = v[:, :, None] ** (2.0 / 3.0) * (b[self.nbr] * b[self.nbr]).sum(3).permute(0, 2, 1)  # [nc, 5, 4]
-        pair = 0.0
+        bn = b[self.nbr_safe]
+        m = self.nmask[:, None, :]                                                     # [nc, 1, 4]
+        b0j = v[:, :, None] ** (2.0 / 3.0) * (bn * bn).sum(3).permute(0, 2, 1)          # [nc, 5, 4]
+        pair, npair = 0.0, 0.0
         for j in range(4):
             for k in range(j):
-                pair = pair + torch.abs(b0j[:, :, j] - b0j[:, :, k])
-        s1 = (pair / 6.0) ** (4.0 / 3.0)
-        w1 = 1.0 + s1[:, :, None] / (eps + b0j)
+                pair = pair + m[:, :, j] * m[:, :, k] * torch.abs(b0j[:, :, j] - b0j[:, :, k])
+                npair = npair + m[:, :, j] * m[:, :, k]
+        s1 = (pair / npair) ** (4.0 / 3.0)
+        w1 = m * (1.0 + s1[:, :, None] / (eps + b0j))
         beta0 = (w1 * b0j).sum(2) / w1.sum(2)
         # beta_2 from the exact integrals of the quadratic over the cell
         lin = a[:, :, :3]
@@ -307,13 +351,52 @@ class Step:
         """per face: sum_k w_k of Fh, F, W(0) n, W(dt) n (global frame)"""
         a, Q0 = self._recon(W, dW)
         L, Rr = self.lr[:, 0], self.lr[:, 1]
+        Ls, Rs = torch.where(L >= 0, L, Rr), torch.where(Rr >= 0, Rr, L)   # a missing side starts as the other
+        kind = self.fkind
         w = self.area / 3.0
         out = [0.0, 0.0, 0.0, 0.0]
         for k in range(3):
-            vl, gl = self._eval(a, Q0, L, self.gpl[:, k])
-            vr, gr = self._eval(a, Q0, Rr, self.gpr[:, k])
+            XL = torch.where((L >= 0)[:, None], self.gpl[:, k], self.gpr[:, k])
+            XR = torch.where((Rr >= 0)[:, None], self.gpr[:, k], self.gpl[:, k])
+            vl, gl = self._eval(a, Q0, Ls, XL)
+            vr, gr = self._eval(a, Q0, Rs, XR)
             Wl, gll = self._to_local(self.R, vl, gl)
             Wr, grl = self._to_local(self.R, vr, gr)
+            sides = [[Wl, gll], [Wr, grl]]
+            for side, missing in ((0, L < 0), (1, Rr < 0)):
+                if not missing.any():
+                    continue
+                inner = Rs if side == 0 else Ls
+                Xi = XR if side == 0 else XL
+                Wg, gg = sides[side]
+                # open: the interior cell's average with zero gradient
+                ow, og = self._to_local(self.R, Q0[inner], torch.zeros_like(gg))
+                sel = (missing & (kind == OPEN))[:, None]
+                Wg = torch.where(sel, ow, Wg)
+                gg = torch.where(sel[:, :, None], og, gg)
+                if self.fixed is not None:
+                    fW, fg = self.fixed[0][inner], self.fixed[1][inner].permute(0, 2, 1)   # [F, 5], [F, 3, 5]
+                    fw, fgl = self._to_local(self.R, fW + torch.einsum("fiq,fi->fq", fg, Xi), fg)
+                    sel = (missing & (kind == FIXED))[:, None]
+                    Wg = torch.where(sel, fw, Wg)
+                    gg = torch.where(sel[:, :, None], fgl, gg)
+                # slip wall (face frame): rho U1 reversed; x1-derivatives reversed
+                # except that of rho U1; x2-, x3-derivatives of rho U1 reversed
+                sw = torch.tensor([1.0, -1.0, 1.0, 1.0, 1.0], dtype=Wg.dtype)
+                sg = torch.tensor([[-1.0, 1.0, -1.0, -1.0, -1.0], [1.0, -1.0, 1.0, 1.0, 1.0],
+                                   [1.0, -1.0, 1.0, 1.0, 1.0]], dtype=Wg.dtype)
+                sel = (missing & (kind == SLIP))[:, None]
+                Wg = torch.where(sel, Wg * sw, Wg)
+                gg = torch.where(sel[:, :, None], gg * sg, gg)
+                # non-slip wall at rest: momenta reversed, their derivatives kept;
+                # every derivative of rho and rho E reversed
+                nw = torch.tensor([1.0, -1.0, -1.0, -1.0, 1.0], dtype=Wg.dtype)
+                ng = torch.tensor([-1.0, 1.0, 1.0, 1.0, -1.0], dtype=Wg.dtype)
+                sel = (missing & (kind == NOSLIP))[:, None]
+                Wg = torch.where(sel, Wg * nw, Wg)
+                gg = torch.where(sel[:, :, None], gg * ng, gg)
+                sides[side] = [Wg, gg]
+            (Wl, gll), (Wr, grl) = sides
             Fh, F, W0, Wt = point_flux(Wl, gll, Wr, grl, dt, **self.kw)
             res = [self._to_global(self.R, x) for x in (Fh, F, W0, Wt)]
             for j in range(4):
@@ -325,8 +408,9 @@ class Step:
         nc = self.vol.shape[0]
         shape = (nc,) + tuple(per_face.shape[1:])
         out = torch.zeros(shape, dtype=per_face.dtype)
-        out = out.index_add(0, self.lr[:, 0], per_face)
-        return out.index_add(0, self.lr[:, 1], -per_face)
+        L, R = self.lr[:, 0], self.lr[:, 1]
+        out = out.index_add(0, L[L >= 0], per_face[L >= 0])
+        return out.index_add(0, R[R >= 0], -per_face[R >= 0])
 
     def __call__(self, W, dW, dt):
         """(W [5, nc], dW [15, nc]) -> (W^{n+1}, grad W^{n+1}) with the step dt"""

@@ -263,13 +263,16 @@ def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
 
 @pytest.mark.parametrize("state,weno,viscous,smooth,prandtl", [
     ("sine", 0, 0, 0, 1.0), ("sine", 0, 1, 0, 1.0), ("sine", 0, 1, 1, 1.0), ("sine", 0, 1, 0, 0.72),
-    ("sine", 0, 0, 1, 1.0), ("sine", 1, 0, 0, 1.0), ("sine", 1, 1, 0, 0.72), ("slab", 1, 0, 0, 1.0)])
+    ("sine", 0, 0, 1, 1.0), ("sine", 1, 0, 0, 1.0), ("sine", 1, 1, 0, 0.72), ("slab", 1, 0, 0, 1.0),
+    ("open", 0, 0, 0, 1.0), ("open", 1, 0, 0, 1.0), ("slip", 1, 0, 0, 1.0), ("noslip", 0, 1, 0, 1.0),
+    ("noslip", 1, 1, 0, 0.72), ("fixed", 1, 0, 0, 1.0), ("fixed", 0, 1, 0, 1.0)])
 def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscous, smooth, prandtl):
     """The adjoint against an FP64 CPU reverse sweep: torch.autograd through
     the plain-PyTorch restatement of the step (oracle/torch_step.py, itself
     pinned to the C oracle's step), linear or WENO weights, full or smooth
     flux, Euler or Navier-Stokes with the Pr fix, periodic meshes (the
-    density wave and the moving slab).  Both are exact derivatives, so they
+    density wave and the moving slab) and boxes with open, wall or fixed
+    ends (the fixed state set apart).  Both are exact derivatives, so they
     agree to rounding, every entry of d J / d (W, grad W)."""
     import torch
     from oracle import torch_step as TS
@@ -277,6 +280,11 @@ def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscou
     g = gks.Mesh(mesh)
     kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, weno=weno)
     s = gks.State(g, gks.params(precision=0, cfl=0.5, **kw))
+    fixed = None
+    if state == "fixed":
+        fixed = (W * (1.0 + 0.02 * rng.standard_normal(W.shape)), 0.5 * dW)
+        s.set_fixed_state(*fixed)
+        mesh["fixed_state"] = fixed
     o = oracle_mod.Mesh(mesh)
     dt = 0.5 * o.timestep(oracle_mod.params(cfl=0.5, **kw), W)
     lam = (rng.standard_normal(W.shape), rng.standard_normal(dW.shape))
@@ -284,7 +292,7 @@ def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscou
     Wt = torch.tensor(W, requires_grad=True)
     dWt = torch.tensor(dW, requires_grad=True)
     Wn, dWn = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl,
-                      weno=bool(weno))(Wt, dWt, dt)
+                      weno=bool(weno), kinds=mesh.get("bkind"), fixed=fixed)(Wt, dWt, dt)
     ((Wn * torch.tensor(lam[0])).sum() + (dWn * torch.tensor(lam[1])).sum()).backward()
     for gpu, cpu in ((lW.cpu().numpy(), Wt.grad.numpy()), (ldW.cpu().numpy(), dWt.grad.numpy())):
         assert np.abs(gpu - cpu).max() < 1e-11 * np.abs(cpu).max(), np.abs(gpu - cpu).max() / np.abs(cpu).max()

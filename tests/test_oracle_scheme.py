@@ -206,27 +206,41 @@ def test_open_boundary_is_stable(oracle_mod):
     assert np.abs(W - W0).max() < 1e-3
 
 
-@pytest.mark.parametrize("weno,viscous,smooth,prandtl", [(0, 0, 0, 1.0), (0, 0, 1, 1.0), (0, 1, 0, 1.0),
-                                                        (0, 1, 1, 1.0), (0, 1, 0, 0.72), (1, 0, 0, 1.0),
-                                                        (1, 1, 0, 0.72)])
-def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, smooth, prandtl):
+@pytest.mark.parametrize("weno,viscous,smooth,prandtl,ends", [
+    (0, 0, 0, 1.0, None), (0, 0, 1, 1.0, None), (0, 1, 0, 1.0, None), (0, 1, 1, 1.0, None), (0, 1, 0, 0.72, None),
+    (1, 0, 0, 1.0, None), (1, 1, 0, 0.72, None), (0, 0, 0, 1.0, "open"), (1, 0, 0, 1.0, "slip"),
+    (0, 1, 0, 1.0, "noslip"), (1, 1, 0, 0.72, "noslip"), (1, 0, 0, 1.0, "fixed"), (0, 1, 0, 1.0, "fixed")])
+def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, smooth, prandtl, ends):
     """oracle/torch_step.py (the step in plain PyTorch CPU operations, for the
     autograd reverse sweep that checks the library's adjoint) reproduces the
-    C oracle's step on a jittered periodic mesh: linear or WENO weights,
-    full or smooth flux, Euler or Navier-Stokes, with the Pr fix."""
+    C oracle's step on a jittered mesh: linear or WENO weights, full or
+    smooth flux, Euler or Navier-Stokes, with the Pr fix; periodic, or with
+    open, slip-wall, non-slip-wall or fixed x ends."""
     import torch
     from oracle import torch_step as TS
-    mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=61)
-    W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
     rng = np.random.Generator(np.random.PCG64(61))
+    fixed = None
+    if ends is None:
+        mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=61)
+        W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
+    else:
+        mesh = I.box_mesh((4, 3, 3), (1.0, 0.75, 0.75), (False, True, True), jitter=0.1, seed=61)
+        if ends != "open":
+            kind = {"slip": I.BC_SLIP_WALL, "noslip": I.BC_NOSLIP_WALL, "fixed": I.BC_FIXED}[ends]
+            mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
+        W, dW = I.sine_wave_state(mesh, k=8.0 * math.pi / 3.0, u=(0.6, 0.5, -0.3))
     W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
     dW = dW + 0.05 * rng.standard_normal(dW.shape)
+    if ends == "fixed":
+        fixed = (W * (1.0 + 0.02 * rng.standard_normal(W.shape)), 0.5 * dW)
+        mesh["fixed_state"] = fixed
     o = oracle_mod.Mesh(mesh)
     kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl)
     p = oracle_mod.params(weno=weno, cfl=0.5, **kw)
     dt = 0.5 * o.timestep(p, W)
     Wo, dWo, _ = o.step(p, W, dW, dt)
-    st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl, weno=bool(weno))
+    st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl, weno=bool(weno),
+                 kinds=mesh.get("bkind"), fixed=fixed)
     Wt, dWt = st(torch.tensor(W), torch.tensor(dW), dt)
     for q in range(5):
         assert np.abs(Wt.numpy()[q] - Wo[q]).max() < 1e-14 * np.abs(Wo[q]).max()
