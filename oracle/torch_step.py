@@ -6,7 +6,9 @@ the library's adjoint (gks_adjoint_step); nothing in the product imports it.
 
 Scope: third-order reconstruction with linear weights (R = P^2 = M2 d, Sec.
 4.1) or the multi-resolution WENO weights of Sec. 4.2-4.3 (beta_0 by the
-two-step construction from the neighbours' P1 slopes), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
+two-step construction from the neighbours' P1 slopes), or the second-order
+one (Eq. final_weno_expression-2nd), with the Gauss-point positivity check
+that falls back to the cell average (reading R9), the full gas-kinetic solver (Eq. 2nd-flux with the equilibrium state of
 Eq. new-equ-part) or the smooth one (Eq. 2nd-smooth-flux), Euler (tau = 0) or
 Navier-Stokes (tau = mu / p_c, Sec. 2.2) with the heat-flux correction for a
 Prandtl number other than 1 (the reading of the oracle), periodic meshes or
@@ -217,10 +219,10 @@ class Step:
     fixed faces hold."""
 
     def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0,
-                 weno=False, eps=1e-8, kinds=None, fixed=None):
+                 weno=False, eps=1e-8, kinds=None, fixed=None, order=3):
         geo, top = om.geometry(), om.topology()
         M1, M2 = om.stencils()
-        self.weno, self.eps = weno, eps
+        self.weno, self.eps, self.order = weno, eps, order
         t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
         self.vol, self.mom = t(geo["vol"]), t(geo["mom2"])
         self.area, self.n = t(geo["farea"]), t(geo["fnorm"])
@@ -249,6 +251,12 @@ class Step:
             d = np.where((csr_sign[:, f] > 0)[:, None], gl[fi] - gr[fi], gr[fi] - gl[fi])
             off[:, f] = np.where((nbr[:, f] >= 0)[:, None], d, 0.0)
         self.off = t(off)
+        # each cell's own Gauss points (offsets from its centroid), [nc, 12, 3]
+        own = np.zeros((nc, 4, 3, 3))
+        for f in range(4):
+            fi = csr_face[:, f]
+            own[:, f] = np.where((csr_sign[:, f] > 0)[:, None, None], geo["gp_l"][fi], geo["gp_r"][fi])
+        self.gp_own = t(own.reshape(nc, 12, 3))
         self.fixed = None if fixed is None else (t(fixed[0]).T, t(fixed[1]).T.reshape(-1, 5, 3))
         self.R = _frame(self.n)
         self.kw = dict(gamma=gamma, tau_eps=tau_eps, tau_c=tau_c, mu=mu, viscous=viscous, smooth=smooth,
@@ -264,11 +272,29 @@ class Step:
         dq = ((Qn - Q0[:, None, :]) * m[:, :, None]).permute(0, 2, 1)                   # [nc, 5, 4]
         d = torch.cat([dq, G.permute(0, 2, 1, 3).reshape(-1, 5, 12)], dim=2)          # [nc, 5, 16]
         a = torch.einsum("ckj,cqj->cqk", self.M2, d)
-        if not self.weno:
-            if self.bcell.any():
-                a = torch.where(self.bcell[:, None, None], self._linear_fit(dq, G), a)
-            return a, Q0
-        return self._weno(a, dq), Q0
+        if self.weno:
+            a = self._weno(a, dq)
+        elif self.order == 2:  # R = P1
+            b = torch.einsum("cij,cqj->cqi", self.M1, dq)
+            a = torch.cat([b, torch.zeros_like(a[:, :, 3:])], dim=2)
+        elif self.bcell.any():
+            a = torch.where(self.bcell[:, None, None], self._linear_fit(dq, G), a)
+        return self._positivity(a, Q0), Q0
+
+    def _positivity(self, a, Q0):
+        """R at the cell's 12 face Gauss points; a negative density or
+        pressure at any of them makes the cell constant (R = P0, all
+        components; a decision, not differentiated)"""
+        with torch.no_grad():
+            X = self.gp_own                                                    # [nc, 12, 3]
+            val = Q0[:, None, :] + torch.einsum("cqk,cgk->cgq", a[:, :, :3], X)
+            for q, (i, j) in enumerate(PAIRS):
+                val = val + a[:, None, :, 3 + q] * (X[:, :, i] * X[:, :, j] - self.mom[:, q][:, None])[:, :, None]
+            rho = val[:, :, 0]
+            pres = (self.kw["gamma"] - 1.0) * (val[:, :, 4] - 0.5 * (val[:, :, 1:4] ** 2).sum(2) / rho)
+            bad = ((rho <= 0.0) | (pres <= 0.0)).any(dim=1)
+        self.fallbacks.append(bad)
+        return torch.where(bad[:, None, None], torch.zeros_like(a), a)
 
     def _linear_fit(self, dq, G):
         """Sec. 4.4 with linear weights: a boundary cell's first-order
@@ -301,6 +327,14 @@ class Step:
         s1 = (pair / npair) ** (4.0 / 3.0)
         w1 = m * (1.0 + s1[:, :, None] / (eps + b0j))
         beta0 = (w1 * b0j).sum(2) / w1.sum(2)
+        g11, g01 = 10.0 / 11.0, 1.0 / 11.0
+        if self.order == 2:
+            # R^2nd = w1 p1 + w0 p0, sigma = |beta_1 - beta_0|^{4/3}
+            sigma = torch.abs(beta1 - beta0) ** (4.0 / 3.0)
+            w0 = g01 * (1.0 + (sigma / (eps + beta0)) ** 2)
+            w1_ = g11 * (1.0 + (sigma / (eps + beta1)) ** 2)
+            p1 = torch.cat([b / g11, torch.zeros_like(a[:, :, 3:])], dim=2)
+            return (w1_ / (w0 + w1_))[:, :, None] * p1
         # beta_2 from the exact integrals of the quadratic over the cell
         lin = a[:, :, :3]
         H = torch.zeros(a.shape[0], 5, 3, 3, dtype=a.dtype)
@@ -318,7 +352,6 @@ class Step:
         g2, g1, g0 = 100.0 / 111.0, 10.0 / 111.0, 1.0 / 111.0
         w = [g * (1.0 + (sigma / (eps + beta)) ** 2) for g, beta in ((g0, beta0), (g1, beta1), (g2, beta2))]
         ws = w[0] + w[1] + w[2]
-        g11, g01 = 10.0 / 11.0, 1.0 / 11.0
         # p0 = Q0, p1 = (P1 - g01 P0) / g11, p2 = (P2 - g1 p1 - g0 p0) / g2; the constants all Q0
         p1 = torch.cat([b / g11, torch.zeros_like(a[:, :, 3:])], dim=2)
         p2 = (a - g1 * p1) / g2
@@ -416,6 +449,7 @@ class Step:
         """(W [5, nc], dW [15, nc]) -> (W^{n+1}, grad W^{n+1}) with the step dt"""
         n = self.n
         vol = self.vol[:, None]
+        self.fallbacks = []  # the positivity decisions of the two stages
         Fh, F, W0, Wt = self._faces(W, dW, dt)
         Ws = W.T - self._cell_sum(Fh) / vol
         half = 0.5 * (W0 + Wt)

@@ -265,20 +265,28 @@ def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
     ("sine", 0, 0, 0, 1.0), ("sine", 0, 1, 0, 1.0), ("sine", 0, 1, 1, 1.0), ("sine", 0, 1, 0, 0.72),
     ("sine", 0, 0, 1, 1.0), ("sine", 1, 0, 0, 1.0), ("sine", 1, 1, 0, 0.72), ("slab", 1, 0, 0, 1.0),
     ("open", 0, 0, 0, 1.0), ("open", 1, 0, 0, 1.0), ("slip", 1, 0, 0, 1.0), ("noslip", 0, 1, 0, 1.0),
-    ("noslip", 1, 1, 0, 0.72), ("fixed", 1, 0, 0, 1.0), ("fixed", 0, 1, 0, 1.0)])
+    ("noslip", 1, 1, 0, 0.72), ("fixed", 1, 0, 0, 1.0), ("fixed", 0, 1, 0, 1.0), ("sine-o2", 0, 0, 0, 1.0),
+    ("sine-o2", 1, 0, 0, 1.0), ("slab-o2", 1, 0, 0, 1.0), ("sine-lowp", 0, 0, 0, 1.0),
+    ("sine-lowp", 1, 0, 0, 1.0)])
 def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscous, smooth, prandtl):
     """The adjoint against an FP64 CPU reverse sweep: torch.autograd through
     the plain-PyTorch restatement of the step (oracle/torch_step.py, itself
     pinned to the C oracle's step), linear or WENO weights, full or smooth
     flux, Euler or Navier-Stokes with the Pr fix, periodic meshes (the
     density wave and the moving slab) and boxes with open, wall or fixed
-    ends (the fixed state set apart).  Both are exact derivatives, so they
-    agree to rounding, every entry of d J / d (W, grad W)."""
+    ends (the fixed state set apart); the second-order R ("-o2") and a cell
+    that falls back to its average ("-lowp").  Both are exact derivatives,
+    so they agree to rounding, every entry of d J / d (W, grad W)."""
     import torch
     from oracle import torch_step as TS
-    mesh, W, dW, rng = _case(state=state)
+    base, _, variant = state.partition("-")
+    mesh, W, dW, rng = _case(state=base)
+    order = 2 if variant == "o2" else 3
+    if variant == "lowp":
+        W = W.copy()
+        W[4, 0] = 0.5 * (W[1, 0] ** 2 + W[2, 0] ** 2 + W[3, 0] ** 2) / W[0, 0] + 0.05 / 0.4
     g = gks.Mesh(mesh)
-    kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, weno=weno)
+    kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, weno=weno, order=order)
     s = gks.State(g, gks.params(precision=0, cfl=0.5, **kw))
     fixed = None
     if state == "fixed":
@@ -291,11 +299,17 @@ def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscou
     lW, ldW = s.adjoint_step(torch.tensor(W), torch.tensor(dW), torch.tensor(lam[0]), torch.tensor(lam[1]), dt)
     Wt = torch.tensor(W, requires_grad=True)
     dWt = torch.tensor(dW, requires_grad=True)
-    Wn, dWn = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl,
-                      weno=bool(weno), kinds=mesh.get("bkind"), fixed=fixed)(Wt, dWt, dt)
+    st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl,
+                 weno=bool(weno), kinds=mesh.get("bkind"), fixed=fixed, order=order)
+    Wn, dWn = st(Wt, dWt, dt)
+    if variant == "lowp":
+        assert st.fallbacks[0][0]
     ((Wn * torch.tensor(lam[0])).sum() + (dWn * torch.tensor(lam[1])).sum()).backward()
-    for gpu, cpu in ((lW.cpu().numpy(), Wt.grad.numpy()), (ldW.cpu().numpy(), dWt.grad.numpy())):
-        assert np.abs(gpu - cpu).max() < 1e-11 * np.abs(cpu).max(), np.abs(gpu - cpu).max() / np.abs(cpu).max()
+    # (the second-order R reads no gradients: the step then does not depend on grad W at all)
+    cpu_dW = dWt.grad.numpy() if dWt.grad is not None else np.zeros_like(dW)
+    for gpu, cpu in ((lW.cpu().numpy(), Wt.grad.numpy()), (ldW.cpu().numpy(), cpu_dW)):
+        scale = np.abs(cpu).max() if np.abs(cpu).any() else np.abs(lW.cpu().numpy()).max()
+        assert np.abs(gpu - cpu).max() < 1e-11 * scale, np.abs(gpu - cpu).max() / scale
 
 
 def test_kinetic_energy_gradient_through_three_steps(cuda, oracle_mod):
@@ -361,7 +375,7 @@ def test_unsupported_configurations_are_rejected(cuda):
 @pytest.mark.parametrize("weno", [0, 1])
 def test_positivity_fallback_cell(cuda, oracle_mod, weno):
     """A low-pressure cell (p = 0.05 among p ~ 1) whose reconstruction falls
-    back to its average in both stages (the positivity branch): its
+    back to its average in the first stage (the positivity branch): its
     adjoint passes the constant's adjoint to its own average only.  The
     fallback decision holds under the differences' perturbations (checked),
     so central differences of the GPU and of the oracle forward map pin the

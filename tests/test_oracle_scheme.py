@@ -209,7 +209,8 @@ def test_open_boundary_is_stable(oracle_mod):
 @pytest.mark.parametrize("weno,viscous,smooth,prandtl,ends", [
     (0, 0, 0, 1.0, None), (0, 0, 1, 1.0, None), (0, 1, 0, 1.0, None), (0, 1, 1, 1.0, None), (0, 1, 0, 0.72, None),
     (1, 0, 0, 1.0, None), (1, 1, 0, 0.72, None), (0, 0, 0, 1.0, "open"), (1, 0, 0, 1.0, "slip"),
-    (0, 1, 0, 1.0, "noslip"), (1, 1, 0, 0.72, "noslip"), (1, 0, 0, 1.0, "fixed"), (0, 1, 0, 1.0, "fixed")])
+    (0, 1, 0, 1.0, "noslip"), (1, 1, 0, 0.72, "noslip"), (1, 0, 0, 1.0, "fixed"), (0, 1, 0, 1.0, "fixed"),
+    (0, 0, 0, 1.0, "order2"), (1, 0, 0, 1.0, "order2"), (0, 0, 0, 1.0, "lowp"), (1, 0, 0, 1.0, "lowp")])
 def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, smooth, prandtl, ends):
     """oracle/torch_step.py (the step in plain PyTorch CPU operations, for the
     autograd reverse sweep that checks the library's adjoint) reproduces the
@@ -220,7 +221,8 @@ def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, sm
     from oracle import torch_step as TS
     rng = np.random.Generator(np.random.PCG64(61))
     fixed = None
-    if ends is None:
+    order = 2 if ends == "order2" else 3
+    if ends in (None, "order2", "lowp"):
         mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=61)
         W, dW = I.sine_wave_state(mesh, u=(0.8, 0.5, -0.3))
     else:
@@ -231,17 +233,20 @@ def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, sm
         W, dW = I.sine_wave_state(mesh, k=8.0 * math.pi / 3.0, u=(0.6, 0.5, -0.3))
     W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
     dW = dW + 0.05 * rng.standard_normal(dW.shape)
+    if ends == "lowp":  # a low-pressure cell whose reconstruction falls back to its average
+        W[4, 0] = 0.5 * (W[1, 0] ** 2 + W[2, 0] ** 2 + W[3, 0] ** 2) / W[0, 0] + 0.05 / 0.4
     if ends == "fixed":
         fixed = (W * (1.0 + 0.02 * rng.standard_normal(W.shape)), 0.5 * dW)
         mesh["fixed_state"] = fixed
     o = oracle_mod.Mesh(mesh)
     kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl)
-    p = oracle_mod.params(weno=weno, cfl=0.5, **kw)
+    p = oracle_mod.params(weno=weno, order=order, cfl=0.5, **kw)
     dt = 0.5 * o.timestep(p, W)
     Wo, dWo, _ = o.step(p, W, dW, dt)
     st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl, weno=bool(weno),
-                 kinds=mesh.get("bkind"), fixed=fixed)
+                 kinds=mesh.get("bkind"), fixed=fixed, order=order)
     Wt, dWt = st(torch.tensor(W), torch.tensor(dW), dt)
+    assert bool(st.fallbacks[0].any()) == (ends == "lowp")
     for q in range(5):
         assert np.abs(Wt.numpy()[q] - Wo[q]).max() < 1e-14 * np.abs(Wo[q]).max()
         ref = dWo[3 * q:3 * q + 3]
