@@ -65,6 +65,7 @@ typedef struct gks_params {
     double tau_c;        /* C of the numerical collision time, Sec. 2.2 (1) */
     double prandtl;      /* Prandtl number of the viscous solver (BGK gives 1; other
                             values correct the heat flux, Pr fix below); 1 default */
+    double wall_temperature; /* T = p / rho of GKS_BC_ISOTHERMAL_WALL faces; 1 default */
     int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2; at order 3 a
                             boundary cell takes the least-squares first-order fit to
                             its P2 stencil's data, Sec. 4.4); 1: nonlinear */
@@ -152,11 +153,20 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
  *                     kept, all derivatives of rho and rho E reversed
  *                     (impermeable, no heat flux; the wall shear comes from
  *                     the viscous solver, params.viscous = 1)
+ *   GKS_BC_ISOTHERMAL_WALL Sec. 4.4 non-slip isothermal wall at rest: the
+ *                     ghost has the interior pressure, the reversed velocity
+ *                     and the temperature 2 T_w - T (T = p / rho,
+ *                     params.wall_temperature = T_w); the derivatives of the
+ *                     velocity and the temperature are kept, that of the
+ *                     pressure reversed (through the chain rule back to the
+ *                     conservative derivatives).  Not differentiated by
+ *                     gks_adjoint_step.
  * The interior reconstruction of a boundary cell is the one-sided one of
  * Sec. 4.4 without constraint rows (for the non-slip wall the paper adds the
  * wall velocity as a constraint; this library does not): the cell's stencil
  * simply lacks the missing neighbour. */
-enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2, GKS_BC_NOSLIP_WALL = 3 };
+enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2, GKS_BC_NOSLIP_WALL = 3,
+       GKS_BC_ISOTHERMAL_WALL = 4 };
 
 /* kind[n_cell][4] (host): the condition of local face f (the face opposite
  * tet vertex f) of each cell, read only where that face is a boundary face.
@@ -330,8 +340,8 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * Supported: FP64 states (precision 0) with the third- or second-order
  * reconstruction with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
- * meshes, periodic or with open, slip-wall, non-slip-wall or fixed-state
- * boundary faces (the last only with a fixed state set by
+ * meshes, periodic or with open, slip-wall, non-slip (adiabatic) wall or
+ * fixed-state boundary faces (the last only with a fixed state set by
  * gks_set_fixed_state: it is then a constant of the step), any Prandtl
  * number; GKS_E_UNSUPPORTED otherwise.  A cell that
  * falls back to its average (the positivity check of Sec. 4.3) passes the

@@ -546,7 +546,8 @@ int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
         for (int f = 0; f < 4; ++f) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             int8_t k = kind[c * 4 + f];
-            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED && k != ORA_BC_NOSLIP_WALL)
+            if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED && k != ORA_BC_NOSLIP_WALL &&
+                k != ORA_BC_ISOTHERMAL_WALL)
                 return -1;
             m->bkind[m->csr_face[c * 4 + f]] = k;
         }
@@ -1204,6 +1205,40 @@ double ora_s2o4_linear_ode(double z) {
 /* face records                                                             */
 /* ------------------------------------------------------------------------ */
 
+/* Sec. 4.4, non-slip isothermal wall at rest, in the face frame (gas
+ * constant R = 1, T = p / rho), following the paper's steps: the ghost keeps
+ * the pressure, reverses the velocity and takes T = 2 T_wall - T; for its
+ * derivatives, the interior's primitive derivatives (dU_i from d(rho U_i)
+ * and d rho; dp from d(rho E), d rho and dQ with Q = |U|^2 / 2; dT from dp
+ * and d rho) are taken with dU and dT kept and dp reversed, then turned
+ * back into conservative derivatives of the ghost (d rho from dp and dT,
+ * d(rho U_i), d(rho E)). */
+static void isothermal_ghost(double W[5], double g[3][5], double gamma, double Tw) {
+    double rho = W[0], U[3], Q = 0.0;
+    for (int i = 0; i < 3; ++i) { U[i] = W[1 + i] / rho; Q += 0.5 * U[i] * U[i]; }
+    double p = (gamma - 1.0) * (W[4] - rho * Q);
+    double Tr = p / rho;
+    double Tl = 2.0 * Tw - Tr;
+    double rl = p / Tl;
+    double Ul[3] = {-U[0], -U[1], -U[2]};
+    double Wl[5] = {rl, rl * Ul[0], rl * Ul[1], rl * Ul[2], p / (gamma - 1.0) + rl * Q};
+    for (int j = 0; j < 3; ++j) {
+        /* interior primitive derivatives along x_j */
+        double dU[3], dQ = 0.0;
+        for (int i = 0; i < 3; ++i) { dU[i] = (g[j][1 + i] - g[j][0] * U[i]) / rho; dQ += U[i] * dU[i]; }
+        double dp = (gamma - 1.0) * (g[j][4] - g[j][0] * Q - dQ * rho);
+        double dT = (dp - g[j][0] * Tr) / rho;
+        /* the ghost's: dU, dT kept, dp reversed */
+        double dpl = -dp, dTl = dT, dQl = 0.0;
+        for (int i = 0; i < 3; ++i) dQl += dU[i] * Ul[i];
+        double drl = (dpl - dTl * rl) / Tl;
+        g[j][0] = drl;
+        for (int i = 0; i < 3; ++i) g[j][1 + i] = drl * Ul[i] + dU[i] * rl;
+        g[j][4] = drl * Q + dQl * rl + dpl / (gamma - 1.0);
+    }
+    for (int k = 0; k < 5; ++k) W[k] = Wl[k];
+}
+
 int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                      const double* dW, double dt, int stage, double* rec) {
     const int64_t nc = m->nc;
@@ -1274,7 +1309,8 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
              * state after the rotation (below); give the missing side the
              * interior values so the rotation leaves them defined */
             int wall = (cl < 0 || cr < 0) &&
-                       (m->bkind[f] == ORA_BC_SLIP_WALL || m->bkind[f] == ORA_BC_NOSLIP_WALL);
+                       (m->bkind[f] == ORA_BC_SLIP_WALL || m->bkind[f] == ORA_BC_NOSLIP_WALL ||
+                        m->bkind[f] == ORA_BC_ISOTHERMAL_WALL);
             if (wall) {
                 if (cl < 0) {
                     memcpy(WL, WR, sizeof WL);
@@ -1316,6 +1352,8 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                         if (a != 1) gg[0][a] = -gg[0][a];
                     gg[1][1] = -gg[1][1];
                     gg[2][1] = -gg[2][1];
+                } else if (m->bkind[f] == ORA_BC_ISOTHERMAL_WALL) {
+                    isothermal_ghost(gW, gg, p->gamma, p->wall_temperature);
                 } else {
                     /* Sec. 4.4, non-slip adiabatic wall (at rest): the ghost
                      * keeps rho and rho E and reverses all three momenta;

@@ -26,6 +26,7 @@ typedef struct {
     int32_t smooth_flux; /* 0: full solver (2nd-flux), 1: smooth solver */
     int32_t viscous;   /* 0: Euler (tau = 0), 1: tau = mu / p */
     double prandtl;    /* viscous only: Pr != 1 corrects the heat flux (Pr fix) */
+    double wall_temperature; /* T = p / rho of isothermal walls */
 } ora_params;
 
 typedef struct ora_mesh ora_mesh;
@@ -39,7 +40,8 @@ ora_mesh* ora_mesh_build(const double* xyz, int64_t nv, const int64_t* tet,
 void ora_mesh_free(ora_mesh* m);
 
 /* Boundary condition of the boundary faces (faces with one cell). */
-enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2, ORA_BC_NOSLIP_WALL = 3 };
+enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2, ORA_BC_NOSLIP_WALL = 3,
+       ORA_BC_ISOTHERMAL_WALL = 4 };
 /* kind[nc][4]: the condition of local face f (opposite vertex f) of cell c,
  * read only where that face is on the boundary.  Default: all open.
  * Returns -1 (mesh unchanged only up to the offending face) on a value

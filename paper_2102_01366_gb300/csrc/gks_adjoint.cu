@@ -755,6 +755,7 @@ static Phys<double> phys64(const HostPhys& p) {
     ph.viscous = p.viscous;
     ph.smooth = p.smooth;
     ph.prf = p.prf;
+    ph.twall = p.twall;
     return ph;
 }
 

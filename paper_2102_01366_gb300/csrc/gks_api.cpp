@@ -46,6 +46,7 @@ extern "C" void gks_params_default(gks_params* p) {
     p->tau_eps = 0.01;
     p->tau_c = 1.0;
     p->prandtl = 1.0;
+    p->wall_temperature = 1.0;
     p->weno = 1;
     p->order = 3;
     p->smooth_flux = 0;
@@ -60,8 +61,8 @@ static gks_status check_params(const gks_params* p) {
         return GKS_E_ARG;
     }
     if (!(p->cfl > 0.0) || !(p->eps_weno > 0.0) || !(p->tau_eps >= 0.0) || !(p->tau_c >= 0.0) ||
-        !(p->mu >= 0.0) || !(p->prandtl > 0.0)) {
-        set_error("cfl, eps_weno, prandtl must be positive; tau_eps, tau_c, mu non-negative");
+        !(p->mu >= 0.0) || !(p->prandtl > 0.0) || !(p->wall_temperature > 0.0)) {
+        set_error("cfl, eps_weno, prandtl, wall_temperature must be positive; tau_eps, tau_c, mu non-negative");
         return GKS_E_ARG;
     }
     if ((p->weno != 0 && p->weno != 1) || (p->order != 2 && p->order != 3) ||
@@ -176,7 +177,8 @@ extern "C" gks_status gks_mesh_set_boundary(gks_mesh* m, const int8_t* kind) {
         for (int f = 0; f < 4; ++f) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             const int8_t k = kind[c * 4 + f];
-            if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED && k != GKS_BC_NOSLIP_WALL) {
+            if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED && k != GKS_BC_NOSLIP_WALL &&
+                k != GKS_BC_ISOTHERMAL_WALL) {
                 set_error("gks_mesh_set_boundary: unknown kind " + std::to_string((int)k) + " at cell " +
                           std::to_string(c) + " face " + std::to_string(f));
                 return GKS_E_ARG;
@@ -521,7 +523,7 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     s->params = *params;
     s->phys = HostPhys{params->gamma, params->cfl, params->mu, params->eps_weno, params->tau_eps,
                        params->tau_c, params->weno, params->order, params->smooth_flux, params->viscous,
-                       params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0};
+                       params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0, params->wall_temperature};
     s->fp32 = fp32;
     s->ws = static_cast<char*>(d_workspace);
     s->L = L;
@@ -931,9 +933,11 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned)) {
-        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh, and on a mesh with "
-                  "fixed-state faces a fixed state set by gks_set_fixed_state");
+    bool isothermal = false;
+    for (int8_t k : g.bkind) isothermal |= k == GKS_BC_ISOTHERMAL_WALL;
+    if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned) || isothermal) {
+        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh without isothermal walls, "
+                  "and on a mesh with fixed-state faces a fixed state set by gks_set_fixed_state");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);

@@ -64,6 +64,7 @@ struct Phys {
     T tau_eps, tau_c, mu;
     T eps_w;
     T prf;               // Pr fix: 1/Pr - 1 (0 without it)
+    T twall;             // temperature p / rho of isothermal walls
     int viscous, smooth;
 };
 

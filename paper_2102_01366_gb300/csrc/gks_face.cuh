@@ -122,8 +122,48 @@ __device__ __forceinline__ void noslip_wall_ghost(T* Wt, T (*gt)[5]) {
     }
 }
 
+// Non-slip isothermal wall at rest (Sec. 4.4) in the face frame, R = 1
+// (T = p / rho): the ghost has the interior pressure, the reversed velocity
+// and the temperature 2 T_w - T; of the primitive derivatives the velocity's
+// and the temperature's are kept and the pressure's reversed, then carried
+// back to the conservative derivatives through the chain rule.
+template <typename T>
+__device__ __forceinline__ void isothermal_wall_ghost(T* Wt, T (*gt)[5], T gm1, T Tw) {
+    const T rho = Wt[0], ir = T(1) / rho;
+    const T U[3] = {Wt[1] * ir, Wt[2] * ir, Wt[3] * ir};
+    const T Q = T(0.5) * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    const T p = gm1 * (Wt[4] - rho * Q);
+    const T Tr = p * ir;
+    const T Tl = T(2) * Tw - Tr;
+    const T rl = p / Tl;
+    Wt[0] = rl;
+    Wt[1] = -rl * U[0];
+    Wt[2] = -rl * U[1];
+    Wt[3] = -rl * U[2];
+    Wt[4] = p / gm1 + rl * Q;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T dU[3], dQ = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dU[i] = (gt[j][1 + i] - gt[j][0] * U[i]) * ir;
+            dQ += U[i] * dU[i];
+        }
+        const T dp = gm1 * (gt[j][4] - gt[j][0] * Q - rho * dQ);
+        const T dT = (dp - gt[j][0] * Tr) * ir;
+        // ghost: dU and dT kept, dp reversed; U reversed, so dQ reverses too
+        const T dpl = -dp;
+        const T drl = (dpl - dT * rl) / Tl;
+        gt[j][0] = drl;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gt[j][1 + i] = -drl * U[i] + dU[i] * rl;
+        gt[j][4] = drl * Q - rl * dQ + dpl / gm1;
+    }
+}
+
 // device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
-inline constexpr int FLR_OPEN = -1, FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4;
+inline constexpr int FLR_OPEN = -1, FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4,
+                     FLR_ISOTHERMAL_WALL = -5;
 
 // fixed boundary: the interior cell's fixed state (average and gradient)
 // extended linearly to the point X (relative to the cell's centroid)

@@ -64,7 +64,8 @@ struct DevState {
 struct HostPhys {
     double gamma, cfl, mu, eps_weno, tau_eps, tau_c;
     int weno, order, smooth, viscous;
-    double prf;  // Pr fix factor 1/Pr - 1 (0: none)
+    double prf;    // Pr fix factor 1/Pr - 1 (0: none)
+    double twall;  // isothermal wall temperature
 };
 
 template <typename T>

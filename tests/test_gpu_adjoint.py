@@ -364,6 +364,14 @@ def test_unsupported_configurations_are_rejected(cuda):
         with pytest.raises(gks.GksError) as e:
             s.adjoint_step(*args, 1e-3)
         assert e.value.status == -8  # GKS_E_UNSUPPORTED
+    iso = I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=42)
+    iso["bkind"] = I.boundary_kinds(iso, {(0, "lo"): I.BC_ISOTHERMAL_WALL, (0, "hi"): I.BC_ISOTHERMAL_WALL})
+    Wi, dWi = I.sine_wave_state(iso, k=4.0 * np.pi, u=(0.3, -0.2, 0.1))
+    s = gks.State(gks.Mesh(iso), gks.params(weno=0, cfl=0.5, viscous=1, mu=0.01))
+    argsi = [torch.tensor(x, device="cuda") for x in (Wi, dWi, np.zeros_like(Wi), np.zeros_like(dWi))]
+    with pytest.raises(gks.GksError) as e:
+        s.adjoint_step(*argsi, 1e-3)
+    assert e.value.status == -8
     fixed_mesh, Wo, dWo = I.shu_osher_case(nx=8, nyz=2)  # fixed-state ends
     s = gks.State(gks.Mesh(fixed_mesh), gks.params(weno=0, cfl=0.5))
     argso = [torch.tensor(x, device="cuda") for x in (Wo, dWo, np.zeros_like(Wo), np.zeros_like(dWo))]

@@ -76,6 +76,11 @@ CASES = {
                                                       seed=38)),
                            lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.6, -0.3, 0.2)),
                            dict(weno=1, viscous=1, mu=0.01)),
+    # non-slip isothermal walls (Sec. 4.4) at T_w = 0.9, viscous
+    "isothermal_box_viscous": (lambda: _isothermal(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True),
+                                                              jitter=0.1, seed=42)),
+                               lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.3, -0.2, 0.1)),
+                               dict(weno=1, viscous=1, mu=0.01, wall_temperature=0.9)),
     # the sphere's O-type shell (pole rows of 3 tets per hexahedron), non-slip
     # wall at r = 0.5, far field held at r = 1.5, viscous, a perturbed free
     # stream; with linear weights the wall cells take the first-order fit
@@ -102,6 +107,11 @@ STEPS = {"sphere_shell_weno_viscous": 4}
 
 def _walled(mesh):
     mesh["bkind"] = I.wall_kinds(mesh, (0,))
+    return mesh
+
+
+def _isothermal(mesh):
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_ISOTHERMAL_WALL, (0, "hi"): I.BC_ISOTHERMAL_WALL})
     return mesh
 
 

@@ -227,3 +227,51 @@ def test_shear_wave_decays_at_the_viscous_rate(oracle_mod):
     W2, _, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, t_end=2.0)
     A2 = I.shear_decay_amplitude(mesh, W2, vol=vol)
     assert A2 - exact > 0.5 * (A0 - exact), (A0, A2, exact)
+
+
+def _isothermal_box(nx=4, nyz=2, seed=40):
+    mesh = I.box_mesh((nx, nyz, nyz), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=seed)
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_ISOTHERMAL_WALL, (0, "hi"): I.BC_ISOTHERMAL_WALL})
+    return mesh
+
+
+def _gas_at_rest(mesh, rho, p=1.0):
+    nc = mesh["tet"].shape[0]
+    W = np.zeros((5, nc))
+    W[0], W[4] = rho, p / 0.4
+    return W, np.zeros((15, nc))
+
+
+def test_isothermal_wall_at_the_gas_temperature_keeps_it_at_rest(oracle_mod):
+    """Sec. 4.4 non-slip isothermal wall: gas at rest whose temperature
+    p / rho equals the wall's is an equilibrium (the ghost is the interior
+    state), so it stays at rest."""
+    mesh = _isothermal_box()
+    W, dW = _gas_at_rest(mesh, rho=1.25)  # T = 0.8
+    om = oracle_mod.Mesh(mesh)
+    W1, dW1, _, _ = om.run(oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.01, wall_temperature=0.8), W, dW,
+                           nsteps=5)
+    assert np.abs(W1 - W).max() < 1e-13
+    assert np.abs(dW1).max() < 1e-12
+
+
+@pytest.mark.parametrize("t_gas,sign", [(1.2, -1.0), (0.8, 1.0)])
+def test_isothermal_wall_heat_flows_from_hot_to_cold(oracle_mod, t_gas, sign):
+    """Gas at rest at temperature t_gas between isothermal walls at T_w = 1,
+    Navier-Stokes solver: the walls take heat from hotter gas and give it to
+    colder gas (the total energy falls or rises), and the gas next to the
+    walls moves toward the wall temperature while the middle has not yet
+    felt it.  (The wall's heat flux is a viscous effect: with the Euler
+    solver the isothermal ghost has no physical meaning.)"""
+    mesh = _isothermal_box(nx=6)
+    W, dW = _gas_at_rest(mesh, rho=1.0 / t_gas)
+    om = oracle_mod.Mesh(mesh)
+    geo = om.geometry()
+    vol, cen = geo["vol"], geo["cen"][:, 0]
+    p = oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.02, wall_temperature=1.0)
+    W1, _, _, _ = om.run(p, W, dW, nsteps=6)
+    assert sign * ((vol * W1[4]).sum() - (vol * W[4]).sum()) > 1e-3
+    T1 = 0.4 * (W1[4] - 0.5 * (W1[1:4] ** 2).sum(0) / W1[0]) / W1[0]
+    near = np.minimum(cen, 1.0 - cen) < 1.0 / 6.0
+    assert sign * (T1[near].mean() - t_gas) > 0.02
+    assert abs(T1[~near].mean() - t_gas) < 0.01
