@@ -159,8 +159,7 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
  *                     params.wall_temperature = T_w); the derivatives of the
  *                     velocity and the temperature are kept, that of the
  *                     pressure reversed (through the chain rule back to the
- *                     conservative derivatives).  Not differentiated by
- *                     gks_adjoint_step.
+ *                     conservative derivatives).
  * The interior reconstruction of a boundary cell is the one-sided one of
  * Sec. 4.4 without constraint rows (for the non-slip wall the paper adds the
  * wall velocity as a constraint; this library does not): the cell's stencil
@@ -340,8 +339,8 @@ gks_status gks_residual(gks_state* state, double* out_l2);
  * Supported: FP64 states (precision 0) with the third- or second-order
  * reconstruction with linear or WENO weights (the weights are differentiated,
  * |x|' taken as sign x), full or smooth flux, Euler or viscous, single-case
- * meshes, periodic or with open, slip-wall, non-slip (adiabatic) wall or
- * fixed-state boundary faces (the last only with a fixed state set by
+ * meshes, periodic or with open, slip-wall, non-slip (adiabatic or
+ * isothermal) wall or fixed-state boundary faces (the last only with a fixed state set by
  * gks_set_fixed_state: it is then a constant of the step), any Prandtl
  * number; GKS_E_UNSUPPORTED otherwise.  A cell that
  * falls back to its average (the positivity check of Sec. 4.3) passes the

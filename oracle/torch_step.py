@@ -210,7 +210,31 @@ def _frame(n):
     return torch.stack([n, t1, t2], dim=1)
 
 
-OPEN, SLIP, FIXED, NOSLIP = 0, 1, 2, 3
+OPEN, SLIP, FIXED, NOSLIP, ISOTHERMAL = 0, 1, 2, 3, 4
+
+
+def _isothermal_ghost(W, g, gamma, Tw):
+    """Sec. 4.4 non-slip isothermal wall (face frame, T = p / rho): pressure
+    kept, velocity reversed, T -> 2 Tw - T; dU, dT kept, dp reversed, back to
+    conservative derivatives; W [F, 5], g [F, 3, 5]"""
+    gm1 = gamma - 1.0
+    rho = W[:, 0]
+    U = W[:, 1:4] / rho[:, None]
+    Q = 0.5 * (U * U).sum(1)
+    p = gm1 * (W[:, 4] - rho * Q)
+    Tr = p / rho
+    Tl = 2.0 * Tw - Tr
+    rl = p / Tl
+    Wl = torch.cat([rl[:, None], -rl[:, None] * U, (p / gm1 + rl * Q)[:, None]], dim=1)
+    dU = (g[:, :, 1:4] - g[:, :, :1] * U[:, None, :]) / rho[:, None, None]          # [F, 3, 3]
+    dQ = (U[:, None, :] * dU).sum(2)                                                 # [F, 3]
+    dp = gm1 * (g[:, :, 4] - g[:, :, 0] * Q[:, None] - rho[:, None] * dQ)
+    dT = (dp - g[:, :, 0] * Tr[:, None]) / rho[:, None]
+    dpl = -dp
+    drl = (dpl - dT * rl[:, None]) / Tl[:, None]
+    gm = drl[:, :, None] * (-U[:, None, :]) + dU * rl[:, None, None]
+    ge = drl * Q[:, None] - rl[:, None] * dQ + dpl / gm1
+    return Wl, torch.cat([drl[:, :, None], gm, ge[:, :, None]], dim=2)
 
 
 class Step:
@@ -219,10 +243,10 @@ class Step:
     fixed faces hold."""
 
     def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0,
-                 weno=False, eps=1e-8, kinds=None, fixed=None, order=3):
+                 weno=False, eps=1e-8, kinds=None, fixed=None, order=3, wall_temperature=1.0):
         geo, top = om.geometry(), om.topology()
         M1, M2 = om.stencils()
-        self.weno, self.eps, self.order = weno, eps, order
+        self.weno, self.eps, self.order, self.twall = weno, eps, order, wall_temperature
         t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
         self.vol, self.mom = t(geo["vol"]), t(geo["mom2"])
         self.area, self.n = t(geo["farea"]), t(geo["fnorm"])
@@ -428,6 +452,11 @@ class Step:
                 sel = (missing & (kind == NOSLIP))[:, None]
                 Wg = torch.where(sel, Wg * nw, Wg)
                 gg = torch.where(sel[:, :, None], gg * ng, gg)
+                sel = missing & (kind == ISOTHERMAL)
+                if sel.any():
+                    iw, ig = _isothermal_ghost(Wg, gg, self.kw["gamma"], self.twall)
+                    Wg = torch.where(sel[:, None], iw, Wg)
+                    gg = torch.where(sel[:, None, None], ig, gg)
                 sides[side] = [Wg, gg]
             (Wl, gll), (Wr, grl) = sides
             Fh, F, W0, Wt = point_flux(Wl, gll, Wr, grl, dt, **self.kw)

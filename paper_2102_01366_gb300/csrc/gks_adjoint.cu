@@ -125,7 +125,8 @@ template <int NR>
 __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const double* __restrict__ poly,
                                                 const double* __restrict__ Xavg, const double* __restrict__ src,
                                                 int64_t f, int k, double (*Rm)[3], double* x, double* lFh,
-                                                double* lD, double* lW0, double* ldWt) {
+                                                double* lD, double* lW0, double* ldWt, double gm1 = 0.0,
+                                                double twall = 0.0) {
     const int L = m.flr[f], R = m.flr[m.nf + f];
     const double* geo = m.fgeo + f * FGEO;
     const double n[3] = {geo[0], geo[1], geo[2]};
@@ -193,7 +194,43 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
             to_local(Rm, Wv, g, xs, gs);
             if (cell == FLR_SLIP_WALL) slip_wall_ghost(xs, gs);
             if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(xs, gs);
+            if (cell == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(xs, gs, gm1, twall);
         }
+    }
+}
+
+// A forward-mode number (value and one derivative) for the Jacobian of the
+// isothermal-wall ghost, the one nonlinear ghost.
+struct Fwd {
+    double v, d;
+    __device__ Fwd() : v(0.0), d(0.0) {}
+    __device__ Fwd(double x) : v(x), d(0.0) {}
+    __device__ Fwd(double x, double dx) : v(x), d(dx) {}
+};
+__device__ __forceinline__ Fwd operator+(Fwd a, Fwd b) { return Fwd(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Fwd operator-(Fwd a, Fwd b) { return Fwd(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Fwd operator-(Fwd a) { return Fwd(-a.v, -a.d); }
+__device__ __forceinline__ Fwd operator*(Fwd a, Fwd b) { return Fwd(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Fwd operator/(Fwd a, Fwd b) {
+    const double q = a.v / b.v;
+    return Fwd(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ Fwd& operator+=(Fwd& a, Fwd b) { return a = a + b; }
+
+// li += J^T ls for the isothermal ghost G at the interior face-frame state x
+// (W, grad W: 20 values), by one forward pass per input
+__device__ void isothermal_ghost_adj(const double* x, const double* ls, double gm1, double twall, double* li) {
+    for (int i = 0; i < 20; ++i) {
+        Fwd Wd[5], gd[3][5];
+        for (int q = 0; q < 5; ++q) Wd[q] = Fwd(x[q], i == q ? 1.0 : 0.0);
+        for (int j = 0; j < 3; ++j)
+            for (int q = 0; q < 5; ++q) gd[j][q] = Fwd(x[5 + 5 * j + q], i == 5 + 5 * j + q ? 1.0 : 0.0);
+        isothermal_wall_ghost(Wd, gd, Fwd(gm1), Fwd(twall));
+        double acc = 0.0;
+        for (int q = 0; q < 5; ++q) acc += ls[q] * Wd[q].d;
+        for (int j = 0; j < 3; ++j)
+            for (int q = 0; q < 5; ++q) acc += ls[5 + 5 * j + q] * gd[j][q].d;
+        li[i] += acc;
     }
 }
 
@@ -210,7 +247,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
     const int64_t f = t / 3;
     const int k = (int)(t - f * 3);
     double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
-    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt);
+    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt, ph.gm1, ph.twall);
     double* l = lx + t * ADJ_IN;
     double lin[ADJ_IN];
     for (int i = 0; i < ADJ_IN; ++i) lin[i] = 0.0;
@@ -223,11 +260,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
 // One thread per face: the input adjoints of its three points carried back
 // through the rotations and the evaluation at the points into
 // lpf[f][side][5][10].
-// A wall side's adjoint (the mirror is its own transpose) joins the interior
-// side's at the same point; an open side's goes to the interior cell's
-// average, lwo[f][5] (zero on every other face).
+// A wall side's adjoint joins the interior side's at the same point (a
+// mirror is its own transpose; the isothermal ghost's Jacobian is transposed
+// at the interior state); an open side's goes to the interior cell's average,
+// lwo[f][5] (zero on every other face).
 __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf,
-                                double* __restrict__ lwo) {
+                                double* __restrict__ lwo, const double* __restrict__ poly, double gm1,
+                                double twall) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= m.nf) return;
     const int L = m.flr[f], R = m.flr[m.nf + f];
@@ -252,6 +291,16 @@ __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx
                 for (int q = 0; q < 5; ++q) lw[q] += lW[q];
             } else if (cell == FLR_FIXED) {
                 // a set fixed state is a constant of the step: nothing flows back
+            } else if (cell == FLR_ISOTHERMAL_WALL) {
+                // the interior state at the point, face frame, then the ghost's transpose
+                const int src_side = 1 - side;
+                const int64_t c = side == 0 ? R : L;
+                const double X[3] = {geo[4 + 9 * src_side + 3 * k], geo[5 + 9 * src_side + 3 * k],
+                                     geo[6 + 9 * src_side + 3 * k]};
+                double Wv[5], g[3][5], x[20];
+                eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
+                to_local(Rm, Wv, g, x, reinterpret_cast<double (*)[5]>(x + 5));
+                isothermal_ghost_adj(x, ls, gm1, twall, li);
             } else {
                 if (cell == FLR_SLIP_WALL) slip_wall_ghost(ls, lg);
                 if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(ls, lg);
@@ -793,7 +842,7 @@ static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const Ad
     else
         k_adj_point_rev<NR, false><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
                                                                                         b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph.gm1, ph.twall);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }
 

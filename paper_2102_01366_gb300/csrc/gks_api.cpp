@@ -933,11 +933,9 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
         set_error("gks_adjoint_step: scratch smaller than gks_adjoint_workspace_bytes");
         return GKS_E_NOMEM;
     }
-    bool isothermal = false;
-    for (int8_t k : g.bkind) isothermal |= k == GKS_BC_ISOTHERMAL_WALL;
-    if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned) || isothermal) {
-        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh without isothermal walls, "
-                  "and on a mesh with fixed-state faces a fixed state set by gks_set_fixed_state");
+    if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned)) {
+        set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh, and on a mesh with "
+                  "fixed-state faces a fixed state set by gks_set_fixed_state");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);
