@@ -66,6 +66,8 @@ typedef struct gks_params {
     double prandtl;      /* Prandtl number of the viscous solver (BGK gives 1; other
                             values correct the heat flux, Pr fix below); 1 default */
     double wall_temperature; /* T = p / rho of GKS_BC_ISOTHERMAL_WALL faces; 1 default */
+    double wall_velocity[3]; /* velocity of GKS_BC_MOVING_WALL faces (global frame, along
+                                the walls); 0 default */
     int32_t weno;        /* 0: linear weights, R = P2 (or P1 at order 2; at order 3 a
                             boundary cell takes the least-squares first-order fit to
                             its P2 stencil's data, Sec. 4.4); 1: nonlinear */
@@ -160,12 +162,18 @@ gks_status gks_mesh_create_cases(const double* xyz, int64_t n_vert, const int64_
  *                     velocity and the temperature are kept, that of the
  *                     pressure reversed (through the chain rule back to the
  *                     conservative derivatives).
+ *   GKS_BC_MOVING_WALL non-slip adiabatic wall moving along itself with
+ *                     params.wall_velocity U_w (the paper's driven lid; it
+ *                     prints no ghost for it): the ghost has the interior
+ *                     density and pressure and the velocity 2 U_w - U; the
+ *                     velocity derivatives are kept, those of density and
+ *                     pressure reversed.  At U_w = 0 it is GKS_BC_NOSLIP_WALL.
  * The interior reconstruction of a boundary cell is the one-sided one of
  * Sec. 4.4 without constraint rows (for the non-slip wall the paper adds the
  * wall velocity as a constraint; this library does not): the cell's stencil
  * simply lacks the missing neighbour. */
 enum { GKS_BC_OPEN = 0, GKS_BC_SLIP_WALL = 1, GKS_BC_FIXED = 2, GKS_BC_NOSLIP_WALL = 3,
-       GKS_BC_ISOTHERMAL_WALL = 4 };
+       GKS_BC_ISOTHERMAL_WALL = 4, GKS_BC_MOVING_WALL = 5 };
 
 /* kind[n_cell][4] (host): the condition of local face f (the face opposite
  * tet vertex f) of each cell, read only where that face is a boundary face.

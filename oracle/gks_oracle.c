@@ -547,7 +547,7 @@ int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             int8_t k = kind[c * 4 + f];
             if (k != ORA_BC_OPEN && k != ORA_BC_SLIP_WALL && k != ORA_BC_FIXED && k != ORA_BC_NOSLIP_WALL &&
-                k != ORA_BC_ISOTHERMAL_WALL)
+                k != ORA_BC_ISOTHERMAL_WALL && k != ORA_BC_MOVING_WALL)
                 return -1;
             m->bkind[m->csr_face[c * 4 + f]] = k;
         }
@@ -1239,6 +1239,37 @@ static void isothermal_ghost(double W[5], double g[3][5], double gamma, double T
     for (int k = 0; k < 5; ++k) W[k] = Wl[k];
 }
 
+/* Non-slip adiabatic wall moving along itself with velocity Uw (face frame;
+ * the paper prints no ghost for it).  READING: the at-rest rules written in
+ * primitive variables and shifted to the wall's frame: the ghost has the
+ * interior density and pressure and the velocity 2 Uw - U; the velocity
+ * derivatives are kept, the density and pressure derivatives reversed (at
+ * Uw = 0 exactly the non-slip adiabatic ghost). */
+static void moving_ghost(double W[5], double g[3][5], double gamma, const double Uw[3]) {
+    double rho = W[0], U[3], Ul[3], Q = 0.0, Ql = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        U[i] = W[1 + i] / rho;
+        Ul[i] = 2.0 * Uw[i] - U[i];
+        Q += 0.5 * U[i] * U[i];
+        Ql += 0.5 * Ul[i] * Ul[i];
+    }
+    double p = (gamma - 1.0) * (W[4] - rho * Q);
+    for (int j = 0; j < 3; ++j) {
+        double dU[3], dQ = 0.0;
+        for (int i = 0; i < 3; ++i) { dU[i] = (g[j][1 + i] - g[j][0] * U[i]) / rho; dQ += U[i] * dU[i]; }
+        double dp = (gamma - 1.0) * (g[j][4] - g[j][0] * Q - dQ * rho);
+        /* ghost: d rho and dp reversed, dU kept */
+        double drho = -g[j][0], dpl = -dp, dQl = 0.0;
+        for (int i = 0; i < 3; ++i) dQl += Ul[i] * dU[i];
+        g[j][0] = drho;
+        for (int i = 0; i < 3; ++i) g[j][1 + i] = drho * Ul[i] + rho * dU[i];
+        g[j][4] = dpl / (gamma - 1.0) + drho * Ql + rho * dQl;
+    }
+    W[0] = rho;
+    for (int i = 0; i < 3; ++i) W[1 + i] = rho * Ul[i];
+    W[4] = p / (gamma - 1.0) + rho * Ql;
+}
+
 int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                      const double* dW, double dt, int stage, double* rec) {
     const int64_t nc = m->nc;
@@ -1310,7 +1341,7 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
              * interior values so the rotation leaves them defined */
             int wall = (cl < 0 || cr < 0) &&
                        (m->bkind[f] == ORA_BC_SLIP_WALL || m->bkind[f] == ORA_BC_NOSLIP_WALL ||
-                        m->bkind[f] == ORA_BC_ISOTHERMAL_WALL);
+                        m->bkind[f] == ORA_BC_ISOTHERMAL_WALL || m->bkind[f] == ORA_BC_MOVING_WALL);
             if (wall) {
                 if (cl < 0) {
                     memcpy(WL, WR, sizeof WL);
@@ -1354,6 +1385,12 @@ int ora_face_records(const ora_mesh* m, const ora_params* p, const double* W,
                     gg[2][1] = -gg[2][1];
                 } else if (m->bkind[f] == ORA_BC_ISOTHERMAL_WALL) {
                     isothermal_ghost(gW, gg, p->gamma, p->wall_temperature);
+                } else if (m->bkind[f] == ORA_BC_MOVING_WALL) {
+                    double Uw[3];
+                    for (int j = 0; j < 3; ++j)
+                        Uw[j] = T[1 + j][1] * p->wall_velocity[0] + T[1 + j][2] * p->wall_velocity[1] +
+                                T[1 + j][3] * p->wall_velocity[2];
+                    moving_ghost(gW, gg, p->gamma, Uw);
                 } else {
                     /* Sec. 4.4, non-slip adiabatic wall (at rest): the ghost
                      * keeps rho and rho E and reverses all three momenta;

@@ -27,6 +27,7 @@ typedef struct {
     int32_t viscous;   /* 0: Euler (tau = 0), 1: tau = mu / p */
     double prandtl;    /* viscous only: Pr != 1 corrects the heat flux (Pr fix) */
     double wall_temperature; /* T = p / rho of isothermal walls */
+    double wall_velocity[3]; /* velocity of moving walls (global frame) */
 } ora_params;
 
 typedef struct ora_mesh ora_mesh;
@@ -41,7 +42,7 @@ void ora_mesh_free(ora_mesh* m);
 
 /* Boundary condition of the boundary faces (faces with one cell). */
 enum { ORA_BC_OPEN = 0, ORA_BC_SLIP_WALL = 1, ORA_BC_FIXED = 2, ORA_BC_NOSLIP_WALL = 3,
-       ORA_BC_ISOTHERMAL_WALL = 4 };
+       ORA_BC_ISOTHERMAL_WALL = 4, ORA_BC_MOVING_WALL = 5 };
 /* kind[nc][4]: the condition of local face f (opposite vertex f) of cell c,
  * read only where that face is on the boundary.  Default: all open.
  * Returns -1 (mesh unchanged only up to the offending face) on a value

@@ -34,13 +34,14 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double),
                 ("eps_weno", C.c_double), ("tau_eps", C.c_double), ("tau_c", C.c_double),
                 ("weno", C.c_int32), ("order", C.c_int32), ("smooth_flux", C.c_int32),
-                ("viscous", C.c_int32), ("prandtl", C.c_double), ("wall_temperature", C.c_double)]
+                ("viscous", C.c_int32), ("prandtl", C.c_double), ("wall_temperature", C.c_double),
+                ("wall_velocity", C.c_double * 3)]
 
 
 def params(gamma=1.4, cfl=0.5, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, weno=0,
-           order=3, smooth_flux=0, viscous=0, prandtl=1.0, wall_temperature=1.0):
+           order=3, smooth_flux=0, viscous=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0)):
     return Params(gamma, cfl, mu, eps_weno, tau_eps, tau_c, weno, order, smooth_flux, viscous, prandtl,
-                  wall_temperature)
+                  wall_temperature, (C.c_double * 3)(*[float(u) for u in wall_velocity]))
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")

@@ -210,7 +210,22 @@ def _frame(n):
     return torch.stack([n, t1, t2], dim=1)
 
 
-OPEN, SLIP, FIXED, NOSLIP, ISOTHERMAL = 0, 1, 2, 3, 4
+OPEN, SLIP, FIXED, NOSLIP, ISOTHERMAL, MOVING = 0, 1, 2, 3, 4, 5
+
+
+def _moving_ghost(W, g, gamma, Uw):
+    """non-slip adiabatic wall moving with Uw [F, 3] (face frame): the
+    at-rest ghost taken in the wall's frame, m -> 2 rho Uw - m,
+    E -> E - 2 Uw.m + 2 rho |Uw|^2; derivatives d rho -> -d rho,
+    dm -> dm - 2 Uw d rho, dE -> -dE + 2 Uw.dm - 2 |Uw|^2 d rho"""
+    rho, m, E = W[:, 0], W[:, 1:4], W[:, 4]
+    uu = (Uw * Uw).sum(1)
+    Wl = torch.cat([rho[:, None], 2.0 * rho[:, None] * Uw - m,
+                    (E - 2.0 * (Uw * m).sum(1) + 2.0 * rho * uu)[:, None]], dim=1)
+    dr, dm, dE = g[:, :, 0], g[:, :, 1:4], g[:, :, 4]
+    gl = torch.cat([-dr[:, :, None], dm - 2.0 * Uw[:, None, :] * dr[:, :, None],
+                    (-dE + 2.0 * (Uw[:, None, :] * dm).sum(2) - 2.0 * uu[:, None] * dr)[:, :, None]], dim=2)
+    return Wl, gl
 
 
 def _isothermal_ghost(W, g, gamma, Tw):
@@ -243,10 +258,12 @@ class Step:
     fixed faces hold."""
 
     def __init__(self, om, gamma=1.4, tau_eps=0.01, tau_c=1.0, mu=0.0, viscous=False, smooth=False, prandtl=1.0,
-                 weno=False, eps=1e-8, kinds=None, fixed=None, order=3, wall_temperature=1.0):
+                 weno=False, eps=1e-8, kinds=None, fixed=None, order=3, wall_temperature=1.0,
+                 wall_velocity=(0.0, 0.0, 0.0)):
         geo, top = om.geometry(), om.topology()
         M1, M2 = om.stencils()
         self.weno, self.eps, self.order, self.twall = weno, eps, order, wall_temperature
+        self.uwall = torch.tensor(wall_velocity, dtype=torch.float64)
         t = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64)
         self.vol, self.mom = t(geo["vol"]), t(geo["mom2"])
         self.area, self.n = t(geo["farea"]), t(geo["fnorm"])
@@ -452,6 +469,12 @@ class Step:
                 sel = (missing & (kind == NOSLIP))[:, None]
                 Wg = torch.where(sel, Wg * nw, Wg)
                 gg = torch.where(sel[:, :, None], gg * ng, gg)
+                sel = missing & (kind == MOVING)
+                if sel.any():
+                    Uw = torch.einsum("fij,j->fi", self.R, self.uwall)
+                    mw, mg = _moving_ghost(Wg, gg, self.kw["gamma"], Uw)
+                    Wg = torch.where(sel[:, None], mw, Wg)
+                    gg = torch.where(sel[:, None, None], mg, gg)
                 sel = missing & (kind == ISOTHERMAL)
                 if sel.any():
                     iw, ig = _isothermal_ghost(Wg, gg, self.kw["gamma"], self.twall)

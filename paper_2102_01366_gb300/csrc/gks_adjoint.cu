@@ -125,8 +125,8 @@ template <int NR>
 __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const double* __restrict__ poly,
                                                 const double* __restrict__ Xavg, const double* __restrict__ src,
                                                 int64_t f, int k, double (*Rm)[3], double* x, double* lFh,
-                                                double* lD, double* lW0, double* ldWt, double gm1 = 0.0,
-                                                double twall = 0.0) {
+                                                double* lD, double* lW0, double* ldWt,
+                                                const Phys<double>* ph = nullptr) {
     const int L = m.flr[f], R = m.flr[m.nf + f];
     const double* geo = m.fgeo + f * FGEO;
     const double n[3] = {geo[0], geo[1], geo[2]};
@@ -194,7 +194,12 @@ __device__ __forceinline__ void adj_point_setup(const DevMesh<double>& m, const 
             to_local(Rm, Wv, g, xs, gs);
             if (cell == FLR_SLIP_WALL) slip_wall_ghost(xs, gs);
             if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(xs, gs);
-            if (cell == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(xs, gs, gm1, twall);
+            if (cell == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(xs, gs, ph->gm1, ph->twall);
+            if (cell == FLR_MOVING_WALL) {
+                double Uw[3];
+                rotate_vec(Rm, ph->uwall, Uw);
+                moving_wall_ghost(xs, gs, ph->gm1, Uw);
+            }
         }
     }
 }
@@ -217,15 +222,21 @@ __device__ __forceinline__ Fwd operator/(Fwd a, Fwd b) {
 }
 __device__ __forceinline__ Fwd& operator+=(Fwd& a, Fwd b) { return a = a + b; }
 
-// li += J^T ls for the isothermal ghost G at the interior face-frame state x
-// (W, grad W: 20 values), by one forward pass per input
-__device__ void isothermal_ghost_adj(const double* x, const double* ls, double gm1, double twall, double* li) {
+// li += J^T ls for a nonlinear wall ghost G (isothermal or moving wall) at
+// the interior face-frame state x (W, grad W: 20 values), by one forward pass
+// per input; Uw is the wall velocity in the face frame
+__device__ void wall_ghost_adj(int kind, const double* x, const double* ls, double gm1, double twall,
+                               const double* Uw, double* li) {
+    const Fwd Uwd[3] = {Fwd(Uw[0]), Fwd(Uw[1]), Fwd(Uw[2])};
     for (int i = 0; i < 20; ++i) {
         Fwd Wd[5], gd[3][5];
         for (int q = 0; q < 5; ++q) Wd[q] = Fwd(x[q], i == q ? 1.0 : 0.0);
         for (int j = 0; j < 3; ++j)
             for (int q = 0; q < 5; ++q) gd[j][q] = Fwd(x[5 + 5 * j + q], i == 5 + 5 * j + q ? 1.0 : 0.0);
-        isothermal_wall_ghost(Wd, gd, Fwd(gm1), Fwd(twall));
+        if (kind == FLR_ISOTHERMAL_WALL)
+            isothermal_wall_ghost(Wd, gd, Fwd(gm1), Fwd(twall));
+        else
+            moving_wall_ghost(Wd, gd, Fwd(gm1), Uwd);
         double acc = 0.0;
         for (int q = 0; q < 5; ++q) acc += ls[q] * Wd[q].d;
         for (int j = 0; j < 3; ++j)
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
     const int64_t f = t / 3;
     const int k = (int)(t - f * 3);
     double Rm[3][3], x[ADJ_IN], lFh[5], lD[5], lW0[5], ldWt[5];
-    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt, ph.gm1, ph.twall);
+    adj_point_setup<NR>(m, poly, Xavg, src, f, k, Rm, x, lFh, lD, lW0, ldWt, &ph);
     double* l = lx + t * ADJ_IN;
     double lin[ADJ_IN];
     for (int i = 0; i < ADJ_IN; ++i) lin[i] = 0.0;
@@ -261,12 +272,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
 // through the rotations and the evaluation at the points into
 // lpf[f][side][5][10].
 // A wall side's adjoint joins the interior side's at the same point (a
-// mirror is its own transpose; the isothermal ghost's Jacobian is transposed
-// at the interior state); an open side's goes to the interior cell's average,
+// mirror is its own transpose; the isothermal and moving walls' ghost
+// Jacobians are transposed at the interior state); an open side's goes to the interior cell's average,
 // lwo[f][5] (zero on every other face).
 __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf,
-                                double* __restrict__ lwo, const double* __restrict__ poly, double gm1,
-                                double twall) {
+                                double* __restrict__ lwo, const double* __restrict__ poly, Phys<double> ph) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= m.nf) return;
     const int L = m.flr[f], R = m.flr[m.nf + f];
@@ -291,7 +301,7 @@ __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx
                 for (int q = 0; q < 5; ++q) lw[q] += lW[q];
             } else if (cell == FLR_FIXED) {
                 // a set fixed state is a constant of the step: nothing flows back
-            } else if (cell == FLR_ISOTHERMAL_WALL) {
+            } else if (cell == FLR_ISOTHERMAL_WALL || cell == FLR_MOVING_WALL) {
                 // the interior state at the point, face frame, then the ghost's transpose
                 const int src_side = 1 - side;
                 const int64_t c = side == 0 ? R : L;
@@ -300,7 +310,9 @@ __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx
                 double Wv[5], g[3][5], x[20];
                 eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
                 to_local(Rm, Wv, g, x, reinterpret_cast<double (*)[5]>(x + 5));
-                isothermal_ghost_adj(x, ls, gm1, twall, li);
+                double Uw[3];
+                rotate_vec(Rm, ph.uwall, Uw);
+                wall_ghost_adj(cell, x, ls, ph.gm1, ph.twall, Uw, li);
             } else {
                 if (cell == FLR_SLIP_WALL) slip_wall_ghost(ls, lg);
                 if (cell == FLR_NOSLIP_WALL) noslip_wall_ghost(ls, lg);
@@ -805,6 +817,7 @@ static Phys<double> phys64(const HostPhys& p) {
     ph.smooth = p.smooth;
     ph.prf = p.prf;
     ph.twall = p.twall;
+    for (int i = 0; i < 3; ++i) ph.uwall[i] = p.uwall[i];
     return ph;
 }
 
@@ -842,7 +855,7 @@ static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const Ad
     else
         k_adj_point_rev<NR, false><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
                                                                                         b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph.gm1, ph.twall);
+    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }
 

@@ -178,7 +178,7 @@ extern "C" gks_status gks_mesh_set_boundary(gks_mesh* m, const int8_t* kind) {
             if (m->nbr[c * 4 + f] >= 0) continue;
             const int8_t k = kind[c * 4 + f];
             if (k != GKS_BC_OPEN && k != GKS_BC_SLIP_WALL && k != GKS_BC_FIXED && k != GKS_BC_NOSLIP_WALL &&
-                k != GKS_BC_ISOTHERMAL_WALL) {
+                k != GKS_BC_ISOTHERMAL_WALL && k != GKS_BC_MOVING_WALL) {
                 set_error("gks_mesh_set_boundary: unknown kind " + std::to_string((int)k) + " at cell " +
                           std::to_string(c) + " face " + std::to_string(f));
                 return GKS_E_ARG;
@@ -523,7 +523,8 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     s->params = *params;
     s->phys = HostPhys{params->gamma, params->cfl, params->mu, params->eps_weno, params->tau_eps,
                        params->tau_c, params->weno, params->order, params->smooth_flux, params->viscous,
-                       params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0, params->wall_temperature};
+                       params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0, params->wall_temperature,
+                       {params->wall_velocity[0], params->wall_velocity[1], params->wall_velocity[2]}};
     s->fp32 = fp32;
     s->ws = static_cast<char*>(d_workspace);
     s->L = L;

@@ -65,6 +65,7 @@ struct Phys {
     T eps_w;
     T prf;               // Pr fix: 1/Pr - 1 (0 without it)
     T twall;             // temperature p / rho of isothermal walls
+    T uwall[3];          // velocity of moving walls (global frame)
     int viscous, smooth;
 };
 

@@ -161,9 +161,51 @@ __device__ __forceinline__ void isothermal_wall_ghost(T* Wt, T (*gt)[5], T gm1, 
     }
 }
 
+// a global-frame vector in the face frame (rows of Rm: n, t1, t2)
+template <typename T>
+__device__ __forceinline__ void rotate_vec(const T (*Rm)[3], const T* v, T* o) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = Rm[i][0] * v[0] + Rm[i][1] * v[1] + Rm[i][2] * v[2];
+}
+
+// Non-slip adiabatic wall moving with velocity Uw (face frame, tangential):
+// the ghost's velocity is 2 Uw - U, its density and pressure the interior's;
+// of the primitive derivatives the velocity's are kept and the density's and
+// pressure's reversed, then carried back to the conservative derivatives.
+// At Uw = 0 this is noslip_wall_ghost.
+template <typename T>
+__device__ __forceinline__ void moving_wall_ghost(T* Wt, T (*gt)[5], T gm1, const T* Uw) {
+    const T rho = Wt[0], ir = T(1) / rho;
+    const T U[3] = {Wt[1] * ir, Wt[2] * ir, Wt[3] * ir};
+    const T Q = T(0.5) * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    const T p = gm1 * (Wt[4] - rho * Q);
+    const T Ul[3] = {T(2) * Uw[0] - U[0], T(2) * Uw[1] - U[1], T(2) * Uw[2] - U[2]};
+    const T Ql = T(0.5) * (Ul[0] * Ul[0] + Ul[1] * Ul[1] + Ul[2] * Ul[2]);
+    Wt[1] = rho * Ul[0];
+    Wt[2] = rho * Ul[1];
+    Wt[3] = rho * Ul[2];
+    Wt[4] = p / gm1 + rho * Ql;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T dU[3], dQ = T(0), dQl = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dU[i] = (gt[j][1 + i] - gt[j][0] * U[i]) * ir;
+            dQ += U[i] * dU[i];
+            dQl += Ul[i] * dU[i];
+        }
+        const T dp = gm1 * (gt[j][4] - gt[j][0] * Q - rho * dQ);
+        const T drl = -gt[j][0];
+        gt[j][0] = drl;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gt[j][1 + i] = drl * Ul[i] + rho * dU[i];
+        gt[j][4] = -dp / gm1 + drl * Ql + rho * dQl;
+    }
+}
+
 // device encoding of a boundary face's missing side (flr): -1 - GKS_BC_*
 inline constexpr int FLR_OPEN = -1, FLR_SLIP_WALL = -2, FLR_FIXED = -3, FLR_NOSLIP_WALL = -4,
-                     FLR_ISOTHERMAL_WALL = -5;
+                     FLR_ISOTHERMAL_WALL = -5, FLR_MOVING_WALL = -6;
 
 // fixed boundary: the interior cell's fixed state (average and gradient)
 // extended linearly to the point X (relative to the cell's centroid)

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 
     // ---- phase 1 ----
     const int mine = side == 0 ? L : Rc;
-    const bool wall = mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL || mine == FLR_ISOTHERMAL_WALL;
+    const bool wall =
+        mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL || mine == FLR_ISOTHERMAL_WALL || mine == FLR_MOVING_WALL;
     T Ws[5], gs[3][5];
     if (mine >= 0 || wall) {
         // a wall side starts from the interior cell's value at the point
@@ -111,6 +112,11 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     if (mine == FLR_SLIP_WALL) slip_wall_ghost(tW, tg);
     if (mine == FLR_NOSLIP_WALL) noslip_wall_ghost(tW, tg);
     if (mine == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(tW, tg, ph.gm1, ph.twall);
+    if (mine == FLR_MOVING_WALL) {
+        T Uw[3];
+        rotate_vec(Rm, ph.uwall, Uw);
+        moving_wall_ghost(tW, tg, ph.gm1, Uw);
+    }
     const Prim<T> S = to_prim(tW, ph.gm1);
     Tab<T> t;
     T a[3][5], A[5];
@@ -367,7 +373,8 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
             const int cell = side == 0 ? L : Rc;
             T* Wv = side == 0 ? WL : WR;
             T (*g)[5] = side == 0 ? gL : gR;
-            if (cell >= 0 || cell == FLR_SLIP_WALL || cell == FLR_NOSLIP_WALL || cell == FLR_ISOTHERMAL_WALL) {
+            if (cell >= 0 || cell == FLR_SLIP_WALL || cell == FLR_NOSLIP_WALL || cell == FLR_ISOTHERMAL_WALL ||
+                cell == FLR_MOVING_WALL) {
                 // a wall side starts from the interior cell's value at the point
                 const int src = cell >= 0 ? side : 1 - side;
                 const int64_t c = cell >= 0 ? cell : (side == 0 ? Rc : L);
@@ -398,6 +405,12 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
         if (Rc == FLR_NOSLIP_WALL) noslip_wall_ghost(tWR, tgR);
         if (L == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(tWL, tgL, ph.gm1, ph.twall);
         if (Rc == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(tWR, tgR, ph.gm1, ph.twall);
+        if (L == FLR_MOVING_WALL || Rc == FLR_MOVING_WALL) {
+            T Uw[3];
+            rotate_vec(Rm, ph.uwall, Uw);
+            if (L == FLR_MOVING_WALL) moving_wall_ghost(tWL, tgL, ph.gm1, Uw);
+            if (Rc == FLR_MOVING_WALL) moving_wall_ghost(tWR, tgR, ph.gm1, Uw);
+        }
         T Fh[5], D[5], W0[5], dWt[5];
         gks_point(ph, tWL, tgL, tWR, tgR, dt, Fh, D, W0, dWt);
         to_global(Rm, Fh);
@@ -452,6 +465,7 @@ static Phys<T> make_phys(const HostPhys& p) {
     ph.smooth = p.smooth;
     ph.prf = (T)p.prf;
     ph.twall = (T)p.twall;
+    for (int i = 0; i < 3; ++i) ph.uwall[i] = (T)p.uwall[i];
     return ph;
 }
 

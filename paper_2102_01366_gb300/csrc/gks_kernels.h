@@ -65,7 +65,8 @@ struct HostPhys {
     double gamma, cfl, mu, eps_weno, tau_eps, tau_c;
     int weno, order, smooth, viscous;
     double prf;    // Pr fix factor 1/Pr - 1 (0: none)
-    double twall;  // isothermal wall temperature
+    double twall;     // isothermal wall temperature
+    double uwall[3];  // moving wall velocity
 };
 
 template <typename T>

@@ -31,7 +31,7 @@ class GksError(RuntimeError):
 class gks_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double),
                 ("eps_weno", C.c_double), ("tau_eps", C.c_double), ("tau_c", C.c_double),
-                ("prandtl", C.c_double), ("wall_temperature", C.c_double),
+                ("prandtl", C.c_double), ("wall_temperature", C.c_double), ("wall_velocity", C.c_double * 3),
                 ("weno", C.c_int32), ("order", C.c_int32), ("smooth_flux", C.c_int32),
                 ("viscous", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32)]
 
@@ -113,12 +113,14 @@ def _np_ptr(a):
 
 
 def params(gamma=1.4, cfl=1.0, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, weno=1, order=3,
-           smooth_flux=0, viscous=0, precision=0, prandtl=1.0, wall_temperature=1.0):
+           smooth_flux=0, viscous=0, precision=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0)):
     p = gks_params()
     lib().gks_params_default(C.byref(p))
     p.gamma, p.cfl, p.mu, p.eps_weno, p.tau_eps, p.tau_c = gamma, cfl, mu, eps_weno, tau_eps, tau_c
     p.prandtl = prandtl
     p.wall_temperature = wall_temperature
+    for i in range(3):
+        p.wall_velocity[i] = float(wall_velocity[i])
     p.weno, p.order, p.smooth_flux, p.viscous, p.precision = weno, order, smooth_flux, viscous, precision
     return p
 

@@ -364,7 +364,7 @@ def riemann_x_exact_density(mesh, t, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.
     return cell_average(mesh, f, order=order)[:, 0]
 
 
-BC_OPEN, BC_SLIP_WALL, BC_FIXED, BC_NOSLIP_WALL, BC_ISOTHERMAL_WALL = 0, 1, 2, 3, 4
+BC_OPEN, BC_SLIP_WALL, BC_FIXED, BC_NOSLIP_WALL, BC_ISOTHERMAL_WALL, BC_MOVING_WALL = 0, 1, 2, 3, 4, 5
 
 
 def boundary_kinds(mesh, spec):

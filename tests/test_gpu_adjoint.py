@@ -32,12 +32,12 @@ def cuda():
 
 
 def _case(seed=61, state="sine"):
-    if state in ("open", "slip", "noslip", "fixed", "isothermal"):
+    if state in ("open", "slip", "noslip", "fixed", "isothermal", "moving"):
         # open, wall or fixed-state ends on x, y and z periodic; a smooth moving state
         mesh = I.box_mesh((4, 3, 3), (1.0, 0.75, 0.75), (False, True, True), jitter=0.1, seed=seed)
         if state != "open":
             kind = {"slip": I.BC_SLIP_WALL, "noslip": I.BC_NOSLIP_WALL, "fixed": I.BC_FIXED,
-                    "isothermal": I.BC_ISOTHERMAL_WALL}[state]
+                    "isothermal": I.BC_ISOTHERMAL_WALL, "moving": I.BC_MOVING_WALL}[state]
             mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
         W, dW = I.sine_wave_state(mesh, k=8.0 * np.pi / 3.0, u=(0.6, 0.5, -0.3))
     elif state == "sine":
@@ -60,7 +60,7 @@ def _dot(a, b):
                                                        (0, 1, 1, "sine"), (1, 0, 0, "sine"), (1, 0, 0, "slab"),
                                                        (1, 0, 1, "slab"), (1, 0, 0, "open"), (1, 0, 1, "open"),
                                                        (1, 0, 0, "slip"), (0, 0, 1, "noslip"), (1, 0, 0, "fixed"),
-                                                       (0, 0, 1, "fixed"), (0, 0, 1, "isothermal")])
+                                                       (0, 0, 1, "fixed"), (0, 0, 1, "isothermal"), (1, 0, 1, "moving")])
 def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, viscous, state):
     """Viscous runs carry tau = mu / p_c and each side's time slope A
     through the reverse-mode point adjoint; weno = 1 differentiates the
@@ -77,7 +77,8 @@ def test_adjoint_matches_finite_differences(cuda, oracle_mod, weno, smooth, visc
     mesh, W, dW, rng = _case(state=state)
     H = 1e-7 if state == "slab" or (weno and viscous) else 1e-6
     g = gks.Mesh(mesh)
-    kw = dict(weno=weno, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous)
+    kw = dict(weno=weno, cfl=0.5, smooth_flux=smooth, viscous=viscous, mu=0.01 * viscous,
+              wall_velocity=(0.0, 0.4, -0.2) if state == "moving" else (0.0, 0.0, 0.0))
     s = gks.State(g, gks.params(precision=0, **kw))
     if state == "fixed":
         # the boundary state, set apart from the (perturbed) initialisations
@@ -268,7 +269,8 @@ def test_second_order_reconstruction_adjoint(cuda, oracle_mod, weno, state):
     ("open", 0, 0, 0, 1.0), ("open", 1, 0, 0, 1.0), ("slip", 1, 0, 0, 1.0), ("noslip", 0, 1, 0, 1.0),
     ("noslip", 1, 1, 0, 0.72), ("fixed", 1, 0, 0, 1.0), ("fixed", 0, 1, 0, 1.0), ("sine-o2", 0, 0, 0, 1.0),
     ("sine-o2", 1, 0, 0, 1.0), ("slab-o2", 1, 0, 0, 1.0), ("sine-lowp", 0, 0, 0, 1.0),
-    ("sine-lowp", 1, 0, 0, 1.0), ("isothermal", 0, 1, 0, 1.0), ("isothermal", 1, 1, 0, 0.72)])
+    ("sine-lowp", 1, 0, 0, 1.0), ("isothermal", 0, 1, 0, 1.0), ("isothermal", 1, 1, 0, 0.72),
+    ("moving", 0, 1, 0, 1.0), ("moving", 1, 1, 0, 1.0)])
 def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscous, smooth, prandtl):
     """The adjoint against an FP64 CPU reverse sweep: torch.autograd through
     the plain-PyTorch restatement of the step (oracle/torch_step.py, itself
@@ -288,7 +290,7 @@ def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscou
         W[4, 0] = 0.5 * (W[1, 0] ** 2 + W[2, 0] ** 2 + W[3, 0] ** 2) / W[0, 0] + 0.05 / 0.4
     g = gks.Mesh(mesh)
     kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, weno=weno, order=order,
-              wall_temperature=0.9)
+              wall_temperature=0.9, wall_velocity=(0.0, 0.4, -0.2))
     s = gks.State(g, gks.params(precision=0, cfl=0.5, **kw))
     fixed = None
     if state == "fixed":
@@ -302,7 +304,8 @@ def test_adjoint_matches_cpu_reverse_sweep(cuda, oracle_mod, state, weno, viscou
     Wt = torch.tensor(W, requires_grad=True)
     dWt = torch.tensor(dW, requires_grad=True)
     st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl,
-                 weno=bool(weno), kinds=mesh.get("bkind"), fixed=fixed, order=order, wall_temperature=0.9)
+                 weno=bool(weno), kinds=mesh.get("bkind"), fixed=fixed, order=order, wall_temperature=0.9,
+                 wall_velocity=(0.0, 0.4, -0.2))
     Wn, dWn = st(Wt, dWt, dt)
     if variant == "lowp":
         assert st.fallbacks[0][0]

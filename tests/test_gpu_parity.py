@@ -81,6 +81,11 @@ CASES = {
                                                               jitter=0.1, seed=42)),
                                lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.3, -0.2, 0.1)),
                                dict(weno=1, viscous=1, mu=0.01, wall_temperature=0.9)),
+    # a non-slip wall at x = 0 and a wall moving along y and z at x = 1, viscous
+    "moving_wall_box_viscous": (lambda: _moving(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True),
+                                                           jitter=0.1, seed=45)),
+                                lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.3, -0.2, 0.1)),
+                                dict(weno=1, viscous=1, mu=0.01, wall_velocity=(0.0, 0.4, -0.2))),
     # the sphere's O-type shell (pole rows of 3 tets per hexahedron), non-slip
     # wall at r = 0.5, far field held at r = 1.5, viscous, a perturbed free
     # stream; with linear weights the wall cells take the first-order fit
@@ -107,6 +112,11 @@ STEPS = {"sphere_shell_weno_viscous": 4}
 
 def _walled(mesh):
     mesh["bkind"] = I.wall_kinds(mesh, (0,))
+    return mesh
+
+
+def _moving(mesh):
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL, (0, "hi"): I.BC_MOVING_WALL})
     return mesh
 
 

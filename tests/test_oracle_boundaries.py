@@ -275,3 +275,65 @@ def test_isothermal_wall_heat_flows_from_hot_to_cold(oracle_mod, t_gas, sign):
     near = np.minimum(cen, 1.0 - cen) < 1.0 / 6.0
     assert sign * (T1[near].mean() - t_gas) > 0.02
     assert abs(T1[~near].mean() - t_gas) < 0.01
+
+
+def _moving_box(nx=6, nyz=2, seed=43):
+    mesh = I.box_mesh((nx, nyz, nyz), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=seed)
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL, (0, "hi"): I.BC_MOVING_WALL})
+    return mesh
+
+
+def test_moving_wall_at_rest_is_the_noslip_wall(oracle_mod):
+    """A moving wall with zero velocity is the non-slip adiabatic wall: the
+    face records agree to rounding."""
+    mesh = _moving_box()
+    W, dW = _smooth_state(mesh)
+    om = oracle_mod.Mesh(mesh)
+    mesh2 = dict(mesh)
+    mesh2["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL, (0, "hi"): I.BC_NOSLIP_WALL})
+    om2 = oracle_mod.Mesh(mesh2)
+    p = oracle_mod.params(weno=1, viscous=1, mu=0.01, wall_velocity=(0.0, 0.0, 0.0))
+    for stage in (1, 2):
+        a = om.face_records(p, W, dW, 2e-3, stage)
+        b = om2.face_records(p, W, dW, 2e-3, stage)
+        assert np.abs(a - b).max() < 1e-14 * np.abs(b).max()
+
+
+def test_gas_moving_with_the_wall_stays_uniform(oracle_mod):
+    """Gas moving along the walls with the walls' velocity (both x ends
+    moving with U_w = (0, 0.3, -0.2)) is a uniform steady flow: the moving
+    wall's ghost is then the interior state itself."""
+    mesh = I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=44)
+    mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): I.BC_MOVING_WALL, (0, "hi"): I.BC_MOVING_WALL})
+    nc = mesh["tet"].shape[0]
+    U = np.array([0.0, 0.3, -0.2])
+    W = np.zeros((5, nc))
+    W[0], W[1:4], W[4] = 1.1, 1.1 * U[:, None], 1.0 / 0.4 + 0.5 * 1.1 * U @ U
+    om = oracle_mod.Mesh(mesh)
+    p = oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.01, wall_velocity=tuple(U))
+    W1, dW1, _, _ = om.run(p, W, np.zeros((15, nc)), nsteps=5)
+    assert np.abs(W1 - W).max() < 1e-13
+    assert np.abs(dW1).max() < 1e-12
+
+
+def test_moving_wall_drives_the_gas(oracle_mod):
+    """Gas at rest; the x = 1 wall moves along y: the gas next to the moving
+    wall picks up y momentum (the viscous shear) while the far side has not
+    felt it yet, and the wall does work on the gas.  The ghost is the
+    at-rest one in the wall's frame, but the flux is evaluated at a fixed
+    point that the wall slides past, so with tangential gradients a little
+    mass (here 2e-6 of it in 6 steps) crosses the moving wall."""
+    mesh = _moving_box()
+    nc = mesh["tet"].shape[0]
+    W = np.zeros((5, nc))
+    W[0], W[4] = 1.0, 1.0 / 0.4
+    om = oracle_mod.Mesh(mesh)
+    geo = om.geometry()
+    vol, cx = geo["vol"], geo["cen"][:, 0]
+    p = oracle_mod.params(weno=1, cfl=0.5, viscous=1, mu=0.02, wall_velocity=(0.0, 0.3, 0.0))
+    W1, _, _, _ = om.run(p, W, np.zeros((15, nc)), nsteps=6)
+    assert abs((vol * W1[0]).sum() - (vol * W[0]).sum()) < 1e-5 * (vol * W[0]).sum()
+    v = W1[2] / W1[0]
+    assert v[cx > 5.0 / 6.0].mean() > 0.02
+    assert abs(v[cx < 1.0 / 6.0].mean()) < 1e-3
+    assert (vol * W1[4]).sum() > (vol * W[4]).sum()

@@ -211,7 +211,7 @@ def test_open_boundary_is_stable(oracle_mod):
     (1, 0, 0, 1.0, None), (1, 1, 0, 0.72, None), (0, 0, 0, 1.0, "open"), (1, 0, 0, 1.0, "slip"),
     (0, 1, 0, 1.0, "noslip"), (1, 1, 0, 0.72, "noslip"), (1, 0, 0, 1.0, "fixed"), (0, 1, 0, 1.0, "fixed"),
     (0, 0, 0, 1.0, "order2"), (1, 0, 0, 1.0, "order2"), (0, 0, 0, 1.0, "lowp"), (1, 0, 0, 1.0, "lowp"),
-    (1, 1, 0, 0.72, "isothermal")])
+    (1, 1, 0, 0.72, "isothermal"), (1, 1, 0, 1.0, "moving")])
 def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, smooth, prandtl, ends):
     """oracle/torch_step.py (the step in plain PyTorch CPU operations, for the
     autograd reverse sweep that checks the library's adjoint) reproduces the
@@ -230,7 +230,7 @@ def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, sm
         mesh = I.box_mesh((4, 3, 3), (1.0, 0.75, 0.75), (False, True, True), jitter=0.1, seed=61)
         if ends != "open":
             kind = {"slip": I.BC_SLIP_WALL, "noslip": I.BC_NOSLIP_WALL, "fixed": I.BC_FIXED,
-                    "isothermal": I.BC_ISOTHERMAL_WALL}[ends]
+                    "isothermal": I.BC_ISOTHERMAL_WALL, "moving": I.BC_MOVING_WALL}[ends]
             mesh["bkind"] = I.boundary_kinds(mesh, {(0, "lo"): kind, (0, "hi"): kind})
         W, dW = I.sine_wave_state(mesh, k=8.0 * math.pi / 3.0, u=(0.6, 0.5, -0.3))
     W = W * (1.0 + 0.01 * rng.standard_normal(W.shape))
@@ -241,12 +241,14 @@ def test_torch_restatement_matches_the_oracle_step(oracle_mod, weno, viscous, sm
         fixed = (W * (1.0 + 0.02 * rng.standard_normal(W.shape)), 0.5 * dW)
         mesh["fixed_state"] = fixed
     o = oracle_mod.Mesh(mesh)
-    kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, wall_temperature=0.9)
+    kw = dict(mu=0.01 * viscous, viscous=viscous, smooth_flux=smooth, prandtl=prandtl, wall_temperature=0.9,
+              wall_velocity=(0.0, 0.4, -0.2))
     p = oracle_mod.params(weno=weno, order=order, cfl=0.5, **kw)
     dt = 0.5 * o.timestep(p, W)
     Wo, dWo, _ = o.step(p, W, dW, dt)
     st = TS.Step(o, mu=kw["mu"], viscous=bool(viscous), smooth=bool(smooth), prandtl=prandtl, weno=bool(weno),
-                 kinds=mesh.get("bkind"), fixed=fixed, order=order, wall_temperature=0.9)
+                 kinds=mesh.get("bkind"), fixed=fixed, order=order, wall_temperature=0.9,
+                 wall_velocity=(0.0, 0.4, -0.2))
     Wt, dWt = st(torch.tensor(W), torch.tensor(dW), dt)
     assert bool(st.fallbacks[0].any()) == (ends == "lowp")
     for q in range(5):
