@@ -93,6 +93,20 @@ def test_rejects_bad_input(built):
     assert st == -7 and not h.value
     p.order = 4
     assert gks.lib().gks_workspace_bytes(g._h, C.byref(p)) == 0
+    for field, value in (("prandtl", 0.0), ("wall_temperature", -1.0), ("gamma", 1.0), ("cfl", 0.0)):
+        p = gks.params()
+        setattr(p, field, value)
+        assert gks.lib().gks_workspace_bytes(g._h, C.byref(p)) == 0, field
+    # unknown boundary kinds are refused, the known ones (open .. moving wall) accepted
+    gb = gks.Mesh(I.box_mesh((3, 2, 2), (1.0, 0.5, 0.5), (False, True, True), jitter=0.1, seed=5))
+    kinds = np.zeros((gb.nc, 4), np.int8)
+    for k in range(6):
+        kinds[:] = k
+        gb.set_boundary(kinds)
+    kinds[:] = 6
+    with pytest.raises(gks.GksError) as e:
+        gb.set_boundary(kinds)
+    assert e.value.status == -1
 
 
 def test_batch_connectivity_matches_each_case(built, oracle_mod):
