@@ -146,8 +146,26 @@ def l1_at(torch, gks, mesh, W0, dW0, precision, t_end):
     return float((vol * np.abs(W[0].cpu().numpy() - exact)).sum() / vol.sum()), W.cpu().numpy()
 
 
+_ORACLE_WORKER = """
+import sys, time
+sys.path.insert(0, {root!r})
+from paper_2102_01366_gb300 import inputs as I
+from oracle import oracle as O
+mesh, W, dW = I.sod_case(nx={nx}, nyz={nyz})
+om = O.Mesh(mesh)
+p = O.params(weno=1, cfl=0.5)
+t0 = time.perf_counter()
+for _ in range({n}):
+    W, dW, _ = om.step(p, W, dW)
+print(time.perf_counter() - t0)
+"""
+
+
 def cpu_baseline(max_seconds=20.0, max_steps=40):
-    """The FP64 oracle as it stands, single thread, on a bounded sample."""
+    """The FP64 oracle as it stands on a bounded sample: one thread, then one
+    independent copy of the same sample on every host core at once (separate
+    processes; the oracle itself is serial), the aggregate being the line's
+    value."""
     from oracle import oracle as O
     mesh, W, dW = I.sod_case(**CPU_SAMPLE)
     om = O.Mesh(mesh)
@@ -158,9 +176,27 @@ def cpu_baseline(max_seconds=20.0, max_steps=40):
         W, dW, _ = om.step(p, W, dW)
         n += 1
     el = time.perf_counter() - t0
-    return {"value": om.nc * 2 * n / el / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "%d steps of the Sod tube at 16x4x4 hexes x 6 = %d cells (same recipe, 1/16 size), "
-                      "FP64 C oracle, 1 thread" % (n, om.nc)}
+    single = om.nc * 2 * n / el / 1e6
+    sample = "%d steps of the Sod tube at 16x4x4 hexes x 6 = %d cells (same recipe, 1/16 size), FP64 C oracle" % (
+        n, om.nc)
+    out = {"value": single, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample + ", 1 thread"}
+    cores = os.cpu_count() or 1
+    if cores > 1:
+        code = _ORACLE_WORKER.format(root=ROOT, nx=CPU_SAMPLE["nx"], nyz=CPU_SAMPLE["nyz"], n=n)
+        procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                  text=True) for _ in range(cores)]
+        times = []
+        for pr in procs:
+            try:
+                o, _ = pr.communicate(timeout=20 * max_seconds)
+                times.append(float(o.strip().splitlines()[-1]))
+            except (subprocess.TimeoutExpired, ValueError, IndexError):
+                pr.kill()
+        if len(times) == cores:
+            out = {"value": cores * om.nc * 2 * n / max(times) / 1e6, "unit": METRIC, "cores": cores,
+                   "kind": "oracle", "sample": sample + ", one independent copy per core (%d processes)" % cores,
+                   "single_thread": {"value": single, "cores": 1}}
+    return out
 
 
 def batched_leg(torch, gks, args, flush):
