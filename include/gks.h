@@ -405,6 +405,14 @@ gks_status gks_debug_reconstruct(gks_state* state, double* d_poly, double* d_slo
  * (Sec. 2.2, Sec. 3 Eqs. linear-system, step-du). */
 gks_status gks_debug_face_records(gks_state* state, double dt, int32_t stage, double* d_rec);
 
+/* Failure path of the bounded device waits, without a fault: runs the
+ * reconstruction's mbarrier wait on a barrier that no copy completes
+ * (nothing is in flight), polling it `tries` times (0..65536); the give-up
+ * sets the state's device error flag as a stalled tile copy would.  Returns
+ * what the next synchronisation reports (GKS_E_TIMEOUT), then clears the
+ * flag so that the state stays usable.  Synchronises.  For tests. */
+gks_status gks_debug_wait_timeout(gks_state* state, int32_t tries);
+
 /* Last error message of this thread ("" if none). */
 const char* gks_last_error(void);
 

@@ -155,6 +155,9 @@ struct AdjBuffers {
     const int8_t* rev;
     int32_t* fallback;
 };
+// a bounded mbarrier wait that gives up (nothing completes it): sets ERR_TIMEOUT
+cudaError_t launch_wait_probe(int32_t* err, int tries, cudaStream_t s);
+
 // lambda (W^n, grad W^n) from lambda (W^{n+1}, grad W^{n+1}) for one step
 // with the frozen time step dt (public [component][cell] FP64 layouts)
 cudaError_t adjoint_reverse(const DevMesh<double>& m, const HostPhys& p, double dt, const AdjBuffers& b,

@@ -380,4 +380,24 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X,
 GKS_RECON_INST(double)
 GKS_RECON_INST(float)
 
+// The bounded wait's failure path without a fault: an mbarrier that expects
+// bytes no copy will deliver (nothing is in flight), polled `tries` times by
+// the same try_wait as the reconstruction's tile wait; giving up sets
+// ERR_TIMEOUT exactly as a stalled tile copy would.
+__global__ void k_wait_probe(int32_t* __restrict__ err, int tries) {
+    __shared__ alignas(8) unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);
+    __syncthreads();
+    bool ok = false;
+    for (int i = 0; i < tries && !ok; ++i) ok = mbar_try_wait(&bar, 0);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(int32_t* err, int tries, cudaStream_t s) {
+    k_wait_probe<<<1, 64, 0, s>>>(err, tries);
+    return cudaGetLastError();
+}
+
 }  // namespace gks

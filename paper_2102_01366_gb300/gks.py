@@ -89,6 +89,7 @@ def lib():
         "gks_adjoint_step": (C.c_int32, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
+        "gks_debug_wait_timeout": (C.c_int32, [_vp, C.c_int32]),
         "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32]),
         "gks_autotune": (C.c_int32, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32), _vp]),
@@ -392,6 +393,10 @@ class State:
         _call("gks_debug_reconstruct", self._h, _dptr(poly), _dptr(slopes), _dptr(fb))
         self.sync()
         return poly, slopes, fb
+
+    def debug_wait_timeout(self, tries=8):
+        """Status of a bounded device wait that gives up (gks_debug_wait_timeout)."""
+        return lib().gks_debug_wait_timeout(self._h, int(tries))
 
     def debug_face_records(self, dt, stage):
         t = self.torch

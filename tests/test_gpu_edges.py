@@ -61,3 +61,24 @@ def test_single_hexahedron(cuda, oracle_mod, precision, walls):
         vol = g.geometry()["vol"]
         for q in (0, 4):
             assert abs((Wg[q] * vol).sum() - (W[q] * vol).sum()) < 10 * TOL[precision] * abs((W[q] * vol).sum())
+
+
+def test_bounded_wait_gives_up_with_a_status_and_the_state_stays_usable(cuda, oracle_mod):
+    """The failure path of the bounded device waits, without a GPU fault:
+    the reconstruction's mbarrier wait, run on a barrier that nothing
+    completes (no copy in flight), gives up after its polls, the device
+    error flag reaches the host as GKS_E_TIMEOUT with its message, and the
+    same state then steps normally (matching the oracle)."""
+    mesh, W, dW = I.sine_wave_case(n=3)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5))
+    s.init(W, dW)
+    for tries in (0, 8):
+        assert s.debug_wait_timeout(tries) == -6  # GKS_E_TIMEOUT
+        assert b"bounded device wait" in gks.lib().gks_last_error()
+    s.init(W, dW)
+    s.step(1)
+    s.sync()
+    Wg = s.get()[0].cpu().numpy()
+    Wo, _, _, _ = oracle_mod.Mesh(mesh).run(oracle_mod.params(weno=1, cfl=0.5), W, dW, nsteps=1)
+    assert max(np.abs(Wg[q] - Wo[q]).max() / np.abs(Wo[q]).max() for q in range(5)) < 1e-11
