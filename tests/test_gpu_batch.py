@@ -118,3 +118,114 @@ def test_autotune_restores_state(cuda, tmp_path):
     s2 = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
     s2.init(W, dW)
     assert s2.autotune(steps=3, cache=str(tmp_path / "tune.json"))["cached"]
+
+
+def _rel_state(a, ref):
+    """Largest error of each conserved quantity over a case, relative to the
+    largest magnitude of that quantity there; the three momentum components
+    share one scale (the largest |rho U| entry), so a component that is zero
+    at the start (the Riemann slabs' transverse momentum) is not divided by
+    its own rounding-level values."""
+    mom = np.abs(ref[1:4]).max()
+    out = 0.0
+    for q in range(5):
+        scale = mom if 1 <= q <= 3 else np.abs(ref[q]).max()
+        out = max(out, np.abs(a[q] - ref[q]).max() / max(scale, 1e-300))
+    return out
+
+
+def _rel_grad(a, ref):
+    """The same for the gradients ([15][n], direction-minor): each
+    quantity's three directions share its largest magnitude, the momentum
+    components one scale between them; a quantity with no gradient above
+    1e-10 is skipped."""
+    mom = np.abs(ref[3:12]).max()
+    out = 0.0
+    for q in range(5):
+        scale = mom if 1 <= q <= 3 else np.abs(ref[3 * q:3 * q + 3]).max()
+        if scale > 1e-10:
+            out = max(out, np.abs(a[3 * q:3 * q + 3] - ref[3 * q:3 * q + 3]).max() / scale)
+    return out
+
+
+def test_batched_workload_full_size_one_step(cuda, oracle_mod):
+    """The 48-case batched workload at full size (6,486,324 cells: periodic
+    unit cubes of 8^3..40^3 hexes x 6 tets, seed 5, density waves and Riemann
+    slabs at Mach 0.5-3), run the way the benchmark times it: FP32 bulk,
+    WENO, CFL 0.5, the autotuned variant, one CUDA graph per step.  After one
+    step:
+      * the two smallest cases (a Riemann slab, 10^3 hexes, and a density
+        wave, 12^3) match the oracle element by element, averages and
+        gradients, at the FP32 tolerance;
+      * every case conserves mass, momentum and energy to FP64 rounding
+        (each face record enters its two cells with opposite signs, and the
+        cell sums are FP64);
+      * every case's cell averages agree with the FP64 path within the FP32
+        tolerance, and the FP64 path matches the oracle on the sampled cases
+        at 1e-11;
+      * every case's gradients agree with the FP64 path within a bound that
+        grows as the cells shrink.  The gradients are evolved from the face
+        states by the divergence theorem (Sec. 3, Eq. step-du), so a face
+        state rounded to FP32 (relative error delta) moves a cell's gradient
+        by about delta |W| sum_f A_f / |Omega| = 3 delta |W| / dr, with dr
+        = 3 |Omega| / sum_f A_f (Sec. 5).  The bound is 32 FP32 unit
+        roundoffs of the case's largest state entry times the largest
+        3 / dr of the case; a missing face or a wrong sign would exceed it by
+        about five orders of magnitude.  (The cell averages carry no such
+        factor: their flux increments scale with dt, which shrinks with the
+        cells.)"""
+    batch, W, dW, desc, meshes = I.batch_cases(n_cases=48, n_range=(8, 40), seed=5)
+    g = gks.Mesh(batch)
+    first = g.case_first
+    assert g.ncase == 48 and g.nc == 6486324
+    geo = g.geometry()
+    vol, dr = geo["vol"], geo["dr"]
+    res = {}
+    for precision in (1, 0):
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+        s.init(W, dW)
+        if precision == 1:
+            s.autotune(steps=5, cache=False)  # restores the initial state
+        s.step(1)
+        s.sync()
+        res[precision] = [x.cpu().numpy() for x in s.get()] + [s.case_times()[0]]
+        del s
+        cuda.cuda.empty_cache()
+
+    # sampled cases against the oracle, both precisions
+    sample = sorted(range(48), key=lambda k: desc[k]["n"])[:2]
+    assert {desc[k]["kind"] for k in sample} == {"sine", "riemann"}
+    p = oracle_mod.params(weno=1, cfl=0.5)
+    for k in sample:
+        c0, c1 = first[k], first[k + 1]
+        Wo, dWo, to, _ = oracle_mod.Mesh(meshes[k]).run(p, W[:, c0:c1], dW[:, c0:c1], nsteps=1)
+        for precision, (Wg, dWg, tg) in res.items():
+            assert abs(tg[k] - to) <= TOL[precision] * to, (k, precision)
+            assert _rel_state(Wg[:, c0:c1], Wo) < TOL[precision], (k, precision)
+            assert _rel_grad(dWg[:, c0:c1], dWo) < 10 * TOL[precision], (k, precision)
+
+    # every case: conservation and FP32 against FP64
+    W32, dW32, t32 = res[1]
+    W64, dW64, t64 = res[0]
+    # the FP32 path forms its time step from its FP32 copy of the state
+    np.testing.assert_allclose(t32, t64, rtol=TOL[1], atol=0)
+    u32 = 2.0 ** -24
+    worst = {"drift": 0.0, "state": 0.0, "grad_rel": 0.0, "grad_bound": 0.0}
+    for k in range(48):
+        c0, c1 = first[k], first[k + 1]
+        v = vol[c0:c1]
+        total0 = W[:, c0:c1] @ v
+        scale = (np.abs(W[:, c0:c1]) @ v).max()
+        for Wg in (W32, W64):
+            drift = np.abs(Wg[:, c0:c1] @ v - total0).max()
+            assert drift <= 1e-11 * scale, (k, drift / scale)
+            worst["drift"] = max(worst["drift"], drift / scale)
+        state = _rel_state(W32[:, c0:c1], W64[:, c0:c1])
+        assert state < TOL[1], (k, state)
+        worst["state"] = max(worst["state"], state)
+        bound = 32 * u32 * np.abs(W64[:, c0:c1]).max() * (3.0 / dr[c0:c1]).max()
+        gerr = np.abs(dW32[:, c0:c1] - dW64[:, c0:c1]).max()
+        assert gerr <= bound, (k, desc[k], gerr / bound)
+        worst["grad_bound"] = max(worst["grad_bound"], gerr / bound)
+        worst["grad_rel"] = max(worst["grad_rel"], _rel_grad(dW32[:, c0:c1], dW64[:, c0:c1]))
+    print("batched full size, worst over 48 cases:", {k: float("%.3g" % v) for k, v in worst.items()})
