@@ -338,3 +338,58 @@ def test_residual_matches_state_change(cuda):
     r = s.residual()
     ref = np.sqrt((((Wb - Wa).cpu().numpy() / dt) ** 2).mean(1))
     np.testing.assert_allclose(r, ref, rtol=1e-10)
+
+
+def test_config4_vortex_full_size_one_step(cuda, oracle_mod):
+    """The isentropic vortex (strength 5, free stream Ma 0.5 along the
+    diagonal, periodic [0,10]^3) in the configuration the benchmark's adjoint
+    leg runs: linear weights, CFL 0.5.  The recipe is checked against the
+    oracle element by element on 16^3 hexes x 6 (24,576 cells), FP64 and
+    FP32 bulk.  At full size (64^3 x 6 = 1,572,864 cells), where the oracle
+    would take minutes, one step is checked by what holds at any size:
+    Sum |Omega| W conserved to FP64 rounding in both precisions, the FP32
+    cell averages within 2e-5 of the FP64 path's (momentum components on one
+    shared scale), and the FP32 gradients within the bound that grows as the
+    cells shrink (32 FP32 unit roundoffs x the largest state entry x the
+    largest 3 / dr: the gradients come from the face states by the divergence
+    theorem, Sec. 3, Eq. step-du)."""
+    kw = dict(weno=0, cfl=0.5)
+    mesh, W, dW = I.isentropic_vortex_case(n=16, order=2)
+    Wo, dWo, to, _ = oracle_mod.Mesh(mesh).run(oracle_mod.params(**kw), W, dW, nsteps=1)
+    g = gks.Mesh(mesh)
+    for precision in (0, 1):
+        s = gks.State(g, gks.params(precision=precision, **kw))
+        s.init(W, dW)
+        s.step(1)
+        s.sync()
+        Wg, dWg = [x.cpu().numpy() for x in s.get()]
+        assert abs(s.time()[0] - to) <= TOL[precision] * to
+        assert _state_rel(Wg, Wo) < TOL[precision]
+        for q in range(5):
+            assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10, q
+
+    mesh, W, dW = I.isentropic_vortex_case(n=64, order=2)
+    g = gks.Mesh(mesh)
+    assert g.nc == 1572864
+    geo = g.geometry()
+    vol, dr = geo["vol"], geo["dr"]
+    res = {}
+    for precision in (0, 1):
+        s = gks.State(g, gks.params(precision=precision, **kw))
+        s.init(W, dW)
+        s.step(1)
+        s.sync()
+        res[precision] = [x.cpu().numpy() for x in s.get()] + [s.time()[0]]
+        del s
+    total0 = W @ vol
+    scale = (np.abs(W) @ vol).max()
+    for precision, (Wg, _, _) in res.items():
+        assert np.abs(Wg @ vol - total0).max() <= 1e-11 * scale, precision
+    (W64, dW64, t64), (W32, dW32, t32) = res[0], res[1]
+    assert abs(t32 - t64) <= TOL[1] * t64
+    mom = np.abs(W64[1:4]).max()
+    for q in range(5):
+        sc = mom if 1 <= q <= 3 else np.abs(W64[q]).max()
+        assert np.abs(W32[q] - W64[q]).max() < TOL[1] * sc, q
+    bound = 32 * 2.0 ** -24 * np.abs(W64).max() * (3.0 / dr).max()
+    assert np.abs(dW32 - dW64).max() <= bound, np.abs(dW32 - dW64).max() / bound
