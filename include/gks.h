@@ -322,9 +322,10 @@ gks_status gks_timestep(gks_state* state, double* dt);
  * Enqueues two small kernels and returns without synchronising.  Its
  * scratch is a fixed device array of GKS_NOALLOC_MAX_BLOCKS doubles held by
  * every GPU that loads the library; n_cell above 256 * that count is
- * rejected with GKS_E_ARG.  The first call on a device resolves the array's
- * address (cudaGetSymbolAddress) with that device current, so make it
- * before any stream capture.  All calls share the array: calls that overlap
+ * rejected with GKS_E_ARG, as is a current device ordinal of 64 or more
+ * (the per-device address cache has 64 slots).  The first call on a
+ * device resolves the array's address (cudaGetSymbolAddress) with that
+ * device current, so make it before any stream capture.  All calls share the array: calls that overlap
  * on the GPU (unordered streams) race.  Allocates nothing, frees nothing. */
 gks_status gks_timestep_noalloc(const gks_params* p, const double* d_W, const double* d_dr,
                                 int64_t n_cell, double* d_dt, void* stream);

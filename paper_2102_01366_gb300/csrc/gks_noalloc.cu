@@ -96,9 +96,14 @@ extern "C" gks_status gks_timestep_noalloc(const gks_params* p, const double* d_
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    if (e != cudaSuccess) {
         set_error(std::string("gks_timestep_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return GKS_E_CUDA;
+    }
+    if (dev < 0 || dev >= NA_MAX_DEVICES) {
+        set_error("gks_timestep_noalloc: device ordinal " + std::to_string(dev) + " beyond the " +
+                  std::to_string(NA_MAX_DEVICES) + " devices it keeps scratch addresses for");
+        return GKS_E_ARG;
     }
     double* part = nullptr;
     {
