@@ -139,3 +139,31 @@ def test_empty_mesh_is_rejected(built):
     with pytest.raises(gks.GksError) as e:
         gks.Mesh(mesh)
     assert e.value.status == -1
+
+
+def test_mesh_errors_found_on_worker_threads_reach_the_caller(built):
+    """Mesh set-up splits its loops over the host's threads (48,000 cells
+    here, so the last cells belong to a worker); a fault found there must
+    come back as GKS_E_MESH with its message on the calling thread."""
+    mesh = I.box_mesh((20, 20, 20), jitter=0.1, seed=6)
+    nc = mesh["tet"].shape[0]
+    # a tetrahedron that repeats a vertex id, in the last cell
+    bad = dict(mesh)
+    tet = mesh["tet"].copy()
+    tet[nc - 1, 3] = tet[nc - 1, 0]
+    bad["tet"] = tet
+    with pytest.raises(gks.GksError) as e:
+        gks.Mesh(bad)
+    assert e.value.status == -2 and "repeats a vertex" in str(e.value)
+    # a duplicated last cell: each of its faces is shared by three cells
+    bad = dict(mesh)
+    bad["tet"] = np.concatenate([mesh["tet"], mesh["tet"][-1:]])
+    bad["shift"] = np.concatenate([mesh["shift"], mesh["shift"][-1:]])
+    with pytest.raises(gks.GksError) as e:
+        gks.Mesh(bad)
+    assert e.value.status == -2 and "more than two cells" in str(e.value)
+    # and the intact mesh still builds, every local face in the face list
+    g = gks.Mesh(mesh)
+    top = g.topology()
+    assert g.nf == 2 * nc and (top["csr_face"] >= 0).all()
+    assert np.bincount(top["csr_face"].ravel(), minlength=g.nf).tolist() == [2] * g.nf
