@@ -457,7 +457,8 @@ def wall_pressure_force(mesh, kinds, gamma=1.4, wall=(1, 3), device="cuda"):
     return force
 
 
-def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=20, primal_precision=0):
+def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=20, primal_precision=0,
+                          device="cuda"):
     """Gradient of loss(W_N) after N steps of frozen step dt with respect to
     the initial (W0, dW0), by the adjoint with checkpointing: the primal run
     keeps every `checkpoint_every`-th state (in FP64, on the device), the
@@ -469,7 +470,9 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
     scalar.  primal_precision 1 runs the primal in FP32 bulk (the checkpoints
     are its FP64 master states); the reverse sweep is FP64 either way, so the
     gradient then belongs to FP64 segments restarted from FP32-run
-    checkpoints.  Returns (loss value, dJ/dW0, dJ/d dW0)."""
+    checkpoints.  device: where the inputs, checkpoints and adjoints are
+    kept (the library's states live on the GPU).  Returns (loss value,
+    dJ/dW0, dJ/d dW0)."""
     import torch
     if not isinstance(mesh, Mesh):
         mesh = Mesh(mesh)
@@ -484,9 +487,9 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
         pp.precision = 1
         primal = State(mesh, pp)
     W = torch.as_tensor(np.ascontiguousarray(W0) if isinstance(W0, np.ndarray) else W0,
-                        dtype=torch.float64, device="cuda")
+                        dtype=torch.float64, device=device)
     dW = torch.as_tensor(np.ascontiguousarray(dW0) if isinstance(dW0, np.ndarray) else dW0,
-                         dtype=torch.float64, device="cuda")
+                         dtype=torch.float64, device=device)
     checkpoints = {0: (W.clone(), dW.clone())}
     primal.init(W, dW)
     for n in range(1, nsteps + 1):
@@ -499,7 +502,7 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
     J = loss(Wn)
     J.backward()
     lam_W = Wn.grad.detach().clone()
-    lam_dW = torch.zeros((15, mesh.nc), dtype=torch.float64, device="cuda")
+    lam_dW = torch.zeros((15, mesh.nc), dtype=torch.float64, device=device)
     starts = sorted(checkpoints)
     for k in reversed(range(len(starts))):
         n0 = starts[k]
