@@ -1,4 +1,6 @@
-"""The checkpoint schedule of gks.checkpointed_gradient (host logic, no GPU).
+"""Host logic of the gradient helpers, on the CPU: the checkpoint schedule
+of gks.checkpointed_gradient, the autograd wrapper gks.make_step_function,
+and the wall-force output gks.wall_pressure_force.
 
 The library's State is replaced by a stand-in whose step is a nonlinear
 pointwise map and whose adjoint_step is that map's exact transpose at the
@@ -7,10 +9,12 @@ once in the primal, every segment is recomputed from its own checkpoint,
 and each adjoint step receives the state its forward step started from.
 The result is compared with torch.autograd through the same steps run
 without checkpoints."""
+import numpy as np
 import pytest
 import torch
 
 from paper_2102_01366_gb300 import gks
+from paper_2102_01366_gb300 import inputs as I
 
 NC = 7
 
@@ -24,8 +28,10 @@ def _f(W, dW, dt):
 class _FakeState:
     log = []
 
-    def __init__(self, mesh, params):
-        self.precision = params.precision
+    torch = torch
+
+    def __init__(self, mesh=None, params=None):
+        self.precision = params.precision if params is not None else 0
         self.W = self.dW = None
 
     def init(self, W, dW):
@@ -44,10 +50,11 @@ class _FakeState:
 
     def adjoint_step(self, Ws, dWs, lam_W, lam_dW, dt):
         _FakeState.log.append(("adjoint", self.precision))
-        W = Ws.clone().requires_grad_(True)
-        dW = dWs.clone().requires_grad_(True)
-        W1, dW1 = _f(W, dW, dt)
-        gW, gdW = torch.autograd.grad((W1, dW1), (W, dW), (lam_W, lam_dW))
+        with torch.enable_grad():  # also when called from a backward pass
+            W = Ws.clone().requires_grad_(True)
+            dW = dWs.clone().requires_grad_(True)
+            W1, dW1 = _f(W, dW, dt)
+            gW, gdW = torch.autograd.grad((W1, dW1), (W, dW), (lam_W, lam_dW))
         return gW, gdW
 
 
@@ -105,3 +112,62 @@ def test_fp32_primal_uses_its_own_state_and_fp64_segments(monkeypatch):
     primal = [p for k, p in _FakeState.log[:6]]
     assert primal == [1] * 6  # the primal run in FP32 bulk
     assert all(p == 0 for _, p in _FakeState.log[6:])  # recomputation and adjoint in FP64
+
+
+@pytest.mark.parametrize("use_dW", [True, False])
+def test_step_function_chain_matches_autograd(use_dW):
+    """Four chained applications of make_step_function (backward through
+    the state's adjoint step, each step's input kept) against autograd
+    through the same steps; with use_dW False the loss ignores the final
+    gradients, so the wrapper's backward gets no gradient for them."""
+    st = _FakeState()
+    dt = 0.09
+    step = gks.make_step_function(st, dt)
+    W0, dW0 = _inputs()
+
+    def run(fn):
+        W = W0.clone().requires_grad_(True)
+        dW = dW0.clone().requires_grad_(True)
+        Wn, dWn = W, dW
+        for _ in range(4):
+            Wn, dWn = fn(Wn, dWn)
+        J = _loss(Wn) + ((dWn ** 2).sum() if use_dW else 0.0)
+        return torch.autograd.grad(J, (W, dW))
+
+    got = run(step)
+    ref = run(lambda W, dW: _f(W, dW, dt))
+    for a, b in zip(got, ref):
+        torch.testing.assert_close(a, b, rtol=1e-13, atol=1e-15)
+
+
+def test_wall_pressure_force_on_a_closed_wall():
+    """The inner sphere of a shell mesh is a closed wall: a uniform pressure
+    gives no net force (every wall face found, each with its outward
+    sign), and the force's derivative with respect to one wall cell's
+    pressure is the sum of A n over that cell's wall faces."""
+    mesh = I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08)
+    g = gks.Mesh(mesh, build_stencils=False)
+    force = gks.wall_pressure_force(g, mesh["bkind"], device="cpu")
+    gamma = 1.4
+    p0 = 0.8
+    W = torch.zeros((5, g.nc), dtype=torch.float64)
+    W[0] = 1.0
+    W[1] = 0.3
+    W[4] = p0 / (gamma - 1.0) + 0.5 * 0.3 ** 2
+    top, geo = g.topology(), g.geometry()
+    kinds = np.asarray(mesh["bkind"]).reshape(g.nc, 4)
+    on = (top["nbr"] < 0) & np.isin(kinds, (1, 3))
+    area = geo["farea"][top["csr_face"][on]].sum()
+    assert 0.9 * np.pi < area < 1.01 * np.pi  # the polyhedral sphere of radius 0.5
+    F = force(W)
+    assert float(F.abs().max()) < 1e-13 * p0 * area
+    # d F / d p of one wall cell, through rho E at fixed rho and rho U
+    c = int(np.nonzero(on.any(1))[0][0])
+    Wc = W.clone().requires_grad_(True)
+    Fx = force(Wc)
+    rows = [torch.autograd.grad(Fx[i], Wc, retain_graph=True)[0][4, c] / (gamma - 1.0) for i in range(3)]
+    an = np.zeros(3)
+    for f in np.nonzero(on[c])[0]:
+        e = top["csr_face"][c, f]
+        an += geo["farea"][e] * geo["fnorm"][e] * top["csr_sign"][c, f]
+    np.testing.assert_allclose([float(r) for r in rows], an, rtol=1e-12, atol=1e-15)
