@@ -685,6 +685,66 @@ static void monomial_eval(const double* P, const double X[3], double* val, doubl
     }
 }
 
+/* beta_0 of the two-step reconstruction (Sec. 4.3, Eq. p0-non-linear-weight)
+ * from the step-1 slopes b[j] of the cell's nn neighbours:
+ *   beta_0,j = |Delta_0| |b_j|^2 with |Delta_0| = |Omega_0|^(2/3) (READING),
+ *   sigma^1st = (mean over the neighbour pairs j > k of |beta_0,j - beta_0,k|)^(4/3)
+ *   (READING: the mean over the existing pairs, 6 for an interior cell),
+ *   omega^1st_j = 1 + sigma^1st / (eps + beta_0,j), normalised, and
+ *   beta_0 = sum_j wbar^1st_j beta_0,j.
+ * sigma1 and wbar1[nn] (each may be NULL) receive the intermediate values. */
+static double weno_beta0(double vol, const double b[][3], int nn, double eps, double* sigma1,
+                         double* wbar1) {
+    double b0j[4];
+    for (int j = 0; j < nn; ++j) b0j[j] = pow(vol, 2.0 / 3.0) * (b[j][0] * b[j][0] + b[j][1] * b[j][1] + b[j][2] * b[j][2]);
+    double beta0 = 0.0, s1 = 0.0;
+    if (nn > 0) {
+        double sum = 0.0;
+        int npair = 0;
+        for (int j = 0; j < nn; ++j)
+            for (int k = 0; k < j; ++k) { sum += fabs(b0j[j] - b0j[k]); ++npair; }
+        s1 = npair ? pow(sum / npair, 4.0 / 3.0) : 0.0;
+        double w1[4], ws = 0.0;
+        for (int j = 0; j < nn; ++j) { w1[j] = 1.0 + s1 / (eps + b0j[j]); ws += w1[j]; }
+        for (int j = 0; j < nn; ++j) {
+            beta0 += w1[j] / ws * b0j[j];
+            if (wbar1) wbar1[j] = w1[j] / ws;
+        }
+    }
+    if (sigma1) *sigma1 = s1;
+    return beta0;
+}
+
+/* normalised nonlinear weights (Sec. 4.2, Eq. non-linear-weight) of p_0, p_1
+ * (order 2) or p_0, p_1, p_2 (order 3) into wbar[3]:
+ *   sigma = |beta_1 - beta_0|^(4/3) (order 2) or
+ *   (1/2 (|beta_2 - beta_1| + |beta_2 - beta_0|))^(4/3) (order 3),
+ *   omega_m = gamma_m (1 + (sigma / (eps + beta_m))^2), wbar_m = omega_m / sum omega,
+ * with gamma_1,1 : gamma_0,1 = 10 : 1 and gamma_2,2 : gamma_1,2 : gamma_0,2 =
+ * 100 : 10 : 1 (READING of the Table 2 caption).  wbar[2] = 0 for order 2. */
+static void weno_weights(int order, double eps, double beta0, double beta1, double beta2, double wbar[3]) {
+    if (order == 2) {
+        const double g11 = 10.0 / 11.0, g01 = 1.0 / 11.0;
+        double sigma = pow(fabs(beta1 - beta0), 4.0 / 3.0);
+        double w0 = g01 * (1.0 + pow(sigma / (eps + beta0), 2));
+        double w1 = g11 * (1.0 + pow(sigma / (eps + beta1), 2));
+        double ws = w0 + w1;
+        wbar[0] = w0 / ws;
+        wbar[1] = w1 / ws;
+        wbar[2] = 0.0;
+    } else {
+        const double g22 = 100.0 / 111.0, g12 = 10.0 / 111.0, g02 = 1.0 / 111.0;
+        double sigma = pow(0.5 * (fabs(beta2 - beta1) + fabs(beta2 - beta0)), 4.0 / 3.0);
+        double w0 = g02 * (1.0 + pow(sigma / (eps + beta0), 2));
+        double w1 = g12 * (1.0 + pow(sigma / (eps + beta1), 2));
+        double w2 = g22 * (1.0 + pow(sigma / (eps + beta2), 2));
+        double ws = w0 + w1 + w2;
+        wbar[0] = w0 / ws;
+        wbar[1] = w1 / ws;
+        wbar[2] = w2 / ws;
+    }
+}
+
 static void slopes_all(const ora_mesh* m, const double* W, double* b) {
     /* Reconstruction step 1 (Sec. 4.3): P1 slopes of every cell */
     for (int64_t c = 0; c < m->nc; ++c)
@@ -747,29 +807,20 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
             if (!p->weno) {
                 for (int k = 0; k < 10; ++k) Rb[k] = p->order == 2 ? P1[k] : P2[k];
             } else {
-                /* beta_0 from the neighbours' step-1 slopes (Eq. p0-non-linear-weight);
-                 * READING: |Delta_0| = |Omega_0|^(2/3); the pair average uses the
-                 * number of neighbour pairs (6 for an interior cell). */
-                double b0j[4];
+                /* beta_0 from the neighbours' step-1 slopes (Eq. p0-non-linear-weight) */
+                double bj[4][3];
                 int nn = 0;
                 for (int f = 0; f < 4; ++f) {
                     int64_t nb = m->nbr[c * 4 + f];
                     if (nb < 0) continue;
-                    const double* bj = &b[(nb * 5 + q) * 3];
-                    b0j[nn++] = pow(vol, 2.0 / 3.0) * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
+                    for (int i = 0; i < 3; ++i) bj[nn][i] = b[(nb * 5 + q) * 3 + i];
+                    ++nn;
                 }
-                double beta0 = 0.0;
-                if (nn > 0) {
-                    double sum = 0.0;
-                    int npair = 0;
-                    for (int j = 0; j < nn; ++j)
-                        for (int k = 0; k < j; ++k) { sum += fabs(b0j[j] - b0j[k]); ++npair; }
-                    double s1 = npair ? pow(sum / npair, 4.0 / 3.0) : 0.0;
-                    double w1[4], ws = 0.0;
-                    for (int j = 0; j < nn; ++j) { w1[j] = 1.0 + s1 / (eps + b0j[j]); ws += w1[j]; }
-                    for (int j = 0; j < nn; ++j) beta0 += w1[j] / ws * b0j[j];
-                }
+                double beta0 = weno_beta0(vol, bj, nn, eps, NULL, NULL);
                 double beta1 = smoothness(m, c, P1, 1);
+                double beta2 = p->order == 2 ? 0.0 : smoothness(m, c, P2, 2);
+                double wbar[3];
+                weno_weights(p->order, eps, beta0, beta1, beta2, wbar);
                 double p0[10], p1[10], p2[10];
                 for (int k = 0; k < 10; ++k) {
                     p0[k] = P0[k];
@@ -777,20 +828,10 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
                 }
                 for (int k = 0; k < 10; ++k) p2[k] = (P2[k] - g12 * p1[k] - g02 * p0[k]) / g22;
                 if (p->order == 2) {
-                    double sigma = pow(fabs(beta1 - beta0), 4.0 / 3.0);
-                    double w0 = g01 * (1.0 + pow(sigma / (eps + beta0), 2));
-                    double w1 = g11 * (1.0 + pow(sigma / (eps + beta1), 2));
-                    double ws = w0 + w1;
-                    for (int k = 0; k < 10; ++k) Rb[k] = w1 / ws * p1[k] + w0 / ws * p0[k];
+                    for (int k = 0; k < 10; ++k) Rb[k] = wbar[1] * p1[k] + wbar[0] * p0[k];
                 } else {
-                    double beta2 = smoothness(m, c, P2, 2);
-                    double sigma = pow(0.5 * (fabs(beta2 - beta1) + fabs(beta2 - beta0)), 4.0 / 3.0);
-                    double w0 = g02 * (1.0 + pow(sigma / (eps + beta0), 2));
-                    double w1 = g12 * (1.0 + pow(sigma / (eps + beta1), 2));
-                    double w2 = g22 * (1.0 + pow(sigma / (eps + beta2), 2));
-                    double ws = w0 + w1 + w2;
                     for (int k = 0; k < 10; ++k)
-                        Rb[k] = w2 / ws * p2[k] + w1 / ws * p1[k] + w0 / ws * p0[k];
+                        Rb[k] = wbar[2] * p2[k] + wbar[1] * p1[k] + wbar[0] * p0[k];
                 }
             }
             basis_to_monomial(m, c, Rb, R[q]);
@@ -820,6 +861,21 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
     if (slopes_out) memcpy(slopes_out, b, sizeof(double) * nc * 15);
     free(b);
     return 0;
+}
+
+double ora_smoothness(const ora_mesh* m, int64_t c, const double* v, int r) {
+    return smoothness(m, c, v, r);
+}
+
+double ora_weno_beta0(double vol, const double* b, int nn, double eps, double* sigma1, double* wbar1) {
+    double bj[4][3];
+    for (int j = 0; j < nn && j < 4; ++j)
+        for (int i = 0; i < 3; ++i) bj[j][i] = b[3 * j + i];
+    return weno_beta0(vol, (const double(*)[3])bj, nn < 4 ? nn : 4, eps, sigma1, wbar1);
+}
+
+void ora_weno_weights(int order, double eps, double beta0, double beta1, double beta2, double* wbar) {
+    weno_weights(order, eps, beta0, beta1, beta2, wbar);
 }
 
 /* ------------------------------------------------------------------------ */

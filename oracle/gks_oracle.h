@@ -81,6 +81,21 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
                     const double* dW, double* poly, double* slopes,
                     int32_t* fallback);
 
+/* Pieces of the reconstruction, exposed so that tests can pin them:
+ * ora_smoothness: the smoothness indicator of Eq. smooth-indicator (Sec. 4.2)
+ * of cell c for a polynomial v[10] in the cell's zero-mean basis form
+ * (v[0] constant, v[1..3] linear, v[4..9] the quadratic basis in the order
+ * xx, xy, xz, yy, yz, zz), r = 1 (first derivatives only) or 2.
+ * ora_weno_beta0: beta_0 of Sec. 4.3 (Eq. p0-non-linear-weight) from the
+ * step-1 slopes b[nn][3] of nn <= 4 neighbours on a cell of volume vol;
+ * sigma1 and wbar1[nn] (may be NULL) receive sigma^1st and the normalised
+ * weights omega-bar^1st_j.
+ * ora_weno_weights: the normalised nonlinear weights (Eq. non-linear-weight)
+ * of p_0, p_1 (order 2) or p_0, p_1, p_2 (order 3) into wbar[3]. */
+double ora_smoothness(const ora_mesh* m, int64_t c, const double* v, int r);
+double ora_weno_beta0(double vol, const double* b, int nn, double eps, double* sigma1, double* wbar1);
+void ora_weno_weights(int order, double eps, double beta0, double beta1, double beta2, double* wbar);
+
 /* Time-dependent kinetic solution at one Gauss point, everything in the local
  * face frame (x1 along the normal).  dWl[i][q] = d W_q / d x_i.  Outputs the
  * time integrals of the flux over [0, dt/2] and [0, dt] and the point values

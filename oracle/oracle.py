@@ -78,6 +78,11 @@ def lib():
                                C.POINTER(C.c_double)]
         L.ora_s2o4_linear_ode.restype = C.c_double
         L.ora_s2o4_linear_ode.argtypes = [C.c_double]
+        L.ora_smoothness.restype = C.c_double
+        L.ora_smoothness.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int]
+        L.ora_weno_beta0.restype = C.c_double
+        L.ora_weno_beta0.argtypes = [C.c_double, _dp, C.c_int, C.c_double, C.POINTER(C.c_double), _dp]
+        L.ora_weno_weights.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _dp]
         _lib = L
     return _lib
 
@@ -152,6 +157,11 @@ class Mesh:
                               np.ascontiguousarray(dW, dtype=np.float64), poly, slopes, fb)
         return poly, slopes, fb
 
+    def smoothness(self, c, v, r):
+        """Smoothness indicator (Sec. 4.2) of cell c for the basis-form
+        polynomial v[10]; r = 1 or 2."""
+        return lib().ora_smoothness(self._h, int(c), np.ascontiguousarray(v, dtype=np.float64), int(r))
+
     def face_records(self, p, W, dW, dt, stage):
         rec = np.zeros((self.nf, 40 if stage == 1 else 20))
         if lib().ora_face_records(self._h, C.byref(p), np.ascontiguousarray(W, dtype=np.float64),
@@ -197,6 +207,24 @@ def gp_flux(p, Wl, dWl, Wr, dWr, dt):
                       np.ascontiguousarray(Wr, dtype=np.float64),
                       np.ascontiguousarray(dWr, dtype=np.float64), float(dt), *out)
     return tuple(out)
+
+
+def weno_beta0(vol, b, eps=1e-8):
+    """beta_0 of the two-step reconstruction (Sec. 4.3) from the neighbours'
+    step-1 slopes b[nn][3]; returns (beta_0, sigma^1st, wbar^1st[nn])."""
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 3)
+    s1 = C.c_double(0.0)
+    w1 = np.zeros(max(len(b), 1))
+    beta0 = lib().ora_weno_beta0(float(vol), b.reshape(-1) if len(b) else np.zeros(3), len(b), float(eps),
+                                 C.byref(s1), w1)
+    return beta0, s1.value, w1[:len(b)]
+
+
+def weno_weights(order, beta0, beta1, beta2=0.0, eps=1e-8):
+    """Normalised nonlinear weights (Sec. 4.2) [wbar_0, wbar_1, wbar_2]."""
+    w = np.zeros(3)
+    lib().ora_weno_weights(int(order), float(eps), float(beta0), float(beta1), float(beta2), w)
+    return w
 
 
 def s2o4_linear_ode(z):
