@@ -325,8 +325,13 @@ gks_status gks_timestep(gks_state* state, double* dt);
  * rejected with GKS_E_ARG, as is a current device ordinal of 64 or more
  * (the per-device address cache has 64 slots).  The first call on a
  * device resolves the array's address (cudaGetSymbolAddress) with that
- * device current, so make it before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (unordered streams) race.  Allocates nothing, frees nothing. */
+ * device current, so make it before any stream capture.  The address is
+ * cached per device for the life of the process and belongs to the device's
+ * primary context: after cudaDeviceReset (or any other teardown of that
+ * context) the cached address is stale, so do not call this function on a
+ * device that was reset after its first call.  All calls share the array:
+ * calls that overlap on the GPU (unordered streams) race.  Allocates
+ * nothing, frees nothing. */
 gks_status gks_timestep_noalloc(const gks_params* p, const double* d_W, const double* d_dr,
                                 int64_t n_cell, double* d_dt, void* stream);
 

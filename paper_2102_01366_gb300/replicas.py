@@ -6,6 +6,8 @@ data-path collective.  What remains on the host is
 
 * ``assign_cases``: longest-processing-time-first partition of cases (by cell
   count) over ranks, deterministic;
+* ``rank_batch``: this rank's share of a batch of independent cases (its
+  cases' meshes and the matching columns of the state);
 * ``max_over_ranks``: the barrier and max-reduction of a per-rank time, on
   whatever torch.distributed backend the process group uses (NCCL on GPUs,
   gloo in the CPU tests);
@@ -38,6 +40,18 @@ def assign_cases(cells, world_size):
         out[r].append(i)
         heapq.heappush(heap, (load + int(cells[i]), r))
     return [sorted(x) for x in out]
+
+
+def rank_batch(meshes, W, dW, world_size, rank):
+    """This rank's cases of a batch: (case ids, their meshes, W[:, cells],
+    dW[:, cells]).  W and dW hold the cases' cells one case after another,
+    in case order (as the batch generator returns them)."""
+    import numpy as np
+    cells = [int(m["tet"].shape[0]) for m in meshes]
+    first = np.concatenate([[0], np.cumsum(cells)]).astype(np.int64)
+    mine = assign_cases(cells, world_size)[rank]
+    cols = np.concatenate([np.arange(first[k], first[k + 1]) for k in mine]) if mine else np.zeros(0, np.int64)
+    return mine, [meshes[k] for k in mine], np.ascontiguousarray(W[:, cols]), np.ascontiguousarray(dW[:, cols])
 
 
 def max_over_ranks(value, device=None):
