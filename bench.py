@@ -46,8 +46,24 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # a launch), and its DRAM bytes per stage-1 launch from the same capture (the
 # flux kernel's summary under profiles/)
 FLUX_FLOPS_PER_GP = {"fp32": (4216.6, 4114.3)}
-FLUX_DRAM_BYTES_PER_LAUNCH = 10.42e6
+FLUX_DRAM_BYTES_PER_LAUNCH = None
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# algorithmic HBM traffic of one cell-stage: the minimum of the four passes
+# the method's two global dependencies impose (neighbour slopes; both sides'
+# reconstructions), with perfect on-chip reuse of neighbour data -- FP64
+# path 536 words = 4,288 B; FP32 bulk 180 FP64 words (stencil operators,
+# geometric moments, averages) + 356 FP32 words = 2,864 B
+BYTES_PER_CELL_STAGE = {"fp32": 2864.0, "fp64": 4288.0}
+
+
+def step_hbm(value_mcs, precision, peaks):
+    """HBM roofline of the whole step: algorithmic bytes per cell-stage x the
+    measured cell-stage rate, against the measured copy bandwidth."""
+    b = BYTES_PER_CELL_STAGE[precision]
+    achieved = value_mcs * 1e6 * b / 1e9
+    peak = peaks.get("hbm_gbs")
+    return {"bound": "hbm", "bytes_per_cell_stage": b, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if peak else None}
 
 
 def _peaks():
@@ -224,10 +240,13 @@ def batched_leg(torch, gks, args, flush):
     ms_mine = time_device(torch, s, steps, args.warmup, flush)
     ms = replicas.max_over_ranks(ms_mine)
     t, dt = s.case_times()
+    value = total_cells * 2 / (ms / 1000.0) / 1e6
+    peaks, src = _peaks()
     return {"workload": "%d periodic cubes of 8^3..40^3 hexes x 6 tets (seed 5), density waves and "
                         "Riemann slabs at Mach 0.5-3, WENO, FP32 bulk, per-case dt" % args.batch_cases,
+            "step_hbm": dict(step_hbm(value, "fp32", peaks), peak_source=src),
             "cells": int(total_cells), "faces_rank0": g.nf, "cases": len(meshes), "steps": steps,
-            "ms_per_step": ms, "value": total_cells * 2 / (ms / 1000.0) / 1e6, "unit": METRIC,
+            "ms_per_step": ms, "value": value, "unit": METRIC,
             "scaling": "strong (cases split over ranks)" if ws > 1 else "one GPU",
             "rank0_cases": len(mine), "rank0_cells": g.nc,
             "dt_range": [float(dt.min()), float(dt.max())], "host_setup_s": setup_s,
@@ -384,6 +403,9 @@ def sphere_leg(torch, gks, args, flush):
     out["fp32_vs_fp64_after_3_steps"] = {n: float(np.abs(a[q] - b[q]).max() / scale[q])
                                          for q, n in enumerate(("rho", "rho_u", "rho_v", "rho_w", "rho_E"))}
     out["unit"] = METRIC
+    peaks, src = _peaks()
+    out["step_hbm"] = {"fp32": step_hbm(out["fp32"]["value"], "fp32", peaks),
+                       "fp64": step_hbm(out["fp64"]["value"], "fp64", peaks), "peak_source": src}
     return out
 
 
@@ -604,7 +626,10 @@ def main():
         "config": {"workload": WORKLOAD, "cells": nc, "faces": g.nf, "precision": "fp32-bulk",
                    "l2": "flushed between timed steps (512 MB write)", "graph": "one CUDA graph per step",
                    "replicas": ws},
-        "fp64": {"value": value64, "ms_per_step": results["fp64"]["ms"], "dtype": "f64"},
+        "fp64": {"value": value64, "ms_per_step": results["fp64"]["ms"], "dtype": "f64",
+                 "step_hbm": step_hbm(value64, "fp64", peaks)},
+        "step_hbm": dict(step_hbm(value, "fp32", peaks), peak_source=peak_src,
+                         note="latency-bound size: the 24,576-cell workspace fits in L2"),
         "autotuned_variant": {"fp32": results["fp32"]["variant"], "fp64": results["fp64"]["variant"],
                               "meaning": "[face_order, flux_blocks_per_SM, slopes_pass]"},
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32,

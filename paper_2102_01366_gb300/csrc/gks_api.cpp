@@ -262,7 +262,7 @@ namespace {
 struct Layout {
     size_t total = 0;
     // mesh
-    size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, cell_case, perm;
+    size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, fan, cell_case, perm;
     // state
     size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
     size_t add(size_t bytes) {
@@ -290,17 +290,19 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool f
     L.tile = L.add(T * TILE_ROWS * CELLS_PER_BLOCK * nblk);
     L.flr = L.add(4 * 2 * nf);
     L.fgeo = L.add(T * FGEO * nf);
+    L.fan = fp32 ? L.add(8 * 4 * nf) : 0;  // FP32 bulk: FP64 face area vectors A n
     L.cell_case = L.add(4 * nc);
     L.perm = L.add(4 * nf);
     L.Wd = L.add(8 * 5 * nc);
-    L.X = L.add(T * XS * nc);
-    L.Xs = L.add(T * XS * nc);
-    L.X0 = fixed ? L.add(T * XS * nc) : 0;  // state held by fixed boundary faces
+    const size_t xs = fp32 ? Stride<float>::xs : Stride<double>::xs;
+    L.X = L.add(T * xs * nc);
+    L.Xs = L.add(T * xs * nc);
+    L.X0 = fixed ? L.add(T * xs * nc) : 0;  // state held by fixed boundary faces
     L.S = L.add(8 * 5 * nc);
     L.G = L.add(T * 15 * nc);
     L.slopes = L.add(T * 15 * nc);
-    L.poly = L.add(T * POLY_STRIDE * nc);
-    L.rec = L.add(T * 40 * nf);
+    L.poly = L.add(T * (fp32 ? Stride<float>::poly : Stride<double>::poly) * nc);
+    L.rec = L.add(T * (fp32 ? REC1_F32 : 40) * nf);
     L.ctrl = L.add(8 * CTRL_N);
     L.case_t = L.add(8 * ncase);
     L.case_dt = L.add(8 * ncase);
@@ -357,6 +359,7 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.tile = at<T>(s, L.tile);
     m.flr = at<int32_t>(s, L.flr);
     m.fgeo = at<T>(s, L.fgeo);
+    m.fan = L.fan ? at<double>(s, L.fan) : nullptr;
     m.fixed = L.X0 ? at<T>(s, L.X0) : nullptr;
     st.Wd = at<double>(s, L.Wd);
     st.X = at<T>(s, L.X);
@@ -400,6 +403,7 @@ static gks_status upload_faces(gks_state* s) {
     for (int64_t d = 0; d < nf; ++d) inv[perm[d]] = (int32_t)d;
     std::vector<int32_t> cface(4 * nc), flr(2 * nf);
     std::vector<T> fgeo(FGEO * nf, T(0));
+    std::vector<double> fan(s->L.fan ? 4 * nf : 0, 0.0);
     for (int64_t c = 0; c < nc; ++c)
         for (int f = 0; f < 4; ++f) {
             const int64_t fi = g.csr_face[c * 4 + f];
@@ -419,6 +423,8 @@ static gks_status upload_faces(gks_state* s) {
             r[4 + k] = (T)g.gp_l[f * 9 + k];
             r[13 + k] = (T)g.gp_r[f * 9 + k];
         }
+        if (!fan.empty())
+            for (int a = 0; a < 3; ++a) fan[d * 4 + a] = g.farea[f] * g.fnorm[f * 3 + a];
     }
     auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
@@ -426,6 +432,7 @@ static gks_status upload_faces(gks_state* s) {
     GKS_CHECK_CUDA(put(L.cface, cface.data(), 4 * cface.size()));
     GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
     GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
+    if (!fan.empty()) GKS_CHECK_CUDA(put(L.fan, fan.data(), 8 * fan.size()));
     GKS_CHECK_CUDA(put(L.perm, perm.data(), 4 * perm.size()));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
     return GKS_OK;
@@ -579,7 +586,8 @@ static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const 
     GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, d_dW, st.X, nc, s->stream));
     if (m.fixed && !s->fixed_pinned)  // fixed boundaries hold the initial state
-        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * Stride<T>::xs * nc, cudaMemcpyDeviceToDevice,
+                                       s->stream));
     GKS_CHECK_CUDA(launch_set_control(st.ctrl, st.case_t, st.case_dt, st.case_dtmin, m.ncase, 0.0, 0.0, 1, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(st.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
@@ -640,7 +648,7 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
         if ((e = enqueue_recon(s, m, st, X, stage == 1 ? &fin : nullptr)) != cudaSuccess) return e;
         if ((e = Launch<T>::flux(m, p, X, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant)) != cudaSuccess)
             return e;
-        if ((e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q)) != cudaSuccess) return e;
+        if ((e = stage == 1 ? Launch<T>::update1(m, p, st, q) : Launch<T>::update2(m, p, st, q)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -723,7 +731,7 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
             if (e == cudaSuccess) e = mark(GKS_K_RECON);
             if (e == cudaSuccess) e = Launch<T>::flux(m, p, X, st.poly, st.rec, st.case_dt, 0.0, stage, q, s->flux_variant);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_FLUX1 : GKS_K_FLUX2);
-            if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, st, q) : Launch<T>::update2(m, p, st, q);
+            if (e == cudaSuccess) e = stage == 1 ? Launch<T>::update1(m, p, st, q) : Launch<T>::update2(m, p, st, q);
             if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_UPDATE1 : GKS_K_UPDATE2);
         }
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[ne - 1]);
@@ -826,7 +834,8 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
     if (m.fixed && !s->fixed_pinned)
-        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * XS * nc, cudaMemcpyDeviceToDevice, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * Stride<T>::xs * nc, cudaMemcpyDeviceToDevice,
+                                       s->stream));
     GKS_CHECK_CUDA(set_control(s, 0.0, 0.0, 1));
     GKS_CHECK_CUDA(Launch<T>::init_dtmin(m, s->phys, st.X, st.case_dtmin, s->stream));
     s->initialised = true;
@@ -972,7 +981,7 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     GKS_CHECK_CUDA(cudaMemcpyAsync(poly1, st.poly, 8 * POLY_STRIDE * nc, cudaMemcpyDeviceToDevice, s->stream));
     GKS_CHECK_CUDA(Launch<double>::flux(m, s->phys, st.X, st.poly, st.rec, st.case_dt, 0.0, 1, s->stream,
                                         s->flux_variant));
-    GKS_CHECK_CUDA(Launch<double>::update1(m, st, s->stream));
+    GKS_CHECK_CUDA(Launch<double>::update1(m, s->phys, st, s->stream));
     GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.Xs, nullptr, nullptr, st.poly, fb + nc, nullptr, st.err,
                                          s->stream));
     AdjBuffers b;
@@ -1030,7 +1039,7 @@ static gks_status debug_rec_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, d
     if (r != GKS_OK) return r;
     GKS_CHECK_CUDA(Launch<T>::flux(m, s->phys, st.X, st.poly, st.rec, nullptr, dt, stage, s->stream, s->flux_variant));
     GKS_CHECK_CUDA(Launch<T>::rec_to_double(st.rec, at<int32_t>(s, s->L.perm), d_rec, m.nf, stage == 1 ? 40 : 20,
-                                            s->stream));
+                                            &m, st.X, s->phys.gamma - 1.0, dt, s->stream));
     return GKS_OK;
 }
 
@@ -1087,7 +1096,7 @@ static gks_status snapshot(gks_state* s, DevState<T>& st, bool save) {
     char* base = s->ws + s->L.stage;
     struct Item { void* dev; size_t bytes; };
     const Item items[] = {{st.Wd, 8 * 5 * (size_t)nc},
-                          {st.X, sizeof(T) * XS * (size_t)nc},
+                          {st.X, sizeof(T) * Stride<T>::xs * (size_t)nc},
                           {st.case_t, 8 * (size_t)nk},
                           {st.case_dt, 8 * (size_t)nk},
                           {st.case_dtmin, 8 * (size_t)nk},

@@ -236,6 +236,40 @@ __device__ __forceinline__ void state_slopes(const Prim<T>& s, const Tab<T>& ful
         for (int k = 0; k < 5; ++k) r_out[k] = r[k];
 }
 
+// Directional derivative of the Euler flux along x_dir (face frame) of the
+// state W (primitives s): out = (d F_dir / d W) dW, with
+// F_dir = (m_dir, m_j u_dir + p delta_j,dir, (E + p) u_dir) and
+// p = (gamma - 1)(E - |m|^2 / (2 rho)).  For a Maxwellian g(W(x, t)), whose
+// derivatives are g (a . psi) with rho <a psi> = dW (Eq. co), the velocity
+// moments rho <u_dir (a . psi) psi> equal this product.
+template <typename T>
+__device__ __forceinline__ void euler_flux_jvp(const Prim<T>& s, const T* W, T gm1, int dir, const T* dW, T* out) {
+    const T u[3] = {s.u, s.v, s.w};
+    const T ud = u[dir];
+    const T dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) +
+                        T(0.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * dW[0]);
+    const T dud = (dW[1 + dir] - ud * dW[0]) / s.rho;
+    out[0] = dW[1 + dir];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[1 + j] = dW[1 + j] * ud + W[1 + j] * dud + (j == dir ? dp : T(0));
+    out[4] = (dW[4] + dp) * ud + (W[4] + s.p) * dud;
+}
+
+// sum_i (d F_i / d W) g_i: the divergence of the Euler flux for the
+// conservative gradients g[i][q] (face frame)
+template <typename T>
+__device__ __forceinline__ void euler_divergence(const Prim<T>& s, const T* W, T gm1, const T (*g)[5], T* out) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) out[q] = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T d[5];
+        euler_flux_jvp(s, W, gm1, i, g[i], d);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[q] += d[q];
+    }
+}
+
 // Time coefficients of Eq. 2nd-flux over [0, dt/2] (k0, k1 for the kinetic
 // factors e and t e; q1..q3 for C1..C3) and their "dt minus twice dt/2"
 // differences (dk*, dq*), with E = exp(-dt/tau_n) = Eh^2.
@@ -453,5 +487,133 @@ __device__ __forceinline__ void gks_point(const Phys<T>& ph, const T* Wl, const 
     }
 }
 
+
+// --------------------------------------------- half differences --
+// A quantity known on the two sides of a face: its values l, r and,
+// accurate to the rounding of itself, its half-difference h = (l - r) / 2.
+// The rules below are exact identities for finite differences (not
+// linearisations), so h keeps its relative accuracy however small it is,
+// where (l - r) / 2 formed from the rounded values would carry the rounding
+// of l and r.  FP32 bulk uses them to form the interface state W^c
+// (Eq. new-equ-part) relative to the mean of the two sides.
+template <typename T>
+struct HDiff {
+    T l, r, h;
+    __device__ __forceinline__ T mid() const { return T(0.5) * (l + r); }
+};
+
+template <typename T>
+__device__ __forceinline__ HDiff<T> hd_add(const HDiff<T>& a, const HDiff<T>& b) {
+    return {a.l + b.l, a.r + b.r, a.h + b.h};
+}
+
+template <typename T>
+__device__ __forceinline__ HDiff<T> hd_scale(T c, const HDiff<T>& a) {
+    return {c * a.l, c * a.r, c * a.h};
+}
+
+// (l_a l_b - r_a r_b) / 2 = h_a mid_b + mid_a h_b
+template <typename T>
+__device__ __forceinline__ HDiff<T> hd_mul(const HDiff<T>& a, const HDiff<T>& b) {
+    return {a.l * b.l, a.r * b.r, a.h * b.mid() + a.mid() * b.h};
+}
+
+// (l_a / l_b - r_a / r_b) / 2 = (h_a mid_b - mid_a h_b) / (l_b r_b)
+template <typename T>
+__device__ __forceinline__ HDiff<T> hd_div(const HDiff<T>& a, const HDiff<T>& b) {
+    return {a.l / b.l, a.r / b.r, (a.h * b.mid() - a.mid() * b.h) / (b.l * b.r)};
+}
+
+// (sqrt l - sqrt r) / 2 = h / (sqrt l + sqrt r)
+template <typename T>
+__device__ __forceinline__ HDiff<T> hd_sqrt(const HDiff<T>& a) {
+    const T sl = d_sqrt(a.l), sr = d_sqrt(a.r);
+    return {sl, sr, a.h / (sl + sr)};
+}
+
+// (e^{-l} - e^{-r}) / 2 = e^{-r} expm1(-2 h) / 2
+__device__ __forceinline__ HDiff<float> hd_expneg(const HDiff<float>& a) {
+    const float el = expf(-a.l), er = expf(-a.r);
+    return {el, er, 0.5f * er * expm1f(-2.0f * a.h)};
+}
+
+// (erf l - erf r) / 2 = (1 / sqrt pi) int_r^l e^{-t^2} dt.  For |l - r| <= 1
+// the integral is taken by 5-point Gauss-Legendre quadrature on [r, l]
+// (error below 2e-8 of the integral for an interval of length 1, far less
+// for shorter ones); for longer intervals the difference of the two
+// complementary error functions of the tails, which does not cancel there.
+__device__ __forceinline__ HDiff<float> hd_erf(const HDiff<float>& a) {
+    const float el = erff(a.l), er = erff(a.r);
+    float h;
+    if (fabsf(a.h) <= 0.5f) {
+        // nodes and weights of the 5-point Gauss-Legendre rule on [-1, 1]
+        const float x1 = 0.53846931010568309f, x2 = 0.90617984593866399f;
+        const float w0 = 0.56888888888888889f, w1 = 0.47862867049936647f, w2 = 0.23692688505618909f;
+        const float m = a.mid(), d = a.h;
+        auto g = [](float t) { return expf(-t * t); };
+        const float sum = w0 * g(m) + w1 * (g(m + x1 * d) + g(m - x1 * d)) + w2 * (g(m + x2 * d) + g(m - x2 * d));
+        h = 0.56418958354775628695f * d * sum;  // 1 / sqrt(pi)
+    } else if (a.mid() > 0.0f) {
+        h = 0.5f * (erfcf(a.r) - erfcf(a.l));
+    } else {
+        h = 0.5f * (erfcf(-a.l) - erfcf(-a.r));
+    }
+    return {el, er, h};
+}
+
+// Half-difference of psi(W) = rho <psi>_{u1>0} - rho <psi>_{u1<0} between
+// the two states Wl, Wr (face frame, x1 along the normal), given the
+// half-difference h of the states themselves.  With s = sqrt(lambda) U1 =
+// W1 / sqrt(2 p rho), e0 = erf(s) and g = e^{-s^2} / sqrt(pi lambda) =
+// e^{-s^2} sqrt(2 p / (pi rho)), the half-space moments of Sec. 2.2 give
+//   psi(W) = (rho e0, W1 e0 + rho g, W2 e0, W3 e0, W4 e0 + W1 g / 2),
+// and W^c = rho_l <psi>_{u1>0} + rho_r <psi>_{u1<0} = (Wl + Wr) / 2 +
+// (psi(Wl) - psi(Wr)) / 2, so W^c minus the mean of the two states is h_psi.
+__device__ __forceinline__ void psi_half_difference(const float* Wl, const float* Wr, const float* h, float gm1,
+                                                    float* out) {
+    const HDiff<float> rho{Wl[0], Wr[0], h[0]}, m1{Wl[1], Wr[1], h[1]}, m2{Wl[2], Wr[2], h[2]};
+    const HDiff<float> m3{Wl[3], Wr[3], h[3]}, E{Wl[4], Wr[4], h[4]};
+    const HDiff<float> mm = hd_add(hd_add(hd_mul(m1, m1), hd_mul(m2, m2)), hd_mul(m3, m3));
+    const HDiff<float> p = hd_scale(gm1, hd_add(E, hd_scale(-0.5f, hd_div(mm, rho))));
+    const HDiff<float> sy = hd_sqrt(hd_scale(2.0f, hd_mul(p, rho)));
+    const HDiff<float> sv = hd_div(m1, sy);
+    const HDiff<float> e0 = hd_erf(sv);
+    const HDiff<float> ex = hd_expneg(hd_mul(sv, sv));
+    const HDiff<float> g = hd_scale(0.79788456080286536f, hd_mul(ex, hd_sqrt(hd_div(p, rho))));  // sqrt(2 / pi)
+    out[0] = hd_mul(rho, e0).h;
+    out[1] = hd_mul(m1, e0).h + hd_mul(rho, g).h;
+    out[2] = hd_mul(m2, e0).h;
+    out[3] = hd_mul(m3, e0).h;
+    out[4] = hd_mul(E, e0).h + 0.5f * hd_mul(m1, g).h;
+}
+
+// Normal Euler flux F_n(W) = (m.n, m u_n + p n, (E + p) u_n), u_n = m.n / rho,
+// of a global-frame state.
+__device__ __forceinline__ void normal_flux(const float* W, const float* n, float gm1, float* out) {
+    const float mn = W[1] * n[0] + W[2] * n[1] + W[3] * n[2];
+    const float un = mn / W[0];
+    const float p = gm1 * (W[4] - 0.5f * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+    out[0] = mn;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[1 + j] = W[1 + j] * un + p * n[j];
+    out[4] = (W[4] + p) * un;
+}
+
+// (F_n(Wl) - F_n(Wr)) / 2 of the normal Euler flux by the half-difference
+// rules, given the half-difference h of the two global-frame states: exact
+// to the rounding of the result itself, however close the two states.
+__device__ __forceinline__ void normal_flux_half_difference(const float* Wl, const float* Wr, const float* h,
+                                                            const float* n, float gm1, float* out) {
+    const HDiff<float> rho{Wl[0], Wr[0], h[0]}, E{Wl[4], Wr[4], h[4]};
+    const HDiff<float> m[3] = {{Wl[1], Wr[1], h[1]}, {Wl[2], Wr[2], h[2]}, {Wl[3], Wr[3], h[3]}};
+    const HDiff<float> mn = hd_add(hd_add(hd_scale(n[0], m[0]), hd_scale(n[1], m[1])), hd_scale(n[2], m[2]));
+    const HDiff<float> un = hd_div(mn, rho);
+    const HDiff<float> mm = hd_add(hd_add(hd_mul(m[0], m[0]), hd_mul(m[1], m[1])), hd_mul(m[2], m[2]));
+    const HDiff<float> p = hd_scale(gm1, hd_add(E, hd_scale(-0.5f, hd_div(mm, rho))));
+    out[0] = mn.h;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[1 + j] = hd_mul(m[j], un).h + n[j] * p.h;
+    out[4] = hd_mul(hd_add(E, p), un).h;
+}
 
 }  // namespace gks

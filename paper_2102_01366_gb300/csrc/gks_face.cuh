@@ -8,14 +8,21 @@
 
 namespace gks {
 
+// R and its gradient at X (relative to the centroid) from a cell's
+// reconstruction record.  FP64 records hold R in centroid-monomial form; FP32
+// records hold R minus the cell average and the average's hi / lo parts, and
+// val = hi + (R - average).  dev, ahi, alo (FP32, each may be NULL) receive
+// R - average at X and the average's parts.
 template <typename T>
-__device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T* val, T (*g)[5]) {
-    // the record is 16-byte aligned (POLY_STRIDE words): load it in vectors
-    T c[POLY_STRIDE];
+__device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T* val, T (*g)[5],
+                                          T* dev = nullptr, T* ahi = nullptr, T* alo = nullptr) {
+    // the record is 16-byte aligned: load it in vectors
+    constexpr int PS = Stride<T>::poly;
+    T c[PS];
     if constexpr (sizeof(T) == 4) {
         const float4* p4 = reinterpret_cast<const float4*>(P);
 #pragma unroll
-        for (int i = 0; i < POLY_STRIDE / 4; ++i) {
+        for (int i = 0; i < PS / 4; ++i) {
             const float4 v = __ldg(p4 + i);
             c[4 * i] = v.x;
             c[4 * i + 1] = v.y;
@@ -25,7 +32,7 @@ __device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T
     } else {
         const double2* p2 = reinterpret_cast<const double2*>(P);
 #pragma unroll
-        for (int i = 0; i < POLY_STRIDE / 2; ++i) {
+        for (int i = 0; i < PS / 2; ++i) {
             const double2 v = __ldg(p2 + i);
             c[2 * i] = v.x;
             c[2 * i + 1] = v.y;
@@ -35,8 +42,16 @@ __device__ __forceinline__ void eval_poly(const T* __restrict__ P, const T* X, T
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const T* cq = c + q * 10;
-        val[q] = cq[0] + cq[1] * x + cq[2] * y + cq[3] * z + cq[4] * x * x + cq[5] * x * y + cq[6] * x * z +
-                 cq[7] * y * y + cq[8] * y * z + cq[9] * z * z;
+        const T v = cq[0] + cq[1] * x + cq[2] * y + cq[3] * z + cq[4] * x * x + cq[5] * x * y + cq[6] * x * z +
+                    cq[7] * y * y + cq[8] * y * z + cq[9] * z * z;
+        if constexpr (sizeof(T) == 4) {
+            val[q] = c[PHI + q] + v;
+            if (dev) dev[q] = v;
+            if (ahi) ahi[q] = c[PHI + q];
+            if (alo) alo[q] = c[PLO + q];
+        } else {
+            val[q] = v;
+        }
         g[0][q] = cq[1] + T(2) * cq[4] * x + cq[5] * y + cq[6] * z;
         g[1][q] = cq[2] + cq[5] * x + T(2) * cq[7] * y + cq[8] * z;
         g[2][q] = cq[3] + cq[6] * x + cq[8] * y + T(2) * cq[9] * z;

@@ -30,11 +30,18 @@ namespace gks {
 //   phase 1  own side: state at the point, face frame, slopes, rho <psi>+-
 //   phase 2  W^c, collision times; own kinetic part; rho <a_i psi>+-
 //   phase 3  right warps form the equilibrium slopes (once per point) and
-//            share a^c; then left warps add the C2 (a^c.u) flux terms,
-//            right warps the C1, C3 flux terms and the dW term
+//            share a^c, while in stage 1 the left warps form W^c relative to
+//            the mean of the two cell averages (for the gradient records);
+//            then left warps add the C2 (a^c.u) flux terms, right warps the
+//            C1, C3 flux terms and the dW term
 //   phase 4  left warps finish the flux entries, right warps the gradient
 //            entries of the record; the 3 points of each face are summed.
 constexpr int FP_GP = 3 * FLUX_FACES;  // Gauss points per block (96)
+
+// FP32 stage-1 records carry 10 more entries: the face's reference flux
+// (dt / 2) A F_n(W_m), formed in FP64, as FP32 hi and lo parts
+template <int NR>
+constexpr int rec_stride() { return NR == 40 ? REC1_F32 : NR; }
 
 template <typename T, int NR>
 struct FluxSmem {
@@ -43,7 +50,11 @@ struct FluxSmem {
     T dwc[2][FP_GP][15]; // rho <a_i psi>+- of each side
     T ac[FP_GP][15];     // equilibrium slopes a^c_i (formed once, by the right warps)
     T out[2][FP_GP][20]; // partial Fh, D, W0, dW of each side
-    T red[FP_GP * NR];   // weighted record entries per Gauss point
+    T red[FP_GP * rec_stride<NR>()];  // weighted record entries per Gauss point
+    // stage 1: each side's cell average (hi, lo) and R - average at the point
+    // (phase 1); from phase 3 the left side's R - average slots hold W^c - W_m
+    // (global frame)
+    T dv[NR == 40 ? 2 : 1][NR == 40 ? FP_GP : 1][15];
 };
 
 // The two warps that hold the two sides of the same 32 Gauss points (warp w
@@ -51,6 +62,88 @@ struct FluxSmem {
 // they meet at a named barrier of their own instead of the whole block's.
 __device__ __forceinline__ void pair_barrier(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + (g >> 5)), "r"(64) : "memory");
+}
+
+// Stage 1, FP32: the interface state W^c of Eq. new-equ-part relative to W_m,
+// the mean of the two cells' averages (the interior cell's average on a
+// boundary face), in the global frame, into the left side's dv slot.  The
+// gradient records sum w W(0) n over a cell's faces, where the O(|W|) parts
+// cancel to |Omega| grad W; an FP32 W^c would leave its rounding, eps |W|,
+// in each face term, i.e. an error ~ eps |W| / dr in the gradient.  Taken
+// relative to W_m (exact differences of the hi / lo averages) and by the
+// half-difference rules, W^c - W_m carries rounding relative to itself only.
+// Interior and open faces; wall and fixed faces subtract directly.
+template <typename T>
+__device__ __forceinline__ void interface_deviation(T (*dv)[FP_GP][15], int g, int L, int Rc, const T (*Rm)[3],
+                                                    const T (*w0)[FP_GP][5], T gm1) {
+    T out[5];
+    const bool pair = (L >= 0 || L == FLR_OPEN) && (Rc >= 0 || Rc == FLR_OPEN);
+    if (pair) {
+        T Wl[5], Wr[5], hg[5], sg[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const T D = T(0.5) * ((dv[0][g][q] - dv[1][g][q]) + (dv[0][g][5 + q] - dv[1][g][5 + q]));
+            const T dl = D + dv[0][g][10 + q], dr = dv[1][g][10 + q] - D;
+            hg[q] = T(0.5) * (dl - dr);
+            sg[q] = T(0.5) * (dl + dr);
+            Wl[q] = dv[0][g][q] + dv[0][g][10 + q];
+            Wr[q] = dv[1][g][q] + dv[1][g][10 + q];
+        }
+        T tl[5] = {Wl[0], 0, 0, 0, Wl[4]}, tr[5] = {Wr[0], 0, 0, 0, Wr[4]}, th[5] = {hg[0], 0, 0, 0, hg[4]};
+        rotate_vec(Rm, Wl + 1, tl + 1);
+        rotate_vec(Rm, Wr + 1, tr + 1);
+        rotate_vec(Rm, hg + 1, th + 1);
+        psi_half_difference(tl, tr, th, gm1, out);
+        to_global(Rm, out);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[q] += sg[q];
+    } else {
+        const int in = L >= 0 ? 0 : 1;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[q] = w0[0][g][q] + w0[1][g][q];
+        to_global(Rm, out);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[q] = (out[q] - dv[in][g][q]) - dv[in][g][5 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dv[0][g][10 + q] = out[q];
+}
+
+// Stage 1, FP32: F_n(W^c) - F_n(W_m) (global frame) for the flux entries of
+// the record, which hold the interface flux relative to the flux of W_m:
+// over a cell's faces the O(|F|) parts cancel to |Omega| div F, and an FP32
+// flux would leave eps |F| in each face term (an error ~ eps |W| per step in
+// the averages, seen by the next stage's reconstruction as ~ eps |W| / h in
+// the slopes).  W^c - W_m (phase 3) enters through the half-difference rules
+// on interior and open faces; wall and fixed faces subtract directly.
+template <typename T>
+__device__ __forceinline__ void face_flux_deviation(const T (*dv)[FP_GP][15], int g, int L, int Rc,
+                                                    const T (*Rm)[3], const T* Wcl, const T* n, T gm1, T* dF) {
+    T Wc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wc[q] = Wcl[q];
+    to_global(Rm, Wc);
+    const bool pair = (L >= 0 || L == FLR_OPEN) && (Rc >= 0 || Rc == FLR_OPEN);
+    if (pair) {
+        T Wm[5], h[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Wm[q] = T(0.5) * (dv[0][g][q] + dv[1][g][q]);
+            h[q] = T(0.5) * dv[0][g][10 + q];
+        }
+        normal_flux_half_difference(Wc, Wm, h, n, gm1, dF);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) dF[q] *= T(2);
+    } else {
+        const int in = L >= 0 ? 0 : 1;
+        T Wm[5], Fc[5], Fm[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Wm[q] = dv[in][g][q] + dv[in][g][5 + q];
+        normal_flux(Wc, n, gm1, Fc);
+        normal_flux(Wm, n, gm1, Fm);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) dF[q] = Fc[q] - Fm[q];
+    }
 }
 
 template <typename T, int NR, int MINB, bool PRF>
@@ -78,31 +171,49 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     const T w = geo[3];
 
     // ---- phase 1 ----
+    constexpr int XSR = Stride<T>::xs;
     const int mine = side == 0 ? L : Rc;
     const bool wall =
         mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL || mine == FLR_ISOTHERMAL_WALL || mine == FLR_MOVING_WALL;
     T Ws[5], gs[3][5];
+    // stage 1: the average this side refers to and R - average at the point
+    T ahi[5], alo[5], dev[5];
     if (mine >= 0 || wall) {
         // a wall side starts from the interior cell's value at the point
         const int src = mine >= 0 ? side : 1 - side;
         const int64_t cell = mine >= 0 ? mine : (side == 0 ? Rc : L);
         const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
-        eval_poly(poly + cell * POLY_STRIDE, X, Ws, gs);
-    } else if (mine == FLR_FIXED) {
-        const int64_t in = side == 0 ? Rc : L;
-        const int src = 1 - side;
-        const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
-        fixed_ghost(m.fixed + in * XS, X, Ws, gs);
+        eval_poly(poly + cell * Stride<T>::poly, X, Ws, gs, dev, ahi, alo);
     } else {
-        // open boundary: the missing side is the interior cell's average with
-        // zero gradient (zeroth-order extrapolation; the paper leaves outflow
-        // boundaries open, and copying the interior Gauss-point state is not
-        // stable)
         const int64_t in = side == 0 ? Rc : L;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            Ws[q] = Wavg[in * XS + q];
-            gs[0][q] = gs[1][q] = gs[2][q] = T(0);
+            ahi[q] = Wavg[in * XSR + q];
+            alo[q] = Wavg[in * XSR + XLO + q];
+            dev[q] = T(0);
+        }
+        if (mine == FLR_FIXED) {
+            const int src = 1 - side;
+            const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
+            fixed_ghost(m.fixed + in * XSR, X, Ws, gs);
+        } else {
+            // open boundary: the missing side is the interior cell's average
+            // with zero gradient (zeroth-order extrapolation; the paper leaves
+            // outflow boundaries open, and copying the interior Gauss-point
+            // state is not stable)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                Ws[q] = ahi[q];
+                gs[0][q] = gs[1][q] = gs[2][q] = T(0);
+            }
+        }
+    }
+    if constexpr (NR == 40) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            sm.dv[side][g][q] = ahi[q];
+            sm.dv[side][g][5 + q] = alo[q];
+            sm.dv[side][g][10 + q] = dev[q];
         }
     }
     T Rm[3][3];
@@ -158,7 +269,10 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         axpy5(-(tau * tc.k0 + tc.k1), mf1, Fh);
         axpy5(tc.dk0, mf0, D);
         axpy5(-(tau * tc.dk0 + tc.dk1), mf1, D);
-        axpy5(T(1), mw0, W0);
+        // stage 1: the zeroth moments sum to W^c, which the record takes
+        // relative to the mean of the two averages (phase 3); W0 keeps the
+        // tau terms only
+        if (NR != 40) axpy5(T(1), mw0, W0);
         axpy5(-tau, mw1, W0);
         axpy5(tau - (tau + dt) * tc.E, mw1, dWt);
         T mw2[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -190,7 +304,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     // ---- phase 3 ----
     {
         make_tab(t, C, ph.K, 0);
-        T ac[3][5], Ac[5], rA[5];
+        T ac[3][5], divF[5];
         if (side == 1) {
             // the equilibrium slopes, once per point (Eq. co for g^c)
             T dWc[3][5];
@@ -198,11 +312,27 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int q = 0; q < 5; ++q) dWc[i][q] = sm.dwc[0][g][5 * i + q] + sm.dwc[1][g][5 * i + q];
-            state_slopes(C, t, ph.K, dWc, ac, Ac, rA);
+            const T ir = T(1) / C.rho;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T b[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) b[q] = dWc[i][q] * ir;
+                micro_slope(C, ph.K, b, ac[i]);
+            }
+            // rho sum_i <(a_i . psi) u_i psi> = sum_i d F_i / d x_i: the
+            // equilibrium's moments differentiated along x_i are its Euler
+            // fluxes' derivatives (Eq. co), taken here through the flux
+            // Jacobians, which FP32 evaluates without the cancellation of the
+            // fourth- and fifth-order velocity moments
+            euler_divergence(C, Wc, ph.gm1, dWc, divF);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
+        } else if constexpr (NR == 40) {
+            // the left warps meanwhile: stage 1's W^c - W_m for the gradient records
+            interface_deviation(sm.dv, g, L, Rc, Rm, sm.w0, ph.gm1);
         }
         pair_barrier(g);
         // Pr fix: the state integrals move to this side's (now unused) slope
@@ -226,18 +356,23 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
                 axpy5(tc.dq2, mf1, D);
             }
         } else {
-            T mf0[5] = {0}, mf2[5] = {0}, mw1[5];
+            T mf0[5] = {0}, mf2[5], mw1[5], dtW[5];
             acc_psi<1, 0, 0>(t, C.rho, mf0);
-            acc_apsi<1, 0, 0>(t, Ac, C.rho, mf2);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) mw1[q] = -C.rho * rA[q];  // rho sum_i <(a_i . psi) u_i psi> (Eq. co)
+            for (int q = 0; q < 5; ++q) {
+                mw1[q] = divF[q];   // rho sum_i <(a_i . psi) u_i psi> (Eq. co)
+                dtW[q] = -divF[q];  // rho <A psi>: the compatibility condition
+            }
+            // rho <u1 (A . psi) psi> = d F_1 / d t = J_1(W^c) rho <A psi>
+            euler_flux_jvp(C, Wc, ph.gm1, 0, dtW, mf2);
             if (ph.smooth) {
                 const T hd = T(0.5) * dt;
-                axpy5(hd, mf0, Fh);
+                // stage 1: hd F(W^c) joins the record in phase 4, relative to W_m
+                if (NR != 40) axpy5(hd, mf0, Fh);
                 axpy5(T(0.5) * hd * hd - tau * hd, mf2, Fh);
                 axpy5(T(0.25) * dt * dt, mf2, D);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) W0[q] = Wc[q];  // tau terms cancel: <(a.u + A) psi> = 0
+                for (int q = 0; q < 5; ++q) W0[q] = NR == 40 ? T(0) : Wc[q];  // tau terms cancel: <(a.u + A) psi> = 0
                 axpy5(-dt, mw1, dWt);
                 if (PRF) {
 #pragma unroll
@@ -247,7 +382,9 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
                     }
                 }
             } else {
-                axpy5(tc.q1, mf0, Fh);
+                // q1 = dt / 2 - k0; stage 1 keeps -k0 here and takes (dt / 2) F(W^c)
+                // relative to W_m in phase 4
+                axpy5(NR == 40 ? -tc.k0 : tc.q1, mf0, Fh);
                 axpy5(tc.q3, mf2, Fh);
                 axpy5(tc.dq1, mf0, D);
                 axpy5(tc.dq3, mf2, D);
@@ -277,7 +414,8 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     pair_barrier(g);
 
     // ---- phase 4: left warps the flux entries, right warps the gradient entries
-    T* mine_rec = sm.red + g * NR;
+    constexpr int RS = rec_stride<NR>();
+    T* mine_rec = sm.red + g * RS;
     if (side == 0) {
         T Fs[5], Ds[5];
 #pragma unroll
@@ -285,20 +423,74 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             Fs[q] = sm.out[0][g][q] + sm.out[1][g][q];
             Ds[q] = sm.out[0][g][5 + q] + sm.out[1][g][5 + q];
         }
+        T Wcl[5];  // W^c, face frame
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Wcl[q] = sm.w0[0][g][q] + sm.w0[1][g][q];
         if (PRF) {
-            T IWh[5], IWd[5], Wc[5];
+            T IWh[5], IWd[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 IWh[q] = sm.dwc[0][g][q] + sm.dwc[1][g][q];
                 IWd[q] = sm.dwc[0][g][5 + q] + sm.dwc[1][g][5 + q];
-                Wc[q] = sm.w0[0][g][q] + sm.w0[1][g][q];
             }
-            const T U[3] = {Wc[1] / Wc[0], Wc[2] / Wc[0], Wc[3] / Wc[0]};
-            prandtl_fix(ph.prf, U, IWh, Fs);
+            const T U[3] = {Wcl[1] / Wcl[0], Wcl[2] / Wcl[0], Wcl[3] / Wcl[0]};
+            if constexpr (NR == 40) {
+                // the Pr fix acts on the whole flux: put back (dt / 2) F_1(W^c)
+                // for it and keep only its change of the energy entry
+                const Prim<T> Cc = to_prim(Wcl, ph.gm1);
+                const T F1c[5] = {Wcl[1], Wcl[1] * Cc.u + Cc.p, Wcl[1] * Cc.v, Wcl[1] * Cc.w, (Wcl[4] + Cc.p) * Cc.u};
+                T Ff[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) Ff[q] = Fs[q] + T(0.5) * dt * F1c[q];
+                const T before = Ff[4];
+                prandtl_fix(ph.prf, U, IWh, Ff);
+                Fs[4] += Ff[4] - before;
+            } else {
+                prandtl_fix(ph.prf, U, IWh, Fs);
+            }
             prandtl_fix(ph.prf, U, IWd, Ds);
         }
         to_global(Rm, Fs);
         to_global(Rm, Ds);
+        if constexpr (NR == 40) {
+            // (dt / 2) (F_n(W^c) - F_n(W_m)): the flux of the interface state
+            // relative to that of the mean of the two cell averages, whose
+            // own flux, (dt / 2) A F_n(W_m), the record carries in FP64 terms
+            T dF[5];
+            face_flux_deviation(sm.dv, g, L, Rc, Rm, Wcl, n, ph.gm1, dF);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) Fs[q] += T(0.5) * dt * dF[q];
+            // once per face (its first Gauss point): the reference flux in
+            // FP64, W_m from the hi / lo averages and the FP64 area vector
+            // A n (whose sum over a closed cell vanishes to FP64 rounding,
+            // where the FP32 weights and normals leave eps A), split into
+            // FP32 hi and lo parts; entering both cells with opposite signs,
+            // it keeps the update exactly conservative
+            double ref[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (k == 0) {
+                double Wm[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    Wm[q] = 0.5 * (((double)sm.dv[0][g][q] + (double)sm.dv[0][g][5 + q]) +
+                                   ((double)sm.dv[1][g][q] + (double)sm.dv[1][g][5 + q]));
+                const double* an = m.fan + 4 * f;
+                const double mn = Wm[1] * an[0] + Wm[2] * an[1] + Wm[3] * an[2];  // A m.n
+                const double ir = 1.0 / Wm[0];
+                const double un = mn * ir;
+                const double pm = (double)ph.gm1 * (Wm[4] - 0.5 * (Wm[1] * Wm[1] + Wm[2] * Wm[2] + Wm[3] * Wm[3]) * ir);
+                const double c = 0.5 * (double)dt;
+                ref[0] = c * mn;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ref[1 + j] = c * (Wm[1 + j] * un + pm * an[j]);
+                ref[4] = c * ((Wm[4] + pm) * un);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const T hi = (T)ref[q];
+                mine_rec[REC1_REF + q] = hi;
+                mine_rec[REC1_REF + 5 + q] = (T)(ref[q] - (double)hi);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             if (NR == 40) {
@@ -318,6 +510,11 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
         }
         to_global(Rm, Zs);
         to_global(Rm, Ys);
+        if constexpr (NR == 40) {
+            // W(0) - W_m: the tau terms plus W^c - W_m from phase 3
+#pragma unroll
+            for (int q = 0; q < 5; ++q) Zs[q] += sm.dv[0][g][10 + q];
+        }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             if (NR == 40) {
@@ -338,11 +535,11 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     __syncthreads();
     // sum the three Gauss points of each face; coalesced record store
     const int64_t base = (int64_t)blockIdx.x * FLUX_FACES;
-    for (int idx = threadIdx.x; idx < FLUX_FACES * NR; idx += 2 * FP_GP) {
-        const int fl = idx / NR, j = idx - fl * NR;
+    for (int idx = threadIdx.x; idx < FLUX_FACES * RS; idx += 2 * FP_GP) {
+        const int fl = idx / RS, j = idx - fl * RS;
         if (base + fl < m.nf) {
-            const T* r = sm.red + fl * 3 * NR + j;
-            rec[(base + fl) * NR + j] = (r[0] + r[NR]) + r[2 * NR];
+            const T* r = sm.red + fl * 3 * RS + j;
+            rec[(base + fl) * RS + j] = (r[0] + r[RS]) + r[2 * RS];
         }
     }
 }
@@ -379,17 +576,17 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
                 const int src = cell >= 0 ? side : 1 - side;
                 const int64_t c = cell >= 0 ? cell : (side == 0 ? Rc : L);
                 const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
-                eval_poly(poly + c * POLY_STRIDE, X, Wv, g);
+                eval_poly(poly + c * Stride<T>::poly, X, Wv, g);
             } else if (cell == FLR_FIXED) {
                 const int64_t in = side == 0 ? Rc : L;
                 const int src = 1 - side;
                 const T X[3] = {geo[4 + 9 * src + 3 * k], geo[5 + 9 * src + 3 * k], geo[6 + 9 * src + 3 * k]};
-                fixed_ghost(m.fixed + in * XS, X, Wv, g);
+                fixed_ghost(m.fixed + in * Stride<T>::xs, X, Wv, g);
             } else {
                 // open boundary: interior cell average, zero gradient
                 const int64_t in = side == 0 ? Rc : L;
                 for (int q = 0; q < 5; ++q) {
-                    Wv[q] = Wavg[in * XS + q];
+                    Wv[q] = Wavg[in * Stride<T>::xs + q];
                     g[0][q] = g[1][q] = g[2][q] = T(0);
                 }
             }

@@ -61,7 +61,7 @@ __device__ void block_case_min(double v, int32_t cas, bool valid, int lc, unsign
 // cell updates (5 lanes per cell)
 // --------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState<T> st) {
+__global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, HostPhys p, DevState<T> st) {
     const CellLane cl = cell_lane(m.nc);
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
@@ -72,12 +72,21 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState
     s1.init();
     T gs[3] = {T(0), T(0), T(0)}, g0[3] = {T(0), T(0), T(0)};
 #pragma unroll
+    constexpr int RS = sizeof(T) == 4 ? REC1_F32 : 40;
     for (int f = 0; f < 4; ++f) {
         const int e = m.cface[f * nc + c];
         const T s = (e & 1) ? T(-1) : T(1);
-        const T* r = st.rec + (int64_t)(e >> 1) * 40;
+        const T* r = st.rec + (int64_t)(e >> 1) * RS;
         fh.add(s * r[q]);
         s1.add(s * r[5 + q]);
+        if constexpr (sizeof(T) == 4) {
+            // the reference flux (dt / 2) A F_n(W_m) of the face, hi + lo; the
+            // S entry takes it twice (2 Fh - D / 3)
+            fh.add(s * r[REC1_REF + q]);
+            fh.add(s * r[REC1_REF + 5 + q]);
+            s1.add(T(2) * s * r[REC1_REF + q]);
+            s1.add(T(2) * s * r[REC1_REF + 5 + q]);
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             gs[i] += s * r[10 + 3 * q + i];
@@ -85,9 +94,38 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update1(DevMesh<T> m, DevState
         }
     }
     const double iv = m.inv_vol[c];
-    T* xs = st.Xs + c * XS;
+    constexpr int XSR = Stride<T>::xs;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 records hold the interface states relative to the mean of the
+        // face's two cell averages W_m (the interior cell's average on a
+        // boundary face).  The cell needs sum_f s_f W_m A_f n_f back; as
+        // sum_f s_f A_f n_f = 0 over a closed cell, that is
+        // 1/2 sum_f s_f (W_nb - W_c) A_f n_f over its interior faces, formed
+        // from the exact differences of the hi / lo pairs (A = 3 w).
+        const T hc = st.X[c * XSR + q], lc = st.X[c * XSR + XLO + q];
+        T ab[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int nb = m.nbr[f * nc + c];
+            if (nb < 0) continue;
+            const int e = m.cface[f * nc + c];
+            const T* geo = m.fgeo + (int64_t)(e >> 1) * FGEO;
+            const T dw = (st.X[(int64_t)nb * XSR + q] - hc) + (st.X[(int64_t)nb * XSR + XLO + q] - lc);
+            const T a = ((e & 1) ? T(-1.5) : T(1.5)) * geo[3] * dw;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ab[i] += a * geo[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gs[i] += ab[i];
+            g0[i] += ab[i];
+        }
+    }
+    T* xs = st.Xs + c * XSR;
     // W* = W^n - (1/|Omega|) sum s sum_k w Fh  (Eq. s2o4, first stage)
-    xs[q] = (T)(st.Wd[q * nc + c] - fh.value() * iv);
+    const double wstar = st.Wd[q * nc + c] - fh.value() * iv;
+    xs[q] = (T)wstar;
+    if constexpr (sizeof(T) == 4) xs[XLO + q] = (T)(wstar - (double)(T)wstar);
     st.S[q * nc + c] = s1.value();
     const T ivr = (T)iv;
 #pragma unroll
@@ -159,8 +197,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_update2(DevMesh<T> m, HostPhys
     const T Wq = (T)wn;
     if (live) {
         st.Wd[q * nc + c] = wn;
-        T* x = st.X + c * XS;
+        T* x = st.X + c * Stride<T>::xs;
         x[q] = Wq;
+        if constexpr (sizeof(T) == 4) x[XLO + q] = (T)(wn - (double)Wq);
         const T ivr = (T)iv;
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[5 + 3 * q + i] = (st.G[(3 * q + i) * nc + c] + dg[i]) * ivr;
@@ -196,7 +235,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dt_partials(DevMesh<T> m, Host
     if (cl.active && cl.q == 0) {
         T Wv[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * XS + q];
+        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * Stride<T>::xs + q];
         mn = local_dt(Wv, m.dr[cl.c], p);
     }
     block_reduce_part<T>(mn, zero, part + (int64_t)blockIdx.x * PART_N);
@@ -211,7 +250,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_init_dtmin(DevMesh<T> m, HostP
     if (lead) {
         T Wv[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * XS + q];
+        for (int q = 0; q < 5; ++q) Wv[q] = X[cl.c * Stride<T>::xs + q];
         mn = (double)local_dt(Wv, m.dr[cl.c], p);
     }
     const int lc = (int)(cl.c - (int64_t)blockIdx.x * CELLS_PER_BLOCK);
@@ -240,10 +279,20 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
 
 template <typename T>
 __global__ void k_pack(const double* __restrict__ W, const double* __restrict__ dW, T* __restrict__ X, int64_t nc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * XS; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i / XS;
-        const int j = (int)(i - c * XS);
-        X[i] = (T)(j < 5 ? W[j * nc + c] : dW[(j - 5) * nc + c]);
+    constexpr int XSR = Stride<T>::xs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * XSR; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / XSR;
+        const int j = (int)(i - c * XSR);
+        T v = T(0);
+        if (j < 5) {
+            v = (T)W[j * nc + c];
+        } else if (j < 20) {
+            v = (T)dW[(j - 5) * nc + c];
+        } else if (sizeof(T) == 4 && j < XLO + 5) {
+            const double w = W[(j - XLO) * nc + c];
+            v = (T)(w - (double)(T)w);  // lo part of the FP32 pair
+        }
+        X[i] = v;
     }
 }
 
@@ -251,23 +300,55 @@ template <typename T>
 __global__ void k_unpack_grad(const T* __restrict__ X, double* __restrict__ dW, int64_t nc) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 15; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = i / nc, c = i - j * nc;
-        dW[i] = (double)X[c * XS + 5 + j];
+        dW[i] = (double)X[c * Stride<T>::xs + 5 + j];
     }
 }
 
 template <typename T>
 __global__ void k_rec_out(const T* __restrict__ rec, const int32_t* __restrict__ perm, double* __restrict__ out,
-                          int64_t nf, int nr) {
+                          int64_t nf, int nr, DevMesh<T> m, const T* __restrict__ X, int addback, double gm1,
+                          double dt) {
+    constexpr int XSR = Stride<T>::xs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf * nr; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = i / nr;
-        out[(int64_t)perm[d] * nr + (i - d * nr)] = (double)rec[i];
+        const int j = (int)(i - d * nr);
+        // FP32 stage-1 records: device stride 50 (reference flux at 40..49)
+        const int rs = (sizeof(T) == 4 && nr == 40) ? REC1_F32 : nr;
+        const T* r = rec + d * rs;
+        double v = (double)r[j];
+        if (sizeof(T) == 4 && nr == 40 && j < 10) {
+            // the reference flux (dt / 2) A F_n(W_m), twice in the S entries
+            const double ref = (double)r[REC1_REF + j % 5] + (double)r[REC1_REF + 5 + j % 5];
+            v += j < 5 ? ref : 2.0 * ref;
+        }
+        if (sizeof(T) == 4 && addback && j >= 10) {
+            // the mean of the two averages (the interior one on a boundary
+            // face) times sum_k w_k n = 3 w n
+            const int k = (j - 10) % 15, q = k / 3, dir = k - 3 * q;
+            const int L = m.flr[d], R = m.flr[m.nf + d];
+            auto avg = [&](int c) { return (double)X[(int64_t)c * XSR + q] + (double)X[(int64_t)c * XSR + XLO + q]; };
+            const double wm = (L >= 0 && R >= 0) ? 0.5 * (avg(L) + avg(R)) : avg(L >= 0 ? L : R);
+            const T* geo = m.fgeo + d * FGEO;
+            v += wm * 3.0 * (double)geo[3] * (double)geo[dir];
+        }
+        out[(int64_t)perm[d] * nr + j] = v;
     }
 }
 
 template <typename T>
 __global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, int64_t nc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 50; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (double)in[(i / 50) * POLY_STRIDE + i % 50];
+    constexpr int PS = Stride<T>::poly;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 50; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / 50;
+        const int k = (int)(i - c * 50);
+        double v = (double)in[c * PS + k];
+        if (sizeof(T) == 4 && k % 10 == 0) {
+            // FP32 records hold R(centroid) minus the average: add the average back
+            const int q = k / 10;
+            v += (double)in[c * PS + PHI + q] + (double)in[c * PS + PLO + q];
+        }
+        out[i] = v;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -276,9 +357,9 @@ __global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, i
 int update_blocks(int64_t nc) { return (int)cell_grid(nc); }
 
 template <typename T>
-cudaError_t Launch<T>::update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s) {
+cudaError_t Launch<T>::update1(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st, cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_update1<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, st);
+    k_update1<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, p, st);
     return cudaGetLastError();
 }
 
@@ -311,7 +392,7 @@ static inline unsigned ew_grid(int64_t n) { return (unsigned)((n + 255) / 256 < 
 template <typename T>
 cudaError_t Launch<T>::pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
-    k_pack<T><<<ew_grid(nc * XS), 256, 0, s>>>(W, dW, X, nc);
+    k_pack<T><<<ew_grid(nc * Stride<T>::xs), 256, 0, s>>>(W, dW, X, nc);
     return cudaGetLastError();
 }
 
@@ -338,10 +419,14 @@ cudaError_t Launch<T>::from_double(const double* in, T* out, int64_t n, cudaStre
 
 template <typename T>
 cudaError_t Launch<T>::rec_to_double(const T* rec, const int32_t* perm, double* out, int64_t nf, int nr,
-                                     cudaStream_t s) {
+                                     const DevMesh<T>* m, const T* X, double gm1, double dt, cudaStream_t s) {
     if (nf == 0) return cudaSuccess;
     const int64_t n = nf * nr;
-    k_rec_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(rec, perm, out, nf, nr);
+    const int addback = (m && X && nr == 40) ? 1 : 0;
+    DevMesh<T> mv{};
+    if (m) mv = *m;
+    k_rec_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(rec, perm, out, nf, nr,
+                                                                                            mv, X, addback, gm1, dt);
     return cudaGetLastError();
 }
 
@@ -363,7 +448,8 @@ cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt, un
 
 
 #define GKS_CELLS_INST(T)                                                                                   \
-    template cudaError_t Launch<T>::update1(const DevMesh<T>&, const DevState<T>&, cudaStream_t);           \
+    template cudaError_t Launch<T>::update1(const DevMesh<T>&, const HostPhys&, const DevState<T>&,         \
+                                            cudaStream_t);                                                  \
     template cudaError_t Launch<T>::update2(const DevMesh<T>&, const HostPhys&, const DevState<T>&,         \
                                             cudaStream_t);                                                  \
     template cudaError_t Launch<T>::dt_partials(const DevMesh<T>&, const HostPhys&, const T*, double*,      \
@@ -375,7 +461,7 @@ cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt, un
     template cudaError_t Launch<T>::to_double(const T*, double*, int64_t, cudaStream_t);                    \
     template cudaError_t Launch<T>::from_double(const double*, T*, int64_t, cudaStream_t);                  \
     template cudaError_t Launch<T>::rec_to_double(const T*, const int32_t*, double*, int64_t, int,          \
-                                                  cudaStream_t);                                            \
+                                                  const DevMesh<T>*, const T*, double, double, cudaStream_t); \
     template cudaError_t Launch<T>::poly_to_double(const T*, double*, int64_t, cudaStream_t);
 GKS_CELLS_INST(double)
 GKS_CELLS_INST(float)

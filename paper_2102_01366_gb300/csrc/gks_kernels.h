@@ -18,8 +18,29 @@ constexpr int FLUX_FACES = 32;       // faces per flux block (3 threads each)
 constexpr int CELL_THREADS = 128;    // threads per cell-kernel block
 constexpr int CELLS_PER_BLOCK = 24;  // 4 warps x 6 cells, 5 lanes per cell
 constexpr int FGEO = 24;             // reals per face geometry record
-constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record (50 used)
-constexpr int XS = 20;               // reals per cell working-state record: W (5), grad W (15, 3q+i)
+constexpr int POLY_STRIDE = 52;      // reals per cell reconstruction record, FP64 (50 used)
+constexpr int XS = 20;               // reals per cell working-state record, FP64: W (5), grad W (15, 3q+i)
+// FP32 bulk keeps each cell average as an unevaluated pair hi + lo of FP32
+// numbers (the FP64 average to ~48 bits), so that differences between
+// neighbouring averages stay exact to FP32 rounding of the difference:
+//   working state [nc][28]: W hi (5), grad W (15), W lo (5), pad (3)
+//   reconstruction record [nc][60]: per component the constant R(centroid)
+//   minus the average and the 9 slopes/curvatures (50), the average's hi (5)
+//   and lo (5) parts
+constexpr int XS32 = 28;
+// FP32 stage-1 face records: the 40 entries of the definition (the flux and
+// interface-state entries relative to the mean W_m of the face's two cell
+// averages), then the reference flux (dt / 2) A F_n(W_m) as FP32 hi (5) and
+// lo (5) parts
+constexpr int REC1_F32 = 50, REC1_REF = 40;
+constexpr int XLO = 20;              // offset of the lo parts in an FP32 working-state record
+constexpr int POLY_STRIDE32 = 60;
+constexpr int PHI = 50, PLO = 55;    // offsets of the average's hi / lo parts in an FP32 record
+template <typename T>
+struct Stride {
+    static constexpr int xs = sizeof(T) == 4 ? XS32 : XS;
+    static constexpr int poly = sizeof(T) == 4 ? POLY_STRIDE32 : POLY_STRIDE;
+};
 // Per-block tile of the reconstruction's static cell data, one contiguous
 // [TILE_ROWS][CELLS_PER_BLOCK] record per block of cells, loaded into shared
 // memory by one bulk copy: M2 (144 rows), the cell's 12 face Gauss points
@@ -40,18 +61,19 @@ struct DevMesh {
     const T* tile;         // [blocks][TILE_ROWS][CELLS_PER_BLOCK] reconstruction data
     const int32_t* flr;    // [2][nf]
     const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
-    const T* fixed;        // [nc][XS] state held by fixed boundary faces (NULL: none)
+    const double* fan;     // FP32 bulk: [nf][4] FP64 face area vectors A n (NULL in FP64)
+    const T* fixed;        // [nc][Stride<T>::xs] state held by fixed boundary faces (NULL: none)
 };
 
 template <typename T>
 struct DevState {
     double* Wd;   // [5][nc] master cell averages (FP64)
-    T* X;         // [nc][XS] working state W^n, grad W^n (cell-major for neighbour gathers)
-    T* Xs;        // [nc][XS] stage state W*, grad W*
+    T* X;         // [nc][Stride<T>::xs] working state W^n, grad W^n (cell-major for neighbour gathers)
+    T* Xs;        // [nc][Stride<T>::xs] stage state W*, grad W*
     double* S;    // [5][nc] saved stage-1 flux term
     T* G;         // [15][nc] saved stage-1 gradient term
     T* slopes;    // [nc][15]
-    T* poly;      // [nc][POLY_STRIDE], 50 used
+    T* poly;      // [nc][Stride<T>::poly]
     T* rec;       // [nf][40]
     double* ctrl; // [CTRL_N] global controls (dt_fixed, t_end)
     double* case_t;   // [ncase] time of each case
@@ -97,7 +119,7 @@ struct Launch {
     static cudaError_t flux(const DevMesh<T>& m, const HostPhys& p, const T* X, const T* poly, T* rec,
                             const double* case_dt, double dt_override, int stage, cudaStream_t s,
                             int variant = 1);
-    static cudaError_t update1(const DevMesh<T>& m, const DevState<T>& st, cudaStream_t s);
+    static cudaError_t update1(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st, cudaStream_t s);
     static cudaError_t update2(const DevMesh<T>& m, const HostPhys& p, const DevState<T>& st,
                                cudaStream_t s);
     static cudaError_t dt_partials(const DevMesh<T>& m, const HostPhys& p, const T* X,
@@ -112,10 +134,15 @@ struct Launch {
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
-    // face records in device order -> FP64 in canonical order (perm: device -> canonical)
+    // face records in device order -> FP64 in canonical order (perm: device -> canonical).
+    // FP32 stage-1 records hold the interface states and fluxes relative to
+    // the mean W_m of the two cells' averages (Stride comment above); with m
+    // and X given, W_m sum_k w_k n and the flux terms (dt / 2) A F_n(W_m),
+    // dt A F_n(W_m) are added back so that the output is the record of the
+    // definition.
     static cudaError_t rec_to_double(const T* rec, const int32_t* perm, double* out, int64_t nf, int nr,
-                                     cudaStream_t s);
-    // padded reconstruction records [nc][POLY_STRIDE] -> compact FP64 [nc][50]
+                                     const DevMesh<T>* m, const T* X, double gm1, double dt, cudaStream_t s);
+    // padded reconstruction records -> compact FP64 [nc][50] in centroid-monomial form
     static cudaError_t poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s);
 };
 

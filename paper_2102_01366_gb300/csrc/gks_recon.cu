@@ -105,6 +105,17 @@ struct FinArg {
     double cfl;
     const double* ctrl;
 };
+// Q_a - Q_b of component q of two cell averages: in FP32 bulk from the hi
+// and lo parts (exact to the rounding of the difference itself)
+template <typename T>
+__device__ __forceinline__ T avg_diff(const T* __restrict__ X, int64_t a, int64_t b, int q) {
+    constexpr int XSR = Stride<T>::xs;
+    if constexpr (sizeof(T) == 4)
+        return (X[a * XSR + q] - X[b * XSR + q]) + (X[a * XSR + XLO + q] - X[b * XSR + XLO + q]);
+    else
+        return X[a * XSR + q] - X[b * XSR + q];
+}
+
 // reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3
 template <typename T>
 __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ X,
@@ -114,13 +125,12 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
-    const T Q0 = X[c * XS + q];
     T b0 = T(0), b1 = T(0), b2 = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + c];
         if (nb < 0) continue;
-        const T dq = X[(int64_t)nb * XS + q] - Q0;
+        const T dq = avg_diff(X, nb, c, q);
         b0 += m.M1[(0 * 4 + f) * nc + c] * dq;
         b1 += m.M1[(1 * 4 + f) * nc + c] * dq;
         b2 += m.M1[(2 * 4 + f) * nc + c] * dq;
@@ -136,13 +146,12 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
 template <typename T>
 __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ X, int64_t x, int q, T* b) {
     const int64_t nc = m.nc;
-    const T Qx = X[x * XS + q];
     b[0] = b[1] = b[2] = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + x];
         if (nb < 0) continue;
-        const T dq = X[(int64_t)nb * XS + q] - Qx;
+        const T dq = avg_diff(X, nb, x, q);
         b[0] += m.M1[(0 * 4 + f) * nc + x] * dq;
         b[1] += m.M1[(1 * 4 + f) * nc + x] * dq;
         b[2] += m.M1[(2 * 4 + f) * nc + x] * dq;
@@ -185,15 +194,21 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     int nb[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
-    const T Q0 = X[c * XS + q];
+    constexpr int XSR = Stride<T>::xs;
+    const T Q0 = X[c * XSR + q];
+    T Q0lo = T(0);  // lo part of the FP32 pair (FP64: unused)
+    if constexpr (sizeof(T) == 4) Q0lo = X[c * XSR + XLO + q];
 
     // data vector [dQ_f (4); grad Q_{f,l} (12)] of this component
     T d[16];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool ok = nb[f] >= 0;
-        const T* xn = X + (ok ? (int64_t)nb[f] : c) * XS;
-        d[f] = ok ? xn[q] - Q0 : T(0);
+        const T* xn = X + (ok ? (int64_t)nb[f] : c) * XSR;
+        if constexpr (sizeof(T) == 4)
+            d[f] = ok ? (xn[q] - Q0) + (xn[XLO + q] - Q0lo) : T(0);
+        else
+            d[f] = ok ? xn[q] - Q0 : T(0);
 #pragma unroll
         for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? xn[5 + 3 * q + l] : T(0);
     }
@@ -305,8 +320,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
             for (int k = 0; k < 9; ++k) R[k] = c2 * a[k] + (k < 3 ? cb * b[k] : T(0));
         }
     }
-    // constant of the monomial form
-    const T c0 = Q0 - (R[3] * Mxx + R[4] * Mxy + R[5] * Mxz + R[6] * Myy + R[7] * Myz + R[8] * Mzz);
+    // constant of the monomial form, less the cell average: R(centroid) - Q0
+    const T dc = -(R[3] * Mxx + R[4] * Mxy + R[5] * Mxz + R[6] * Myy + R[7] * Myz + R[8] * Mzz);
+    const T c0 = Q0 + dc;
     // positivity: the 5 lanes of the cell exchange their values at each point
     bool bad = false;
 #pragma unroll 4
@@ -326,8 +342,16 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     }
     if (!tile_ok) mbar_wait(&bar, 0);  // a late copy lands before the block exits
     if (!cl.active) return;
-    T* out = poly + c * POLY_STRIDE + q * 10;
-    out[0] = bad ? Q0 : c0;
+    T* rec = poly + c * Stride<T>::poly;
+    T* out = rec + q * 10;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: R(centroid) - Q0 and the average's hi / lo parts
+        out[0] = bad ? T(0) : dc;
+        rec[PHI + q] = Q0;
+        rec[PLO + q] = Q0lo;
+    } else {
+        out[0] = bad ? Q0 : c0;
+    }
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[1 + k] = bad ? T(0) : R[k];
     if (fallback && q == 0) fallback[c] = bad ? 1 : 0;

@@ -148,15 +148,13 @@ def _setup(cuda, oracle_mod, name, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_reconstruction_parity(cuda, oracle_mod, name, precision):
-    """The FP32 path reconstructs from FP32 copies of the state, so its
-    oracle runs on the same FP32-rounded state: what remains is the FP32
-    arithmetic, not the rounding of the data (whose differences between
-    neighbours can be far smaller than the data, e.g. the energy of a
-    slow flow)."""
+    """Both paths against the oracle on the same FP64 state.  The FP32 path
+    keeps each cell average as an FP32 hi / lo pair, so the differences
+    between neighbouring averages (which can be far smaller than the
+    averages, e.g. the energy of a slow flow) are exact to their own FP32
+    rounding."""
     mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, precision)
     poly_g, slopes_g, fb_g = [x.cpu().numpy() for x in s.debug_reconstruct()]
-    if precision == 1:
-        W, dW = W.astype(np.float32).astype(np.float64), dW.astype(np.float32).astype(np.float64)
     poly_o, slopes_o, fb_o = o.reconstruct(p, W, dW)
     np.testing.assert_array_equal(fb_g, fb_o)
     tol = TOL[precision]
@@ -164,9 +162,9 @@ def test_reconstruction_parity(cuda, oracle_mod, name, precision):
         # each coefficient family relative to its own size
         for lo, hi in ((0, 1), (1, 4), (4, 10)):
             if np.abs(poly_o[:, q, lo:hi]).max() > 1e-12:
-                assert _rel(poly_g[:, q, lo:hi], poly_o[:, q, lo:hi]) < tol * 10, (q, lo)
+                assert _rel(poly_g[:, q, lo:hi], poly_o[:, q, lo:hi]) < tol, (q, lo)
     if p.weno or p.order == 2:
-        assert _rel(slopes_g, slopes_o) < tol * 10
+        assert _rel(slopes_g, slopes_o) < tol
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -186,7 +184,7 @@ def test_face_record_parity(cuda, oracle_mod, name, stage, precision):
         ref = rec_o[:, lo:hi]
         scale = max(np.abs(ref).max(), floor)
         err = np.abs(rec_g[:, lo:hi] - ref).max() / scale
-        assert err < TOL[precision] * 10, (lo, hi, err)
+        assert err < TOL[precision], (lo, hi, err)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -205,7 +203,7 @@ def test_ten_steps_parity(cuda, oracle_mod, name, precision):
     for q in range(5):
         ref = dWo[3 * q:3 * q + 3]
         if np.abs(ref).max() > 1e-10:
-            assert _rel(dWg[3 * q:3 * q + 3], ref) < TOL[precision] * 10, q
+            assert _rel(dWg[3 * q:3 * q + 3], ref) < TOL[precision], q
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -223,7 +221,7 @@ def test_config1_sine_wave_ten_steps(cuda, oracle_mod, precision):
     Wg, dWg = [x.cpu().numpy() for x in s.get()]
     assert _state_rel(Wg, Wo) < TOL[precision]
     for q in range(5):
-        assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10
+        assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision]
     # accuracy against the exact solution is the same in both precisions
     We, _ = I.sine_wave_state(mesh, t=t_o)
     vol = g.geometry()["vol"]
@@ -232,23 +230,70 @@ def test_config1_sine_wave_ten_steps(cuda, oracle_mod, precision):
     assert abs(l1_g - l1_o) < 1e-3 * l1_o
 
 
+def _grad_rel(dWg, dWo):
+    """max over components with a gradient above 1e-10 of the normwise
+    relative error of the gradient (its three directions share one scale)."""
+    return max(_rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) for q in range(5)
+               if np.abs(dWo[3 * q:3 * q + 3]).max() > 1e-10)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-def test_config2_sod_full_size_one_step(cuda, oracle_mod, precision):
+def test_config2_sod_full_size_three_steps(cuda, oracle_mod, precision):
     """The 24,576-cell Sod tube (64 x 8 x 8 hexes x 6, WENO) at full size,
-    in the launch configuration the benchmark times: one step, every cell."""
+    in the launch configuration the benchmark times (its autotuned variant
+    included): three steps, every cell, averages and gradients."""
     mesh, W, dW = I.sod_case()
     g = gks.Mesh(mesh)
     assert (g.nc, g.nf, g.n_boundary) == (24576, 49280, 256)
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
     s.init(W, dW)
+    s.autotune(steps=3, cache=False)  # restores the initial state
     o = oracle_mod.Mesh(mesh)
-    Wo, dWo, _, _ = o.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, nsteps=1)
-    s.step(1)
+    Wo, dWo, to, _ = o.run(oracle_mod.params(weno=1, cfl=0.5), W, dW, nsteps=3)
+    s.step(3)
     s.sync()
     Wg, dWg = [x.cpu().numpy() for x in s.get()]
-    assert _state_rel(Wg, Wo) < TOL[precision]
-    for q in (0, 1, 4):
-        assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10
+    assert abs(s.time()[0] - to) <= TOL[precision] * to
+    assert _state_rel(Wg, Wo) < TOL[precision], _state_rel(Wg, Wo)
+    assert _grad_rel(dWg, dWo) < TOL[precision], _grad_rel(dWg, dWo)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sod_tube_16x4x4_ten_steps(cuda, oracle_mod, precision):
+    """WENO over ten steps on a Sod tube of 16 x 4 x 4 hexes x 6 (1,536
+    cells, open x ends, y and z periodic): the shock, the contact and the
+    rarefaction cross several cells, averages and gradients in full."""
+    mesh = I.box_mesh((16, 4, 4), (1.0, 0.25, 0.25), (False, True, True), jitter=0.1, seed=51)
+    W, dW = I.riemann_x_state(mesh)
+    kw = dict(weno=1, cfl=0.5)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(precision=precision, **kw))
+    s.init(W, dW)
+    Wo, dWo, to, _ = oracle_mod.Mesh(mesh).run(oracle_mod.params(**kw), W, dW, nsteps=10)
+    s.step(10)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    assert abs(s.time()[0] - to) <= TOL[precision] * to
+    assert _state_rel(Wg, Wo) < TOL[precision], _state_rel(Wg, Wo)
+    assert _grad_rel(dWg, dWo) < TOL[precision], _grad_rel(dWg, dWo)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_density_wave_12_cubed_weno_ten_steps(cuda, oracle_mod, precision):
+    """WENO over ten steps on the periodic density wave at 12^3 hexes x 6
+    (10,368 cells): a smooth field, where the gradients are the most
+    exposed to rounding (no jump sets their scale)."""
+    mesh, W, dW = I.sine_wave_case(n=12)
+    kw = dict(weno=1, cfl=0.5)
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(precision=precision, **kw))
+    s.init(W, dW)
+    Wo, dWo, to, _ = oracle_mod.Mesh(mesh).run(oracle_mod.params(**kw), W, dW, nsteps=10)
+    s.step(10)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    assert _state_rel(Wg, Wo) < TOL[precision], _state_rel(Wg, Wo)
+    assert _grad_rel(dWg, dWo) < TOL[precision], _grad_rel(dWg, dWo)
 
 
 def test_time_step_rule_and_t_end(cuda, oracle_mod):
@@ -347,12 +392,10 @@ def test_config4_vortex_full_size_one_step(cuda, oracle_mod):
     oracle element by element on 16^3 hexes x 6 (24,576 cells), FP64 and
     FP32 bulk.  At full size (64^3 x 6 = 1,572,864 cells), where the oracle
     would take minutes, one step is checked by what holds at any size:
-    Sum |Omega| W conserved to FP64 rounding in both precisions, the FP32
-    cell averages within 2e-5 of the FP64 path's (momentum components on one
-    shared scale), and the FP32 gradients within the bound that grows as the
-    cells shrink (32 FP32 unit roundoffs x the largest state entry x the
-    largest 3 / dr: the gradients come from the face states by the divergence
-    theorem, Sec. 3, Eq. step-du)."""
+    Sum |Omega| W conserved to FP64 rounding in both precisions, and the FP32
+    cell averages (momentum components on one shared scale) and gradients
+    within 2e-5 of the FP64 path's, which matches the oracle at 1e-11 on the
+    16^3 mesh."""
     kw = dict(weno=0, cfl=0.5)
     mesh, W, dW = I.isentropic_vortex_case(n=16, order=2)
     Wo, dWo, to, _ = oracle_mod.Mesh(mesh).run(oracle_mod.params(**kw), W, dW, nsteps=1)
@@ -366,7 +409,7 @@ def test_config4_vortex_full_size_one_step(cuda, oracle_mod):
         assert abs(s.time()[0] - to) <= TOL[precision] * to
         assert _state_rel(Wg, Wo) < TOL[precision]
         for q in range(5):
-            assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision] * 10, q
+            assert _rel(dWg[3 * q:3 * q + 3], dWo[3 * q:3 * q + 3]) < TOL[precision], q
 
     mesh, W, dW = I.isentropic_vortex_case(n=64, order=2)
     g = gks.Mesh(mesh)
@@ -391,5 +434,4 @@ def test_config4_vortex_full_size_one_step(cuda, oracle_mod):
     for q in range(5):
         sc = mom if 1 <= q <= 3 else np.abs(W64[q]).max()
         assert np.abs(W32[q] - W64[q]).max() < TOL[1] * sc, q
-    bound = 32 * 2.0 ** -24 * np.abs(W64).max() * (3.0 / dr).max()
-    assert np.abs(dW32 - dW64).max() <= bound, np.abs(dW32 - dW64).max() / bound
+    assert _grad_rel(dW32, dW64) < TOL[1], _grad_rel(dW32, dW64)
