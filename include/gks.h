@@ -76,7 +76,12 @@ typedef struct gks_params {
     int32_t viscous;     /* 0: Euler, tau = 0; 1: tau = mu / p (Sec. 2.2) */
     int32_t precision;   /* 0: FP64 throughout; 1: FP32 bulk (reconstruction, flux,
                             face records and stage states in FP32; FP64 master cell
-                            averages updated by compensated sums) */
+                            averages updated by compensated sums; cell averages
+                            kept as FP32 hi + lo pairs, and the stage-1 face
+                            records relative to the mean of the face's two
+                            averages, with its flux in FP64); 2: FP32 bulk as 1
+                            with the stencil operators M1, M2, the cell moments
+                            and their products in the reconstruction in FP64 */
     int32_t reserved;    /* must be 0 */
 } gks_params;
 

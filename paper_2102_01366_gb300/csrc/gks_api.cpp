@@ -67,8 +67,8 @@ static gks_status check_params(const gks_params* p) {
     }
     if ((p->weno != 0 && p->weno != 1) || (p->order != 2 && p->order != 3) ||
         (p->smooth_flux != 0 && p->smooth_flux != 1) || (p->viscous != 0 && p->viscous != 1) ||
-        (p->precision != 0 && p->precision != 1) || p->reserved != 0) {
-        set_error("weno, smooth_flux, viscous, precision must be 0 or 1; order 2 or 3; reserved 0");
+        (p->precision < 0 || p->precision > 2) || p->reserved != 0) {
+        set_error("weno, smooth_flux, viscous must be 0 or 1; precision 0, 1 or 2; order 2 or 3; reserved 0");
         return GKS_E_ARG;
     }
     if (p->viscous && !(p->mu > 0.0)) {
@@ -278,19 +278,22 @@ bool has_fixed(const gks_mesh& m) {
     return false;
 }
 
-Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool fixed) {
+Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool fixed, bool ops64 = false) {
     Layout L;
     const size_t T = fp32 ? 4 : 8;
+    // FP32 bulk with FP64 stencil operators: the reconstruction tile and the
+    // step-1 operator stay FP64 (as in the FP64 path)
+    const size_t TO = ops64 ? 8 : T;
     const size_t nblk = (size_t)update_blocks(nc);
     L.nbr = L.add(4 * 4 * nc);
     L.cface = L.add(4 * 4 * nc);
     L.inv_vol = L.add(8 * nc);
     L.dr = L.add(T * nc);
-    L.M1 = L.add(T * 12 * nc);
-    L.tile = L.add(T * TILE_ROWS * CELLS_PER_BLOCK * nblk);
+    L.M1 = L.add(TO * 12 * nc);
+    L.tile = L.add(TO * TILE_ROWS * CELLS_PER_BLOCK * nblk);
     L.flr = L.add(4 * 2 * nf);
     L.fgeo = L.add(T * FGEO * nf);
-    L.fan = fp32 ? L.add(8 * 4 * nf) : 0;  // FP32 bulk: FP64 face area vectors A n
+    L.fan = fp32 ? L.add(4 * 6 * nf) : 0;  // FP32 bulk: face area vectors A n as FP32 hi / lo pairs
     L.cell_case = L.add(4 * nc);
     L.perm = L.add(4 * nf);
     L.Wd = L.add(8 * 5 * nc);
@@ -322,6 +325,7 @@ struct gks_state {
     gks_params params;
     HostPhys phys;
     bool fp32 = false;
+    bool ops64 = false;  // precision 2: FP32 bulk with FP64 stencil operators
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     char* ws = nullptr;
@@ -355,11 +359,20 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.cface = at<int32_t>(s, L.cface);
     m.inv_vol = at<double>(s, L.inv_vol);
     m.dr = at<T>(s, L.dr);
-    m.M1 = at<T>(s, L.M1);
-    m.tile = at<T>(s, L.tile);
+    if (s->ops64) {
+        m.M1 = nullptr;
+        m.tile = nullptr;
+        m.M1d = at<double>(s, L.M1);
+        m.tiled = at<double>(s, L.tile);
+    } else {
+        m.M1 = at<T>(s, L.M1);
+        m.tile = at<T>(s, L.tile);
+        m.M1d = nullptr;
+        m.tiled = nullptr;
+    }
     m.flr = at<int32_t>(s, L.flr);
     m.fgeo = at<T>(s, L.fgeo);
-    m.fan = L.fan ? at<double>(s, L.fan) : nullptr;
+    m.fan = L.fan ? at<float>(s, L.fan) : nullptr;
     m.fixed = L.X0 ? at<T>(s, L.X0) : nullptr;
     st.Wd = at<double>(s, L.Wd);
     st.X = at<T>(s, L.X);
@@ -403,7 +416,7 @@ static gks_status upload_faces(gks_state* s) {
     for (int64_t d = 0; d < nf; ++d) inv[perm[d]] = (int32_t)d;
     std::vector<int32_t> cface(4 * nc), flr(2 * nf);
     std::vector<T> fgeo(FGEO * nf, T(0));
-    std::vector<double> fan(s->L.fan ? 4 * nf : 0, 0.0);
+    std::vector<float> fan(s->L.fan ? 6 * nf : 0, 0.0f);
     for (int64_t c = 0; c < nc; ++c)
         for (int f = 0; f < 4; ++f) {
             const int64_t fi = g.csr_face[c * 4 + f];
@@ -424,7 +437,11 @@ static gks_status upload_faces(gks_state* s) {
             r[13 + k] = (T)g.gp_r[f * 9 + k];
         }
         if (!fan.empty())
-            for (int a = 0; a < 3; ++a) fan[d * 4 + a] = g.farea[f] * g.fnorm[f * 3 + a];
+            for (int a = 0; a < 3; ++a) {
+                const double v = g.farea[f] * g.fnorm[f * 3 + a];
+                fan[d * 6 + 2 * a] = (float)v;
+                fan[d * 6 + 2 * a + 1] = (float)(v - (double)(float)v);
+            }
     }
     auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
         return cudaMemcpyAsync(s->ws + off, src, bytes, cudaMemcpyHostToDevice, s->stream);
@@ -432,29 +449,31 @@ static gks_status upload_faces(gks_state* s) {
     GKS_CHECK_CUDA(put(L.cface, cface.data(), 4 * cface.size()));
     GKS_CHECK_CUDA(put(L.flr, flr.data(), 4 * flr.size()));
     GKS_CHECK_CUDA(put(L.fgeo, fgeo.data(), sizeof(T) * fgeo.size()));
-    if (!fan.empty()) GKS_CHECK_CUDA(put(L.fan, fan.data(), 8 * fan.size()));
+    if (!fan.empty()) GKS_CHECK_CUDA(put(L.fan, fan.data(), 4 * fan.size()));
     GKS_CHECK_CUDA(put(L.perm, perm.data(), 4 * perm.size()));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
     return GKS_OK;
 }
 
-template <typename T>
-static gks_status upload_mesh(gks_state* s) {
+// the reconstruction's static cell data in the operator precision TO
+template <typename T, typename TO>
+static gks_status upload_cells(gks_state* s) {
     const gks_mesh& g = *s->mesh;
     const int64_t nc = g.nc;
     const Layout& L = s->L;
     std::vector<int32_t> nbr(4 * nc);
     std::vector<double> inv_vol(nc);
     const int64_t nblk = update_blocks(nc);
-    std::vector<T> dr(nc), M1(12 * nc);
+    std::vector<T> dr(nc);
+    std::vector<TO> M1(12 * nc);
     // per-block tile [blk][TILE_ROWS][CELLS_PER_BLOCK], zero past the last cell
-    std::vector<T> tile((size_t)nblk * TILE_ROWS * CELLS_PER_BLOCK, T(0));
+    std::vector<TO> tile((size_t)nblk * TILE_ROWS * CELLS_PER_BLOCK, TO(0));
     // Sec. 4.4: with linear weights a boundary cell's third-order step is the
     // least-squares first-order fit to its P2 stencil
     const bool linear_boundary = !s->params.weno && s->params.order == 3;
     for (int64_t c = 0; c < nc; ++c) {
-        T* tc = &tile[(size_t)(c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK];
-        auto put_row = [&](int row, double v) { tc[(size_t)row * CELLS_PER_BLOCK] = (T)v; };
+        TO* tc = &tile[(size_t)(c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK];
+        auto put_row = [&](int row, double v) { tc[(size_t)row * CELLS_PER_BLOCK] = (TO)v; };
         for (int f = 0; f < 4; ++f) {
             nbr[f * nc + c] = (int32_t)g.nbr[c * 4 + f];
             const int64_t fi = g.csr_face[c * 4 + f];
@@ -468,7 +487,7 @@ static gks_status upload_mesh(gks_state* s) {
         dr[c] = (T)g.dr[c];
         for (int q = 0; q < 6; ++q) put_row(TILE_MOM + q, g.mom2[c * 6 + q]);
         for (int k = 0; k < 12; ++k) {
-            M1[k * nc + c] = (T)g.M1[c * 12 + k];
+            M1[k * nc + c] = (TO)g.M1[c * 12 + k];
             put_row(TILE_M1 + k, g.M1[c * 12 + k]);
         }
         const double* M2c = &g.M2[c * 144];
@@ -485,8 +504,8 @@ static gks_status upload_mesh(gks_state* s) {
     GKS_CHECK_CUDA(put(L.nbr, nbr.data(), 4 * nbr.size()));
     GKS_CHECK_CUDA(put(L.inv_vol, inv_vol.data(), 8 * inv_vol.size()));
     GKS_CHECK_CUDA(put(L.dr, dr.data(), sizeof(T) * dr.size()));
-    GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(T) * M1.size()));
-    GKS_CHECK_CUDA(put(L.tile, tile.data(), sizeof(T) * tile.size()));
+    GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(TO) * M1.size()));
+    GKS_CHECK_CUDA(put(L.tile, tile.data(), sizeof(TO) * tile.size()));
     GKS_CHECK_CUDA(put(L.cell_case, g.cell_case.data(), 4 * g.cell_case.size()));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
@@ -494,9 +513,16 @@ static gks_status upload_mesh(gks_state* s) {
     return upload_faces<T>(s);
 }
 
+template <typename T>
+static gks_status upload_mesh(gks_state* s) {
+    return s->ops64 ? upload_cells<T, double>(s) : upload_cells<T, T>(s);
+}
+
 extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
     if (!mesh || check_params(params) != GKS_OK) return 0;
-    return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision == 1, has_fixed(*mesh)).total;
+    return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision != 0, has_fixed(*mesh),
+                            params->precision == 2)
+        .total;
 }
 
 extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* params,
@@ -508,8 +534,9 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     gks_status ps = check_params(params);
     if (ps != GKS_OK) return ps;
     if (!mesh->has_stencils) { set_error("gks_state_create: stencils not built"); return GKS_E_STENCIL; }
-    const bool fp32 = params->precision == 1;
-    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32, has_fixed(*mesh));
+    const bool fp32 = params->precision != 0;
+    const bool ops64 = params->precision == 2;
+    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32, has_fixed(*mesh), ops64);
     if (!d_workspace || workspace_bytes < L.total) {
         set_error("gks_state_create: workspace missing or smaller than gks_workspace_bytes()");
         return GKS_E_NOMEM;
@@ -533,6 +560,7 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
                        params->viscous ? 1.0 / params->prandtl - 1.0 : 0.0, params->wall_temperature,
                        {params->wall_velocity[0], params->wall_velocity[1], params->wall_velocity[2]}};
     s->fp32 = fp32;
+    s->ops64 = ops64;
     s->ws = static_cast<char*>(d_workspace);
     s->L = L;
     if (stream) {

@@ -531,10 +531,14 @@ __device__ __forceinline__ HDiff<T> hd_sqrt(const HDiff<T>& a) {
     return {sl, sr, a.h / (sl + sr)};
 }
 
-// (e^{-l} - e^{-r}) / 2 = e^{-r} expm1(-2 h) / 2
+// (e^{-l} - e^{-r}) / 2, factored on the larger exponential so that expm1
+// stays within (-1, 0] (the other factoring overflows times underflows for
+// far-apart arguments): -e^{-l} expm1(2 h) / 2 for h <= 0, e^{-r}
+// expm1(-2 h) / 2 otherwise
 __device__ __forceinline__ HDiff<float> hd_expneg(const HDiff<float>& a) {
     const float el = expf(-a.l), er = expf(-a.r);
-    return {el, er, 0.5f * er * expm1f(-2.0f * a.h)};
+    const float h = a.h <= 0.0f ? -0.5f * el * expm1f(2.0f * a.h) : 0.5f * er * expm1f(-2.0f * a.h);
+    return {el, er, h};
 }
 
 // (erf l - erf r) / 2 = (1 / sqrt pi) int_r^l e^{-t^2} dt.  For |l - r| <= 1
@@ -615,5 +619,52 @@ __device__ __forceinline__ void normal_flux_half_difference(const float* Wl, con
     for (int j = 0; j < 3; ++j) out[1 + j] = hd_mul(m[j], un).h + n[j] * p.h;
     out[4] = hd_mul(hd_add(E, p), un).h;
 }
+
+// ------------------------------------------------- FP32 pair numbers --
+// A value hi + lo carried as two FP32 numbers (|lo| <= ulp(hi) / 2): about
+// 48 significant bits at FP32-pipe speed.  Sums by Knuth's TwoSum, products
+// by the FMA form of Dekker's TwoProduct, quotients by one correction of an
+// FP32 quotient with the exact residual.  Used where a value of O(|W|) or
+// O(|F|) must stay exact to far below FP32 rounding without the FP64 unit
+// (the FP32-bulk reference flux).
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_norm(float s, float e) {
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    return f2_norm(s, e);
+}
+
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e += a.hi * b.lo + a.lo * b.hi;
+    return f2_norm(p, e);
+}
+
+__device__ __forceinline__ F2 f2_scale(float c, F2 a) {
+    const float p = c * a.hi;
+    float e = fmaf(c, a.hi, -p);
+    e += c * a.lo;
+    return f2_norm(p, e);
+}
+
+__device__ __forceinline__ F2 f2_div(F2 a, F2 b) {
+    const float q = a.hi / b.hi;
+    // residual a - q b, exact to the pair's precision
+    const F2 qb = f2_mul({q, 0.0f}, b);
+    const F2 r = f2_add(a, {-qb.hi, -qb.lo});
+    return f2_norm(q, r.hi / b.hi);
+}
+
+__device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
 
 }  // namespace gks

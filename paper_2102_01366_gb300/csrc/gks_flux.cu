@@ -460,35 +460,37 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             face_flux_deviation(sm.dv, g, L, Rc, Rm, Wcl, n, ph.gm1, dF);
 #pragma unroll
             for (int q = 0; q < 5; ++q) Fs[q] += T(0.5) * dt * dF[q];
-            // once per face (its first Gauss point): the reference flux in
-            // FP64, W_m from the hi / lo averages and the FP64 area vector
-            // A n (whose sum over a closed cell vanishes to FP64 rounding,
-            // where the FP32 weights and normals leave eps A), split into
-            // FP32 hi and lo parts; entering both cells with opposite signs,
-            // it keeps the update exactly conservative
-            double ref[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            // once per face (its first Gauss point): the reference flux with
+            // W_m from the hi / lo averages and the face's area vector A n
+            // taken exactly (its sum over a closed cell vanishes to FP64
+            // rounding, where the FP32 weights and normals leave eps A), in
+            // FP32 pairs, stored as hi and lo parts; entering both cells with
+            // opposite signs, it keeps the update exactly conservative
+            F2 ref[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             if (k == 0) {
-                double Wm[5];
+                F2 Wm[5];
 #pragma unroll
-                for (int q = 0; q < 5; ++q)
-                    Wm[q] = 0.5 * (((double)sm.dv[0][g][q] + (double)sm.dv[0][g][5 + q]) +
-                                   ((double)sm.dv[1][g][q] + (double)sm.dv[1][g][5 + q]));
-                const double* an = m.fan + 4 * f;
-                const double mn = Wm[1] * an[0] + Wm[2] * an[1] + Wm[3] * an[2];  // A m.n
-                const double ir = 1.0 / Wm[0];
-                const double un = mn * ir;
-                const double pm = (double)ph.gm1 * (Wm[4] - 0.5 * (Wm[1] * Wm[1] + Wm[2] * Wm[2] + Wm[3] * Wm[3]) * ir);
-                const double c = 0.5 * (double)dt;
-                ref[0] = c * mn;
+                for (int q = 0; q < 5; ++q) {
+                    const F2 a = f2_add({sm.dv[0][g][q], sm.dv[0][g][5 + q]}, {sm.dv[1][g][q], sm.dv[1][g][5 + q]});
+                    Wm[q] = {0.5f * a.hi, 0.5f * a.lo};
+                }
+                const float* an = m.fan + 6 * f;
+                const F2 A[3] = {{an[0], an[1]}, {an[2], an[3]}, {an[4], an[5]}};
+                const F2 mn = f2_add(f2_add(f2_mul(Wm[1], A[0]), f2_mul(Wm[2], A[1])), f2_mul(Wm[3], A[2]));
+                const F2 un = f2_div(mn, Wm[0]);  // A u.n
+                const F2 mm = f2_add(f2_add(f2_mul(Wm[1], Wm[1]), f2_mul(Wm[2], Wm[2])), f2_mul(Wm[3], Wm[3]));
+                const F2 ke = f2_div(f2_scale(0.5f, mm), Wm[0]);
+                const F2 pm = f2_scale((float)ph.gm1, f2_add(Wm[4], {-ke.hi, -ke.lo}));
+                const float hd = 0.5f * (float)dt;
+                ref[0] = f2_scale(hd, mn);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) ref[1 + j] = c * (Wm[1 + j] * un + pm * an[j]);
-                ref[4] = c * ((Wm[4] + pm) * un);
+                for (int j = 0; j < 3; ++j) ref[1 + j] = f2_scale(hd, f2_add(f2_mul(Wm[1 + j], un), f2_mul(pm, A[j])));
+                ref[4] = f2_scale(hd, f2_mul(f2_add(Wm[4], pm), un));
             }
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                const T hi = (T)ref[q];
-                mine_rec[REC1_REF + q] = hi;
-                mine_rec[REC1_REF + 5 + q] = (T)(ref[q] - (double)hi);
+                mine_rec[REC1_REF + q] = ref[q].hi;
+                mine_rec[REC1_REF + 5 + q] = ref[q].lo;
             }
         }
 #pragma unroll

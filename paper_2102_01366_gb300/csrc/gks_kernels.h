@@ -59,9 +59,13 @@ struct DevMesh {
     const T* dr;           // [nc]
     const T* M1;           // [12][nc]
     const T* tile;         // [blocks][TILE_ROWS][CELLS_PER_BLOCK] reconstruction data
+    // FP32 bulk with FP64 stencil operators (precision 2): the same two in
+    // FP64, M1 and tile NULL (else these are NULL)
+    const double* M1d;
+    const double* tiled;
     const int32_t* flr;    // [2][nf]
     const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
-    const double* fan;     // FP32 bulk: [nf][4] FP64 face area vectors A n (NULL in FP64)
+    const float* fan;      // FP32 bulk: [nf][6] face area vectors A n as FP32 hi / lo pairs (NULL in FP64)
     const T* fixed;        // [nc][Stride<T>::xs] state held by fixed boundary faces (NULL: none)
 };
 

@@ -107,17 +107,27 @@ struct FinArg {
 };
 // Q_a - Q_b of component q of two cell averages: in FP32 bulk from the hi
 // and lo parts (exact to the rounding of the difference itself)
-template <typename T>
-__device__ __forceinline__ T avg_diff(const T* __restrict__ X, int64_t a, int64_t b, int q) {
+template <typename T, typename TO = T>
+__device__ __forceinline__ TO avg_diff(const T* __restrict__ X, int64_t a, int64_t b, int q) {
     constexpr int XSR = Stride<T>::xs;
     if constexpr (sizeof(T) == 4)
-        return (X[a * XSR + q] - X[b * XSR + q]) + (X[a * XSR + XLO + q] - X[b * XSR + XLO + q]);
+        return ((TO)X[a * XSR + q] - (TO)X[b * XSR + q]) + ((TO)X[a * XSR + XLO + q] - (TO)X[b * XSR + XLO + q]);
     else
         return X[a * XSR + q] - X[b * XSR + q];
 }
 
-// reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3
-template <typename T>
+// the step-1 operator entry M1[row][c] in the operator precision TO
+template <typename T, typename TO>
+__device__ __forceinline__ TO m1_at(const DevMesh<T>& m, int row, int64_t c) {
+    if constexpr (sizeof(TO) > sizeof(T))
+        return m.M1d[row * m.nc + c];
+    else
+        return m.M1[row * m.nc + c];
+}
+
+// reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3, the
+// products in the operator precision TO
+template <typename T, typename TO>
 __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* __restrict__ X,
                                                           T* __restrict__ slopes, FinArg<T> fin) {
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
@@ -125,37 +135,38 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
-    T b0 = T(0), b1 = T(0), b2 = T(0);
+    TO b0 = TO(0), b1 = TO(0), b2 = TO(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + c];
         if (nb < 0) continue;
-        const T dq = avg_diff(X, nb, c, q);
-        b0 += m.M1[(0 * 4 + f) * nc + c] * dq;
-        b1 += m.M1[(1 * 4 + f) * nc + c] * dq;
-        b2 += m.M1[(2 * 4 + f) * nc + c] * dq;
+        const TO dq = avg_diff<T, TO>(X, nb, c, q);
+        b0 += m1_at<T, TO>(m, 0 * 4 + f, c) * dq;
+        b1 += m1_at<T, TO>(m, 1 * 4 + f, c) * dq;
+        b2 += m1_at<T, TO>(m, 2 * 4 + f, c) * dq;
     }
     T* out = slopes + c * 15 + 3 * q;
-    out[0] = b0;
-    out[1] = b1;
-    out[2] = b2;
+    out[0] = (T)b0;
+    out[1] = (T)b1;
+    out[2] = (T)b2;
 }
 
 // P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
 // b = M1 (Q_nb - Q_x) over the existing neighbours
-template <typename T>
+template <typename T, typename TO>
 __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ X, int64_t x, int q, T* b) {
     const int64_t nc = m.nc;
-    b[0] = b[1] = b[2] = T(0);
+    TO s[3] = {TO(0), TO(0), TO(0)};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + x];
         if (nb < 0) continue;
-        const T dq = avg_diff(X, nb, x, q);
-        b[0] += m.M1[(0 * 4 + f) * nc + x] * dq;
-        b[1] += m.M1[(1 * 4 + f) * nc + x] * dq;
-        b[2] += m.M1[(2 * 4 + f) * nc + x] * dq;
+        const TO dq = avg_diff<T, TO>(X, nb, x, q);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[i] += m1_at<T, TO>(m, i * 4 + f, x) * dq;
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b[i] = (T)s[i];
 }
 
 // reconstruction (Sec. 4.1-4.3): the cell's own P1 slopes and, for the
@@ -164,8 +175,10 @@ __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restric
 // M1, moments) brought into shared memory by one bulk copy that overlaps the
 // neighbour gathers;
 // smoothness indicators, nonlinear weights, positivity at the cell's 12 face
-// Gauss points (Sec. 4.2); R written about the centroid in monomial form
-template <typename T>
+// Gauss points (Sec. 4.2); R written about the centroid in monomial form.
+// TO is the precision of the stencil operators and of their products
+// (FP32 bulk: FP32, or FP64 with precision 2; the FP64 path: FP64).
+template <typename T, typename TO>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
                                                          const T* __restrict__ X,
                                                          const T* __restrict__ slopes_in,
@@ -173,15 +186,20 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
                                                          T* __restrict__ poly,
                                                          int32_t* __restrict__ fallback,
                                                          FinArg<T> fin, int32_t* __restrict__ err) {
-    __shared__ alignas(128) T sT[TILE_ROWS][CELLS_PER_BLOCK];
+    __shared__ alignas(128) TO sT[TILE_ROWS][CELLS_PER_BLOCK];
     __shared__ alignas(8) unsigned long long bar;
-    constexpr unsigned TILE_BYTES = TILE_ROWS * CELLS_PER_BLOCK * sizeof(T);
+    constexpr unsigned TILE_BYTES = TILE_ROWS * CELLS_PER_BLOCK * sizeof(TO);
     static_assert(TILE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+    const TO* tile = nullptr;
+    if constexpr (sizeof(TO) > sizeof(T))
+        tile = m.tiled;
+    else
+        tile = m.tile;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();  // the barrier exists before anyone waits on it
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&bar, TILE_BYTES);
-        bulk_load(&sT[0][0], m.tile + (int64_t)blockIdx.x * TILE_ROWS * CELLS_PER_BLOCK, TILE_BYTES, &bar);
+        bulk_load(&sT[0][0], tile + (int64_t)blockIdx.x * TILE_ROWS * CELLS_PER_BLOCK, TILE_BYTES, &bar);
     }
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
     const int64_t nc = m.nc;
@@ -200,17 +218,17 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     if constexpr (sizeof(T) == 4) Q0lo = X[c * XSR + XLO + q];
 
     // data vector [dQ_f (4); grad Q_{f,l} (12)] of this component
-    T d[16];
+    TO d[16];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool ok = nb[f] >= 0;
         const T* xn = X + (ok ? (int64_t)nb[f] : c) * XSR;
         if constexpr (sizeof(T) == 4)
-            d[f] = ok ? (xn[q] - Q0) + (xn[XLO + q] - Q0lo) : T(0);
+            d[f] = ok ? ((TO)xn[q] - (TO)Q0) + ((TO)xn[XLO + q] - (TO)Q0lo) : TO(0);
         else
             d[f] = ok ? xn[q] - Q0 : T(0);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? xn[5 + 3 * q + l] : T(0);
+        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? (TO)xn[5 + 3 * q + l] : TO(0);
     }
     // the tile has landed (all threads wait; a give-up is reported, and the
     // values computed from an incomplete tile are never trusted by the host)
@@ -220,13 +238,13 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     T a[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        T acc = T(0);
+        TO acc = TO(0);
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc += sT[TILE_M2 + k * 16 + j][lc] * d[j];
-        a[k] = acc;
+        a[k] = (T)acc;
     }
-    const T Mxx = sT[TILE_MOM + 0][lc], Mxy = sT[TILE_MOM + 1][lc], Mxz = sT[TILE_MOM + 2][lc];
-    const T Myy = sT[TILE_MOM + 3][lc], Myz = sT[TILE_MOM + 4][lc], Mzz = sT[TILE_MOM + 5][lc];
+    const T Mxx = (T)sT[TILE_MOM + 0][lc], Mxy = (T)sT[TILE_MOM + 1][lc], Mxz = (T)sT[TILE_MOM + 2][lc];
+    const T Myy = (T)sT[TILE_MOM + 3][lc], Myz = (T)sT[TILE_MOM + 4][lc], Mzz = (T)sT[TILE_MOM + 5][lc];
 
     const T g22 = T(100.0 / 111.0), g12 = T(10.0 / 111.0), g02 = T(1.0 / 111.0);
     const T g11 = T(10.0 / 11.0), g01 = T(1.0 / 11.0);
@@ -234,13 +252,15 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     T b[3] = {T(0), T(0), T(0)};
     if (rc.weno || rc.order == 2) {
         // own P1 slope from the neighbour differences already loaded
+        TO bo[3] = {TO(0), TO(0), TO(0)};
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (nb[f] < 0) continue;
-            b[0] += sT[TILE_M1 + 0 * 4 + f][lc] * d[f];
-            b[1] += sT[TILE_M1 + 1 * 4 + f][lc] * d[f];
-            b[2] += sT[TILE_M1 + 2 * 4 + f][lc] * d[f];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) bo[i] += sT[TILE_M1 + i * 4 + f][lc] * d[f];
         }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) b[i] = (T)bo[i];
         if (slopes_out && cl.active) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) slopes_out[c * 15 + 3 * q + i] = b[i];
@@ -250,7 +270,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = rc.order == 2 ? (k < 3 ? b[k] : T(0)) : a[k];
     } else {
-        const T v23 = sT[TILE_V23][lc], v43 = sT[TILE_V43][lc];
+        const T v23 = (T)sT[TILE_V23][lc], v43 = (T)sT[TILE_V43][lc];
         // smoothness indicators, Eq. smooth-indicator
         const T beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
         // two-step beta_0 from the neighbours' P1 slopes, Eq. p0-non-linear-weight
@@ -266,7 +286,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
                 bj[1] = sj[1];
                 bj[2] = sj[2];
             } else {
-                p1_slope(m, X, nb[f], q, bj);
+                p1_slope<T, TO>(m, X, nb[f], q, bj);
             }
             b0j[nn++] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
         }
@@ -321,15 +341,17 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
         }
     }
     // constant of the monomial form, less the cell average: R(centroid) - Q0
-    const T dc = -(R[3] * Mxx + R[4] * Mxy + R[5] * Mxz + R[6] * Myy + R[7] * Myz + R[8] * Mzz);
+    const T dc = (T)(-((TO)R[3] * sT[TILE_MOM + 0][lc] + (TO)R[4] * sT[TILE_MOM + 1][lc] +
+                       (TO)R[5] * sT[TILE_MOM + 2][lc] + (TO)R[6] * sT[TILE_MOM + 3][lc] +
+                       (TO)R[7] * sT[TILE_MOM + 4][lc] + (TO)R[8] * sT[TILE_MOM + 5][lc]));
     const T c0 = Q0 + dc;
     // positivity: the 5 lanes of the cell exchange their values at each point
     bool bad = false;
 #pragma unroll 4
     for (int g = 0; g < 12; ++g) {
-        const T gx = sT[TILE_G + g * 3 + 0][lc];
-        const T gy = sT[TILE_G + g * 3 + 1][lc];
-        const T gz = sT[TILE_G + g * 3 + 2][lc];
+        const T gx = (T)sT[TILE_G + g * 3 + 0][lc];
+        const T gy = (T)sT[TILE_G + g * 3 + 1][lc];
+        const T gz = (T)sT[TILE_G + g * 3 + 2][lc];
         const T v = c0 + R[0] * gx + R[1] * gy + R[2] * gz + R[3] * gx * gx + R[4] * gx * gy + R[5] * gx * gz +
                     R[6] * gy * gy + R[7] * gy * gz + R[8] * gz * gz;
         const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
@@ -376,7 +398,10 @@ template <typename T>
 cudaError_t Launch<T>::slopes(const DevMesh<T>& m, const T* X, T* slopes, const Finalize* fin,
                               cudaStream_t s) {
     if (m.nc == 0) return cudaSuccess;
-    k_slopes<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, X, slopes, fin_arg<T>(fin));
+    if (m.M1d && sizeof(T) == 4)
+        k_slopes<T, double><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, X, slopes, fin_arg<T>(fin));
+    else
+        k_slopes<T, T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, X, slopes, fin_arg<T>(fin));
     return cudaGetLastError();
 }
 
@@ -390,8 +415,12 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X,
     rc.eps = (T)p.eps_weno;
     rc.weno = p.weno;
     rc.order = p.order;
-    k_recon<T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback, fin_arg<T>(fin),
-                                                        err);
+    if (m.tiled && sizeof(T) == 4)
+        k_recon<T, double><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback,
+                                                                    fin_arg<T>(fin), err);
+    else
+        k_recon<T, T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback,
+                                                               fin_arg<T>(fin), err);
     return cudaGetLastError();
 }
 

@@ -369,7 +369,7 @@ class State:
         fo, fb, sp = C.c_int32(), C.c_int32(), C.c_int32()
         ms = np.zeros(8)
         _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), C.byref(sp), _np_ptr(ms))
-        nvar = 8 if self.params.precision == 1 else 4
+        nvar = 8 if self.params.precision != 0 else 4
         self.variant = (fo.value, fb.value, sp.value)
         res = {"variant": list(self.variant), "ms_per_step": ms[:nvar].tolist()}
         if cache:

@@ -296,6 +296,53 @@ def test_density_wave_12_cubed_weno_ten_steps(cuda, oracle_mod, precision):
     assert _grad_rel(dWg, dWo) < TOL[precision], _grad_rel(dWg, dWo)
 
 
+@pytest.mark.parametrize("name", ["sod_small_weno", "sine_n3_weno", "closed_box_weno", "sine_n2_weno2"])
+def test_fp64_operator_variant_parity(cuda, oracle_mod, name):
+    """Precision 2 (FP32 bulk with the stencil operators, moments and their
+    products in FP64): reconstruction and ten steps against the oracle at
+    the FP32 tolerance, and within the same tolerance of precision 1."""
+    mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, name, 2)
+    poly_g, slopes_g, fb_g = [x.cpu().numpy() for x in s.debug_reconstruct()]
+    poly_o, slopes_o, fb_o = o.reconstruct(p, W, dW)
+    np.testing.assert_array_equal(fb_g, fb_o)
+    for q in range(5):
+        for lo, hi in ((0, 1), (1, 4), (4, 10)):
+            if np.abs(poly_o[:, q, lo:hi]).max() > 1e-12:
+                assert _rel(poly_g[:, q, lo:hi], poly_o[:, q, lo:hi]) < TOL[1], (q, lo)
+    nsteps = STEPS.get(name, 10)
+    Wo, dWo, t_o, _ = o.run(p, W, dW, nsteps=nsteps)
+    s.step(nsteps)
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    assert _state_rel(Wg, Wo) < TOL[1], _state_rel(Wg, Wo)
+    assert _grad_rel(dWg, dWo) < TOL[1], _grad_rel(dWg, dWo)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_config2_sod_to_t_end_equal_l1(cuda, precision):
+    """The full Sod tube to t = 0.2 (about 300 steps, every shock-tube wave
+    well developed): the FP32-bulk runs stay within the FP32 tolerance of the
+    FP64 run in density, and their L1 error against the exact Riemann
+    solution equals the FP64 run's to three significant digits."""
+    mesh, W, dW = I.sod_case()
+    g = gks.Mesh(mesh)
+    vol = g.geometry()["vol"]
+    exact = None
+    out = {}
+    for prec in (0, precision):
+        s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
+        s.init(W, dW)
+        t = s.run(t_end=0.2, chunk=64)
+        Wg = s.get()[0].cpu().numpy()
+        if exact is None:
+            exact = I.riemann_x_exact_density(mesh, t)
+        out[prec] = (Wg, (vol * np.abs(Wg[0] - exact)).sum() / vol.sum())
+        del s
+    (W64, l1_64), (W32, l1_32) = out[0], out[precision]
+    assert abs(l1_32 - l1_64) < 1e-3 * l1_64, (l1_32, l1_64)
+    assert np.abs(W32[0] - W64[0]).max() / np.abs(W64[0]).max() < 1e-3
+
+
 def test_time_step_rule_and_t_end(cuda, oracle_mod):
     mesh, W, dW, s, o, p = _setup(cuda, oracle_mod, "sod_small_weno", 0)
     assert abs(s.timestep() - o.timestep(p, W)) <= 1e-14 * o.timestep(p, W)
