@@ -541,15 +541,21 @@ __device__ __forceinline__ HDiff<float> hd_expneg(const HDiff<float>& a) {
     return {el, er, h};
 }
 
-// (erf l - erf r) / 2 = (1 / sqrt pi) int_r^l e^{-t^2} dt.  For |l - r| <= 1
-// the integral is taken by 5-point Gauss-Legendre quadrature on [r, l]
-// (error below 2e-8 of the integral for an interval of length 1, far less
-// for shorter ones); for longer intervals the difference of the two
+// (erf l - erf r) / 2 = (1 / sqrt pi) int_r^l e^{-t^2} dt, given erf l and
+// erf r (el, er).  For |l - r| <= 0.1 the integral is taken by 3-point and
+// up to |l - r| <= 1 by 5-point Gauss-Legendre quadrature on [r, l] (errors
+// below 1e-9 and 2e-8 of the integral at those lengths, far less for
+// shorter intervals); for longer intervals the difference of the two
 // complementary error functions of the tails, which does not cancel there.
-__device__ __forceinline__ HDiff<float> hd_erf(const HDiff<float>& a) {
-    const float el = erff(a.l), er = erff(a.r);
+__device__ __forceinline__ HDiff<float> hd_erf(const HDiff<float>& a, float el, float er) {
     float h;
-    if (fabsf(a.h) <= 0.5f) {
+    if (fabsf(a.h) <= 0.05f) {
+        // nodes and weights of the 3-point Gauss-Legendre rule on [-1, 1]
+        const float x1 = 0.77459666924148338f, w0 = 0.88888888888888889f, w1 = 0.55555555555555556f;
+        const float m = a.mid(), d = a.h;
+        auto g = [](float t) { return expf(-t * t); };
+        h = 0.56418958354775628695f * d * (w0 * g(m) + w1 * (g(m + x1 * d) + g(m - x1 * d)));
+    } else if (fabsf(a.h) <= 0.5f) {
         // nodes and weights of the 5-point Gauss-Legendre rule on [-1, 1]
         const float x1 = 0.53846931010568309f, x2 = 0.90617984593866399f;
         const float w0 = 0.56888888888888889f, w1 = 0.47862867049936647f, w2 = 0.23692688505618909f;
@@ -567,21 +573,22 @@ __device__ __forceinline__ HDiff<float> hd_erf(const HDiff<float>& a) {
 
 // Half-difference of psi(W) = rho <psi>_{u1>0} - rho <psi>_{u1<0} between
 // the two states Wl, Wr (face frame, x1 along the normal), given the
-// half-difference h of the states themselves.  With s = sqrt(lambda) U1 =
+// half-difference h of the states themselves and erf of each state's s
+// (below).  With s = sqrt(lambda) U1 =
 // W1 / sqrt(2 p rho), e0 = erf(s) and g = e^{-s^2} / sqrt(pi lambda) =
 // e^{-s^2} sqrt(2 p / (pi rho)), the half-space moments of Sec. 2.2 give
 //   psi(W) = (rho e0, W1 e0 + rho g, W2 e0, W3 e0, W4 e0 + W1 g / 2),
 // and W^c = rho_l <psi>_{u1>0} + rho_r <psi>_{u1<0} = (Wl + Wr) / 2 +
 // (psi(Wl) - psi(Wr)) / 2, so W^c minus the mean of the two states is h_psi.
 __device__ __forceinline__ void psi_half_difference(const float* Wl, const float* Wr, const float* h, float gm1,
-                                                    float* out) {
+                                                    float erf_l, float erf_r, float* out) {
     const HDiff<float> rho{Wl[0], Wr[0], h[0]}, m1{Wl[1], Wr[1], h[1]}, m2{Wl[2], Wr[2], h[2]};
     const HDiff<float> m3{Wl[3], Wr[3], h[3]}, E{Wl[4], Wr[4], h[4]};
     const HDiff<float> mm = hd_add(hd_add(hd_mul(m1, m1), hd_mul(m2, m2)), hd_mul(m3, m3));
     const HDiff<float> p = hd_scale(gm1, hd_add(E, hd_scale(-0.5f, hd_div(mm, rho))));
     const HDiff<float> sy = hd_sqrt(hd_scale(2.0f, hd_mul(p, rho)));
     const HDiff<float> sv = hd_div(m1, sy);
-    const HDiff<float> e0 = hd_erf(sv);
+    const HDiff<float> e0 = hd_erf(sv, erf_l, erf_r);
     const HDiff<float> ex = hd_expneg(hd_mul(sv, sv));
     const HDiff<float> g = hd_scale(0.79788456080286536f, hd_mul(ex, hd_sqrt(hd_div(p, rho))));  // sqrt(2 / pi)
     out[0] = hd_mul(rho, e0).h;

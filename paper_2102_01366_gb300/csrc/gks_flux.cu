@@ -48,13 +48,16 @@ struct FluxSmem {
     T w0[2][FP_GP][5];   // rho <psi>+- of each side
     T p[2][FP_GP];       // pressure of each side
     T dwc[2][FP_GP][15]; // rho <a_i psi>+- of each side
-    T ac[FP_GP][15];     // equilibrium slopes a^c_i (formed once, by the right warps)
+    T ac[NR == 40 ? 1 : FP_GP][15];  // stage 2: equilibrium slopes a^c_i (formed once, by the right warps)
     T out[2][FP_GP][20]; // partial Fh, D, W0, dW of each side
     T red[FP_GP * rec_stride<NR>()];  // weighted record entries per Gauss point
     // stage 1: each side's cell average (hi, lo) and R - average at the point
     // (phase 1); from phase 3 the left side's R - average slots hold W^c - W_m
     // (global frame)
     T dv[NR == 40 ? 2 : 1][NR == 40 ? FP_GP : 1][15];
+    // stage 1: each side's half-space rho-moment <u^0> (erfc of its s), whose
+    // erf the interface deviation reuses
+    T m0[NR == 40 ? 2 : 1][NR == 40 ? FP_GP : 1];
 };
 
 // The two warps that hold the two sides of the same 32 Gauss points (warp w
@@ -74,8 +77,8 @@ __device__ __forceinline__ void pair_barrier(int g) {
 // half-difference rules, W^c - W_m carries rounding relative to itself only.
 // Interior and open faces; wall and fixed faces subtract directly.
 template <typename T>
-__device__ __forceinline__ void interface_deviation(T (*dv)[FP_GP][15], int g, int L, int Rc, const T (*Rm)[3],
-                                                    const T (*w0)[FP_GP][5], T gm1) {
+__device__ __forceinline__ void interface_deviation(T (*dv)[FP_GP][15], const T (*m0)[FP_GP], int g, int L, int Rc,
+                                                    const T (*Rm)[3], const T (*w0)[FP_GP][5], T gm1) {
     T out[5];
     const bool pair = (L >= 0 || L == FLR_OPEN) && (Rc >= 0 || Rc == FLR_OPEN);
     if (pair) {
@@ -93,7 +96,9 @@ __device__ __forceinline__ void interface_deviation(T (*dv)[FP_GP][15], int g, i
         rotate_vec(Rm, Wl + 1, tl + 1);
         rotate_vec(Rm, Wr + 1, tr + 1);
         rotate_vec(Rm, hg + 1, th + 1);
-        psi_half_difference(tl, tr, th, gm1, out);
+        // erf of each side's s from its half-space moment <u^0> (phase 1):
+        // 2 <u^0>_{u1>0} - 1 on the left, 1 - 2 <u^0>_{u1<0} on the right
+        psi_half_difference(tl, tr, th, gm1, T(2) * m0[0][g] - T(1), T(1) - T(2) * m0[1][g], out);
         to_global(Rm, out);
 #pragma unroll
         for (int q = 0; q < 5; ++q) out[q] += sg[q];
@@ -237,6 +242,7 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
 #pragma unroll
     for (int q = 0; q < 5; ++q) sm.w0[side][g][q] = mw0[q];
     sm.p[side][g] = S.p;
+    if constexpr (NR == 40) sm.m0[side][g] = t.u[0];
     pair_barrier(g);
 
     // ---- phase 2 ----
@@ -302,9 +308,15 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
     pair_barrier(g);
 
     // ---- phase 3 ----
+    // Stage 1: the left warps form W^c - W_m (the gradient records' interface
+    // state) while the right warps take all of the equilibrium part, the
+    // a^c.u flux terms included, so the pair need not meet here; stage 2:
+    // the left warps take the a^c.u terms after the right warps share a^c.
+    constexpr bool RIGHT_GRAD = (NR == 40);
     {
-        make_tab(t, C, ph.K, 0);
+        if (side == 1 || !RIGHT_GRAD) make_tab(t, C, ph.K, 0);
         T ac[3][5], divF[5];
+        T mf1r[5] = {T(0), T(0), T(0), T(0), T(0)};
         if (side == 1) {
             // the equilibrium slopes, once per point (Eq. co for g^c)
             T dWc[3][5];
@@ -326,15 +338,19 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             // Jacobians, which FP32 evaluates without the cancellation of the
             // fourth- and fifth-order velocity moments
             euler_divergence(C, Wc, ph.gm1, dWc, divF);
+            if (RIGHT_GRAD) {
+                acc_grad<1>(t, ac, C.rho, mf1r);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
+                    for (int q = 0; q < 5; ++q) sm.ac[g][5 * i + q] = ac[i][q];
+            }
         } else if constexpr (NR == 40) {
             // the left warps meanwhile: stage 1's W^c - W_m for the gradient records
-            interface_deviation(sm.dv, g, L, Rc, Rm, sm.w0, ph.gm1);
+            interface_deviation(sm.dv, sm.m0, g, L, Rc, Rm, sm.w0, ph.gm1);
         }
-        pair_barrier(g);
+        if (!RIGHT_GRAD || PRF) pair_barrier(g);
         // Pr fix: the state integrals move to this side's (now unused) slope
         // slots; the right side adds the equilibrium part below
         T IW[10];
@@ -343,19 +359,29 @@ __global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> 
             for (int q = 0; q < 10; ++q) IW[q] = sm.out[side][g][q];
         }
         if (side == 0) {
+            if (!RIGHT_GRAD) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) ac[i][q] = sm.ac[g][5 * i + q];
-            T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
-            acc_grad<1>(t, ac, C.rho, mf1);
-            if (ph.smooth) {
-                axpy5(-tau * T(0.5) * dt, mf1, Fh);
-            } else {
-                axpy5(tc.q2, mf1, Fh);
-                axpy5(tc.dq2, mf1, D);
+                    for (int q = 0; q < 5; ++q) ac[i][q] = sm.ac[g][5 * i + q];
+                T mf1[5] = {T(0), T(0), T(0), T(0), T(0)};
+                acc_grad<1>(t, ac, C.rho, mf1);
+                if (ph.smooth) {
+                    axpy5(-tau * T(0.5) * dt, mf1, Fh);
+                } else {
+                    axpy5(tc.q2, mf1, Fh);
+                    axpy5(tc.dq2, mf1, D);
+                }
             }
         } else {
+            if (RIGHT_GRAD) {
+                if (ph.smooth) {
+                    axpy5(-tau * T(0.5) * dt, mf1r, Fh);
+                } else {
+                    axpy5(tc.q2, mf1r, Fh);
+                    axpy5(tc.dq2, mf1r, D);
+                }
+            }
             T mf0[5] = {0}, mf2[5], mw1[5], dtW[5];
             acc_psi<1, 0, 0>(t, C.rho, mf0);
 #pragma unroll
