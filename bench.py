@@ -235,7 +235,7 @@ def batched_leg(torch, gks, args, flush):
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
     s.init(W, dW)
     setup_s = time.perf_counter() - t0
-    tuned = s.autotune(steps=5, cache=False)
+    tuned = s.autotune(steps=5, cache=False, orders=True)
     steps = max(5, args.steps // 5)
     ms_mine = time_device(torch, s, steps, args.warmup, flush)
     ms = replicas.max_over_ranks(ms_mine)
@@ -245,6 +245,7 @@ def batched_leg(torch, gks, args, flush):
     torch.cuda.empty_cache()
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=2))
     s.init(W, dW)
+    s.set_cell_order(tuned["cell_order"])
     s.set_variant(*tuned["variant"])
     ms_ops64 = replicas.max_over_ranks(time_device(torch, s, max(3, steps // 3), min(args.warmup, 3), flush))
     del s
@@ -260,7 +261,8 @@ def batched_leg(torch, gks, args, flush):
             "scaling": "strong (cases split over ranks)" if ws > 1 else "one GPU",
             "rank0_cases": len(mine), "rank0_cells": g.nc,
             "dt_range": [float(dt.min()), float(dt.max())], "host_setup_s": setup_s,
-            "autotuned_variant": tuned["variant"], "variant_ms": tuned["ms_per_step"],
+            "autotuned_variant": tuned["variant"], "cell_order": tuned["cell_order"],
+            "ms_per_cell_order": dict(zip(("caller", "rcm", "morton"), tuned["ms_per_order"])),
             "l2": "inputs larger than L2 (plus the flush)"}
 
 
@@ -395,11 +397,13 @@ def sphere_leg(torch, gks, args, flush):
         s = gks.State(g, gks.params(precision=prec, **kw))
         s.init(W, dW)
         if prec == 1:
-            s.autotune(steps=3, cache=False)
+            tuned = s.autotune(steps=3, cache=False, orders=True)
         ms = replicas.max_over_ranks(time_device(torch, s, steps, min(args.warmup, 3), flush))
         t, _ = s.time()
         out[name] = {"ms_per_step": ms, "value": replicas.world()[0] * g.nc * 2 / (ms / 1000.0) / 1e6,
-                     "steps_timed": steps, "t": t, "variant": list(s.variant)}
+                     "steps_timed": steps, "t": t, "variant": list(s.variant), "cell_order": s.cell_order}
+        if prec == 1:
+            out[name]["ms_per_cell_order"] = dict(zip(("caller", "rcm", "morton"), tuned["ms_per_order"]))
         s.init(W, dW)
         s.step(3)
         s.sync()
@@ -569,7 +573,7 @@ def main():
     for name, prec in (("fp64", 0), ("fp32", 1), ("fp32_ops64", 2)):
         s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=prec))
         s.init(W0, dW0)
-        tuned = s.autotune(steps=10, cache=False)  # restores the state
+        tuned = s.autotune(steps=10, cache=False, orders=prec != 0)  # restores the state
         if name == "fp32":
             with ClockSampler(local) as clk:
                 ms = time_device(torch, s, args.steps, args.warmup, flush)
@@ -583,7 +587,8 @@ def main():
             s.step(1)
         s.sync()
         br = s.step_timed(max(3, args.steps // 5 if name != "fp32" else args.steps))
-        results[name] = {"ms": ms, "breakdown": br, "variant": tuned["variant"]}
+        results[name] = {"ms": ms, "breakdown": br, "variant": tuned["variant"],
+                         "cell_order": tuned.get("cell_order", 0)}
     # equal-L1 comparison at t = 0.2 (untimed)
     l1_64, W64 = l1_at(torch, gks, mesh, W0, dW0, 0, 0.2)
     l1_32, W32 = l1_at(torch, gks, mesh, W0, dW0, 1, 0.2)
@@ -593,6 +598,7 @@ def main():
 
     # end to end through the host-buffer entry point (pinned buffers, copies timed)
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    s.set_cell_order(results["fp32"]["cell_order"])
     s.set_variant(*results["fp32"]["variant"])  # the autotuned variant, as a user's cached autotune() sets it
     Wh = torch.tensor(W0).pin_memory()
     dWh = torch.tensor(dW0).pin_memory()
@@ -643,7 +649,9 @@ def main():
         "step_hbm": dict(step_hbm(value, "fp32", peaks), peak_source=peak_src,
                          note="latency-bound size: the 24,576-cell workspace fits in L2"),
         "autotuned_variant": {"fp32": results["fp32"]["variant"], "fp64": results["fp64"]["variant"],
-                              "meaning": "[face_order, flux_blocks_per_SM, slopes_pass]"},
+                              "meaning": "[face_order, flux_blocks_per_SM, slopes_pass]",
+                              "fp32_cell_order": results["fp32"]["cell_order"],
+                              "cell_orders": "0 caller's, 1 reverse Cuthill-McKee, 2 Morton"},
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32, "l1_rho_fp32_ops64": l1_32o,
                           "fp32_vs_fp64_rel": fp32_vs_fp64, "fp32_ops64_vs_fp64_rel": ops64_vs_fp64},
         "fp32_ops64": {"value": ws * nc * 2 / (results["fp32_ops64"]["ms"] / 1000.0) / 1e6,

@@ -396,6 +396,28 @@ gks_status gks_state_set_variant(gks_state* state, int32_t face_order, int32_t f
 gks_status gks_autotune(gks_state* state, int32_t steps, int32_t* face_order, int32_t* flux_blocks,
                         int32_t* slopes_pass, double* ms_per_step);
 
+/* Cell ordering of the state's device arrays (FP32-bulk states, precision 1
+ * or 2): 0 the caller's order, 1 reverse Cuthill-McKee on the face-neighbour
+ * graph, 2 Morton (Z) order of the centroids; either taken within each case,
+ * the cases staying contiguous.  An implementation choice for memory
+ * locality that the paper does not discuss; every interface still speaks the
+ * caller's cell order (states, gradients, diagnostics), and results are
+ * bit-identical across orderings (every cell and face computes the same
+ * arithmetic in the same order).  Changing the order of an initialised state
+ * carries its averages, working state and fixed state over exactly;
+ * synchronises.  GKS_E_ARG for another order, GKS_E_UNSUPPORTED for a
+ * non-zero order on an FP64 state.  The next gks_step captures a new graph. */
+gks_status gks_state_set_cell_order(gks_state* state, int32_t order);
+gks_status gks_state_get_cell_order(const gks_state* state, int32_t* order);
+
+/* gks_autotune over the cell orderings as well: for each ordering (FP64:
+ * the caller's only) times every variant, keeps the fastest ordering and
+ * variant, and restores the state.  Outputs (may be NULL): the chosen
+ * cell_order, face_order, flux_blocks, slopes_pass, and ms_per_order[3], the
+ * best step time of each ordering.  Synchronises. */
+gks_status gks_autotune_orders(gks_state* state, int32_t steps, int32_t* cell_order, int32_t* face_order,
+                               int32_t* flux_blocks, int32_t* slopes_pass, double* ms_per_order);
+
 /* ------------------------------------------------------- diagnostics -- */
 
 /* Reconstruction of the current state (Sec. 4), written to device arrays:

@@ -264,7 +264,7 @@ struct Layout {
     // mesh
     size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, fan, cell_case, perm;
     // state
-    size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage;
+    size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage, cperm, cinv;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -312,9 +312,13 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool f
     L.case_dtmin = L.add(8 * ncase);
     L.part = L.add(8 * PART_N * nblk);
     L.err = L.add(4);
-    // scratch: host-buffer staging, time-step partials, autotune snapshot
-    // (FP64 averages and the working state: 25 doubles a cell at most)
-    L.stage = L.add(8 * (25 * nc + 3 * ncase + CTRL_N + 1));
+    // scratch: host-buffer staging, time-step partials, autotune snapshot,
+    // re-ordering of the cells (FP64 averages, the working state and the
+    // fixed state: 40 doubles a cell at most)
+    L.stage = L.add(8 * (40 * nc + 3 * ncase + CTRL_N + 1));
+    // FP32 bulk: device cell -> caller's cell (the cell ordering)
+    L.cperm = fp32 ? L.add(4 * nc) : 0;
+    L.cinv = fp32 ? L.add(4 * nc) : 0;
     return L;
 }
 
@@ -340,8 +344,116 @@ struct gks_state {
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
     int slopes_pass = 0;   // 1: reconstruction step 1 as its own pass
+    // cell ordering of the device arrays (FP32 bulk): 0 the caller's, 1
+    // reverse Cuthill-McKee, 2 Morton, each within each case; cperm maps a
+    // device cell to the caller's cell, cinv back (empty: identity)
+    int cell_order = 0;
+    std::vector<int32_t> cperm, cinv;
     std::vector<int8_t> adj_rev;  // reverse face slots of the adjoint (built on first use)
+    // device copy of cperm, or NULL for the caller's order
+    const int32_t* dperm() const { return cperm.empty() ? nullptr : reinterpret_cast<const int32_t*>(ws + L.cperm); }
+    const int32_t* dinv() const { return cinv.empty() ? nullptr : reinterpret_cast<const int32_t*>(ws + L.cinv); }
+    int64_t pub(int64_t d) const { return cperm.empty() ? d : cperm[d]; }
+    int64_t dev(int64_t c) const { return cinv.empty() ? c : cinv[c]; }
 };
+
+// ---------------------------------------------------------- orderings --
+
+// Cell ordering within each case (the cases stay contiguous and in order).
+// 1: reverse Cuthill-McKee on the face-neighbour graph, breadth first from a
+// cell of least degree at the end of a few sweeps (a pseudo-peripheral
+// cell), neighbours taken by increasing degree, the order reversed;
+// 2: Morton (Z) order of the centroids, 10 bits per axis over the case's
+// bounding box.  Returns device cell -> caller's cell.
+static std::vector<int32_t> cell_permutation(const gks_mesh& g, int order) {
+    const int64_t nc = g.nc;
+    std::vector<int32_t> perm((size_t)nc);
+    for (int64_t c = 0; c < nc; ++c) perm[c] = (int32_t)c;
+    if (order == 0) return perm;
+    int64_t c0 = 0;
+    while (c0 < nc) {
+        int64_t c1 = c0;
+        while (c1 < nc && g.cell_case[c1] == g.cell_case[c0]) ++c1;
+        const int64_t n = c1 - c0;
+        if (order == 2) {
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int64_t c = c0; c < c1; ++c)
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = std::min(lo[a], g.cen[c * 3 + a]);
+                    hi[a] = std::max(hi[a], g.cen[c * 3 + a]);
+                }
+            std::vector<std::pair<uint64_t, int32_t>> key((size_t)n);
+            for (int64_t c = c0; c < c1; ++c) {
+                uint64_t code = 0;
+                uint32_t q[3];
+                for (int a = 0; a < 3; ++a) {
+                    const double t = hi[a] > lo[a] ? (g.cen[c * 3 + a] - lo[a]) / (hi[a] - lo[a]) : 0.0;
+                    q[a] = (uint32_t)std::min(1023.0, std::max(0.0, std::floor(t * 1024.0)));
+                }
+                for (int b = 9; b >= 0; --b)
+                    for (int a = 0; a < 3; ++a) code = (code << 1) | ((q[a] >> b) & 1u);
+                key[c - c0] = {code, (int32_t)c};
+            }
+            std::stable_sort(key.begin(), key.end(),
+                             [](const auto& x, const auto& y) { return x.first < y.first; });
+            for (int64_t i = 0; i < n; ++i) perm[c0 + i] = key[i].second;
+        } else {
+            auto deg = [&](int64_t c) {
+                int d = 0;
+                for (int f = 0; f < 4; ++f) d += g.nbr[c * 4 + f] >= 0;
+                return d;
+            };
+            std::vector<int64_t> level((size_t)n, -1), out;
+            out.reserve((size_t)n);
+            std::vector<char> seen((size_t)n, 0);
+            // breadth-first order from `start` over the unvisited cells of the case;
+            // returns the last cell reached (the far end of the sweep)
+            auto sweep = [&](int64_t start, bool emit) {
+                std::vector<int64_t> queue{start};
+                std::vector<char> vis((size_t)n, 0);
+                vis[start - c0] = 1;
+                int64_t last = start;
+                for (size_t h = 0; h < queue.size(); ++h) {
+                    const int64_t c = queue[h];
+                    last = c;
+                    if (emit) {
+                        out.push_back(c);
+                        seen[c - c0] = 1;
+                    }
+                    int64_t nb[4];
+                    int k = 0;
+                    for (int f = 0; f < 4; ++f) {
+                        const int64_t m = g.nbr[c * 4 + f];
+                        if (m >= c0 && m < c1 && !vis[m - c0] && !(emit && seen[m - c0])) nb[k++] = m;
+                    }
+                    std::sort(nb, nb + k, [&](int64_t a, int64_t b) {
+                        const int da = deg(a), db = deg(b);
+                        return da != db ? da < db : a < b;
+                    });
+                    for (int i = 0; i < k; ++i) {
+                        if (vis[nb[i] - c0]) continue;
+                        vis[nb[i] - c0] = 1;
+                        queue.push_back(nb[i]);
+                    }
+                }
+                return last;
+            };
+            for (int64_t s0 = c0; s0 < c1; ++s0) {
+                if (seen[s0 - c0]) continue;
+                // least-degree unvisited cell, then two sweeps to a far end
+                int64_t start = s0;
+                for (int64_t c = s0; c < c1; ++c)
+                    if (!seen[c - c0] && deg(c) < deg(start)) start = c;
+                int64_t far = start;
+                for (int it = 0; it < 2; ++it) far = sweep(far, false);
+                sweep(far, true);
+            }
+            for (int64_t i = 0; i < n; ++i) perm[c0 + i] = (int32_t)out[(size_t)(n - 1 - i)];
+        }
+        c0 = c1;
+    }
+    return perm;
+}
 
 template <typename T>
 static T* at(gks_state* s, size_t off) {
@@ -393,13 +505,14 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
 // Device face order: canonical (0) or grouped by left cell (1).  perm maps a
 // device face index to its canonical index; the cell-to-face list, the face
 // arrays and the records use device indices.
-static std::vector<int32_t> face_permutation(const gks_mesh& g, int order) {
+static std::vector<int32_t> face_permutation(const gks_mesh& g, int order, const std::vector<int32_t>& cinv) {
     std::vector<int32_t> perm((size_t)g.nf);
     for (int64_t f = 0; f < g.nf; ++f) perm[f] = (int32_t)f;
     if (order == 1) {
         auto key = [&](int32_t f) {
             const int64_t l = g.face_lr[f * 2], r = g.face_lr[f * 2 + 1];
-            return std::make_pair(l >= 0 ? l : r, (int64_t)f);
+            const int64_t c = l >= 0 ? l : r;
+            return std::make_pair(cinv.empty() ? c : (int64_t)cinv[c], (int64_t)f);
         };
         std::sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
     }
@@ -411,24 +524,26 @@ static gks_status upload_faces(gks_state* s) {
     const gks_mesh& g = *s->mesh;
     const int64_t nc = g.nc, nf = g.nf;
     const Layout& L = s->L;
-    const std::vector<int32_t> perm = face_permutation(g, s->face_order);
+    const std::vector<int32_t> perm = face_permutation(g, s->face_order, s->cinv);
     std::vector<int32_t> inv((size_t)nf);
     for (int64_t d = 0; d < nf; ++d) inv[perm[d]] = (int32_t)d;
     std::vector<int32_t> cface(4 * nc), flr(2 * nf);
     std::vector<T> fgeo(FGEO * nf, T(0));
     std::vector<float> fan(s->L.fan ? 6 * nf : 0, 0.0f);
-    for (int64_t c = 0; c < nc; ++c)
+    for (int64_t d = 0; d < nc; ++d) {
+        const int64_t c = s->pub(d);
         for (int f = 0; f < 4; ++f) {
             const int64_t fi = g.csr_face[c * 4 + f];
             const bool left = g.csr_sign[c * 4 + f] > 0;
-            cface[f * nc + c] = (int32_t)((int64_t)inv[fi] * 2 + (left ? 0 : 1));
+            cface[f * nc + d] = (int32_t)((int64_t)inv[fi] * 2 + (left ? 0 : 1));
         }
+    }
     for (int64_t d = 0; d < nf; ++d) {
         const int64_t f = perm[d];
         // a boundary face's missing side carries its kind: -1 - GKS_BC_*
         const int32_t miss = -1 - (int32_t)g.bkind[f];
-        flr[d] = g.face_lr[f * 2] >= 0 ? (int32_t)g.face_lr[f * 2] : miss;
-        flr[nf + d] = g.face_lr[f * 2 + 1] >= 0 ? (int32_t)g.face_lr[f * 2 + 1] : miss;
+        flr[d] = g.face_lr[f * 2] >= 0 ? (int32_t)s->dev(g.face_lr[f * 2]) : miss;
+        flr[nf + d] = g.face_lr[f * 2 + 1] >= 0 ? (int32_t)s->dev(g.face_lr[f * 2 + 1]) : miss;
         T* r = &fgeo[d * FGEO];
         for (int a = 0; a < 3; ++a) r[a] = (T)g.fnorm[f * 3 + a];
         r[3] = (T)(g.farea[f] / 3.0);
@@ -471,23 +586,27 @@ static gks_status upload_cells(gks_state* s) {
     // Sec. 4.4: with linear weights a boundary cell's third-order step is the
     // least-squares first-order fit to its P2 stencil
     const bool linear_boundary = !s->params.weno && s->params.order == 3;
-    for (int64_t c = 0; c < nc; ++c) {
-        TO* tc = &tile[(size_t)(c / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + c % CELLS_PER_BLOCK];
+    std::vector<int32_t> cell_case((size_t)nc);
+    // d: device cell; c: the caller's cell it holds
+    for (int64_t d = 0; d < nc; ++d) {
+        const int64_t c = s->pub(d);
+        cell_case[d] = g.cell_case[c];
+        TO* tc = &tile[(size_t)(d / CELLS_PER_BLOCK) * TILE_ROWS * CELLS_PER_BLOCK + d % CELLS_PER_BLOCK];
         auto put_row = [&](int row, double v) { tc[(size_t)row * CELLS_PER_BLOCK] = (TO)v; };
         for (int f = 0; f < 4; ++f) {
-            nbr[f * nc + c] = (int32_t)g.nbr[c * 4 + f];
+            nbr[f * nc + d] = g.nbr[c * 4 + f] >= 0 ? (int32_t)s->dev(g.nbr[c * 4 + f]) : -1;
             const int64_t fi = g.csr_face[c * 4 + f];
             const bool left = g.csr_sign[c * 4 + f] > 0;
             const double* gp = left ? &g.gp_l[fi * 9] : &g.gp_r[fi * 9];
             for (int k = 0; k < 9; ++k) put_row(TILE_G + f * 9 + k, gp[k]);
         }
-        inv_vol[c] = 1.0 / g.vol[c];
+        inv_vol[d] = 1.0 / g.vol[c];
         put_row(TILE_V23, std::pow(g.vol[c], 2.0 / 3.0));
         put_row(TILE_V43, std::pow(g.vol[c], 4.0 / 3.0));
-        dr[c] = (T)g.dr[c];
+        dr[d] = (T)g.dr[c];
         for (int q = 0; q < 6; ++q) put_row(TILE_MOM + q, g.mom2[c * 6 + q]);
         for (int k = 0; k < 12; ++k) {
-            M1[k * nc + c] = (TO)g.M1[c * 12 + k];
+            M1[k * nc + d] = (TO)g.M1[c * 12 + k];
             put_row(TILE_M1 + k, g.M1[c * 12 + k]);
         }
         const double* M2c = &g.M2[c * 144];
@@ -506,7 +625,11 @@ static gks_status upload_cells(gks_state* s) {
     GKS_CHECK_CUDA(put(L.dr, dr.data(), sizeof(T) * dr.size()));
     GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(TO) * M1.size()));
     GKS_CHECK_CUDA(put(L.tile, tile.data(), sizeof(TO) * tile.size()));
-    GKS_CHECK_CUDA(put(L.cell_case, g.cell_case.data(), 4 * g.cell_case.size()));
+    GKS_CHECK_CUDA(put(L.cell_case, cell_case.data(), 4 * cell_case.size()));
+    if (!s->cperm.empty()) {
+        GKS_CHECK_CUDA(put(L.cperm, s->cperm.data(), 4 * s->cperm.size()));
+        GKS_CHECK_CUDA(put(L.cinv, s->cinv.data(), 4 * s->cinv.size()));
+    }
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.ctrl, 0, 8 * CTRL_N, s->stream));
     GKS_CHECK_CUDA(cudaMemsetAsync(s->ws + L.err, 0, 4, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // host vectors die here
@@ -611,8 +734,11 @@ template <typename T>
 static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const double* d_W,
                             const double* d_dW) {
     const int64_t nc = m.nc;
-    GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, d_dW, st.X, nc, s->stream));
+    if (s->dperm())
+        GKS_CHECK_CUDA(launch_cells_perm(d_W, st.Wd, nc, 5, s->dperm(), 0, s->stream));
+    else
+        GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, d_W, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
+    GKS_CHECK_CUDA(Launch<T>::pack(d_W, d_dW, st.X, nc, s->stream, s->dperm()));
     if (m.fixed && !s->fixed_pinned)  // fixed boundaries hold the initial state
         GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * Stride<T>::xs * nc, cudaMemcpyDeviceToDevice,
                                        s->stream));
@@ -628,7 +754,7 @@ extern "C" gks_status gks_set_fixed_state(gks_state* s, const double* d_W, const
     order_after_caller(s);
     const int64_t nc = s->mesh->nc;
     if (s->fp32)
-        GKS_CHECK_CUDA(Launch<float>::pack(d_W, d_dW, const_cast<float*>(s->m32.fixed), nc, s->stream));
+        GKS_CHECK_CUDA(Launch<float>::pack(d_W, d_dW, const_cast<float*>(s->m32.fixed), nc, s->stream, s->dperm()));
     else
         GKS_CHECK_CUDA(Launch<double>::pack(d_W, d_dW, const_cast<double*>(s->m64.fixed), nc, s->stream));
     s->fixed_pinned = true;
@@ -813,8 +939,13 @@ extern "C" gks_status gks_sync(gks_state* s) {
 
 template <typename T>
 static gks_status get_impl(gks_state* s, DevState<T>& st, int64_t nc, double* d_W, double* d_dW) {
-    if (d_W) GKS_CHECK_CUDA(cudaMemcpyAsync(d_W, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
-    if (d_dW) GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, d_dW, nc, s->stream));
+    if (d_W) {
+        if (s->dperm())
+            GKS_CHECK_CUDA(launch_cells_perm(st.Wd, d_W, nc, 5, s->dperm(), 1, s->stream));
+        else
+            GKS_CHECK_CUDA(cudaMemcpyAsync(d_W, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if (d_dW) GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, d_dW, nc, s->stream, s->dperm()));
     return GKS_OK;
 }
 
@@ -858,9 +989,17 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
                                  double* h_dW_out) {
     const int64_t nc = m.nc;
     double* stage = at<double>(s, s->L.stage);
-    GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
-    GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
+    if (s->dperm()) {
+        // the caller's order in the staging buffer, then into device order
+        GKS_CHECK_CUDA(cudaMemcpyAsync(stage + 15 * nc, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
+        GKS_CHECK_CUDA(launch_cells_perm(stage + 15 * nc, st.Wd, nc, 5, s->dperm(), 0, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
+        GKS_CHECK_CUDA(Launch<T>::pack(stage + 15 * nc, stage, st.X, nc, s->stream, s->dperm()));
+    } else {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(st.Wd, h_W, 8 * 5 * nc, cudaMemcpyHostToDevice, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync(stage, h_dW, 8 * 15 * nc, cudaMemcpyHostToDevice, s->stream));
+        GKS_CHECK_CUDA(Launch<T>::pack(st.Wd, stage, st.X, nc, s->stream));
+    }
     if (m.fixed && !s->fixed_pinned)
         GKS_CHECK_CUDA(cudaMemcpyAsync((void*)m.fixed, st.X, sizeof(T) * Stride<T>::xs * nc, cudaMemcpyDeviceToDevice,
                                        s->stream));
@@ -869,8 +1008,13 @@ static gks_status step_host_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, c
     s->initialised = true;
     gks_status r = gks_step(s, nsteps, dt_fixed, 0.0);
     if (r != GKS_OK) return r;
-    GKS_CHECK_CUDA(cudaMemcpyAsync(h_W_out, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToHost, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, stage, nc, s->stream));
+    if (s->dperm()) {
+        GKS_CHECK_CUDA(launch_cells_perm(st.Wd, stage + 15 * nc, nc, 5, s->dperm(), 1, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync(h_W_out, stage + 15 * nc, 8 * 5 * nc, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(h_W_out, st.Wd, 8 * 5 * nc, cudaMemcpyDeviceToHost, s->stream));
+    }
+    GKS_CHECK_CUDA(Launch<T>::unpack_grad(st.X, stage, nc, s->stream, s->dperm()));
     GKS_CHECK_CUDA(cudaMemcpyAsync(h_dW_out, stage, 8 * 15 * nc, cudaMemcpyDeviceToHost, s->stream));
     return gks_sync(s);
 }
@@ -1042,10 +1186,22 @@ static gks_status debug_recon_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st,
     const bool need_b = p.weno || p.order == 2;
     const int64_t nc = m.nc;
     if (!need_b) GKS_CHECK_CUDA(cudaMemsetAsync(st.slopes, 0, sizeof(T) * 15 * nc, s->stream));
-    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.X, nullptr, need_b ? st.slopes : nullptr, st.poly, d_fallback,
+    // a reordered state writes per-cell outputs in device order to the
+    // staging buffer first, then gathers them into the caller's order
+    double* stage = at<double>(s, s->L.stage);
+    int32_t* fb = (d_fallback && s->dinv()) ? reinterpret_cast<int32_t*>(stage) : d_fallback;
+    GKS_CHECK_CUDA(Launch<T>::recon(m, p, st.X, nullptr, need_b ? st.slopes : nullptr, st.poly, fb,
                                     nullptr, st.err, s->stream));
-    if (d_poly) GKS_CHECK_CUDA(Launch<T>::poly_to_double(st.poly, d_poly, nc, s->stream));
-    if (d_slopes) GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
+    if (fb != d_fallback) GKS_CHECK_CUDA(launch_rows_gather(fb, d_fallback, nc, 1, s->dinv(), s->stream));
+    if (d_poly) GKS_CHECK_CUDA(Launch<T>::poly_to_double(st.poly, d_poly, nc, s->stream, s->dperm()));
+    if (d_slopes) {
+        if (s->dinv()) {
+            GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, stage + nc, 15 * nc, s->stream));
+            GKS_CHECK_CUDA(launch_rows_gather(stage + nc, d_slopes, nc, 30, s->dinv(), s->stream));
+        } else {
+            GKS_CHECK_CUDA(Launch<T>::to_double(st.slopes, d_slopes, 15 * nc, s->stream));
+        }
+    }
     return GKS_OK;
 }
 
@@ -1118,6 +1274,72 @@ extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, in
     return GKS_OK;
 }
 
+// Re-numbers the device cells (FP32 bulk): the mesh arrays are uploaded in
+// the new order and the per-cell state (averages, working state, fixed
+// state) is carried over by an exact gather, so the run continues unchanged.
+template <typename T>
+static gks_status reorder_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, int order) {
+    const gks_mesh& g = *s->mesh;
+    const int64_t nc = g.nc;
+    std::vector<int32_t> np = cell_permutation(g, order);  // new device cell -> caller's cell
+    std::vector<int32_t> map((size_t)nc);                  // new device cell -> old device cell
+    for (int64_t d = 0; d < nc; ++d) map[d] = (int32_t)s->dev(np[d]);
+    char* sb = s->ws + s->L.stage;
+    const size_t wd_b = 8 * 5 * (size_t)nc, x_b = sizeof(T) * Stride<T>::xs * (size_t)nc;
+    char* map_d = sb + wd_b + 2 * x_b;
+    if (s->initialised) {
+        GKS_CHECK_CUDA(cudaMemcpyAsync(sb, st.Wd, wd_b, cudaMemcpyDeviceToDevice, s->stream));
+        GKS_CHECK_CUDA(cudaMemcpyAsync(sb + wd_b, st.X, x_b, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if (m.fixed) GKS_CHECK_CUDA(cudaMemcpyAsync(sb + wd_b + x_b, m.fixed, x_b, cudaMemcpyDeviceToDevice, s->stream));
+    GKS_CHECK_CUDA(cudaMemcpyAsync(map_d, map.data(), 4 * (size_t)nc, cudaMemcpyHostToDevice, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));  // map dies with this call
+    s->cell_order = order;
+    if (order == 0) {
+        s->cperm.clear();
+        s->cinv.clear();
+    } else {
+        s->cperm = np;
+        s->cinv.assign((size_t)nc, 0);
+        for (int64_t d = 0; d < nc; ++d) s->cinv[np[d]] = (int32_t)d;
+    }
+    gks_status r = upload_mesh<T>(s);
+    if (r != GKS_OK) return r;
+    const int32_t* mp = reinterpret_cast<const int32_t*>(map_d);
+    if (s->initialised) {
+        for (int q = 0; q < 5; ++q)
+            GKS_CHECK_CUDA(launch_rows_gather(sb + q * 8 * (size_t)nc, st.Wd + q * nc, nc, 2, mp, s->stream));
+        GKS_CHECK_CUDA(launch_rows_gather(sb + wd_b, st.X, nc, (int)(sizeof(T) * Stride<T>::xs / 4), mp, s->stream));
+    }
+    if (m.fixed)
+        GKS_CHECK_CUDA(launch_rows_gather(sb + wd_b + x_b, const_cast<T*>(m.fixed), nc,
+                                          (int)(sizeof(T) * Stride<T>::xs / 4), mp, s->stream));
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_state_set_cell_order(gks_state* s, int32_t order) {
+    if (!s) { set_error("gks_state_set_cell_order: state is NULL"); return GKS_E_ARG; }
+    if (order < 0 || order > 2) { set_error("gks_state_set_cell_order: order must be 0, 1 or 2"); return GKS_E_ARG; }
+    if (order == s->cell_order) return GKS_OK;
+    if (!s->fp32) {
+        set_error("gks_state_set_cell_order: FP64 states keep the caller's cell order");
+        return GKS_E_UNSUPPORTED;
+    }
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    order_after_caller(s);
+    return reorder_impl<float>(s, s->m32, s->s32, order);
+}
+
+extern "C" gks_status gks_state_get_cell_order(const gks_state* s, int32_t* order) {
+    if (!s || !order) { set_error("gks_state_get_cell_order: NULL argument"); return GKS_E_ARG; }
+    *order = s->cell_order;
+    return GKS_OK;
+}
+
 template <typename T>
 static gks_status snapshot(gks_state* s, DevState<T>& st, bool save) {
     const int64_t nc = s->mesh->nc, nk = s->mesh->ncase;
@@ -1183,5 +1405,41 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
     if (face_order) *face_order = orders[bi];
     if (flux_blocks) *flux_blocks = blocks[bi];
     if (slopes_pass) *slopes_pass = passes[bi];
+    return gks_sync(s);
+}
+
+extern "C" gks_status gks_autotune_orders(gks_state* s, int32_t steps, int32_t* cell_order, int32_t* face_order,
+                                          int32_t* flux_blocks, int32_t* slopes_pass, double* ms_per_order) {
+    if (!s || steps < 1) { set_error("gks_autotune_orders: NULL state or steps < 1"); return GKS_E_ARG; }
+    if (!s->initialised) { set_error("gks_autotune_orders: state not initialised"); return GKS_E_STATE; }
+    const int norder = s->fp32 ? 3 : 1;
+    double best = INFINITY;
+    int bo = 0;
+    int32_t bfo = 0, bfb = 3, bsp = 0;
+    for (int o = 0; o < norder; ++o) {
+        gks_status r = gks_state_set_cell_order(s, o);
+        if (r != GKS_OK) return r;
+        int32_t fo = 0, fb = 3, sp = 0;
+        double ms[8];
+        r = gks_autotune(s, steps, &fo, &fb, &sp, ms);
+        if (r != GKS_OK) return r;
+        double m = INFINITY;
+        for (int v = 0; v < (s->fp32 ? 8 : 4); ++v) m = std::fmin(m, ms[v]);
+        if (ms_per_order) ms_per_order[o] = m;
+        if (m < best) {
+            best = m;
+            bo = o;
+            bfo = fo;
+            bfb = fb;
+            bsp = sp;
+        }
+    }
+    gks_status r = gks_state_set_cell_order(s, bo);
+    if (r == GKS_OK) r = gks_state_set_variant(s, bfo, bfb, bsp);
+    if (r != GKS_OK) return r;
+    if (cell_order) *cell_order = bo;
+    if (face_order) *face_order = bfo;
+    if (flux_blocks) *flux_blocks = bfb;
+    if (slopes_pass) *slopes_pass = bsp;
     return gks_sync(s);
 }

@@ -277,12 +277,15 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
         out[i] = (B)in[i];
 }
 
+// cperm (may be NULL): device cell -> the caller's cell of W, dW
 template <typename T>
-__global__ void k_pack(const double* __restrict__ W, const double* __restrict__ dW, T* __restrict__ X, int64_t nc) {
+__global__ void k_pack(const double* __restrict__ W, const double* __restrict__ dW, T* __restrict__ X, int64_t nc,
+                       const int32_t* __restrict__ cperm) {
     constexpr int XSR = Stride<T>::xs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * XSR; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i / XSR;
-        const int j = (int)(i - c * XSR);
+        const int64_t d = i / XSR;
+        const int64_t c = cperm ? (int64_t)cperm[d] : d;
+        const int j = (int)(i - d * XSR);
         T v = T(0);
         if (j < 5) {
             v = (T)W[j * nc + c];
@@ -297,10 +300,33 @@ __global__ void k_pack(const double* __restrict__ W, const double* __restrict__ 
 }
 
 template <typename T>
-__global__ void k_unpack_grad(const T* __restrict__ X, double* __restrict__ dW, int64_t nc) {
+__global__ void k_unpack_grad(const T* __restrict__ X, double* __restrict__ dW, int64_t nc,
+                              const int32_t* __restrict__ cperm) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 15; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / nc, c = i - j * nc;
-        dW[i] = (double)X[c * Stride<T>::xs + 5 + j];
+        const int64_t j = i / nc, d = i - j * nc;
+        dW[j * nc + (cperm ? (int64_t)cperm[d] : d)] = (double)X[d * Stride<T>::xs + 5 + j];
+    }
+}
+
+// component-major [ncomp][nc] arrays between the device cell order and the
+// caller's (cperm: device cell -> caller's cell)
+__global__ void k_cells_perm(const double* __restrict__ in, double* __restrict__ out, int64_t nc, int ncomp,
+                             const int32_t* __restrict__ cperm, int to_public) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * ncomp; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / nc, d = i - k * nc, c = cperm[d];
+        if (to_public)
+            out[k * nc + c] = in[i];
+        else
+            out[i] = in[k * nc + c];
+    }
+}
+
+// out row r = in row map[r], rows of `width` words of 4 bytes
+__global__ void k_rows_gather(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t nrows, int width,
+                              const int32_t* __restrict__ map) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows * width; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / width;
+        out[i] = in[(int64_t)map[r] * width + (i - r * width)];
     }
 }
 
@@ -336,18 +362,20 @@ __global__ void k_rec_out(const T* __restrict__ rec, const int32_t* __restrict__
 }
 
 template <typename T>
-__global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, int64_t nc) {
+__global__ void k_poly_out(const T* __restrict__ in, double* __restrict__ out, int64_t nc,
+                           const int32_t* __restrict__ cperm) {
     constexpr int PS = Stride<T>::poly;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 50; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = i / 50;
         const int k = (int)(i - c * 50);
+        const int64_t o = (cperm ? (int64_t)cperm[c] : c) * 50 + k;
         double v = (double)in[c * PS + k];
         if (sizeof(T) == 4 && k % 10 == 0) {
             // FP32 records hold R(centroid) minus the average: add the average back
             const int q = k / 10;
             v += (double)in[c * PS + PHI + q] + (double)in[c * PS + PLO + q];
         }
-        out[i] = v;
+        out[o] = v;
     }
 }
 
@@ -390,16 +418,32 @@ cudaError_t Launch<T>::init_dtmin(const DevMesh<T>& m, const HostPhys& p, const 
 static inline unsigned ew_grid(int64_t n) { return (unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192); }
 
 template <typename T>
-cudaError_t Launch<T>::pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s) {
+cudaError_t Launch<T>::pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s,
+                            const int32_t* cperm) {
     if (nc == 0) return cudaSuccess;
-    k_pack<T><<<ew_grid(nc * Stride<T>::xs), 256, 0, s>>>(W, dW, X, nc);
+    k_pack<T><<<ew_grid(nc * Stride<T>::xs), 256, 0, s>>>(W, dW, X, nc, cperm);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s) {
+cudaError_t Launch<T>::unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s, const int32_t* cperm) {
     if (nc == 0) return cudaSuccess;
-    k_unpack_grad<T><<<ew_grid(nc * 15), 256, 0, s>>>(X, dW, nc);
+    k_unpack_grad<T><<<ew_grid(nc * 15), 256, 0, s>>>(X, dW, nc, cperm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells_perm(const double* in, double* out, int64_t nc, int ncomp, const int32_t* cperm,
+                              int to_public, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_cells_perm<<<ew_grid(nc * ncomp), 256, 0, s>>>(in, out, nc, ncomp, cperm, to_public);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_gather(const void* in, void* out, int64_t nrows, int width_words, const int32_t* map,
+                               cudaStream_t s) {
+    if (nrows == 0) return cudaSuccess;
+    k_rows_gather<<<ew_grid(nrows * width_words), 256, 0, s>>>(static_cast<const uint32_t*>(in),
+                                                               static_cast<uint32_t*>(out), nrows, width_words, map);
     return cudaGetLastError();
 }
 
@@ -431,10 +475,10 @@ cudaError_t Launch<T>::rec_to_double(const T* rec, const int32_t* perm, double* 
 }
 
 template <typename T>
-cudaError_t Launch<T>::poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s) {
+cudaError_t Launch<T>::poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s, const int32_t* cperm) {
     if (nc == 0) return cudaSuccess;
     const int64_t n = nc * 50;
-    k_poly_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, nc);
+    k_poly_out<T><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(in, out, nc, cperm);
     return cudaGetLastError();
 }
 
@@ -456,13 +500,14 @@ cudaError_t launch_set_control(double* ctrl, double* case_t, double* case_dt, un
                                                 cudaStream_t);                                              \
     template cudaError_t Launch<T>::init_dtmin(const DevMesh<T>&, const HostPhys&, const T*,                \
                                                unsigned long long*, cudaStream_t);                          \
-    template cudaError_t Launch<T>::pack(const double*, const double*, T*, int64_t, cudaStream_t);          \
-    template cudaError_t Launch<T>::unpack_grad(const T*, double*, int64_t, cudaStream_t);                  \
+    template cudaError_t Launch<T>::pack(const double*, const double*, T*, int64_t, cudaStream_t,           \
+                                         const int32_t*);                                                   \
+    template cudaError_t Launch<T>::unpack_grad(const T*, double*, int64_t, cudaStream_t, const int32_t*);  \
     template cudaError_t Launch<T>::to_double(const T*, double*, int64_t, cudaStream_t);                    \
     template cudaError_t Launch<T>::from_double(const double*, T*, int64_t, cudaStream_t);                  \
     template cudaError_t Launch<T>::rec_to_double(const T*, const int32_t*, double*, int64_t, int,          \
                                                   const DevMesh<T>*, const T*, double, double, cudaStream_t); \
-    template cudaError_t Launch<T>::poly_to_double(const T*, double*, int64_t, cudaStream_t);
+    template cudaError_t Launch<T>::poly_to_double(const T*, double*, int64_t, cudaStream_t, const int32_t*);
 GKS_CELLS_INST(double)
 GKS_CELLS_INST(float)
 

@@ -132,9 +132,12 @@ struct Launch {
     static cudaError_t init_dtmin(const DevMesh<T>& m, const HostPhys& p, const T* X,
                                   unsigned long long* case_dtmin, cudaStream_t s);
     // X = [W | grad W] per cell from FP64 component-major W[5][nc], dW[15][nc]
-    static cudaError_t pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s);
-    // FP64 component-major dW[15][nc] from X
-    static cudaError_t unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s);
+    // (cperm, may be NULL: device cell -> cell of W, dW)
+    static cudaError_t pack(const double* W, const double* dW, T* X, int64_t nc, cudaStream_t s,
+                            const int32_t* cperm = nullptr);
+    // FP64 component-major dW[15][nc] from X (in the order of cperm's cells)
+    static cudaError_t unpack_grad(const T* X, double* dW, int64_t nc, cudaStream_t s,
+                                   const int32_t* cperm = nullptr);
     // conversions for diagnostics
     static cudaError_t to_double(const T* in, double* out, int64_t n, cudaStream_t s);
     static cudaError_t from_double(const double* in, T* out, int64_t n, cudaStream_t s);
@@ -147,7 +150,9 @@ struct Launch {
     static cudaError_t rec_to_double(const T* rec, const int32_t* perm, double* out, int64_t nf, int nr,
                                      const DevMesh<T>* m, const T* X, double gm1, double dt, cudaStream_t s);
     // padded reconstruction records -> compact FP64 [nc][50] in centroid-monomial form
-    static cudaError_t poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s);
+    // (rows in the order of cperm's cells)
+    static cudaError_t poly_to_double(const T* in, double* out, int64_t nc, cudaStream_t s,
+                                      const int32_t* cperm = nullptr);
 };
 
 // Local time-step limit of one cell (Sec. 5, Eq. time-step, without C_CFL):
@@ -186,6 +191,13 @@ struct AdjBuffers {
     const int8_t* rev;
     int32_t* fallback;
 };
+// [ncomp][nc] FP64 arrays between device cell order and the caller's
+// (cperm: device cell -> caller's cell; to_public 1: out[cperm[d]] = in[d])
+cudaError_t launch_cells_perm(const double* in, double* out, int64_t nc, int ncomp, const int32_t* cperm,
+                              int to_public, cudaStream_t s);
+// out row r = in row map[r] for rows of width_words 4-byte words
+cudaError_t launch_rows_gather(const void* in, void* out, int64_t nrows, int width_words, const int32_t* map,
+                               cudaStream_t s);
 // a bounded mbarrier wait that gives up (nothing completes it): sets ERR_TIMEOUT
 cudaError_t launch_wait_probe(int32_t* err, int tries, cudaStream_t s);
 

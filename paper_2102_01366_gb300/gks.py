@@ -208,6 +208,7 @@ class State:
         self.mesh = mesh
         self.params = p
         self.variant = (0, 3, 0)  # the library default: canonical faces, 3 flux blocks per SM, fused slopes
+        self.cell_order = 0  # the caller's cell order
         self.device = torch.device(device)
         nbytes = lib().gks_workspace_bytes(mesh._h, C.byref(p))
         if nbytes == 0:
@@ -340,6 +341,12 @@ class State:
         _call("gks_state_set_variant", self._h, int(face_order), int(flux_blocks), int(slopes_pass))
         self.variant = (int(face_order), int(flux_blocks), int(slopes_pass))
 
+    def set_cell_order(self, order):
+        """Device cell ordering (FP32 bulk): 0 the caller's, 1 reverse
+        Cuthill-McKee, 2 Morton; results are unchanged (gks_state_set_cell_order)."""
+        _call("gks_state_set_cell_order", self._h, int(order))
+        self.cell_order = int(order)
+
     def _tune_key(self):
         p = self.params
         name = self.torch.cuda.get_device_name(self.device)
@@ -347,16 +354,18 @@ class State:
             name, self.mesh.nc, self.mesh.nf, self.mesh.ncase, p.precision, p.weno, p.order,
             p.smooth_flux, p.viscous)
 
-    def autotune(self, steps=10, cache=None):
+    def autotune(self, steps=10, cache=None, orders=False):
         """Choose the fastest execution variant for this mesh and options by
-        timing them (gks_autotune); results are cached in a JSON file keyed by
-        GPU name, mesh size and options (``cache``: path, None for the default
-        ~/.cache/paper_2102_01366_gb300/autotune.json, False for no cache)."""
+        timing them (gks_autotune; with ``orders`` also over the cell
+        orderings, gks_autotune_orders); results are cached in a JSON file
+        keyed by GPU name, mesh size and options (``cache``: path, None for
+        the default ~/.cache/paper_2102_01366_gb300/autotune.json, False for
+        no cache)."""
         import json
         if cache is None:
             cache = os.environ.get("GKS_AUTOTUNE_CACHE", os.path.join(
                 os.path.expanduser("~"), ".cache", "paper_2102_01366_gb300", "autotune.json"))
-        key = self._tune_key()
+        key = self._tune_key() + ("|orders" if orders else "")
         table = {}
         if cache and os.path.exists(cache):
             try:
@@ -364,14 +373,26 @@ class State:
             except (OSError, ValueError):
                 table = {}
         if key in table and len(table[key].get("variant", ())) == 3:
+            if orders and "cell_order" in table[key]:
+                self.set_cell_order(table[key]["cell_order"])
             self.set_variant(*table[key]["variant"])
             return dict(table[key], cached=True)
         fo, fb, sp = C.c_int32(), C.c_int32(), C.c_int32()
-        ms = np.zeros(8)
-        _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), C.byref(sp), _np_ptr(ms))
-        nvar = 8 if self.params.precision != 0 else 4
-        self.variant = (fo.value, fb.value, sp.value)
-        res = {"variant": list(self.variant), "ms_per_step": ms[:nvar].tolist()}
+        if orders:
+            co = C.c_int32()
+            ms = np.zeros(3)
+            _call("gks_autotune_orders", self._h, int(steps), C.byref(co), C.byref(fo), C.byref(fb), C.byref(sp),
+                  _np_ptr(ms))
+            self.cell_order = co.value
+            self.variant = (fo.value, fb.value, sp.value)
+            res = {"variant": list(self.variant), "cell_order": co.value,
+                   "ms_per_order": ms[:3 if self.params.precision != 0 else 1].tolist()}
+        else:
+            ms = np.zeros(8)
+            _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), C.byref(sp), _np_ptr(ms))
+            nvar = 8 if self.params.precision != 0 else 4
+            self.variant = (fo.value, fb.value, sp.value)
+            res = {"variant": list(self.variant), "ms_per_step": ms[:nvar].tolist()}
         if cache:
             try:
                 os.makedirs(os.path.dirname(cache), exist_ok=True)

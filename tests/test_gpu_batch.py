@@ -224,3 +224,82 @@ def test_batched_workload_full_size_one_step(cuda, oracle_mod):
         assert grad < TOL[1], (k, desc[k], grad)
         worst["grad"] = max(worst["grad"], grad)
     print("batched full size, worst over 48 cases:", {k: float("%.3g" % v) for k, v in worst.items()})
+
+
+def _orderings_case(kind):
+    if kind == "batch":
+        batch, W, dW, desc, meshes = I.batch_cases(n_cases=3, n_range=(3, 5), seed=13)
+        return batch, W, dW, dict(weno=1, cfl=0.5)
+    if kind == "sod":
+        mesh, W, dW = I.sod_case(nx=16, nyz=3)
+        return mesh, W, dW, dict(weno=1, cfl=0.5)
+    # the sphere shell: non-slip wall, far field held fixed, viscous, Pr fix
+    mesh = I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08)
+    W, dW = I.sine_wave_state(mesh, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4)
+    return mesh, W, dW, dict(weno=1, cfl=0.5, viscous=1, mu=0.01, prandtl=0.72)
+
+
+@pytest.mark.parametrize("kind", ["batch", "sod", "shell"])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_cell_orderings_give_bit_identical_results(cuda, kind, precision):
+    """The device cell orderings (caller's, reverse Cuthill-McKee, Morton)
+    change memory locality only: every cell and face computes the same
+    arithmetic in the same order, so states, gradients, case times and the
+    reconstruction diagnostics are bit-identical, with either face order
+    and the separate slopes pass; and re-ordering mid-run carries the state
+    over exactly."""
+    mesh, W, dW, kw = _orderings_case(kind)
+    g = gks.Mesh(mesh)
+    ref = None
+    for order in (0, 1, 2):
+        for variant in ((0, 3, 0), (1, 3, 1)):
+            s = gks.State(g, gks.params(precision=precision, **kw))
+            s.set_cell_order(order)
+            s.set_variant(*variant)
+            s.init(W, dW)
+            s.step(3)
+            s.sync()
+            out = [x.cpu() for x in s.get()] + [cuda.tensor(s.case_times()[0])] + \
+                  [x.cpu() for x in s.debug_reconstruct()]
+            if ref is None:
+                ref = out
+            else:
+                for a, b in zip(ref, out):
+                    assert cuda.equal(a, b), (order, variant)
+    # re-order between steps: 3 steps, Morton, 3 steps, RCM, 2 steps, caller's
+    s = gks.State(g, gks.params(precision=precision, **kw))
+    s.init(W, dW)
+    s.step(3)
+    s.set_cell_order(2)
+    s.step(3)
+    s.set_cell_order(1)
+    s.step(2)
+    s.set_cell_order(0)
+    s.sync()
+    a = [x.cpu() for x in s.get()]
+    s2 = gks.State(g, gks.params(precision=precision, **kw))
+    s2.init(W, dW)
+    s2.step(8)
+    s2.sync()
+    b = [x.cpu() for x in s2.get()]
+    for x, y in zip(a, b):
+        assert cuda.equal(x, y)
+
+
+def test_autotune_over_orderings_restores_state(cuda):
+    batch, W, dW, desc, meshes = I.batch_cases(n_cases=3, n_range=(3, 5), seed=11)
+    g = gks.Mesh(batch)
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
+    s.init(W, dW)
+    s.step(2)
+    s.sync()
+    before = [x.clone() for x in s.get()]
+    res = s.autotune(steps=2, cache=False, orders=True)
+    assert res["cell_order"] in (0, 1, 2) and len(res["ms_per_order"]) == 3
+    after = s.get()
+    assert cuda.equal(before[0], after[0]) and cuda.equal(before[1], after[1])
+    # FP64 states keep the caller's order
+    s64 = gks.State(g, gks.params(weno=1, cfl=0.5, precision=0))
+    with pytest.raises(gks.GksError) as e:
+        s64.set_cell_order(1)
+    assert e.value.status == -8
