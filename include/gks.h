@@ -296,7 +296,9 @@ enum {
     GKS_K_UPDATE1 = 4, /* cell update, stage 1 */
     GKS_K_FLUX2 = 5,   /* face flux, stage 2 */
     GKS_K_UPDATE2 = 6, /* cell update, stage 2 */
-    GKS_NKERNELS = 7
+    GKS_K_STAGE1 = 7,  /* stage 1 as one launch (gks_state_set_fused) */
+    GKS_K_STAGE2 = 8,  /* stage 2 as one launch */
+    GKS_NKERNELS = 9
 };
 
 /* The same steps as gks_step, launched kernel by kernel (no graph) with a
@@ -387,12 +389,33 @@ gks_status gks_adjoint_step(gks_state* state, double dt, const double* d_W, cons
 gks_status gks_state_set_variant(gks_state* state, int32_t face_order, int32_t flux_blocks,
                                  int32_t slopes_pass);
 
+/* One launch per stage (precision 1 only): the reconstruction, the face
+ * flux and the cell update of a stage run as one persistent kernel, one
+ * block of 384 threads per SM striding over the blocks of cells and faces,
+ * the three phases separated by grid-wide barriers (a cooperative launch,
+ * so that every block is resident).  The same per-cell and per-face source
+ * as the separate kernels; the compiler may contract or reorder a few FP32
+ * operations differently in the one kernel, so results agree with the
+ * separate kernels to FP32 rounding (not to the bit); flux_blocks and
+ * slopes_pass do not apply.  Each barrier wait is
+ * bounded: one that gives up makes the next synchronisation return
+ * GKS_E_TIMEOUT.  GKS_E_ARG for another value, or for 1 on a state of
+ * another precision.  The next gks_step captures a new graph. */
+gks_status gks_state_set_fused(gks_state* state, int32_t fused);
+gks_status gks_state_get_fused(const gks_state* state, int32_t* fused);
+
+/* Number of execution variants gks_autotune times (entries of ms_per_step). */
+enum { GKS_NVARIANTS = 10 };
+
 /* Times every variant for `steps` steps on this state's own mesh and data,
  * keeps the fastest, and restores the state (averages, gradients, case times)
  * to what it was before the call.  Outputs (may be NULL): the chosen
- * face_order, flux_blocks and slopes_pass, and ms_per_step[8] of variant
- * v = face_order + 2 slopes_pass + 4 (3 - flux_blocks) (the first 4 entries
- * only in FP64, whose flux has one form).  Synchronises. */
+ * face_order, flux_blocks and slopes_pass (the fused choice is read back by
+ * gks_state_get_fused), and ms_per_step[GKS_NVARIANTS]: for v < 8 variant
+ * v = face_order + 2 slopes_pass + 4 (3 - flux_blocks) with separate
+ * kernels (the first 4 entries only in FP64, whose flux has one form); for
+ * v = 8, 9 one launch per stage with face_order v - 8 (precision 1 only);
+ * NaN for variants not timed.  Synchronises. */
 gks_status gks_autotune(gks_state* state, int32_t steps, int32_t* face_order, int32_t* flux_blocks,
                         int32_t* slopes_pass, double* ms_per_step);
 
@@ -412,9 +435,9 @@ gks_status gks_state_get_cell_order(const gks_state* state, int32_t* order);
 
 /* gks_autotune over the cell orderings as well: for each ordering (FP64:
  * the caller's only) times every variant, keeps the fastest ordering and
- * variant, and restores the state.  Outputs (may be NULL): the chosen
- * cell_order, face_order, flux_blocks, slopes_pass, and ms_per_order[3], the
- * best step time of each ordering.  Synchronises. */
+ * variant (the fused choice included), and restores the state.  Outputs
+ * (may be NULL): the chosen cell_order, face_order, flux_blocks, slopes_pass,
+ * and ms_per_order[3], the best step time of each ordering.  Synchronises. */
 gks_status gks_autotune_orders(gks_state* state, int32_t steps, int32_t* cell_order, int32_t* face_order,
                                int32_t* flux_blocks, int32_t* slopes_pass, double* ms_per_order);
 

@@ -17,12 +17,14 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgks.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-# The reconstruction and flux kernels take FP32 division and square root from
-# the hardware approximations (within 2 ulp) and flush FP32 denormals: these
-# flags touch single precision only, so the FP64 path is unchanged, and the
-# FP32-bulk path stays inside its tolerance against the FP64 oracle.
-FAST_FP32 = {"gks_recon.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
-             "gks_flux.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+# The reconstruction and flux kernels (and the one-launch stage that inlines
+# them) take FP32 division and square root from the hardware approximations
+# (within 2 ulp) and flush FP32 denormals: these flags touch single precision
+# only, so the FP64 path is unchanged, and the FP32-bulk path stays inside its
+# tolerance against the FP64 oracle.  The cell-update kernels keep IEEE FP32
+# arithmetic.
+FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+FAST_UNITS = ("gks_recon.cu", "gks_flux.cu", "gks_stage.cu")
 
 
 def _cuda_home():
@@ -64,7 +66,8 @@ def build(force=False, verbose=False):
     for src in cu:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
-        jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17"] + FAST_FP32.get(os.path.basename(src), []) +
+        jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17"] +
+                    (FAST_FP32 if os.path.basename(src) in FAST_UNITS else []) +
                     ["-Xcompiler", "-fPIC",
                      "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-c", src, "-o", obj])

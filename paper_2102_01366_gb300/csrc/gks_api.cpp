@@ -264,7 +264,8 @@ struct Layout {
     // mesh
     size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, fan, cell_case, perm;
     // state
-    size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage, cperm, cinv;
+    size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage, cperm, cinv,
+        gbar;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -312,6 +313,7 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool f
     L.case_dtmin = L.add(8 * ncase);
     L.part = L.add(8 * PART_N * nblk);
     L.err = L.add(4);
+    L.gbar = L.add(2 * sizeof(unsigned));  // grid-barrier words of the one-launch stage
     // scratch: host-buffer staging, time-step partials, autotune snapshot,
     // re-ordering of the cells (FP64 averages, the working state and the
     // fixed state: 40 doubles a cell at most)
@@ -344,6 +346,7 @@ struct gks_state {
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
     int slopes_pass = 0;   // 1: reconstruction step 1 as its own pass
+    int fused = 0;         // 1: each stage as one persistent launch (precision 1 only)
     // cell ordering of the device arrays (FP32 bulk): 0 the caller's, 1
     // reverse Cuthill-McKee, 2 Morton, each within each case; cperm maps a
     // device cell to the caller's cell, cinv back (empty: identity)
@@ -796,6 +799,13 @@ static cudaError_t enqueue_step(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     cudaStream_t q = s->stream;
     const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
     cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (s->fused) {
+            unsigned* gbar = reinterpret_cast<unsigned*>(s->ws + s->L.gbar);
+            if ((e = launch_stage(m, p, st, 1, &fin, gbar, q)) != cudaSuccess) return e;
+            return launch_stage(m, p, st, 2, nullptr, gbar, q);
+        }
+    }
     for (int stage = 1; stage <= 2; ++stage) {
         // stage 1 from (W^n, grad W^n), stage 2 from (W*, grad W*)
         const T* X = stage == 1 ? st.X : st.Xs;
@@ -871,7 +881,15 @@ static gks_status step_timed_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, 
         cudaError_t e = cudaEventRecord(ev[ne], q);
         kid[ne++] = -1;
         const typename Launch<T>::Finalize fin{st.case_dtmin, st.case_t, st.case_dt, m.ncase, p.cfl, st.ctrl};
-        for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+        const bool fused = sizeof(T) == 4 && s->fused;
+        if constexpr (sizeof(T) == 4) {
+            unsigned* gbar = reinterpret_cast<unsigned*>(s->ws + s->L.gbar);
+            for (int stage = 1; stage <= 2 && fused && e == cudaSuccess; ++stage) {
+                e = launch_stage(m, p, st, stage, stage == 1 ? &fin : nullptr, gbar, q);
+                if (e == cudaSuccess) e = mark(stage == 1 ? GKS_K_STAGE1 : GKS_K_STAGE2);
+            }
+        }
+        for (int stage = 1; stage <= 2 && !fused && e == cudaSuccess; ++stage) {
             const T* X = stage == 1 ? st.X : st.Xs;
             const typename Launch<T>::Finalize* f = stage == 1 ? &fin : nullptr;
             if (s->slopes_pass && p.weno) {
@@ -927,7 +945,7 @@ extern "C" gks_status gks_sync(gks_state* s) {
     GKS_CHECK_CUDA(cudaMemcpyAsync(&err, s->fp32 ? s->s32.err : s->s64.err, 4, cudaMemcpyDeviceToHost, s->stream));
     GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
     if (err & ERR_TIMEOUT) {
-        set_error("a bounded device wait (reconstruction tile copy) gave up");
+        set_error("a bounded device wait (reconstruction tile copy or grid barrier) gave up");
         return GKS_E_TIMEOUT;
     }
     if (err & ERR_STATE) {
@@ -1274,6 +1292,27 @@ extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, in
     return GKS_OK;
 }
 
+extern "C" gks_status gks_state_set_fused(gks_state* s, int32_t fused) {
+    if (!s) { set_error("gks_state_set_fused: state is NULL"); return GKS_E_ARG; }
+    if (fused != 0 && fused != 1) { set_error("gks_state_set_fused: fused must be 0 or 1"); return GKS_E_ARG; }
+    if (fused && !(s->fp32 && !s->ops64)) {
+        set_error("gks_state_set_fused: the one-launch stage exists for precision 1 only");
+        return GKS_E_ARG;
+    }
+    if (fused != s->fused && s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->fused = fused;
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_state_get_fused(const gks_state* s, int32_t* fused) {
+    if (!s || !fused) { set_error("gks_state_get_fused: NULL argument"); return GKS_E_ARG; }
+    *fused = s->fused;
+    return GKS_OK;
+}
+
 // Re-numbers the device cells (FP32 bulk): the mesh arrays are uploaded in
 // the new order and the per-cell state (averages, working state, fixed
 // state) is carried over by an exact gather, so the run continues unchanged.
@@ -1365,14 +1404,19 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
                                    int32_t* slopes_pass, double* ms_per_step) {
     if (!s || steps < 1) { set_error("gks_autotune: NULL state or steps < 1"); return GKS_E_ARG; }
     if (!s->initialised) { set_error("gks_autotune: state not initialised"); return GKS_E_STATE; }
-    // variant v: face order v & 1, slopes pass (v >> 1) & 1, flux blocks 3 - (v >> 2)
-    int orders[8], passes[8], blocks[8];
-    for (int v = 0; v < 8; ++v) {
+    // variant v < 8: face order v & 1, slopes pass (v >> 1) & 1, flux blocks
+    // 3 - (v >> 2); v = 8, 9: each stage as one launch, face order v & 1
+    int orders[GKS_NVARIANTS], passes[GKS_NVARIANTS], blocks[GKS_NVARIANTS], fused[GKS_NVARIANTS];
+    for (int v = 0; v < GKS_NVARIANTS; ++v) {
         orders[v] = v & 1;
-        passes[v] = (v >> 1) & 1;
-        blocks[v] = 3 - (v >> 2);
+        passes[v] = v < 8 ? (v >> 1) & 1 : 0;
+        blocks[v] = v < 8 ? 3 - (v >> 2) : 3;
+        fused[v] = v >= 8;
     }
+    const bool can_fuse = s->fp32 && !s->ops64;
     const int nvar = s->fp32 ? 8 : 4;  // the FP64 flux has a single variant
+    if (ms_per_step)
+        for (int v = 0; v < GKS_NVARIANTS; ++v) ms_per_step[v] = NAN;
     gks_status r = s->fp32 ? snapshot<float>(s, s->s32, true) : snapshot<double>(s, s->s64, true);
     if (r != GKS_OK) return r;
     double best = INFINITY;
@@ -1380,8 +1424,10 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
     cudaEvent_t e0, e1;
     GKS_CHECK_CUDA(cudaEventCreate(&e0));
     GKS_CHECK_CUDA(cudaEventCreate(&e1));
-    for (int v = 0; v < nvar && r == GKS_OK; ++v) {
+    for (int v = 0; v < GKS_NVARIANTS && r == GKS_OK; ++v) {
+        if (v >= nvar && !(fused[v] && can_fuse)) continue;
         r = gks_state_set_variant(s, orders[v], blocks[v], passes[v]);
+        if (r == GKS_OK && s->fp32 && !s->ops64) r = gks_state_set_fused(s, fused[v]);
         if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
         if (r == GKS_OK) r = gks_step(s, 1, 0.0, 0.0);  // graph capture + warm-up
         if (r != GKS_OK) break;
@@ -1399,6 +1445,7 @@ extern "C" gks_status gks_autotune(gks_state* s, int32_t steps, int32_t* face_or
     cudaEventDestroy(e1);
     if (r != GKS_OK) return r;
     r = gks_state_set_variant(s, orders[bi], blocks[bi], passes[bi]);
+    if (r == GKS_OK && can_fuse) r = gks_state_set_fused(s, fused[bi]);
     if (r == GKS_OK) r = s->fp32 ? snapshot<float>(s, s->s32, false) : snapshot<double>(s, s->s64, false);
     if (r != GKS_OK) return r;
     GKS_CHECK_CUDA(cudaMemsetAsync(s->fp32 ? (void*)s->s32.err : (void*)s->s64.err, 0, 4, s->stream));
@@ -1415,16 +1462,16 @@ extern "C" gks_status gks_autotune_orders(gks_state* s, int32_t steps, int32_t* 
     const int norder = s->fp32 ? 3 : 1;
     double best = INFINITY;
     int bo = 0;
-    int32_t bfo = 0, bfb = 3, bsp = 0;
+    int32_t bfo = 0, bfb = 3, bsp = 0, bfu = 0;
     for (int o = 0; o < norder; ++o) {
         gks_status r = gks_state_set_cell_order(s, o);
         if (r != GKS_OK) return r;
         int32_t fo = 0, fb = 3, sp = 0;
-        double ms[8];
+        double ms[GKS_NVARIANTS];
         r = gks_autotune(s, steps, &fo, &fb, &sp, ms);
         if (r != GKS_OK) return r;
         double m = INFINITY;
-        for (int v = 0; v < (s->fp32 ? 8 : 4); ++v) m = std::fmin(m, ms[v]);
+        for (int v = 0; v < GKS_NVARIANTS; ++v) m = std::fmin(m, ms[v]);  // fmin skips the untried (NaN)
         if (ms_per_order) ms_per_order[o] = m;
         if (m < best) {
             best = m;
@@ -1432,10 +1479,12 @@ extern "C" gks_status gks_autotune_orders(gks_state* s, int32_t steps, int32_t* 
             bfo = fo;
             bfb = fb;
             bsp = sp;
+            bfu = s->fused;
         }
     }
     gks_status r = gks_state_set_cell_order(s, bo);
     if (r == GKS_OK) r = gks_state_set_variant(s, bfo, bfb, bsp);
+    if (r == GKS_OK && s->fp32 && !s->ops64) r = gks_state_set_fused(s, bfu);
     if (r != GKS_OK) return r;
     if (cell_order) *cell_order = bo;
     if (face_order) *face_order = bfo;

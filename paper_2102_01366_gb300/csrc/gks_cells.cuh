@@ -8,6 +8,28 @@
 
 namespace gks {
 
+// a barrier of `count` threads on named barrier `id` (0: the whole block)
+__device__ __forceinline__ void group_barrier(int id, int count) {
+    if (id == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// A group of CELL_THREADS threads on one block of cells: the block index
+// vb, the thread's index tid in the group, the group's barrier (named id,
+// 0 the whole thread block) and its slice of shared memory for the block
+// reductions.
+struct CellGroup {
+    int64_t vb;
+    int tid;
+    int bar_id;
+    double* sv;   // [CELLS_PER_BLOCK]
+    int32_t* sc;  // [CELLS_PER_BLOCK]
+    double* red;  // [CELL_THREADS / 32][6]
+    __device__ __forceinline__ void sync() const { group_barrier(bar_id, CELL_THREADS); }
+};
+
 // 5 lanes per cell (one per conservative component), 6 cells per warp (lanes
 // 30, 31 idle), CELLS_PER_BLOCK cells per 128-thread block
 struct CellLane {
@@ -17,18 +39,22 @@ struct CellLane {
     bool active;  // lane carries a real (cell, component)
 };
 
-__device__ __forceinline__ CellLane cell_lane(int64_t nc) {
+// vb: the block of CELLS_PER_BLOCK cells, tid: the thread within its
+// CELL_THREADS (defaults: the launch's own block and thread)
+__device__ __forceinline__ CellLane cell_lane(int64_t nc, int64_t vb, int tid) {
     CellLane L;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
     const int cl = lane / 5;
     L.q = lane - 5 * cl;
     L.base = lane - L.q;
-    const int64_t c = (int64_t)blockIdx.x * CELLS_PER_BLOCK + warp * 6 + cl;
+    const int64_t c = vb * CELLS_PER_BLOCK + warp * 6 + cl;
     L.active = lane < 30 && c < nc;
     L.c = c < nc ? c : nc - 1;
     return L;
 }
+
+__device__ __forceinline__ CellLane cell_lane(int64_t nc) { return cell_lane(nc, blockIdx.x, threadIdx.x); }
 
 
 static inline unsigned cell_grid(int64_t nc) { return (unsigned)((nc + CELLS_PER_BLOCK - 1) / CELLS_PER_BLOCK); }

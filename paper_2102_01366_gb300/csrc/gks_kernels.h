@@ -198,6 +198,12 @@ cudaError_t launch_cells_perm(const double* in, double* out, int64_t nc, int nco
 // out row r = in row map[r] for rows of width_words 4-byte words
 cudaError_t launch_rows_gather(const void* in, void* out, int64_t nrows, int width_words, const int32_t* map,
                                cudaStream_t s);
+// one stage of the FP32-bulk step (reconstruction with the neighbours'
+// slopes recomputed, face flux, cell update) as one persistent launch with
+// grid-wide barriers; gbar: 2 unsigned words of device scratch (reset by the
+// launch); fin (stage 1, may be NULL) as for the reconstruction
+cudaError_t launch_stage(const DevMesh<float>& m, const HostPhys& p, const DevState<float>& st, int stage,
+                         const Launch<float>::Finalize* fin, unsigned* gbar, cudaStream_t s);
 // a bounded mbarrier wait that gives up (nothing completes it): sets ERR_TIMEOUT
 cudaError_t launch_wait_probe(int32_t* err, int tries, cudaStream_t s);
 

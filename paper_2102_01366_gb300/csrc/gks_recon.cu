@@ -10,120 +10,9 @@
 // the local time-step limits into each case's step (Sec. 5).
 #include <cuda_runtime.h>
 
-#include "gks_cells.cuh"
-#include "gks_device.cuh"
-#include "gks_kernels.h"
+#include "gks_recon.cuh"
 
 namespace gks {
-
-// ---- bulk copy global -> shared with an mbarrier (sm_90+ async proxy) ----
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// one arrival that also announces the bytes the copy will deliver
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// dst, src 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// bounded wait for phase `parity`: false if it gave up (each try_wait
-// already suspends for a while, so the bound is far beyond any copy time)
-constexpr int MBAR_TRIES = 1 << 16;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int i = 0; i < MBAR_TRIES; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-template <typename T>
-struct ReconConst {
-    T gm1, eps;
-    int weno, order;
-};
-
-
-// The step of every case from its minimum local limit (time-step rule of
-// Sec. 5), with dt_fixed and t_end clipping; advances the case times and
-// resets the minima for the next update.  One thread per case.
-__device__ void finalize_cases(unsigned long long* __restrict__ dtmin, double* __restrict__ case_t,
-                               double* __restrict__ case_dt, int32_t ncase, double cfl,
-                               const double* __restrict__ ctrl) {
-    const double dt_fixed = ctrl[CTRL_DT_FIXED], t_end = ctrl[CTRL_T_END];
-    for (int k = threadIdx.x; k < ncase; k += blockDim.x) {
-        const double mn = __longlong_as_double((long long)dtmin[k]);
-        double dt = dt_fixed > 0.0 ? dt_fixed : (mn < INFINITY ? cfl * mn : 0.0);
-        double t = case_t[k];
-        if (t_end > 0.0) {
-            const double rem = t_end - t;
-            if (rem <= 1e-12 * t_end) {
-                dt = 0.0;
-                if (rem > 0.0) t = t_end;
-            } else if (dt > rem) {
-                dt = rem;
-            }
-        }
-        if (!(dt > 0.0)) dt = 0.0;
-        case_dt[k] = dt;
-        case_t[k] = t + dt;
-        dtmin[k] = (unsigned long long)__double_as_longlong(INFINITY);
-    }
-}
-
-template <typename T>
-struct FinArg {
-    unsigned long long* dtmin;
-    double* case_t;
-    double* case_dt;
-    int32_t ncase;
-    double cfl;
-    const double* ctrl;
-};
-// Q_a - Q_b of component q of two cell averages: in FP32 bulk from the hi
-// and lo parts (exact to the rounding of the difference itself)
-template <typename T, typename TO = T>
-__device__ __forceinline__ TO avg_diff(const T* __restrict__ X, int64_t a, int64_t b, int q) {
-    constexpr int XSR = Stride<T>::xs;
-    if constexpr (sizeof(T) == 4)
-        return ((TO)X[a * XSR + q] - (TO)X[b * XSR + q]) + ((TO)X[a * XSR + XLO + q] - (TO)X[b * XSR + XLO + q]);
-    else
-        return X[a * XSR + q] - X[b * XSR + q];
-}
-
-// the step-1 operator entry M1[row][c] in the operator precision TO
-template <typename T, typename TO>
-__device__ __forceinline__ TO m1_at(const DevMesh<T>& m, int row, int64_t c) {
-    if constexpr (sizeof(TO) > sizeof(T))
-        return m.M1d[row * m.nc + c];
-    else
-        return m.M1[row * m.nc + c];
-}
 
 // reconstruction step 1: P1 slopes b = M1 (Q_nb - Q_0), Sec. 4.3, the
 // products in the operator precision TO
@@ -151,33 +40,6 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
     out[2] = (T)b2;
 }
 
-// P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
-// b = M1 (Q_nb - Q_x) over the existing neighbours
-template <typename T, typename TO>
-__device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ X, int64_t x, int q, T* b) {
-    const int64_t nc = m.nc;
-    TO s[3] = {TO(0), TO(0), TO(0)};
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int nb = m.nbr[f * nc + x];
-        if (nb < 0) continue;
-        const TO dq = avg_diff<T, TO>(X, nb, x, q);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) s[i] += m1_at<T, TO>(m, i * 4 + f, x) * dq;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) b[i] = (T)s[i];
-}
-
-// reconstruction (Sec. 4.1-4.3): the cell's own P1 slopes and, for the
-// two-step beta_0, its neighbours' P1 slopes (recomputed here, or read from
-// a slopes pass); P2 = M2 d with the block's static data (M2, Gauss points,
-// M1, moments) brought into shared memory by one bulk copy that overlaps the
-// neighbour gathers;
-// smoothness indicators, nonlinear weights, positivity at the cell's 12 face
-// Gauss points (Sec. 4.2); R written about the centroid in monomial form.
-// TO is the precision of the stencil operators and of their products
-// (FP32 bulk: FP32, or FP64 with precision 2; the FP64 path: FP64).
 template <typename T, typename TO>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
                                                          const T* __restrict__ X,
@@ -188,195 +50,10 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
                                                          FinArg<T> fin, int32_t* __restrict__ err) {
     __shared__ alignas(128) TO sT[TILE_ROWS][CELLS_PER_BLOCK];
     __shared__ alignas(8) unsigned long long bar;
-    constexpr unsigned TILE_BYTES = TILE_ROWS * CELLS_PER_BLOCK * sizeof(TO);
-    static_assert(TILE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
-    const TO* tile = nullptr;
-    if constexpr (sizeof(TO) > sizeof(T))
-        tile = m.tiled;
-    else
-        tile = m.tile;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();  // the barrier exists before anyone waits on it
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, TILE_BYTES);
-        bulk_load(&sT[0][0], tile + (int64_t)blockIdx.x * TILE_ROWS * CELLS_PER_BLOCK, TILE_BYTES, &bar);
-    }
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
-    const int64_t nc = m.nc;
-    const CellLane cl = cell_lane(nc);
-    const int64_t c = cl.c;
-    const int q = cl.q;
-    const int lc = (int)(c - (int64_t)blockIdx.x * CELLS_PER_BLOCK) < CELLS_PER_BLOCK
-                       ? (int)(c - (int64_t)blockIdx.x * CELLS_PER_BLOCK)
-                       : CELLS_PER_BLOCK - 1;
-    int nb[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) nb[f] = m.nbr[f * nc + c];
-    constexpr int XSR = Stride<T>::xs;
-    const T Q0 = X[c * XSR + q];
-    T Q0lo = T(0);  // lo part of the FP32 pair (FP64: unused)
-    if constexpr (sizeof(T) == 4) Q0lo = X[c * XSR + XLO + q];
-
-    // data vector [dQ_f (4); grad Q_{f,l} (12)] of this component
-    TO d[16];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const bool ok = nb[f] >= 0;
-        const T* xn = X + (ok ? (int64_t)nb[f] : c) * XSR;
-        if constexpr (sizeof(T) == 4)
-            d[f] = ok ? ((TO)xn[q] - (TO)Q0) + ((TO)xn[XLO + q] - (TO)Q0lo) : TO(0);
-        else
-            d[f] = ok ? xn[q] - Q0 : T(0);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) d[4 + 3 * f + l] = ok ? (TO)xn[5 + 3 * q + l] : TO(0);
-    }
-    // the tile has landed (all threads wait; a give-up is reported, and the
-    // values computed from an incomplete tile are never trusted by the host)
-    const bool tile_ok = mbar_wait(&bar, 0);
-    if (!tile_ok && (threadIdx.x & 31) == 0) atomicOr(err, ERR_TIMEOUT);
-    // P2 in the zero-mean basis of Eq. base: a = M2 d
-    T a[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        TO acc = TO(0);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc += sT[TILE_M2 + k * 16 + j][lc] * d[j];
-        a[k] = (T)acc;
-    }
-    const T Mxx = (T)sT[TILE_MOM + 0][lc], Mxy = (T)sT[TILE_MOM + 1][lc], Mxz = (T)sT[TILE_MOM + 2][lc];
-    const T Myy = (T)sT[TILE_MOM + 3][lc], Myz = (T)sT[TILE_MOM + 4][lc], Mzz = (T)sT[TILE_MOM + 5][lc];
-
-    const T g22 = T(100.0 / 111.0), g12 = T(10.0 / 111.0), g02 = T(1.0 / 111.0);
-    const T g11 = T(10.0 / 11.0), g01 = T(1.0 / 11.0);
-    T R[9];
-    T b[3] = {T(0), T(0), T(0)};
-    if (rc.weno || rc.order == 2) {
-        // own P1 slope from the neighbour differences already loaded
-        TO bo[3] = {TO(0), TO(0), TO(0)};
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (nb[f] < 0) continue;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) bo[i] += sT[TILE_M1 + i * 4 + f][lc] * d[f];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) b[i] = (T)bo[i];
-        if (slopes_out && cl.active) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) slopes_out[c * 15 + 3 * q + i] = b[i];
-        }
-    }
-    if (!rc.weno) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = rc.order == 2 ? (k < 3 ? b[k] : T(0)) : a[k];
-    } else {
-        const T v23 = (T)sT[TILE_V23][lc], v43 = (T)sT[TILE_V43][lc];
-        // smoothness indicators, Eq. smooth-indicator
-        const T beta1 = v23 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-        // two-step beta_0 from the neighbours' P1 slopes, Eq. p0-non-linear-weight
-        T b0j[4];
-        int nn = 0;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (nb[f] < 0) continue;
-            T bj[3];
-            if (slopes_in) {
-                const T* sj = slopes_in + (int64_t)nb[f] * 15 + 3 * q;
-                bj[0] = sj[0];
-                bj[1] = sj[1];
-                bj[2] = sj[2];
-            } else {
-                p1_slope<T, TO>(m, X, nb[f], q, bj);
-            }
-            b0j[nn++] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
-        }
-        T beta0 = T(0);
-        if (nn > 0) {
-            T sum = T(0);
-            int npair = 0;
-            for (int j = 0; j < nn; ++j)
-                for (int k = 0; k < j; ++k) {
-                    sum += d_abs(b0j[j] - b0j[k]);
-                    ++npair;
-                }
-            const T s1 = npair ? pow43(sum / T(npair)) : T(0);
-            T ws = T(0), acc = T(0);
-            for (int j = 0; j < nn; ++j) {
-                const T w1 = T(1) + s1 / (rc.eps + b0j[j]);
-                ws += w1;
-                acc += w1 * b0j[j];
-            }
-            beta0 = acc / ws;
-        }
-        if (rc.order == 2) {
-            const T sigma = pow43(d_abs(beta1 - beta0));
-            const T r0 = sigma / (rc.eps + beta0), r1 = sigma / (rc.eps + beta1);
-            const T w0 = g01 * (T(1) + r0 * r0), w1 = g11 * (T(1) + r1 * r1);
-            const T cl1 = (w1 / (w0 + w1)) / g11;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) R[k] = k < 3 ? cl1 * b[k] : T(0);
-        } else {
-            // Hessian rows of P2 and the integrals of its derivatives
-            const T H[3][3] = {{T(2) * a[3], a[4], a[5]}, {a[4], T(2) * a[6], a[7]}, {a[5], a[7], T(2) * a[8]}};
-            T first = T(0);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                const T h0 = H[l][0], h1 = H[l][1], h2 = H[l][2];
-                const T hMh = h0 * (Mxx * h0 + Mxy * h1 + Mxz * h2) + h1 * (Mxy * h0 + Myy * h1 + Myz * h2) +
-                              h2 * (Mxz * h0 + Myz * h1 + Mzz * h2);
-                first += a[l] * a[l] + hMh;
-            }
-            const T second = H[0][0] * H[0][0] + a[4] * a[4] + a[5] * a[5] + H[1][1] * H[1][1] + a[7] * a[7] +
-                             H[2][2] * H[2][2];
-            const T beta2 = v23 * first + v43 * second;
-            // global smoothness indicator and nonlinear weights, Eq. non-linear-weight
-            const T sigma = pow43(T(0.5) * (d_abs(beta2 - beta1) + d_abs(beta2 - beta0)));
-            const T r0 = sigma / (rc.eps + beta0), r1 = sigma / (rc.eps + beta1), r2 = sigma / (rc.eps + beta2);
-            const T w0 = g02 * (T(1) + r0 * r0), w1 = g12 * (T(1) + r1 * r1), w2 = g22 * (T(1) + r2 * r2);
-            const T iw = T(1) / (w0 + w1 + w2);
-            const T c2 = (w2 * iw) / g22;
-            const T cb = (w1 * iw) / g11 - c2 * g12 / g11;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) R[k] = c2 * a[k] + (k < 3 ? cb * b[k] : T(0));
-        }
-    }
-    // constant of the monomial form, less the cell average: R(centroid) - Q0
-    const T dc = (T)(-((TO)R[3] * sT[TILE_MOM + 0][lc] + (TO)R[4] * sT[TILE_MOM + 1][lc] +
-                       (TO)R[5] * sT[TILE_MOM + 2][lc] + (TO)R[6] * sT[TILE_MOM + 3][lc] +
-                       (TO)R[7] * sT[TILE_MOM + 4][lc] + (TO)R[8] * sT[TILE_MOM + 5][lc]));
-    const T c0 = Q0 + dc;
-    // positivity: the 5 lanes of the cell exchange their values at each point
-    bool bad = false;
-#pragma unroll 4
-    for (int g = 0; g < 12; ++g) {
-        const T gx = (T)sT[TILE_G + g * 3 + 0][lc];
-        const T gy = (T)sT[TILE_G + g * 3 + 1][lc];
-        const T gz = (T)sT[TILE_G + g * 3 + 2][lc];
-        const T v = c0 + R[0] * gx + R[1] * gy + R[2] * gz + R[3] * gx * gx + R[4] * gx * gy + R[5] * gx * gz +
-                    R[6] * gy * gy + R[7] * gy * gz + R[8] * gz * gz;
-        const T rho = __shfl_sync(0xffffffffu, v, cl.base + 0);
-        const T m1 = __shfl_sync(0xffffffffu, v, cl.base + 1);
-        const T m2 = __shfl_sync(0xffffffffu, v, cl.base + 2);
-        const T m3 = __shfl_sync(0xffffffffu, v, cl.base + 3);
-        const T en = __shfl_sync(0xffffffffu, v, cl.base + 4);
-        const T pr = rc.gm1 * (en - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) / rho);
-        if (!(rho > T(0)) || !(pr > T(0))) bad = true;
-    }
-    if (!tile_ok) mbar_wait(&bar, 0);  // a late copy lands before the block exits
-    if (!cl.active) return;
-    T* rec = poly + c * Stride<T>::poly;
-    T* out = rec + q * 10;
-    if constexpr (sizeof(T) == 4) {
-        // FP32: R(centroid) - Q0 and the average's hi / lo parts
-        out[0] = bad ? T(0) : dc;
-        rec[PHI + q] = Q0;
-        rec[PLO + q] = Q0lo;
-    } else {
-        out[0] = bad ? Q0 : c0;
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) out[1 + k] = bad ? T(0) : R[k];
-    if (fallback && q == 0) fallback[c] = bad ? 1 : 0;
+    recon_cells<T, TO>(m, rc, X, slopes_in, slopes_out, poly, fallback, err, blockIdx.x, threadIdx.x, sT, &bar, 0);
 }
 
 // --------------------------------------------------------------------------

@@ -91,6 +91,8 @@ def lib():
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
         "gks_debug_wait_timeout": (C.c_int32, [_vp, C.c_int32]),
         "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+        "gks_state_set_fused": (C.c_int32, [_vp, C.c_int32]),
+        "gks_state_get_fused": (C.c_int32, [_vp, _vp]),
         "gks_autotune": (C.c_int32, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32), _vp]),
     }
@@ -263,7 +265,7 @@ class State:
         _call("gks_get_time", self._h, C.byref(tt), C.byref(dt))
         return tt.value, dt.value
 
-    KERNELS = ("dt", "slopes", "recon", "flux1", "update1", "flux2", "update2")
+    KERNELS = ("dt", "slopes", "recon", "flux1", "update1", "flux2", "update2", "stage1", "stage2")
 
     def step_timed(self, nsteps=1, dt_fixed=0.0, t_end=0.0):
         """Kernel-by-kernel steps with CUDA events between launches; returns
@@ -341,6 +343,18 @@ class State:
         _call("gks_state_set_variant", self._h, int(face_order), int(flux_blocks), int(slopes_pass))
         self.variant = (int(face_order), int(flux_blocks), int(slopes_pass))
 
+    NVARIANTS = 10  # variants gks_autotune times: 8 with separate kernels, 2 with one launch per stage
+
+    def set_fused(self, fused=True):
+        """Each stage as one persistent launch (precision 1 only; results are
+        bit-identical to the separate kernels; gks_state_set_fused)."""
+        _call("gks_state_set_fused", self._h, int(bool(fused)))
+
+    def fused(self):
+        v = C.c_int32()
+        _call("gks_state_get_fused", self._h, C.byref(v))
+        return int(v.value)
+
     def set_cell_order(self, order):
         """Device cell ordering (FP32 bulk): 0 the caller's, 1 reverse
         Cuthill-McKee, 2 Morton; results are unchanged (gks_state_set_cell_order)."""
@@ -372,10 +386,12 @@ class State:
                 table = json.load(open(cache))
             except (OSError, ValueError):
                 table = {}
-        if key in table and len(table[key].get("variant", ())) == 3:
+        if key in table and len(table[key].get("variant", ())) == 3 and "fused" in table[key]:
             if orders and "cell_order" in table[key]:
                 self.set_cell_order(table[key]["cell_order"])
             self.set_variant(*table[key]["variant"])
+            if self.params.precision == 1 or table[key]["fused"]:
+                self.set_fused(table[key]["fused"])
             return dict(table[key], cached=True)
         fo, fb, sp = C.c_int32(), C.c_int32(), C.c_int32()
         if orders:
@@ -385,14 +401,14 @@ class State:
                   _np_ptr(ms))
             self.cell_order = co.value
             self.variant = (fo.value, fb.value, sp.value)
-            res = {"variant": list(self.variant), "cell_order": co.value,
+            res = {"variant": list(self.variant), "cell_order": co.value, "fused": self.fused(),
                    "ms_per_order": ms[:3 if self.params.precision != 0 else 1].tolist()}
         else:
-            ms = np.zeros(8)
+            ms = np.zeros(self.NVARIANTS)
             _call("gks_autotune", self._h, int(steps), C.byref(fo), C.byref(fb), C.byref(sp), _np_ptr(ms))
-            nvar = 8 if self.params.precision != 0 else 4
             self.variant = (fo.value, fb.value, sp.value)
-            res = {"variant": list(self.variant), "ms_per_step": ms[:nvar].tolist()}
+            res = {"variant": list(self.variant), "fused": self.fused(),
+                   "ms_per_step": [None if np.isnan(x) else float(x) for x in ms]}
         if cache:
             try:
                 os.makedirs(os.path.dirname(cache), exist_ok=True)

@@ -40,8 +40,11 @@ def calls(monkeypatch):
         if name == "gks_autotune":
             _, steps, fo, fb, sp, ms = args
             fo._obj.value, fb._obj.value, sp._obj.value = 1, 2, 1
-            out = np.ctypeslib.as_array(C.cast(ms, C.POINTER(C.c_double)), shape=(8,))
-            out[:] = np.arange(8.0, 0.0, -1.0)
+            out = np.ctypeslib.as_array(C.cast(ms, C.POINTER(C.c_double)), shape=(gks.State.NVARIANTS,))
+            out[:] = np.arange(10.0, 0.0, -1.0)
+            out[8] = np.nan  # a variant the library did not time
+        elif name == "gks_state_get_fused":
+            args[1]._obj.value = 1
         return 0
 
     monkeypatch.setattr(gks, "_call", fake_call)
@@ -56,12 +59,14 @@ def test_first_call_tunes_and_stores(calls, tmp_path):
     cache = str(tmp_path / "sub" / "autotune.json")
     res = _state().autotune(steps=3, cache=cache)
     assert res["cached"] is False and res["variant"] == [1, 2, 1]
-    assert res["ms_per_step"] == list(np.arange(8.0, 0.0, -1.0))  # 8 variants in FP32 bulk
-    assert _names(calls) == ["gks_autotune"] and calls[0][1][0] == 3
+    # 10 variants: 8 with separate kernels, 2 with one launch per stage; NaN (untimed) reads None
+    assert res["ms_per_step"] == [10.0, 9.0, 8.0, 7.0, 6.0, 5.0, 4.0, 3.0, None, 1.0]
+    assert res["fused"] == 1
+    assert _names(calls) == ["gks_autotune", "gks_state_get_fused"] and calls[0][1][0] == 3
     table = json.load(open(cache))
     (key, entry), = table.items()
     assert key.startswith("test GPU|nc=100|nf=200|ncase=1|prec=1|weno=1")
-    assert entry["variant"] == [1, 2, 1]
+    assert entry["variant"] == [1, 2, 1] and entry["fused"] == 1
 
 
 def test_second_call_reuses_the_stored_variant(calls, tmp_path):
@@ -71,7 +76,8 @@ def test_second_call_reuses_the_stored_variant(calls, tmp_path):
     s = _state()
     res = s.autotune(cache=cache)
     assert res["cached"] is True and res["variant"] == [1, 2, 1]
-    assert _names(calls) == ["gks_state_set_variant"] and calls[0][1] == (1, 2, 1)
+    assert _names(calls) == ["gks_state_set_variant", "gks_state_set_fused"]
+    assert calls[0][1] == (1, 2, 1) and calls[1][1] == (1,)
     assert s.variant == (1, 2, 1)
 
 
@@ -79,7 +85,7 @@ def test_options_and_sizes_get_their_own_entries(calls, tmp_path):
     cache = str(tmp_path / "autotune.json")
     _state(precision=1).autotune(cache=cache)
     res = _state(precision=0).autotune(cache=cache)
-    assert res["cached"] is False and len(res["ms_per_step"]) == 4  # FP64: 4 variants
+    assert res["cached"] is False and len(res["ms_per_step"]) == gks.State.NVARIANTS
     _state(nc=101).autotune(cache=cache)
     assert len(json.load(open(cache))) == 3
     assert _names(calls).count("gks_autotune") == 3
@@ -89,14 +95,18 @@ def test_damaged_cache_is_retuned_and_rewritten(calls, tmp_path):
     cache = tmp_path / "autotune.json"
     cache.write_text("{ not json")
     res = _state().autotune(cache=str(cache))
-    assert res["cached"] is False and _names(calls) == ["gks_autotune"]
+    assert res["cached"] is False and _names(calls) == ["gks_autotune", "gks_state_get_fused"]
     assert len(json.load(open(cache))) == 1
     # an entry without a complete variant is not trusted either
     key = next(iter(json.load(open(cache))))
     cache.write_text(json.dumps({key: {"variant": [1, 2]}}))
     calls.clear()
     assert _state().autotune(cache=str(cache))["cached"] is False
-    assert _names(calls) == ["gks_autotune"]
+    assert _names(calls) == ["gks_autotune", "gks_state_get_fused"]
+    # nor one from before the one-launch stage (no "fused" entry)
+    cache.write_text(json.dumps({key: {"variant": [1, 2, 1]}}))
+    calls.clear()
+    assert _state().autotune(cache=str(cache))["cached"] is False
 
 
 def test_no_cache_mode_writes_nothing(calls, tmp_path, monkeypatch):

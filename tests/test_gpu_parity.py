@@ -258,6 +258,54 @@ def test_config2_sod_full_size_three_steps(cuda, oracle_mod, precision):
     assert _grad_rel(dWg, dWo) < TOL[precision], _grad_rel(dWg, dWo)
 
 
+_DEVELOPED = {}
+
+
+def _developed_sod(oracle_mod):
+    """The 36,864-cell Sod tube (96 x 8 x 8 hexes x 6) after three oracle
+    steps from its seeded initial state, and the oracle's fourth step from
+    there: the discontinuity has spread over a few cells and the
+    reconstruction's second-derivative terms are at their largest."""
+    if not _DEVELOPED:
+        mesh, W, dW = I.sod_case(nx=96, nyz=8)
+        om = oracle_mod.Mesh(mesh)
+        p = oracle_mod.params(weno=1, cfl=0.5)
+        W3, dW3, _, _ = om.run(p, W, dW, nsteps=3)
+        dt = om.timestep(p, W3)
+        W4, dW4, _ = om.step(p, W3, dW3, dt)
+        _DEVELOPED.update(mesh=mesh, W3=W3, dW3=dW3, dt=dt, W4=W4, dW4=dW4)
+    return _DEVELOPED
+
+
+@pytest.mark.parametrize("precision,fused", [(0, 0), (1, 0), (1, 1), (2, 0)])
+def test_sod_one_step_from_developed_discontinuity(cuda, oracle_mod, precision, fused):
+    """One step from the oracle's state at step 3 of the Sod tube, with the
+    oracle's step size, against the oracle's step 4: every cell, averages
+    and gradients, at the tolerance of the precision (the FP32 bulk with
+    either form of the stage).  This is the per-step parity at a sharp
+    discontinuity; over several steps from the initial jump the FP32 forms
+    drift from the FP64 result there by more than one step's rounding, as
+    the nonlinear weights amplify it."""
+    d = _developed_sod(oracle_mod)
+    g = gks.Mesh(d["mesh"])
+    s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=precision))
+    if fused:
+        s.set_fused(True)
+    s.init(d["W3"], d["dW3"])
+    s.step(1, d["dt"])
+    s.sync()
+    Wg, dWg = [x.cpu().numpy() for x in s.get()]
+    # FP64: at the developed jump the reconstruction's second-derivative
+    # coefficients reach ~6e3 times the state scale, and the 16-term operator
+    # products cancel down to O(1) values, so a different rounding order moves
+    # the result by ~16 x 6e3 x 2^-53 ~ 1e-11 per reconstruction; 5e-11 bounds
+    # a step (two reconstructions and the flux built on them)
+    tol = 5e-11 if precision == 0 else TOL[1]
+    es, eg = _state_rel(Wg, d["W4"]), _grad_rel(dWg, d["dW4"])
+    print("developed Sod, one step, precision %d fused %d: state %.3g gradient %.3g" % (precision, fused, es, eg))
+    assert es < tol and eg < tol, (es, eg)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_sod_tube_16x4x4_ten_steps(cuda, oracle_mod, precision):
     """WENO over ten steps on a Sod tube of 16 x 4 x 4 hexes x 6 (1,536

@@ -133,6 +133,12 @@ def test_shu_osher(cuda, precision):
     assert abs(t - 1.8) < 1e-12
     x = g.geometry()["cen"][:, 0]
     rho = Wg[0]
+    # the flow is one-dimensional: the tetrahedra of the thin periodic cross
+    # section imprint a transverse velocity of about 0.2-0.35 behind the Mach-3
+    # shock; a transverse instability of that layer (seeded by rounding, it
+    # reached 0.74 in an FP32 build with approximate division in the update
+    # and smeared the shock) stays out
+    assert np.abs(Wg[2:4] / rho).max() < 0.5, np.abs(Wg[2:4] / rho).max()
     ahead = x > 7.8
     assert np.abs(rho[ahead] - W[0][ahead]).max() < 2e-3
     assert abs(rho[x < 0.5].mean() - 3.857134) < 1e-3
