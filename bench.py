@@ -43,10 +43,11 @@ CPU_SAMPLE = dict(nx=16, nyz=4)  # same recipe, 1,536 cells: oracle per-cell cos
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # work of the dominant kernel (face flux) per Gauss point and stage, FP32 flop
 # (fadd + fmul + 2 ffma) counted by ncu on this workload (147,840 Gauss points
-# a launch), and its DRAM bytes per stage-1 launch from the same capture (the
-# flux kernel's summary under profiles/)
-FLUX_FLOPS_PER_GP = {"fp32": (4216.6, 4114.3)}
-FLUX_DRAM_BYTES_PER_LAUNCH = None
+# a launch), and its DRAM bytes (read + write) per launch, the mean of the
+# stage-1 and stage-2 launches, from the same capture (the flux kernel's
+# summary under profiles/)
+FLUX_FLOPS_PER_GP = {"fp32": (4546.7, 3874.2)}
+FLUX_DRAM_BYTES_PER_LAUNCH = 11827840.0
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # algorithmic HBM traffic of one cell-stage: the minimum of the four passes
 # the method's two global dependencies impose (neighbour slopes; both sides'
@@ -240,13 +241,14 @@ def batched_leg(torch, gks, args, flush):
     ms_mine = time_device(torch, s, steps, args.warmup, flush)
     ms = replicas.max_over_ranks(ms_mine)
     t, dt = s.case_times()
+    forms = stage_forms(torch, s, max(3, steps // 2), min(args.warmup, 3), flush, ms)
     # the same batch with FP64 stencil operators (precision 2), fewer steps
     del s
     torch.cuda.empty_cache()
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=2))
     s.init(W, dW)
     s.set_cell_order(tuned["cell_order"])
-    s.set_variant(*tuned["variant"])
+    s.set_variant(*tuned["variant"])  # precision 2 has no one-launch stage
     ms_ops64 = replicas.max_over_ranks(time_device(torch, s, max(3, steps // 3), min(args.warmup, 3), flush))
     del s
     torch.cuda.empty_cache()
@@ -262,8 +264,23 @@ def batched_leg(torch, gks, args, flush):
             "rank0_cases": len(mine), "rank0_cells": g.nc,
             "dt_range": [float(dt.min()), float(dt.max())], "host_setup_s": setup_s,
             "autotuned_variant": tuned["variant"], "cell_order": tuned["cell_order"],
+            "stage_forms": forms,
             "ms_per_cell_order": dict(zip(("caller", "rcm", "morton"), tuned["ms_per_order"])),
             "l2": "inputs larger than L2 (plus the flush)"}
+
+
+def stage_forms(torch, s, steps, warmup, flush, ms_chosen):
+    """Step time of both forms of a stage on an FP32-bulk state: separate
+    reconstruction / flux / update kernels, and one persistent launch per
+    stage (gks_state_set_fused); the autotuned one (timed already: ms_chosen)
+    is restored.  Timing changes the state; the caller has taken its numbers."""
+    chosen = s.fused()
+    s.set_fused(1 - chosen)
+    ms_other = replicas.max_over_ranks(time_device(torch, s, steps, warmup, flush))
+    s.set_fused(chosen)
+    ms = {chosen: ms_chosen, 1 - chosen: ms_other}
+    return {"chosen": "one launch per stage" if chosen else "separate kernels",
+            "ms_per_step_separate": ms[0], "ms_per_step_fused": ms[1]}
 
 
 def adjoint_leg(torch, gks, args):
@@ -404,6 +421,7 @@ def sphere_leg(torch, gks, args, flush):
                      "steps_timed": steps, "t": t, "variant": list(s.variant), "cell_order": s.cell_order}
         if prec == 1:
             out[name]["ms_per_cell_order"] = dict(zip(("caller", "rcm", "morton"), tuned["ms_per_order"]))
+            out[name]["stage_forms"] = stage_forms(torch, s, steps, min(args.warmup, 3), flush, ms)
         s.init(W, dW)
         s.step(3)
         s.sync()
@@ -511,6 +529,9 @@ def main():
     ap.add_argument("--variant", default="auto",
                     help="execution variant of --profile-case: face_order,flux_blocks,slopes_pass "
                          "(e.g. 1,3,1) or auto (tuned as in the full run)")
+    ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
+                    help="stage form of --profile-case: 1 one launch per stage, 0 separate kernels, "
+                         "-1 as tuned (auto) or separate (explicit --variant)")
     ap.add_argument("--batch-cases", type=int, default=48,
                     help="independent cases of the batched leg (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
@@ -563,10 +584,12 @@ def main():
             s.autotune(steps=10, cache=False)
         else:
             s.set_variant(*[int(v) for v in args.variant.split(",")])
+        if args.fused >= 0:
+            s.set_fused(args.fused)
         ms = time_device(torch, s, args.steps, args.warmup, flush)
         if rank == 0:
             print(json.dumps({"profile_case": WORKLOAD, "precision": args.precision, "variant": s.variant,
-                              "ms_per_step": ms}))
+                              "fused": s.fused(), "ms_per_step": ms}))
         return
 
     results = {}
@@ -581,13 +604,26 @@ def main():
         else:
             ms = time_device(torch, s, max(3, args.steps // 5), args.warmup, flush)
         ms = replicas.max_over_ranks(ms)
+        fused = s.fused()
+        forms = stage_forms(torch, s, max(3, args.steps // 5), args.warmup, flush, ms) if prec == 1 else None
         # kernel breakdown: same steps, kernel by kernel, events between launches
-        s.init(W0, dW0)
-        for _ in range(args.warmup):
-            s.step(1)
-        s.sync()
-        br = s.step_timed(max(3, args.steps // 5 if name != "fp32" else args.steps))
-        results[name] = {"ms": ms, "breakdown": br, "variant": tuned["variant"],
+        # (the separate kernels, so that the flux launches are timed alone;
+        # with the one-launch stage also its two launches)
+        nbr = max(3, args.steps // 5 if name != "fp32" else args.steps)
+        br = {}
+        for f in ((0, 1) if prec == 1 else (0,)):
+            if prec == 1:
+                s.set_fused(f)
+            s.init(W0, dW0)
+            for _ in range(args.warmup):
+                s.step(1)
+            s.sync()
+            for k, v in s.step_timed(nbr).items():
+                if v[1] > 0:
+                    br[k] = v
+        if prec == 1:
+            s.set_fused(fused)
+        results[name] = {"ms": ms, "breakdown": br, "variant": tuned["variant"], "fused": fused, "forms": forms,
                          "cell_order": tuned.get("cell_order", 0)}
     # equal-L1 comparison at t = 0.2 (untimed)
     l1_64, W64 = l1_at(torch, gks, mesh, W0, dW0, 0, 0.2)
@@ -600,6 +636,7 @@ def main():
     s = gks.State(g, gks.params(weno=1, cfl=0.5, precision=1))
     s.set_cell_order(results["fp32"]["cell_order"])
     s.set_variant(*results["fp32"]["variant"])  # the autotuned variant, as a user's cached autotune() sets it
+    s.set_fused(results["fp32"]["fused"])
     Wh = torch.tensor(W0).pin_memory()
     dWh = torch.tensor(dW0).pin_memory()
     for _ in range(args.warmup):
@@ -616,9 +653,14 @@ def main():
     value64 = ws * nc * 2 / (results["fp64"]["ms"] / 1000.0) / 1e6
     br = results["fp32"]["breakdown"]
     flux_ms = (br["flux1"][0] + br["flux2"][0]) / max(1, br["flux1"][1] + br["flux2"][1])
-    total_ms = sum(v[0] for v in br.values())
+    sep = ("slopes", "recon", "flux1", "update1", "flux2", "update2")
+    total_ms = sum(br[k][0] for k in sep if k in br)
     nst = max(1, br["flux1"][1])  # steps in the breakdown pass
-    launches_per_step = sum(v[1] for v in br.values()) / nst + 1  # + control kernel
+    # launches per timed step: the control kernel + the chosen form's kernels
+    if results["fp32"]["fused"]:
+        launches_per_step = 1 + (br["stage1"][1] + br["stage2"][1]) / nst
+    else:
+        launches_per_step = 1 + sum(br[k][1] for k in sep if k in br) / nst
     gps = 3 * g.nf
     peaks, peak_src = _peaks()
     clk_mhz = SM_MAX_MHZ
@@ -650,6 +692,7 @@ def main():
                          note="latency-bound size: the 24,576-cell workspace fits in L2"),
         "autotuned_variant": {"fp32": results["fp32"]["variant"], "fp64": results["fp64"]["variant"],
                               "meaning": "[face_order, flux_blocks_per_SM, slopes_pass]",
+                              "fp32_stage_forms": results["fp32"]["forms"],
                               "fp32_cell_order": results["fp32"]["cell_order"],
                               "cell_orders": "0 caller's, 1 reverse Cuthill-McKee, 2 Morton"},
         "accuracy_t0.2": {"l1_rho_fp64": l1_64, "l1_rho_fp32": l1_32, "l1_rho_fp32_ops64": l1_32o,
