@@ -60,6 +60,11 @@ struct ora_mesh {
     double *M1, *M2;
     double* M2L;  /* [nc][3][16]: boundary cells' first-order fit (Sec. 4.4), else 0 */
     int64_t n_singular;
+    /* Sec. 4.4 constrained stencils of cells with non-slip adiabatic wall
+     * faces (built with the boundary kinds) */
+    double* MW1;     /* [nc][3][5] */
+    double* MW2;     /* [nc][9][17] */
+    int8_t* wallc;   /* [nc] 1 where built */
     /* boundary kind of each face (ORA_BC_*), meaningful on boundary faces */
     int8_t* bkind;      /* [nf] */
     /* the fixed boundary state: a copy of W[5][nc], dW[15][nc] (or NULL) */
@@ -510,6 +515,164 @@ static void build_stencils(ora_mesh* m) {
     }
 }
 
+/* Sec. 4.4, boundary cells at non-slip adiabatic walls: the momenta are
+ * reconstructed by constrained least squares, the wall velocity (zero)
+ * imposed on the polynomial at the wall faces, one point per face (its
+ * centroid) in step 1 and the three Gauss points per face in step 2.  The
+ * constraint value rho U_wall is zero whatever the density, so each
+ * constrained polynomial is linear in the stencil data and the cell average
+ * Q0: the operators below take Q0 as one more data column.
+ *
+ * Step 1: unknowns b (the slopes of P1(x) = Q0 + b.(x - x_c)); least-squares
+ * rows d_r . b = dQ_r for the existing neighbours (as in the unconstrained
+ * P1), equality rows e_w . b = -Q0 for each wall face w (e_w = its centroid
+ * relative to the cell's).  Solved through the KKT system
+ *   [sum d d^T  E^T] [b     ]   [sum d dQ]
+ *   [E          0  ] [lambda] = [-Q0     ].
+ * Used when neighbours + constraints >= 3 and constraints <= 3.
+ *
+ * Step 2: unknowns the nine zero-mean basis coefficients, as the
+ * unconstrained P2: the neighbours' averages exact, their averaged gradients
+ * in the least-squares sense, and P2(x_g) = 0 at each wall Gauss point
+ * (sum_k a_k p^k(x_g) = -Q0) as further equality rows.  READING: the paper's
+ * bullet for this case says "first-order polynomial"; its counts (data plus
+ * constraints >= 9, constraints <= 9) are those of the nine P2 unknowns, and
+ * its fallbacks are the first-order fits, so the constrained polynomial is
+ * taken to be P2.  Built when the equality rows (neighbours + 3 x wall faces)
+ * number at most 9 and neighbours + 3 x wall faces + 3 x neighbours >= 9.
+ */
+static void build_wall_stencils(ora_mesh* m) {
+    free(m->MW1);
+    free(m->MW2);
+    free(m->wallc);
+    m->MW1 = (double*)calloc((size_t)m->nc * 15, sizeof(double));
+    m->MW2 = (double*)calloc((size_t)m->nc * 153, sizeof(double));
+    m->wallc = (int8_t*)calloc((size_t)m->nc, 1);
+    for (int64_t c = 0; c < m->nc; ++c) {
+        int wf[4], nw = 0, faces[4], nn = 0;
+        double d[4][3];
+        for (int f = 0; f < 4; ++f) {
+            if (m->nbr[c * 4 + f] >= 0) {
+                faces[nn] = f;
+                neighbour_offset(m, c, f, d[nn]);
+                ++nn;
+            } else if (m->bkind[m->csr_face[c * 4 + f]] == ORA_BC_NOSLIP_WALL) {
+                wf[nw++] = f;
+            }
+        }
+        if (nw == 0) continue;
+        if (nn + nw < 3 || nw > 3 || nn + 3 * nw > 9 || nn + 3 * nw + 3 * nn < 9) continue;
+        /* the wall faces' Gauss points relative to this cell's centroid */
+        double xg[4][3][3], xc[4][3];
+        for (int w = 0; w < nw; ++w) {
+            int64_t fi = m->csr_face[c * 4 + wf[w]];
+            const double* gp = m->csr_sign[c * 4 + wf[w]] > 0 ? &m->gp_l[fi * 9] : &m->gp_r[fi * 9];
+            for (int a = 0; a < 3; ++a) {
+                xc[w][a] = 0.0;
+                for (int g = 0; g < 3; ++g) {
+                    xg[w][g][a] = gp[g * 3 + a];
+                    xc[w][a] += gp[g * 3 + a] / 3.0; /* the three points' mean is the centroid */
+                }
+            }
+        }
+        /* step 1 */
+        int n1 = 3 + nw;
+        double K1[6 * 6], R1[6 * 5], pmin, pmax;
+        memset(K1, 0, sizeof(K1));
+        memset(R1, 0, sizeof(R1));
+        for (int r = 0; r < nn; ++r)
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) K1[i * n1 + j] += d[r][i] * d[r][j];
+                R1[i * 5 + faces[r]] = d[r][i];
+            }
+        for (int w = 0; w < nw; ++w) {
+            for (int i = 0; i < 3; ++i) {
+                K1[(3 + w) * n1 + i] = xc[w][i];
+                K1[i * n1 + 3 + w] = xc[w][i];
+            }
+            R1[(3 + w) * 5 + 4] = -1.0;
+        }
+        if (gauss_solve(n1, 5, K1, R1, &pmin, &pmax) != 0 || pmin < 1e-12 * pmax) continue;
+        /* step 2 (unknowns and rows scaled by powers of h0 as in the
+         * unconstrained P2; the solution is unchanged) */
+        double h0 = cbrt(m->vol[c]);
+        double sc[9];
+        for (int k = 0; k < 9; ++k) sc[k] = k < 3 ? h0 : h0 * h0;
+        int ne = nn + 3 * nw, n2 = 9 + ne;
+        double K2[18 * 18], R2[18 * 17], Bm[12][9];
+        memset(K2, 0, sizeof(K2));
+        memset(R2, 0, sizeof(R2));
+        const double* M0 = &m->mom2[c * 6];
+        for (int r = 0; r < nn; ++r) {
+            const double* Mm = &m->mom2[m->nbr[c * 4 + faces[r]] * 6];
+            double row[9];
+            for (int k = 0; k < 3; ++k) row[k] = d[r][k] / sc[k];
+            for (int q = 0; q < 6; ++q) row[3 + q] = (Mm[q] + d[r][QI[q]] * d[r][QJ[q]] - M0[q]) / sc[3 + q];
+            for (int k = 0; k < 9; ++k) {
+                K2[(9 + r) * n2 + k] = row[k];
+                K2[k * n2 + 9 + r] = row[k];
+            }
+            R2[(9 + r) * 17 + faces[r]] = 1.0;
+            for (int l = 0; l < 3; ++l) {
+                double* g = Bm[r * 3 + l];
+                for (int k = 0; k < 3; ++k) g[k] = h0 * (k == l ? 1.0 : 0.0) / sc[k];
+                for (int q = 0; q < 6; ++q) {
+                    double v = 0.0;
+                    if (QI[q] == l) v += d[r][QJ[q]];
+                    if (QJ[q] == l) v += d[r][QI[q]];
+                    g[3 + q] = h0 * v / sc[3 + q];
+                }
+            }
+        }
+        for (int w = 0; w < nw; ++w)
+            for (int gpt = 0; gpt < 3; ++gpt) {
+                const double* X = xg[w][gpt];
+                int e = 9 + nn + 3 * w + gpt;
+                double row[9];
+                for (int k = 0; k < 3; ++k) row[k] = X[k] / sc[k];
+                for (int q = 0; q < 6; ++q) row[3 + q] = (X[QI[q]] * X[QJ[q]] - M0[q]) / sc[3 + q];
+                for (int k = 0; k < 9; ++k) {
+                    K2[e * n2 + k] = row[k];
+                    K2[k * n2 + e] = row[k];
+                }
+                R2[e * 17 + 16] = -1.0;
+            }
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) {
+                double s = 0.0;
+                for (int r = 0; r < 3 * nn; ++r) s += Bm[r][i] * Bm[r][j];
+                K2[i * n2 + j] = 2.0 * s;
+            }
+        for (int r = 0; r < nn; ++r)
+            for (int l = 0; l < 3; ++l)
+                for (int i = 0; i < 9; ++i) R2[i * 17 + 4 + 3 * faces[r] + l] = 2.0 * Bm[r * 3 + l][i] * h0;
+        if (gauss_solve(n2, 17, K2, R2, &pmin, &pmax) != 0 || pmin < 1e-12 * pmax) continue;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 5; ++j) m->MW1[c * 15 + i * 5 + j] = R1[i * 5 + j];
+        for (int k = 0; k < 9; ++k)
+            for (int j = 0; j < 17; ++j) m->MW2[c * 153 + k * 17 + j] = R2[k * 17 + j] / sc[k];
+        m->wallc[c] = 1;
+    }
+}
+
+int64_t ora_mesh_wall_stencils(const ora_mesh* m, double* MW1, double* MW2, int8_t* wallc) {
+    int64_t n = 0;
+    for (int64_t c = 0; c < m->nc; ++c) n += m->wallc && m->wallc[c];
+    if (MW1) {
+        if (m->MW1) memcpy(MW1, m->MW1, sizeof(double) * 15 * m->nc);
+        else memset(MW1, 0, sizeof(double) * 15 * m->nc);
+    }
+    if (MW2) {
+        if (m->MW2) memcpy(MW2, m->MW2, sizeof(double) * 153 * m->nc);
+        else memset(MW2, 0, sizeof(double) * 153 * m->nc);
+    }
+    if (wallc) {
+        if (m->wallc) memcpy(wallc, m->wallc, (size_t)m->nc);
+        else memset(wallc, 0, (size_t)m->nc);
+    }
+    return n;
+}
+
 ora_mesh* ora_mesh_build(const double* xyz, int64_t nv, const int64_t* tet,
                          const int8_t* shift, int64_t nc, const double* period,
                          char* err, int errlen) {
@@ -551,6 +714,7 @@ int ora_mesh_set_boundary(ora_mesh* m, const int8_t* kind) {
                 return -1;
             m->bkind[m->csr_face[c * 4 + f]] = k;
         }
+    build_wall_stencils(m);
     return 0;
 }
 
@@ -571,6 +735,7 @@ void ora_mesh_free(ora_mesh* m) {
     free(m->vol); free(m->cen); free(m->mom2); free(m->dr);
     free(m->farea); free(m->fnorm); free(m->gp_l); free(m->gp_r);
     free(m->M1); free(m->M2); free(m->M2L); free(m->bkind); free(m->fixW); free(m->fixdW);
+    free(m->MW1); free(m->MW2); free(m->wallc);
     free(m);
 }
 
@@ -745,8 +910,16 @@ static void weno_weights(int order, double eps, double beta0, double beta1, doub
     }
 }
 
-static void slopes_all(const ora_mesh* m, const double* W, double* b) {
-    /* Reconstruction step 1 (Sec. 4.3): P1 slopes of every cell */
+/* 1 where component q of cell c takes the Sec. 4.4 wall-constrained
+ * stencils: a momentum component of a cell with a non-slip adiabatic wall
+ * face whose constrained operators were built */
+static int wall_constrained(const ora_mesh* m, const ora_params* p, int64_t c, int q) {
+    return p->wall_constraint && m->wallc && m->wallc[c] && q >= 1 && q <= 3;
+}
+
+static void slopes_all(const ora_mesh* m, const ora_params* p, const double* W, double* b) {
+    /* Reconstruction step 1 (Sec. 4.3; Sec. 4.4 at non-slip walls): P1
+     * slopes of every cell */
     for (int64_t c = 0; c < m->nc; ++c)
         for (int q = 0; q < 5; ++q) {
             double dq[4];
@@ -754,9 +927,15 @@ static void slopes_all(const ora_mesh* m, const double* W, double* b) {
                 int64_t nb = m->nbr[c * 4 + f];
                 dq[f] = nb >= 0 ? W[q * m->nc + nb] - W[q * m->nc + c] : 0.0;
             }
+            int wall = wall_constrained(m, p, c, q);
             for (int i = 0; i < 3; ++i) {
                 double s = 0.0;
-                for (int f = 0; f < 4; ++f) s += m->M1[c * 12 + i * 4 + f] * dq[f];
+                if (wall) {
+                    for (int f = 0; f < 4; ++f) s += m->MW1[c * 15 + i * 5 + f] * dq[f];
+                    s += m->MW1[c * 15 + i * 5 + 4] * W[q * m->nc + c];
+                } else {
+                    for (int f = 0; f < 4; ++f) s += m->M1[c * 12 + i * 4 + f] * dq[f];
+                }
                 b[(c * 5 + q) * 3 + i] = s;
             }
         }
@@ -767,7 +946,7 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
                     int32_t* fallback) {
     const int64_t nc = m->nc;
     double* b = (double*)malloc(sizeof(double) * nc * 15);
-    slopes_all(m, W, b);
+    slopes_all(m, p, W, b);
     const double g22 = 100.0 / 111.0, g12 = 10.0 / 111.0, g02 = 1.0 / 111.0;
     const double g11 = 10.0 / 11.0, g01 = 1.0 / 11.0;
     const double eps = p->eps_weno;
@@ -789,7 +968,14 @@ int ora_reconstruct(const ora_mesh* m, const ora_params* p, const double* W,
             for (int i = 0; i < 3; ++i) P1[1 + i] = b[(c * 5 + q) * 3 + i];
             int boundary = 0;
             for (int f = 0; f < 4; ++f) boundary |= m->nbr[c * 4 + f] < 0;
-            if (boundary && !p->weno && p->order == 3) {
+            if (wall_constrained(m, p, c, q)) {
+                /* Sec. 4.4: P2 vanishing at the wall faces' Gauss points */
+                for (int k = 0; k < 9; ++k) {
+                    double s = m->MW2[c * 153 + k * 17 + 16] * Q0;
+                    for (int j = 0; j < 16; ++j) s += m->MW2[c * 153 + k * 17 + j] * data[j];
+                    P2[1 + k] = s;
+                }
+            } else if (boundary && !p->weno && p->order == 3) {
                 /* Sec. 4.4: the first-order least-squares fit instead of P2 */
                 for (int k = 0; k < 3; ++k) {
                     double s = 0.0;

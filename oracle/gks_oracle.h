@@ -28,6 +28,10 @@ typedef struct {
     double prandtl;    /* viscous only: Pr != 1 corrects the heat flux (Pr fix) */
     double wall_temperature; /* T = p / rho of isothermal walls */
     double wall_velocity[3]; /* velocity of moving walls (global frame) */
+    int32_t wall_constraint; /* 1: Sec. 4.4 constrained least squares for the
+                                momenta of cells with non-slip adiabatic wall
+                                faces (velocity zero at the wall); 0: the
+                                unconstrained one-sided stencil */
 } ora_params;
 
 typedef struct ora_mesh ora_mesh;
@@ -71,6 +75,19 @@ void ora_mesh_geometry(const ora_mesh* m, double* vol, double* cen, double* mom2
                        double* gp_r);
 /* M1[nc][3][4], M2[nc][9][16]; columns of absent neighbours are zero. */
 void ora_mesh_stencils(const ora_mesh* m, double* M1, double* M2);
+
+/* The constrained stencils of Sec. 4.4 at non-slip adiabatic walls (built
+ * by ora_mesh_set_boundary for every cell with an ORA_BC_NOSLIP_WALL face):
+ * MW1[nc][3][5] gives a momentum component's step-1 slopes as
+ * b = MW1 [dQ_f (4); Q0], the P1 of the least-squares fit to the
+ * neighbours' averages that vanishes at the centroid of each wall face;
+ * MW2[nc][9][17] gives its P2 coefficients (zero-mean basis, as M2) as
+ * a = MW2 [data (16); Q0], P2 fitted like the unconstrained one and
+ * vanishing at the three Gauss points of each wall face.  wallc[nc] is 1
+ * where both were built, else 0 (no wall face, too few data, or a singular
+ * system: the cell keeps its unconstrained stencils).  Any output may be
+ * NULL.  Returns the number of cells with wallc = 1. */
+int64_t ora_mesh_wall_stencils(const ora_mesh* m, double* MW1, double* MW2, int8_t* wallc);
 
 /* Reconstruction of every cell.  poly[nc][5][10] is R in centroid-monomial
  * form: c0 + c_x X + c_y Y + c_z Z + c_xx X^2 + c_xy XY + c_xz XZ + c_yy Y^2

@@ -35,13 +35,14 @@ class Params(C.Structure):
                 ("eps_weno", C.c_double), ("tau_eps", C.c_double), ("tau_c", C.c_double),
                 ("weno", C.c_int32), ("order", C.c_int32), ("smooth_flux", C.c_int32),
                 ("viscous", C.c_int32), ("prandtl", C.c_double), ("wall_temperature", C.c_double),
-                ("wall_velocity", C.c_double * 3)]
+                ("wall_velocity", C.c_double * 3), ("wall_constraint", C.c_int32)]
 
 
 def params(gamma=1.4, cfl=0.5, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, weno=0,
-           order=3, smooth_flux=0, viscous=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0)):
+           order=3, smooth_flux=0, viscous=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0),
+           wall_constraint=0):
     return Params(gamma, cfl, mu, eps_weno, tau_eps, tau_c, weno, order, smooth_flux, viscous, prandtl,
-                  wall_temperature, (C.c_double * 3)(*[float(u) for u in wall_velocity]))
+                  wall_temperature, (C.c_double * 3)(*[float(u) for u in wall_velocity]), int(wall_constraint))
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -67,6 +68,8 @@ def lib():
         L.ora_mesh_topology.argtypes = [C.c_void_p, _ip, _ip, _ip, _ip, _bp]
         L.ora_mesh_geometry.argtypes = [C.c_void_p] + [_dp] * 8
         L.ora_mesh_stencils.argtypes = [C.c_void_p, _dp, _dp]
+        L.ora_mesh_wall_stencils.restype = C.c_int64
+        L.ora_mesh_wall_stencils.argtypes = [C.c_void_p, _dp, _dp, _bp]
         L.ora_reconstruct.argtypes = [C.c_void_p, C.POINTER(Params), _dp, _dp, _dp, _dp, _i32p]
         L.ora_gp_flux.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, C.c_double,
                                   _dp, _dp, _dp, _dp]
@@ -148,6 +151,15 @@ class Mesh:
         M2 = np.zeros((self.nc, 9, 16))
         lib().ora_mesh_stencils(self._h, M1, M2)
         return M1, M2
+
+    def wall_stencils(self):
+        """Sec. 4.4 constrained stencils of the non-slip wall cells:
+        (MW1[nc][3][5], MW2[nc][9][17], wallc[nc])."""
+        MW1 = np.zeros((self.nc, 3, 5))
+        MW2 = np.zeros((self.nc, 9, 17))
+        wc = np.zeros(self.nc, np.int8)
+        lib().ora_mesh_wall_stencils(self._h, MW1, MW2, wc)
+        return MW1, MW2, wc
 
     def reconstruct(self, p, W, dW):
         poly = np.zeros((self.nc, 5, 10))
