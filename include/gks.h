@@ -82,7 +82,14 @@ typedef struct gks_params {
                             averages, with its flux in FP64); 2: FP32 bulk as 1
                             with the stencil operators M1, M2, the cell moments
                             and their products in the reconstruction in FP64 */
-    int32_t reserved;    /* must be 0 */
+    int32_t wall_constraint; /* 1: at non-slip adiabatic walls (GKS_BC_NOSLIP_WALL) the
+                            momenta of the wall cells are reconstructed by the
+                            constrained least squares of Sec. 4.4: the step-1 P1
+                            vanishes at each wall face's centroid, the step-2 P2 at
+                            its three Gauss points (density and energy keep the
+                            one-sided stencil); 0 (default): the one-sided stencil
+                            for every component.  FP32 and FP64 alike; the adjoint
+                            step rejects a state that uses it (GKS_E_UNSUPPORTED) */
 } gks_params;
 
 /* Fills the paper's defaults: gamma 1.4, cfl 1, mu 0, eps_weno 1e-8,
@@ -227,6 +234,25 @@ gks_status gks_stencil_build(gks_mesh* mesh, int64_t* n_singular);
 
 /* Host copies of M1[nc][3][4] and M2[nc][9][16] (GKS_E_STENCIL if not built). */
 gks_status gks_mesh_stencils(const gks_mesh* mesh, double* M1, double* M2);
+
+/* The constrained operators of Sec. 4.4 that params.wall_constraint = 1
+ * applies to the momenta of cells with non-slip adiabatic wall faces
+ * (GKS_BC_NOSLIP_WALL, as set by gks_mesh_set_boundary), built from the
+ * mesh's FP64 geometry on each call:
+ *   W1[nc][3][5]:  step-1 slopes b = W1 [dQ_f (4); Q0], the least-squares
+ *                  P1 that vanishes at each wall face's centroid;
+ *   W2[nc][9][17]: step-2 coefficients a = W2 [dQ_f (4); grad Q_{f,l} (12);
+ *                  Q0] in the zero-mean basis of M2, the P2 with the
+ *                  neighbour averages exact, the neighbour gradients in the
+ *                  least-squares sense and zero at each wall face's three
+ *                  Gauss points;
+ *   built[nc]:     1 where both were built; zero rows elsewhere (no wall
+ *                  face, fewer than 3 neighbours + wall faces, more than 9
+ *                  equality rows, or a singular system: such a cell keeps
+ *                  its one-sided stencil).
+ * Any output may be NULL; *n_built (may be NULL) receives the count. */
+gks_status gks_mesh_wall_stencils(const gks_mesh* mesh, double* W1, double* W2, int8_t* built,
+                                  int64_t* n_built);
 
 /* --------------------------------------------------------------- state -- */
 

@@ -67,8 +67,8 @@ static gks_status check_params(const gks_params* p) {
     }
     if ((p->weno != 0 && p->weno != 1) || (p->order != 2 && p->order != 3) ||
         (p->smooth_flux != 0 && p->smooth_flux != 1) || (p->viscous != 0 && p->viscous != 1) ||
-        (p->precision < 0 || p->precision > 2) || p->reserved != 0) {
-        set_error("weno, smooth_flux, viscous must be 0 or 1; precision 0, 1 or 2; order 2 or 3; reserved 0");
+        (p->precision < 0 || p->precision > 2) || (p->wall_constraint != 0 && p->wall_constraint != 1)) {
+        set_error("weno, smooth_flux, viscous, wall_constraint must be 0 or 1; precision 0, 1 or 2; order 2 or 3");
         return GKS_E_ARG;
     }
     if (p->viscous && !(p->mu > 0.0)) {
@@ -255,17 +255,38 @@ extern "C" gks_status gks_mesh_stencils(const gks_mesh* m, double* M1, double* M
     return GKS_OK;
 }
 
+extern "C" gks_status gks_mesh_wall_stencils(const gks_mesh* m, double* W1, double* W2, int8_t* built,
+                                             int64_t* n_built) {
+    if (!m) { set_error("mesh is NULL"); return GKS_E_ARG; }
+    int64_t n = 0;
+    for (int64_t c = 0; c < m->nc; ++c) {
+        double w1[15], w2[153];
+        const bool ok = has_wall_face(*m, c) && cell_wall_stencil(*m, c, w2, w1);
+        if (!ok) {
+            std::memset(w1, 0, sizeof(w1));
+            std::memset(w2, 0, sizeof(w2));
+        }
+        if (W1) std::memcpy(W1 + c * 15, w1, sizeof(w1));
+        if (W2) std::memcpy(W2 + c * 153, w2, sizeof(w2));
+        if (built) built[c] = ok ? 1 : 0;
+        n += ok;
+    }
+    if (n_built) *n_built = n;
+    return GKS_OK;
+}
+
 // ----------------------------------------------------------------- state --
 
 namespace {
 
 struct Layout {
     size_t total = 0;
+    int64_t nwall = 0;  // slots of wall-constrained operators
     // mesh
     size_t nbr, cface, inv_vol, dr, M1, tile, flr, fgeo, fan, cell_case, perm;
     // state
     size_t Wd, X, Xs, X0, S, G, slopes, poly, rec, ctrl, case_t, case_dt, case_dtmin, part, err, stage, cperm, cinv,
-        gbar;
+        gbar, wslot, wop;
     size_t add(size_t bytes) {
         size_t off = total;
         total += (bytes + 255) & ~(size_t)255;
@@ -279,7 +300,17 @@ bool has_fixed(const gks_mesh& m) {
     return false;
 }
 
-Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool fixed, bool ops64 = false) {
+// cells that take the Sec. 4.4 wall-constrained stencils (an upper bound:
+// every cell with a non-slip adiabatic wall face) when the option is on
+int64_t wall_cells(const gks_mesh& m, const gks_params& p) {
+    if (!p.wall_constraint) return 0;
+    int64_t n = 0;
+    for (int64_t c = 0; c < m.nc; ++c) n += has_wall_face(m, c);
+    return n;
+}
+
+Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool fixed, bool ops64 = false,
+                        int64_t nwall = 0) {
     Layout L;
     const size_t T = fp32 ? 4 : 8;
     // FP32 bulk with FP64 stencil operators: the reconstruction tile and the
@@ -321,6 +352,11 @@ Layout layout_workspace(int64_t nc, int64_t nf, int64_t ncase, bool fp32, bool f
     // FP32 bulk: device cell -> caller's cell (the cell ordering)
     L.cperm = fp32 ? L.add(4 * nc) : 0;
     L.cinv = fp32 ? L.add(4 * nc) : 0;
+    // Sec. 4.4 wall-constrained momentum operators: slot of each (device)
+    // cell, -1 for none, and per slot W2 [9][17] then W1 [3][5] in TO
+    L.nwall = nwall;
+    L.wslot = nwall ? L.add(4 * nc) : 0;
+    L.wop = nwall ? L.add(TO * WOP_STRIDE * nwall) : 0;
     return L;
 }
 
@@ -489,6 +525,9 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.fgeo = at<T>(s, L.fgeo);
     m.fan = L.fan ? at<float>(s, L.fan) : nullptr;
     m.fixed = L.X0 ? at<T>(s, L.X0) : nullptr;
+    m.wslot = L.wslot ? at<int32_t>(s, L.wslot) : nullptr;
+    m.wop = L.wslot && !s->ops64 ? at<T>(s, L.wop) : nullptr;
+    m.wopd = L.wslot && s->ops64 ? at<double>(s, L.wop) : nullptr;
     st.Wd = at<double>(s, L.Wd);
     st.X = at<T>(s, L.X);
     st.Xs = at<T>(s, L.Xs);
@@ -590,6 +629,10 @@ static gks_status upload_cells(gks_state* s) {
     // least-squares first-order fit to its P2 stencil
     const bool linear_boundary = !s->params.weno && s->params.order == 3;
     std::vector<int32_t> cell_case((size_t)nc);
+    // Sec. 4.4 wall-constrained operators, slots in device-cell order
+    std::vector<int32_t> wslot(L.wslot ? (size_t)nc : 0, -1);
+    std::vector<TO> wop((size_t)L.nwall * WOP_STRIDE, TO(0));
+    int64_t nwop = 0;
     // d: device cell; c: the caller's cell it holds
     for (int64_t d = 0; d < nc; ++d) {
         const int64_t c = s->pub(d);
@@ -612,6 +655,15 @@ static gks_status upload_cells(gks_state* s) {
             M1[k * nc + d] = (TO)g.M1[c * 12 + k];
             put_row(TILE_M1 + k, g.M1[c * 12 + k]);
         }
+        if (L.wslot) {
+            double w2[153], w1[15];
+            if (has_wall_face(g, c) && cell_wall_stencil(g, c, w2, w1)) {
+                wslot[d] = (int32_t)(nwop++);
+                TO* o = &wop[(size_t)wslot[d] * WOP_STRIDE];
+                for (int k = 0; k < 153; ++k) o[k] = (TO)w2[k];
+                for (int k = 0; k < 15; ++k) o[WOP_W1 + k] = (TO)w1[k];
+            }
+        }
         const double* M2c = &g.M2[c * 144];
         double M2lin[144];
         if (linear_boundary && !g.singular[c] &&
@@ -629,6 +681,10 @@ static gks_status upload_cells(gks_state* s) {
     GKS_CHECK_CUDA(put(L.M1, M1.data(), sizeof(TO) * M1.size()));
     GKS_CHECK_CUDA(put(L.tile, tile.data(), sizeof(TO) * tile.size()));
     GKS_CHECK_CUDA(put(L.cell_case, cell_case.data(), 4 * cell_case.size()));
+    if (L.wslot) {
+        GKS_CHECK_CUDA(put(L.wslot, wslot.data(), 4 * wslot.size()));
+        if (nwop) GKS_CHECK_CUDA(put(L.wop, wop.data(), sizeof(TO) * WOP_STRIDE * nwop));
+    }
     if (!s->cperm.empty()) {
         GKS_CHECK_CUDA(put(L.cperm, s->cperm.data(), 4 * s->cperm.size()));
         GKS_CHECK_CUDA(put(L.cinv, s->cinv.data(), 4 * s->cinv.size()));
@@ -647,7 +703,7 @@ static gks_status upload_mesh(gks_state* s) {
 extern "C" size_t gks_workspace_bytes(const gks_mesh* mesh, const gks_params* params) {
     if (!mesh || check_params(params) != GKS_OK) return 0;
     return layout_workspace(mesh->nc, mesh->nf, mesh->ncase, params->precision != 0, has_fixed(*mesh),
-                            params->precision == 2)
+                            params->precision == 2, wall_cells(*mesh, *params))
         .total;
 }
 
@@ -662,7 +718,8 @@ extern "C" gks_status gks_state_create(const gks_mesh* mesh, const gks_params* p
     if (!mesh->has_stencils) { set_error("gks_state_create: stencils not built"); return GKS_E_STENCIL; }
     const bool fp32 = params->precision != 0;
     const bool ops64 = params->precision == 2;
-    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32, has_fixed(*mesh), ops64);
+    Layout L = layout_workspace(mesh->nc, mesh->nf, mesh->ncase, fp32, has_fixed(*mesh), ops64,
+                                wall_cells(*mesh, *params));
     if (!d_workspace || workspace_bytes < L.total) {
         set_error("gks_state_create: workspace missing or smaller than gks_workspace_bytes()");
         return GKS_E_NOMEM;
@@ -1136,6 +1193,10 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     if (s->fp32 || g.ncase != 1 || (has_fixed(g) && !s->fixed_pinned)) {
         set_error("gks_adjoint_step: needs an FP64 state on a single-case mesh, and on a mesh with "
                   "fixed-state faces a fixed state set by gks_set_fixed_state");
+        return GKS_E_UNSUPPORTED;
+    }
+    if (s->L.wslot) {
+        set_error("gks_adjoint_step: the wall-constrained reconstruction (wall_constraint = 1) has no adjoint");
         return GKS_E_UNSUPPORTED;
     }
     order_after_caller(s);

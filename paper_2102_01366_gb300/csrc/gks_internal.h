@@ -41,4 +41,8 @@ void set_error(const std::string& msg);
 gks_status build_mesh(gks_mesh& m);      // topology + geometry
 gks_status build_stencils(gks_mesh& m);  // M1, M2
 bool cell_linear_fit(const gks_mesh& m, int64_t c, double* M2);  // boundary cells, linear weights
+// Sec. 4.4 constrained operators of a cell with non-slip adiabatic wall
+// faces (see gks_stencil.cpp); false when it has none or they cannot be built
+bool cell_wall_stencil(const gks_mesh& m, int64_t c, double* W2, double* W1);
+bool has_wall_face(const gks_mesh& m, int64_t c);
 }  // namespace gks

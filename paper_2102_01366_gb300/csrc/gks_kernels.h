@@ -47,6 +47,9 @@ struct Stride {
 // about its centroid (36), M1 (12), central second moments (6), |Omega|^(2/3),
 // |Omega|^(4/3).
 enum { TILE_M2 = 0, TILE_G = 144, TILE_M1 = 180, TILE_MOM = 192, TILE_V23 = 198, TILE_V43 = 199, TILE_ROWS = 200 };
+// a wall-constrained operator slot: W2 [9][17] (P2 from [data (16); Q0])
+// then W1 [3][5] (P1 slopes from [dQ_f (4); Q0])
+enum { WOP_W1 = 153, WOP_STRIDE = 168 };
 
 template <typename T>
 struct DevMesh {
@@ -67,6 +70,12 @@ struct DevMesh {
     const T* fgeo;         // [nf][FGEO]: n(3), w, XL(9), XR(9), pad
     const float* fan;      // FP32 bulk: [nf][6] face area vectors A n as FP32 hi / lo pairs (NULL in FP64)
     const T* fixed;        // [nc][Stride<T>::xs] state held by fixed boundary faces (NULL: none)
+    // Sec. 4.4 wall-constrained momentum stencils (NULL: none): slot of each
+    // cell (-1: none) and per slot W2 [9][17] at 0, W1 [3][5] at WOP_W1, in
+    // the operator precision (wop; precision 2: wopd)
+    const int32_t* wslot;
+    const T* wop;
+    const double* wopd;
 };
 
 template <typename T>

@@ -24,23 +24,15 @@ __global__ void __launch_bounds__(CELL_THREADS) k_slopes(DevMesh<T> m, const T* 
     if (!cl.active) return;
     const int64_t nc = m.nc, c = cl.c;
     const int q = cl.q;
-    TO b0 = TO(0), b1 = TO(0), b2 = TO(0);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int nb = m.nbr[f * nc + c];
-        if (nb < 0) continue;
-        const TO dq = avg_diff<T, TO>(X, nb, c, q);
-        b0 += m1_at<T, TO>(m, 0 * 4 + f, c) * dq;
-        b1 += m1_at<T, TO>(m, 1 * 4 + f, c) * dq;
-        b2 += m1_at<T, TO>(m, 2 * 4 + f, c) * dq;
-    }
+    T b[3];
+    p1_slope<T, TO>(m, X, c, q, b);  // with the wall-constrained slopes of Sec. 4.4
     T* out = slopes + c * 15 + 3 * q;
-    out[0] = (T)b0;
-    out[1] = (T)b1;
-    out[2] = (T)b2;
+    out[0] = b[0];
+    out[1] = b[1];
+    out[2] = b[2];
 }
 
-template <typename T, typename TO>
+template <typename T, typename TO, bool WALL>
 __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst<T> rc,
                                                          const T* __restrict__ X,
                                                          const T* __restrict__ slopes_in,
@@ -53,7 +45,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_recon(DevMesh<T> m, ReconConst
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();  // the barrier exists before anyone waits on it
     if (fin.dtmin && blockIdx.x == 0) finalize_cases(fin.dtmin, fin.case_t, fin.case_dt, fin.ncase, fin.cfl, fin.ctrl);
-    recon_cells<T, TO>(m, rc, X, slopes_in, slopes_out, poly, fallback, err, blockIdx.x, threadIdx.x, sT, &bar, 0);
+    recon_cells<T, TO, WALL>(m, rc, X, slopes_in, slopes_out, poly, fallback, err, blockIdx.x, threadIdx.x, sT, &bar,
+                             0);
 }
 
 // --------------------------------------------------------------------------
@@ -92,12 +85,15 @@ cudaError_t Launch<T>::recon(const DevMesh<T>& m, const HostPhys& p, const T* X,
     rc.eps = (T)p.eps_weno;
     rc.weno = p.weno;
     rc.order = p.order;
+    // the wall-constrained instances only where the mesh has such cells
+    auto go = [&](auto kernel) {
+        kernel<<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback, fin_arg<T>(fin),
+                                                         err);
+    };
     if (m.tiled && sizeof(T) == 4)
-        k_recon<T, double><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback,
-                                                                    fin_arg<T>(fin), err);
+        m.wslot ? go(k_recon<T, double, true>) : go(k_recon<T, double, false>);
     else
-        k_recon<T, T><<<cell_grid(m.nc), CELL_THREADS, 0, s>>>(m, rc, X, slopes_in, slopes, poly, fallback,
-                                                               fin_arg<T>(fin), err);
+        m.wslot ? go(k_recon<T, T, true>) : go(k_recon<T, T, false>);
     return cudaGetLastError();
 }
 

@@ -120,19 +120,50 @@ __device__ __forceinline__ TO m1_at(const DevMesh<T>& m, int row, int64_t c) {
         return m.M1[row * m.nc + c];
 }
 
-// P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
-// b = M1 (Q_nb - Q_x) over the existing neighbours
+// The wall-constrained operator slot (Sec. 4.4) of component q of cell c:
+// the momenta of a cell with non-slip adiabatic wall faces whose
+// constrained stencils were built; NULL otherwise
+template <typename T, typename TO, bool WALL = true>
+__device__ __forceinline__ const TO* wall_ops(const DevMesh<T>& m, int64_t c, int q) {
+    if (!WALL || !m.wslot || q < 1 || q > 3) return nullptr;
+    const int32_t w = m.wslot[c];
+    if (w < 0) return nullptr;
+    if constexpr (sizeof(TO) > sizeof(T))
+        return m.wopd + (int64_t)w * WOP_STRIDE;
+    else
+        return m.wop + (int64_t)w * WOP_STRIDE;
+}
+
+// cell average Q0 of component q in TO (FP32 bulk: hi + lo)
 template <typename T, typename TO>
+__device__ __forceinline__ TO avg_at(const T* __restrict__ X, int64_t c, int q) {
+    constexpr int XSR = Stride<T>::xs;
+    if constexpr (sizeof(T) == 4)
+        return (TO)X[c * XSR + q] + (TO)X[c * XSR + XLO + q];
+    else
+        return X[c * XSR + q];
+}
+
+// P1 slope of cell x for component q (Sec. 4.3, reconstruction step 1):
+// b = M1 (Q_nb - Q_x) over the existing neighbours; at a non-slip wall the
+// constrained slope b = W1 [Q_nb - Q_x; Q_x] (Sec. 4.4)
+template <typename T, typename TO, bool WALL = true>
 __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restrict__ X, int64_t x, int q, T* b) {
     const int64_t nc = m.nc;
     TO s[3] = {TO(0), TO(0), TO(0)};
+    const TO* wo = wall_ops<T, TO, WALL>(m, x, q);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int nb = m.nbr[f * nc + x];
         if (nb < 0) continue;
         const TO dq = avg_diff<T, TO>(X, nb, x, q);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s[i] += m1_at<T, TO>(m, i * 4 + f, x) * dq;
+        for (int i = 0; i < 3; ++i) s[i] += (wo ? wo[WOP_W1 + i * 5 + f] : m1_at<T, TO>(m, i * 4 + f, x)) * dq;
+    }
+    if (wo) {
+        const TO q0 = avg_at<T, TO>(X, x, q);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[i] += wo[WOP_W1 + i * 5 + 4] * q0;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) b[i] = (T)s[i];
@@ -156,7 +187,7 @@ __device__ __forceinline__ void p1_slope(const DevMesh<T>& m, const T* __restric
 template <typename TO>
 using Tile = TO[TILE_ROWS][CELLS_PER_BLOCK];
 
-template <typename T, typename TO>
+template <typename T, typename TO, bool WALL>
 __device__ __forceinline__ void recon_cells(const DevMesh<T>& m, const ReconConst<T>& rc, const T* __restrict__ X,
                                             const T* __restrict__ slopes_in, T* __restrict__ slopes_out,
                                             T* __restrict__ poly, int32_t* __restrict__ fallback,
@@ -204,14 +235,28 @@ __device__ __forceinline__ void recon_cells(const DevMesh<T>& m, const ReconCons
     // values computed from an incomplete tile are never trusted by the host)
     const bool tile_ok = mbar_wait(bar, parity);
     if (!tile_ok && (threadIdx.x & 31) == 0) atomicOr(err, ERR_TIMEOUT);
-    // P2 in the zero-mean basis of Eq. base: a = M2 d
+    // P2 in the zero-mean basis of Eq. base: a = M2 d (at a non-slip wall
+    // the momenta's constrained a = W2 [d; Q0], Sec. 4.4)
+    const TO* wo = wall_ops<T, TO, WALL>(m, c, q);
+    TO q0w = TO(0);
+    if (wo) q0w = avg_at<T, TO>(X, c, q);
     T a[9];
+    if (wo) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        TO acc = TO(0);
+        for (int k = 0; k < 9; ++k) {
+            TO acc = wo[k * 17 + 16] * q0w;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc += sT[TILE_M2 + k * 16 + j][lc] * d[j];
-        a[k] = (T)acc;
+            for (int j = 0; j < 16; ++j) acc += wo[k * 17 + j] * d[j];
+            a[k] = (T)acc;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            TO acc = TO(0);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc += sT[TILE_M2 + k * 16 + j][lc] * d[j];
+            a[k] = (T)acc;
+        }
     }
     const T Mxx = (T)sT[TILE_MOM + 0][lc], Mxy = (T)sT[TILE_MOM + 1][lc], Mxz = (T)sT[TILE_MOM + 2][lc];
     const T Myy = (T)sT[TILE_MOM + 3][lc], Myz = (T)sT[TILE_MOM + 4][lc], Mzz = (T)sT[TILE_MOM + 5][lc];
@@ -227,7 +272,11 @@ __device__ __forceinline__ void recon_cells(const DevMesh<T>& m, const ReconCons
         for (int f = 0; f < 4; ++f) {
             if (nb[f] < 0) continue;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) bo[i] += sT[TILE_M1 + i * 4 + f][lc] * d[f];
+            for (int i = 0; i < 3; ++i) bo[i] += (wo ? wo[WOP_W1 + i * 5 + f] : sT[TILE_M1 + i * 4 + f][lc]) * d[f];
+        }
+        if (wo) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) bo[i] += wo[WOP_W1 + i * 5 + 4] * q0w;
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i) b[i] = (T)bo[i];
@@ -256,7 +305,7 @@ __device__ __forceinline__ void recon_cells(const DevMesh<T>& m, const ReconCons
                 bj[1] = sj[1];
                 bj[2] = sj[2];
             } else {
-                p1_slope<T, TO>(m, X, nb[f], q, bj);
+                p1_slope<T, TO, WALL>(m, X, nb[f], q, bj);
             }
             b0j[nn++] = v23 * (bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
         }

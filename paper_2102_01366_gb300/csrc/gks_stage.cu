@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, 1)
         __syncthreads();
         unsigned parity = 0;
         for (int64_t vb = (int64_t)blockIdx.x * CELL_GROUPS + grp; vb < ncb; vb += (int64_t)gridDim.x * CELL_GROUPS) {
-            recon_cells<float, float>(m, rc, X, nullptr, nullptr, st.poly, nullptr, st.err, vb, tid, tiles[grp],
+            recon_cells<float, float, true>(m, rc, X, nullptr, nullptr, st.poly, nullptr, st.err, vb, tid, tiles[grp],
                                       &bars[grp], parity);
             parity ^= 1u;
             group_barrier(BAR_CELL_GROUP + grp, CELL_THREADS);  // the tile is free for the next copy

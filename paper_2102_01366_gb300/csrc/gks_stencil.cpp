@@ -286,3 +286,179 @@ gks_status build_stencils(gks_mesh& m) {
 }
 
 }  // namespace gks
+
+namespace gks {
+namespace {
+
+// Least squares with equality constraints by the null-space method: over x
+// (n unknowns) minimise |A x - h| subject to E x = g, E (ne x n, full row
+// rank), A (nl x n).  The solution is linear in (g, h): x = Pe g + Pl h,
+// written to Pe (n x ne) and Pl (n x nl).  A QR of E^T splits x into the
+// part fixed by the constraints, Q1 R^-T g, and a free part Q2 z; z is the
+// least-squares solution of (A Q2) z = h - A Q1 R^-T g (a second QR).
+// False when either factor is numerically singular.
+bool constrained_ls(int n, int ne, const double* E, int nl, const double* A, double* Pe, double* Pl) {
+    const int nz = n - ne;
+    if (ne < 1 || nz < 0 || nl < nz) return false;
+    double Et[9 * 9], Qe[81], Re[81];
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < ne; ++r) Et[i * ne + r] = E[r * n + i];
+    householder_qr(n, ne, Et, Qe, Re);
+    if (diag_ratio(ne, Re) < 1e-12) return false;
+    // G = R^-T (ne x ne): the constrained part is Q1 G g
+    double G[81];
+    for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < ne; ++j) G[i * ne + j] = i == j ? 1.0 : 0.0;
+    lower_solve_transposed(ne, Re, ne, G);
+    double Q1G[9 * 9];  // n x ne
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < ne; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < ne; ++l) s += Qe[i * n + l] * G[l * ne + j];
+            Q1G[i * ne + j] = s;
+        }
+    if (nz == 0) {
+        std::memcpy(Pe, Q1G, sizeof(double) * n * ne);
+        std::memset(Pl, 0, sizeof(double) * n * nl);
+        return true;
+    }
+    // AQ2 (nl x nz), AQ1G (nl x ne)
+    double AQ2[16 * 9], AQ1G[16 * 9];
+    for (int r = 0; r < nl; ++r) {
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += A[r * n + k] * Qe[k * n + ne + j];
+            AQ2[r * nz + j] = s;
+        }
+        for (int j = 0; j < ne; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += A[r * n + k] * Q1G[k * ne + j];
+            AQ1G[r * ne + j] = s;
+        }
+    }
+    double Qa[256], Ra[81];
+    householder_qr(nl, nz, AQ2, Qa, Ra);
+    if (diag_ratio(nz, Ra) < 1e-12) return false;
+    // Z = Ra^-1 Qa1^T (nz x nl): z = Z (h - AQ1G g)
+    double Z[9 * 16];
+    for (int j = 0; j < nz; ++j)
+        for (int r = 0; r < nl; ++r) Z[j * nl + r] = Qa[r * nl + j];
+    upper_solve(nz, Ra, nl, Z);
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < nl; ++r) {
+            double s = 0.0;
+            for (int j = 0; j < nz; ++j) s += Qe[i * n + ne + j] * Z[j * nl + r];
+            Pl[i * nl + r] = s;
+        }
+        for (int c = 0; c < ne; ++c) {
+            double s = Q1G[i * ne + c];
+            for (int r = 0; r < nl; ++r) s -= Pl[i * nl + r] * AQ1G[r * ne + c];
+            Pe[i * ne + c] = s;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+bool has_wall_face(const gks_mesh& m, int64_t c) {
+    for (int f = 0; f < 4; ++f)
+        if (m.nbr[c * 4 + f] < 0 && m.bkind[m.csr_face[c * 4 + f]] == GKS_BC_NOSLIP_WALL) return true;
+    return false;
+}
+
+// Sec. 4.4: a cell with non-slip adiabatic wall faces reconstructs its
+// momenta by constrained least squares, the wall velocity (zero) imposed on
+// the polynomial at the wall faces -- at each face's centroid for the step-1
+// P1, at its three Gauss points for the step-2 P2 (the unconstrained P2's
+// data, with the wall rows as further equality constraints).  The imposed
+// value is zero, so the result is linear in the stencil data and the cell
+// average Q0:
+//   W1 [3][5]:  b = W1 [dQ_f (4); Q0]
+//   W2 [9][17]: a = W2 [dQ_f (4); grad Q_f (12); Q0]   (zero-mean basis)
+// Used when there are at least 3 neighbours + wall faces, at most 3 wall
+// faces, at most 9 equality rows in step 2 (neighbours + 3 per wall face)
+// and at least 9 rows in all.
+bool cell_wall_stencil(const gks_mesh& m, int64_t c, double* W2, double* W1) {
+    int fl[4], wl[4], nn = 0, nw = 0;
+    double d[4][3];
+    for (int f = 0; f < 4; ++f) {
+        int64_t nb = m.nbr[c * 4 + f];
+        if (nb >= 0) {
+            for (int a = 0; a < 3; ++a)
+                d[nn][a] = (m.cen[nb * 3 + a] + (double)m.nbr_img[(c * 4 + f) * 3 + a] * m.per(c)[a]) -
+                           m.cen[c * 3 + a];
+            fl[nn++] = f;
+        } else if (m.bkind[m.csr_face[c * 4 + f]] == GKS_BC_NOSLIP_WALL) {
+            wl[nw++] = f;
+        }
+    }
+    std::memset(W1, 0, sizeof(double) * 15);
+    std::memset(W2, 0, sizeof(double) * 153);
+    if (nw == 0 || nn + nw < 3 || nw > 3 || nn + 3 * nw > 9 || 4 * nn + 3 * nw < 9) return false;
+    const double h0 = std::cbrt(m.vol[c]);
+    // each wall face's Gauss points relative to the cell centroid
+    double xg[4][3][3];
+    for (int w = 0; w < nw; ++w) {
+        const int64_t fi = m.csr_face[c * 4 + wl[w]];
+        const double* gp = m.csr_sign[c * 4 + wl[w]] > 0 ? &m.gp_l[fi * 9] : &m.gp_r[fi * 9];
+        for (int g = 0; g < 3; ++g)
+            for (int a = 0; a < 3; ++a) xg[w][g][a] = gp[g * 3 + a];
+    }
+    // ---- step 1: unknown y = h0 b; rows scaled by 1 / h0 ------------------
+    {
+        double E[3 * 3], A[4 * 3], Pe[3 * 3], Pl[3 * 4];
+        for (int w = 0; w < nw; ++w)
+            for (int a = 0; a < 3; ++a)
+                E[w * 3 + a] = (xg[w][0][a] + xg[w][1][a] + xg[w][2][a]) / (3.0 * h0);  // the face centroid
+        for (int r = 0; r < nn; ++r)
+            for (int a = 0; a < 3; ++a) A[r * 3 + a] = d[r][a] / h0;
+        if (!constrained_ls(3, nw, E, nn, A, Pe, Pl)) return false;
+        for (int i = 0; i < 3; ++i) {
+            for (int r = 0; r < nn; ++r) W1[i * 5 + fl[r]] = Pl[i * nn + r] / h0;
+            double q0 = 0.0;  // each wall row asks for b . x_w = -Q0
+            for (int w = 0; w < nw; ++w) q0 -= Pe[i * nw + w];
+            W1[i * 5 + 4] = q0 / h0;
+        }
+    }
+    // ---- step 2: unknowns scaled by powers of h0 as the unconstrained P2 ---
+    double sc[9];
+    for (int k = 0; k < 9; ++k) sc[k] = k < 3 ? h0 : h0 * h0;
+    const double* M0 = &m.mom2[c * 6];
+    const int ne = nn + 3 * nw, nl = 3 * nn;
+    double E[9 * 9], A[12 * 9], Pe[9 * 9], Pl[9 * 12];
+    for (int r = 0; r < nn; ++r) {
+        const double* Mn = &m.mom2[m.nbr[c * 4 + fl[r]] * 6];
+        for (int k = 0; k < 3; ++k) E[r * 9 + k] = d[r][k] / sc[k];
+        for (int q = 0; q < 6; ++q)
+            E[r * 9 + 3 + q] = (Mn[q] - M0[q] + d[r][PI_[q]] * d[r][PJ_[q]]) / sc[3 + q];
+        for (int l = 0; l < 3; ++l) {
+            double* row = &A[(3 * r + l) * 9];
+            for (int k = 0; k < 3; ++k) row[k] = (k == l ? h0 : 0.0) / sc[k];
+            for (int q = 0; q < 6; ++q) {
+                double g = (PI_[q] == l ? d[r][PJ_[q]] : 0.0) + (PJ_[q] == l ? d[r][PI_[q]] : 0.0);
+                row[3 + q] = h0 * g / sc[3 + q];
+            }
+        }
+    }
+    for (int w = 0; w < nw; ++w)
+        for (int g = 0; g < 3; ++g) {
+            double* row = &E[(nn + 3 * w + g) * 9];
+            const double* X = xg[w][g];
+            for (int k = 0; k < 3; ++k) row[k] = X[k] / sc[k];
+            for (int q = 0; q < 6; ++q) row[3 + q] = (X[PI_[q]] * X[PJ_[q]] - M0[q]) / sc[3 + q];
+        }
+    if (!constrained_ls(9, ne, E, nl, A, Pe, Pl)) return false;
+    for (int k = 0; k < 9; ++k) {
+        for (int r = 0; r < nn; ++r) {
+            W2[k * 17 + fl[r]] = Pe[k * ne + r] / sc[k];
+            for (int l = 0; l < 3; ++l) W2[k * 17 + 4 + 3 * fl[r] + l] = Pl[k * nl + 3 * r + l] * h0 / sc[k];
+        }
+        double q0 = 0.0;  // each wall row asks for P2(x_g) - Q0 = -Q0
+        for (int w = 0; w < 3 * nw; ++w) q0 -= Pe[k * ne + nn + w];
+        W2[k * 17 + 16] = q0 / sc[k];
+    }
+    return true;
+}
+
+}  // namespace gks

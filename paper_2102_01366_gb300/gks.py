@@ -33,7 +33,7 @@ class gks_params(C.Structure):
                 ("eps_weno", C.c_double), ("tau_eps", C.c_double), ("tau_c", C.c_double),
                 ("prandtl", C.c_double), ("wall_temperature", C.c_double), ("wall_velocity", C.c_double * 3),
                 ("weno", C.c_int32), ("order", C.c_int32), ("smooth_flux", C.c_int32),
-                ("viscous", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("viscous", C.c_int32), ("precision", C.c_int32), ("wall_constraint", C.c_int32)]
 
 
 _lib = None
@@ -71,6 +71,7 @@ def lib():
         "gks_mesh_geometry": (C.c_int32, [_vp] * 9),
         "gks_stencil_build": (C.c_int32, [_vp, _i64p]),
         "gks_mesh_stencils": (C.c_int32, [_vp, _vp, _vp]),
+        "gks_mesh_wall_stencils": (C.c_int32, [_vp, _vp, _vp, _vp, _vp]),
         "gks_workspace_bytes": (C.c_size_t, [_vp, C.POINTER(gks_params)]),
         "gks_state_create": (C.c_int32, [_vp, C.POINTER(gks_params), _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
         "gks_state_destroy": (None, [_vp]),
@@ -116,7 +117,8 @@ def _np_ptr(a):
 
 
 def params(gamma=1.4, cfl=1.0, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, weno=1, order=3,
-           smooth_flux=0, viscous=0, precision=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0)):
+           smooth_flux=0, viscous=0, precision=0, prandtl=1.0, wall_temperature=1.0, wall_velocity=(0.0, 0.0, 0.0),
+           wall_constraint=0):
     p = gks_params()
     lib().gks_params_default(C.byref(p))
     p.gamma, p.cfl, p.mu, p.eps_weno, p.tau_eps, p.tau_c = gamma, cfl, mu, eps_weno, tau_eps, tau_c
@@ -125,6 +127,7 @@ def params(gamma=1.4, cfl=1.0, mu=0.0, eps_weno=1e-8, tau_eps=0.01, tau_c=1.0, w
     for i in range(3):
         p.wall_velocity[i] = float(wall_velocity[i])
     p.weno, p.order, p.smooth_flux, p.viscous, p.precision = weno, order, smooth_flux, viscous, precision
+    p.wall_constraint = wall_constraint
     return p
 
 
@@ -195,6 +198,16 @@ class Mesh:
         M2 = np.zeros((self.nc, 9, 16))
         _call("gks_mesh_stencils", self._h, _np_ptr(M1), _np_ptr(M2))
         return M1, M2
+
+    def wall_stencils(self):
+        """Sec. 4.4 constrained operators of the non-slip wall cells:
+        (W1[nc][3][5], W2[nc][9][17], built[nc]) (gks_mesh_wall_stencils)."""
+        W1 = np.zeros((self.nc, 3, 5))
+        W2 = np.zeros((self.nc, 9, 17))
+        built = np.zeros(self.nc, np.int8)
+        n = C.c_int64()
+        _call("gks_mesh_wall_stencils", self._h, _np_ptr(W1), _np_ptr(W2), _np_ptr(built), C.byref(n))
+        return W1, W2, built
 
 
 def _dptr(t):

@@ -68,6 +68,61 @@ def test_stencils_match_oracle(built, oracle_mod, name):
         assert (np.abs(Mg - Mo) / scale).max() < 1e-10
 
 
+WALL_MESHES = {
+    # one wall plane; cells on the wall have 3 neighbours and 1 wall face
+    "wall_x": lambda: dict(I.box_mesh((3, 3, 3), periodic=(False, True, True), jitter=0.1, seed=6),
+                           bkind=None),
+    # walls on every face of a closed box: edge and corner cells with 2
+    # neighbours and 2 wall faces
+    "closed": lambda: dict(I.box_mesh((3, 3, 3), periodic=(False, False, False), jitter=0.1, seed=7),
+                           bkind=None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WALL_MESHES))
+def test_wall_stencils_match_oracle(built, oracle_mod, name):
+    """The Sec. 4.4 constrained operators of the library (QR null-space
+    method) against the oracle's (Gaussian elimination of the KKT system):
+    the same cells built, the same operators to rounding."""
+    mesh = WALL_MESHES[name]()
+    axes = [a for a in range(3) if not mesh["period"][..., a].any()]
+    mesh["bkind"] = I.boundary_kinds(mesh, {(a, e): I.BC_NOSLIP_WALL for a in axes for e in ("lo", "hi")})
+    g = gks.Mesh(mesh)
+    o = oracle_mod.Mesh(mesh)
+    W1g, W2g, bg = g.wall_stencils()
+    W1o, W2o, bo = o.wall_stencils()
+    np.testing.assert_array_equal(bg, bo)
+    assert bg.sum() > 0
+    for Mg, Mo in ((W1g, W1o), (W2g, W2o)):
+        scale = np.abs(Mo).max(axis=2, keepdims=True) + 1e-300
+        assert (np.abs(Mg - Mo) / scale).max() < 1e-10
+    if name == "closed":
+        top = o.topology()
+        assert ((top["nbr"] < 0).sum(axis=1)[bg == 1] == 2).any()  # two wall faces
+
+
+def test_workspace_grows_only_for_constrained_walls(built):
+    """wall_constraint = 1 adds one slot of constrained operators per cell
+    with a non-slip wall face (168 operator words) plus a slot index per
+    cell, and nothing on a mesh without such faces."""
+    mesh = I.box_mesh((3, 2, 2), periodic=(False, True, True), jitter=0.1, seed=8)
+    plain = gks.Mesh(mesh)
+    walled_mesh = dict(mesh, bkind=I.boundary_kinds(mesh, {(0, "lo"): I.BC_NOSLIP_WALL}))
+    walled = gks.Mesh(walled_mesh)
+    nwall = int(walled.wall_stencils()[2].sum())
+    assert nwall == 8
+    for prec, word in ((0, 8), (1, 4), (2, 8)):
+        def nbytes(g, wc):
+            p = gks.params(precision=prec, wall_constraint=wc)
+            return gks.lib().gks_workspace_bytes(g._h, C.byref(p))
+        assert nbytes(plain, 1) == nbytes(plain, 0)
+        extra = nbytes(walled, 1) - nbytes(walled, 0)
+        assert extra >= 168 * word * nwall + 4 * plain.nc
+        assert extra < 168 * word * nwall + 4 * plain.nc + 512  # two 256-byte alignments
+    p = gks.params(wall_constraint=2)
+    assert gks.lib().gks_workspace_bytes(walled._h, C.byref(p)) == 0  # invalid option
+
+
 def test_rejects_bad_input(built):
     mesh = I.box_mesh((3, 3, 3), jitter=0.1, seed=5)
     bad = dict(mesh)

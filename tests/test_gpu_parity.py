@@ -95,6 +95,25 @@ CASES = {
     "sphere_shell_weno_viscous": (lambda: I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08),
                                   lambda m: I.sine_wave_state(m, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0), p=1 / 1.4),
                                   dict(weno=1, viscous=1, mu=0.01, prandtl=0.72)),
+    # Sec. 4.4 constrained least squares for the momenta of the non-slip wall
+    # cells (wall velocity zero at the wall face centroids in step 1, at the
+    # wall Gauss points in step 2): WENO, linear weights, second order
+    "noslip_box_constrained_weno": (lambda: _noslip(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True),
+                                                               jitter=0.1, seed=46)),
+                                    lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.6, -0.3, 0.2)),
+                                    dict(weno=1, viscous=1, mu=0.01, wall_constraint=1)),
+    "noslip_box_constrained_linear": (lambda: _noslip(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True),
+                                                                 jitter=0.1, seed=47)),
+                                      lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(0.3, 0.4, -0.2)),
+                                      dict(weno=0, viscous=1, mu=0.01, wall_constraint=1)),
+    "noslip_box_constrained_order2": (lambda: _noslip(I.box_mesh((4, 2, 2), (1.0, 0.5, 0.5), (False, True, True),
+                                                                 jitter=0.1, seed=48)),
+                                      lambda m: I.sine_wave_state(m, k=4.0 * math.pi, u=(-0.4, 0.2, 0.3)),
+                                      dict(weno=1, order=2, viscous=1, mu=0.01, wall_constraint=1)),
+    "sphere_shell_constrained_weno": (lambda: I.sphere_shell_mesh(3, 6, 12, 0.5, 1.5, 1.08),
+                                      lambda m: I.sine_wave_state(m, amp=0.2, k=2.0, u=(0.35, 0.15, 0.0),
+                                                                  p=1 / 1.4),
+                                      dict(weno=1, viscous=1, mu=0.01, prandtl=0.72, wall_constraint=1)),
     # both ends fixed to the initial state (inflow state, wave profile)
     "shu_osher_small_weno": (lambda: I.shu_osher_case(nx=20, nyz=2, jitter=0.1)[0],
                              lambda m: I.shu_osher_state(m), dict(weno=1)),
@@ -107,7 +126,7 @@ CASES = {
 # after 10 in the oracle itself (the same run twice, once perturbed; with
 # linear weights it stays at 8e-15), so two implementations can agree to the
 # stated tolerance only over the first steps; those cases compare fewer.
-STEPS = {"sphere_shell_weno_viscous": 4}
+STEPS = {"sphere_shell_weno_viscous": 4, "sphere_shell_constrained_weno": 4}
 
 
 def _walled(mesh):
