@@ -286,8 +286,13 @@ def stage_forms(torch, s, steps, warmup, flush, ms_chosen):
 def adjoint_leg(torch, gks, args):
     """Cost of the adjoint step against the forward step it differentiates:
     the isentropic vortex on the periodic 64^3 x 6 box (1,572,864 cells),
-    FP64, linear weights, the time step frozen.  Both are timed end to end
-    (the adjoint call includes its forward recomputation and host set-up)."""
+    FP64, linear weights, the time step frozen.  Both timed with CUDA events
+    on the state's stream; the forward step's initialisation is outside its
+    timed region, the adjoint call includes the forward recomputation of the
+    step it differentiates.  Then a shortened configuration-4 chain: the
+    gradient through 20 frozen steps (gks.checkpointed_gradient, its default
+    checkpoint spacing) against the 20-step primal run alone, wall clock with
+    the device synchronised on both sides."""
     mesh, W, dW = I.isentropic_vortex_case(n=64, order=2)
     g = gks.Mesh(mesh)
     s = gks.State(g, gks.params(weno=0, cfl=0.5, precision=0))
@@ -305,21 +310,50 @@ def adjoint_leg(torch, gks, args):
         s.sync()
         s.adjoint_step(Wt, dWt, lam_W, lam_dW, dt)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        fn()
+        b.record(s.stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+    fwd, adj = 0.0, 0.0
     for _ in range(reps):
         s.init(Wt, dWt)
-        s.step(1, dt, 0.0)
         s.sync()
-    fwd = (time.perf_counter() - t0) / reps
-    t0 = time.perf_counter()
+        fwd += timed(lambda: s.step(1, dt, 0.0)) / reps
     for _ in range(reps):
-        s.adjoint_step(Wt, dWt, lam_W, lam_dW, dt)
+        adj += timed(lambda: s.adjoint_step(Wt, dWt, lam_W, lam_dW, dt)) / reps
+    out = {"workload": "isentropic vortex (strength 5, Ma 0.5 along the diagonal), periodic [0,10]^3, "
+                       "64^3 hexes x 6 tets = %d cells, FP64, linear weights, dt frozen" % g.nc,
+           "forward_ms": fwd, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
+           "timing": "CUDA events on the state's stream, %d each after warm-up (forward: the step alone; "
+                     "adjoint: its call, which recomputes the step's forward stages)" % reps}
+    # the shortened chain: 20 steps, J = kinetic energy at the end
+    vol = torch.tensor(g.geometry()["vol"], device="cuda")
+    energy = lambda Wc: (vol * (Wc[1:4] ** 2).sum(0) / (2.0 * Wc[0])).sum()
+    nsteps = 20
+    every = gks.checkpoint_interval(g.nc, nsteps)
+    del s
     torch.cuda.synchronize()
-    adj = (time.perf_counter() - t0) / reps
-    return {"workload": "isentropic vortex (strength 5, Ma 0.5 along the diagonal), periodic [0,10]^3, "
-                        "64^3 hexes x 6 tets = %d cells, FP64, linear weights, dt frozen" % g.nc,
-            "forward_ms": fwd * 1e3, "adjoint_ms": adj * 1e3, "adjoint_over_forward": adj / fwd,
-            "timing": "wall clock of the library calls, %d each after warm-up (forward: init + step)" % reps}
+    t0 = time.perf_counter()
+    s = gks.State(g, gks.params(weno=0, cfl=0.5, precision=0))  # as the gradient call creates its state
+    s.init(Wt, dWt)
+    s.step(nsteps, dt, 0.0)
+    s.sync()
+    primal_s = time.perf_counter() - t0
+    del s
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gks.checkpointed_gradient(g, gks.params(weno=0, cfl=0.5, precision=0), Wt, dWt, nsteps, dt, energy)
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    out["chain20"] = {"steps": nsteps, "checkpoint_every": every, "primal_s": primal_s, "gradient_s": grad_s,
+                      "gradient_over_primal": grad_s / primal_s,
+                      "timing": "wall clock, device synchronised; each side includes creating its state "
+                                "(workspace upload) and one initialisation"}
+    return out
 
 
 def adjoint_chain_leg(torch, gks, args):
@@ -400,14 +434,17 @@ def sphere_leg(torch, gks, args, flush):
     faces (the split mirrored in theta on the southern half), WENO,
     started from the free stream.  The first steps are timed
     in FP32 bulk and in FP64 (CUDA events per step, L2 flushed), and the two
-    states are compared after the same steps."""
+    states are compared after the same steps.  The wall cells reconstruct
+    their momenta by the constrained least squares of Sec. 4.4."""
     t0 = time.perf_counter()
     mesh, W, dW, mu = I.sphere_case()
     g = gks.Mesh(mesh)
     setup_s = time.perf_counter() - t0
-    kw = dict(weno=1, cfl=0.5, viscous=1, mu=mu, prandtl=0.72)
+    # the wall cells' momenta by the constrained least squares of Sec. 4.4
+    kw = dict(weno=1, cfl=0.5, viscous=1, mu=mu, prandtl=0.72, wall_constraint=1)
     out = {"workload": "sphere Re 100 Ma 0.2, O-type shell 64 x 96 x 192 hexes x 6 tets (3 on pole rows), "
-                       "r 0.5..20, radial ratio 1.08, flat faces, WENO, viscous (mu 0.002, Pr 0.72), from the free stream",
+                       "r 0.5..20, radial ratio 1.08, flat faces, WENO, viscous (mu 0.002, Pr 0.72), "
+                       "constrained wall reconstruction, from the free stream",
            "cells": g.nc, "faces": g.nf, "boundary_faces": g.n_boundary, "host_setup_s": setup_s}
     states = {}
     for name, prec, steps in (("fp32", 1, max(5, args.steps // 5)), ("fp64", 0, 3)):

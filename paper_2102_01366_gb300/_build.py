@@ -24,7 +24,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 # tolerance against the FP64 oracle.  The cell-update kernels keep IEEE FP32
 # arithmetic.
 FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-FAST_UNITS = ("gks_recon.cu", "gks_flux.cu", "gks_stage.cu")
+FAST_UNITS = ("gks_recon.cu", "gks_flux.cu", "gks_flux_xw.cu", "gks_stage.cu")
 
 
 def _cuda_home():

@@ -528,6 +528,9 @@ static void make_views(gks_state* s, DevMesh<T>& m, DevState<T>& st) {
     m.wslot = L.wslot ? at<int32_t>(s, L.wslot) : nullptr;
     m.wop = L.wslot && !s->ops64 ? at<T>(s, L.wop) : nullptr;
     m.wopd = L.wslot && s->ops64 ? at<double>(s, L.wop) : nullptr;
+    m.xwalls = 0;
+    for (int64_t f = 0; f < s->mesh->nf; ++f)
+        if (s->mesh->bkind[f] == GKS_BC_ISOTHERMAL_WALL || s->mesh->bkind[f] == GKS_BC_MOVING_WALL) m.xwalls = 1;
     st.Wd = at<double>(s, L.Wd);
     st.X = at<T>(s, L.X);
     st.Xs = at<T>(s, L.Xs);

@@ -21,17 +21,6 @@ namespace gks {
 // --------------------------------------------------------------------------
 
 
-template <typename T, int NR, int MINB, bool PRF>
-__global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
-                                                     const T* __restrict__ Wavg,
-                                                     const T* __restrict__ poly,
-                                                     T* __restrict__ rec,
-                                                     const double* __restrict__ ctrl,
-                                                     double dt_override) {
-    __shared__ FluxSmem<T, NR> sm;
-    flux_faces<T, NR, PRF>(m, ph, Wavg, poly, rec, ctrl, dt_override, blockIdx.x, threadIdx.x, sm, 1, 0);
-}
-
 // 3 threads per face, one Gauss point each (used for FP64, whose register
 // footprint leaves no room for the lane-pair split)
 template <typename T, int NR>
@@ -136,23 +125,6 @@ __global__ void __launch_bounds__(3 * FLUX_FACES) k_flux_single(DevMesh<T> m, Ph
 // --------------------------------------------------------------------------
 // launcher
 // --------------------------------------------------------------------------
-template <typename T>
-static Phys<T> make_phys(const HostPhys& p) {
-    Phys<T> ph;
-    ph.gamma = (T)p.gamma;
-    ph.gm1 = (T)(p.gamma - 1.0);
-    ph.K = (T)((5.0 - 3.0 * p.gamma) / (p.gamma - 1.0));
-    ph.tau_eps = (T)p.tau_eps;
-    ph.tau_c = (T)p.tau_c;
-    ph.mu = (T)p.mu;
-    ph.eps_w = (T)p.eps_weno;
-    ph.viscous = p.viscous;
-    ph.smooth = p.smooth;
-    ph.prf = (T)p.prf;
-    ph.twall = (T)p.twall;
-    for (int i = 0; i < 3; ++i) ph.uwall[i] = (T)p.uwall[i];
-    return ph;
-}
 
 
 template <typename T>
@@ -167,17 +139,20 @@ cudaError_t Launch<T>::flux(const DevMesh<T>& m, const HostPhys& p, const T* W, 
         // 1 trades registers for occupancy (3 blocks per SM), variant 0 keeps
         // 2 blocks per SM without spills; the Pr fix has its own instances
         const bool prf = p.prf != 0.0;
+        // meshes with isothermal or moving walls: the instances that carry
+        // their ghosts (gks_flux_xw.cu)
+        if (m.xwalls) return launch_flux_xw(m, ph, W, poly, rec, ctrl, dt_override, stage, s, variant, prf);
         auto go = [&](auto kernel) { kernel<<<grid, 2 * FP_GP, 0, s>>>(m, ph, W, poly, rec, ctrl, dt_override); };
         if (variant == 1) {
             if (stage == 1)
-                prf ? go(k_flux<T, 40, 3, true>) : go(k_flux<T, 40, 3, false>);
+                prf ? go(k_flux<T, 40, 3, true, false>) : go(k_flux<T, 40, 3, false, false>);
             else
-                prf ? go(k_flux<T, 20, 3, true>) : go(k_flux<T, 20, 3, false>);
+                prf ? go(k_flux<T, 20, 3, true, false>) : go(k_flux<T, 20, 3, false, false>);
         } else {
             if (stage == 1)
-                prf ? go(k_flux<T, 40, 2, true>) : go(k_flux<T, 40, 2, false>);
+                prf ? go(k_flux<T, 40, 2, true, false>) : go(k_flux<T, 40, 2, false, false>);
             else
-                prf ? go(k_flux<T, 20, 2, true>) : go(k_flux<T, 20, 2, false>);
+                prf ? go(k_flux<T, 20, 2, true, false>) : go(k_flux<T, 20, 2, false, false>);
         }
     } else {
         if (stage == 1)

@@ -145,8 +145,9 @@ __device__ __forceinline__ void face_flux_deviation(const T (*dv)[FP_GP][15], in
 // sm its shared memory, pair_base the first of the three named barriers of
 // its side pairs, grp_id / 2 FP_GP the barrier of all its threads (0: the
 // whole thread block).  The standalone kernel and the persistent stage
-// kernel both run it.
-template <typename T, int NR, bool PRF>
+// kernel both run it.  XW: the mesh may have isothermal or moving wall
+// faces (their ghosts are compiled only into those instances).
+template <typename T, int NR, bool PRF, bool XW = true>
 __device__ __forceinline__ void flux_faces(const DevMesh<T>& m, const Phys<T>& ph, const T* __restrict__ Wavg,
                                            const T* __restrict__ poly, T* __restrict__ rec,
                                            const double* __restrict__ ctrl, double dt_override, int64_t fb,
@@ -170,8 +171,8 @@ __device__ __forceinline__ void flux_faces(const DevMesh<T>& m, const Phys<T>& p
     // ---- phase 1 ----
     constexpr int XSR = Stride<T>::xs;
     const int mine = side == 0 ? L : Rc;
-    const bool wall =
-        mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL || mine == FLR_ISOTHERMAL_WALL || mine == FLR_MOVING_WALL;
+    const bool wall = mine == FLR_SLIP_WALL || mine == FLR_NOSLIP_WALL ||
+                      (XW && (mine == FLR_ISOTHERMAL_WALL || mine == FLR_MOVING_WALL));
     T Ws[5], gs[3][5];
     // stage 1: the average this side refers to and R - average at the point
     T ahi[5], alo[5], dev[5];
@@ -219,11 +220,13 @@ __device__ __forceinline__ void flux_faces(const DevMesh<T>& m, const Phys<T>& p
     to_local(Rm, Ws, gs, tW, tg);
     if (mine == FLR_SLIP_WALL) slip_wall_ghost(tW, tg);
     if (mine == FLR_NOSLIP_WALL) noslip_wall_ghost(tW, tg);
-    if (mine == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(tW, tg, ph.gm1, ph.twall);
-    if (mine == FLR_MOVING_WALL) {
-        T Uw[3];
-        rotate_vec(Rm, ph.uwall, Uw);
-        moving_wall_ghost(tW, tg, ph.gm1, Uw);
+    if constexpr (XW) {
+        if (mine == FLR_ISOTHERMAL_WALL) isothermal_wall_ghost(tW, tg, ph.gm1, ph.twall);
+        if (mine == FLR_MOVING_WALL) {
+            T Uw[3];
+            rotate_vec(Rm, ph.uwall, Uw);
+            moving_wall_ghost(tW, tg, ph.gm1, Uw);
+        }
     }
     const Prim<T> S = to_prim(tW, ph.gm1);
     Tab<T> t;
@@ -563,5 +566,44 @@ __device__ __forceinline__ void flux_faces(const DevMesh<T>& m, const Phys<T>& p
         }
     }
 }
+
+
+template <typename T>
+inline Phys<T> make_phys(const HostPhys& p) {
+    Phys<T> ph;
+    ph.gamma = (T)p.gamma;
+    ph.gm1 = (T)(p.gamma - 1.0);
+    ph.K = (T)((5.0 - 3.0 * p.gamma) / (p.gamma - 1.0));
+    ph.tau_eps = (T)p.tau_eps;
+    ph.tau_c = (T)p.tau_c;
+    ph.mu = (T)p.mu;
+    ph.eps_w = (T)p.eps_weno;
+    ph.viscous = p.viscous;
+    ph.smooth = p.smooth;
+    ph.prf = (T)p.prf;
+    ph.twall = (T)p.twall;
+    for (int i = 0; i < 3; ++i) ph.uwall[i] = (T)p.uwall[i];
+    return ph;
+}
+
+// the FP32 face-flux launch on a mesh with isothermal or moving wall faces
+// (the instances with their ghosts, in a translation unit of their own)
+cudaError_t launch_flux_xw(const DevMesh<float>& m, const Phys<float>& ph, const float* W, const float* poly,
+                           float* rec, const double* ctrl, double dt_override, int stage, cudaStream_t s,
+                           int variant, bool prf);
+
+// the face-flux kernel (6 threads per face): FLUX_FACES faces per block;
+// MINB resident blocks per SM; PRF the Pr fix; XW isothermal / moving walls
+template <typename T, int NR, int MINB, bool PRF, bool XW>
+__global__ void __launch_bounds__(2 * FP_GP, MINB) k_flux(DevMesh<T> m, Phys<T> ph,
+                                                     const T* __restrict__ Wavg,
+                                                     const T* __restrict__ poly,
+                                                     T* __restrict__ rec,
+                                                     const double* __restrict__ ctrl,
+                                                     double dt_override) {
+    __shared__ FluxSmem<T, NR> sm;
+    flux_faces<T, NR, PRF, XW>(m, ph, Wavg, poly, rec, ctrl, dt_override, blockIdx.x, threadIdx.x, sm, 1, 0);
+}
+
 
 }  // namespace gks

@@ -76,6 +76,7 @@ struct DevMesh {
     const int32_t* wslot;
     const T* wop;
     const double* wopd;
+    int32_t xwalls;        // 1: the mesh has isothermal or moving wall faces
 };
 
 template <typename T>

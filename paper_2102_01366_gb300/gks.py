@@ -507,14 +507,31 @@ def wall_pressure_force(mesh, kinds, gamma=1.4, wall=(1, 3), device="cuda"):
     return force
 
 
-def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=20, primal_precision=0,
+def checkpoint_interval(nc, nsteps, device="cuda", fraction=0.5):
+    """The checkpoint spacing checkpointed_gradient uses by default: 1 (keep
+    every state, no recomputation) when the nsteps FP64 states (160 B a
+    cell) fit in `fraction` of the device's free memory, else the smallest
+    spacing whose checkpoints plus one segment do."""
+    import torch
+    per_state = 160 * int(nc)
+    free = torch.cuda.mem_get_info(torch.device(device))[0] if str(device).startswith("cuda") else 1 << 40
+    budget = fraction * free
+    for every in range(1, max(1, nsteps) + 1):
+        if (nsteps // every + every) * per_state <= budget:
+            return every
+    return max(1, nsteps)
+
+
+def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_every=None, primal_precision=0,
                           device="cuda"):
     """Gradient of loss(W_N) after N steps of frozen step dt with respect to
     the initial (W0, dW0), by the adjoint with checkpointing: the primal run
     keeps every `checkpoint_every`-th state (in FP64, on the device), the
     reverse sweep recomputes each segment from its checkpoint in FP64 and
     applies gks_adjoint_step backwards through it, so the memory is one
-    segment plus the checkpoints.
+    segment plus the checkpoints.  checkpoint_every None: the spacing of
+    checkpoint_interval (every step where the states fit in memory, so that
+    nothing is recomputed beyond what each adjoint step recomputes itself).
 
     loss: a torch function of the final W [5, nc] (FP64 tensor) returning a
     scalar.  primal_precision 1 runs the primal in FP32 bulk (the checkpoints
@@ -540,6 +557,8 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
                         dtype=torch.float64, device=device)
     dW = torch.as_tensor(np.ascontiguousarray(dW0) if isinstance(dW0, np.ndarray) else dW0,
                          dtype=torch.float64, device=device)
+    if checkpoint_every is None:
+        checkpoint_every = checkpoint_interval(mesh.nc, nsteps, device)
     checkpoints = {0: (W.clone(), dW.clone())}
     primal.init(W, dW)
     for n in range(1, nsteps + 1):
@@ -559,10 +578,11 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
         n1 = starts[k + 1] if k + 1 < len(starts) else nsteps
         Wc, dWc = checkpoints[n0]
         segment = [(Wc, dWc)]
-        s64.init(Wc, dWc)
-        for _ in range(n0 + 1, n1):
-            s64.step(1, float(dt), 0.0)
-            segment.append(s64.get())
+        if n1 - n0 > 1:  # (each adjoint step initialises the state itself)
+            s64.init(Wc, dWc)
+            for _ in range(n0 + 1, n1):
+                s64.step(1, float(dt), 0.0)
+                segment.append(s64.get())
         for Ws, dWs in reversed(segment):
             lam_W, lam_dW = s64.adjoint_step(Ws, dWs, lam_W, lam_dW, dt)
     return float(J.detach()), lam_W, lam_dW

@@ -103,6 +103,29 @@ def test_checkpointed_gradient_matches_autograd(monkeypatch, nsteps, every):
     assert sum(1 for k, _ in _FakeState.log if k == "adjoint") == nsteps
 
 
+def test_checkpoint_interval_fits_the_memory_budget():
+    """Every step where all states fit; otherwise the smallest spacing whose
+    checkpoints plus one recomputed segment fit (160 B a cell a state)."""
+    assert gks.checkpoint_interval(1000, 200, device="cpu") == 1
+    nc, n = 1000, 100
+    per = 160 * nc
+    frac = 30.0 * per / (1 << 40)  # room for 30 states (a CPU device reports 2^40 B free)
+    budget = frac * (1 << 40) / per
+    every = gks.checkpoint_interval(nc, n, device="cpu", fraction=frac)
+    assert (n // every + every) <= budget < (n // (every - 1) + every - 1)
+    assert every > 1
+
+
+def test_default_spacing_needs_no_recomputation(monkeypatch):
+    monkeypatch.setattr(gks, "State", _FakeState)
+    _FakeState.log = []
+    W0, dW0 = _inputs()
+    gks.checkpointed_gradient(_mesh(), gks.params(), W0, dW0, 5, 0.05, _loss, device="cpu")
+    # the primal's five steps and five adjoint steps, nothing recomputed
+    assert sum(1 for k, _ in _FakeState.log if k == "step") == 5
+    assert sum(1 for k, _ in _FakeState.log if k == "adjoint") == 5
+
+
 def test_fp32_primal_uses_its_own_state_and_fp64_segments(monkeypatch):
     monkeypatch.setattr(gks, "State", _FakeState)
     _FakeState.log = []
