@@ -401,6 +401,24 @@ gks_status gks_adjoint_step(gks_state* state, double dt, const double* d_W, cons
                             const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
                             double* d_lamdW_out, void* d_scratch, size_t scratch_bytes);
 
+/* The stage state of the last step of an FP64 state (precision 0): W*
+ * [5][nc] and grad W* [15][nc] of the first stage of Eq. s2o4 as that step
+ * computed them (device FP64, the caller's cell order).  GKS_E_UNSUPPORTED on
+ * an FP32-bulk state, GKS_E_STATE when no step has run since the last
+ * initialisation. */
+gks_status gks_get_stage_state(gks_state* state, double* d_Ws, double* d_dWs);
+
+/* gks_adjoint_step given the step's stage state (d_Ws, d_dWs), as
+ * gks_get_stage_state returned it after the step from (d_W, d_dW) with the
+ * same dt on a state of the same mesh and parameters: the forward
+ * recomputation then skips the stage-1 flux and update and takes W*, grad W*
+ * from the caller; everything else, and the result, is that of
+ * gks_adjoint_step.  Same arguments and errors otherwise. */
+gks_status gks_adjoint_step_staged(gks_state* state, double dt, const double* d_W, const double* d_dW,
+                                   const double* d_Ws, const double* d_dWs, const double* d_lamW,
+                                   const double* d_lamdW, double* d_lamW_out, double* d_lamdW_out,
+                                   void* d_scratch, size_t scratch_bytes);
+
 /* ---------------------------------------------------- tuning variants -- */
 
 /* Execution variant of a state (the same arithmetic, only speed differs):

@@ -378,6 +378,7 @@ struct gks_state {
     DevState<float> s32;
     cudaGraphExec_t graph = nullptr;
     bool initialised = false;
+    bool stage_valid = false;  // the stage buffer holds the last step's W*, grad W*
     bool fixed_pinned = false;  // gks_set_fixed_state was called: initialisations keep the fixed state
     int face_order = 0;    // 0: canonical face order, 1: grouped by left cell
     int flux_variant = 1;  // 1: 3 blocks/SM, 0: 2 blocks/SM (FP32 flux)
@@ -796,6 +797,7 @@ static void order_after_caller(gks_state* s) {
 template <typename T>
 static gks_status init_impl(gks_state* s, DevMesh<T>& m, DevState<T>& st, const double* d_W,
                             const double* d_dW) {
+    s->stage_valid = false;
     const int64_t nc = m.nc;
     if (s->dperm())
         GKS_CHECK_CUDA(launch_cells_perm(d_W, st.Wd, nc, 5, s->dperm(), 0, s->stream));
@@ -916,6 +918,7 @@ extern "C" gks_status gks_step(gks_state* s, int32_t nsteps, double dt_fixed, do
     }
     GKS_CHECK_CUDA(set_control(s, dt_fixed, t_end, 0));
     for (int32_t i = 0; i < nsteps; ++i) GKS_CHECK_CUDA(cudaGraphLaunch(s->graph, s->stream));
+    if (nsteps > 0) s->stage_valid = true;
     return GKS_OK;
 }
 
@@ -996,6 +999,7 @@ extern "C" gks_status gks_step_timed(gks_state* s, int32_t nsteps, double dt_fix
     gks_status st = s->fp32 ? step_timed_impl<float>(s, s->m32, s->s32, nsteps, kernel_ms, launches)
                             : step_timed_impl<double>(s, s->m64, s->s64, nsteps, kernel_ms, launches);
     if (st != GKS_OK) return st;
+    if (nsteps > 0) s->stage_valid = true;
     return gks_sync(s);
 }
 
@@ -1179,9 +1183,10 @@ extern "C" size_t gks_adjoint_workspace_bytes(const gks_state* s) {
     return adj_layout(s->mesh->nc, s->mesh->nf).total;
 }
 
-extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_W, const double* d_dW,
-                                       const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
-                                       double* d_lamdW_out, void* d_scratch, size_t scratch_bytes) {
+// d_Ws, d_dWs: the step's stage state from the caller (NULL: recomputed)
+static gks_status adjoint_impl(gks_state* s, double dt, const double* d_W, const double* d_dW, const double* d_Ws,
+                               const double* d_dWs, const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
+                               double* d_lamdW_out, void* d_scratch, size_t scratch_bytes) {
     if (!s || !d_W || !d_dW || !d_lamW || !d_lamdW || !d_lamW_out || !d_lamdW_out || !d_scratch) {
         set_error("gks_adjoint_step: NULL argument");
         return GKS_E_ARG;
@@ -1233,9 +1238,14 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.X, nullptr, nullptr, st.poly, fb, nullptr, st.err,
                                          s->stream));
     GKS_CHECK_CUDA(cudaMemcpyAsync(poly1, st.poly, 8 * POLY_STRIDE * nc, cudaMemcpyDeviceToDevice, s->stream));
-    GKS_CHECK_CUDA(Launch<double>::flux(m, s->phys, st.X, st.poly, st.rec, st.case_dt, 0.0, 1, s->stream,
-                                        s->flux_variant));
-    GKS_CHECK_CUDA(Launch<double>::update1(m, s->phys, st, s->stream));
+    if (d_Ws) {
+        // the caller's stage state in place of the stage-1 flux and update
+        GKS_CHECK_CUDA(Launch<double>::pack(d_Ws, d_dWs, st.Xs, nc, s->stream));
+    } else {
+        GKS_CHECK_CUDA(Launch<double>::flux(m, s->phys, st.X, st.poly, st.rec, st.case_dt, 0.0, 1, s->stream,
+                                            s->flux_variant));
+        GKS_CHECK_CUDA(Launch<double>::update1(m, s->phys, st, s->stream));
+    }
     GKS_CHECK_CUDA(Launch<double>::recon(m, s->phys, st.Xs, nullptr, nullptr, st.poly, fb + nc, nullptr, st.err,
                                          s->stream));
     AdjBuffers b;
@@ -1256,6 +1266,31 @@ extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_
     b.fallback = fb;
     GKS_CHECK_CUDA(adjoint_reverse(m, s->phys, dt, b, st.X, st.Xs, d_lamW, d_lamdW, d_lamW_out, d_lamdW_out,
                                    s->stream));
+    return gks_sync(s);
+}
+
+extern "C" gks_status gks_adjoint_step(gks_state* s, double dt, const double* d_W, const double* d_dW,
+                                       const double* d_lamW, const double* d_lamdW, double* d_lamW_out,
+                                       double* d_lamdW_out, void* d_scratch, size_t scratch_bytes) {
+    return adjoint_impl(s, dt, d_W, d_dW, nullptr, nullptr, d_lamW, d_lamdW, d_lamW_out, d_lamdW_out, d_scratch,
+                        scratch_bytes);
+}
+
+extern "C" gks_status gks_adjoint_step_staged(gks_state* s, double dt, const double* d_W, const double* d_dW,
+                                              const double* d_Ws, const double* d_dWs, const double* d_lamW,
+                                              const double* d_lamdW, double* d_lamW_out, double* d_lamdW_out,
+                                              void* d_scratch, size_t scratch_bytes) {
+    if (!d_Ws || !d_dWs) { set_error("gks_adjoint_step_staged: NULL stage state"); return GKS_E_ARG; }
+    return adjoint_impl(s, dt, d_W, d_dW, d_Ws, d_dWs, d_lamW, d_lamdW, d_lamW_out, d_lamdW_out, d_scratch,
+                        scratch_bytes);
+}
+
+extern "C" gks_status gks_get_stage_state(gks_state* s, double* d_Ws, double* d_dWs) {
+    if (!s || !d_Ws || !d_dWs) { set_error("gks_get_stage_state: NULL argument"); return GKS_E_ARG; }
+    if (s->fp32) { set_error("gks_get_stage_state: FP64 states only"); return GKS_E_UNSUPPORTED; }
+    if (!s->stage_valid) { set_error("gks_get_stage_state: no step since the initialisation"); return GKS_E_STATE; }
+    GKS_CHECK_CUDA(launch_unpack_avg(s->s64.Xs, d_Ws, s->mesh->nc, s->stream));
+    GKS_CHECK_CUDA(Launch<double>::unpack_grad(s->s64.Xs, d_dWs, s->mesh->nc, s->stream));
     return gks_sync(s);
 }
 

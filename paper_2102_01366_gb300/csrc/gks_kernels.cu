@@ -15,6 +15,8 @@
 // exact).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gks_update.cuh"
 
 namespace gks {
@@ -121,6 +123,21 @@ __global__ void k_unpack_grad(const T* __restrict__ X, double* __restrict__ dW, 
         const int64_t j = i / nc, d = i - j * nc;
         dW[j * nc + (cperm ? (int64_t)cperm[d] : d)] = (double)X[d * Stride<T>::xs + 5 + j];
     }
+}
+
+// the averages of an FP64 working state [nc][XS] to W [5][nc]
+__global__ void k_unpack_avg(const double* __restrict__ X, double* __restrict__ W, int64_t nc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc * 5; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i / nc, c = i - q * nc;
+        W[q * nc + c] = X[c * Stride<double>::xs + q];
+    }
+}
+
+cudaError_t launch_unpack_avg(const double* X, double* W, int64_t nc, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((5 * nc + 255) / 256, 65535);
+    k_unpack_avg<<<(unsigned)blocks, 256, 0, s>>>(X, W, nc);
+    return cudaGetLastError();
 }
 
 // component-major [ncomp][nc] arrays between the device cell order and the

@@ -88,6 +88,9 @@ def lib():
         "gks_adjoint_workspace_bytes": (C.c_size_t, [_vp]),
         "gks_set_fixed_state": (C.c_int32, [_vp, _vp, _vp]),
         "gks_adjoint_step": (C.c_int32, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
+        "gks_adjoint_step_staged": (C.c_int32, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                C.c_size_t]),
+        "gks_get_stage_state": (C.c_int32, [_vp, _vp, _vp]),
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
         "gks_debug_wait_timeout": (C.c_int32, [_vp, C.c_int32]),
@@ -313,21 +316,36 @@ class State:
         self.stream.wait_stream(t.cuda.current_stream(self.device))
         _call("gks_set_fixed_state", self._h, *[_dptr(x) for x in args])
 
-    def adjoint_step(self, W, dW, lamW, lamdW, dt):
+    def stage_state(self):
+        """(W*, grad W*) of the last step's first stage (gks_get_stage_state;
+        FP64 states)."""
+        t = self.torch
+        Ws = t.empty((5, self.mesh.nc), dtype=t.float64, device=self.device)
+        dWs = t.empty((15, self.mesh.nc), dtype=t.float64, device=self.device)
+        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        _call("gks_get_stage_state", self._h, _dptr(Ws), _dptr(dWs))
+        return Ws, dWs
+
+    def adjoint_step(self, W, dW, lamW, lamdW, dt, stage=None):
         """Adjoint of one step at (W, dW) with the frozen step dt
         (gks_adjoint_step): returns d J / d (W, dW) given d J / d (W', dW') of
         the step's result.  All [5|15, nc] float64 CUDA tensors; the state is
-        left initialised at (W, dW)."""
+        left initialised at (W, dW).  stage: the step's (W*, grad W*) from
+        stage_state() after that step (gks_adjoint_step_staged: the same
+        result without recomputing the first stage's flux and update)."""
         t = self.torch
         args = [t.as_tensor(x, dtype=t.float64, device=self.device).contiguous() for x in (W, dW, lamW, lamdW)]
+        if stage is not None:
+            args = args[:2] + [t.as_tensor(x, dtype=t.float64, device=self.device).contiguous()
+                               for x in stage] + args[2:]
         oW = t.empty((5, self.mesh.nc), dtype=t.float64, device=self.device)
         odW = t.empty((15, self.mesh.nc), dtype=t.float64, device=self.device)
         nbytes = lib().gks_adjoint_workspace_bytes(self._h)
         if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nbytes:
             self._adj_ws = t.empty(nbytes, dtype=t.uint8, device=self.device)
         self.stream.wait_stream(t.cuda.current_stream(self.device))
-        _call("gks_adjoint_step", self._h, float(dt), *[_dptr(x) for x in args], _dptr(oW), _dptr(odW),
-              _dptr(self._adj_ws), nbytes)
+        _call("gks_adjoint_step" if stage is None else "gks_adjoint_step_staged", self._h, float(dt),
+              *[_dptr(x) for x in args], _dptr(oW), _dptr(odW), _dptr(self._adj_ws), nbytes)
         return oW, odW
 
     def step_host(self, W_host, dW_host, nsteps=1, dt_fixed=0.0, W_out=None, dW_out=None):
@@ -507,13 +525,14 @@ def wall_pressure_force(mesh, kinds, gamma=1.4, wall=(1, 3), device="cuda"):
     return force
 
 
-def checkpoint_interval(nc, nsteps, device="cuda", fraction=0.5):
+def checkpoint_interval(nc, nsteps, device="cuda", fraction=0.5, per_cell=160):
     """The checkpoint spacing checkpointed_gradient uses by default: 1 (keep
-    every state, no recomputation) when the nsteps FP64 states (160 B a
-    cell) fit in `fraction` of the device's free memory, else the smallest
-    spacing whose checkpoints plus one segment do."""
+    every state, no recomputation) when the nsteps saved states (per_cell
+    bytes a cell each: 160 for an FP64 state, 320 with its stage state) fit
+    in `fraction` of the device's free memory, else the smallest spacing
+    whose checkpoints plus one segment do."""
     import torch
-    per_state = 160 * int(nc)
+    per_state = int(per_cell) * int(nc)
     free = torch.cuda.mem_get_info(torch.device(device))[0] if str(device).startswith("cuda") else 1 << 40
     budget = fraction * free
     for every in range(1, max(1, nsteps) + 1):
@@ -532,6 +551,9 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
     segment plus the checkpoints.  checkpoint_every None: the spacing of
     checkpoint_interval (every step where the states fit in memory, so that
     nothing is recomputed beyond what each adjoint step recomputes itself).
+    With every step kept and an FP64 primal, each step's stage state (W*,
+    grad W*) is kept as well and handed to the adjoint step, which then
+    skips the first stage's flux and update (the gradient is unchanged).
 
     loss: a torch function of the final W [5, nc] (FP64 tensor) returning a
     scalar.  primal_precision 1 runs the primal in FP32 bulk (the checkpoints
@@ -558,11 +580,15 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
     dW = torch.as_tensor(np.ascontiguousarray(dW0) if isinstance(dW0, np.ndarray) else dW0,
                          dtype=torch.float64, device=device)
     if checkpoint_every is None:
-        checkpoint_every = checkpoint_interval(mesh.nc, nsteps, device)
+        checkpoint_every = checkpoint_interval(mesh.nc, nsteps, device, per_cell=160 if primal_precision else 320)
+    staged = checkpoint_every == 1 and not primal_precision
+    stages = {}
     checkpoints = {0: (W.clone(), dW.clone())}
     primal.init(W, dW)
     for n in range(1, nsteps + 1):
         primal.step(1, float(dt), 0.0)
+        if staged:
+            stages[n - 1] = primal.stage_state()
         if n % checkpoint_every == 0 and n < nsteps:
             checkpoints[n] = primal.get()
     primal.sync()
@@ -584,5 +610,8 @@ def checkpointed_gradient(mesh, params, W0, dW0, nsteps, dt, loss, checkpoint_ev
                 s64.step(1, float(dt), 0.0)
                 segment.append(s64.get())
         for Ws, dWs in reversed(segment):
-            lam_W, lam_dW = s64.adjoint_step(Ws, dWs, lam_W, lam_dW, dt)
+            if staged:
+                lam_W, lam_dW = s64.adjoint_step(Ws, dWs, lam_W, lam_dW, dt, stage=stages.pop(n0))
+            else:
+                lam_W, lam_dW = s64.adjoint_step(Ws, dWs, lam_W, lam_dW, dt)
     return float(J.detach()), lam_W, lam_dW

@@ -488,3 +488,36 @@ def test_checkpointed_gradient(cuda):
     J3, gW3, _ = gks.checkpointed_gradient(g, p, W, dW, 6, dt, loss, checkpoint_every=2, primal_precision=1)
     assert abs(J3 - J1) < 1e-5 * abs(J1)
     assert float((gW3 - gW1).abs().max() / gW1.abs().max()) < 1e-3
+
+
+@pytest.mark.parametrize("kw", [dict(weno=1), dict(weno=0, order=2),
+                                dict(weno=1, viscous=1, mu=0.01, prandtl=0.72)])
+def test_staged_adjoint_step_equals_the_recomputing_one(cuda, kw):
+    """The adjoint step given its step's stage state (W*, grad W*) from the
+    primal skips the first stage's flux and update and returns the same
+    adjoint to the bit; stage_state() is defined only after a step of an
+    FP64 state."""
+    torch = cuda
+    mesh, W, dW, _ = _case(seed=66, state="noslip")
+    g = gks.Mesh(mesh)
+    s = gks.State(g, gks.params(cfl=0.5, **kw))
+    s.init(W, dW)
+    with pytest.raises(gks.GksError) as e:
+        s.stage_state()  # no step yet
+    assert e.value.status == -4  # GKS_E_STATE
+    dt = s.timestep()
+    s.step(1, dt, 0.0)
+    stage = s.stage_state()
+    Wt, dWt = torch.tensor(W, device="cuda"), torch.tensor(dW, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    lW = torch.randn((5, g.nc), generator=gen, device="cuda", dtype=torch.float64)
+    ldW = torch.randn((15, g.nc), generator=gen, device="cuda", dtype=torch.float64)
+    a = s.adjoint_step(Wt, dWt, lW, ldW, dt)
+    b = s.adjoint_step(Wt, dWt, lW, ldW, dt, stage=stage)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    s32 = gks.State(g, gks.params(cfl=0.5, precision=1, **kw))
+    s32.init(W, dW)
+    s32.step(1)
+    with pytest.raises(gks.GksError) as e:
+        s32.stage_state()
+    assert e.value.status == -8  # GKS_E_UNSUPPORTED

@@ -40,7 +40,12 @@ class _FakeState:
     def step(self, n, dt, t_end):
         for _ in range(n):
             _FakeState.log.append(("step", self.precision))
+            # the stand-in's "stage state": a marker of the step's input
+            self.stage = (self.W + 100.0, self.dW - 100.0)
             self.W, self.dW = _f(self.W, self.dW, dt)
+
+    def stage_state(self):
+        return self.stage[0].clone(), self.stage[1].clone()
 
     def get(self):
         return self.W.clone(), self.dW.clone()
@@ -48,8 +53,12 @@ class _FakeState:
     def sync(self):
         pass
 
-    def adjoint_step(self, Ws, dWs, lam_W, lam_dW, dt):
+    def adjoint_step(self, Ws, dWs, lam_W, lam_dW, dt, stage=None):
         _FakeState.log.append(("adjoint", self.precision))
+        if stage is not None:
+            # the stage state handed over belongs to this very step
+            _FakeState.log.append(("staged", self.precision))
+            assert torch.equal(stage[0], Ws + 100.0) and torch.equal(stage[1], dWs - 100.0)
         with torch.enable_grad():  # also when called from a backward pass
             W = Ws.clone().requires_grad_(True)
             dW = dWs.clone().requires_grad_(True)
@@ -121,9 +130,11 @@ def test_default_spacing_needs_no_recomputation(monkeypatch):
     _FakeState.log = []
     W0, dW0 = _inputs()
     gks.checkpointed_gradient(_mesh(), gks.params(), W0, dW0, 5, 0.05, _loss, device="cpu")
-    # the primal's five steps and five adjoint steps, nothing recomputed
+    # the primal's five steps and five adjoint steps, nothing recomputed; each
+    # adjoint step gets its own step's stage state
     assert sum(1 for k, _ in _FakeState.log if k == "step") == 5
     assert sum(1 for k, _ in _FakeState.log if k == "adjoint") == 5
+    assert sum(1 for k, _ in _FakeState.log if k == "staged") == 5
 
 
 def test_fp32_primal_uses_its_own_state_and_fp64_segments(monkeypatch):
