@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_point_rev(DevMesh<double> m
 // mirror is its own transpose; the isothermal and moving walls' ghost
 // Jacobians are transposed at the interior state); an open side's goes to the interior cell's average,
 // lwo[f][5] (zero on every other face).
+// XW: the mesh has isothermal or moving wall faces, whose ghosts' Jacobians
+// (and the local frame they need) only those instances carry
+template <bool XW>
 __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx, double* __restrict__ lpf,
                                 double* __restrict__ lwo, const double* __restrict__ poly, Phys<double> ph) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,7 +304,7 @@ __global__ void k_adj_face_back(DevMesh<double> m, const double* __restrict__ lx
                 for (int q = 0; q < 5; ++q) lw[q] += lW[q];
             } else if (cell == FLR_FIXED) {
                 // a set fixed state is a constant of the step: nothing flows back
-            } else if (cell == FLR_ISOTHERMAL_WALL || cell == FLR_MOVING_WALL) {
+            } else if (XW && (cell == FLR_ISOTHERMAL_WALL || cell == FLR_MOVING_WALL)) {
                 // the interior state at the point, face frame, then the ghost's transpose
                 const int src_side = 1 - side;
                 const int64_t c = side == 0 ? R : L;
@@ -855,7 +858,10 @@ static void flux_back(const DevMesh<double>& m, const Phys<double>& ph, const Ad
     else
         k_adj_point_rev<NR, false><<<grid_of(m.nf * 3, ADJ_THREADS), ADJ_THREADS, 0, s>>>(m, ph, poly, X, b.src, dt,
                                                                                         b.lx);
-    k_adj_face_back<<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph);
+    if (m.xwalls)
+        k_adj_face_back<true><<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph);
+    else
+        k_adj_face_back<false><<<grid_of(m.nf, B), B, 0, s>>>(m, b.lx, b.lpf, b.lwo, poly, ph);
     k_adj_gather_poly<<<grid_of(m.nc, B), B, 0, s>>>(m, b.lpf, b.lp);
 }
 
