@@ -513,6 +513,14 @@ gks_status gks_debug_face_records(gks_state* state, double dt, int32_t stage, do
  * flag so that the state stays usable.  Synchronises.  For tests. */
 gks_status gks_debug_wait_timeout(gks_state* state, int32_t tries);
 
+/* The same for the one-launch stage's grid-wide barrier (gks_state_set_fused):
+ * two blocks wait on a barrier that no arrival can complete, each polling
+ * `tries` times (0..65536) before it gives up and sets the error flag, as a
+ * stage whose blocks were not all resident would.  Returns what the next
+ * synchronisation reports (GKS_E_TIMEOUT), then clears the flag.  Any
+ * precision.  Synchronises.  For tests. */
+gks_status gks_debug_grid_barrier_timeout(gks_state* state, int32_t tries);
+
 /* Last error message of this thread ("" if none). */
 const char* gks_last_error(void);
 

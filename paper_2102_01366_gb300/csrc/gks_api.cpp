@@ -1367,6 +1367,21 @@ extern "C" gks_status gks_debug_wait_timeout(gks_state* s, int32_t tries) {
     return st;
 }
 
+extern "C" gks_status gks_debug_grid_barrier_timeout(gks_state* s, int32_t tries) {
+    if (!s) { set_error("gks_debug_grid_barrier_timeout: state is NULL"); return GKS_E_ARG; }
+    if (tries < 0 || tries > (1 << 16)) {
+        set_error("gks_debug_grid_barrier_timeout: tries must be in [0, 65536]");
+        return GKS_E_ARG;
+    }
+    int32_t* err = s->fp32 ? s->s32.err : s->s64.err;
+    order_after_caller(s);
+    GKS_CHECK_CUDA(launch_grid_barrier_probe(reinterpret_cast<unsigned*>(s->ws + s->L.gbar), err, tries, s->stream));
+    const gks_status st = gks_sync(s);
+    GKS_CHECK_CUDA(cudaMemsetAsync(err, 0, 4, s->stream));  // the state stays usable
+    GKS_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    return st;
+}
+
 // ------------------------------------------------------------- variants --
 
 extern "C" gks_status gks_state_set_variant(gks_state* s, int32_t face_order, int32_t flux_blocks,

@@ -208,6 +208,9 @@ cudaError_t launch_cells_perm(const double* in, double* out, int64_t nc, int nco
 // out row r = in row map[r] for rows of width_words 4-byte words
 cudaError_t launch_rows_gather(const void* in, void* out, int64_t nrows, int width_words, const int32_t* map,
                                cudaStream_t s);
+// the one-launch stage's grid barrier on a barrier nothing completes: each
+// of two blocks polls `limit` times, gives up and sets ERR_TIMEOUT
+cudaError_t launch_grid_barrier_probe(unsigned* gbar, int32_t* err, int limit, cudaStream_t s);
 // the averages W [5][nc] of an FP64 working state X [nc][XS]
 cudaError_t launch_unpack_avg(const double* X, double* W, int64_t nc, cudaStream_t s);
 // one stage of the FP32-bulk step (reconstruction with the neighbours'

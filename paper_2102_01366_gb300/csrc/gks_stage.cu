@@ -31,8 +31,8 @@ constexpr int GRID_TRIES = 1 << 23;
 
 // Bounded grid-wide barrier: the last block to arrive resets the count and
 // advances the generation the others wait on.  Returns false (and sets
-// ERR_TIMEOUT) if this block gave up waiting.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* err) {
+// ERR_TIMEOUT) if this block gave up waiting after `limit` polls.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* err, int limit = GRID_TRIES) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -46,7 +46,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* err) {
             atomicAdd(gen, 1u);
         } else {
             for (int tries = 0; *vgen == g0; ++tries) {
-                if (tries > GRID_TRIES) {
+                if (tries >= limit) {
                     ok = 0;
                     atomicOr(err, ERR_TIMEOUT);
                     break;
@@ -59,6 +59,24 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* err) {
     }
     __syncthreads();
     return ok_s != 0;
+}
+
+// The grid barrier's failure path without a fault: the count word starts
+// far from the value the last arrival would make it equal to the grid size,
+// so no block releases the others; each polls `limit` times, gives up, sets
+// ERR_TIMEOUT and returns.  Nothing else is touched.
+__global__ void k_grid_barrier_probe(unsigned* gbar, int32_t* err, int limit) {
+    grid_barrier(gbar, gbar + 1, err, limit);
+}
+
+cudaError_t launch_grid_barrier_probe(unsigned* gbar, int32_t* err, int limit, cudaStream_t s) {
+    // count = generation = 0x80808080: two arrivals bring the count to
+    // 0x80808082, never to the grid size 2
+    cudaError_t e = cudaMemsetAsync(gbar, 0x80, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_grid_barrier_probe<<<2, 32, 0, s>>>(gbar, err, limit);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), s);
 }
 
 template <int NR>

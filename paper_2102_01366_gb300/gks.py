@@ -94,6 +94,7 @@ def lib():
         "gks_debug_reconstruct": (C.c_int32, [_vp, _vp, _vp, _vp]),
         "gks_debug_face_records": (C.c_int32, [_vp, C.c_double, C.c_int32, _vp]),
         "gks_debug_wait_timeout": (C.c_int32, [_vp, C.c_int32]),
+        "gks_debug_grid_barrier_timeout": (C.c_int32, [_vp, C.c_int32]),
         "gks_state_set_variant": (C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32]),
         "gks_state_set_fused": (C.c_int32, [_vp, C.c_int32]),
         "gks_state_get_fused": (C.c_int32, [_vp, _vp]),
@@ -465,6 +466,11 @@ class State:
     def debug_wait_timeout(self, tries=8):
         """Status of a bounded device wait that gives up (gks_debug_wait_timeout)."""
         return lib().gks_debug_wait_timeout(self._h, int(tries))
+
+    def debug_grid_barrier_timeout(self, tries=8):
+        """Status of the one-launch stage's grid barrier giving up
+        (gks_debug_grid_barrier_timeout)."""
+        return lib().gks_debug_grid_barrier_timeout(self._h, int(tries))
 
     def debug_face_records(self, dt, stage):
         t = self.torch

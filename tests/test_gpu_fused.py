@@ -199,3 +199,27 @@ def test_fused_stage_only_for_precision_1(cuda, precision):
     assert s.fused() == 0
     s1 = gks.State(gks.Mesh(mesh), gks.params(precision=1, **kw))
     assert gks.lib().gks_state_set_fused(s1._h, 2) == -1
+
+
+def test_grid_barrier_gives_up_with_a_status_and_the_state_stays_usable(cuda):
+    """The failure path of the one-launch stage's bounded grid barrier,
+    without a GPU fault: two blocks wait on a barrier that no arrival can
+    complete, give up after their polls, the device error flag reaches the
+    host as GKS_E_TIMEOUT with its message, and the same state then steps
+    (fused) exactly as a fresh one."""
+    mesh, W, dW, kw = _case("sod")
+    g = gks.Mesh(mesh)
+    ref, t0, _, _ = _run(g, W, dW, kw, True, nsteps=2)
+    s = gks.State(g, gks.params(precision=1, **kw))
+    s.set_fused(True)
+    s.init(W, dW)
+    for tries in (0, 8, 4096):
+        assert s.debug_grid_barrier_timeout(tries) == -6  # GKS_E_TIMEOUT
+        assert b"grid barrier" in gks.lib().gks_last_error()
+    assert gks.lib().gks_debug_grid_barrier_timeout(s._h, 1 << 17) == -1  # GKS_E_ARG: too many polls
+    s.init(W, dW)
+    s.step(2)
+    s.sync()
+    for a, b in zip(ref, [x.cpu() for x in s.get()]):
+        assert cuda.equal(a, b)
+    np.testing.assert_array_equal(s.case_times()[0], t0)
