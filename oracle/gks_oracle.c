@@ -1717,8 +1717,8 @@ int ora_step(const ora_mesh* m, const ora_params* p, double* W, double* dW,
     if (dt_used) *dt_used = dt;
     double* rec1 = (double*)malloc(sizeof(double) * nf * 40);
     double* rec2 = (double*)malloc(sizeof(double) * nf * 20);
-    double* Ws = (double*)malloc(sizeof(double) * nc * 5);
-    double* dWs = (double*)malloc(sizeof(double) * nc * 15);
+    double* Ws = (double*)calloc((size_t)nc * 5, sizeof(double));
+    double* dWs = (double*)calloc((size_t)nc * 15, sizeof(double));
     double* S = (double*)malloc(sizeof(double) * nc * 5);
     double* G = (double*)malloc(sizeof(double) * nc * 15);
     if (ora_face_records(m, p, W, dW, dt, 1, rec1) != 0) {

@@ -466,10 +466,14 @@ static std::vector<int32_t> cell_permutation(const gks_mesh& g, int order) {
                         const int64_t m = g.nbr[c * 4 + f];
                         if (m >= c0 && m < c1 && !vis[m - c0] && !(emit && seen[m - c0])) nb[k++] = m;
                     }
-                    std::sort(nb, nb + k, [&](int64_t a, int64_t b) {
+                    // by increasing degree, then id (a total order): insertion
+                    // sort of the at most 4 candidates
+                    auto before = [&](int64_t a, int64_t b) {
                         const int da = deg(a), db = deg(b);
                         return da != db ? da < db : a < b;
-                    });
+                    };
+                    for (int i = 1; i < k; ++i)
+                        for (int j = i; j > 0 && before(nb[j], nb[j - 1]); --j) std::swap(nb[j], nb[j - 1]);
                     for (int i = 0; i < k; ++i) {
                         if (vis[nb[i] - c0]) continue;
                         vis[nb[i] - c0] = 1;

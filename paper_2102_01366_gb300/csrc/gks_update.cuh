@@ -62,7 +62,6 @@ __device__ __forceinline__ void update1_cells(const DevMesh<T>& m, const HostPhy
     fh.init();
     s1.init();
     T gs[3] = {T(0), T(0), T(0)}, g0[3] = {T(0), T(0), T(0)};
-#pragma unroll
     constexpr int RS = sizeof(T) == 4 ? REC1_F32 : 40;
     for (int f = 0; f < 4; ++f) {
         const int e = m.cface[f * nc + c];
